@@ -1,0 +1,199 @@
+"""Particle-mesh gravity in FP64 on the CPU (test infrastructure only).
+
+Restates, step by step and without blocking or fusion, the PM force of Sec. 4.1 of arXiv 2405.12913 ("the
+most computationally expensive operation ... calculate grad phi via the FFT") and the particle leapfrog that
+``nbody_reverse_step`` of Alg. 1 stands for:
+
+  * mesh nodes sit at j * cell, j = 0..N-1, periodic; arrays are indexed [ix, iy, iz] with iz fastest;
+  * CIC (cloud-in-cell, trilinear) deposit: a particle at u = x / cell gives weight (1 - f) to node
+    floor(u) and f to node floor(u) + 1 along each axis; each particle carries N_mesh^3 / N_particles, so
+    the mesh holds rho / rho_mean = 1 + delta;
+  * Poisson (Sec. 2):  lap phi = pref * delta, so phi_k = -pref * delta_k / k^2 with phi_0 = 0;
+    pref = (3/2) Omega_m / a in the expanding case and 4 pi G rho_mean in the static point-mass case;
+  * gradient: (d_j phi)_k = i k_j phi_k * prod_i sinc(k_i cell / 2)^-p * exp(-k^2 sigma^2 / 2), the CIC
+    deconvolution and the Gaussian smoothing of the kick operator of Sec. 4.2 taken on the 3D mesh (power
+    p per axis, smoothing length sigma in comoving units, the decaying sign of the Gaussian); the signed
+    frequency n_i lies in [-N/2, N/2), k_i = 2 pi n_i / L, and the derivative factor i k_j is set to 0 on
+    the j-Nyquist plane so that the gradient is real;
+  * the same CIC weights interpolate the three gradient fields back to the particles;
+  * leapfrog with one force per step: p <- p - grad phi(x) * K, then x <- x + p * D, with K and D the signed
+    time integrals of ``cosmology``; positions are kept as displacements from the Lagrangian lattice;
+  * Zel'dovich initial conditions: delta_k = w_k sqrt(P(k) / V_cell), Psi_k = i k delta_k / k^2 (0 on the
+    Nyquist planes), x = q + D1 Psi, p = a^2 E f D1 Psi.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+import torch
+
+from . import cosmology as cosmo
+
+_CORNERS = list(itertools.product((0, 1), repeat=3))
+
+
+def lattice(n_side: int, box: float) -> torch.Tensor:
+    """Lagrangian lattice q = (i, j, k) * box / n_side, particle index (i*n + j)*n + k; shape (n^3, 3)."""
+    g = torch.arange(n_side, dtype=torch.float64) * (box / n_side)
+    qx, qy, qz = torch.meshgrid(g, g, g, indexing="ij")
+    return torch.stack([qx.reshape(-1), qy.reshape(-1), qz.reshape(-1)], dim=1)
+
+
+def _cic_parts(x: torch.Tensor, box: float, n_mesh: int):
+    """Lower-node indices and fractional offsets of positions x (n, 3), wrapped into the periodic box."""
+    cell = box / n_mesh
+    u = torch.remainder(x, box) / cell
+    i0 = torch.floor(u)
+    f = u - i0
+    i0 = i0.to(torch.int64) % n_mesh
+    return i0, f
+
+
+def cic_deposit(x: torch.Tensor, box: float, n_mesh: int, mass: float | None = None) -> torch.Tensor:
+    """Mesh of rho / rho_mean from particle positions x (n, 3); each particle carries ``mass`` (default
+    n_mesh^3 / n so that the mean is 1)."""
+    n = x.shape[0]
+    if mass is None:
+        mass = n_mesh ** 3 / n
+    x = x.to(torch.float64)
+    i0, f = _cic_parts(x, box, n_mesh)
+    rho = torch.zeros(n_mesh ** 3, dtype=torch.float64)
+    for a, b, c in _CORNERS:
+        w = (f[:, 0] if a else 1 - f[:, 0]) * (f[:, 1] if b else 1 - f[:, 1]) * (f[:, 2] if c else 1 - f[:, 2])
+        idx = (((i0[:, 0] + a) % n_mesh) * n_mesh + (i0[:, 1] + b) % n_mesh) * n_mesh + (i0[:, 2] + c) % n_mesh
+        rho.index_add_(0, idx, w * mass)
+    return rho.reshape(n_mesh, n_mesh, n_mesh)
+
+
+def signed_freq(n: int) -> torch.Tensor:
+    """Signed integer frequencies of a length-n FFT axis, in [-n/2, n/2)."""
+    return torch.fft.fftfreq(n, d=1.0 / n).round().to(torch.int64)
+
+
+def _wavevectors(n_mesh: int, box: float):
+    """Integer frequencies (nx, ny, nz) of the rfftn half spectrum, broadcastable, z axis non-negative.
+
+    The z axis of rfftn keeps n_z = 0..N/2; n_z = N/2 is the Nyquist frequency and counts as -N/2 (its
+    sinc factor is the same and its derivative factor is zero)."""
+    nx = signed_freq(n_mesh).view(-1, 1, 1)
+    ny = signed_freq(n_mesh).view(1, -1, 1)
+    nz = torch.arange(n_mesh // 2 + 1, dtype=torch.int64).view(1, 1, -1)
+    return nx, ny, nz
+
+
+def sinc(x: torch.Tensor) -> torch.Tensor:
+    """sin(x) / x with sinc(0) = 1."""
+    safe = torch.where(x == 0, torch.ones_like(x), x)
+    return torch.where(x == 0, torch.ones_like(x), torch.sin(safe) / safe)
+
+
+def poisson_gradient_hat(rho_hat: torch.Tensor, box: float, pref: float, deconv_p: float,
+                         smooth: float = 0.0, g_of_k=None) -> list[torch.Tensor]:
+    """Three gradient spectra (d_x phi, d_y phi, d_z phi) from the half spectrum of rho (any k = 0 value).
+
+    ``smooth`` is the Gaussian smoothing length in Mpc/h (0 = none).  ``g_of_k``, if given, is a callable
+    on |k| (tensor) returning a multiplicative correction of the Green's function (the learned force
+    correction of the ray fields)."""
+    n_mesh = rho_hat.shape[0]
+    cell = box / n_mesh
+    kf = 2.0 * math.pi / box
+    nx, ny, nz = _wavevectors(n_mesh, box)
+    kx, ky, kz = kf * nx.double(), kf * ny.double(), kf * nz.double()
+    k2 = kx * kx + ky * ky + kz * kz
+    green = torch.where(k2 > 0, -pref / torch.where(k2 > 0, k2, torch.ones_like(k2)), torch.zeros_like(k2))
+    window = (sinc(kx * cell / 2) * sinc(ky * cell / 2) * sinc(kz * cell / 2)) ** (-deconv_p)
+    if smooth > 0.0:
+        window = window * torch.exp(-0.5 * k2 * smooth * smooth)
+    phi_hat = rho_hat * (green * window)
+    if g_of_k is not None:
+        phi_hat = phi_hat * g_of_k(torch.sqrt(k2))
+    out = []
+    half = n_mesh // 2
+    for kj, nj, last in ((kx, nx, False), (ky, ny, False), (kz, nz, True)):
+        nyq = (nj == half) if last else (nj == -half)
+        d = torch.where(nyq, torch.zeros_like(kj), kj)
+        out.append(phi_hat * (1j * d))
+    return out
+
+
+def poisson_gradient(rho: torch.Tensor, box: float, pref: float, deconv_p: float, smooth: float = 0.0,
+                     g_of_k=None):
+    """Real gradient fields [d_x phi, d_y phi, d_z phi] on the mesh from rho / rho_mean."""
+    n_mesh = rho.shape[0]
+    rho_hat = torch.fft.rfftn(rho)
+    spectra = poisson_gradient_hat(rho_hat, box, pref, deconv_p, smooth, g_of_k)
+    return [torch.fft.irfftn(s, s=(n_mesh,) * 3) for s in spectra]
+
+
+def cic_gather(fields, x: torch.Tensor, box: float) -> torch.Tensor:
+    """CIC (trilinear) interpolation of each field at positions x (n, 3); returns (n, n_fields)."""
+    n_mesh = fields[0].shape[0]
+    i0, f = _cic_parts(x, box, n_mesh)
+    out = torch.zeros(x.shape[0], len(fields), dtype=torch.float64)
+    flat = [fl.reshape(-1) for fl in fields]
+    for a, b, c in _CORNERS:
+        w = (f[:, 0] if a else 1 - f[:, 0]) * (f[:, 1] if b else 1 - f[:, 1]) * (f[:, 2] if c else 1 - f[:, 2])
+        idx = (((i0[:, 0] + a) % n_mesh) * n_mesh + (i0[:, 1] + b) % n_mesh) * n_mesh + (i0[:, 2] + c) % n_mesh
+        for j, fl in enumerate(flat):
+            out[:, j] += w * fl[idx]
+    return out
+
+
+def particle_kick_drift(disp: torch.Tensor, mom: torch.Tensor, q: torch.Tensor, grads, box: float,
+                        kick: float, drift: float):
+    """One fused leapfrog update: p <- p - grad phi(q + disp) * kick; disp <- disp + p * drift."""
+    g = cic_gather(grads, q + disp, box)
+    mom = mom - g * kick
+    disp = disp + mom * drift
+    return disp, mom
+
+
+def zeldovich(noise: np.ndarray, box: float, om: float, h: float, ns: float, sigma8: float, a_init: float):
+    """Zel'dovich displacement and momentum of the lattice particles at a_init from white noise (n,n,n).
+
+    Returns (disp, mom) as (n^3, 3) float64 tensors."""
+    n = noise.shape[0]
+    amp = cosmo.power_amplitude(om, h, ns, sigma8)
+    v_cell = (box / n) ** 3
+    w_hat = torch.fft.rfftn(torch.as_tensor(noise, dtype=torch.float64))
+    kf = 2.0 * math.pi / box
+    nx, ny, nz = _wavevectors(n, box)
+    kx, ky, kz = kf * nx.double(), kf * ny.double(), kf * nz.double()
+    k2 = kx * kx + ky * ky + kz * kz
+    kmag = torch.sqrt(k2)
+    pk = torch.as_tensor(cosmo.linear_power(kmag.numpy(), om, h, ns, amp))
+    delta_hat = w_hat * torch.sqrt(pk / v_cell)
+    delta_hat = torch.where(k2 > 0, delta_hat, torch.zeros_like(delta_hat))
+    inv_k2 = torch.where(k2 > 0, 1.0 / torch.where(k2 > 0, k2, torch.ones_like(k2)), torch.zeros_like(k2))
+    half = n // 2
+    psi = []
+    for kj, nj, last in ((kx, nx, False), (ky, ny, False), (kz, nz, True)):
+        nyq = (nj == half) if last else (nj == -half)
+        d = torch.where(nyq, torch.zeros_like(kj), kj)
+        psi.append(torch.fft.irfftn(1j * d * inv_k2 * delta_hat, s=(n, n, n)).reshape(-1))
+    psi = torch.stack(psi, dim=1)
+    d1 = cosmo.growth_D1(a_init, om)
+    f1 = cosmo.growth_f(a_init, om)
+    e1 = cosmo.E(a_init, om)
+    return d1 * psi, (a_init ** 2 * e1 * f1 * d1) * psi
+
+
+def matter_power(rho: torch.Tensor, box: float, nbins: int):
+    """Spherically averaged power of delta = rho - 1 in linear k bins of width k_f (test utility).
+
+    Returns (k_mean, P) over bins 1..nbins of |n| (integer shells [b, b+1))."""
+    n = rho.shape[0]
+    d_hat = torch.fft.fftn(rho - rho.mean())
+    p = (d_hat.abs() ** 2) * (box ** 3) / n ** 6
+    f = signed_freq(n).double()
+    nn = torch.sqrt(f.view(-1, 1, 1) ** 2 + f.view(1, -1, 1) ** 2 + f.view(1, 1, -1) ** 2)
+    b = torch.floor(nn).to(torch.int64)
+    kf = 2.0 * math.pi / box
+    ks, ps = [], []
+    for i in range(1, nbins + 1):
+        m = b == i
+        ks.append(float(nn[m].mean()) * kf)
+        ps.append(float(p[m].mean()))
+    return np.array(ks), np.array(ps)

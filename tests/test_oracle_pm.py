@@ -1,0 +1,199 @@
+"""Pins of the oracle's particle-mesh force: deposit, FFT Poisson gradient, gather, leapfrog, ICs."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synthetic
+from oracle import cosmology as cosmo
+from oracle import ewald, pm, sim
+from oracle.units import G_NEWTON
+
+
+def test_cic_mass_conservation_and_mean():
+    x = torch.tensor(synthetic.uniform_positions(1, 5000, 50.0))
+    rho = pm.cic_deposit(x, 50.0, 16)
+    assert float(rho.sum()) == pytest.approx(16 ** 3, rel=1e-13)
+    assert float(rho.min()) >= 0.0
+
+
+def test_cic_single_particle_on_node_and_at_cell_centre():
+    n, L = 8, 8.0
+    rho = pm.cic_deposit(torch.tensor([[3.0, 5.0, 7.0]], dtype=torch.float64), L, n)
+    assert float(rho[3, 5, 7]) == n ** 3 and int((rho != 0).sum()) == 1
+    rho = pm.cic_deposit(torch.tensor([[3.5, 5.5, 7.5]], dtype=torch.float64), L, n)
+    for a, b, c in itertools.product((3, 4), (5, 6), (7, 0)):
+        assert float(rho[a, b, c]) == pytest.approx(n ** 3 / 8)
+    assert int((rho != 0).sum()) == 8
+
+
+def test_cic_integer_translation_commutes_with_roll():
+    L, n = 32.0, 16
+    x = torch.tensor(synthetic.uniform_positions(2, 300, L))
+    shift = torch.tensor([2 * L / n, -3 * L / n, 5 * L / n], dtype=torch.float64)
+    a = pm.cic_deposit(x + shift, L, n)
+    b = torch.roll(pm.cic_deposit(x, L, n), shifts=(2, -3, 5), dims=(0, 1, 2))
+    assert torch.allclose(a, b, atol=1e-12)
+
+
+def _brute_gradient(rho, L, pref, p, sigma):
+    """Full-grid DFT sum, O(N^6): grad_j(x) = N^-3 sum_k i k_j G(k) F(k) rho_k e^{ikx}, k_j = 0 at n_j = -N/2."""
+    n = rho.shape[0]
+    f = np.array([i if i < n // 2 else i - n for i in range(n)])
+    idx = np.arange(n)
+    ph = np.exp(-2j * math.pi * np.outer(f, idx) / n)  # [freq, pos]
+    rho_k = np.einsum("ai,bj,ck,ijk->abc", ph, ph, ph, rho)
+    kf = 2 * math.pi / L
+    K = [kf * f.reshape(-1, 1, 1), kf * f.reshape(1, -1, 1), kf * f.reshape(1, 1, -1)]
+    k2 = K[0] ** 2 + K[1] ** 2 + K[2] ** 2
+    cell = L / n
+    win = np.ones_like(k2)
+    for kk in K:
+        win = win * np.sinc(kk * cell / 2 / math.pi) ** (-p)
+    win = win * np.exp(-0.5 * k2 * sigma ** 2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        phik = np.where(k2 > 0, -pref * rho_k * win / k2, 0.0)
+    out = []
+    for j, nf in enumerate((f.reshape(-1, 1, 1), f.reshape(1, -1, 1), f.reshape(1, 1, -1))):
+        d = np.where(nf == -n // 2, 0.0, K[j])
+        g = 1j * d * phik
+        ip = np.conj(ph)  # e^{+ikx}
+        out.append(np.einsum("ai,bj,ck,abc->ijk", ip, ip, ip, g).real / n ** 3)
+    return out
+
+
+@pytest.mark.parametrize("p,sigma", [(0.0, 0.0), (4.0, 1.0)])
+def test_fft_gradient_matches_brute_force_dft(p, sigma):
+    n, L = 8, 16.0
+    rho = synthetic.gaussian_field(3, (n, n, n)) + 1.0
+    got = pm.poisson_gradient(torch.tensor(rho), L, 0.7, p, sigma)
+    want = _brute_gradient(rho, L, 0.7, p, sigma)
+    for g, w in zip(got, want):
+        assert np.allclose(g.numpy(), w, atol=1e-12 * np.abs(w).max() + 1e-14)
+
+
+@pytest.mark.parametrize("axis,m", [(0, 3), (1, 5), (2, 2), (2, 7)])
+def test_single_mode_poisson_gradient(axis, m):
+    # delta = A cos(k x_axis), lap phi = pref delta  =>  d_axis phi = pref A sin(k x) / k, other components 0,
+    # times the filter sinc(k cell / 2)^-p exp(-k^2 sigma^2 / 2).
+    n, L, A, pref, p, sig = 16, 40.0, 0.3, 2.5, 4.0, 1.7
+    x = torch.arange(n, dtype=torch.float64) * (L / n)
+    k = 2 * math.pi * m / L
+    shape = [1, 1, 1]
+    shape[axis] = n
+    rho = (1.0 + A * torch.cos(k * x)).view(shape).expand(n, n, n).contiguous()
+    grads = pm.poisson_gradient(rho, L, pref, p, sig)
+    filt = (math.sin(k * L / n / 2) / (k * L / n / 2)) ** (-p) * math.exp(-0.5 * k * k * sig * sig)
+    want = (pref * A / k * filt * torch.sin(k * x)).view(shape).expand(n, n, n)
+    for j in range(3):
+        if j == axis:
+            assert torch.allclose(grads[j], want, atol=1e-12)
+        else:
+            assert float(grads[j].abs().max()) < 1e-12
+
+
+def test_pm_force_matches_periodic_direct_sum():
+    # One mass in a periodic box; the PM gradient interpolated at test points 5..12 cells away agrees with the
+    # 3D Ewald sum to the PM force accuracy with the 1-cell smoothing and sinc^-4 deconvolution.
+    n, L, M = 32, 64.0, 1e14
+    cell = L / n
+    src = np.array([20.3, 31.7, 11.2])
+    rho = pm.cic_deposit(torch.tensor(src[None, :]), L, n)
+    pref = 4 * math.pi * G_NEWTON * M / L ** 3
+    grads = pm.poisson_gradient(rho, L, pref, 4.0, cell)
+    rng = np.random.default_rng(7)
+    dirs = rng.standard_normal((40, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    r = cell * rng.uniform(5.0, 12.0, 40)[:, None] * dirs
+    got = pm.cic_gather(grads, torch.tensor(src + r), L).numpy()
+    want = ewald.grad_phi_3d(r, L) * G_NEWTON * M
+    err = np.linalg.norm(got - want, axis=1) / np.linalg.norm(want, axis=1)
+    assert np.median(err) < 0.01
+    assert err.max() < 0.03
+
+
+def test_gather_of_linear_field_is_exact():
+    n, L = 16, 32.0
+    cell = L / n
+    g = torch.arange(n, dtype=torch.float64) * cell
+    X, Y, Z = torch.meshgrid(g, g, g, indexing="ij")
+    field = 0.3 + 1.1 * X - 0.7 * Y + 2.3 * Z
+    pts = torch.tensor(synthetic.uniform_positions(4, 200, L - 2 * cell))
+    got = pm.cic_gather([field], pts, L)[:, 0]
+    want = 0.3 + 1.1 * pts[:, 0] - 0.7 * pts[:, 1] + 2.3 * pts[:, 2]
+    assert torch.allclose(got, want, atol=1e-12)
+
+
+def test_kick_drift_with_zero_field():
+    n = 4
+    q = pm.lattice(n, 8.0)
+    d = torch.tensor(synthetic.small_displacements(5, n, 0.3).T.copy())
+    p = torch.tensor(synthetic.small_displacements(6, n, 0.3).T.copy())
+    zero = [torch.zeros(8, 8, 8, dtype=torch.float64)] * 3
+    d2, p2 = pm.particle_kick_drift(d, p, q, zero, 8.0, kick=0.4, drift=0.25)
+    assert torch.equal(p2, p)
+    assert torch.allclose(d2, d + 0.25 * p, atol=0)
+
+
+def test_zeldovich_momentum_ratio_and_power():
+    om, h, ns, s8, a = 0.3, 0.7, 0.96, 0.8, 0.05
+    n, L = 32, 256.0
+    amp = cosmo.power_amplitude(om, h, ns, s8)
+    ratio = a ** 2 * cosmo.E(a, om) * cosmo.growth_f(a, om)
+    pk_sum = 0.0
+    seeds = range(8)
+    for seed in seeds:
+        disp, mom = pm.zeldovich(synthetic.white_noise(seed, n), L, om, h, ns, s8, a)
+        assert torch.allclose(mom, ratio * disp, rtol=1e-12, atol=0)
+        # linear density of the Zel'dovich field: delta = -div Psi, measured spectrally on the lattice
+        psi = (disp / cosmo.growth_D1(a, om)).T.reshape(3, n, n, n)
+        f = pm.signed_freq(n).double() * (2 * math.pi / L)
+        kk = [f.view(-1, 1, 1), f.view(1, -1, 1), f.view(1, 1, -1)]
+        div_hat = sum(1j * kk[j] * torch.fft.fftn(psi[j]) for j in range(3))
+        pk_sum = pk_sum + (div_hat.abs() ** 2) * (L ** 3) / n ** 6
+    pk = pk_sum / len(seeds)
+    nn = torch.sqrt(sum((pm.signed_freq(n).double().view(*s)) ** 2 for s in ((-1, 1, 1), (1, -1, 1), (1, 1, -1))))
+    for lo in (3, 5, 8):
+        sel = (nn >= lo) & (nn < lo + 1)
+        kmean = float(nn[sel].mean()) * 2 * math.pi / L
+        want = float(cosmo.linear_power(kmean, om, h, ns, amp))
+        got = float(pk[sel].mean())
+        nmodes = int(sel.sum()) * len(seeds) / 2
+        assert got == pytest.approx(want, rel=4.0 / math.sqrt(nmodes) + 0.05)
+
+
+def test_forward_then_reverse_returns_to_initial_conditions():
+    # Time reversibility of the symplectic leapfrog (footnote of Sec. 2, [LiEtAl2024] Table 2).
+    c, flt = sim.Cosmo(), sim.Filter()
+    n, nm, L = 16, 32, 64.0
+    part0 = sim.initial_particles(synthetic.white_noise(11, n), L, c, 0.1)
+    grid = [0.1 + 0.9 * i / 6 for i in range(7)]
+    part1, grads = sim.run_forward(part0, grid, L, nm, c, flt)
+    assert float((part1.disp - part0.disp).abs().max()) > 1.0
+    back = list(reversed(grid))
+    part = part1
+    for a_next in back[1:]:
+        part = sim.particle_step(part, grads, a_next, c.omega_m, L)
+        grads = sim.pm_force(part, L, nm, 1.5 * c.omega_m / a_next, flt)
+    part = sim.particle_sync(part, grads, c.omega_m, L)
+    assert float((part.disp - part0.disp).abs().max()) < 1e-9
+    assert float((part.mom - part0.mom).abs().max()) < 1e-9 * float(part0.mom.abs().max())
+
+
+def test_low_k_power_grows_as_growth_factor_squared():
+    # Linear theory: delta(k) grows as D1(a).  With the mesh equal to the particle lattice (no lattice alias)
+    # and no filter, the lowest-k shell follows D1^2 and the CIC windows only ever slow the growth down.
+    c, flt = sim.Cosmo(), sim.Filter(0.0, 0.0)
+    n, L = 32, 512.0
+    part = sim.initial_particles(synthetic.white_noise(12, n), L, c, 0.02)
+    rho0 = pm.cic_deposit(part.q + part.disp, L, n)
+    grid = list(np.exp(np.linspace(math.log(0.02), math.log(0.1), 17)))
+    part1, _ = sim.run_forward(part, grid, L, n, c, flt)
+    rho1 = pm.cic_deposit(part1.q + part1.disp, L, n)
+    _, p0 = pm.matter_power(rho0, L, 4)
+    _, p1 = pm.matter_power(rho1, L, 4)
+    ratio = p1 / p0 / (cosmo.growth_D1(0.1, c.omega_m) / cosmo.growth_D1(0.02, c.omega_m)) ** 2
+    assert ratio[0] == pytest.approx(1.0, rel=0.02)
+    assert np.all(np.diff(ratio) < 0.0) and ratio.max() < 1.02
