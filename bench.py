@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Throughput of the HRT hot path on GB300: reverse co-evolution sim-steps/s (Alg. 1 per step: ray KDK with
+readout, particle gather-kick-drift, CIC scatter, R2C FFT, fused k-space kernel, 3 C2R FFTs).
+
+Default workload: 512^3 particles, 1024^3 mesh, box 1 Gpc/h, 2048^2 rays over 10 deg, reverse steps uniform in a
+from 1 to 1/3 (source planes z = 0.5, 1, 2), synthetic Zel'dovich ICs evolved forward from a = 0.02 first.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun each rank runs an independent replica (its own seed); the timed region is bracketed by a
+barrier and a device synchronise, and rank 0 reports the maximum over ranks.  The reference arm times the
+FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HRT sim-steps/s (512³ p,1024³ mesh,4M rays) vs plain path at κ P(ℓ) err<1%"
+UNIT = "sim-steps/s"
+KERNEL_SOURCES = {
+    "ray_step": ["ray_kernels.cu", "mesh_kernels.h"],
+    "kick_drift": ["mesh_kernels.cu"],
+    "cic_scatter": ["mesh_kernels.cu"],
+    "kspace": ["mesh_kernels.cu"],
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=64)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--workload", default="cosmo_512p_1024m_2048r")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="hrt_clocks_", suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------------------------- helpers
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash(kernel: str) -> str:
+    h = hashlib.sha256()
+    for fn in KERNEL_SOURCES.get(kernel, []):
+        h.update(open(os.path.join(ROOT, "paper_2405_12913_gb300", "csrc", fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged since."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path)).get(workload, {}).get(kernel)
+    if not d or d.get("source_hash") != kernel_source_hash(kernel):
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def algorithmic_bytes(W):
+    """Algorithmic HBM bytes per launch (one read or write per element)."""
+    mesh = W.n_mesh ** 3 * 4
+    spec = W.n_mesh * W.n_mesh * (W.n_mesh // 2 + 1) * 8
+    npart = W.n_side ** 3
+    rays = W.n_rays
+    return {
+        "cic_scatter": 3 * 4 * npart + mesh,                 # positions read + density written
+        "kspace": spec + 3 * spec,                           # density spectrum read + 3 gradient spectra written
+        "kick_drift": 3 * mesh + 2 * 2 * 3 * 4 * npart,      # 3 fields read + disp, mom read and written
+        "ray_step": 2 * rays * (16 + 8 + 16 + 16),           # ray state read and written (slab reads extra)
+        "fft_r2c": mesh + spec,
+        "fft_c2r": 3 * (spec + mesh),
+    }
+
+
+# ----------------------------------------------------------------------------------------------- GPU arm
+def run_gpu(args, W, world, rank, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_12913_gb300 import hrt
+    import synthetic
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    seed = W.seed + rank
+    cfg = hrt.make_config(W.n_mesh, W.box, W.n_side, W.omega_m, W.h, W.n_s, W.sigma8, W.deconv_p, W.smooth_cells,
+                          W.samples_per_cell, W.observer, n_sources=len(W.source_steps))
+    ctx = hrt.Context(cfg)
+    noise = torch.from_numpy(synthetic.white_noise(seed, W.n_side).astype(np.float32)).to(dev)
+    theta0_h = torch.from_numpy(synthetic.pixel_grid(W.n_pix, W.fov_deg * synthetic.DEGREE))
+    theta0 = theta0_h.to(dev)
+    ctx.hrt_init_particles_zeldovich(noise, W.a_init)
+    del noise
+    for a in W.forward_grid[1:]:
+        ctx.hrt_step(a)
+    ctx.hrt_sync_particles()
+    disp0, mom0, _, _ = ctx.hrt_read_particles()
+    grid = W.reverse_grid
+    slots = {s: i for i, s in enumerate(W.source_steps)}
+
+    def reset():
+        ctx.hrt_init_particles(disp0, mom0, 1.0)
+        ctx.hrt_init_rays(theta0)
+
+    def run_steps(k, start=0):
+        """k reverse steps continuing at reverse index `start`, cycling through the reverse grid."""
+        launches = 0
+        pos = start
+        for _ in range(k):
+            if pos == len(grid) - 1:
+                reset()
+                pos = 0
+            n = pos + 1
+            ctx.hrt_step(grid[n], slots.get(n, -1))
+            launches += 4
+            pos = n
+        return pos, launches
+
+    reset()
+    pos, _ = run_steps(args.warmup)
+    reset()  # the timed run starts at a = 1 like the workload
+    pos = 0
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    pos, launches = run_steps(args.steps, pos)
+    t1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    ms_max = ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * args.steps / (ms_max / 1e3)
+
+    # per-phase timing pass (CUDA events on the context stream around each kernel of the step)
+    reset()
+    ctx.hrt_ctx_set_profiling(True)
+    run_steps(min(args.steps, len(grid) - 1), 0)
+    phases = ctx.hrt_ctx_phase_times()
+    ctx.hrt_ctx_set_profiling(False)
+
+    # end-to-end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        disp_h = torch.empty(disp0.shape, dtype=torch.float32, pin_memory=True)
+        mom_h = torch.empty(mom0.shape, dtype=torch.float32, pin_memory=True)
+        disp_h.copy_(disp0)
+        mom_h.copy_(mom0)
+        th_h = theta0_h.pin_memory()
+        kmaps_h = torch.empty(len(slots), W.n_rays, dtype=torch.float32, pin_memory=True)
+        disp_d = torch.empty_like(disp0)
+        mom_d = torch.empty_like(mom0)
+        th_d = torch.empty_like(theta0)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        disp_d.copy_(disp_h, non_blocking=True)
+        mom_d.copy_(mom_h, non_blocking=True)
+        th_d.copy_(th_h, non_blocking=True)
+        ctx.hrt_init_particles(disp_d, mom_d, 1.0)
+        ctx.hrt_init_rays(th_d)
+        h2d = disp_h.numel() * 4 + mom_h.numel() * 4 + th_h.numel() * 8
+        d2h = 0
+        p = 0
+        for i in range(args.steps):
+            if p == len(grid) - 1:
+                disp_d.copy_(disp_h, non_blocking=True)
+                mom_d.copy_(mom_h, non_blocking=True)
+                ctx.hrt_init_particles(disp_d, mom_d, 1.0)
+                ctx.hrt_init_rays(th_d)
+                h2d += disp_h.numel() * 4 + mom_h.numel() * 4
+                p = 0
+            n = p + 1
+            ctx.hrt_step(grid[n], slots.get(n, -1))
+            if n in slots:
+                kmaps_h[slots[n]].copy_(ctx.hrt_read_maps(slots[n])[0], non_blocking=True)
+                d2h += W.n_rays * 4
+            p = n
+        last = torch.empty(1, dtype=torch.float32, pin_memory=True)
+        last.copy_(ctx.hrt_read_maps(0)[0][:1], non_blocking=True)
+        d2h += 4
+        e1.record(stream)
+        barrier()
+        e_ms = e0.elapsed_time(e1)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": world * args.steps / (e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps)}
+
+    # roofline of the dominant kernel of this library (by time in the phase pass)
+    algo = algorithmic_bytes(W)
+    own = {k: phases[k] for k in ("ray_step", "kick_drift", "cic_scatter", "kspace")}
+    dom = max(own, key=lambda k: own[k][0])
+    t_ms, cnt = own[dom]
+    peak, peak_kind = measured_peaks()
+    achieved = algo[dom] / (t_ms / cnt / 1e3) / 1e9
+    phase_summary = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1],
+                         "algo_GBps": (algo[k] / (v[0] / max(v[1], 1) / 1e3) / 1e9) if k in algo and v[1] else None}
+                     for k, v in phases.items()}
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 ray angles and time coefficients)",
+        "data": "synthetic (seeded Gaussian ICs, power law x BBKS, sigma8 = 0.8)",
+        "config": {"workload": W.name, "n_particles": W.n_side ** 3, "n_mesh": W.n_mesh, "box_mpc_h": W.box,
+                   "n_rays": W.n_rays, "fov_deg": W.fov_deg, "reverse_steps": W.n_reverse,
+                   "timed_steps_start_at_a": 1.0, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (4.3 GB mesh per field)"},
+        "clocks": clk, "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": recorded_traffic(dom, W.name), "algorithmic_bytes": algo[dom]},
+        "phases": phase_summary,
+        "e2e": e2e,
+    }
+    return line
+
+
+# ----------------------------------------------------------------------------------------------- oracle (CPU)
+def oracle_sample(W, n_side, n_mesh, n_pix, seed=7):
+    """Times one reverse sim-step of the FP64 oracle on a scaled copy of the workload (same box and field of
+    view; particles, mesh and rays reduced), and extrapolates linearly in the work units to the full size.
+
+    Returns (seconds per full-size step, sample description, threads)."""
+    import numpy as np
+    import torch
+    import synthetic
+    from oracle import cosmology as oc
+    from oracle import pm as opm
+    from oracle import rays as orays
+    from oracle import sim as osim
+
+    torch.set_num_threads(os.cpu_count() or 1)
+    threads = torch.get_num_threads()
+    om = W.omega_m
+    grid = W.reverse_grid
+    mid = len(grid) // 2
+    a0, a1 = grid[mid], grid[mid + 1]
+    q = opm.lattice(n_side, W.box)
+    disp = torch.tensor(synthetic.small_displacements(seed, n_side, 2.0).T.copy())
+    mom = torch.tensor(synthetic.small_displacements(seed + 1, n_side, 1.0).T.copy())
+    flt = osim.Filter(W.deconv_p, W.smooth_cells)
+    t = time.perf_counter()
+    rho = opm.cic_deposit(q + disp, W.box, n_mesh)
+    grads = opm.poisson_gradient(rho, W.box, 1.5 * om / a0, flt.deconv_p, flt.smooth_cells * W.box / n_mesh)
+    kick = oc.kick_integral(a0, 0.5 * (a0 + a1), om)
+    drift = oc.drift_integral(a0, a1, om)
+    opm.particle_kick_drift(disp, mom, q, grads, W.box, kick, drift)
+    t_pm = time.perf_counter() - t
+    theta0 = torch.tensor(synthetic.pixel_grid(n_pix, W.fov_deg * synthetic.DEGREE))
+    st = orays.init_state(theta0)
+    c0, c1 = oc.chi_of_a(a0, om), oc.chi_of_a(a1, om)
+    t = time.perf_counter()
+    orays.ray_step(st, grads[0], grads[1], W.box, W.observer, c0, c1, W.samples_per_cell,
+                   osim.growth_weight(a0, om))
+    t_ray = time.perf_counter() - t
+    # work units: particles + mesh cells for the PM part, ray-node evaluations for the rays
+    ratio_pm = (W.n_side / n_side) ** 3
+    cell_s, cell_f = W.box / n_mesh, W.box / W.n_mesh
+    nodes_s = math.ceil(abs(c1 - c0) / 2 / cell_s) * 2
+    nodes_f = math.ceil(abs(c1 - c0) / 2 / cell_f) * 2
+    ratio_ray = (W.n_rays / n_pix ** 2) * (nodes_f / nodes_s)
+    full = t_pm * ratio_pm + t_ray * ratio_ray
+    desc = (f"one reverse step (a {a0:.4f}->{a1:.4f}) at {n_side}^3 particles, {n_mesh}^3 mesh, {n_pix}^2 rays "
+            f"({t_pm:.2f} s PM + {t_ray:.2f} s rays), scaled x{ratio_pm:.0f} (particles, cells) and "
+            f"x{ratio_ray:.0f} (ray-node samples) to the full workload")
+    return full, desc, threads
+
+
+def run_reference(args, W, rank):
+    if rank != 0:
+        return None
+    sizes = (32, 64, 128)  # n_side, n_mesh, n_pix per sampled step
+    for _ in range(args.warmup):
+        oracle_sample(W, *sizes)
+    per = []
+    desc = threads = None
+    for i in range(args.steps):
+        full, desc, threads = oracle_sample(W, *sizes, seed=100 + i)
+        per.append(full)
+    sec = sum(per) / len(per)
+    value = 1.0 / sec
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": W.name, "parallelism": "cpu"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    from paper_2405_12913_gb300.configs import WORKLOADS
+    W = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        line = run_reference(args, W, rank)
+        if line is not None:
+            print(json.dumps(line))
+        return 0
+    line = run_gpu(args, W, world, rank, local)
+    if line is None:
+        return 0
+    if world == 1 and not args.no_cpu_baseline:
+        full, desc, threads = oracle_sample(W, 128, 256, 512)
+        line["cpu_baseline"] = {"value": 1.0 / full, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": desc}
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,278 @@
+/*
+ * hrt.h -- C ABI of the GB300 (sm_103a) hot path of Hamiltonian ray tracing (HRT), after Zhou et al.,
+ * "A Hamiltonian, post-Born, three-dimensional, on-the-fly ray tracing algorithm for gravitational lensing"
+ * (arXiv 2405.12913).
+ *
+ * Units: lengths in Mpc/h, velocities in 100 km/s (H0 = 1), masses in Msun/h, angles in radians.  The speed
+ * of light is c = 2997.92458 and G = 4.30091727e-13 in these units.
+ *
+ * Conventions shared by every call
+ *   - Meshes are n^3 single-precision arrays indexed [ix][iy][iz] with iz fastest; node (ix, iy, iz) sits at
+ *     (ix, iy, iz) * box / n and the mesh is periodic.  Half spectra are interleaved complex64 arrays
+ *     [ix][iy][kz], kz = 0..n/2 (the layout of an out-of-place real-to-complex FFT).
+ *   - Particles are on an n_side^3 Lagrangian lattice q = (i, j, k) * box / n_side with particle index
+ *     (i * n_side + j) * n_side + k; positions are stored as float32 displacements from q, momenta as
+ *     p = a^2 dx/dt, both structure-of-arrays [3][n_side^3].  n (mesh) must be a multiple of n_side.
+ *   - Ray state, ray-major: theta [R][2] float64, eta [R][2] float32, A [R][4] and B [R][4] float32
+ *     (row-major 2x2: A11, A12, A21, A22).
+ *   - Pointer arguments are device pointers unless a name ends in _host.  They are borrowed for the call
+ *     only; work is enqueued on the caller's CUDA stream (a cudaStream_t passed as void*, NULL = legacy
+ *     default stream) and the caller keeps the buffers alive until that stream has reached the work.
+ *     Calls documented as "synchronises" wait for the stream before returning.
+ *   - Every call returns an hrt_status; nothing is thrown across the ABI.  After HRT_ERR_CUDA a context is
+ *     poisoned: every later call on it returns HRT_ERR_STATE except hrt_destroy.
+ */
+#ifndef HRT_H
+#define HRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hrt_status {
+  HRT_OK = 0,
+  HRT_ERR_INVALID_ARG = 1, /* a size, pointer or parameter is out of range; nothing was enqueued       */
+  HRT_ERR_OOM = 2,         /* a device or host allocation failed; the context stays destroyable       */
+  HRT_ERR_CUDA = 3,        /* a CUDA runtime or cuFFT call failed                                     */
+  HRT_ERR_STATE = 4,       /* calls out of order (e.g. a step before particles exist), or poisoned    */
+  HRT_ERR_NONFINITE = 5,   /* a NaN or infinity was found in an output that the call checks          */
+  HRT_ERR_TIMEOUT = 6      /* a host wait for the stream exceeded its limit                           */
+} hrt_status;
+
+/* Human-readable name of a status code (static string). */
+const char* hrt_status_string(hrt_status s);
+
+/* Last error message of the calling thread (static thread-local buffer, empty if none). */
+const char* hrt_last_error(void);
+
+/* ------------------------------------------------------------------------------------------------------
+ * FP64 host cosmology (flat LCDM without radiation), Sec. 2 (Poisson equation, r = chi) and Sec. 3.2
+ * (growth time correction of Eq. "kick").  Host-only, no GPU needed.
+ * ---------------------------------------------------------------------------------------------------- */
+
+/* out[0] = E(a) = H/H0, out[1] = chi(a) (comoving distance of the light front at a from the observer at
+ * a = 1), out[2] = D1(a) (linear growth, D1(1) = 1), out[3] = f(a) = dlnD1/dlna. */
+hrt_status hrt_cosmo_eval(double omega_m, double a, double out_host[4]);
+
+/* Signed particle time integrals: out[0] = K(a->b) = int_a^b da/(a E), out[1] = Dr(a->b) = int da/(a^3 E);
+ * the leapfrog kick is p -= grad(phi) K and the drift x += p Dr (momentum p = a^2 dx/dt). */
+hrt_status hrt_cosmo_time_integrals(double omega_m, double a, double b, double out_host[2]);
+
+/* Scale factor of the light front at comoving distance chi (inverse of chi(a)). */
+hrt_status hrt_cosmo_a_of_chi(double omega_m, double chi, double* a_host);
+
+/* Amplitude A of P(k) = A k^n_s T_BBKS(k / (omega_m h))^2 with sigma(8 Mpc/h) = sigma8 at a = 1. */
+hrt_status hrt_cosmo_power_amplitude(double omega_m, double h, double n_s, double sigma8, double* amp_host);
+
+/* ------------------------------------------------------------------------------------------------------
+ * Mesh kernels (stateless; the PM object below owns FFT plans and tables)
+ * ---------------------------------------------------------------------------------------------------- */
+
+/* CIC (cloud-in-cell) mass assignment, the density step of the PM force ("the most computationally
+ * expensive operation", Sec. 4.1).  Overwrites rho[n^3] with rho/rho_mean = 1 + delta: each of the
+ * n_side^3 particles carries n^3 / n_side^3 and gives weight (1-f) to node floor(u), f to floor(u)+1 per
+ * axis, u = (q + disp) / cell, periodic.  disp is [3][n_side^3].  Accumulation order is not fixed (float32
+ * atomics), so results are reproducible to rounding only.  n_side >= 1, n % n_side == 0, n >= 2. */
+hrt_status hrt_cic_scatter(const float* disp, int64_t n_side, int64_t n, double box, float* rho,
+                           void* stream);
+
+/* Fused particle update of the leapfrog (nbody_reverse_step of Alg. 1): CIC-interpolate the three gradient
+ * fields grad[3][n^3] (d_x phi, d_y phi, d_z phi) at q + disp, then p -= grad phi * kick and
+ * disp += p * drift.  kick and drift are the signed FP64 time integrals (K, Dr above; drift = 0 for a
+ * kick-only synchronisation), rounded to float32 for the arithmetic. */
+hrt_status hrt_particle_kick_drift(const float* grad, int64_t n, double box, int64_t n_side, float* disp,
+                                   float* mom, double kick, double drift, void* stream);
+
+/* k-space filter of the gradient fields (Sec. 4.2 kick operator taken on the 3D mesh):
+ *   prod_i sinc(k_i cell/2)^-deconv_p  *  exp(-k^2 smooth^2 / 2)  *  g(|k|)
+ * with g the optional learned correction table: g_table[nk] (device, float32) sampled uniformly on
+ * |k| in [0, g_kmax], linearly interpolated, 1 beyond g_kmax; NULL means g = 1. */
+typedef struct hrt_filter {
+  double deconv_p;      /* power p of the per-axis sinc deconvolution (0 = none)                   */
+  double smooth;        /* Gaussian smoothing length in Mpc/h (0 = none)                           */
+  const float* g_table; /* learned multiplicative correction, or NULL                              */
+  int32_t g_nk;         /* entries of g_table (>= 2 when given)                                    */
+  double g_kmax;        /* |k| of the last entry, h/Mpc                                            */
+} hrt_filter;
+
+/* Fused k-space kernel of the Poisson solve (Sec. 2 Poisson equation, Sec. 4.2 deconvolution):
+ * from rho_hat (half spectrum of rho, any k = 0 value) write n_out gradient spectra
+ *   out_j = i k_j * (-pref / k^2) * F(k) * rho_hat / n^3,   j = 0..n_out-1 (x, y[, z])
+ * with out = 0 at k = 0 and on the j-Nyquist plane, k_i = 2 pi n_i / box, n_i in [-n/2, n/2).  The 1/n^3
+ * makes an unnormalised complex-to-real inverse FFT return d_j phi.  pref = (3/2) Omega_m / a for the
+ * expanding universe or 4 pi G rho_mean for a static lens.  out holds n_out spectra back to back.
+ * If second != NULL, n_second (0..3) more spectra with the filter *f2 are written to second (the ray
+ * fields when they differ from the particle fields); the density spectrum is read once. */
+hrt_status hrt_kspace_gradient(const void* rho_hat, int64_t n, double box, double pref, const hrt_filter* f,
+                               int32_t n_out, void* out, const hrt_filter* f2, int32_t n_second,
+                               void* second, void* stream);
+
+/* ------------------------------------------------------------------------------------------------------
+ * PM solver object: cuFFT plans and buffers for one mesh size, rho -> grad phi (R2C, k-space, C2R).
+ * ---------------------------------------------------------------------------------------------------- */
+typedef struct hrt_pm hrt_pm;
+
+/* Creates plans for an n^3 mesh on `stream`, with device buffers for rho_hat and the gradient spectra.
+ * n_ray_fields (0 or 2) adds two separately filtered ray gradient fields. */
+hrt_status hrt_pm_create(int64_t n, double box, int32_t n_ray_fields, void* stream, hrt_pm** out);
+hrt_status hrt_pm_destroy(hrt_pm* pm); /* NULL is fine; synchronises the stream */
+
+/* grad[3][n^3] <- gradient of phi from rho[n^3] (rho is overwritten as FFT scratch);
+ * ray_grad[2][n^3] (only if the object has ray fields; else pass NULL) with the ray filter. */
+hrt_status hrt_pm_solve(hrt_pm* pm, float* rho, double pref, const hrt_filter* f, float* grad,
+                        const hrt_filter* f_ray, float* ray_grad);
+
+/* ------------------------------------------------------------------------------------------------------
+ * Rays
+ * ---------------------------------------------------------------------------------------------------- */
+
+/* Device ray state (caller-owned), n_rays rays, layouts as in the header comment. */
+typedef struct hrt_rays {
+  double* theta;
+  float* eta;
+  float* A;
+  float* B;
+  int64_t n_rays;
+} hrt_rays;
+
+/* theta = theta0[n][2], eta = 0, A = I, B = 0 (initial conditions of Sec. 2 and Sec. 4). */
+hrt_status hrt_rays_init(const hrt_rays* rays, const double* theta0, void* stream);
+
+/* Geometry of a ray step: box, mesh, observer and the line-of-sight quadrature density. */
+typedef struct hrt_ray_geom {
+  int64_t n;                 /* mesh cells per side                                                  */
+  double box;                /* box side, Mpc/h                                                      */
+  double observer[3];        /* observer position; line of sight along +z                            */
+  double samples_per_cell;   /* s: each half shell uses max(1, ceil(s |half shell| / cell)) nodes    */
+  double window_lo;          /* only nodes with window_lo <= chi < window_hi kick (static lens box)   */
+  double window_hi;
+} hrt_ray_geom;
+
+/* One KDK step of every ray through the shell [chi_from, chi_to] with the A/B recursion, Alg. 1 order
+ * (Eqs. "symp_1".."symp_3", "obsv_recurse1".."obsv_recurse3"):
+ *   eta += K(theta) over [chi_from, chi_mid];  B += (dK/dtheta) A;
+ *   theta += eta d;  A += d B,  d = (chi_to - chi_from) / (c chi_mid^2)       (Eq. "drift", midpoint r);
+ *   eta += K(theta) over [chi_mid, chi_to];    B += (dK/dtheta) A.
+ * K = sum_j c_j (d_x phi, d_y phi)(X_j) with X_j = observer + (chi_j theta, chi_j), midpoint nodes chi_j and
+ * c_j = -(2/c) h chi_j g(chi_j) (Eq. "kick"), g = D1(a(chi)) a_ref / (D1(a_ref) a(chi)) when a_ref > 0 and
+ * g = 1 when a_ref == 0 (static potential); dK/dtheta = sum_j c_j chi_j T_j, T the transverse derivative of
+ * the trilinear interpolant.  grad_x, grad_y are the n^3 gradient fields.  If maps != NULL the readout of
+ * Eqs. "obs_first_set"/"obs_second_set" is written after the step: maps[4][n_rays] = kappa, gamma1,
+ * gamma2, omega.  At most 1024 nodes per step (else HRT_ERR_INVALID_ARG). */
+hrt_status hrt_ray_step(const hrt_rays* rays, const float* grad_x, const float* grad_y,
+                        const hrt_ray_geom* geom, double chi_from, double chi_to, double a_ref,
+                        double omega_m, float* maps, void* stream);
+
+/* Exact drift with no force over [chi_from, chi_to] (chi_from > 0): theta += eta (1/chi_from -
+ * 1/chi_to)/c, A += B (1/chi_from - 1/chi_to)/c.  Used where the potential is known to vanish. */
+hrt_status hrt_ray_drift_free(const hrt_rays* rays, double chi_from, double chi_to, void* stream);
+
+/* Readout only: maps[4][n_rays] = kappa, gamma1, gamma2, omega from A (Eqs. "obs_first_set"). */
+hrt_status hrt_ray_readout(const hrt_rays* rays, float* maps, void* stream);
+
+/* ------------------------------------------------------------------------------------------------------
+ * Convergence power spectrum: P(ell) = <|FFT2(kappa) dtheta^2|^2>_bin / (m dtheta)^2 over nbins log bins
+ * in [ell_min, ell_max) (bin b = floor(nbins ln(ell/ell_min)/ln(ell_max/ell_min) + 1e-9), the 1e-9 placing
+ * exact edges in the upper bin), ell = 2 pi |n| / (m dtheta).  Outputs the mean ell, mean power and mode
+ * count per bin to host arrays of nbins.  kappa is m x m float32 (m even, 2 <= m <= 16384,
+ * 1 <= nbins <= 256).  Synchronises the stream.
+ * ---------------------------------------------------------------------------------------------------- */
+hrt_status hrt_kappa_power(const float* kappa, int64_t m, double dtheta, int32_t nbins, double ell_min,
+                           double ell_max, double* ell_host, double* p_host, int64_t* count_host,
+                           void* stream);
+
+/* ------------------------------------------------------------------------------------------------------
+ * Zel'dovich initial conditions (particle lattice, a_init): delta_k = w_k sqrt(P(k)/V_cell) from white
+ * noise w[n_side^3] (float32), Psi_k = i k delta_k / k^2 (0 at k = 0 and on Nyquist planes),
+ * disp = D1(a) Psi, mom = a^2 E(a) f(a) D1(a) Psi.  disp, mom are [3][n_side^3].
+ * ---------------------------------------------------------------------------------------------------- */
+typedef struct hrt_cosmology {
+  double omega_m, h, n_s, sigma8;
+} hrt_cosmology;
+
+hrt_status hrt_ic_zeldovich(const float* noise, int64_t n_side, double box, const hrt_cosmology* cosmo,
+                            double a_init, float* disp, float* mom, void* stream);
+
+/* ------------------------------------------------------------------------------------------------------
+ * Simulation context: particles + mesh + rays co-evolved as in Alg. 1 (one PM force per step).
+ * ---------------------------------------------------------------------------------------------------- */
+typedef struct hrt_config {
+  int64_t n_mesh;           /* mesh cells per side                                                  */
+  double box;               /* Mpc/h                                                                */
+  int64_t n_side;           /* particles per side (n_mesh % n_side == 0)                            */
+  hrt_cosmology cosmo;      /* ignored in static mode except omega_m                                */
+  double deconv_p;          /* k-space filter of the gradient fields (see hrt_filter)               */
+  double smooth_cells;      /* Gaussian smoothing length in mesh cells                              */
+  double samples_per_cell;  /* ray line-of-sight samples per mesh cell                              */
+  double observer[3];
+  int32_t static_mode;      /* 1: flat static space, a = 1, Poisson prefactor static_pref           */
+  double static_pref;       /* 4 pi G rho_mean for the static lens                                  */
+  double window_lo, window_hi; /* chi range in which rays feel the force (static lens box)         */
+  int32_t n_sources;        /* number of source planes (maps)                                       */
+  int32_t ray_fields;       /* 0: rays use the particle fields; 2: separately filtered ray fields   */
+  double ray_deconv_p, ray_smooth_cells; /* ray filter when ray_fields == 2                          */
+} hrt_config;
+
+typedef struct hrt_ctx hrt_ctx;
+
+hrt_status hrt_create(const hrt_config* cfg, void* stream, hrt_ctx** out);
+hrt_status hrt_destroy(hrt_ctx* ctx);  /* NULL is fine; synchronises the context's stream */
+
+/* Device bytes a context of this configuration allocates (plans and buffers), for capacity planning. */
+hrt_status hrt_workspace_bytes(const hrt_config* cfg, int64_t n_rays, size_t* bytes_host);
+
+/* Particles from Zel'dovich ICs (noise[n_side^3] device float32) at a_init, then the PM force at a_init. */
+hrt_status hrt_init_particles_zeldovich(hrt_ctx* ctx, const float* noise, double a_init);
+
+/* Particles from caller state (copied) at scale factor a (momentum synchronised at a), then the force. */
+hrt_status hrt_init_particles(hrt_ctx* ctx, const float* disp, const float* mom, double a);
+
+/* Rays at the observer (copied): theta0[n_rays][2]. */
+hrt_status hrt_init_rays(hrt_ctx* ctx, const double* theta0, int64_t n_rays);
+
+/* One co-evolution step from the current a to a_next (Alg. 1): if rays exist and a_next < a they are
+ * traced through [chi(a), chi(a_next)] with the current force (and read out to map `source` if
+ * source >= 0); then particles kick from their momentum time to (a + a_next)/2 and drift to a_next; then
+ * the PM force is recomputed at a_next.  Forward steps (a_next > a) move particles only. */
+hrt_status hrt_step(hrt_ctx* ctx, double a_next, int32_t source);
+
+/* Kick the momenta from their time to the current a with the current force (synchronise). */
+hrt_status hrt_sync_particles(hrt_ctx* ctx);
+
+/* Static mode: trace rays through [chi_from, chi_to] in the fixed potential (a = 1, no growth), readout
+ * to map `source` if >= 0.  Particles do not move. */
+hrt_status hrt_step_static(hrt_ctx* ctx, double chi_from, double chi_to, int32_t source);
+
+/* Exact force-free drift of the rays (see hrt_ray_drift_free). */
+hrt_status hrt_drift_free(hrt_ctx* ctx, double chi_from, double chi_to);
+
+/* Copies of the context state into caller device buffers (any pointer may be NULL). */
+hrt_status hrt_read_rays(hrt_ctx* ctx, double* theta, float* eta, float* A, float* B);
+hrt_status hrt_read_maps(hrt_ctx* ctx, int32_t source, float* kappa, float* gamma1, float* gamma2,
+                         float* omega);
+hrt_status hrt_read_particles(hrt_ctx* ctx, float* disp, float* mom, double* a_host, double* a_mom_host);
+hrt_status hrt_read_grad(hrt_ctx* ctx, float* grad /* [3][n^3] */);
+
+/* Power spectrum of the kappa map of `source` (the rays must form an m x m image, m^2 = n_rays). */
+hrt_status hrt_ctx_kappa_power(hrt_ctx* ctx, int32_t source, int64_t m, double dtheta, int32_t nbins,
+                               double ell_min, double ell_max, double* ell_host, double* p_host,
+                               int64_t* count_host);
+
+/* Phase timing with CUDA events recorded on the context's stream around each part of a step.  Phases:
+ * 0 ray step, 1 particle kick-drift, 2 CIC scatter (with its memset), 3 R2C FFT, 4 k-space kernel,
+ * 5 C2R FFTs (all fields), 6 whole hrt_step.  hrt_ctx_phase_times synchronises, returns the summed
+ * milliseconds and launch counts since the last call (arrays of 8), and resets them. */
+hrt_status hrt_ctx_set_profiling(hrt_ctx* ctx, int32_t on);
+hrt_status hrt_ctx_phase_times(hrt_ctx* ctx, double* ms_host, int64_t* counts_host);
+
+/* Device pointers of the context's ray state (for callers that launch the ray kernels directly). */
+hrt_status hrt_ctx_rays(hrt_ctx* ctx, hrt_rays* out_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HRT_H */

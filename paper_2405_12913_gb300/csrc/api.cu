@@ -1,0 +1,871 @@
+// C ABI of the HRT library (include/hrt.h): argument checks, FP64 host tables, cuFFT plans and the
+// simulation context that sequences the kernels of one co-evolution step (Alg. 1).
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.h"
+#include "cosmo.h"
+#include "mesh_kernels.h"
+
+namespace hrt {
+
+static thread_local char g_err[512];
+
+hrt_status fail(hrt_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+hrt_status cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return HRT_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(HRT_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  }
+  return fail(HRT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static hrt_status cufft_status(cufftResult r, const char* what) {
+  if (r == CUFFT_SUCCESS) return HRT_OK;
+  if (r == CUFFT_ALLOC_FAILED) return fail(HRT_ERR_OOM, "%s: cuFFT allocation failed", what);
+  return fail(HRT_ERR_CUDA, "%s: cuFFT error %d", what, static_cast<int>(r));
+}
+#define HRT_CUFFT(expr) HRT_TRY(::hrt::cufft_status((expr), #expr))
+
+bool inject_alloc_failure() {
+  static long target = [] {
+    const char* v = std::getenv("HRT_FAIL_ALLOC_AT");
+    return v ? std::atol(v) : 0L;
+  }();
+  static long count = 0;
+  if (target <= 0) return false;
+  return ++count == target;
+}
+
+hrt_status device_alloc(void** p, size_t bytes, cudaStream_t stream, const char* what) {
+  *p = nullptr;
+  if (bytes == 0) return HRT_OK;
+  if (inject_alloc_failure()) return fail(HRT_ERR_OOM, "%s: injected allocation failure", what);
+  return cuda_status(cudaMallocAsync(p, bytes, stream), what);
+}
+
+static void device_free(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+// Uploads host floats to a fresh stream-ordered device buffer (the host copy is consumed before return).
+static hrt_status upload(const std::vector<float>& h, float** d, cudaStream_t s, const char* what) {
+  HRT_TRY(device_alloc(reinterpret_cast<void**>(d), h.size() * sizeof(float), s, what));
+  return cuda_status(cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, s), what);
+}
+
+static hrt_status check_mesh(int64_t n, double box) {
+  if (n < 2 || n % 2 != 0 || n > 2048) return fail(HRT_ERR_INVALID_ARG, "mesh size %lld must be even, 2..2048", (long long)n);
+  if (!(box > 0.0) || !std::isfinite(box)) return fail(HRT_ERR_INVALID_ARG, "box must be positive");
+  return HRT_OK;
+}
+
+static hrt_status check_particles(int64_t n_side, int64_t n) {
+  if (n_side < 1 || n % n_side != 0) return fail(HRT_ERR_INVALID_ARG, "n_side %lld must divide the mesh %lld", (long long)n_side, (long long)n);
+  return HRT_OK;
+}
+
+static hrt_status check_filter(const hrt_filter* f) {
+  if (!f) return fail(HRT_ERR_INVALID_ARG, "filter is NULL");
+  if (!std::isfinite(f->deconv_p) || !(f->smooth >= 0.0)) return fail(HRT_ERR_INVALID_ARG, "bad filter");
+  if (f->g_table && (f->g_nk < 2 || !(f->g_kmax > 0.0))) return fail(HRT_ERR_INVALID_ARG, "bad learned table");
+  return HRT_OK;
+}
+
+static hrt_status filter_upload(int64_t n, double box, const hrt_filter& f, float** d, cudaStream_t s) {
+  std::vector<float> wxy, wz;
+  filter_tables(n, box, f, wxy, wz);
+  wxy.insert(wxy.end(), wz.begin(), wz.end());
+  return upload(wxy, d, s, "filter table");
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// Ray step parameters: FP64 node table of the half shells (Eq. "kick" with the growth correction).
+// ---------------------------------------------------------------------------------------------------------
+static hrt_status build_ray_params(const hrt_ray_geom& g, double chi_from, double chi_to, double a_ref,
+                                   double omega_m, RayStepParams& p) {
+  if (!(g.samples_per_cell > 0.0)) return fail(HRT_ERR_INVALID_ARG, "samples_per_cell must be > 0");
+  HRT_TRY(check_mesh(g.n, g.box));
+  const double cell = g.box / g.n;
+  const double chi_mid = 0.5 * (chi_from + chi_to);
+  if (!(chi_mid > 0.0)) return fail(HRT_ERR_INVALID_ARG, "shell midpoint must be at chi > 0");
+  Cosmo cosmo(omega_m);
+  const double d1_ref = a_ref > 0.0 ? cosmo.D1(a_ref) : 1.0;
+  p.n = static_cast<int>(g.n);
+  p.cell = cell;
+  p.box = g.box;
+  p.obs_x = g.observer[0];
+  p.obs_y = g.observer[1];
+  p.drift_d = (chi_to - chi_from) / (kCLight * chi_mid * chi_mid);
+  p.drift = static_cast<float>(p.drift_d);
+  int total = 0;
+  const double lo[2] = {chi_from, chi_mid}, hi[2] = {chi_mid, chi_to};
+  for (int h = 0; h < 2; ++h) {
+    int cnt = half_shell_count(lo[h], hi[h], g.samples_per_cell, cell);
+    double hh = (hi[h] - lo[h]) / cnt;
+    p.ref_r[h] = lo[h] + 0.5 * hh;
+    int kept = 0;
+    for (int j = 0; j < cnt; ++j) {
+      double chi = lo[h] + (j + 0.5) * hh;
+      if (!(g.window_lo <= chi && chi < g.window_hi)) continue;
+      if (total >= kMaxRayNodes) return fail(HRT_ERR_INVALID_ARG, "more than %d line-of-sight nodes in one step", kMaxRayNodes);
+      double gw = 1.0;
+      if (a_ref > 0.0) {
+        double a = cosmo.a_of_chi(chi);
+        gw = cosmo.D1(a) / d1_ref * a_ref / a;
+      }
+      double r = chi;
+      double c = -(2.0 / kCLight) * hh * r * gw;
+      p.dr[total] = static_cast<float>((r - p.ref_r[h]) / cell);
+      p.cw[total] = static_cast<float>(c);
+      p.cwr[total] = static_cast<float>(c * r / cell);
+      double uz = (g.observer[2] + chi) / cell;
+      uz -= g.n * std::floor(uz / g.n);
+      double fl = std::floor(uz);
+      int kz = static_cast<int>(fl);
+      float fz = static_cast<float>(uz - fl);
+      if (kz >= g.n) kz -= static_cast<int>(g.n);
+      p.kz[total] = kz;
+      p.fz[total] = fz;
+      ++total;
+      ++kept;
+    }
+    if (h == 0) p.n1 = kept; else p.n2 = kept;
+  }
+  return HRT_OK;
+}
+
+static hrt_status check_rays(const hrt_rays* r) {
+  if (!r) return fail(HRT_ERR_INVALID_ARG, "rays is NULL");
+  if (r->n_rays < 0) return fail(HRT_ERR_INVALID_ARG, "negative ray count");
+  if (r->n_rays > 0 && (!r->theta || !r->eta || !r->A || !r->B)) return fail(HRT_ERR_INVALID_ARG, "ray state pointer is NULL");
+  return HRT_OK;
+}
+
+}  // namespace hrt
+
+// ---------------------------------------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------------------------------------
+struct hrt_ctx {
+  hrt_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool poisoned = false;
+  hrt_pm* pm = nullptr;
+  float* disp = nullptr;
+  float* mom = nullptr;
+  float* rho = nullptr;
+  float* grad = nullptr;
+  float* ray_grad = nullptr;
+  bool have_particles = false;
+  double a = 1.0, a_mom = 1.0;
+  hrt_rays rays{};
+  float* maps = nullptr;
+  int64_t maps_rays = 0;
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> phases[8];
+};
+
+namespace hrt {
+
+// Records a CUDA event pair around a phase of a step when profiling is on.
+struct PhaseScope {
+  hrt_ctx* ctx;
+  int phase;
+  cudaEvent_t end = nullptr;
+  PhaseScope(hrt_ctx* c, int p) : ctx(c), phase(p) {
+    if (!ctx->profiling) return;
+    cudaEvent_t start;
+    if (cudaEventCreate(&start) != cudaSuccess) return;
+    if (cudaEventCreate(&end) != cudaSuccess) {
+      cudaEventDestroy(start);
+      end = nullptr;
+      return;
+    }
+    cudaEventRecord(start, ctx->stream);
+    ctx->phases[phase].emplace_back(start, end);
+  }
+  ~PhaseScope() {
+    if (end) cudaEventRecord(end, ctx->stream);
+  }
+};
+
+}  // namespace hrt
+
+// ---------------------------------------------------------------------------------------------------------
+// PM object
+// ---------------------------------------------------------------------------------------------------------
+
+struct hrt_pm {
+  int64_t n = 0;
+  double box = 0.0;
+  int32_t n_ray = 0;
+  cudaStream_t stream = nullptr;
+  cufftHandle r2c = 0, c2r = 0;
+  bool have_r2c = false, have_c2r = false;
+  void* work = nullptr;
+  void* rho_hat = nullptr;
+  void* grad_hat = nullptr;     // 3 + n_ray spectra
+  float* tab_a = nullptr;       // filter tables (particles)
+  float* tab_b = nullptr;       // filter tables (rays)
+  hrt_filter key_a{}, key_b{};  // filters the tables were built for
+};
+
+namespace hrt {
+
+static size_t spectrum_bytes(int64_t n) { return static_cast<size_t>(n) * n * (n / 2 + 1) * sizeof(float2); }
+
+static hrt_status pm_make(int64_t n, double box, int32_t n_ray, cudaStream_t s, hrt_pm* pm) {
+  pm->n = n;
+  pm->box = box;
+  pm->n_ray = n_ray;
+  pm->stream = s;
+  long long dims[3] = {n, n, n};
+  size_t w1 = 0, w2 = 0;
+  HRT_CUFFT(cufftCreate(&pm->r2c));
+  pm->have_r2c = true;
+  HRT_CUFFT(cufftSetAutoAllocation(pm->r2c, 0));
+  HRT_CUFFT(cufftMakePlanMany64(pm->r2c, 3, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_R2C, 1, &w1));
+  HRT_CUFFT(cufftCreate(&pm->c2r));
+  pm->have_c2r = true;
+  HRT_CUFFT(cufftSetAutoAllocation(pm->c2r, 0));
+  HRT_CUFFT(cufftMakePlanMany64(pm->c2r, 3, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, 1, &w2));
+  size_t w = std::max(w1, w2);
+  HRT_TRY(device_alloc(&pm->work, w, s, "cuFFT work area"));
+  HRT_CUFFT(cufftSetWorkArea(pm->r2c, pm->work));
+  HRT_CUFFT(cufftSetWorkArea(pm->c2r, pm->work));
+  HRT_CUFFT(cufftSetStream(pm->r2c, s));
+  HRT_CUFFT(cufftSetStream(pm->c2r, s));
+  HRT_TRY(device_alloc(&pm->rho_hat, spectrum_bytes(n), s, "rho_hat"));
+  HRT_TRY(device_alloc(&pm->grad_hat, spectrum_bytes(n) * (3 + n_ray), s, "gradient spectra"));
+  return HRT_OK;
+}
+
+static void pm_release(hrt_pm* pm) {
+  if (!pm) return;
+  cudaStreamSynchronize(pm->stream);
+  if (pm->have_r2c) cufftDestroy(pm->r2c);
+  if (pm->have_c2r) cufftDestroy(pm->c2r);
+  device_free(pm->work, pm->stream);
+  device_free(pm->rho_hat, pm->stream);
+  device_free(pm->grad_hat, pm->stream);
+  device_free(pm->tab_a, pm->stream);
+  device_free(pm->tab_b, pm->stream);
+  cudaStreamSynchronize(pm->stream);
+}
+
+static bool same_filter(const hrt_filter& a, const hrt_filter& b) {
+  return a.deconv_p == b.deconv_p && a.smooth == b.smooth;
+}
+
+static hrt_status pm_tables(hrt_pm* pm, const hrt_filter& f, float** tab, hrt_filter* key) {
+  if (*tab && same_filter(f, *key)) return HRT_OK;
+  device_free(*tab, pm->stream);
+  *tab = nullptr;
+  HRT_TRY(filter_upload(pm->n, pm->box, f, tab, pm->stream));
+  *key = f;
+  return HRT_OK;
+}
+
+static hrt_status pm_solve(hrt_pm* pm, float* rho, double pref, const hrt_filter* f, float* grad,
+                           const hrt_filter* fr, float* ray_grad, hrt_ctx* prof = nullptr) {
+  static hrt_ctx no_profiling;
+  hrt_ctx* pc = prof ? prof : &no_profiling;
+  HRT_TRY(check_filter(f));
+  const bool rays = pm->n_ray > 0 && ray_grad != nullptr;
+  if (rays) HRT_TRY(check_filter(fr));
+  HRT_TRY(pm_tables(pm, *f, &pm->tab_a, &pm->key_a));
+  if (rays) HRT_TRY(pm_tables(pm, *fr, &pm->tab_b, &pm->key_b));
+  {
+    PhaseScope ps(pc, 3);
+    HRT_CUFFT(cufftExecR2C(pm->r2c, rho, static_cast<cufftComplex*>(pm->rho_hat)));
+  }
+  const size_t sb = spectrum_bytes(pm->n);
+  char* gh = static_cast<char*>(pm->grad_hat);
+  {
+    PhaseScope ps(pc, 4);
+    HRT_TRY(launch_kspace(pm->rho_hat, pm->n, pm->box, pref, pm->tab_a, f, 3, gh, rays ? pm->tab_b : nullptr, fr,
+                          rays ? pm->n_ray : 0, gh + 3 * sb, pm->stream));
+  }
+  const size_t mb = static_cast<size_t>(pm->n) * pm->n * pm->n;
+  PhaseScope ps(pc, 5);
+  for (int j = 0; j < 3; ++j)
+    HRT_CUFFT(cufftExecC2R(pm->c2r, reinterpret_cast<cufftComplex*>(gh + j * sb), grad + j * mb));
+  if (rays)
+    for (int j = 0; j < pm->n_ray; ++j)
+      HRT_CUFFT(cufftExecC2R(pm->c2r, reinterpret_cast<cufftComplex*>(gh + (3 + j) * sb), ray_grad + j * mb));
+  return HRT_OK;
+}
+
+}  // namespace hrt
+
+
+namespace hrt {
+
+static hrt_status ctx_guard(hrt_ctx* ctx) {
+  if (!ctx) return fail(HRT_ERR_INVALID_ARG, "context is NULL");
+  if (ctx->poisoned) return fail(HRT_ERR_STATE, "context is poisoned by an earlier CUDA error");
+  return HRT_OK;
+}
+
+static hrt_status ctx_mark(hrt_ctx* ctx, hrt_status s) {
+  if (s == HRT_ERR_CUDA) ctx->poisoned = true;
+  return s;
+}
+
+static hrt_filter ctx_filter(const hrt_config& c, bool ray) {
+  hrt_filter f{};
+  const double cell = c.box / c.n_mesh;
+  f.deconv_p = ray ? c.ray_deconv_p : c.deconv_p;
+  f.smooth = (ray ? c.ray_smooth_cells : c.smooth_cells) * cell;
+  return f;
+}
+
+static double ctx_pref(const hrt_ctx* ctx, double a) {
+  return ctx->cfg.static_mode ? ctx->cfg.static_pref : 1.5 * ctx->cfg.cosmo.omega_m / a;
+}
+
+static hrt_status ctx_force(hrt_ctx* ctx) {
+  const hrt_config& c = ctx->cfg;
+  {
+    PhaseScope ps(ctx, 2);
+    HRT_TRY(launch_cic_scatter(ctx->disp, c.n_side, c.n_mesh, c.box, ctx->rho, ctx->stream));
+  }
+  hrt_filter f = ctx_filter(c, false), fr = ctx_filter(c, true);
+  return pm_solve(ctx->pm, ctx->rho, ctx_pref(ctx, ctx->a), &f, ctx->grad, &fr, ctx->ray_grad, ctx);
+}
+
+
+static hrt_ray_geom ctx_geom(const hrt_config& c) {
+  hrt_ray_geom g{};
+  g.n = c.n_mesh;
+  g.box = c.box;
+  std::memcpy(g.observer, c.observer, sizeof(g.observer));
+  g.samples_per_cell = c.samples_per_cell;
+  g.window_lo = c.window_lo;
+  g.window_hi = c.window_hi;
+  return g;
+}
+
+static hrt_status ctx_ray_step(hrt_ctx* ctx, double chi_from, double chi_to, double a_ref, int32_t source) {
+  const hrt_config& c = ctx->cfg;
+  if (source >= c.n_sources) return fail(HRT_ERR_INVALID_ARG, "source %d out of range", source);
+  static thread_local RayStepParams p;
+  HRT_TRY(build_ray_params(ctx_geom(c), chi_from, chi_to, a_ref, c.cosmo.omega_m, p));
+  const int64_t m = c.n_mesh * c.n_mesh * c.n_mesh;
+  const float* gx = ctx->ray_grad ? ctx->ray_grad : ctx->grad;
+  float* maps = source >= 0 ? ctx->maps + static_cast<int64_t>(source) * 4 * ctx->rays.n_rays : nullptr;
+  return launch_ray_step(ctx->rays, gx, gx + m, p, maps, ctx->stream);
+}
+
+}  // namespace hrt
+
+using namespace hrt;
+
+extern "C" {
+
+const char* hrt_status_string(hrt_status s) {
+  switch (s) {
+    case HRT_OK: return "HRT_OK";
+    case HRT_ERR_INVALID_ARG: return "HRT_ERR_INVALID_ARG";
+    case HRT_ERR_OOM: return "HRT_ERR_OOM";
+    case HRT_ERR_CUDA: return "HRT_ERR_CUDA";
+    case HRT_ERR_STATE: return "HRT_ERR_STATE";
+    case HRT_ERR_NONFINITE: return "HRT_ERR_NONFINITE";
+    case HRT_ERR_TIMEOUT: return "HRT_ERR_TIMEOUT";
+  }
+  return "HRT_ERR_UNKNOWN";
+}
+
+const char* hrt_last_error(void) { return g_err; }
+
+hrt_status hrt_cosmo_eval(double omega_m, double a, double out[4]) {
+  if (!out || !(omega_m > 0.0 && omega_m <= 1.0) || !(a > 0.0 && a <= 1.0)) return fail(HRT_ERR_INVALID_ARG, "bad cosmology arguments");
+  Cosmo c(omega_m);
+  out[0] = c.E(a);
+  out[1] = c.chi(a);
+  out[2] = c.D1(a);
+  out[3] = c.f(a);
+  return HRT_OK;
+}
+
+hrt_status hrt_cosmo_time_integrals(double omega_m, double a, double b, double out[2]) {
+  if (!out || !(omega_m > 0.0 && omega_m <= 1.0) || !(a > 0.0) || !(b > 0.0)) return fail(HRT_ERR_INVALID_ARG, "bad arguments");
+  Cosmo c(omega_m);
+  out[0] = c.kick(a, b);
+  out[1] = c.drift(a, b);
+  return HRT_OK;
+}
+
+hrt_status hrt_cosmo_a_of_chi(double omega_m, double chi, double* a) {
+  if (!a || !(omega_m > 0.0 && omega_m <= 1.0) || !(chi >= 0.0)) return fail(HRT_ERR_INVALID_ARG, "bad arguments");
+  *a = Cosmo(omega_m).a_of_chi(chi);
+  return HRT_OK;
+}
+
+hrt_status hrt_cosmo_power_amplitude(double omega_m, double h, double n_s, double sigma8, double* amp) {
+  if (!amp || !(omega_m > 0.0) || !(h > 0.0) || !(sigma8 > 0.0)) return fail(HRT_ERR_INVALID_ARG, "bad arguments");
+  *amp = power_amplitude(omega_m, h, n_s, sigma8);
+  return HRT_OK;
+}
+
+hrt_status hrt_cic_scatter(const float* disp, int64_t n_side, int64_t n, double box, float* rho, void* stream) {
+  HRT_TRY(check_mesh(n, box));
+  HRT_TRY(check_particles(n_side, n));
+  if (!disp || !rho) return fail(HRT_ERR_INVALID_ARG, "NULL buffer");
+  return launch_cic_scatter(disp, n_side, n, box, rho, as_stream(stream));
+}
+
+hrt_status hrt_particle_kick_drift(const float* grad, int64_t n, double box, int64_t n_side, float* disp,
+                                   float* mom, double kick, double drift, void* stream) {
+  HRT_TRY(check_mesh(n, box));
+  HRT_TRY(check_particles(n_side, n));
+  if (!grad || !disp || !mom) return fail(HRT_ERR_INVALID_ARG, "NULL buffer");
+  if (!std::isfinite(kick) || !std::isfinite(drift)) return fail(HRT_ERR_INVALID_ARG, "non-finite coefficient");
+  return launch_kick_drift(grad, n, box, n_side, disp, mom, kick, drift, as_stream(stream));
+}
+
+hrt_status hrt_kspace_gradient(const void* rho_hat, int64_t n, double box, double pref, const hrt_filter* f,
+                               int32_t n_out, void* out, const hrt_filter* f2, int32_t n_second, void* second,
+                               void* stream) {
+  HRT_TRY(check_mesh(n, box));
+  HRT_TRY(check_filter(f));
+  if (!rho_hat || !out || n_out < 1 || n_out > 3) return fail(HRT_ERR_INVALID_ARG, "bad primary output");
+  if (second && (n_second < 1 || n_second > 3)) return fail(HRT_ERR_INVALID_ARG, "bad second output count");
+  if (second) HRT_TRY(check_filter(f2));
+  if (!std::isfinite(pref)) return fail(HRT_ERR_INVALID_ARG, "non-finite prefactor");
+  cudaStream_t s = as_stream(stream);
+  float* ta = nullptr;
+  float* tb = nullptr;
+  hrt_status st = filter_upload(n, box, *f, &ta, s);
+  if (st == HRT_OK && second) st = filter_upload(n, box, *f2, &tb, s);
+  if (st == HRT_OK)
+    st = launch_kspace(rho_hat, n, box, pref, ta, f, n_out, out, tb, f2, second ? n_second : 0, second, s);
+  device_free(ta, s);
+  device_free(tb, s);
+  return st;
+}
+
+hrt_status hrt_pm_create(int64_t n, double box, int32_t n_ray_fields, void* stream, hrt_pm** out) {
+  if (!out) return fail(HRT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  HRT_TRY(check_mesh(n, box));
+  if (n_ray_fields != 0 && n_ray_fields != 2) return fail(HRT_ERR_INVALID_ARG, "n_ray_fields must be 0 or 2");
+  hrt_pm* pm = new (std::nothrow) hrt_pm();
+  if (!pm) return fail(HRT_ERR_OOM, "host allocation");
+  hrt_status s = pm_make(n, box, n_ray_fields, as_stream(stream), pm);
+  if (s != HRT_OK) {
+    pm_release(pm);
+    delete pm;
+    return s;
+  }
+  *out = pm;
+  return HRT_OK;
+}
+
+hrt_status hrt_pm_destroy(hrt_pm* pm) {
+  if (!pm) return HRT_OK;
+  pm_release(pm);
+  delete pm;
+  return HRT_OK;
+}
+
+hrt_status hrt_pm_solve(hrt_pm* pm, float* rho, double pref, const hrt_filter* f, float* grad,
+                        const hrt_filter* f_ray, float* ray_grad) {
+  if (!pm || !rho || !grad) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  if (ray_grad && pm->n_ray == 0) return fail(HRT_ERR_INVALID_ARG, "PM object has no ray fields");
+  return pm_solve(pm, rho, pref, f, grad, f_ray, ray_grad);
+}
+
+hrt_status hrt_rays_init(const hrt_rays* rays, const double* theta0, void* stream) {
+  HRT_TRY(check_rays(rays));
+  if (rays->n_rays > 0 && !theta0) return fail(HRT_ERR_INVALID_ARG, "theta0 is NULL");
+  return launch_rays_init(*rays, theta0, as_stream(stream));
+}
+
+hrt_status hrt_ray_step(const hrt_rays* rays, const float* grad_x, const float* grad_y, const hrt_ray_geom* geom,
+                        double chi_from, double chi_to, double a_ref, double omega_m, float* maps, void* stream) {
+  HRT_TRY(check_rays(rays));
+  if (!geom || !grad_x || !grad_y) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  if (!std::isfinite(chi_from) || !std::isfinite(chi_to) || !(a_ref >= 0.0) || a_ref > 1.0)
+    return fail(HRT_ERR_INVALID_ARG, "bad step range");
+  if (a_ref > 0.0 && !(omega_m > 0.0 && omega_m <= 1.0)) return fail(HRT_ERR_INVALID_ARG, "bad omega_m");
+  static thread_local RayStepParams p;
+  HRT_TRY(build_ray_params(*geom, chi_from, chi_to, a_ref, omega_m, p));
+  return launch_ray_step(*rays, grad_x, grad_y, p, maps, as_stream(stream));
+}
+
+hrt_status hrt_ray_drift_free(const hrt_rays* rays, double chi_from, double chi_to, void* stream) {
+  HRT_TRY(check_rays(rays));
+  if (!(chi_from > 0.0) || !(chi_to > 0.0)) return fail(HRT_ERR_INVALID_ARG, "free drift needs chi > 0");
+  return launch_ray_drift_free(*rays, (1.0 / chi_from - 1.0 / chi_to) / kCLight, as_stream(stream));
+}
+
+hrt_status hrt_ray_readout(const hrt_rays* rays, float* maps, void* stream) {
+  HRT_TRY(check_rays(rays));
+  if (!maps) return fail(HRT_ERR_INVALID_ARG, "maps is NULL");
+  return launch_ray_readout(*rays, maps, as_stream(stream));
+}
+
+hrt_status hrt_kappa_power(const float* kappa, int64_t m, double dtheta, int32_t nbins, double ell_min,
+                           double ell_max, double* ell_host, double* p_host, int64_t* count_host, void* stream) {
+  if (!kappa || !ell_host || !p_host || !count_host) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  if (m < 2 || m % 2 || m > 16384 || nbins < 1 || nbins > 256 || !(dtheta > 0.0) || !(ell_min > 0.0) ||
+      !(ell_max > ell_min))
+    return fail(HRT_ERR_INVALID_ARG, "bad power-spectrum arguments");
+  cudaStream_t s = as_stream(stream);
+  cufftHandle plan;
+  HRT_CUFFT(cufftPlan2d(&plan, static_cast<int>(m), static_cast<int>(m), CUFFT_R2C));
+  void* spec = nullptr;
+  double* sums = nullptr;
+  hrt_status st = cufft_status(cufftSetStream(plan, s), "cufftSetStream");
+  if (st == HRT_OK) st = device_alloc(&spec, static_cast<size_t>(m) * (m / 2 + 1) * sizeof(float2), s, "kappa spectrum");
+  if (st == HRT_OK) st = device_alloc(reinterpret_cast<void**>(&sums), 3 * nbins * sizeof(double), s, "power bins");
+  if (st == HRT_OK)
+    st = cufft_status(cufftExecR2C(plan, const_cast<float*>(kappa), static_cast<cufftComplex*>(spec)), "cufftExecR2C");
+  if (st == HRT_OK) st = launch_power_bin(spec, m, dtheta, nbins, ell_min, ell_max, sums, s);
+  std::vector<double> h(3 * nbins);
+  if (st == HRT_OK) st = cuda_status(cudaMemcpyAsync(h.data(), sums, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "power bins copy");
+  if (st == HRT_OK) st = cuda_status(cudaStreamSynchronize(s), "power bins sync");
+  device_free(spec, s);
+  device_free(sums, s);
+  cudaStreamSynchronize(s);
+  cufftDestroy(plan);
+  if (st != HRT_OK) return st;
+  for (int b = 0; b < nbins; ++b) {
+    double cnt = h[2 * nbins + b];
+    count_host[b] = static_cast<int64_t>(std::llround(cnt));
+    p_host[b] = cnt > 0 ? h[b] / cnt : 0.0;
+    ell_host[b] = cnt > 0 ? h[nbins + b] / cnt : 0.0;
+  }
+  return HRT_OK;
+}
+
+hrt_status hrt_ic_zeldovich(const float* noise, int64_t n_side, double box, const hrt_cosmology* cosmo,
+                            double a_init, float* disp, float* mom, void* stream) {
+  HRT_TRY(check_mesh(n_side, box));
+  if (!noise || !cosmo || !disp || !mom) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  if (!(a_init > 0.0 && a_init <= 1.0) || !(cosmo->omega_m > 0.0 && cosmo->omega_m <= 1.0))
+    return fail(HRT_ERR_INVALID_ARG, "bad cosmology");
+  cudaStream_t s = as_stream(stream);
+  const int64_t n = n_side;
+  Cosmo c(cosmo->omega_m);
+  const double amp = power_amplitude(cosmo->omega_m, cosmo->h, cosmo->n_s, cosmo->sigma8);
+  const double d1 = c.D1(a_init);
+  const double ratio = a_init * a_init * c.E(a_init) * c.f(a_init);
+  const double kf = 2.0 * M_PI / box, v_cell = std::pow(box / n, 3);
+  const int64_t max_n2 = 3 * (n / 2) * (n / 2);
+  std::vector<float> table(max_n2 + 1);
+  table[0] = 0.f;
+  for (int64_t i = 1; i <= max_n2; ++i) {
+    double k = kf * std::sqrt(static_cast<double>(i));
+    double pk = amp * std::pow(k, cosmo->n_s) * std::pow(bbks_transfer(k / (cosmo->omega_m * cosmo->h)), 2);
+    table[i] = static_cast<float>(d1 * std::sqrt(pk / v_cell) / (k * k) / (static_cast<double>(n) * n * n));
+  }
+  hrt_pm tmp;
+  hrt_status st = pm_make(n, box, 0, s, &tmp);
+  float* tab = nullptr;
+  if (st == HRT_OK) st = upload(table, &tab, s, "IC table");
+  if (st == HRT_OK)
+    st = cufft_status(cufftExecR2C(tmp.r2c, const_cast<float*>(noise), static_cast<cufftComplex*>(tmp.rho_hat)), "IC R2C");
+  if (st == HRT_OK) st = launch_ic_kspace(tmp.rho_hat, n, box, tab, tmp.grad_hat, s);
+  const size_t sb = spectrum_bytes(n);
+  const int64_t np = n * n * n;
+  for (int j = 0; j < 3 && st == HRT_OK; ++j)
+    st = cufft_status(cufftExecC2R(tmp.c2r, reinterpret_cast<cufftComplex*>(static_cast<char*>(tmp.grad_hat) + j * sb),
+                                   disp + j * np), "IC C2R");
+  if (st == HRT_OK) st = launch_scale_copy(disp, mom, ratio, 3 * np, s);
+  device_free(tab, s);
+  pm_release(&tmp);
+  return st;
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------------------------------------
+static hrt_status check_config(const hrt_config* c) {
+  if (!c) return fail(HRT_ERR_INVALID_ARG, "config is NULL");
+  HRT_TRY(check_mesh(c->n_mesh, c->box));
+  HRT_TRY(check_particles(c->n_side, c->n_mesh));
+  if (!(c->samples_per_cell > 0.0)) return fail(HRT_ERR_INVALID_ARG, "samples_per_cell must be > 0");
+  if (!(c->smooth_cells >= 0.0) || !std::isfinite(c->deconv_p)) return fail(HRT_ERR_INVALID_ARG, "bad filter");
+  if (c->n_sources < 0 || c->n_sources > 64) return fail(HRT_ERR_INVALID_ARG, "n_sources must be 0..64");
+  if (c->ray_fields != 0 && c->ray_fields != 2) return fail(HRT_ERR_INVALID_ARG, "ray_fields must be 0 or 2");
+  if (!c->static_mode && !(c->cosmo.omega_m > 0.0 && c->cosmo.omega_m <= 1.0)) return fail(HRT_ERR_INVALID_ARG, "bad omega_m");
+  if (!(c->window_hi > c->window_lo)) return fail(HRT_ERR_INVALID_ARG, "empty force window");
+  return HRT_OK;
+}
+
+hrt_status hrt_workspace_bytes(const hrt_config* cfg, int64_t n_rays, size_t* bytes) {
+  HRT_TRY(check_config(cfg));
+  if (!bytes || n_rays < 0) return fail(HRT_ERR_INVALID_ARG, "bad arguments");
+  const size_t n = cfg->n_mesh, mesh = n * n * n * sizeof(float), np = cfg->n_side * cfg->n_side * cfg->n_side;
+  size_t b = 6 * np * sizeof(float) + mesh * (4 + cfg->ray_fields);
+  b += spectrum_bytes(cfg->n_mesh) * (1 + 3 + cfg->ray_fields) + 2 * spectrum_bytes(cfg->n_mesh);  // + cuFFT work
+  b += static_cast<size_t>(n_rays) * (2 * sizeof(double) + 10 * sizeof(float));
+  b += static_cast<size_t>(n_rays) * 4 * sizeof(float) * cfg->n_sources;
+  *bytes = b;
+  return HRT_OK;
+}
+
+hrt_status hrt_destroy(hrt_ctx* ctx) {
+  if (!ctx) return HRT_OK;
+  cudaStream_t s = ctx->stream;
+  cudaStreamSynchronize(s);
+  for (auto& v : ctx->phases)
+    for (auto& ev : v) {
+      cudaEventDestroy(ev.first);
+      cudaEventDestroy(ev.second);
+    }
+  hrt_pm_destroy(ctx->pm);
+  device_free(ctx->disp, s);
+  device_free(ctx->mom, s);
+  device_free(ctx->rho, s);
+  device_free(ctx->grad, s);
+  device_free(ctx->ray_grad, s);
+  device_free(ctx->rays.theta, s);
+  device_free(ctx->rays.eta, s);
+  device_free(ctx->rays.A, s);
+  device_free(ctx->rays.B, s);
+  device_free(ctx->maps, s);
+  cudaStreamSynchronize(s);
+  cudaGetLastError();
+  delete ctx;
+  return HRT_OK;
+}
+
+hrt_status hrt_create(const hrt_config* cfg, void* stream, hrt_ctx** out) {
+  if (!out) return fail(HRT_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  HRT_TRY(check_config(cfg));
+  hrt_ctx* ctx = new (std::nothrow) hrt_ctx();
+  if (!ctx) return fail(HRT_ERR_OOM, "host allocation");
+  ctx->cfg = *cfg;
+  ctx->stream = as_stream(stream);
+  const int64_t n = cfg->n_mesh, m = n * n * n, np = cfg->n_side * cfg->n_side * cfg->n_side;
+  hrt_status s = hrt_pm_create(n, cfg->box, cfg->ray_fields, stream, &ctx->pm);
+  if (s == HRT_OK) s = device_alloc(reinterpret_cast<void**>(&ctx->disp), 3 * np * sizeof(float), ctx->stream, "disp");
+  if (s == HRT_OK) s = device_alloc(reinterpret_cast<void**>(&ctx->mom), 3 * np * sizeof(float), ctx->stream, "mom");
+  if (s == HRT_OK) s = device_alloc(reinterpret_cast<void**>(&ctx->rho), m * sizeof(float), ctx->stream, "rho");
+  if (s == HRT_OK) s = device_alloc(reinterpret_cast<void**>(&ctx->grad), 3 * m * sizeof(float), ctx->stream, "grad");
+  if (s == HRT_OK && cfg->ray_fields)
+    s = device_alloc(reinterpret_cast<void**>(&ctx->ray_grad), 2 * m * sizeof(float), ctx->stream, "ray grad");
+  if (s != HRT_OK) {
+    hrt_destroy(ctx);
+    return s;
+  }
+  *out = ctx;
+  return HRT_OK;
+}
+
+hrt_status hrt_init_particles_zeldovich(hrt_ctx* ctx, const float* noise, double a_init) {
+  HRT_TRY(ctx_guard(ctx));
+  if (ctx->cfg.static_mode) return fail(HRT_ERR_STATE, "Zel'dovich ICs need the expanding mode");
+  hrt_status s = hrt_ic_zeldovich(noise, ctx->cfg.n_side, ctx->cfg.box, &ctx->cfg.cosmo, a_init, ctx->disp,
+                                  ctx->mom, ctx->stream);
+  if (s != HRT_OK) return ctx_mark(ctx, s);
+  ctx->a = ctx->a_mom = a_init;
+  ctx->have_particles = true;
+  return ctx_mark(ctx, ctx_force(ctx));
+}
+
+hrt_status hrt_init_particles(hrt_ctx* ctx, const float* disp, const float* mom, double a) {
+  HRT_TRY(ctx_guard(ctx));
+  if (!disp || !mom || !(a > 0.0 && a <= 1.0)) return fail(HRT_ERR_INVALID_ARG, "bad particle arguments");
+  const size_t bytes = 3 * static_cast<size_t>(ctx->cfg.n_side * ctx->cfg.n_side * ctx->cfg.n_side) * sizeof(float);
+  hrt_status s = cuda_status(cudaMemcpyAsync(ctx->disp, disp, bytes, cudaMemcpyDeviceToDevice, ctx->stream), "copy disp");
+  if (s == HRT_OK) s = cuda_status(cudaMemcpyAsync(ctx->mom, mom, bytes, cudaMemcpyDeviceToDevice, ctx->stream), "copy mom");
+  if (s != HRT_OK) return ctx_mark(ctx, s);
+  ctx->a = ctx->a_mom = ctx->cfg.static_mode ? 1.0 : a;
+  ctx->have_particles = true;
+  return ctx_mark(ctx, ctx_force(ctx));
+}
+
+hrt_status hrt_init_rays(hrt_ctx* ctx, const double* theta0, int64_t n_rays) {
+  HRT_TRY(ctx_guard(ctx));
+  if (n_rays < 1 || !theta0) return fail(HRT_ERR_INVALID_ARG, "bad ray arguments");
+  cudaStream_t st = ctx->stream;
+  device_free(ctx->rays.theta, st);
+  device_free(ctx->rays.eta, st);
+  device_free(ctx->rays.A, st);
+  device_free(ctx->rays.B, st);
+  device_free(ctx->maps, st);
+  ctx->rays = hrt_rays{};
+  ctx->maps = nullptr;
+  hrt_rays r{};
+  r.n_rays = n_rays;
+  hrt_status s = device_alloc(reinterpret_cast<void**>(&r.theta), 2 * n_rays * sizeof(double), st, "theta");
+  if (s == HRT_OK) s = device_alloc(reinterpret_cast<void**>(&r.eta), 2 * n_rays * sizeof(float), st, "eta");
+  if (s == HRT_OK) s = device_alloc(reinterpret_cast<void**>(&r.A), 4 * n_rays * sizeof(float), st, "A");
+  if (s == HRT_OK) s = device_alloc(reinterpret_cast<void**>(&r.B), 4 * n_rays * sizeof(float), st, "B");
+  if (s == HRT_OK && ctx->cfg.n_sources > 0)
+    s = device_alloc(reinterpret_cast<void**>(&ctx->maps), 4 * n_rays * ctx->cfg.n_sources * sizeof(float), st, "maps");
+  if (s == HRT_OK && ctx->maps)
+    s = cuda_status(cudaMemsetAsync(ctx->maps, 0, 4 * n_rays * ctx->cfg.n_sources * sizeof(float), st), "maps memset");
+  if (s == HRT_OK) s = launch_rays_init(r, theta0, st);
+  if (s != HRT_OK) {
+    device_free(r.theta, st);
+    device_free(r.eta, st);
+    device_free(r.A, st);
+    device_free(r.B, st);
+    return ctx_mark(ctx, s);
+  }
+  ctx->rays = r;
+  return HRT_OK;
+}
+
+hrt_status hrt_step(hrt_ctx* ctx, double a_next, int32_t source) {
+  HRT_TRY(ctx_guard(ctx));
+  if (ctx->cfg.static_mode) return fail(HRT_ERR_STATE, "hrt_step needs the expanding mode");
+  if (!ctx->have_particles) return fail(HRT_ERR_STATE, "no particles");
+  if (!(a_next > 0.0 && a_next <= 1.0) || a_next == ctx->a) return fail(HRT_ERR_INVALID_ARG, "bad a_next");
+  Cosmo c(ctx->cfg.cosmo.omega_m);
+  hrt_status s = HRT_OK;
+  PhaseScope whole(ctx, 6);
+  if (ctx->rays.n_rays > 0 && a_next < ctx->a) {
+    PhaseScope ps(ctx, 0);
+    s = ctx_ray_step(ctx, c.chi(ctx->a), c.chi(a_next), ctx->a, source);
+    if (s != HRT_OK) return ctx_mark(ctx, s);
+  }
+  const double a_half = 0.5 * (ctx->a + a_next);
+  const double kick = c.kick(ctx->a_mom, a_half), drift = c.drift(ctx->a, a_next);
+  {
+    PhaseScope ps(ctx, 1);
+    s = launch_kick_drift(ctx->grad, ctx->cfg.n_mesh, ctx->cfg.box, ctx->cfg.n_side, ctx->disp, ctx->mom, kick,
+                          drift, ctx->stream);
+  }
+  if (s != HRT_OK) return ctx_mark(ctx, s);
+  ctx->a = a_next;
+  ctx->a_mom = a_half;
+  return ctx_mark(ctx, ctx_force(ctx));
+}
+
+hrt_status hrt_sync_particles(hrt_ctx* ctx) {
+  HRT_TRY(ctx_guard(ctx));
+  if (!ctx->have_particles) return fail(HRT_ERR_STATE, "no particles");
+  if (ctx->cfg.static_mode || ctx->a_mom == ctx->a) return HRT_OK;
+  Cosmo c(ctx->cfg.cosmo.omega_m);
+  hrt_status s = launch_kick_drift(ctx->grad, ctx->cfg.n_mesh, ctx->cfg.box, ctx->cfg.n_side, ctx->disp, ctx->mom,
+                                   c.kick(ctx->a_mom, ctx->a), 0.0, ctx->stream);
+  if (s == HRT_OK) ctx->a_mom = ctx->a;
+  return ctx_mark(ctx, s);
+}
+
+hrt_status hrt_step_static(hrt_ctx* ctx, double chi_from, double chi_to, int32_t source) {
+  HRT_TRY(ctx_guard(ctx));
+  if (!ctx->cfg.static_mode) return fail(HRT_ERR_STATE, "hrt_step_static needs the static mode");
+  if (!ctx->have_particles) return fail(HRT_ERR_STATE, "no lens particles");
+  if (ctx->rays.n_rays == 0) return fail(HRT_ERR_STATE, "no rays");
+  return ctx_mark(ctx, ctx_ray_step(ctx, chi_from, chi_to, 0.0, source));
+}
+
+hrt_status hrt_drift_free(hrt_ctx* ctx, double chi_from, double chi_to) {
+  HRT_TRY(ctx_guard(ctx));
+  if (ctx->rays.n_rays == 0) return fail(HRT_ERR_STATE, "no rays");
+  return ctx_mark(ctx, hrt_ray_drift_free(&ctx->rays, chi_from, chi_to, ctx->stream));
+}
+
+hrt_status hrt_read_rays(hrt_ctx* ctx, double* theta, float* eta, float* A, float* B) {
+  HRT_TRY(ctx_guard(ctx));
+  const int64_t r = ctx->rays.n_rays;
+  if (r == 0) return fail(HRT_ERR_STATE, "no rays");
+  hrt_status s = HRT_OK;
+  if (theta) s = cuda_status(cudaMemcpyAsync(theta, ctx->rays.theta, 2 * r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream), "read theta");
+  if (s == HRT_OK && eta) s = cuda_status(cudaMemcpyAsync(eta, ctx->rays.eta, 2 * r * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream), "read eta");
+  if (s == HRT_OK && A) s = cuda_status(cudaMemcpyAsync(A, ctx->rays.A, 4 * r * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream), "read A");
+  if (s == HRT_OK && B) s = cuda_status(cudaMemcpyAsync(B, ctx->rays.B, 4 * r * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream), "read B");
+  return ctx_mark(ctx, s);
+}
+
+hrt_status hrt_read_maps(hrt_ctx* ctx, int32_t source, float* kappa, float* gamma1, float* gamma2, float* omega) {
+  HRT_TRY(ctx_guard(ctx));
+  const int64_t r = ctx->rays.n_rays;
+  if (r == 0 || !ctx->maps) return fail(HRT_ERR_STATE, "no maps");
+  if (source < 0 || source >= ctx->cfg.n_sources) return fail(HRT_ERR_INVALID_ARG, "source out of range");
+  float* base = ctx->maps + static_cast<int64_t>(source) * 4 * r;
+  float* dst[4] = {kappa, gamma1, gamma2, omega};
+  for (int i = 0; i < 4; ++i)
+    if (dst[i]) {
+      hrt_status s = cuda_status(cudaMemcpyAsync(dst[i], base + i * r, r * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream), "read map");
+      if (s != HRT_OK) return ctx_mark(ctx, s);
+    }
+  return HRT_OK;
+}
+
+hrt_status hrt_read_particles(hrt_ctx* ctx, float* disp, float* mom, double* a_host, double* a_mom_host) {
+  HRT_TRY(ctx_guard(ctx));
+  if (!ctx->have_particles) return fail(HRT_ERR_STATE, "no particles");
+  const size_t bytes = 3 * static_cast<size_t>(ctx->cfg.n_side * ctx->cfg.n_side * ctx->cfg.n_side) * sizeof(float);
+  hrt_status s = HRT_OK;
+  if (disp) s = cuda_status(cudaMemcpyAsync(disp, ctx->disp, bytes, cudaMemcpyDeviceToDevice, ctx->stream), "read disp");
+  if (s == HRT_OK && mom) s = cuda_status(cudaMemcpyAsync(mom, ctx->mom, bytes, cudaMemcpyDeviceToDevice, ctx->stream), "read mom");
+  if (a_host) *a_host = ctx->a;
+  if (a_mom_host) *a_mom_host = ctx->a_mom;
+  return ctx_mark(ctx, s);
+}
+
+hrt_status hrt_read_grad(hrt_ctx* ctx, float* grad) {
+  HRT_TRY(ctx_guard(ctx));
+  if (!grad) return fail(HRT_ERR_INVALID_ARG, "grad is NULL");
+  if (!ctx->have_particles) return fail(HRT_ERR_STATE, "no force yet");
+  const size_t n = ctx->cfg.n_mesh;
+  return ctx_mark(ctx, cuda_status(cudaMemcpyAsync(grad, ctx->grad, 3 * n * n * n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream), "read grad"));
+}
+
+hrt_status hrt_ctx_kappa_power(hrt_ctx* ctx, int32_t source, int64_t m, double dtheta, int32_t nbins, double ell_min,
+                               double ell_max, double* ell_host, double* p_host, int64_t* count_host) {
+  HRT_TRY(ctx_guard(ctx));
+  if (!ctx->maps || source < 0 || source >= ctx->cfg.n_sources) return fail(HRT_ERR_INVALID_ARG, "no such map");
+  if (m * m != ctx->rays.n_rays) return fail(HRT_ERR_INVALID_ARG, "rays do not form an m x m image");
+  const float* kappa = ctx->maps + static_cast<int64_t>(source) * 4 * ctx->rays.n_rays;
+  return ctx_mark(ctx, hrt_kappa_power(kappa, m, dtheta, nbins, ell_min, ell_max, ell_host, p_host, count_host, ctx->stream));
+}
+
+hrt_status hrt_ctx_set_profiling(hrt_ctx* ctx, int32_t on) {
+  HRT_TRY(ctx_guard(ctx));
+  ctx->profiling = on != 0;
+  return HRT_OK;
+}
+
+hrt_status hrt_ctx_phase_times(hrt_ctx* ctx, double* ms, int64_t* counts) {
+  HRT_TRY(ctx_guard(ctx));
+  if (!ms || !counts) return fail(HRT_ERR_INVALID_ARG, "NULL output");
+  hrt_status st = cuda_status(cudaStreamSynchronize(ctx->stream), "phase sync");
+  for (int p = 0; p < 8; ++p) {
+    double sum = 0.0;
+    for (auto& ev : ctx->phases[p]) {
+      float t = 0.f;
+      if (st == HRT_OK && cudaEventElapsedTime(&t, ev.first, ev.second) == cudaSuccess) sum += t;
+      cudaEventDestroy(ev.first);
+      cudaEventDestroy(ev.second);
+    }
+    ms[p] = sum;
+    counts[p] = static_cast<int64_t>(ctx->phases[p].size());
+    ctx->phases[p].clear();
+  }
+  return ctx_mark(ctx, st);
+}
+
+hrt_status hrt_ctx_rays(hrt_ctx* ctx, hrt_rays* out) {
+  HRT_TRY(ctx_guard(ctx));
+  if (!out) return fail(HRT_ERR_INVALID_ARG, "out is NULL");
+  *out = ctx->rays;
+  return HRT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+// Launch wrappers of the mesh kernels (mesh_kernels.cu) and the ray kernels (ray_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "common.h"
+
+namespace hrt {
+
+hrt_status launch_cic_scatter(const float* disp, int64_t n_side, int64_t n, double box, float* rho,
+                              cudaStream_t s);
+
+void filter_tables(int64_t n, double box, const hrt_filter& f, std::vector<float>& wxy, std::vector<float>& wz);
+
+// tab_* are device tables laid out [wxy (n) | wz (n/2+1)] for each filter set.
+hrt_status launch_kspace(const void* rho_hat, int64_t n, double box, double pref, const float* tab_a,
+                         const hrt_filter* fa, int n_a, void* out_a, const float* tab_b, const hrt_filter* fb,
+                         int n_b, void* out_b, cudaStream_t s);
+
+hrt_status launch_kick_drift(const float* grad, int64_t n, double box, int64_t n_side, float* disp, float* mom,
+                             double kick, double drift, cudaStream_t s);
+
+hrt_status launch_ic_kspace(const void* w_hat, int64_t n, double box, const float* table, void* out,
+                            cudaStream_t s);
+
+hrt_status launch_scale_copy(const float* in, float* out, double ratio, int64_t m, cudaStream_t s);
+
+// ---- rays ----
+constexpr int kMaxRayNodes = 1024;
+
+struct RayStepParams {
+  int n1, n2;            // nodes of the first and second half shell (after the force window)
+  int n;                 // mesh cells per side
+  float drift;           // (chi_to - chi_from) / (c chi_mid^2), float32 copy for A
+  double drift_d;        // the same in FP64 for theta
+  double ref_r[2];       // reference radius of each half shell for the FP64 base position
+  double obs_x, obs_y;   // observer transverse position
+  double cell, box;
+  float dr[kMaxRayNodes];   // (r_j - ref_r) / cell
+  float cw[kMaxRayNodes];   // c_j
+  float cwr[kMaxRayNodes];  // c_j r_j / cell
+  int kz[kMaxRayNodes];     // lower z node of the sample
+  float fz[kMaxRayNodes];   // z fraction of the sample
+};
+
+hrt_status launch_ray_step(const hrt_rays& rays, const float* gx, const float* gy, const RayStepParams& p,
+                           float* maps, cudaStream_t s);
+hrt_status launch_ray_drift_free(const hrt_rays& rays, double d, cudaStream_t s);
+hrt_status launch_ray_readout(const hrt_rays& rays, float* maps, cudaStream_t s);
+hrt_status launch_rays_init(const hrt_rays& rays, const double* theta0, cudaStream_t s);
+
+// Power-spectrum binning of an m x (m/2+1) half spectrum into sums[3][nbins] (power, ell, count).
+hrt_status launch_power_bin(const void* spec, int64_t m, double dtheta, int nbins, double ell_min, double ell_max,
+                            double* sums, cudaStream_t s);
+
+}  // namespace hrt

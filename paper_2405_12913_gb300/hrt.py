@@ -1,0 +1,435 @@
+"""Thin Python binding of the C ABI in ``include/hrt.h`` (argument marshalling only).
+
+Every function keeps the C name and forwards torch CUDA tensors as raw device pointers on the current torch
+stream (or an explicit ``stream``).  All arithmetic happens in ``libhrt.so``; if the library is missing the
+import of this module raises, so there is no silent CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhrt.so")
+
+HRT_OK = 0
+STATUS_NAMES = {0: "HRT_OK", 1: "HRT_ERR_INVALID_ARG", 2: "HRT_ERR_OOM", 3: "HRT_ERR_CUDA", 4: "HRT_ERR_STATE",
+                5: "HRT_ERR_NONFINITE", 6: "HRT_ERR_TIMEOUT"}
+
+
+class HRTError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class hrt_filter(C.Structure):
+    _fields_ = [("deconv_p", C.c_double), ("smooth", C.c_double), ("g_table", C.c_void_p), ("g_nk", C.c_int32),
+                ("g_kmax", C.c_double)]
+
+
+class hrt_rays(C.Structure):
+    _fields_ = [("theta", C.c_void_p), ("eta", C.c_void_p), ("A", C.c_void_p), ("B", C.c_void_p),
+                ("n_rays", C.c_int64)]
+
+
+class hrt_ray_geom(C.Structure):
+    _fields_ = [("n", C.c_int64), ("box", C.c_double), ("observer", C.c_double * 3),
+                ("samples_per_cell", C.c_double), ("window_lo", C.c_double), ("window_hi", C.c_double)]
+
+
+class hrt_cosmology(C.Structure):
+    _fields_ = [("omega_m", C.c_double), ("h", C.c_double), ("n_s", C.c_double), ("sigma8", C.c_double)]
+
+
+class hrt_config(C.Structure):
+    _fields_ = [("n_mesh", C.c_int64), ("box", C.c_double), ("n_side", C.c_int64), ("cosmo", hrt_cosmology),
+                ("deconv_p", C.c_double), ("smooth_cells", C.c_double), ("samples_per_cell", C.c_double),
+                ("observer", C.c_double * 3), ("static_mode", C.c_int32), ("static_pref", C.c_double),
+                ("window_lo", C.c_double), ("window_hi", C.c_double), ("n_sources", C.c_int32),
+                ("ray_fields", C.c_int32), ("ray_deconv_p", C.c_double), ("ray_smooth_cells", C.c_double)]
+
+
+_P = C.c_void_p
+_D = C.c_double
+_I64 = C.c_int64
+_I32 = C.c_int32
+_SIGS = {
+    "hrt_status_string": ([C.c_int], C.c_char_p),
+    "hrt_last_error": ([], C.c_char_p),
+    "hrt_cosmo_eval": ([_D, _D, _P], C.c_int),
+    "hrt_cosmo_time_integrals": ([_D, _D, _D, _P], C.c_int),
+    "hrt_cosmo_a_of_chi": ([_D, _D, _P], C.c_int),
+    "hrt_cosmo_power_amplitude": ([_D, _D, _D, _D, _P], C.c_int),
+    "hrt_cic_scatter": ([_P, _I64, _I64, _D, _P, _P], C.c_int),
+    "hrt_particle_kick_drift": ([_P, _I64, _D, _I64, _P, _P, _D, _D, _P], C.c_int),
+    "hrt_kspace_gradient": ([_P, _I64, _D, _D, _P, _I32, _P, _P, _I32, _P, _P], C.c_int),
+    "hrt_pm_create": ([_I64, _D, _I32, _P, _P], C.c_int),
+    "hrt_pm_destroy": ([_P], C.c_int),
+    "hrt_pm_solve": ([_P, _P, _D, _P, _P, _P, _P], C.c_int),
+    "hrt_rays_init": ([_P, _P, _P], C.c_int),
+    "hrt_ray_step": ([_P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
+    "hrt_ray_drift_free": ([_P, _D, _D, _P], C.c_int),
+    "hrt_ray_readout": ([_P, _P, _P], C.c_int),
+    "hrt_kappa_power": ([_P, _I64, _D, _I32, _D, _D, _P, _P, _P, _P], C.c_int),
+    "hrt_ic_zeldovich": ([_P, _I64, _D, _P, _D, _P, _P, _P], C.c_int),
+    "hrt_create": ([_P, _P, _P], C.c_int),
+    "hrt_destroy": ([_P], C.c_int),
+    "hrt_workspace_bytes": ([_P, _I64, _P], C.c_int),
+    "hrt_init_particles_zeldovich": ([_P, _P, _D], C.c_int),
+    "hrt_init_particles": ([_P, _P, _P, _D], C.c_int),
+    "hrt_init_rays": ([_P, _P, _I64], C.c_int),
+    "hrt_step": ([_P, _D, _I32], C.c_int),
+    "hrt_sync_particles": ([_P], C.c_int),
+    "hrt_step_static": ([_P, _D, _D, _I32], C.c_int),
+    "hrt_drift_free": ([_P, _D, _D], C.c_int),
+    "hrt_read_rays": ([_P, _P, _P, _P, _P], C.c_int),
+    "hrt_read_maps": ([_P, _I32, _P, _P, _P, _P], C.c_int),
+    "hrt_read_particles": ([_P, _P, _P, _P, _P], C.c_int),
+    "hrt_read_grad": ([_P, _P], C.c_int),
+    "hrt_ctx_kappa_power": ([_P, _I32, _I64, _D, _I32, _D, _D, _P, _P, _P], C.c_int),
+    "hrt_ctx_set_profiling": ([_P, _I32], C.c_int),
+    "hrt_ctx_phase_times": ([_P, _P, _P], C.c_int),
+    "hrt_ctx_rays": ([_P, _P], C.c_int),
+}
+EXPORTED = tuple(_SIGS)
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(LIB_PATH)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def _check(status: int, where: str) -> None:
+    if status != HRT_OK:
+        raise HRTError(status, where, _lib.hrt_last_error().decode())
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t: torch.Tensor | None, dtype=None, name: str = "tensor") -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def _host_ptr(t: torch.Tensor | None, dtype, name: str) -> int | None:
+    if t is None:
+        return None
+    if t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous host {dtype} tensor")
+    return t.data_ptr()
+
+
+def status_string(status: int) -> str:
+    return _lib.hrt_status_string(status).decode()
+
+
+# ------------------------------------------------------------------------------------------------ cosmology
+def hrt_cosmo_eval(omega_m: float, a: float):
+    out = (C.c_double * 4)()
+    _check(_lib.hrt_cosmo_eval(omega_m, a, out), "hrt_cosmo_eval")
+    return tuple(out)
+
+
+def hrt_cosmo_time_integrals(omega_m: float, a: float, b: float):
+    out = (C.c_double * 2)()
+    _check(_lib.hrt_cosmo_time_integrals(omega_m, a, b, out), "hrt_cosmo_time_integrals")
+    return tuple(out)
+
+
+def hrt_cosmo_a_of_chi(omega_m: float, chi: float) -> float:
+    out = C.c_double()
+    _check(_lib.hrt_cosmo_a_of_chi(omega_m, chi, C.byref(out)), "hrt_cosmo_a_of_chi")
+    return out.value
+
+
+def hrt_cosmo_power_amplitude(omega_m: float, h: float, n_s: float, sigma8: float) -> float:
+    out = C.c_double()
+    _check(_lib.hrt_cosmo_power_amplitude(omega_m, h, n_s, sigma8, C.byref(out)), "hrt_cosmo_power_amplitude")
+    return out.value
+
+
+# ------------------------------------------------------------------------------------------------ mesh kernels
+def make_filter(deconv_p: float = 0.0, smooth: float = 0.0, g_table: torch.Tensor | None = None,
+                g_kmax: float = 0.0) -> hrt_filter:
+    f = hrt_filter()
+    f.deconv_p = deconv_p
+    f.smooth = smooth
+    if g_table is not None:
+        f.g_table = _ptr(g_table, torch.float32, "g_table")
+        f.g_nk = g_table.numel()
+        f.g_kmax = g_kmax
+    return f
+
+
+def hrt_cic_scatter(disp: torch.Tensor, n_side: int, n: int, box: float, rho: torch.Tensor, stream=None):
+    _check(_lib.hrt_cic_scatter(_ptr(disp, torch.float32, "disp"), n_side, n, box, _ptr(rho, torch.float32, "rho"),
+                                _stream(stream)), "hrt_cic_scatter")
+
+
+def hrt_particle_kick_drift(grad: torch.Tensor, n: int, box: float, n_side: int, disp: torch.Tensor,
+                            mom: torch.Tensor, kick: float, drift: float, stream=None):
+    _check(_lib.hrt_particle_kick_drift(_ptr(grad, torch.float32, "grad"), n, box, n_side,
+                                        _ptr(disp, torch.float32, "disp"), _ptr(mom, torch.float32, "mom"), kick,
+                                        drift, _stream(stream)), "hrt_particle_kick_drift")
+
+
+def hrt_kspace_gradient(rho_hat: torch.Tensor, n: int, box: float, pref: float, f: hrt_filter, n_out: int,
+                        out: torch.Tensor, f2: hrt_filter | None = None, n_second: int = 0,
+                        second: torch.Tensor | None = None, stream=None):
+    _check(_lib.hrt_kspace_gradient(_ptr(rho_hat, torch.complex64, "rho_hat"), n, box, pref, C.byref(f), n_out,
+                                    _ptr(out, torch.complex64, "out"), C.byref(f2) if f2 is not None else None,
+                                    n_second, _ptr(second, torch.complex64, "second"), _stream(stream)),
+           "hrt_kspace_gradient")
+
+
+class PM:
+    """Owner of an ``hrt_pm`` object (cuFFT plans and spectra for one mesh size)."""
+
+    def __init__(self, n: int, box: float, n_ray_fields: int = 0, stream=None):
+        self._h = C.c_void_p()
+        _check(_lib.hrt_pm_create(n, box, n_ray_fields, _stream(stream), C.byref(self._h)), "hrt_pm_create")
+        self.n, self.box = n, box
+
+    def solve(self, rho: torch.Tensor, pref: float, f: hrt_filter, grad: torch.Tensor,
+              f_ray: hrt_filter | None = None, ray_grad: torch.Tensor | None = None):
+        _check(_lib.hrt_pm_solve(self._h, _ptr(rho, torch.float32, "rho"), pref, C.byref(f),
+                                 _ptr(grad, torch.float32, "grad"), C.byref(f_ray) if f_ray is not None else None,
+                                 _ptr(ray_grad, torch.float32, "ray_grad")), "hrt_pm_solve")
+
+    def close(self):
+        if self._h:
+            _lib.hrt_pm_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+# ------------------------------------------------------------------------------------------------ rays
+class RayState:
+    """Caller-owned device ray state (theta f64 [R,2], eta f32 [R,2], A, B f32 [R,4])."""
+
+    def __init__(self, n_rays: int, device="cuda"):
+        self.theta = torch.empty(n_rays, 2, dtype=torch.float64, device=device)
+        self.eta = torch.empty(n_rays, 2, dtype=torch.float32, device=device)
+        self.A = torch.empty(n_rays, 4, dtype=torch.float32, device=device)
+        self.B = torch.empty(n_rays, 4, dtype=torch.float32, device=device)
+        self.n_rays = n_rays
+
+    def c(self) -> hrt_rays:
+        r = hrt_rays()
+        r.theta, r.eta, r.A, r.B = self.theta.data_ptr(), self.eta.data_ptr(), self.A.data_ptr(), self.B.data_ptr()
+        r.n_rays = self.n_rays
+        return r
+
+
+def make_geom(n: int, box: float, observer, samples_per_cell: float = 1.0, window=(-1e300, 1e300)) -> hrt_ray_geom:
+    g = hrt_ray_geom()
+    g.n, g.box = n, box
+    for i in range(3):
+        g.observer[i] = observer[i]
+    g.samples_per_cell = samples_per_cell
+    g.window_lo, g.window_hi = window
+    return g
+
+
+def hrt_rays_init(rays: RayState, theta0: torch.Tensor, stream=None):
+    r = rays.c()
+    _check(_lib.hrt_rays_init(C.byref(r), _ptr(theta0, torch.float64, "theta0"), _stream(stream)), "hrt_rays_init")
+
+
+def hrt_ray_step(rays: RayState, grad_x: torch.Tensor, grad_y: torch.Tensor, geom: hrt_ray_geom, chi_from: float,
+                 chi_to: float, a_ref: float = 0.0, omega_m: float = 0.3, maps: torch.Tensor | None = None,
+                 stream=None):
+    r = rays.c()
+    _check(_lib.hrt_ray_step(C.byref(r), _ptr(grad_x, torch.float32, "grad_x"), _ptr(grad_y, torch.float32, "grad_y"),
+                             C.byref(geom), chi_from, chi_to, a_ref, omega_m, _ptr(maps, torch.float32, "maps"),
+                             _stream(stream)), "hrt_ray_step")
+
+
+def hrt_ray_drift_free(rays: RayState, chi_from: float, chi_to: float, stream=None):
+    r = rays.c()
+    _check(_lib.hrt_ray_drift_free(C.byref(r), chi_from, chi_to, _stream(stream)), "hrt_ray_drift_free")
+
+
+def hrt_ray_readout(rays: RayState, maps: torch.Tensor, stream=None):
+    r = rays.c()
+    _check(_lib.hrt_ray_readout(C.byref(r), _ptr(maps, torch.float32, "maps"), _stream(stream)), "hrt_ray_readout")
+
+
+def hrt_kappa_power(kappa: torch.Tensor, m: int, dtheta: float, nbins: int, ell_min: float, ell_max: float,
+                    stream=None):
+    ell = torch.zeros(nbins, dtype=torch.float64)
+    p = torch.zeros(nbins, dtype=torch.float64)
+    cnt = torch.zeros(nbins, dtype=torch.int64)
+    _check(_lib.hrt_kappa_power(_ptr(kappa, torch.float32, "kappa"), m, dtheta, nbins, ell_min, ell_max,
+                                ell.data_ptr(), p.data_ptr(), cnt.data_ptr(), _stream(stream)), "hrt_kappa_power")
+    return ell.numpy(), p.numpy(), cnt.numpy()
+
+
+def hrt_ic_zeldovich(noise: torch.Tensor, n_side: int, box: float, omega_m: float, h: float, n_s: float,
+                     sigma8: float, a_init: float, disp: torch.Tensor, mom: torch.Tensor, stream=None):
+    c = hrt_cosmology(omega_m, h, n_s, sigma8)
+    _check(_lib.hrt_ic_zeldovich(_ptr(noise, torch.float32, "noise"), n_side, box, C.byref(c), a_init,
+                                 _ptr(disp, torch.float32, "disp"), _ptr(mom, torch.float32, "mom"), _stream(stream)),
+           "hrt_ic_zeldovich")
+
+
+# ------------------------------------------------------------------------------------------------ context
+def make_config(n_mesh: int, box: float, n_side: int, omega_m=0.3, h=0.7, n_s=0.96, sigma8=0.8, deconv_p=4.0,
+                smooth_cells=1.0, samples_per_cell=1.0, observer=(0.0, 0.0, 0.0), static_mode=False,
+                static_pref=0.0, window=(-1e300, 1e300), n_sources=1, ray_fields=0, ray_deconv_p=4.0,
+                ray_smooth_cells=1.0) -> hrt_config:
+    c = hrt_config()
+    c.n_mesh, c.box, c.n_side = n_mesh, box, n_side
+    c.cosmo = hrt_cosmology(omega_m, h, n_s, sigma8)
+    c.deconv_p, c.smooth_cells, c.samples_per_cell = deconv_p, smooth_cells, samples_per_cell
+    for i in range(3):
+        c.observer[i] = observer[i]
+    c.static_mode, c.static_pref = int(static_mode), static_pref
+    c.window_lo, c.window_hi = window
+    c.n_sources, c.ray_fields = n_sources, ray_fields
+    c.ray_deconv_p, c.ray_smooth_cells = ray_deconv_p, ray_smooth_cells
+    return c
+
+
+def hrt_workspace_bytes(cfg: hrt_config, n_rays: int) -> int:
+    out = C.c_size_t()
+    _check(_lib.hrt_workspace_bytes(C.byref(cfg), n_rays, C.byref(out)), "hrt_workspace_bytes")
+    return out.value
+
+
+class Context:
+    """Owner of an ``hrt_ctx`` (the co-evolution state); methods map one to one onto the C calls."""
+
+    def __init__(self, cfg: hrt_config, stream=None):
+        self.cfg = cfg
+        self._h = C.c_void_p()
+        _check(_lib.hrt_create(C.byref(cfg), _stream(stream), C.byref(self._h)), "hrt_create")
+        self.n_rays = 0
+
+    @property
+    def handle(self):
+        return self._h
+
+    def hrt_init_particles_zeldovich(self, noise: torch.Tensor, a_init: float):
+        _check(_lib.hrt_init_particles_zeldovich(self._h, _ptr(noise, torch.float32, "noise"), a_init),
+               "hrt_init_particles_zeldovich")
+
+    def hrt_init_particles(self, disp: torch.Tensor, mom: torch.Tensor, a: float):
+        _check(_lib.hrt_init_particles(self._h, _ptr(disp, torch.float32, "disp"), _ptr(mom, torch.float32, "mom"), a),
+               "hrt_init_particles")
+
+    def hrt_init_rays(self, theta0: torch.Tensor):
+        _check(_lib.hrt_init_rays(self._h, _ptr(theta0, torch.float64, "theta0"), theta0.shape[0]), "hrt_init_rays")
+        self.n_rays = theta0.shape[0]
+
+    def hrt_step(self, a_next: float, source: int = -1):
+        _check(_lib.hrt_step(self._h, a_next, source), "hrt_step")
+
+    def hrt_sync_particles(self):
+        _check(_lib.hrt_sync_particles(self._h), "hrt_sync_particles")
+
+    def hrt_step_static(self, chi_from: float, chi_to: float, source: int = -1):
+        _check(_lib.hrt_step_static(self._h, chi_from, chi_to, source), "hrt_step_static")
+
+    def hrt_drift_free(self, chi_from: float, chi_to: float):
+        _check(_lib.hrt_drift_free(self._h, chi_from, chi_to), "hrt_drift_free")
+
+    def hrt_read_rays(self):
+        r = self.n_rays
+        dev = "cuda"
+        th = torch.empty(r, 2, dtype=torch.float64, device=dev)
+        eta = torch.empty(r, 2, dtype=torch.float32, device=dev)
+        A = torch.empty(r, 4, dtype=torch.float32, device=dev)
+        B = torch.empty(r, 4, dtype=torch.float32, device=dev)
+        _check(_lib.hrt_read_rays(self._h, th.data_ptr(), eta.data_ptr(), A.data_ptr(), B.data_ptr()), "hrt_read_rays")
+        return th, eta, A, B
+
+    def hrt_read_maps(self, source: int):
+        r = self.n_rays
+        out = torch.empty(4, r, dtype=torch.float32, device="cuda")
+        _check(_lib.hrt_read_maps(self._h, source, out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(),
+                                  out[3].data_ptr()), "hrt_read_maps")
+        return out
+
+    def hrt_read_particles(self):
+        n = self.cfg.n_side ** 3
+        disp = torch.empty(3, n, dtype=torch.float32, device="cuda")
+        mom = torch.empty(3, n, dtype=torch.float32, device="cuda")
+        a, ap = C.c_double(), C.c_double()
+        _check(_lib.hrt_read_particles(self._h, disp.data_ptr(), mom.data_ptr(), C.byref(a), C.byref(ap)),
+               "hrt_read_particles")
+        return disp, mom, a.value, ap.value
+
+    def hrt_read_grad(self):
+        n = self.cfg.n_mesh
+        g = torch.empty(3, n, n, n, dtype=torch.float32, device="cuda")
+        _check(_lib.hrt_read_grad(self._h, g.data_ptr()), "hrt_read_grad")
+        return g
+
+    def hrt_ctx_kappa_power(self, source: int, m: int, dtheta: float, nbins: int, ell_min: float, ell_max: float):
+        ell = torch.zeros(nbins, dtype=torch.float64)
+        p = torch.zeros(nbins, dtype=torch.float64)
+        cnt = torch.zeros(nbins, dtype=torch.int64)
+        _check(_lib.hrt_ctx_kappa_power(self._h, source, m, dtheta, nbins, ell_min, ell_max, ell.data_ptr(),
+                                        p.data_ptr(), cnt.data_ptr()), "hrt_ctx_kappa_power")
+        return ell.numpy(), p.numpy(), cnt.numpy()
+
+    PHASES = ("ray_step", "kick_drift", "cic_scatter", "fft_r2c", "kspace", "fft_c2r", "step", "unused")
+
+    def hrt_ctx_set_profiling(self, on: bool):
+        _check(_lib.hrt_ctx_set_profiling(self._h, int(on)), "hrt_ctx_set_profiling")
+
+    def hrt_ctx_phase_times(self):
+        ms = (C.c_double * 8)()
+        cnt = (C.c_int64 * 8)()
+        _check(_lib.hrt_ctx_phase_times(self._h, ms, cnt), "hrt_ctx_phase_times")
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(self.PHASES[:7])}
+
+    def hrt_ctx_rays(self) -> hrt_rays:
+        r = hrt_rays()
+        _check(_lib.hrt_ctx_rays(self._h, C.byref(r)), "hrt_ctx_rays")
+        return r
+
+    def close(self):
+        if self._h:
+            _lib.hrt_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def raw_status(name: str, *args) -> int:
+    """Calls a C entry point with raw ctypes arguments and returns its status (for error-path tests)."""
+    return getattr(_lib, name)(*args)
