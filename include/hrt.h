@@ -110,6 +110,21 @@ hrt_status hrt_kspace_gradient(const void* rho_hat, int64_t n, double box, doubl
                                int32_t n_out, void* out, const hrt_filter* f2, int32_t n_second,
                                void* second, void* stream);
 
+/* Same computation and arguments as hrt_kspace_gradient, but allocating nothing on the device.  The paper
+ * has no counterpart: this exists for callers that manage all device memory themselves (a host application
+ * with its own memory pool that forbids allocations once running, or a time-stepping loop that must not
+ * allocate mid-step).  The per-axis filter tables live in one fixed array in device global memory
+ * (2 * (2048 + 1025) floats, about 24 KB), held by every GPU that loads the library until the process exits,
+ * so the mesh side n may not exceed 2048 (larger sizes return HRT_ERR_INVALID_ARG).  The first call on each
+ * device looks up that array's device address (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture.  Each call overwrites the whole array with its own tables before its kernel
+ * reads them, so nothing has to start at zero; but every call shares the array, so calls whose work overlaps
+ * on the GPU (different streams, or several host threads) race and may read each other's tables: serialise
+ * them, e.g. on one stream.  No cudaMalloc, cudaFree or allocating library routine is called. */
+hrt_status hrt_kspace_gradient_noalloc(const void* rho_hat, int64_t n, double box, double pref,
+                                       const hrt_filter* f, int32_t n_out, void* out, const hrt_filter* f2,
+                                       int32_t n_second, void* second, void* stream);
+
 /* ------------------------------------------------------------------------------------------------------
  * PM solver object: cuFFT plans and buffers for one mesh size, rho -> grad phi (R2C, k-space, C2R).
  * ---------------------------------------------------------------------------------------------------- */

@@ -66,6 +66,7 @@ _SIGS = {
     "hrt_cic_scatter": ([_P, _I64, _I64, _D, _P, _P], C.c_int),
     "hrt_particle_kick_drift": ([_P, _I64, _D, _I64, _P, _P, _D, _D, _P], C.c_int),
     "hrt_kspace_gradient": ([_P, _I64, _D, _D, _P, _I32, _P, _P, _I32, _P, _P], C.c_int),
+    "hrt_kspace_gradient_noalloc": ([_P, _I64, _D, _D, _P, _I32, _P, _P, _I32, _P, _P], C.c_int),
     "hrt_pm_create": ([_I64, _D, _I32, _P, _P], C.c_int),
     "hrt_pm_destroy": ([_P], C.c_int),
     "hrt_pm_solve": ([_P, _P, _D, _P, _P, _P, _P], C.c_int),
@@ -203,6 +204,17 @@ def hrt_kspace_gradient(rho_hat: torch.Tensor, n: int, box: float, pref: float, 
                                     _ptr(out, torch.complex64, "out"), C.byref(f2) if f2 is not None else None,
                                     n_second, _ptr(second, torch.complex64, "second"), _stream(stream)),
            "hrt_kspace_gradient")
+
+
+def hrt_kspace_gradient_noalloc(rho_hat: torch.Tensor, n: int, box: float, pref: float, f: hrt_filter, n_out: int,
+                                out: torch.Tensor, f2: hrt_filter | None = None, n_second: int = 0,
+                                second: torch.Tensor | None = None, stream=None):
+    """``hrt_kspace_gradient`` for callers that may not allocate device memory (fixed tables, n <= 2048)."""
+    _check(_lib.hrt_kspace_gradient_noalloc(_ptr(rho_hat, torch.complex64, "rho_hat"), n, box, pref, C.byref(f),
+                                            n_out, _ptr(out, torch.complex64, "out"),
+                                            C.byref(f2) if f2 is not None else None, n_second,
+                                            _ptr(second, torch.complex64, "second"), _stream(stream)),
+           "hrt_kspace_gradient_noalloc")
 
 
 class PM:
