@@ -86,6 +86,12 @@ hrt_status hrt_cic_scatter(const float* disp, int64_t n_side, int64_t n, double 
 hrt_status hrt_particle_kick_drift(const float* grad, int64_t n, double box, int64_t n_side, float* disp,
                                    float* mom, double kick, double drift, void* stream);
 
+/* hrt_particle_kick_drift followed by the CIC mass assignment of the drifted particles into rho[n^3]
+ * (overwritten with rho/rho_mean as in hrt_cic_scatter), in one pass over the particles: the density of the
+ * next PM force comes out of the particle update without re-reading the positions. */
+hrt_status hrt_particle_kick_drift_deposit(const float* grad, int64_t n, double box, int64_t n_side, float* disp,
+                                           float* mom, double kick, double drift, float* rho, void* stream);
+
 /* k-space filter of the gradient fields (Sec. 4.2 kick operator taken on the 3D mesh):
  *   prod_i sinc(k_i cell/2)^-deconv_p  *  exp(-k^2 smooth^2 / 2)  *  g(|k|)
  * with g the optional learned correction table: g_table[nk] (device, float32) sampled uniformly on
@@ -277,7 +283,8 @@ hrt_status hrt_ctx_kappa_power(hrt_ctx* ctx, int32_t source, int64_t m, double d
                                int64_t* count_host);
 
 /* Phase timing with CUDA events recorded on the context's stream around each part of a step.  Phases:
- * 0 ray step, 1 particle kick-drift, 2 CIC scatter (with its memset), 3 R2C FFT, 4 k-space kernel,
+ * 0 ray step, 1 particle kick-drift (in hrt_step fused with the CIC deposit of the next density, and with
+ * its memset), 2 stand-alone CIC scatter (initial force only), 3 R2C FFT, 4 k-space kernel,
  * 5 C2R FFTs (all fields), 6 whole hrt_step.  hrt_ctx_phase_times synchronises, returns the summed
  * milliseconds and launch counts since the last call (arrays of 8), and resets them. */
 hrt_status hrt_ctx_set_profiling(hrt_ctx* ctx, int32_t on);

@@ -340,14 +340,21 @@ static double ctx_pref(const hrt_ctx* ctx, double a) {
   return ctx->cfg.static_mode ? ctx->cfg.static_pref : 1.5 * ctx->cfg.cosmo.omega_m / a;
 }
 
+// Gradient fields at ctx->a from the density already deposited in ctx->rho.
+static hrt_status ctx_solve(hrt_ctx* ctx) {
+  const hrt_config& c = ctx->cfg;
+  hrt_filter f = ctx_filter(c, false), fr = ctx_filter(c, true);
+  return pm_solve(ctx->pm, ctx->rho, ctx_pref(ctx, ctx->a), &f, ctx->grad, &fr, ctx->ray_grad, ctx);
+}
+
+// CIC deposit of the current particles, then the gradient fields.
 static hrt_status ctx_force(hrt_ctx* ctx) {
   const hrt_config& c = ctx->cfg;
   {
     PhaseScope ps(ctx, 2);
     HRT_TRY(launch_cic_scatter(ctx->disp, c.n_side, c.n_mesh, c.box, ctx->rho, ctx->stream));
   }
-  hrt_filter f = ctx_filter(c, false), fr = ctx_filter(c, true);
-  return pm_solve(ctx->pm, ctx->rho, ctx_pref(ctx, ctx->a), &f, ctx->grad, &fr, ctx->ray_grad, ctx);
+  return ctx_solve(ctx);
 }
 
 
@@ -438,6 +445,15 @@ hrt_status hrt_particle_kick_drift(const float* grad, int64_t n, double box, int
   if (!grad || !disp || !mom) return fail(HRT_ERR_INVALID_ARG, "NULL buffer");
   if (!std::isfinite(kick) || !std::isfinite(drift)) return fail(HRT_ERR_INVALID_ARG, "non-finite coefficient");
   return launch_kick_drift(grad, n, box, n_side, disp, mom, kick, drift, as_stream(stream));
+}
+
+hrt_status hrt_particle_kick_drift_deposit(const float* grad, int64_t n, double box, int64_t n_side, float* disp,
+                                           float* mom, double kick, double drift, float* rho, void* stream) {
+  HRT_TRY(check_mesh(n, box));
+  HRT_TRY(check_particles(n_side, n));
+  if (!grad || !disp || !mom || !rho) return fail(HRT_ERR_INVALID_ARG, "NULL buffer");
+  if (!std::isfinite(kick) || !std::isfinite(drift)) return fail(HRT_ERR_INVALID_ARG, "non-finite coefficient");
+  return launch_kick_drift(grad, n, box, n_side, disp, mom, kick, drift, as_stream(stream), rho);
 }
 
 hrt_status hrt_kspace_gradient(const void* rho_hat, int64_t n, double box, double pref, const hrt_filter* f,
@@ -745,14 +761,15 @@ hrt_status hrt_step(hrt_ctx* ctx, double a_next, int32_t source) {
   const double a_half = 0.5 * (ctx->a + a_next);
   const double kick = c.kick(ctx->a_mom, a_half), drift = c.drift(ctx->a, a_next);
   {
+    // kick, drift and the CIC deposit of the drifted particles (the density of the next force) in one pass
     PhaseScope ps(ctx, 1);
     s = launch_kick_drift(ctx->grad, ctx->cfg.n_mesh, ctx->cfg.box, ctx->cfg.n_side, ctx->disp, ctx->mom, kick,
-                          drift, ctx->stream);
+                          drift, ctx->stream, ctx->rho);
   }
   if (s != HRT_OK) return ctx_mark(ctx, s);
   ctx->a = a_next;
   ctx->a_mom = a_half;
-  return ctx_mark(ctx, ctx_force(ctx));
+  return ctx_mark(ctx, ctx_solve(ctx));
 }
 
 hrt_status hrt_sync_particles(hrt_ctx* ctx) {

@@ -19,45 +19,128 @@ __device__ __forceinline__ void cic_axis(int q_node, float d_cells, int n, int& 
   float fl = floorf(d_cells);
   f = d_cells - fl;
   int i = q_node + static_cast<int>(fl);
-  i %= n;
-  i0 = i < 0 ? i + n : i;
+  if (static_cast<unsigned>(i) >= static_cast<unsigned>(n)) {  // rare: more than one box away or negative
+    i %= n;
+    if (i < 0) i += n;
+  }
+  i0 = i;
 }
 
 __device__ __forceinline__ int wrap_next(int i, int n) { return i + 1 == n ? 0 : i + 1; }
 
+// Particle launch geometry.  Storage stays in row-major lattice order; only the thread -> particle map changes.
+// Brick mode (n_side a power of two >= 32): each block of 256 threads takes a brick of 2 x 4 x 32 lattice sites
+// (one warp = 32 consecutive sites along z = 128 contiguous bytes per array), and consecutive blocks walk the
+// bricks in Z (Morton) order, so the blocks resident at one time cover a compact region of the mesh whose fields
+// and density lines stay in L2 despite the particles' displacements.  Otherwise blockIdx.x enumerates lattice
+// rows (qi, qj) and blockIdx.y * blockDim.x + threadIdx.x the site along the row.
+struct Lattice {
+  int n_side, ratio, n;
+  float inv_cell;
+  int brick_mode;
+  int lbx, lby, lbz;  // log2 of the brick counts per axis (brick mode)
+};
+
+__device__ __forceinline__ void morton_decode(unsigned code, int lbx, int lby, int lbz, int& bx, int& by, int& bz) {
+  bx = by = bz = 0;
+  int sx = 0, sy = 0, sz = 0;
+  // bits are dealt round-robin z, y, x to the axes that still have bits left
+  while (sx < lbx || sy < lby || sz < lbz) {
+    if (sz < lbz) { bz |= static_cast<int>(code & 1u) << sz; ++sz; code >>= 1; }
+    if (sy < lby) { by |= static_cast<int>(code & 1u) << sy; ++sy; code >>= 1; }
+    if (sx < lbx) { bx |= static_cast<int>(code & 1u) << sx; ++sx; code >>= 1; }
+  }
+}
+
+__device__ __forceinline__ bool particle_of_thread(const Lattice& L, int64_t& p, int& qi, int& qj, int& qk) {
+  if (L.brick_mode) {
+    int bx, by, bz;
+    morton_decode(blockIdx.x, L.lbx, L.lby, L.lbz, bx, by, bz);
+    const int t = threadIdx.x;
+    qi = bx * 2 + (t >> 7);
+    qj = by * 4 + ((t >> 5) & 3);
+    qk = bz * 32 + (t & 31);
+  } else {
+    qk = blockIdx.y * blockDim.x + threadIdx.x;
+    if (qk >= L.n_side) return false;
+    const unsigned row = blockIdx.x;
+    qi = static_cast<int>(row / static_cast<unsigned>(L.n_side));
+    qj = static_cast<int>(row - static_cast<unsigned>(qi) * L.n_side);
+  }
+  p = (static_cast<int64_t>(qi) * L.n_side + qj) * L.n_side + qk;
+  return true;
+}
+
+static inline int ilog2_exact(int64_t v) {
+  int l = 0;
+  while ((int64_t{1} << l) < v) ++l;
+  return (int64_t{1} << l) == v ? l : -1;
+}
+
+static inline bool brick_ok(int64_t n_side) { return n_side >= 32 && ilog2_exact(n_side) >= 0; }
+
+static inline dim3 particle_grid(int64_t n_side, int threads) {
+  if (brick_ok(n_side) && threads == 256) return dim3(static_cast<unsigned>(n_side * n_side * n_side / 256), 1);
+  return dim3(static_cast<unsigned>(n_side * n_side), static_cast<unsigned>((n_side + threads - 1) / threads));
+}
+
+// Adds w0 to cell (col + iz) and w1 to cell (col + jz); z-adjacent pairs starting on an even cell use one
+// 8-byte vector reduction (col is a multiple of the even mesh side, so the address is 8-byte aligned).
+__device__ __forceinline__ void deposit_pair(float* __restrict__ rho, size_t col, int iz, int jz, float w0, float w1) {
+  if (jz == iz + 1 && (iz & 1) == 0) {
+    atomicAdd(reinterpret_cast<float2*>(rho + col + iz), make_float2(w0, w1));
+  } else {
+    atomicAdd(rho + col + iz, w0);
+    atomicAdd(rho + col + jz, w1);
+  }
+}
+
+__device__ __forceinline__ void deposit_cic(float* __restrict__ rho, int n, int ix, int iy, int iz, float fx,
+                                            float fy, float fz, float mass) {
+  const int jx = wrap_next(ix, n), jy = wrap_next(iy, n), jz = wrap_next(iz, n);
+  const float wx0 = (1.f - fx) * mass, wx1 = fx * mass;
+  const float wy0 = 1.f - fy, wy1 = fy, wz0 = 1.f - fz, wz1 = fz;
+  const size_t c00 = static_cast<size_t>(static_cast<unsigned>(ix * n + iy)) * n;
+  const size_t c01 = static_cast<size_t>(static_cast<unsigned>(ix * n + jy)) * n;
+  const size_t c10 = static_cast<size_t>(static_cast<unsigned>(jx * n + iy)) * n;
+  const size_t c11 = static_cast<size_t>(static_cast<unsigned>(jx * n + jy)) * n;
+  deposit_pair(rho, c00, iz, jz, wx0 * wy0 * wz0, wx0 * wy0 * wz1);
+  deposit_pair(rho, c01, iz, jz, wx0 * wy1 * wz0, wx0 * wy1 * wz1);
+  deposit_pair(rho, c10, iz, jz, wx1 * wy0 * wz0, wx1 * wy0 * wz1);
+  deposit_pair(rho, c11, iz, jz, wx1 * wy1 * wz0, wx1 * wy1 * wz1);
+}
+
 // ---------------------------------------------------------------------------------------------------------
-// CIC mass assignment: one thread per particle, eight float32 reductions into the mesh.
+// CIC mass assignment: one thread per particle, four pairs of float32 reductions into the mesh.
 // ---------------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) cic_scatter_kernel(const float* __restrict__ dx,
-                                                          const float* __restrict__ dy,
-                                                          const float* __restrict__ dz, int64_t np,
-                                                          int n_side, int ratio, int n, float inv_cell,
+__global__ void __launch_bounds__(256) cic_scatter_kernel(const float* __restrict__ disp, int64_t np, Lattice L,
                                                           float mass, float* __restrict__ rho) {
-  int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (p >= np) return;
-  int qk = static_cast<int>(p % n_side);
-  int64_t t = p / n_side;
-  int qj = static_cast<int>(t % n_side);
-  int qi = static_cast<int>(t / n_side);
+  int64_t p;
+  int qi, qj, qk;
+  if (!particle_of_thread(L, p, qi, qj, qk)) return;
   int ix, iy, iz;
   float fx, fy, fz;
-  cic_axis(qi * ratio, __ldg(dx + p) * inv_cell, n, ix, fx);
-  cic_axis(qj * ratio, __ldg(dy + p) * inv_cell, n, iy, fy);
-  cic_axis(qk * ratio, __ldg(dz + p) * inv_cell, n, iz, fz);
-  int jx = wrap_next(ix, n), jy = wrap_next(iy, n), jz = wrap_next(iz, n);
-  float wx0 = (1.f - fx) * mass, wx1 = fx * mass;
-  float wy0 = 1.f - fy, wy1 = fy, wz0 = 1.f - fz, wz1 = fz;
-  int64_t nn = n;
-  int64_t r00 = (ix * nn + iy) * nn, r01 = (ix * nn + jy) * nn, r10 = (jx * nn + iy) * nn,
-          r11 = (jx * nn + jy) * nn;
-  atomicAdd(rho + r00 + iz, wx0 * wy0 * wz0);
-  atomicAdd(rho + r00 + jz, wx0 * wy0 * wz1);
-  atomicAdd(rho + r01 + iz, wx0 * wy1 * wz0);
-  atomicAdd(rho + r01 + jz, wx0 * wy1 * wz1);
-  atomicAdd(rho + r10 + iz, wx1 * wy0 * wz0);
-  atomicAdd(rho + r10 + jz, wx1 * wy0 * wz1);
-  atomicAdd(rho + r11 + iz, wx1 * wy1 * wz0);
-  atomicAdd(rho + r11 + jz, wx1 * wy1 * wz1);
+  cic_axis(qi * L.ratio, __ldg(disp + p) * L.inv_cell, L.n, ix, fx);
+  cic_axis(qj * L.ratio, __ldg(disp + np + p) * L.inv_cell, L.n, iy, fy);
+  cic_axis(qk * L.ratio, __ldg(disp + 2 * np + p) * L.inv_cell, L.n, iz, fz);
+  deposit_cic(rho, L.n, ix, iy, iz, fx, fy, fz, mass);
+}
+
+static Lattice make_lattice(int64_t n_side, int64_t n, double box) {
+  Lattice L{static_cast<int>(n_side), static_cast<int>(n / n_side), static_cast<int>(n), static_cast<float>(n / box),
+            0, 0, 0, 0};
+  if (brick_ok(n_side)) {
+    const int l = ilog2_exact(n_side);
+    L.brick_mode = 1;
+    L.lbx = l - 1;  // bricks of 2 sites along x
+    L.lby = l - 2;  // 4 along y
+    L.lbz = l - 5;  // 32 along z
+  }
+  return L;
+}
+
+static float particle_mass(int64_t n_side, int64_t n) {
+  return static_cast<float>(static_cast<double>(n) * n * n / (static_cast<double>(n_side) * n_side * n_side));
 }
 
 hrt_status launch_cic_scatter(const float* disp, int64_t n_side, int64_t n, double box, float* rho,
@@ -66,11 +149,8 @@ hrt_status launch_cic_scatter(const float* disp, int64_t n_side, int64_t n, doub
   size_t mesh_bytes = static_cast<size_t>(n) * n * n * sizeof(float);
   HRT_CUDA(cudaMemsetAsync(rho, 0, mesh_bytes, s));
   if (np == 0) return HRT_OK;
-  float mass = static_cast<float>(static_cast<double>(n) * n * n / static_cast<double>(np));
-  cic_scatter_kernel<<<blocks_for(np, 256), 256, 0, s>>>(disp, disp + np, disp + 2 * np, np,
-                                                         static_cast<int>(n_side),
-                                                         static_cast<int>(n / n_side), static_cast<int>(n),
-                                                         static_cast<float>(n / box), mass, rho);
+  cic_scatter_kernel<<<particle_grid(n_side, 256), 256, 0, s>>>(disp, np, make_lattice(n_side, n, box),
+                                                                particle_mass(n_side, n), rho);
   HRT_LAUNCHED("cic_scatter_kernel");
   return HRT_OK;
 }
@@ -100,41 +180,49 @@ __device__ __forceinline__ float learned_g(const KspaceSet& s, float kmag) {
   return __ldg(s.g + i) * (1.f - w) + __ldg(s.g + i + 1) * w;
 }
 
-__global__ void __launch_bounds__(256) kspace_kernel(const float2* __restrict__ rho_hat, int n, int nzc,
-                                                     float kf, float scale, int64_t elems, KspaceSet a,
-                                                     KspaceSet b) {
-  int iz = blockIdx.y * blockDim.x + threadIdx.x;
-  int64_t row = static_cast<int64_t>(blockIdx.x) * blockDim.y + threadIdx.y;
-  if (iz >= nzc || row >= static_cast<int64_t>(n) * n) return;
-  int ix = static_cast<int>(row / n);
-  int iy = static_cast<int>(row - static_cast<int64_t>(ix) * n);
-  int half = n >> 1;
-  int nx = ix < half ? ix : ix - n;
-  int ny = iy < half ? iy : iy - n;
-  int nz = iz;
-  float kx = kf * nx, ky = kf * ny, kz = kf * nz;
-  float k2 = kx * kx + ky * ky + kz * kz;
-  int64_t e = row * nzc + iz;
-  float2 v = rho_hat[e];
-  float dx = (nx == -half) ? 0.f : kx;
-  float dy = (ny == -half) ? 0.f : ky;
-  float dz = (nz == half) ? 0.f : kz;
-  float green = k2 > 0.f ? scale / k2 : 0.f;
-  float kmag = sqrtf(k2);
+__device__ __forceinline__ void kspace_element(const float2* __restrict__ rho_hat, int n, float kf, float scale,
+                                               int64_t elems, const KspaceSet& a, const KspaceSet& b, int ix,
+                                               int iy, int iz, int64_t e) {
+  const int half = n >> 1;
+  const int nx = ix < half ? ix : ix - n;
+  const int ny = iy < half ? iy : iy - n;
+  const int nz = iz;
+  const float kx = kf * nx, ky = kf * ny, kz = kf * nz;
+  const float k2 = kx * kx + ky * ky + kz * kz;
+  const float2 v = rho_hat[e];
+  const float dx = (nx == -half) ? 0.f : kx;
+  const float dy = (ny == -half) ? 0.f : ky;
+  const float dz = (nz == half) ? 0.f : kz;
+  const float green = k2 > 0.f ? scale / k2 : 0.f;
+  const float kmag = sqrtf(k2);
   {
-    float c = green * __ldg(a.wx + ix) * __ldg(a.wy + iy) * __ldg(a.wz + iz) * learned_g(a, kmag);
-    float2 base = make_float2(-c * v.y, c * v.x);  // i * c * v
+    const float c = green * __ldg(a.wx + ix) * __ldg(a.wy + iy) * __ldg(a.wz + iz) * learned_g(a, kmag);
+    const float2 base = make_float2(-c * v.y, c * v.x);  // i * c * v
     a.out[e] = make_float2(dx * base.x, dx * base.y);
     if (a.n_out > 1) a.out[e + elems] = make_float2(dy * base.x, dy * base.y);
     if (a.n_out > 2) a.out[e + 2 * elems] = make_float2(dz * base.x, dz * base.y);
   }
   if (b.n_out > 0) {
-    float c = green * __ldg(b.wx + ix) * __ldg(b.wy + iy) * __ldg(b.wz + iz) * learned_g(b, kmag);
-    float2 base = make_float2(-c * v.y, c * v.x);
+    const float c = green * __ldg(b.wx + ix) * __ldg(b.wy + iy) * __ldg(b.wz + iz) * learned_g(b, kmag);
+    const float2 base = make_float2(-c * v.y, c * v.x);
     b.out[e] = make_float2(dx * base.x, dx * base.y);
     if (b.n_out > 1) b.out[e + elems] = make_float2(dy * base.x, dy * base.y);
     if (b.n_out > 2) b.out[e + 2 * elems] = make_float2(dz * base.x, dz * base.y);
   }
+}
+
+// Grid: x over rows (ix, iy) in groups of blockDim.y, y over chunks of blockDim.x along kz in [0, n/2).  The
+// Nyquist column kz = n/2 is done by the thread that holds kz = 0, so no thread of the grid is idle.
+__global__ void __launch_bounds__(256) kspace_kernel(const float2* __restrict__ rho_hat, int n, int nzc, float kf,
+                                                     float scale, int64_t elems, KspaceSet a, KspaceSet b) {
+  const int iz = blockIdx.y * blockDim.x + threadIdx.x;
+  const unsigned row = blockIdx.x * blockDim.y + threadIdx.y;
+  if (iz >= nzc - 1 || row >= static_cast<unsigned>(n) * static_cast<unsigned>(n)) return;
+  const int ix = static_cast<int>(row / static_cast<unsigned>(n));
+  const int iy = static_cast<int>(row - static_cast<unsigned>(ix) * n);
+  const int64_t e = static_cast<int64_t>(row) * nzc + iz;
+  kspace_element(rho_hat, n, kf, scale, elems, a, b, ix, iy, iz, e);
+  if (iz == 0) kspace_element(rho_hat, n, kf, scale, elems, a, b, ix, iy, nzc - 1, e + nzc - 1);
 }
 
 // FP64 host tables of the separable filter factor sinc(k_i cell/2)^-p exp(-k_i^2 s^2/2) for the x (= y)
@@ -178,7 +266,7 @@ hrt_status launch_kspace(const void* rho_hat, int64_t n, double box, double pref
   KspaceSet b = make_set(tab_b, fb, n_b, out_b);
   dim3 block(64, 4);
   dim3 grid(static_cast<unsigned>((n * n + block.y - 1) / block.y),
-            static_cast<unsigned>((nzc + block.x - 1) / block.x));
+            static_cast<unsigned>((nzc - 1 + block.x - 1) / block.x));
   kspace_kernel<<<grid, block, 0, s>>>(static_cast<const float2*>(rho_hat), static_cast<int>(n),
                                        static_cast<int>(nzc), static_cast<float>(2.0 * M_PI / box),
                                        static_cast<float>(scale), elems, a, b);
@@ -201,32 +289,34 @@ __device__ __forceinline__ float trilinear(const float* __restrict__ f, int64_t 
   return b0 + fx * (b1 - b0);
 }
 
-__global__ void __launch_bounds__(256) kick_drift_kernel(const float* __restrict__ gx,
-                                                         const float* __restrict__ gy,
-                                                         const float* __restrict__ gz, int n,
-                                                         float inv_cell, int64_t np, int n_side, int ratio,
+// One thread per particle.  With DEPOSIT the drifted particle is deposited at once into rho (zeroed before
+// the launch), which fuses the CIC mass assignment of the next force into the update and saves re-reading the
+// positions.
+template <bool DEPOSIT>
+__global__ void __launch_bounds__(256) kick_drift_kernel(const float* __restrict__ gx, const float* __restrict__ gy,
+                                                         const float* __restrict__ gz, Lattice L, int64_t np,
                                                          float* __restrict__ disp, float* __restrict__ mom,
-                                                         float kick, float drift) {
-  int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (p >= np) return;
-  int qk = static_cast<int>(p % n_side);
-  int64_t t = p / n_side;
-  int qj = static_cast<int>(t % n_side);
-  int qi = static_cast<int>(t / n_side);
+                                                         float kick, float drift, float mass, float* __restrict__ rho) {
+  int64_t p;
+  int qi, qj, qk;
+  if (!particle_of_thread(L, p, qi, qj, qk)) return;
+  const int n = L.n;
   float d0 = disp[p], d1 = disp[p + np], d2 = disp[p + 2 * np];
   float m0 = mom[p], m1 = mom[p + np], m2 = mom[p + 2 * np];
   int ix, iy, iz;
   float fx, fy, fz;
-  cic_axis(qi * ratio, d0 * inv_cell, n, ix, fx);
-  cic_axis(qj * ratio, d1 * inv_cell, n, iy, fy);
-  cic_axis(qk * ratio, d2 * inv_cell, n, iz, fz);
-  int jx = wrap_next(ix, n), jy = wrap_next(iy, n), jz = wrap_next(iz, n);
-  int64_t nn = n;
-  int64_t r00 = (ix * nn + iy) * nn, r01 = (ix * nn + jy) * nn, r10 = (jx * nn + iy) * nn,
-          r11 = (jx * nn + jy) * nn;
-  float a0 = trilinear(gx, r00, r01, r10, r11, iz, jz, fx, fy, fz);
-  float a1 = trilinear(gy, r00, r01, r10, r11, iz, jz, fx, fy, fz);
-  float a2 = trilinear(gz, r00, r01, r10, r11, iz, jz, fx, fy, fz);
+  const int bx = qi * L.ratio, by = qj * L.ratio, bz = qk * L.ratio;
+  cic_axis(bx, d0 * L.inv_cell, n, ix, fx);
+  cic_axis(by, d1 * L.inv_cell, n, iy, fy);
+  cic_axis(bz, d2 * L.inv_cell, n, iz, fz);
+  const int jx = wrap_next(ix, n), jy = wrap_next(iy, n), jz = wrap_next(iz, n);
+  const int64_t r00 = static_cast<int64_t>(static_cast<unsigned>(ix * n + iy)) * n;
+  const int64_t r01 = static_cast<int64_t>(static_cast<unsigned>(ix * n + jy)) * n;
+  const int64_t r10 = static_cast<int64_t>(static_cast<unsigned>(jx * n + iy)) * n;
+  const int64_t r11 = static_cast<int64_t>(static_cast<unsigned>(jx * n + jy)) * n;
+  const float a0 = trilinear(gx, r00, r01, r10, r11, iz, jz, fx, fy, fz);
+  const float a1 = trilinear(gy, r00, r01, r10, r11, iz, jz, fx, fy, fz);
+  const float a2 = trilinear(gz, r00, r01, r10, r11, iz, jz, fx, fy, fz);
   m0 -= a0 * kick;
   m1 -= a1 * kick;
   m2 -= a2 * kick;
@@ -234,22 +324,37 @@ __global__ void __launch_bounds__(256) kick_drift_kernel(const float* __restrict
   mom[p + np] = m1;
   mom[p + 2 * np] = m2;
   if (drift != 0.f) {
-    disp[p] = d0 + m0 * drift;
-    disp[p + np] = d1 + m1 * drift;
-    disp[p + 2 * np] = d2 + m2 * drift;
+    d0 += m0 * drift;
+    d1 += m1 * drift;
+    d2 += m2 * drift;
+    disp[p] = d0;
+    disp[p + np] = d1;
+    disp[p + 2 * np] = d2;
+  }
+  if (DEPOSIT) {
+    cic_axis(bx, d0 * L.inv_cell, n, ix, fx);
+    cic_axis(by, d1 * L.inv_cell, n, iy, fy);
+    cic_axis(bz, d2 * L.inv_cell, n, iz, fz);
+    deposit_cic(rho, n, ix, iy, iz, fx, fy, fz, mass);
   }
 }
 
 hrt_status launch_kick_drift(const float* grad, int64_t n, double box, int64_t n_side, float* disp, float* mom,
-                             double kick, double drift, cudaStream_t s) {
+                             double kick, double drift, cudaStream_t s, float* rho_out) {
   int64_t np = n_side * n_side * n_side;
-  if (np == 0) return HRT_OK;
   int64_t m = n * n * n;
-  kick_drift_kernel<<<blocks_for(np, 256), 256, 0, s>>>(grad, grad + m, grad + 2 * m, static_cast<int>(n),
-                                                        static_cast<float>(n / box), np,
-                                                        static_cast<int>(n_side), static_cast<int>(n / n_side),
-                                                        disp, mom, static_cast<float>(kick),
-                                                        static_cast<float>(drift));
+  if (rho_out) HRT_CUDA(cudaMemsetAsync(rho_out, 0, static_cast<size_t>(m) * sizeof(float), s));
+  if (np == 0) return HRT_OK;
+  const Lattice L = make_lattice(n_side, n, box);
+  const dim3 grid = particle_grid(n_side, 256);
+  if (rho_out) {
+    kick_drift_kernel<true><<<grid, 256, 0, s>>>(grad, grad + m, grad + 2 * m, L, np, disp, mom,
+                                                 static_cast<float>(kick), static_cast<float>(drift),
+                                                 particle_mass(n_side, n), rho_out);
+  } else {
+    kick_drift_kernel<false><<<grid, 256, 0, s>>>(grad, grad + m, grad + 2 * m, L, np, disp, mom,
+                                                  static_cast<float>(kick), static_cast<float>(drift), 0.f, nullptr);
+  }
   HRT_LAUNCHED("kick_drift_kernel");
   return HRT_OK;
 }

@@ -19,8 +19,9 @@ hrt_status launch_kspace(const void* rho_hat, int64_t n, double box, double pref
                          const hrt_filter* fa, int n_a, void* out_a, const float* tab_b, const hrt_filter* fb,
                          int n_b, void* out_b, cudaStream_t s);
 
+// With rho_out != nullptr the drifted particles are also CIC-deposited into rho_out (zeroed first).
 hrt_status launch_kick_drift(const float* grad, int64_t n, double box, int64_t n_side, float* disp, float* mom,
-                             double kick, double drift, cudaStream_t s);
+                             double kick, double drift, cudaStream_t s, float* rho_out = nullptr);
 
 hrt_status launch_ic_kspace(const void* w_hat, int64_t n, double box, const float* table, void* out,
                             cudaStream_t s);

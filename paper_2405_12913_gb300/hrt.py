@@ -65,6 +65,7 @@ _SIGS = {
     "hrt_cosmo_power_amplitude": ([_D, _D, _D, _D, _P], C.c_int),
     "hrt_cic_scatter": ([_P, _I64, _I64, _D, _P, _P], C.c_int),
     "hrt_particle_kick_drift": ([_P, _I64, _D, _I64, _P, _P, _D, _D, _P], C.c_int),
+    "hrt_particle_kick_drift_deposit": ([_P, _I64, _D, _I64, _P, _P, _D, _D, _P, _P], C.c_int),
     "hrt_kspace_gradient": ([_P, _I64, _D, _D, _P, _I32, _P, _P, _I32, _P, _P], C.c_int),
     "hrt_kspace_gradient_noalloc": ([_P, _I64, _D, _D, _P, _I32, _P, _P, _I32, _P, _P], C.c_int),
     "hrt_pm_create": ([_I64, _D, _I32, _P, _P], C.c_int),
@@ -195,6 +196,14 @@ def hrt_particle_kick_drift(grad: torch.Tensor, n: int, box: float, n_side: int,
     _check(_lib.hrt_particle_kick_drift(_ptr(grad, torch.float32, "grad"), n, box, n_side,
                                         _ptr(disp, torch.float32, "disp"), _ptr(mom, torch.float32, "mom"), kick,
                                         drift, _stream(stream)), "hrt_particle_kick_drift")
+
+
+def hrt_particle_kick_drift_deposit(grad: torch.Tensor, n: int, box: float, n_side: int, disp: torch.Tensor,
+                                    mom: torch.Tensor, kick: float, drift: float, rho: torch.Tensor, stream=None):
+    _check(_lib.hrt_particle_kick_drift_deposit(_ptr(grad, torch.float32, "grad"), n, box, n_side,
+                                                _ptr(disp, torch.float32, "disp"), _ptr(mom, torch.float32, "mom"),
+                                                kick, drift, _ptr(rho, torch.float32, "rho"), _stream(stream)),
+           "hrt_particle_kick_drift_deposit")
 
 
 def hrt_kspace_gradient(rho_hat: torch.Tensor, n: int, box: float, pref: float, f: hrt_filter, n_out: int,

@@ -32,7 +32,8 @@ def _lattice_disp(seed, n_side, scale):
     return synthetic.small_displacements(seed, n_side, scale)  # (3, n^3)
 
 
-@pytest.mark.parametrize("n_side,n_mesh,box,scale", [(20, 60, 120.0, 3.0), (16, 64, 64.0, 0.7), (1, 8, 8.0, 0.0)])
+@pytest.mark.parametrize("n_side,n_mesh,box,scale", [(20, 60, 120.0, 3.0), (16, 64, 64.0, 0.7), (1, 8, 8.0, 0.0),
+                                                     (32, 64, 96.0, 4.0), (64, 128, 128.0, 2.0)])
 def test_cic_scatter_matches_oracle(hrt, n_side, n_mesh, box, scale):
     disp = _lattice_disp(1, n_side, scale)
     if n_side == 1:
@@ -116,9 +117,8 @@ def test_pm_solve_matches_oracle(hrt, n):
     pm.close()
 
 
-@pytest.mark.parametrize("drift", [0.37, 0.0])
-def test_particle_kick_drift_matches_oracle(hrt, drift):
-    n_side, n, box = 20, 60, 120.0
+@pytest.mark.parametrize("drift,n_side,n,box", [(0.37, 20, 60, 120.0), (0.0, 20, 60, 120.0), (0.37, 64, 128, 160.0)])
+def test_particle_kick_drift_matches_oracle(hrt, drift, n_side, n, box):
     disp = _lattice_disp(6, n_side, 2.5)
     mom = _lattice_disp(7, n_side, 1.0)
     grads = [synthetic.gaussian_field(8 + j, (n, n, n)) for j in range(3)]
@@ -130,6 +130,23 @@ def test_particle_kick_drift_matches_oracle(hrt, drift):
                                              [torch.tensor(g) for g in grads], box, 0.21, drift)
     assert np.abs(m_dev.cpu().double().numpy() - m_want.numpy().T).max() <= 2e-6
     assert np.abs(d_dev.cpu().double().numpy() - d_want.numpy().T).max() <= 2e-6
+
+
+@pytest.mark.parametrize("n_side,n,box", [(20, 60, 120.0), (32, 64, 80.0)])
+def test_fused_kick_drift_deposit_matches_oracle(hrt, n_side, n, box):
+    disp = _lattice_disp(16, n_side, 2.5)
+    mom = _lattice_disp(17, n_side, 1.0)
+    grads = [synthetic.gaussian_field(18 + j, (n, n, n)) for j in range(3)]
+    d_dev, m_dev = _cuda(disp), _cuda(mom)
+    rho = torch.full((n ** 3,), 7.0, device="cuda")  # overwritten
+    hrt.hrt_particle_kick_drift_deposit(_cuda(np.stack(grads)), n, box, n_side, d_dev, m_dev, -0.13, 0.52, rho)
+    q = opm.lattice(n_side, box)
+    d_want, m_want = opm.particle_kick_drift(torch.tensor(disp.T), torch.tensor(mom.T), q,
+                                             [torch.tensor(g) for g in grads], box, -0.13, 0.52)
+    assert np.abs(d_dev.cpu().double().numpy() - d_want.numpy().T).max() <= 2e-6
+    assert np.abs(m_dev.cpu().double().numpy() - m_want.numpy().T).max() <= 2e-6
+    want = opm.cic_deposit(q + d_want, box, n).reshape(-1).numpy()
+    assert np.abs(rho.cpu().double().numpy() - want).max() <= 2e-5 * np.abs(want).max()
 
 
 def _smooth_grads(n, box, seed):
