@@ -141,6 +141,13 @@ typedef struct hrt_pm hrt_pm;
 hrt_status hrt_pm_create(int64_t n, double box, int32_t n_ray_fields, void* stream, hrt_pm** out);
 hrt_status hrt_pm_destroy(hrt_pm* pm); /* NULL is fine; synchronises the stream */
 
+/* on = 1 builds (once) batched complex-to-real plans with the k-space step linked into cuFFT's load stage (an
+ * LTO load callback, JIT-linked at plan creation; mesh side a power of two up to 1024), so the gradient
+ * spectra are never written to memory, and uses them in hrt_pm_solve; on = 0 returns to the separate k-space
+ * kernel (same results).  Off by default: on a GB300 the callback plans are slower than plain plans plus the
+ * k-space kernel.  Returns HRT_ERR_CUDA if cuFFT refuses the callback. */
+hrt_status hrt_pm_set_fused(hrt_pm* pm, int32_t on);
+
 /* grad[3][n^3] <- gradient of phi from rho[n^3] (rho is overwritten as FFT scratch);
  * ray_grad[2][n^3] (only if the object has ray fields; else pass NULL) with the ray filter. */
 hrt_status hrt_pm_solve(hrt_pm* pm, float* rho, double pref, const hrt_filter* f, float* grad,
@@ -170,6 +177,8 @@ typedef struct hrt_ray_geom {
   double samples_per_cell;   /* s: each half shell uses max(1, ceil(s |half shell| / cell)) nodes    */
   double window_lo;          /* only nodes with window_lo <= chi < window_hi kick (static lens box)   */
   double window_hi;
+  int64_t image_width;       /* > 0: ray r is pixel (r % W, r / W) of an image W pixels wide; the kernel
+                                then walks the rays in 16 x 8 pixel tiles (thread order only, same results) */
 } hrt_ray_geom;
 
 /* One KDK step of every ray through the shell [chi_from, chi_to] with the A/B recursion, Alg. 1 order

@@ -37,14 +37,43 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
+def _callback_blob() -> str:
+    """LTO fatbin of the k-space load callback (linked into cuFFT kernels at plan time), embedded as bytes."""
+    fatbin = os.path.join(OUT, "kspace_callback.fatbin")
+    # compute_100 LTO IR with C++ linkage: the form cuFFT's JIT link accepts (it resolves the plain C++ name
+    # and links the IR into its own kernels for the device's sm_103)
+    cmd = [nvcc(), "-gencode", "arch=compute_100,code=lto_100", "-dc", "-fatbin", "-O3", "-std=c++17",
+           os.path.join(CSRC, "kspace_callback.cu"), "-o", fatbin]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for the callback:\n{r.stdout}\n{r.stderr}")
+    data = open(fatbin, "rb").read()
+    src = os.path.join(OUT, "kspace_callback_blob.c")
+    with open(src, "w") as f:
+        f.write("#include <stddef.h>\n")
+        f.write("const unsigned char hrt_kspace_callback_fatbin[] __attribute__((aligned(16))) = {\n")
+        for i in range(0, len(data), 24):
+            f.write(",".join(str(x) for x in data[i:i + 24]) + ",\n")
+        f.write("};\n")
+        f.write(f"const size_t hrt_kspace_callback_fatbin_size = {len(data)};\n")
+    obj = src + ".o"
+    r = subprocess.run(["gcc", "-c", "-fPIC", "-O1", src, "-o", obj], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"gcc failed for the callback blob:\n{r.stderr}")
+    return obj
+
+
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
-    srcs = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
+    srcs = [os.path.join(CSRC, s) for s in SOURCES + ["kspace_callback.cu"]]
+    srcs += [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
     srcs.append(os.path.join(os.path.dirname(HERE), "include", "hrt.h"))
     if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(s) for s in srcs):
         return LIB
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
+    with cf.ThreadPoolExecutor(len(SOURCES) + 1) as ex:
+        blob = ex.submit(_callback_blob)
         objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
+        objs.append(blob.result())
     cmd = [nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lcufft", "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "common.h"
+#include "kspace_callback.h"
 #include "mesh_kernels.h"
 
 namespace hrt {
@@ -223,6 +224,14 @@ __global__ void __launch_bounds__(256) kspace_kernel(const float2* __restrict__ 
   const int64_t e = static_cast<int64_t>(row) * nzc + iz;
   kspace_element(rho_hat, n, kf, scale, elems, a, b, ix, iy, iz, e);
   if (iz == 0) kspace_element(rho_hat, n, kf, scale, elems, a, b, ix, iy, nzc - 1, e + nzc - 1);
+}
+
+__global__ void set_callback_info_kernel(KspaceCallbackInfo* dst, KspaceCallbackInfo v) { *dst = v; }
+
+hrt_status launch_set_callback_info(KspaceCallbackInfo* dst, const KspaceCallbackInfo& v, cudaStream_t s) {
+  set_callback_info_kernel<<<1, 1, 0, s>>>(dst, v);
+  HRT_LAUNCHED("set_callback_info_kernel");
+  return HRT_OK;
 }
 
 // FP64 host tables of the separable filter factor sinc(k_i cell/2)^-p exp(-k_i^2 s^2/2) for the x (= y)

@@ -20,6 +20,10 @@ hrt_status launch_kspace(const void* rho_hat, int64_t n, double box, double pref
                          int n_b, void* out_b, cudaStream_t s);
 
 // With rho_out != nullptr the drifted particles are also CIC-deposited into rho_out (zeroed first).
+struct KspaceCallbackInfo;
+// Writes the caller info of the k-space load callback in stream order (kernel argument, no host wait).
+hrt_status launch_set_callback_info(KspaceCallbackInfo* dst, const KspaceCallbackInfo& v, cudaStream_t s);
+
 hrt_status launch_kick_drift(const float* grad, int64_t n, double box, int64_t n_side, float* disp, float* mom,
                              double kick, double drift, cudaStream_t s, float* rho_out = nullptr);
 
@@ -34,6 +38,7 @@ constexpr int kMaxRayNodes = 1024;
 struct RayStepParams {
   int n1, n2;            // nodes of the first and second half shell (after the force window)
   int n;                 // mesh cells per side
+  int tile_w;            // > 0: rays form an image tile_w pixels wide, walked in 16 x 8 tiles
   float drift;           // (chi_to - chi_from) / (c chi_mid^2), float32 copy for A
   double drift_d;        // the same in FP64 for theta
   double ref_r[2];       // reference radius of each half shell for the FP64 base position

@@ -107,7 +107,16 @@ __global__ void __launch_bounds__(128) ray_step_kernel(double2* __restrict__ the
                                                        int64_t nr, const float* __restrict__ gx,
                                                        const float* __restrict__ gy, const __grid_constant__ RayStepParams p,
                                                        float* __restrict__ maps) {
-  int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  int64_t r;
+  if (p.tile_w > 0) {
+    // 16 x 8 pixel tiles in row-major tile order; a warp covers 16 x 2 neighbouring pixels
+    const unsigned tiles_x = static_cast<unsigned>(p.tile_w) >> 4;
+    const unsigned tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
+    const int64_t x = tx * 16 + (threadIdx.x & 15), y = ty * 8 + (threadIdx.x >> 4);
+    r = y * p.tile_w + x;
+  } else {
+    r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  }
   if (r >= nr) return;
   double2 th = theta[r];
   float2 et = eta[r];

@@ -37,7 +37,8 @@ class hrt_rays(C.Structure):
 
 class hrt_ray_geom(C.Structure):
     _fields_ = [("n", C.c_int64), ("box", C.c_double), ("observer", C.c_double * 3),
-                ("samples_per_cell", C.c_double), ("window_lo", C.c_double), ("window_hi", C.c_double)]
+                ("samples_per_cell", C.c_double), ("window_lo", C.c_double), ("window_hi", C.c_double),
+                ("image_width", C.c_int64)]
 
 
 class hrt_cosmology(C.Structure):
@@ -71,6 +72,7 @@ _SIGS = {
     "hrt_pm_create": ([_I64, _D, _I32, _P, _P], C.c_int),
     "hrt_pm_destroy": ([_P], C.c_int),
     "hrt_pm_solve": ([_P, _P, _D, _P, _P, _P, _P], C.c_int),
+    "hrt_pm_set_fused": ([_P, _I32], C.c_int),
     "hrt_rays_init": ([_P, _P, _P], C.c_int),
     "hrt_ray_step": ([_P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
     "hrt_ray_drift_free": ([_P, _D, _D, _P], C.c_int),
@@ -240,6 +242,9 @@ class PM:
                                  _ptr(grad, torch.float32, "grad"), C.byref(f_ray) if f_ray is not None else None,
                                  _ptr(ray_grad, torch.float32, "ray_grad")), "hrt_pm_solve")
 
+    def set_fused(self, on: bool):
+        _check(_lib.hrt_pm_set_fused(self._h, int(on)), "hrt_pm_set_fused")
+
     def close(self):
         if self._h:
             _lib.hrt_pm_destroy(self._h)
@@ -270,8 +275,10 @@ class RayState:
         return r
 
 
-def make_geom(n: int, box: float, observer, samples_per_cell: float = 1.0, window=(-1e300, 1e300)) -> hrt_ray_geom:
+def make_geom(n: int, box: float, observer, samples_per_cell: float = 1.0, window=(-1e300, 1e300),
+              image_width: int = 0) -> hrt_ray_geom:
     g = hrt_ray_geom()
+    g.image_width = image_width
     g.n, g.box = n, box
     for i in range(3):
         g.observer[i] = observer[i]

@@ -117,6 +117,40 @@ def test_pm_solve_matches_oracle(hrt, n):
     pm.close()
 
 
+@pytest.mark.parametrize("fused", [True, False])
+def test_pm_solve_fused_callback_and_ray_fields(hrt, fused):
+    # the batched C2R with the k-space load callback (fused) and the separate k-space kernel both match the
+    # oracle, for the particle fields and for separately filtered ray fields with a learned table
+    n, box, pref = 64, 128.0, 1.1
+    rho = synthetic.gaussian_field(15, (n, n, n), 0.5) + 1.0
+    pm = hrt.PM(n, box, n_ray_fields=2)
+    pm.set_fused(fused)
+    kmax = 2 * math.pi / box * n
+    table = np.linspace(1.2, 0.7, 65).astype(np.float32)
+    gt = _cuda(table)
+    grad = torch.empty(3, n, n, n, device="cuda")
+    rgrad = torch.empty(2, n, n, n, device="cuda")
+    pm.solve(_cuda(rho), pref, hrt.make_filter(0.0, 0.0), grad, hrt.make_filter(4.0, box / n, gt, kmax), rgrad)
+
+    def g_of_k(k):
+        t = k / kmax * 64
+        i = torch.clamp(t.floor().long(), 0, 63)
+        w = t - i
+        tab = torch.tensor(table, dtype=torch.float64)
+        v = tab[i] * (1 - w) + tab[torch.clamp(i + 1, max=64)] * w
+        return torch.where(t >= 64, torch.ones_like(v), v)
+
+    want = opm.poisson_gradient(torch.tensor(rho), box, pref, 0.0, 0.0)
+    want_r = opm.poisson_gradient(torch.tensor(rho), box, pref, 4.0, box / n, g_of_k)
+    for j in range(3):
+        w = want[j].numpy()
+        assert np.abs(grad[j].cpu().double().numpy() - w).max() <= 2e-5 * np.abs(w).max()
+    for j in range(2):
+        w = want_r[j].numpy()
+        assert np.abs(rgrad[j].cpu().double().numpy() - w).max() <= 2e-5 * np.abs(w).max()
+    pm.close()
+
+
 @pytest.mark.parametrize("drift,n_side,n,box", [(0.37, 20, 60, 120.0), (0.0, 20, 60, 120.0), (0.37, 64, 128, 160.0)])
 def test_particle_kick_drift_matches_oracle(hrt, drift, n_side, n, box):
     disp = _lattice_disp(6, n_side, 2.5)
@@ -166,10 +200,11 @@ def _smooth_grads(n, box, seed):
     return gx, gy
 
 
-@pytest.mark.parametrize("a_ref,chis,s", [(0.0, [(150.0, 210.0), (210.0, 300.0)], 1.0),
-                                          (0.8, [(600.0, 660.0)], 2.0),
-                                          (0.0, [(300.0, 210.0)], 1.0)])
-def test_ray_step_matches_oracle(hrt, a_ref, chis, s):
+@pytest.mark.parametrize("a_ref,chis,s,npix", [(0.0, [(150.0, 210.0), (210.0, 300.0)], 1.0, 37),
+                                               (0.8, [(600.0, 660.0)], 2.0, 37),
+                                               (0.0, [(300.0, 210.0)], 1.0, 37),
+                                               (0.7, [(900.0, 990.0), (990.0, 1100.0)], 1.0, 48)])
+def test_ray_step_matches_oracle(hrt, a_ref, chis, s, npix):
     from oracle import cosmology as oc
     from oracle import sim
     n, box = 48, 96.0
@@ -177,10 +212,11 @@ def test_ray_step_matches_oracle(hrt, a_ref, chis, s):
     # where float32 and float64 positions may pick different (equally valid) one-sided cells
     obs = (30.3, 61.7, 5.0)
     gx, gy = _smooth_grads(n, box, 9)
-    theta0 = synthetic.pixel_grid(37, 0.3)  # 1369 rays: a ragged last block of 128
+    # 37^2 = 1369 rays: a ragged last block of 128; 48^2 rays: the 16 x 8 tiled walk of an image
+    theta0 = synthetic.pixel_grid(npix, 0.3)
     rays = hrt.RayState(theta0.shape[0])
     hrt.hrt_rays_init(rays, _cuda(theta0, torch.float64))
-    geom = hrt.make_geom(n, box, obs, s)
+    geom = hrt.make_geom(n, box, obs, s, image_width=npix if npix % 16 == 0 else 0)
     maps = torch.empty(4, theta0.shape[0], device="cuda")
     st = orays.init_state(torch.tensor(theta0))
     wfn = (lambda chi: 1.0) if a_ref == 0.0 else sim.growth_weight(a_ref, 0.3)
