@@ -227,6 +227,68 @@ hrt_status hrt_ic_zeldovich(const float* noise, int64_t n_side, double box, cons
                             double a_init, float* disp, float* mom, void* stream);
 
 /* ------------------------------------------------------------------------------------------------------
+ * Adjoints (reverse mode).  Each call is the vector-Jacobian product of the forward call of the same name:
+ * given cotangents of the outputs it returns (or accumulates, where stated) the cotangents of the inputs and
+ * of the host coefficients, so that a caller can run the forward path backwards with checkpointing.  Paper:
+ * the adjoint method is named as future work (Sec. 6); these are the transposes of the operations above.
+ * Coefficient cotangents are FP64 device accumulators that the calls add to.
+ * ---------------------------------------------------------------------------------------------------- */
+
+/* disp_bar[3][n_side^3] += d(sum rho_bar * rho)/d disp for rho = hrt_cic_scatter(disp). */
+hrt_status hrt_cic_scatter_adjoint(const float* rho_bar, const float* disp, int64_t n_side, int64_t n, double box,
+                                   float* disp_bar, void* stream);
+
+/* Transpose of hrt_particle_kick_drift (and of hrt_particle_kick_drift_deposit when rho_bar != NULL) taken at
+ * the PRE-step state disp, mom: on entry disp_bar, mom_bar hold the cotangents of the updated state, on return
+ * those of (disp, mom); grad_bar[3][n^3] accumulates the cotangent of the gradient fields; coef_bar[0] and
+ * coef_bar[1] accumulate dL/dkick and dL/ddrift. */
+hrt_status hrt_particle_kick_drift_adjoint(const float* grad, int64_t n, double box, int64_t n_side, const float* disp,
+                                           const float* mom, double kick, double drift, const float* rho_bar,
+                                           float* disp_bar, float* mom_bar, float* grad_bar, double* coef_bar,
+                                           void* stream);
+
+/* Transpose of hrt_pm_solve: rho_bar[n^3] <- d(<grad_bar, grad> + <ray_grad_bar, ray_grad>)/d rho (the same
+ * FFT pipeline with the conjugate transfer function).  grad_bar (and ray_grad_bar) are used as FFT input and
+ * destroyed.  ray_grad_bar may be NULL. */
+hrt_status hrt_pm_solve_adjoint(hrt_pm* pm, float* grad_bar, double pref, const hrt_filter* f, float* ray_grad_bar,
+                                const hrt_filter* f_ray, float* rho_bar);
+
+/* Transpose of hrt_ray_step at the PRE-step ray state `rays` (not modified): on entry bar holds the
+ * cotangents of the state after the step (its maps readout must already be folded into bar->A), on return
+ * those of the state before it; gx_bar, gy_bar accumulate the field cotangents; node_bar[3][1024]
+ * accumulates, per line-of-sight node j of the step's node table, dL/dc_j, dL/d(c_j r_j / cell) and dL/dchi_j;
+ * drift_bar[0] accumulates dL/dd for the drift coefficient d. */
+hrt_status hrt_ray_step_adjoint(const hrt_rays* rays, const float* grad_x, const float* grad_y, const hrt_ray_geom* geom,
+                                double chi_from, double chi_to, double a_ref, double omega_m, const hrt_rays* bar,
+                                float* gx_bar, float* gy_bar, double* node_bar, double* drift_bar, void* stream);
+
+/* FP64 node table of a ray step as the kernels use it (host): counts of the two half shells and, per kept
+ * node, c_j, c_j r_j / cell and chi_j, plus the drift coefficient.  Arrays hold at least 1024 entries. */
+hrt_status hrt_ray_step_coefficients(const hrt_ray_geom* geom, double chi_from, double chi_to, double a_ref,
+                                     double omega_m, int32_t* n1_host, int32_t* n2_host, double* cw_host,
+                                     double* cwr_host, double* chi_host, double* drift_host);
+
+/* kappa_bar[m^2] <- dL/dkappa for L a function of the binned power (hrt_kappa_power) with dL/dP_b given per bin
+ * (host array of nbins).  Synchronises the stream. */
+hrt_status hrt_kappa_power_adjoint(const float* kappa, int64_t m, double dtheta, int32_t nbins, double ell_min,
+                                   double ell_max, const double* dl_dp_host, float* kappa_bar, void* stream);
+
+/* FP64 host table of the Zel'dovich IC transfer T(|n|^2) = D1 sqrt(P(k)/V_cell) / k^2 / n_side^3 (size
+ * 3 (n_side/2)^2 + 1) and the momentum ratio a^2 E f. */
+hrt_status hrt_ic_table(int64_t n_side, double box, const hrt_cosmology* cosmo, double a_init, double* table_host,
+                        double* ratio_host);
+
+/* Transpose of hrt_ic_zeldovich: noise_bar[n_side^3] <- dL/dnoise given disp_bar, mom_bar (cotangents of its
+ * outputs) and disp (its displacement output); table_bar_host (size as hrt_ic_table, may be NULL) receives
+ * dL/dT(|n|^2) and ratio_bar_host dL/d(a^2 E f).  Synchronises the stream. */
+hrt_status hrt_ic_zeldovich_adjoint(const float* noise, int64_t n_side, double box, const hrt_cosmology* cosmo,
+                                    double a_init, const float* disp_bar, const float* mom_bar, const float* disp,
+                                    float* noise_bar, double* table_bar_host, double* ratio_bar_host, void* stream);
+
+/* out_host = sum_i a[i] b[i] in FP64 over m float32 elements (synchronises). */
+hrt_status hrt_dot(const float* a, const float* b, int64_t m, double* out_host, void* stream);
+
+/* ------------------------------------------------------------------------------------------------------
  * Simulation context: particles + mesh + rays co-evolved as in Alg. 1 (one PM force per step).
  * ---------------------------------------------------------------------------------------------------- */
 typedef struct hrt_config {

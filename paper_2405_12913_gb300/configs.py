@@ -128,4 +128,14 @@ COSMO_1024_SCALED = CosmoWorkload(name="cosmo_1024_recipe_at_128p_256m_512r", n_
 COSMO_TINY = CosmoWorkload(name="cosmo_20p_60m_60r", n_side=20, n_mesh=60, box=120.0, a_init=0.05, n_forward=8,
                            a_min=0.6, n_reverse=8, n_pix=60, fov_deg=6.0, source_steps=(4, 8), nbins=8)
 
-WORKLOADS = {w.name: w for w in (POINT_MASS, COSMO_256, COSMO_1024, COSMO_1024_SCALED, COSMO_TINY)}
+# Differentiation: the 256^3 recipe's ingredients at a size where the FP64 oracle's autograd runs in seconds
+# (8^3 particles, 16^3 mesh, 16^2 rays, 3 forward and 3 reverse steps, one source plane).
+COSMO_GRAD = CosmoWorkload(name="grad_8p_16m_16r", n_side=8, n_mesh=16, box=32.0, a_init=0.1, n_forward=3, a_min=0.7,
+                           n_reverse=3, n_pix=16, fov_deg=6.0, source_steps=(3,), nbins=4)
+
+# Differentiation at the 256^3-recipe sizes (128^3 particles, 256^3 mesh, 512^2 rays; checkpoint every 4 steps).
+COSMO_GRAD_256 = CosmoWorkload(name="grad_128p_256m_512r", n_side=128, n_mesh=256, box=256.0, a_init=0.02,
+                               n_forward=32, a_min=0.5, n_reverse=16, n_pix=512, fov_deg=3.5, source_steps=(16,))
+
+WORKLOADS = {w.name: w for w in (POINT_MASS, COSMO_256, COSMO_1024, COSMO_1024_SCALED, COSMO_TINY,
+                                         COSMO_GRAD, COSMO_GRAD_256)}

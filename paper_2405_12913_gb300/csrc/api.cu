@@ -11,6 +11,7 @@
 #include <new>
 #include <vector>
 
+#include "adjoint.h"
 #include "common.h"
 #include "cosmo.h"
 #include "kspace_callback.h"
@@ -103,7 +104,8 @@ static hrt_status filter_upload(int64_t n, double box, const hrt_filter& f, floa
 // Ray step parameters: FP64 node table of the half shells (Eq. "kick" with the growth correction).
 // ---------------------------------------------------------------------------------------------------------
 static hrt_status build_ray_params(const hrt_ray_geom& g, double chi_from, double chi_to, double a_ref,
-                                   double omega_m, RayStepParams& p) {
+                                   double omega_m, RayStepParams& p, double* cw64 = nullptr,
+                                   double* cwr64 = nullptr, double* chi64 = nullptr) {
   if (!(g.samples_per_cell > 0.0)) return fail(HRT_ERR_INVALID_ARG, "samples_per_cell must be > 0");
   HRT_TRY(check_mesh(g.n, g.box));
   const double cell = g.box / g.n;
@@ -140,6 +142,9 @@ static hrt_status build_ray_params(const hrt_ray_geom& g, double chi_from, doubl
       p.dr[total] = static_cast<float>((r - p.ref_r[h]) / cell);
       p.cw[total] = static_cast<float>(c);
       p.cwr[total] = static_cast<float>(c * r / cell);
+      if (cw64) cw64[total] = c;
+      if (cwr64) cwr64[total] = c * r / cell;
+      if (chi64) chi64[total] = chi;
       double uz = (g.observer[2] + chi) / cell;
       uz -= g.n * std::floor(uz / g.n);
       double fl = std::floor(uz);
@@ -699,6 +704,23 @@ hrt_status hrt_kappa_power(const float* kappa, int64_t m, double dtheta, int32_t
   return HRT_OK;
 }
 
+static std::vector<double> ic_table64(int64_t n, double box, const hrt_cosmology* cosmo, double a_init,
+                                      double* ratio) {
+  Cosmo c(cosmo->omega_m);
+  const double amp = power_amplitude(cosmo->omega_m, cosmo->h, cosmo->n_s, cosmo->sigma8);
+  const double d1 = c.D1(a_init);
+  if (ratio) *ratio = a_init * a_init * c.E(a_init) * c.f(a_init);
+  const double kf = 2.0 * M_PI / box, v_cell = std::pow(box / n, 3);
+  const int64_t max_n2 = 3 * (n / 2) * (n / 2);
+  std::vector<double> table(max_n2 + 1, 0.0);
+  for (int64_t i = 1; i <= max_n2; ++i) {
+    double k = kf * std::sqrt(static_cast<double>(i));
+    double pk = amp * std::pow(k, cosmo->n_s) * std::pow(bbks_transfer(k / (cosmo->omega_m * cosmo->h)), 2);
+    table[i] = d1 * std::sqrt(pk / v_cell) / (k * k) / (static_cast<double>(n) * n * n);
+  }
+  return table;
+}
+
 hrt_status hrt_ic_zeldovich(const float* noise, int64_t n_side, double box, const hrt_cosmology* cosmo,
                             double a_init, float* disp, float* mom, void* stream) {
   HRT_TRY(check_mesh(n_side, box));
@@ -707,19 +729,9 @@ hrt_status hrt_ic_zeldovich(const float* noise, int64_t n_side, double box, cons
     return fail(HRT_ERR_INVALID_ARG, "bad cosmology");
   cudaStream_t s = as_stream(stream);
   const int64_t n = n_side;
-  Cosmo c(cosmo->omega_m);
-  const double amp = power_amplitude(cosmo->omega_m, cosmo->h, cosmo->n_s, cosmo->sigma8);
-  const double d1 = c.D1(a_init);
-  const double ratio = a_init * a_init * c.E(a_init) * c.f(a_init);
-  const double kf = 2.0 * M_PI / box, v_cell = std::pow(box / n, 3);
-  const int64_t max_n2 = 3 * (n / 2) * (n / 2);
-  std::vector<float> table(max_n2 + 1);
-  table[0] = 0.f;
-  for (int64_t i = 1; i <= max_n2; ++i) {
-    double k = kf * std::sqrt(static_cast<double>(i));
-    double pk = amp * std::pow(k, cosmo->n_s) * std::pow(bbks_transfer(k / (cosmo->omega_m * cosmo->h)), 2);
-    table[i] = static_cast<float>(d1 * std::sqrt(pk / v_cell) / (k * k) / (static_cast<double>(n) * n * n));
-  }
+  double ratio = 0.0;
+  const std::vector<double> t64 = ic_table64(n, box, cosmo, a_init, &ratio);
+  std::vector<float> table(t64.begin(), t64.end());
   hrt_pm tmp;
   hrt_status st = pm_make(n, box, 0, s, &tmp);
   float* tab = nullptr;
@@ -735,6 +747,200 @@ hrt_status hrt_ic_zeldovich(const float* noise, int64_t n_side, double box, cons
   if (st == HRT_OK) st = launch_scale_copy(disp, mom, ratio, 3 * np, s);
   device_free(tab, s);
   pm_release(&tmp);
+  return st;
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// Adjoints
+// ---------------------------------------------------------------------------------------------------------
+hrt_status hrt_cic_scatter_adjoint(const float* rho_bar, const float* disp, int64_t n_side, int64_t n, double box,
+                                   float* disp_bar, void* stream) {
+  HRT_TRY(check_mesh(n, box));
+  HRT_TRY(check_particles(n_side, n));
+  if (!rho_bar || !disp || !disp_bar) return fail(HRT_ERR_INVALID_ARG, "NULL buffer");
+  return launch_deposit_adjoint(rho_bar, disp, n_side, n, box, disp_bar, as_stream(stream));
+}
+
+hrt_status hrt_particle_kick_drift_adjoint(const float* grad, int64_t n, double box, int64_t n_side, const float* disp,
+                                           const float* mom, double kick, double drift, const float* rho_bar,
+                                           float* disp_bar, float* mom_bar, float* grad_bar, double* coef_bar,
+                                           void* stream) {
+  HRT_TRY(check_mesh(n, box));
+  HRT_TRY(check_particles(n_side, n));
+  if (!grad || !disp || !mom || !disp_bar || !mom_bar || !grad_bar || !coef_bar)
+    return fail(HRT_ERR_INVALID_ARG, "NULL buffer");
+  return launch_kick_drift_adjoint(grad, n, box, n_side, disp, mom, kick, drift, rho_bar, disp_bar, mom_bar, grad_bar,
+                                   coef_bar, as_stream(stream));
+}
+
+hrt_status hrt_pm_solve_adjoint(hrt_pm* pm, float* grad_bar, double pref, const hrt_filter* f, float* ray_grad_bar,
+                                const hrt_filter* f_ray, float* rho_bar) {
+  if (!pm || !grad_bar || !rho_bar) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  HRT_TRY(check_filter(f));
+  if (ray_grad_bar && (pm->n_ray == 0 || !f_ray)) return fail(HRT_ERR_INVALID_ARG, "PM object has no ray fields");
+  if (ray_grad_bar) HRT_TRY(check_filter(f_ray));
+  HRT_TRY(pm_tables(pm, *f, &pm->tab_a, &pm->key_a));
+  if (ray_grad_bar) HRT_TRY(pm_tables(pm, *f_ray, &pm->tab_b, &pm->key_b));
+  const size_t sb = spectrum_bytes(pm->n), mb = static_cast<size_t>(pm->n) * pm->n * pm->n;
+  char* gh = static_cast<char*>(pm->grad_hat);
+  for (int j = 0; j < 3; ++j)
+    HRT_CUFFT(cufftExecR2C(pm->r2c, grad_bar + j * mb, reinterpret_cast<cufftComplex*>(gh + j * sb)));
+  HRT_TRY(launch_kspace_adjoint(gh, 3, pm->n, pm->box, pref, pm->tab_a, f, pm->rho_hat, false, pm->stream));
+  if (ray_grad_bar) {
+    for (int j = 0; j < pm->n_ray; ++j)
+      HRT_CUFFT(cufftExecR2C(pm->r2c, ray_grad_bar + j * mb, reinterpret_cast<cufftComplex*>(gh + (3 + j) * sb)));
+    HRT_TRY(launch_kspace_adjoint(gh + 3 * sb, pm->n_ray, pm->n, pm->box, pref, pm->tab_b, f_ray, pm->rho_hat, true,
+                                  pm->stream));
+  }
+  HRT_CUFFT(cufftExecC2R(pm->c2r, static_cast<cufftComplex*>(pm->rho_hat), rho_bar));
+  return HRT_OK;
+}
+
+hrt_status hrt_ray_step_adjoint(const hrt_rays* rays, const float* grad_x, const float* grad_y, const hrt_ray_geom* geom,
+                                double chi_from, double chi_to, double a_ref, double omega_m, const hrt_rays* bar,
+                                float* gx_bar, float* gy_bar, double* node_bar, double* drift_bar, void* stream) {
+  HRT_TRY(check_rays(rays));
+  HRT_TRY(check_rays(bar));
+  if (!geom || !grad_x || !grad_y || !gx_bar || !gy_bar || !node_bar || !drift_bar)
+    return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  if (bar->n_rays != rays->n_rays) return fail(HRT_ERR_INVALID_ARG, "ray counts differ");
+  static thread_local RayStepParams p;
+  HRT_TRY(build_ray_params(*geom, chi_from, chi_to, a_ref, omega_m, p));
+  return launch_ray_step_adjoint(*rays, grad_x, grad_y, p, *bar, gx_bar, gy_bar, node_bar, drift_bar, as_stream(stream));
+}
+
+hrt_status hrt_ray_step_coefficients(const hrt_ray_geom* geom, double chi_from, double chi_to, double a_ref,
+                                     double omega_m, int32_t* n1, int32_t* n2, double* cw, double* cwr, double* chi,
+                                     double* drift) {
+  if (!geom || !n1 || !n2 || !cw || !cwr || !chi || !drift) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  static thread_local RayStepParams p;
+  HRT_TRY(build_ray_params(*geom, chi_from, chi_to, a_ref, omega_m, p, cw, cwr, chi));
+  *n1 = p.n1;
+  *n2 = p.n2;
+  *drift = p.drift_d;
+  return HRT_OK;
+}
+
+hrt_status hrt_kappa_power_adjoint(const float* kappa, int64_t m, double dtheta, int32_t nbins, double ell_min,
+                                   double ell_max, const double* dl_dp, float* kappa_bar, void* stream) {
+  if (!kappa || !dl_dp || !kappa_bar) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  if (m < 2 || m % 2 || m > 16384 || nbins < 1 || nbins > 256 || !(dtheta > 0.0) || !(ell_min > 0.0) ||
+      !(ell_max > ell_min))
+    return fail(HRT_ERR_INVALID_ARG, "bad power-spectrum arguments");
+  cudaStream_t s = as_stream(stream);
+  cufftHandle fwd, inv;
+  HRT_CUFFT(cufftPlan2d(&fwd, static_cast<int>(m), static_cast<int>(m), CUFFT_R2C));
+  hrt_status st = cufft_status(cufftPlan2d(&inv, static_cast<int>(m), static_cast<int>(m), CUFFT_C2R), "plan C2R");
+  if (st != HRT_OK) {
+    cufftDestroy(fwd);
+    return st;
+  }
+  void* spec = nullptr;
+  double* sums = nullptr;
+  double* wbin = nullptr;
+  st = cufft_status(cufftSetStream(fwd, s), "cufftSetStream");
+  if (st == HRT_OK) st = cufft_status(cufftSetStream(inv, s), "cufftSetStream");
+  if (st == HRT_OK) st = device_alloc(&spec, static_cast<size_t>(m) * (m / 2 + 1) * sizeof(float2), s, "spectrum");
+  if (st == HRT_OK) st = device_alloc(reinterpret_cast<void**>(&sums), 3 * nbins * sizeof(double), s, "bins");
+  if (st == HRT_OK) st = device_alloc(reinterpret_cast<void**>(&wbin), nbins * sizeof(double), s, "bin weights");
+  if (st == HRT_OK)
+    st = cufft_status(cufftExecR2C(fwd, const_cast<float*>(kappa), static_cast<cufftComplex*>(spec)), "R2C");
+  if (st == HRT_OK) st = launch_power_bin(spec, m, dtheta, nbins, ell_min, ell_max, sums, s);
+  std::vector<double> h(3 * nbins), w(nbins, 0.0);
+  if (st == HRT_OK) st = cuda_status(cudaMemcpyAsync(h.data(), sums, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "bins");
+  if (st == HRT_OK) st = cuda_status(cudaStreamSynchronize(s), "sync");
+  if (st == HRT_OK) {
+    const double theta_field = m * dtheta;
+    const double c = std::pow(dtheta, 4) / (theta_field * theta_field);
+    for (int b = 0; b < nbins; ++b) {
+      const double cnt = h[2 * nbins + b];
+      w[b] = cnt > 0 ? 2.0 * c * dl_dp[b] / cnt : 0.0;
+    }
+    st = cuda_status(cudaMemcpyAsync(wbin, w.data(), nbins * sizeof(double), cudaMemcpyHostToDevice, s), "weights");
+  }
+  if (st == HRT_OK) st = launch_power_adjoint_weight(spec, m, dtheta, nbins, ell_min, ell_max, wbin, s);
+  if (st == HRT_OK)
+    st = cufft_status(cufftExecC2R(inv, static_cast<cufftComplex*>(spec), kappa_bar), "C2R");
+  if (st == HRT_OK) st = cuda_status(cudaStreamSynchronize(s), "sync");
+  device_free(spec, s);
+  device_free(sums, s);
+  device_free(wbin, s);
+  cudaStreamSynchronize(s);
+  cufftDestroy(fwd);
+  cufftDestroy(inv);
+  return st;
+}
+
+hrt_status hrt_ic_table(int64_t n_side, double box, const hrt_cosmology* cosmo, double a_init, double* table_host,
+                        double* ratio_host) {
+  HRT_TRY(check_mesh(n_side, box));
+  if (!cosmo || !table_host || !ratio_host) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  const std::vector<double> t = ic_table64(n_side, box, cosmo, a_init, ratio_host);
+  std::memcpy(table_host, t.data(), t.size() * sizeof(double));
+  return HRT_OK;
+}
+
+hrt_status hrt_ic_zeldovich_adjoint(const float* noise, int64_t n_side, double box, const hrt_cosmology* cosmo,
+                                    double a_init, const float* disp_bar, const float* mom_bar, const float* disp,
+                                    float* noise_bar, double* table_bar_host, double* ratio_bar_host, void* stream) {
+  HRT_TRY(check_mesh(n_side, box));
+  if (!noise || !cosmo || !disp_bar || !mom_bar || !disp || !noise_bar || !ratio_bar_host)
+    return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = as_stream(stream);
+  const int64_t n = n_side, np = n * n * n;
+  double ratio = 0.0;
+  const std::vector<double> t64 = ic_table64(n, box, cosmo, a_init, &ratio);
+  std::vector<float> table(t64.begin(), t64.end());
+  hrt_pm tmp;
+  hrt_status st = pm_make(n, box, 0, s, &tmp);
+  float* tab = nullptr;
+  float* tot = nullptr;
+  double* dbuf = nullptr;  // [0] ratio_bar, [1..] table_bar
+  const size_t nt = table.size();
+  if (st == HRT_OK) st = upload(table, &tab, s, "IC table");
+  if (st == HRT_OK) st = device_alloc(reinterpret_cast<void**>(&tot), 3 * np * sizeof(float), s, "disp_bar total");
+  if (st == HRT_OK) st = device_alloc(reinterpret_cast<void**>(&dbuf), (1 + nt) * sizeof(double), s, "IC cotangents");
+  if (st == HRT_OK) st = cuda_status(cudaMemsetAsync(dbuf, 0, (1 + nt) * sizeof(double), s), "memset");
+  // mom = ratio * disp: ratio_bar = <mom_bar, disp>, disp_bar_total = disp_bar + ratio * mom_bar
+  if (st == HRT_OK) st = launch_dot(mom_bar, disp, 3 * np, dbuf, s);
+  if (st == HRT_OK) st = cuda_status(cudaMemcpyAsync(tot, disp_bar, 3 * np * sizeof(float), cudaMemcpyDeviceToDevice, s), "copy");
+  if (st == HRT_OK) st = launch_axpy(mom_bar, tot, ratio, 3 * np, s);
+  const size_t sb = spectrum_bytes(n);
+  char* gh = static_cast<char*>(tmp.grad_hat);
+  for (int j = 0; j < 3 && st == HRT_OK; ++j)
+    st = cufft_status(cufftExecR2C(tmp.r2c, tot + j * np, reinterpret_cast<cufftComplex*>(gh + j * sb)), "IC adj R2C");
+  // w_hat into the rho_hat buffer, the adjoint spectrum written over the third disp spectrum's neighbour:
+  // use the FFT work-free C2R input buffer = rho_hat after the table cotangent pass
+  void* out = nullptr;
+  if (st == HRT_OK) st = device_alloc(&out, sb, s, "noise_bar spectrum");
+  if (st == HRT_OK)
+    st = cufft_status(cufftExecR2C(tmp.r2c, const_cast<float*>(noise), static_cast<cufftComplex*>(tmp.rho_hat)), "IC R2C");
+  if (st == HRT_OK) st = launch_ic_adjoint(gh, tmp.rho_hat, n, box, tab, out, table_bar_host ? dbuf + 1 : nullptr, s);
+  if (st == HRT_OK) st = cufft_status(cufftExecC2R(tmp.c2r, static_cast<cufftComplex*>(out), noise_bar), "IC adj C2R");
+  std::vector<double> hb(1 + nt);
+  if (st == HRT_OK) st = cuda_status(cudaMemcpyAsync(hb.data(), dbuf, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+  if (st == HRT_OK) st = cuda_status(cudaStreamSynchronize(s), "sync");
+  device_free(tab, s);
+  device_free(tot, s);
+  device_free(dbuf, s);
+  device_free(out, s);
+  pm_release(&tmp);
+  if (st != HRT_OK) return st;
+  *ratio_bar_host = hb[0];
+  if (table_bar_host) std::memcpy(table_bar_host, hb.data() + 1, nt * sizeof(double));
+  return HRT_OK;
+}
+
+hrt_status hrt_dot(const float* a, const float* b, int64_t m, double* out_host, void* stream) {
+  if (!a || !b || !out_host || m < 0) return fail(HRT_ERR_INVALID_ARG, "bad arguments");
+  cudaStream_t s = as_stream(stream);
+  double* d = nullptr;
+  HRT_TRY(device_alloc(reinterpret_cast<void**>(&d), sizeof(double), s, "dot"));
+  hrt_status st = cuda_status(cudaMemsetAsync(d, 0, sizeof(double), s), "memset");
+  if (st == HRT_OK) st = launch_dot(a, b, m, d, s);
+  if (st == HRT_OK) st = cuda_status(cudaMemcpyAsync(out_host, d, sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+  if (st == HRT_OK) st = cuda_status(cudaStreamSynchronize(s), "sync");
+  device_free(d, s);
   return st;
 }
 

@@ -94,6 +94,15 @@ _SIGS = {
     "hrt_read_particles": ([_P, _P, _P, _P, _P], C.c_int),
     "hrt_read_grad": ([_P, _P], C.c_int),
     "hrt_ctx_kappa_power": ([_P, _I32, _I64, _D, _I32, _D, _D, _P, _P, _P], C.c_int),
+    "hrt_cic_scatter_adjoint": ([_P, _P, _I64, _I64, _D, _P, _P], C.c_int),
+    "hrt_particle_kick_drift_adjoint": ([_P, _I64, _D, _I64, _P, _P, _D, _D, _P, _P, _P, _P, _P, _P], C.c_int),
+    "hrt_pm_solve_adjoint": ([_P, _P, _D, _P, _P, _P, _P], C.c_int),
+    "hrt_ray_step_adjoint": ([_P, _P, _P, _P, _D, _D, _D, _D, _P, _P, _P, _P, _P, _P], C.c_int),
+    "hrt_ray_step_coefficients": ([_P, _D, _D, _D, _D, _P, _P, _P, _P, _P, _P], C.c_int),
+    "hrt_kappa_power_adjoint": ([_P, _I64, _D, _I32, _D, _D, _P, _P, _P], C.c_int),
+    "hrt_ic_table": ([_I64, _D, _P, _D, _P, _P], C.c_int),
+    "hrt_ic_zeldovich_adjoint": ([_P, _I64, _D, _P, _D, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "hrt_dot": ([_P, _P, _I64, _P, _P], C.c_int),
     "hrt_ctx_set_profiling": ([_P, _I32], C.c_int),
     "hrt_ctx_phase_times": ([_P, _P, _P], C.c_int),
     "hrt_ctx_rays": ([_P, _P], C.c_int),
@@ -242,6 +251,13 @@ class PM:
                                  _ptr(grad, torch.float32, "grad"), C.byref(f_ray) if f_ray is not None else None,
                                  _ptr(ray_grad, torch.float32, "ray_grad")), "hrt_pm_solve")
 
+    def solve_adjoint(self, grad_bar: torch.Tensor, pref: float, f: hrt_filter, rho_bar: torch.Tensor,
+                      ray_grad_bar: torch.Tensor | None = None, f_ray: hrt_filter | None = None):
+        _check(_lib.hrt_pm_solve_adjoint(self._h, _ptr(grad_bar, torch.float32, "grad_bar"), pref, C.byref(f),
+                                         _ptr(ray_grad_bar, torch.float32, "ray_grad_bar"),
+                                         C.byref(f_ray) if f_ray is not None else None,
+                                         _ptr(rho_bar, torch.float32, "rho_bar")), "hrt_pm_solve_adjoint")
+
     def set_fused(self, on: bool):
         _check(_lib.hrt_pm_set_fused(self._h, int(on)), "hrt_pm_set_fused")
 
@@ -327,6 +343,89 @@ def hrt_ic_zeldovich(noise: torch.Tensor, n_side: int, box: float, omega_m: floa
     _check(_lib.hrt_ic_zeldovich(_ptr(noise, torch.float32, "noise"), n_side, box, C.byref(c), a_init,
                                  _ptr(disp, torch.float32, "disp"), _ptr(mom, torch.float32, "mom"), _stream(stream)),
            "hrt_ic_zeldovich")
+
+
+# ------------------------------------------------------------------------------------------------ adjoints
+MAX_RAY_NODES = 1024
+
+
+def hrt_cic_scatter_adjoint(rho_bar, disp, n_side, n, box, disp_bar, stream=None):
+    _check(_lib.hrt_cic_scatter_adjoint(_ptr(rho_bar, torch.float32, "rho_bar"), _ptr(disp, torch.float32, "disp"),
+                                        n_side, n, box, _ptr(disp_bar, torch.float32, "disp_bar"), _stream(stream)),
+           "hrt_cic_scatter_adjoint")
+
+
+def hrt_particle_kick_drift_adjoint(grad, n, box, n_side, disp, mom, kick, drift, rho_bar, disp_bar, mom_bar,
+                                    grad_bar, coef_bar, stream=None):
+    _check(_lib.hrt_particle_kick_drift_adjoint(
+        _ptr(grad, torch.float32, "grad"), n, box, n_side, _ptr(disp, torch.float32, "disp"),
+        _ptr(mom, torch.float32, "mom"), kick, drift, _ptr(rho_bar, torch.float32, "rho_bar"),
+        _ptr(disp_bar, torch.float32, "disp_bar"), _ptr(mom_bar, torch.float32, "mom_bar"),
+        _ptr(grad_bar, torch.float32, "grad_bar"), _ptr(coef_bar, torch.float64, "coef_bar"), _stream(stream)),
+        "hrt_particle_kick_drift_adjoint")
+
+
+def hrt_ray_step_adjoint(rays: RayState, grad_x, grad_y, geom, chi_from, chi_to, a_ref, omega_m, bar: RayState,
+                         gx_bar, gy_bar, node_bar, drift_bar, stream=None):
+    r, b = rays.c(), bar.c()
+    _check(_lib.hrt_ray_step_adjoint(C.byref(r), _ptr(grad_x, torch.float32, "grad_x"),
+                                     _ptr(grad_y, torch.float32, "grad_y"), C.byref(geom), chi_from, chi_to, a_ref,
+                                     omega_m, C.byref(b), _ptr(gx_bar, torch.float32, "gx_bar"),
+                                     _ptr(gy_bar, torch.float32, "gy_bar"), _ptr(node_bar, torch.float64, "node_bar"),
+                                     _ptr(drift_bar, torch.float64, "drift_bar"), _stream(stream)),
+           "hrt_ray_step_adjoint")
+
+
+def hrt_ray_step_coefficients(geom, chi_from, chi_to, a_ref, omega_m):
+    n1, n2 = C.c_int32(), C.c_int32()
+    cw = (C.c_double * MAX_RAY_NODES)()
+    cwr = (C.c_double * MAX_RAY_NODES)()
+    chi = (C.c_double * MAX_RAY_NODES)()
+    d = C.c_double()
+    _check(_lib.hrt_ray_step_coefficients(C.byref(geom), chi_from, chi_to, a_ref, omega_m, C.byref(n1), C.byref(n2),
+                                          cw, cwr, chi, C.byref(d)), "hrt_ray_step_coefficients")
+    k = n1.value + n2.value
+    import numpy as np
+    return (n1.value, n2.value, np.array(cw[:k]), np.array(cwr[:k]), np.array(chi[:k]), d.value)
+
+
+def hrt_kappa_power_adjoint(kappa, m, dtheta, nbins, ell_min, ell_max, dl_dp, kappa_bar, stream=None):
+    import numpy as np
+    w = np.ascontiguousarray(np.asarray(dl_dp, dtype=np.float64))
+    _check(_lib.hrt_kappa_power_adjoint(_ptr(kappa, torch.float32, "kappa"), m, dtheta, nbins, ell_min, ell_max,
+                                        w.ctypes.data, _ptr(kappa_bar, torch.float32, "kappa_bar"), _stream(stream)),
+           "hrt_kappa_power_adjoint")
+
+
+def hrt_ic_table(n_side, box, omega_m, h, n_s, sigma8, a_init):
+    import numpy as np
+    c = hrt_cosmology(omega_m, h, n_s, sigma8)
+    t = np.zeros(3 * (n_side // 2) ** 2 + 1)
+    ratio = C.c_double()
+    _check(_lib.hrt_ic_table(n_side, box, C.byref(c), a_init, t.ctypes.data, C.byref(ratio)), "hrt_ic_table")
+    return t, ratio.value
+
+
+def hrt_ic_zeldovich_adjoint(noise, n_side, box, omega_m, h, n_s, sigma8, a_init, disp_bar, mom_bar, disp, noise_bar,
+                             want_table=True, stream=None):
+    import numpy as np
+    c = hrt_cosmology(omega_m, h, n_s, sigma8)
+    tb = np.zeros(3 * (n_side // 2) ** 2 + 1) if want_table else None
+    rb = C.c_double()
+    _check(_lib.hrt_ic_zeldovich_adjoint(_ptr(noise, torch.float32, "noise"), n_side, box, C.byref(c), a_init,
+                                         _ptr(disp_bar, torch.float32, "disp_bar"),
+                                         _ptr(mom_bar, torch.float32, "mom_bar"), _ptr(disp, torch.float32, "disp"),
+                                         _ptr(noise_bar, torch.float32, "noise_bar"),
+                                         tb.ctypes.data if tb is not None else None, C.byref(rb), _stream(stream)),
+           "hrt_ic_zeldovich_adjoint")
+    return tb, rb.value
+
+
+def hrt_dot(a, b, stream=None) -> float:
+    out = C.c_double()
+    _check(_lib.hrt_dot(_ptr(a, torch.float32, "a"), _ptr(b, torch.float32, "b"), a.numel(), C.byref(out),
+                        _stream(stream)), "hrt_dot")
+    return out.value
 
 
 # ------------------------------------------------------------------------------------------------ context
