@@ -289,6 +289,47 @@ hrt_status hrt_ic_zeldovich_adjoint(const float* noise, int64_t n_side, double b
 hrt_status hrt_dot(const float* a, const float* b, int64_t m, double* out_host, void* stream);
 
 /* ------------------------------------------------------------------------------------------------------
+ * Learned force correction (the analogue of the force-sharpening factor g of Sec. 5.2, k/k^2 -> (k/k^2) g,
+ * here applied to the ray gradient fields of a coarse mesh): g = 1 + MLP(|k| cell, a, ln N_mesh), a 3-64-64-
+ * 64-1 perceptron with SiLU activations.  Parameters: HRT_MLP_PARAMS floats in the order W1 [64][16] (input
+ * columns 3..15 zero), b1 [64], W2 [64][64], b2 [64], W3 [64][64], b3 [64], W4 [64], b4 [1]; a BF16 copy of the
+ * same layout (2 bytes per entry) feeds the tensor-core forward; biases are read from the FP32 master.
+ * ---------------------------------------------------------------------------------------------------- */
+#define HRT_MLP_PARAMS 9473
+
+/* g[rows] = 1 + MLP(x[rows][3]): BF16 weights and activations, FP32 accumulation (tensor cores). */
+hrt_status hrt_mlp_forward(const float* x, int32_t rows, const void* w_bf16, const float* w_f32, float* g,
+                           void* stream);
+
+/* grad[HRT_MLP_PARAMS] += d(sum_r g_bar[r] g[r]) / d parameters (FP32, with the BF16-rounded weights). */
+hrt_status hrt_mlp_backward(const float* x, int32_t rows, const void* w_bf16, const float* w_f32,
+                            const float* g_bar, float* grad, void* stream);
+
+/* One Adam step (bias-corrected, step >= 1) on the FP32 master, then the BF16 copy. */
+hrt_status hrt_mlp_adam(float* w_f32, void* w_bf16, const float* grad, float* m, float* v, double lr, double beta1,
+                        double beta2, double eps, int32_t step, void* stream);
+
+/* BF16 copy of the FP32 master (padding columns zeroed). */
+hrt_status hrt_mlp_to_bf16(const float* w_f32, void* w_bf16, void* stream);
+
+/* Cotangent of the learned table: table_bar[g_nk] += dL/dg_i for gradient fields made by hrt_kspace_gradient
+ * with filter *f (whose g_table has g_nk entries over [0, g_kmax]) from rho_hat, given gbar_hat = the real-to-
+ * complex FFT of the cotangents of those n_comp fields (x, y[, z]). */
+hrt_status hrt_kspace_table_adjoint(const void* gbar_hat, int32_t n_comp, const void* rho_hat, int64_t n, double box,
+                                    double pref, const hrt_filter* f, float* table_bar, void* stream);
+
+/* Copies the density half spectrum of the last hrt_pm_solve into out (complex64 [n][n][n/2+1]). */
+hrt_status hrt_pm_density_spectrum(hrt_pm* pm, void* out);
+
+/* fields[n_out][n^3] <- gradient fields from a stored density half spectrum rho_hat (not modified): the k-space
+ * kernel with filter *f, then n_out complex-to-real FFTs (the second half of hrt_pm_solve). */
+hrt_status hrt_pm_gradient_from_spectrum(hrt_pm* pm, const void* rho_hat, double pref, const hrt_filter* f,
+                                         int32_t n_out, float* fields);
+
+/* out (complex64 half spectrum) <- real-to-complex FFT of real[n^3] with the object's plan. */
+hrt_status hrt_pm_forward_fft(hrt_pm* pm, const float* real, void* out);
+
+/* ------------------------------------------------------------------------------------------------------
  * Simulation context: particles + mesh + rays co-evolved as in Alg. 1 (one PM force per step).
  * ---------------------------------------------------------------------------------------------------- */
 typedef struct hrt_config {

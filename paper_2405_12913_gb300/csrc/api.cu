@@ -16,6 +16,7 @@
 #include "cosmo.h"
 #include "kspace_callback.h"
 #include "mesh_kernels.h"
+#include "mlp.h"
 
 extern "C" const unsigned char hrt_kspace_callback_fatbin[];
 extern "C" const size_t hrt_kspace_callback_fatbin_size;
@@ -942,6 +943,75 @@ hrt_status hrt_dot(const float* a, const float* b, int64_t m, double* out_host, 
   if (st == HRT_OK) st = cuda_status(cudaStreamSynchronize(s), "sync");
   device_free(d, s);
   return st;
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// Learned correction
+// ---------------------------------------------------------------------------------------------------------
+hrt_status hrt_mlp_forward(const float* x, int32_t rows, const void* w_bf16, const float* w_f32, float* g,
+                           void* stream) {
+  if (!x || !w_bf16 || !w_f32 || !g || rows < 0) return fail(HRT_ERR_INVALID_ARG, "bad MLP arguments");
+  if (rows == 0) return HRT_OK;
+  return launch_mlp_forward(x, rows, w_bf16, w_f32, g, as_stream(stream));
+}
+
+hrt_status hrt_mlp_backward(const float* x, int32_t rows, const void* w_bf16, const float* w_f32, const float* g_bar,
+                            float* grad, void* stream) {
+  if (!x || !w_bf16 || !w_f32 || !g_bar || !grad || rows < 0) return fail(HRT_ERR_INVALID_ARG, "bad MLP arguments");
+  if (rows == 0) return HRT_OK;
+  return launch_mlp_backward(x, rows, w_bf16, w_f32, g_bar, grad, as_stream(stream));
+}
+
+hrt_status hrt_mlp_adam(float* w_f32, void* w_bf16, const float* grad, float* m, float* v, double lr, double beta1,
+                        double beta2, double eps, int32_t step, void* stream) {
+  if (!w_f32 || !w_bf16 || !grad || !m || !v || step < 1) return fail(HRT_ERR_INVALID_ARG, "bad Adam arguments");
+  return launch_adam(w_f32, w_bf16, grad, m, v, lr, beta1, beta2, eps, step, as_stream(stream));
+}
+
+hrt_status hrt_mlp_to_bf16(const float* w_f32, void* w_bf16, void* stream) {
+  if (!w_f32 || !w_bf16) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  return launch_to_bf16(w_f32, w_bf16, as_stream(stream));
+}
+
+hrt_status hrt_kspace_table_adjoint(const void* gbar_hat, int32_t n_comp, const void* rho_hat, int64_t n, double box,
+                                    double pref, const hrt_filter* f, float* table_bar, void* stream) {
+  HRT_TRY(check_mesh(n, box));
+  HRT_TRY(check_filter(f));
+  if (!gbar_hat || !rho_hat || !table_bar || n_comp < 1 || n_comp > 3 || !f->g_table)
+    return fail(HRT_ERR_INVALID_ARG, "bad table-adjoint arguments");
+  cudaStream_t s = as_stream(stream);
+  float* tab = nullptr;
+  hrt_status st = filter_upload(n, box, *f, &tab, s);
+  if (st == HRT_OK)
+    st = launch_kspace_table_adjoint(gbar_hat, n_comp, rho_hat, n, box, pref, tab, f->g_nk, f->g_kmax, table_bar, s);
+  device_free(tab, s);
+  return st;
+}
+
+hrt_status hrt_pm_gradient_from_spectrum(hrt_pm* pm, const void* rho_hat, double pref, const hrt_filter* f,
+                                         int32_t n_out, float* fields) {
+  if (!pm || !rho_hat || !fields || n_out < 1 || n_out > 3) return fail(HRT_ERR_INVALID_ARG, "bad arguments");
+  HRT_TRY(check_filter(f));
+  float* tab = nullptr;
+  HRT_TRY(filter_upload(pm->n, pm->box, *f, &tab, pm->stream));
+  char* gh = static_cast<char*>(pm->grad_hat);
+  const size_t sb = spectrum_bytes(pm->n), mb = static_cast<size_t>(pm->n) * pm->n * pm->n;
+  hrt_status st = launch_kspace(rho_hat, pm->n, pm->box, pref, tab, f, n_out, gh, nullptr, f, 0, nullptr, pm->stream);
+  for (int j = 0; j < n_out && st == HRT_OK; ++j)
+    st = cufft_status(cufftExecC2R(pm->c2r, reinterpret_cast<cufftComplex*>(gh + j * sb), fields + j * mb), "C2R");
+  device_free(tab, pm->stream);
+  return st;
+}
+
+hrt_status hrt_pm_forward_fft(hrt_pm* pm, const float* real, void* out) {
+  if (!pm || !real || !out) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  return cufft_status(cufftExecR2C(pm->r2c, const_cast<float*>(real), static_cast<cufftComplex*>(out)), "R2C");
+}
+
+hrt_status hrt_pm_density_spectrum(hrt_pm* pm, void* out) {
+  if (!pm || !out) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  return cuda_status(cudaMemcpyAsync(out, pm->rho_hat, spectrum_bytes(pm->n), cudaMemcpyDeviceToDevice, pm->stream),
+                     "copy density spectrum");
 }
 
 // ---------------------------------------------------------------------------------------------------------

@@ -1,0 +1,22 @@
+// Launch wrappers of the learned-correction kernels (mlp_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.h"
+
+namespace hrt {
+
+constexpr int kMlpParams = 9473;  // W1 64x16 (3 used), b1 64, W2 64x64, b2 64, W3 64x64, b3 64, W4 64, b4 1
+
+hrt_status launch_mlp_forward(const float* x, int rows, const void* wb, const float* wf, float* y, cudaStream_t s);
+hrt_status launch_mlp_backward(const float* x, int rows, const void* wb, const float* wf, const float* gbar,
+                               float* grad, cudaStream_t s);
+hrt_status launch_adam(float* wf, void* wb, const float* grad, float* m, float* v, double lr, double b1, double b2,
+                       double eps, int step, cudaStream_t s);
+hrt_status launch_to_bf16(const float* wf, void* wb, cudaStream_t s);
+hrt_status launch_kspace_table_adjoint(const void* gbar_hat, int n_comp, const void* rho_hat, int64_t n, double box,
+                                       double pref, const float* tab, int g_nk, double g_kmax, float* table_bar,
+                                       cudaStream_t s);
+
+}  // namespace hrt

@@ -103,6 +103,14 @@ _SIGS = {
     "hrt_ic_table": ([_I64, _D, _P, _D, _P, _P], C.c_int),
     "hrt_ic_zeldovich_adjoint": ([_P, _I64, _D, _P, _D, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "hrt_dot": ([_P, _P, _I64, _P, _P], C.c_int),
+    "hrt_mlp_forward": ([_P, _I32, _P, _P, _P, _P], C.c_int),
+    "hrt_mlp_backward": ([_P, _I32, _P, _P, _P, _P, _P], C.c_int),
+    "hrt_mlp_adam": ([_P, _P, _P, _P, _P, _D, _D, _D, _D, _I32, _P], C.c_int),
+    "hrt_mlp_to_bf16": ([_P, _P, _P], C.c_int),
+    "hrt_kspace_table_adjoint": ([_P, _I32, _P, _I64, _D, _D, _P, _P, _P], C.c_int),
+    "hrt_pm_density_spectrum": ([_P, _P], C.c_int),
+    "hrt_pm_gradient_from_spectrum": ([_P, _P, _D, _P, _I32, _P], C.c_int),
+    "hrt_pm_forward_fft": ([_P, _P, _P], C.c_int),
     "hrt_ctx_set_profiling": ([_P, _I32], C.c_int),
     "hrt_ctx_phase_times": ([_P, _P, _P], C.c_int),
     "hrt_ctx_rays": ([_P, _P], C.c_int),
@@ -257,6 +265,19 @@ class PM:
                                          _ptr(ray_grad_bar, torch.float32, "ray_grad_bar"),
                                          C.byref(f_ray) if f_ray is not None else None,
                                          _ptr(rho_bar, torch.float32, "rho_bar")), "hrt_pm_solve_adjoint")
+
+    def density_spectrum(self, out: torch.Tensor):
+        _check(_lib.hrt_pm_density_spectrum(self._h, _ptr(out, torch.complex64, "out")), "hrt_pm_density_spectrum")
+
+    def gradient_from_spectrum(self, rho_hat: torch.Tensor, pref: float, f: hrt_filter, n_out: int,
+                               fields: torch.Tensor):
+        _check(_lib.hrt_pm_gradient_from_spectrum(self._h, _ptr(rho_hat, torch.complex64, "rho_hat"), pref,
+                                                  C.byref(f), n_out, _ptr(fields, torch.float32, "fields")),
+               "hrt_pm_gradient_from_spectrum")
+
+    def forward_fft(self, real: torch.Tensor, out: torch.Tensor):
+        _check(_lib.hrt_pm_forward_fft(self._h, _ptr(real, torch.float32, "real"), _ptr(out, torch.complex64, "out")),
+               "hrt_pm_forward_fft")
 
     def set_fused(self, on: bool):
         _check(_lib.hrt_pm_set_fused(self._h, int(on)), "hrt_pm_set_fused")
@@ -426,6 +447,41 @@ def hrt_dot(a, b, stream=None) -> float:
     _check(_lib.hrt_dot(_ptr(a, torch.float32, "a"), _ptr(b, torch.float32, "b"), a.numel(), C.byref(out),
                         _stream(stream)), "hrt_dot")
     return out.value
+
+
+# ------------------------------------------------------------------------------------------------ learned correction
+MLP_PARAMS = 9473
+
+
+def hrt_mlp_forward(x, w_bf16, w_f32, g, stream=None):
+    _check(_lib.hrt_mlp_forward(_ptr(x, torch.float32, "x"), x.shape[0], _ptr(w_bf16, torch.bfloat16, "w_bf16"),
+                                _ptr(w_f32, torch.float32, "w_f32"), _ptr(g, torch.float32, "g"), _stream(stream)),
+           "hrt_mlp_forward")
+
+
+def hrt_mlp_backward(x, w_bf16, w_f32, g_bar, grad, stream=None):
+    _check(_lib.hrt_mlp_backward(_ptr(x, torch.float32, "x"), x.shape[0], _ptr(w_bf16, torch.bfloat16, "w_bf16"),
+                                 _ptr(w_f32, torch.float32, "w_f32"), _ptr(g_bar, torch.float32, "g_bar"),
+                                 _ptr(grad, torch.float32, "grad"), _stream(stream)), "hrt_mlp_backward")
+
+
+def hrt_mlp_adam(w_f32, w_bf16, grad, m, v, lr, beta1, beta2, eps, step, stream=None):
+    _check(_lib.hrt_mlp_adam(_ptr(w_f32, torch.float32, "w_f32"), _ptr(w_bf16, torch.bfloat16, "w_bf16"),
+                             _ptr(grad, torch.float32, "grad"), _ptr(m, torch.float32, "m"),
+                             _ptr(v, torch.float32, "v"), lr, beta1, beta2, eps, step, _stream(stream)),
+           "hrt_mlp_adam")
+
+
+def hrt_mlp_to_bf16(w_f32, w_bf16, stream=None):
+    _check(_lib.hrt_mlp_to_bf16(_ptr(w_f32, torch.float32, "w_f32"), _ptr(w_bf16, torch.bfloat16, "w_bf16"),
+                                _stream(stream)), "hrt_mlp_to_bf16")
+
+
+def hrt_kspace_table_adjoint(gbar_hat, n_comp, rho_hat, n, box, pref, f: hrt_filter, table_bar, stream=None):
+    _check(_lib.hrt_kspace_table_adjoint(_ptr(gbar_hat, torch.complex64, "gbar_hat"), n_comp,
+                                         _ptr(rho_hat, torch.complex64, "rho_hat"), n, box, pref, C.byref(f),
+                                         _ptr(table_bar, torch.float32, "table_bar"), _stream(stream)),
+           "hrt_kspace_table_adjoint")
 
 
 # ------------------------------------------------------------------------------------------------ context

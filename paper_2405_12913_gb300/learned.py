@@ -1,0 +1,314 @@
+"""Learned correction of the coarse-mesh ray force, trained on the method's own coarse/fine mesh pairs.
+
+The paper sharpens the PM force with a trained factor g in k/k^2 -> (k/k^2) g (Sec. 5.2).  Here g = 1 + MLP(|k| cell,
+a, ln N_mesh) multiplies the Green's function of the ray gradient fields of a coarse mesh (the particles keep the
+plain force), and is trained so that the convergence power spectrum of the coarse run matches that of a run with
+the same initial conditions on a mesh four times finer.  The plain kernel (g = 1) is both the fallback and the
+judge: ``evaluate`` reports the P(ell) error of both forms against the fine run on held-out seeds.
+
+Training uses only libhrt kernels: the tensor-core MLP forward, the ray-step and k-space-table adjoints, the FP32
+MLP backward and an Adam kernel.  The particles do not depend on g, so the density spectrum of each reverse step is
+computed once per seed (plain coarse run) and every training iteration re-traces only the rays.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+from dataclasses import dataclass, replace
+
+import numpy as np
+import torch
+
+from . import hrt
+
+N_TABLE = 512
+
+
+class MLP:
+    """Parameters (FP32 master + BF16 copy) and Adam state of the correction network on the GPU."""
+
+    def __init__(self, seed: int = 0):
+        rng = np.random.default_rng(seed)
+        p = np.zeros(hrt.MLP_PARAMS, np.float32)
+        H, IN = 64, 16
+        w1 = rng.standard_normal((H, 3)) * math.sqrt(2.0 / 3.0)
+        W1 = np.zeros((H, IN))
+        W1[:, :3] = w1
+        o = 0
+        p[o:o + H * IN] = W1.ravel()
+        o += H * IN + H
+        p[o:o + H * H] = (rng.standard_normal((H, H)) * math.sqrt(2.0 / H)).ravel()
+        o += H * H + H
+        p[o:o + H * H] = (rng.standard_normal((H, H)) * math.sqrt(2.0 / H)).ravel()
+        # output layer zero: g = 1 at the start (the plain kernel)
+        self.w = torch.tensor(p, device="cuda")
+        self.wb = torch.empty(hrt.MLP_PARAMS, dtype=torch.bfloat16, device="cuda")
+        hrt.hrt_mlp_to_bf16(self.w, self.wb)
+        self.m = torch.zeros_like(self.w)
+        self.v = torch.zeros_like(self.w)
+        self.step = 0
+
+    @staticmethod
+    def inputs(kmax: float, cell: float, a: float, n_mesh: int) -> torch.Tensor:
+        k = torch.linspace(0.0, kmax, N_TABLE, dtype=torch.float64)
+        x = torch.stack([k * cell, torch.full_like(k, a), torch.full_like(k, math.log(n_mesh))], dim=1)
+        return x.to(device="cuda", dtype=torch.float32).contiguous()
+
+    def table(self, x: torch.Tensor) -> torch.Tensor:
+        g = torch.empty(x.shape[0], device="cuda")
+        hrt.hrt_mlp_forward(x, self.wb, self.w, g)
+        return g
+
+    def accumulate(self, x, g_bar, grad):
+        hrt.hrt_mlp_backward(x, self.wb, self.w, g_bar, grad)
+
+    def adam(self, grad, lr):
+        self.step += 1
+        hrt.hrt_mlp_adam(self.w, self.wb, grad, self.m, self.v, lr, 0.9, 0.999, 1e-8, self.step)
+
+    def state(self):
+        return self.w.detach().cpu().numpy()
+
+
+@dataclass
+class PairSpec:
+    """Coarse/fine mesh pair: shared particles, box, time grids and rays; meshes differ."""
+    n_side: int = 256
+    n_coarse: int = 256
+    n_fine: int = 1024
+    box: float = 256.0
+    a_init: float = 0.02
+    n_forward: int = 32
+    a_min: float = 0.5
+    n_reverse: int = 16
+    n_pix: int = 1024
+    fov_deg: float = 3.5
+    omega_m: float = 0.3
+    h: float = 0.7
+    n_s: float = 0.96
+    sigma8: float = 0.8
+    deconv_p: float = 4.0
+    smooth_cells: float = 1.0
+    nbins: int = 20
+    ell_cut: float = 1.0e4
+
+    @property
+    def forward_grid(self):
+        return [self.a_init + (1.0 - self.a_init) * i / self.n_forward for i in range(self.n_forward + 1)]
+
+    @property
+    def reverse_grid(self):
+        return [1.0 - (1.0 - self.a_min) * i / self.n_reverse for i in range(self.n_reverse + 1)]
+
+    @property
+    def observer(self):
+        return (0.5 * self.box, 0.5 * self.box, 0.0)
+
+    @property
+    def dtheta(self):
+        return self.fov_deg * math.pi / 180.0 / self.n_pix
+
+    @property
+    def ell_range(self):
+        return 2.0 * math.pi / (self.n_pix * self.dtheta), math.pi / self.dtheta
+
+
+def _theta0(S: PairSpec) -> torch.Tensor:
+    d = S.fov_deg * math.pi / 180.0 / S.n_pix
+    c = (torch.arange(S.n_pix, dtype=torch.float64) + 0.5 - 0.5 * S.n_pix) * d
+    ty, tx = torch.meshgrid(c, c, indexing="ij")
+    return torch.stack([tx.reshape(-1), ty.reshape(-1)], dim=1).cuda()
+
+
+def _noise(seed: int, n: int) -> torch.Tensor:
+    w = np.random.default_rng(seed).standard_normal((n, n, n))
+    return torch.tensor(w, dtype=torch.float32, device="cuda")
+
+
+def plain_run(S: PairSpec, n_mesh: int, seed: int, record_spectra: bool = False):
+    """Plain HRT run on an n_mesh^3 mesh (context API): returns (kappa map, [density spectra per reverse step])."""
+    cfg = hrt.make_config(n_mesh, S.box, S.n_side, S.omega_m, S.h, S.n_s, S.sigma8, S.deconv_p, S.smooth_cells,
+                          1.0, S.observer, n_sources=1)
+    ctx = hrt.Context(cfg)
+    ctx.hrt_init_particles_zeldovich(_noise(seed, S.n_side).reshape(-1), S.a_init)
+    for a in S.forward_grid[1:]:
+        ctx.hrt_step(a)
+    ctx.hrt_sync_particles()
+    ctx.hrt_init_rays(_theta0(S))
+    spectra = []
+    rg = S.reverse_grid
+    for n in range(S.n_reverse):
+        if record_spectra:
+            spectra.append(_ctx_density_spectrum(ctx, S, n_mesh, rg[n]))
+        ctx.hrt_step(rg[n + 1], 0 if n + 1 == S.n_reverse else -1)
+    kappa = ctx.hrt_read_maps(0)[0].clone()
+    ctx.close()
+    return kappa, spectra
+
+
+def _ctx_density_spectrum(ctx, S, n_mesh, a):
+    """Density spectrum of the context's current particles (the density behind its current force)."""
+    disp, _, _, _ = ctx.hrt_read_particles()
+    rho = torch.empty(n_mesh ** 3, device="cuda")
+    hrt.hrt_cic_scatter(disp, S.n_side, n_mesh, S.box, rho)
+    pm = _pm_cache(n_mesh, S.box)
+    spec = torch.empty(n_mesh, n_mesh, n_mesh // 2 + 1, dtype=torch.complex64, device="cuda")
+    pm.forward_fft(rho, spec)
+    return spec
+
+
+_PMS: dict = {}
+
+
+def _pm_cache(n, box):
+    key = (n, box)
+    if key not in _PMS:
+        _PMS[key] = hrt.PM(n, box)
+    return _PMS[key]
+
+
+def power(S: PairSpec, kappa: torch.Tensor):
+    lmin, lmax = S.ell_range
+    return hrt.hrt_kappa_power(kappa.contiguous(), S.n_pix, S.dtheta, S.nbins, lmin, lmax)
+
+
+class RayTrainer:
+    """Ray-only forward/backward of the coarse run with the learned ray table, on stored density spectra."""
+
+    def __init__(self, S: PairSpec):
+        self.S = S
+        n = S.n_coarse
+        self.cell = S.box / n
+        self.kmax = math.sqrt(3.0) * math.pi / self.cell * 1.0001
+        self.pm = _pm_cache(n, S.box)
+        self.geom = hrt.make_geom(n, S.box, S.observer, 1.0, image_width=S.n_pix)
+        self.theta0 = _theta0(S)
+        rg = S.reverse_grid
+        self.steps = []
+        for i in range(S.n_reverse):
+            a0, a1 = rg[i], rg[i + 1]
+            self.steps.append((a0, a1, hrt.hrt_cosmo_eval(S.omega_m, a0)[1], hrt.hrt_cosmo_eval(S.omega_m, a1)[1]))
+        self.x = [MLP.inputs(self.kmax, self.cell, a0, n) for (a0, _, _, _) in self.steps]
+
+    def _filter(self, table):
+        return hrt.make_filter(self.S.deconv_p, self.S.smooth_cells * self.cell, table, self.kmax)
+
+    def forward(self, mlp: MLP | None, spectra, keep: bool):
+        S, n = self.S, self.S.n_coarse
+        rays = hrt.RayState(self.theta0.shape[0])
+        hrt.hrt_rays_init(rays, self.theta0)
+        maps = torch.empty(4, rays.n_rays, device="cuda")
+        saved = []
+        for i, (a0, a1, c0, c1) in enumerate(self.steps):
+            table = mlp.table(self.x[i]) if mlp is not None else torch.ones(N_TABLE, device="cuda")
+            f = self._filter(table)
+            fields = torch.empty(2, n ** 3, device="cuda")
+            self.pm.gradient_from_spectrum(spectra[i], 1.5 * S.omega_m / a0, f, 2, fields)
+            if keep:
+                pre = hrt.RayState(rays.n_rays)
+                for name in ("theta", "eta", "A", "B"):
+                    getattr(pre, name).copy_(getattr(rays, name))
+                saved.append((pre, fields, table))
+            hrt.hrt_ray_step(rays, fields[0], fields[1], self.geom, c0, c1, a0, S.omega_m,
+                             maps if i + 1 == len(self.steps) else None)
+        return maps[0].clone(), saved
+
+    def backward(self, mlp: MLP, spectra, saved, kappa_bar, grad):
+        S, n = self.S, self.S.n_coarse
+        r_bar = hrt.RayState(self.theta0.shape[0])
+        for name in ("theta", "eta", "A", "B"):
+            getattr(r_bar, name).zero_()
+        r_bar.A[:, 0] -= 0.5 * kappa_bar
+        r_bar.A[:, 3] -= 0.5 * kappa_bar
+        nb = torch.zeros(3, hrt.MAX_RAY_NODES, dtype=torch.float64, device="cuda")
+        db = torch.zeros(1, dtype=torch.float64, device="cuda")
+        gbar_hat = torch.empty(2, n, n, n // 2 + 1, dtype=torch.complex64, device="cuda")
+        for i in reversed(range(len(self.steps))):
+            a0, a1, c0, c1 = self.steps[i]
+            pre, fields, table = saved[i]
+            gb = torch.zeros(2, n ** 3, device="cuda")
+            hrt.hrt_ray_step_adjoint(pre, fields[0], fields[1], self.geom, c0, c1, a0, S.omega_m, r_bar, gb[0], gb[1],
+                                     nb, db)
+            self.pm.forward_fft(gb[0], gbar_hat[0])
+            self.pm.forward_fft(gb[1], gbar_hat[1])
+            tb = torch.zeros(N_TABLE, device="cuda")
+            hrt.hrt_kspace_table_adjoint(gbar_hat, 2, spectra[i], n, S.box, 1.5 * S.omega_m / a0, self._filter(table),
+                                         tb)
+            mlp.accumulate(self.x[i], tb, grad)
+
+
+def _bins(S: PairSpec, ell, cnt):
+    return (cnt > 0) & (ell <= S.ell_cut)
+
+
+def train(S: PairSpec, train_seeds, test_seeds, iters: int = 60, lr: float = 2e-3, log=print):
+    t0 = time.time()
+    fine, spectra, plain_p = {}, {}, {}
+    for s in list(train_seeds) + list(test_seeds):
+        kf, _ = plain_run(S, S.n_fine, s)
+        ell, pf, cnt = power(S, kf)
+        kc, sp = plain_run(S, S.n_coarse, s, record_spectra=True)
+        _, pc, _ = power(S, kc)
+        fine[s], spectra[s], plain_p[s] = pf, sp, pc
+    sel = _bins(S, ell, cnt)
+    log(f"paired runs: {len(fine)} seeds in {time.time() - t0:.1f} s")
+    trainer = RayTrainer(S)
+    mlp = MLP(seed=0)
+    history = []
+    for it in range(iters):
+        grad = torch.zeros(hrt.MLP_PARAMS, device="cuda")
+        loss = 0.0
+        for s in train_seeds:
+            kappa, saved = trainer.forward(mlp, spectra[s], keep=True)
+            _, p, _ = power(S, kappa)
+            r = p / fine[s] - 1.0
+            loss += float((r[sel] ** 2).sum()) / len(train_seeds)
+            p_bar = np.where(sel, 2.0 * r / fine[s], 0.0) / len(train_seeds)
+            kb = torch.empty_like(kappa)
+            lmin, lmax = S.ell_range
+            hrt.hrt_kappa_power_adjoint(kappa, S.n_pix, S.dtheta, S.nbins, lmin, lmax, p_bar, kb)
+            trainer.backward(mlp, spectra[s], saved, kb, grad)
+            del saved
+        mlp.adam(grad, lr)
+        history.append(loss)
+        if it % 10 == 0 or it == iters - 1:
+            log(f"iter {it:3d} loss {loss:.4e} ({time.time() - t0:.1f} s)")
+    result = evaluate(S, trainer, mlp, test_seeds, fine, spectra, plain_p, sel)
+    result["history"] = history
+    result["train_seconds"] = time.time() - t0
+    return mlp, result
+
+
+def evaluate(S, trainer, mlp, seeds, fine, spectra, plain_p, sel):
+    err_plain, err_learned = [], []
+    for s in seeds:
+        kappa, _ = trainer.forward(mlp, spectra[s], keep=False)
+        _, p, _ = power(S, kappa)
+        err_learned.append(np.abs(p[sel] / fine[s][sel] - 1.0))
+        err_plain.append(np.abs(plain_p[s][sel] / fine[s][sel] - 1.0))
+    ep, el = np.array(err_plain), np.array(err_learned)
+    return {"bins": int(sel.sum()), "plain_mean_rel_err": float(ep.mean()), "plain_max_rel_err": float(ep.max()),
+            "learned_mean_rel_err": float(el.mean()), "learned_max_rel_err": float(el.max()),
+            "plain_err_per_bin": ep.mean(axis=0).tolist(), "learned_err_per_bin": el.mean(axis=0).tolist()}
+
+
+def main():
+    ap = argparse.ArgumentParser(description="train and evaluate the learned ray-force correction")
+    ap.add_argument("--train-seeds", type=int, default=16)
+    ap.add_argument("--test-seeds", type=int, default=4)
+    ap.add_argument("--iters", type=int, default=60)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--n-pix", type=int, default=1024)
+    ap.add_argument("--out", default=None, help="write the trained FP32 parameters (.npy) here")
+    a = ap.parse_args()
+    S = replace(PairSpec(), n_pix=a.n_pix)
+    mlp, res = train(S, range(a.train_seeds), range(100, 100 + a.test_seeds), a.iters, a.lr)
+    if a.out:
+        np.save(a.out, mlp.state())
+    print(json.dumps({k: v for k, v in res.items() if k != "history"}))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,113 @@
+"""The learned ray-force correction: tensor-core MLP, its backward, the table adjoint, and a training run whose
+trained network must beat the plain kernel against the fine-mesh run on held-out seeds."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synthetic
+from oracle import mlp as omlp
+from oracle import pm as opm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hrt():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_12913_gb300 import hrt as h
+    return h
+
+
+def _params(seed):
+    rng = np.random.default_rng(seed)
+    p = (rng.standard_normal(omlp.N_PARAMS) * 0.25).astype(np.float32)
+    p.reshape(-1)[:64 * 16].reshape(64, 16)[:, 3:] = 0.0
+    return p
+
+
+def _x(rows, seed):
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.uniform(0, 5.4, rows), rng.uniform(0.3, 1.0, rows), np.full(rows, math.log(256.0))], 1)
+
+
+@pytest.mark.parametrize("rows", [512, 77])
+def test_mlp_forward_matches_oracle(hrt, rows):
+    p = _params(1)
+    x = _x(rows, 2)
+    w = torch.tensor(p, device="cuda")
+    wb = torch.empty(hrt.MLP_PARAMS, dtype=torch.bfloat16, device="cuda")
+    hrt.hrt_mlp_to_bf16(w, wb)
+    g = torch.empty(rows, device="cuda")
+    hrt.hrt_mlp_forward(torch.tensor(x, dtype=torch.float32, device="cuda"), wb, w, g)
+    want = omlp.forward(torch.tensor(x.astype(np.float32), dtype=torch.float64), torch.tensor(p, dtype=torch.float64))
+    y = want.numpy() - 1.0
+    assert np.abs(g.cpu().double().numpy() - 1.0 - y).max() <= 2e-3 * np.abs(y).max()
+
+
+def test_mlp_backward_matches_oracle_autograd(hrt):
+    rows = 300
+    p = _params(3)
+    x = _x(rows, 4)
+    gbar = np.random.default_rng(5).standard_normal(rows)
+    w = torch.tensor(p, device="cuda")
+    wb = torch.empty(hrt.MLP_PARAMS, dtype=torch.bfloat16, device="cuda")
+    hrt.hrt_mlp_to_bf16(w, wb)
+    grad = torch.zeros(hrt.MLP_PARAMS, device="cuda")
+    hrt.hrt_mlp_backward(torch.tensor(x, dtype=torch.float32, device="cuda"), wb, w,
+                         torch.tensor(gbar, dtype=torch.float32, device="cuda"), grad)
+    pt = torch.tensor(p, dtype=torch.float64, requires_grad=True)
+    (omlp.forward(torch.tensor(x.astype(np.float32), dtype=torch.float64), pt, True, False)
+     * torch.tensor(gbar)).sum().backward()
+    want = pt.grad.numpy().copy()
+    want[:64 * 16].reshape(64, 16)[:, 3:] = 0.0
+    got = grad.cpu().double().numpy()
+    assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max()
+
+
+def test_table_adjoint_matches_oracle_autograd(hrt):
+    n, box, pref = 32, 64.0, 1.2
+    cell = box / n
+    kmax = math.sqrt(3) * math.pi / cell * 1.0001
+    nk = 40
+    table = 1.0 + 0.3 * np.sin(np.linspace(0, 3, nk)).astype(np.float32)
+    rho = synthetic.gaussian_field(80, (n, n, n), 0.5) + 1.0
+    gbar = synthetic.gaussian_field(81, (2, n, n, n))
+    pm = hrt.PM(n, box)
+    rho_hat = torch.empty(n, n, n // 2 + 1, dtype=torch.complex64, device="cuda")
+    pm.forward_fft(torch.tensor(rho, dtype=torch.float32, device="cuda").reshape(-1), rho_hat)
+    gh = torch.empty(2, n, n, n // 2 + 1, dtype=torch.complex64, device="cuda")
+    gb = torch.tensor(gbar, dtype=torch.float32, device="cuda").reshape(2, -1)
+    pm.forward_fft(gb[0], gh[0])
+    pm.forward_fft(gb[1], gh[1])
+    tt = torch.tensor(table, device="cuda")
+    f = hrt.make_filter(4.0, cell, tt, kmax)
+    tb = torch.zeros(nk, device="cuda")
+    hrt.hrt_kspace_table_adjoint(gh, 2, rho_hat, n, box, pref, f, tb)
+    tab = torch.tensor(table, dtype=torch.float64, requires_grad=True)
+
+    def g_of_k(k):
+        t = k / kmax * (nk - 1)
+        i = torch.clamp(t.floor().long(), 0, nk - 2)
+        w = t - i
+        v = tab[i] * (1 - w) + tab[i + 1] * w
+        return torch.where(t >= nk - 1, torch.ones_like(v), v)
+
+    grads = opm.poisson_gradient(torch.tensor(rho), box, pref, 4.0, cell, g_of_k)
+    sum((grads[j] * torch.tensor(gbar[j])).sum() for j in range(2)).backward()
+    want = tab.grad.numpy()
+    assert np.abs(tb.cpu().double().numpy() - want).max() <= 1e-4 * np.abs(want).max()
+    pm.close()
+
+
+def test_trained_correction_beats_plain_kernel_on_held_out_seeds(hrt):
+    from dataclasses import replace
+
+    from paper_2405_12913_gb300 import learned
+    S = replace(learned.PairSpec(), n_side=64, n_coarse=64, n_fine=256, box=128.0, n_forward=12, n_reverse=6,
+                a_min=0.6, n_pix=256, fov_deg=4.0, nbins=12, ell_cut=6.0e3)
+    mlp, res = learned.train(S, train_seeds=range(4), test_seeds=range(100, 102), iters=40, lr=3e-3, log=lambda s: None)
+    assert res["history"][-1] < 0.5 * res["history"][0]
+    assert res["learned_mean_rel_err"] < 0.7 * res["plain_mean_rel_err"], res
