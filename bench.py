@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--workload", default="cosmo_512p_1024m_2048r")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-learned", action="store_true",
+                   help="skip the learned-correction comparison (coarse learned vs coarse plain vs fine plain)")
     return p.parse_args()
 
 
@@ -319,6 +321,32 @@ def run_gpu(args, W, world, rank, local):
     return line
 
 
+# ----------------------------------------------------------------------------------------------- learned form
+LEARNED_PARAMS = os.path.join(ROOT, "paper_2405_12913_gb300", "data", "ray_correction_256m.npy")
+
+
+def learned_comparison(seed=100):
+    """The learned ray-force correction against the plain kernel on a held-out seed of the coarse/fine pair
+    workload (256^3 particles, 256^3 vs 1024^3 mesh, box 256 Mpc/h, 4096^2 rays over 3.5 deg, source z = 1):
+    reverse co-evolution sim-steps/s of each form (CUDA events) and the kappa P(ell) error of both coarse
+    forms against the fine run, with the committed trained parameters."""
+    import numpy as np
+    import torch
+    from dataclasses import replace
+    from paper_2405_12913_gb300 import learned
+    if not os.path.exists(LEARNED_PARAMS):
+        return {"unavailable": "no trained parameters committed"}
+    w = torch.tensor(np.load(LEARNED_PARAMS), dtype=torch.float32, device="cuda")
+    S = replace(learned.PairSpec(), n_pix=4096)
+    r = learned.compare(S, w, [seed], log=lambda m: None)
+    rates = r["sim_steps_per_s"]
+    return {"workload": "pair_256p_256m_vs_1024m_4096r", "seed": seed, "bins_ell_le": S.ell_cut,
+            "sim_steps_per_s": rates,
+            "learned_over_fine_speed": rates["coarse_learned"] / rates["fine_plain"],
+            "plain_mean_rel_err": r["plain_mean_rel_err"], "plain_max_rel_err": r["plain_max_rel_err"],
+            "learned_mean_rel_err": r["learned_mean_rel_err"], "learned_max_rel_err": r["learned_max_rel_err"]}
+
+
 # ----------------------------------------------------------------------------------------------- oracle (CPU)
 def oracle_sample(W, n_side, n_mesh, n_pix, seed=7):
     """Times one reverse sim-step of the FP64 oracle on a scaled copy of the workload (same box and field of
@@ -406,6 +434,8 @@ def main():
     line = run_gpu(args, W, world, rank, local)
     if line is None:
         return 0
+    if world == 1 and not args.no_learned:
+        line["learned"] = learned_comparison()
     if world == 1 and not args.no_cpu_baseline:
         full, desc, threads = oracle_sample(W, 128, 256, 512)
         line["cpu_baseline"] = {"value": 1.0 / full, "unit": UNIT, "cores": threads, "kind": "oracle",

@@ -72,7 +72,7 @@ hrt_status hrt_cosmo_power_amplitude(double omega_m, double h, double n_s, doubl
  * ---------------------------------------------------------------------------------------------------- */
 
 /* CIC (cloud-in-cell) mass assignment, the density step of the PM force ("the most computationally
- * expensive operation", Sec. 4.1).  Overwrites rho[n^3] with rho/rho_mean = 1 + delta: each of the
+ * expensive operation", Sec. 5.1).  Overwrites rho[n^3] with rho/rho_mean = 1 + delta: each of the
  * n_side^3 particles carries n^3 / n_side^3 and gives weight (1-f) to node floor(u), f to floor(u)+1 per
  * axis, u = (q + disp) / cell, periodic.  disp is [3][n_side^3].  Accumulation order is not fixed (float32
  * atomics), so results are reproducible to rounding only.  n_side >= 1, n % n_side == 0, n >= 2. */
@@ -92,7 +92,7 @@ hrt_status hrt_particle_kick_drift(const float* grad, int64_t n, double box, int
 hrt_status hrt_particle_kick_drift_deposit(const float* grad, int64_t n, double box, int64_t n_side, float* disp,
                                            float* mom, double kick, double drift, float* rho, void* stream);
 
-/* k-space filter of the gradient fields (Sec. 4.2 kick operator taken on the 3D mesh):
+/* k-space filter of the gradient fields (Sec. 5.2 kick operator taken on the 3D mesh):
  *   prod_i sinc(k_i cell/2)^-deconv_p  *  exp(-k^2 smooth^2 / 2)  *  g(|k|)
  * with g the optional learned correction table: g_table[nk] (device, float32) sampled uniformly on
  * |k| in [0, g_kmax], linearly interpolated, 1 beyond g_kmax; NULL means g = 1. */
@@ -104,7 +104,7 @@ typedef struct hrt_filter {
   double g_kmax;        /* |k| of the last entry, h/Mpc                                            */
 } hrt_filter;
 
-/* Fused k-space kernel of the Poisson solve (Sec. 2 Poisson equation, Sec. 4.2 deconvolution):
+/* Fused k-space kernel of the Poisson solve (Sec. 2 Poisson equation, Sec. 5.2 deconvolution):
  * from rho_hat (half spectrum of rho, any k = 0 value) write n_out gradient spectra
  *   out_j = i k_j * (-pref / k^2) * F(k) * rho_hat / n^3,   j = 0..n_out-1 (x, y[, z])
  * with out = 0 at k = 0 and on the j-Nyquist plane, k_i = 2 pi n_i / box, n_i in [-n/2, n/2).  The 1/n^3
@@ -230,7 +230,7 @@ hrt_status hrt_ic_zeldovich(const float* noise, int64_t n_side, double box, cons
  * Adjoints (reverse mode).  Each call is the vector-Jacobian product of the forward call of the same name:
  * given cotangents of the outputs it returns (or accumulates, where stated) the cotangents of the inputs and
  * of the host coefficients, so that a caller can run the forward path backwards with checkpointing.  Paper:
- * the adjoint method is named as future work (Sec. 6); these are the transposes of the operations above.
+ * the adjoint method is named as future work (Sec. 7); these are the transposes of the operations above.
  * Coefficient cotangents are FP64 device accumulators that the calls add to.
  * ---------------------------------------------------------------------------------------------------- */
 
@@ -289,7 +289,7 @@ hrt_status hrt_ic_zeldovich_adjoint(const float* noise, int64_t n_side, double b
 hrt_status hrt_dot(const float* a, const float* b, int64_t m, double* out_host, void* stream);
 
 /* ------------------------------------------------------------------------------------------------------
- * Learned force correction (the analogue of the force-sharpening factor g of Sec. 5.2, k/k^2 -> (k/k^2) g,
+ * Learned force correction (the analogue of the force-sharpening factor g of Sec. 6.2, k/k^2 -> (k/k^2) g,
  * here applied to the ray gradient fields of a coarse mesh): g = 1 + MLP(|k| cell, a, ln N_mesh), a 3-64-64-
  * 64-1 perceptron with SiLU activations.  Parameters: HRT_MLP_PARAMS floats in the order W1 [64][16] (input
  * columns 3..15 zero), b1 [64], W2 [64][64], b2 [64], W3 [64][64], b3 [64], W4 [64], b4 [1]; a BF16 copy of the
@@ -371,6 +371,15 @@ hrt_status hrt_init_rays(hrt_ctx* ctx, const double* theta0, int64_t n_rays);
  * source >= 0); then particles kick from their momentum time to (a + a_next)/2 and drift to a_next; then
  * the PM force is recomputed at a_next.  Forward steps (a_next > a) move particles only. */
 hrt_status hrt_step(hrt_ctx* ctx, double a_next, int32_t source);
+
+/* Learned correction of the ray force (the analogue of the trained force-sharpening factor g of Sec. 6.2):
+ * params (device float32, HRT_MLP_PARAMS values in the hrt_mlp_forward layout) are copied into the
+ * context, rounded to BF16, and from then on every force evaluation at scale factor a first evaluates
+ * g(|k|) = hrt_mlp_forward((|k| cell, a, ln n_mesh)) on 512 points over |k| in [0, 1.0001 sqrt(3) pi / cell]
+ * and multiplies the Green's function of the ray fields by it (linear interpolation in |k|).  The
+ * particle force stays plain.  Needs ray_fields == 2 (HRT_ERR_STATE otherwise).  params == NULL
+ * restores the plain ray kernel.  Takes effect at the next force evaluation (the next hrt_step). */
+hrt_status hrt_set_ray_correction(hrt_ctx* ctx, const float* params);
 
 /* Kick the momenta from their time to the current a with the current force (synchronise). */
 hrt_status hrt_sync_particles(hrt_ctx* ctx);

@@ -6,7 +6,7 @@ Used to pin the oracle's PM force and its point-mass lensing against sums that i
     neutralising background (what an FFT Poisson solve with the k = 0 mode removed computes),
       grad phi / (G M) = sum_n (r_n / |r_n|^3) [erfc(al |r_n|) + 2 al |r_n| exp(-al^2 |r_n|^2) / sqrt(pi)]
                        + (4 pi / L^3) sum_{k != 0} (k / k^2) exp(-k^2 / (4 al^2)) sin(k . r),   r_n = r - n L;
-  * 2D: the lensing sum of the periodic point-mass images of Appendix C (Eq. "pointmass_periodic"),
+  * 2D: the lensing sum of the periodic point-mass images of Appendix D (Eq. "pointmass_periodic"),
     sum_m (b - m) / |b - m|^2, for the zero-mean periodic lattice (the projection of the 3D problem above
     over one period along the line of sight),
       D(b) = sum_m (b_m / |b_m|^2) exp(-al^2 |b_m|^2) + (2 pi / L^2) sum_{k != 0} (k / k^2) exp(-k^2/(4 al^2)) sin(k . b).

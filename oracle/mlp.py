@@ -2,7 +2,7 @@
 
 x = (|k| cell, a, ln N_mesh); three hidden layers of 64 SiLU units (SiLU(z) = z / (1 + e^-z)) and a linear
 output y; g = 1 + y multiplies the Green's function of the ray fields, the analogue of the force-sharpening
-factor of Sec. 5.2.  Parameters are packed as W1 [64][16] (input columns 3..15 unused), b1 [64], W2 [64][64],
+factor of Sec. 6.2.  Parameters are packed as W1 [64][16] (input columns 3..15 unused), b1 [64], W2 [64][64],
 b2 [64], W3 [64][64], b3 [64], W4 [64], b4.  ``round_weights`` / ``round_acts`` reproduce the arithmetic of the
 tensor-core forward: weights W1..W4 and the inputs of layers 1-3 rounded to bfloat16, everything else exact.
 """

@@ -1,6 +1,6 @@
 """Particle-mesh gravity in FP64 on the CPU (test infrastructure only).
 
-Restates, step by step and without blocking or fusion, the PM force of Sec. 4.1 of arXiv 2405.12913 ("the
+Restates, step by step and without blocking or fusion, the PM force of Sec. 5.1 of arXiv 2405.12913 ("the
 most computationally expensive operation ... calculate grad phi via the FFT") and the particle leapfrog that
 ``nbody_reverse_step`` of Alg. 1 stands for:
 
@@ -11,7 +11,7 @@ most computationally expensive operation ... calculate grad phi via the FFT") an
   * Poisson (Sec. 2):  lap phi = pref * delta, so phi_k = -pref * delta_k / k^2 with phi_0 = 0;
     pref = (3/2) Omega_m / a in the expanding case and 4 pi G rho_mean in the static point-mass case;
   * gradient: (d_j phi)_k = i k_j phi_k * prod_i sinc(k_i cell / 2)^-p * exp(-k^2 sigma^2 / 2), the CIC
-    deconvolution and the Gaussian smoothing of the kick operator of Sec. 4.2 taken on the 3D mesh (power
+    deconvolution and the Gaussian smoothing of the kick operator of Sec. 5.2 taken on the 3D mesh (power
     p per axis, smoothing length sigma in comoving units, the decaying sign of the Gaussian); the signed
     frequency n_i lies in [-N/2, N/2), k_i = 2 pi n_i / L, and the derivative factor i k_j is set to 0 on
     the j-Nyquist plane so that the gradient is real;

@@ -1,6 +1,6 @@
 """Convergence power spectrum of a square flat-sky map in FP64 (test infrastructure only).
 
-The map statistic used to compare convergence maps (Sec. 5.2 of arXiv 2405.12913 compares C_ell):
+The map statistic used to compare convergence maps (Sec. 6.2 of arXiv 2405.12913 compares C_ell):
   kappa_tilde(n) = FFT2(kappa)(n) * dtheta^2,  P(ell) = <|kappa_tilde|^2>_bin / Theta^2,  Theta = M dtheta,
   ell(n) = 2 pi |n| / Theta for the signed integer frequency n = (n_x, n_y) of the full M x M transform;
   bins are log-spaced between ell_min and ell_max, left-closed; the bin of a mode is

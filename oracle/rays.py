@@ -4,7 +4,7 @@ Restates Sec. 3 and Sec. 4 of arXiv 2405.12913 for a bundle of independent rays:
 
   * state per ray: angle theta (2), conjugate momentum eta (2), distortion matrix A = d theta / d theta_0 and
     the helper B = d eta / d theta_0 (2x2 each); initially theta = theta_0, eta = 0, A = I, B = 0 (Sec. 2 and
-    Sec. 5, Eq. "B");
+    Sec. 4, Eq. "B");
   * flat sky, line of sight along +z from the observer O: the 3D point at radial distance chi is
     X(theta, chi) = O + (r theta_x, r theta_y, chi), r = chi, wrapped into the periodic box;
   * one step over the shell [chi_n, chi_{n+1}] with midpoint chi_{n+1/2} is the KDK of Eqs. "symp_1..3"

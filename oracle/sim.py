@@ -130,7 +130,7 @@ def run_reverse(part: Particles, grads, a_grid, box: float, n_mesh: int, c: Cosm
 
 
 # ----------------------------------------------------------------------------------------------------------
-# Static point-mass lens (Sec. 5.1): flat space, a = 1, no growth correction.
+# Static point-mass lens (Sec. 6.1): flat space, a = 1, no growth correction.
 # ----------------------------------------------------------------------------------------------------------
 
 @dataclass

@@ -1,6 +1,6 @@
 """Reverse-mode differentiation of the HRT co-evolution with the hand-written adjoint kernels of libhrt.
 
-The paper names an adjoint method for HRT as future work (Sec. 6); this module provides it for the GB300 path:
+The paper names an adjoint method for HRT as future work (Sec. 7); this module provides it for the GB300 path:
 ``HRTKappa`` (a ``torch.autograd.Function``) runs the whole simulation forward -- Zel'dovich ICs from white noise,
 the forward leapfrog to a = 1, the synchronising kick, and the reverse co-evolution of particles and rays of
 Alg. 1 -- and returns the convergence maps of the source planes; its backward pass walks the steps in reverse,

@@ -14,7 +14,7 @@ G_NEWTON = 4.30091727e-13  # (Mpc/h) (100 km/s)^2 / (Msun/h)
 
 @dataclass(frozen=True)
 class PointMassWorkload:
-    """Static point-mass lens (Sec. 5.1 geometry scaled to a 64^3 box): one particle at the box centre on a
+    """Static point-mass lens (Sec. 6.1 geometry scaled to a 64^3 box): one particle at the box centre on a
     mesh node, observer 1 Gpc/h in front of it, 64 KDK steps across the lens box, then a free drift to the
     source plane; rays on a polar grid with impact parameters log-uniform in 0.1..20 mesh cells."""
     name: str = "point_mass_64"

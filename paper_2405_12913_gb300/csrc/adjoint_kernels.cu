@@ -56,15 +56,6 @@ __device__ __forceinline__ float dw(int k, int axis, float fx, float fy, float f
   const float wx = (k & 4) ? fx : 1.f - fx, wy = (k & 2) ? fy : 1.f - fy, wz = (k & 1) ? fz : 1.f - fz;
   return axis == 0 ? sx * wy * wz : (axis == 1 ? wx * sy * wz : wx * wy * sz);
 }
-// mixed second derivative d^2 w / d f_a d f_b (a != b); zero for a == b
-__device__ __forceinline__ float ddw(int k, int a, int b, float fx, float fy, float fz) {
-  if (a == b) return 0.f;
-  const float s[3] = {(k & 4) ? 1.f : -1.f, (k & 2) ? 1.f : -1.f, (k & 1) ? 1.f : -1.f};
-  const float w[3] = {(k & 4) ? fx : 1.f - fx, (k & 2) ? fy : 1.f - fy, (k & 1) ? fz : 1.f - fz};
-  const int c = 3 - a - b;
-  return s[a] * s[b] * w[c];
-}
-
 __device__ __forceinline__ void block_add_double(double v, double* dst) {
   // warp reduction, then one atomic per warp
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -276,14 +267,58 @@ struct RayNodeSample {
   float S[2][3][3];  // mixed second derivatives d^2 v_a / d f_b d f_c
 };
 
-__device__ __forceinline__ void node_cell(const RayStepParams& p, int j, int bx, float fbx, int by, float fby,
-                                          float tx, float ty, Cell& c) {
+// Mesh columns of node j: row offsets of the four (x, y) corners (ix,iy), (ix,jy), (jx,iy), (jx,jy), the two z
+// planes and the fractional position (the same arithmetic as the forward kernel).
+struct NodeCols {
+  int64_t r[4];
+  int iz, jz;
+  float fx, fy, fz;
+};
+
+__device__ __forceinline__ void node_cols(const RayStepParams& p, int j, int bx, float fbx, int by, float fby,
+                                          float tx, float ty, NodeCols& c) {
   const int n = p.n;
   int ix, iy;
-  float fx, fy;
-  axis_split(bx, fbx + p.dr[j] * tx, n, ix, fx);
-  axis_split(by, fby + p.dr[j] * ty, n, iy, fy);
-  make_cell(ix, iy, p.kz[j], fx, fy, p.fz[j], n, c);
+  axis_split(bx, fbx + p.dr[j] * tx, n, ix, c.fx);
+  axis_split(by, fby + p.dr[j] * ty, n, iy, c.fy);
+  c.iz = p.kz[j];
+  c.jz = nxt(c.iz, n);
+  c.fz = p.fz[j];
+  const int jx = nxt(ix, n), jy = nxt(iy, n);
+  const int64_t nn = n;
+  c.r[0] = (ix * nn + iy) * nn;
+  c.r[1] = (ix * nn + jy) * nn;
+  c.r[2] = (jx * nn + iy) * nn;
+  c.r[3] = (jx * nn + jy) * nn;
+}
+
+// Trilinear interpolant of one field at a node and its derivatives in the fractional position: value v,
+// gradient (dx, dy, dz) and the mixed second derivatives (the pure ones vanish for a trilinear interpolant),
+// by successive linear interpolation in z, y, x.
+struct NodeField {
+  float v, dx, dy, dz, sxy, sxz, syz;
+};
+
+__device__ __forceinline__ NodeField node_field(const float* __restrict__ f, const NodeCols& c) {
+  float lo[4], dzc[4], e[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    lo[q] = __ldg(f + c.r[q] + c.iz);
+    dzc[q] = __ldg(f + c.r[q] + c.jz) - lo[q];
+    e[q] = lo[q] + c.fz * dzc[q];
+  }
+  NodeField o;
+  const float h0 = e[1] - e[0], h1 = e[3] - e[2];  // d/dfy at x = 0, 1
+  const float g0 = e[0] + c.fy * h0, g1 = e[2] + c.fy * h1;
+  o.v = g0 + c.fx * (g1 - g0);
+  o.dx = g1 - g0;
+  o.dy = h0 + c.fx * (h1 - h0);
+  o.sxy = h1 - h0;
+  const float z0 = dzc[0] + c.fy * (dzc[1] - dzc[0]), z1 = dzc[2] + c.fy * (dzc[3] - dzc[2]);
+  o.dz = z0 + c.fx * (z1 - z0);
+  o.sxz = z1 - z0;
+  o.syz = (dzc[1] - dzc[0]) + c.fx * ((dzc[3] - dzc[2]) - (dzc[1] - dzc[0]));
+  return o;
 }
 
 __device__ __forceinline__ void base_pos(double obs, double r_ref, double theta, double cell, int n, int& i0,
@@ -309,19 +344,14 @@ __device__ void half_forward(const RayStepParams& p, int j0, int j1, double thx,
   const float tx = static_cast<float>(thx), ty = static_cast<float>(thy);
   const float* f[2] = {gx, gy};
   for (int j = j0; j < j1; ++j) {
-    Cell c;
-    node_cell(p, j, bx, fbx, by, fby, tx, ty, c);
+    NodeCols c;
+    node_cols(p, j, bx, fbx, by, fby, tx, ty, c);
+#pragma unroll
     for (int a = 0; a < 2; ++a) {
-      float v = 0.f, dx = 0.f, dy = 0.f;
-      for (int k = 0; k < 8; ++k) {
-        const float val = __ldg(f[a] + c.idx[k]);
-        v += wgt(k, c.fx, c.fy, c.fz) * val;
-        dx += dw(k, 0, c.fx, c.fy, c.fz) * val;
-        dy += dw(k, 1, c.fx, c.fy, c.fz) * val;
-      }
-      K[a] += p.cw[j] * v;
-      J[a][0] += p.cwr[j] * dx;
-      J[a][1] += p.cwr[j] * dy;
+      const NodeField o = node_field(f[a], c);
+      K[a] += p.cw[j] * o.v;
+      J[a][0] += p.cwr[j] * o.dx;
+      J[a][1] += p.cwr[j] * o.dy;
     }
   }
 }
@@ -346,51 +376,37 @@ __device__ void half_backward(const RayStepParams& p, int j0, int j1, double thx
   for (int j = j0; j < j1; ++j) {
     float cwb = 0.f, cwrb = 0.f, chib = 0.f;
     if (active) {
-      Cell c;
-      node_cell(p, j, bx, fbx, by, fby, tx, ty, c);
+      NodeCols c;
+      node_cols(p, j, bx, fbx, by, fby, tx, ty, c);
       const float cw = p.cw[j], cwr = p.cwr[j];
-      float v[2], D[2][3], S[2][3][3];
+      float fbar_x = 0.f, fbar_y = 0.f, fbar_z = 0.f;
+#pragma unroll
       for (int a = 0; a < 2; ++a) {
-        v[a] = 0.f;
-        for (int b = 0; b < 3; ++b) {
-          D[a][b] = 0.f;
-          for (int e = 0; e < 3; ++e) S[a][b][e] = 0.f;
+        const NodeField o = node_field(f[a], c);
+        // K_a = cw v_a and J_ab = cwr d_b v_a (b = x, y): cotangent weights of v, dx v, dy v
+        const float al = cw * Kb[a], bex = cwr * Jb[a][0], bey = cwr * Jb[a][1];
+        // field cotangents: w_k = WX WY WZ, d w_k / d fx = SX WY WZ, ... -> per (x, y) corner, times WZ
+        const float ux = 1.f - c.fx, uy = 1.f - c.fy;
+        const float q[4] = {al * ux * uy - bex * uy - bey * ux, al * ux * c.fy - bex * c.fy + bey * ux,
+                            al * c.fx * uy + bex * uy - bey * c.fx, al * c.fx * c.fy + bex * c.fy + bey * c.fx};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float t0 = (1.f - c.fz) * q[k], t1 = c.fz * q[k];
+          if (t0 != 0.f) atomicAdd(fb[a] + c.r[k] + c.iz, t0);
+          if (t1 != 0.f) atomicAdd(fb[a] + c.r[k] + c.jz, t1);
         }
-        for (int k = 0; k < 8; ++k) {
-          const float val = __ldg(f[a] + c.idx[k]);
-          v[a] += wgt(k, c.fx, c.fy, c.fz) * val;
-          for (int b = 0; b < 3; ++b) {
-            D[a][b] += dw(k, b, c.fx, c.fy, c.fz) * val;
-            for (int e = 0; e < 3; ++e) S[a][b][e] += ddw(k, b, e, c.fx, c.fy, c.fz) * val;
-          }
-        }
-      }
-      // field cotangents: K_a = cw v_a, J_ab = cwr D_ab (b = x, y)
-      for (int k = 0; k < 8; ++k) {
-        const float w = wgt(k, c.fx, c.fy, c.fz);
-        const float dwx = dw(k, 0, c.fx, c.fy, c.fz), dwy = dw(k, 1, c.fx, c.fy, c.fz);
-        for (int a = 0; a < 2; ++a) {
-          const float t = cw * Kb[a] * w + cwr * (Jb[a][0] * dwx + Jb[a][1] * dwy);
-          if (t != 0.f) atomicAdd(fb[a] + c.idx[k], t);
-        }
-      }
-      // cotangent of the fractional position f_e (e = x, y, z)
-      float fbar[3];
-      for (int e = 0; e < 3; ++e) {
-        float s = 0.f;
-        for (int a = 0; a < 2; ++a) {
-          s += cw * Kb[a] * D[a][e];
-          s += cwr * (Jb[a][0] * S[a][0][e] + Jb[a][1] * S[a][1][e]);
-        }
-        fbar[e] = s;
+        // cotangent of the fractional position (the mixed second derivatives couple the J terms)
+        fbar_x += al * o.dx + bey * o.sxy;
+        fbar_y += al * o.dy + bex * o.sxy;
+        fbar_z += al * o.dz + bex * o.sxz + bey * o.syz;
+        cwb += Kb[a] * o.v;
+        cwrb += Jb[a][0] * o.dx + Jb[a][1] * o.dy;
       }
       // f_x = (O_x + chi_j theta_x) / cell - cell index: d f_x / d theta_x = chi_j / cell, d f / d chi_j = theta/cell
       const float r_over_cell = static_cast<float>(ref_r / p.cell) + p.dr[j];
-      thb[0] += fbar[0] * r_over_cell;
-      thb[1] += fbar[1] * r_over_cell;
-      chib = (fbar[0] * tx + fbar[1] * ty + fbar[2]) * inv_cell;
-      cwb = Kb[0] * v[0] + Kb[1] * v[1];
-      cwrb = Jb[0][0] * D[0][0] + Jb[0][1] * D[0][1] + Jb[1][0] * D[1][0] + Jb[1][1] * D[1][1];
+      thb[0] += fbar_x * r_over_cell;
+      thb[1] += fbar_y * r_over_cell;
+      chib = (fbar_x * tx + fbar_y * ty + fbar_z) * inv_cell;
     }
     // block reduction of the node cotangents into shared memory
     for (int o = 16; o > 0; o >>= 1) {
@@ -416,7 +432,15 @@ __global__ void __launch_bounds__(128) ray_step_adjoint_kernel(
   const int n_nodes = p.n1 + p.n2;
   for (int i = threadIdx.x; i < 3 * n_nodes; i += blockDim.x) sh[i] = 0.f;
   __syncthreads();
-  const int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  int64_t r;
+  if (p.tile_w > 0) {
+    // 16 x 8 pixel tiles, as in the forward kernel (neighbouring rays share mesh cells and cache lines)
+    const unsigned tiles_x = static_cast<unsigned>(p.tile_w) >> 4;
+    const unsigned tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
+    r = (ty * 8 + (threadIdx.x >> 4)) * static_cast<int64_t>(p.tile_w) + tx * 16 + (threadIdx.x & 15);
+  } else {
+    r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  }
   const bool active = r < nr;
   double db = 0.0;
   double2 th0 = active ? theta[r] : make_double2(0.0, 0.0);

@@ -198,6 +198,16 @@ struct hrt_ctx {
   int64_t maps_rays = 0;
   bool profiling = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> phases[8];
+  // second stream for the ray step, which overlaps the particle update of the same step (both only read
+  // the force fields); ev_fields: fields ready, ev_rays: ray step done (the next C2R waits for it)
+  cudaStream_t ray_stream = nullptr;
+  cudaEvent_t ev_fields = nullptr, ev_rays = nullptr;
+  bool rays_pending = false;
+  // learned ray-force correction (NULL: plain)
+  float* corr_w = nullptr;
+  void* corr_wb = nullptr;
+  float* corr_x = nullptr;
+  float* corr_table = nullptr;
 };
 
 namespace hrt {
@@ -392,8 +402,11 @@ static KspaceCallbackInfo callback_info(const hrt_pm* pm, const float* tab, cons
   return ci;
 }
 
+// before_fields (optional): an event the stream waits for before the C2Rs overwrite grad / ray_grad (work on
+// another stream that still reads the previous fields).
 static hrt_status pm_solve(hrt_pm* pm, float* rho, double pref, const hrt_filter* f, float* grad,
-                           const hrt_filter* fr, float* ray_grad, hrt_ctx* prof = nullptr) {
+                           const hrt_filter* fr, float* ray_grad, hrt_ctx* prof = nullptr,
+                           cudaEvent_t before_fields = nullptr) {
   static hrt_ctx no_profiling;
   hrt_ctx* pc = prof ? prof : &no_profiling;
   HRT_TRY(check_filter(f));
@@ -413,6 +426,7 @@ static hrt_status pm_solve(hrt_pm* pm, float* rho, double pref, const hrt_filter
     HRT_TRY(launch_set_callback_info(pm->cb_info, callback_info(pm, pm->tab_a, *f, pref, 3), pm->stream));
     if (rays) HRT_TRY(launch_set_callback_info(pm->cb_info + 1, callback_info(pm, pm->tab_b, *fr, pref, pm->n_ray),
                                                pm->stream));
+    if (before_fields) HRT_CUDA(cudaStreamWaitEvent(pm->stream, before_fields, 0));
     PhaseScope ps(pc, 5);
     HRT_CUFFT(cufftExecC2R(pm->c2r_cb3, reinterpret_cast<cufftComplex*>(gh), grad));
     if (rays) HRT_CUFFT(cufftExecC2R(pm->c2r_cb2, reinterpret_cast<cufftComplex*>(gh + 3 * sb), ray_grad));
@@ -423,6 +437,7 @@ static hrt_status pm_solve(hrt_pm* pm, float* rho, double pref, const hrt_filter
     HRT_TRY(launch_kspace(pm->rho_hat, pm->n, pm->box, pref, pm->tab_a, f, 3, gh, rays ? pm->tab_b : nullptr, fr,
                           rays ? pm->n_ray : 0, gh + 3 * sb, pm->stream));
   }
+  if (before_fields) HRT_CUDA(cudaStreamWaitEvent(pm->stream, before_fields, 0));
   PhaseScope ps(pc, 5);
   for (int j = 0; j < 3; ++j)
     HRT_CUFFT(cufftExecC2R(pm->c2r, reinterpret_cast<cufftComplex*>(gh + j * sb), grad + j * mb));
@@ -460,11 +475,24 @@ static double ctx_pref(const hrt_ctx* ctx, double a) {
   return ctx->cfg.static_mode ? ctx->cfg.static_pref : 1.5 * ctx->cfg.cosmo.omega_m / a;
 }
 
-// Gradient fields at ctx->a from the density already deposited in ctx->rho.
+// Gradient fields at ctx->a from the density already deposited in ctx->rho (with the learned ray table
+// evaluated at ctx->a first when a correction is set).
 static hrt_status ctx_solve(hrt_ctx* ctx) {
   const hrt_config& c = ctx->cfg;
   hrt_filter f = ctx_filter(c, false), fr = ctx_filter(c, true);
-  return pm_solve(ctx->pm, ctx->rho, ctx_pref(ctx, ctx->a), &f, ctx->grad, &fr, ctx->ray_grad, ctx);
+  if (ctx->corr_w) {
+    const double cell = c.box / c.n_mesh;
+    HRT_TRY(launch_correction_inputs(ctx->corr_x, kCorrectionRows, kCorrectionKmaxCell / (kCorrectionRows - 1),
+                                     ctx->a, std::log(static_cast<double>(c.n_mesh)), ctx->stream));
+    HRT_TRY(launch_mlp_forward(ctx->corr_x, kCorrectionRows, ctx->corr_wb, ctx->corr_w, ctx->corr_table,
+                               ctx->stream));
+    fr.g_table = ctx->corr_table;
+    fr.g_nk = kCorrectionRows;
+    fr.g_kmax = kCorrectionKmaxCell / cell;
+  }
+  cudaEvent_t wait = ctx->rays_pending ? ctx->ev_rays : nullptr;
+  ctx->rays_pending = false;
+  return pm_solve(ctx->pm, ctx->rho, ctx_pref(ctx, ctx->a), &f, ctx->grad, &fr, ctx->ray_grad, ctx, wait);
 }
 
 // CIC deposit of the current particles, then the gradient fields.
@@ -489,7 +517,8 @@ static hrt_ray_geom ctx_geom(const hrt_config& c) {
   return g;
 }
 
-static hrt_status ctx_ray_step(hrt_ctx* ctx, double chi_from, double chi_to, double a_ref, int32_t source) {
+static hrt_status ctx_ray_step(hrt_ctx* ctx, double chi_from, double chi_to, double a_ref, int32_t source,
+                               cudaStream_t stream) {
   const hrt_config& c = ctx->cfg;
   if (source >= c.n_sources) return fail(HRT_ERR_INVALID_ARG, "source %d out of range", source);
   static thread_local RayStepParams p;
@@ -502,7 +531,7 @@ static hrt_status ctx_ray_step(hrt_ctx* ctx, double chi_from, double chi_to, dou
   const int64_t m = c.n_mesh * c.n_mesh * c.n_mesh;
   const float* gx = ctx->ray_grad ? ctx->ray_grad : ctx->grad;
   float* maps = source >= 0 ? ctx->maps + static_cast<int64_t>(source) * 4 * ctx->rays.n_rays : nullptr;
-  return launch_ray_step(ctx->rays, gx, gx + m, p, maps, ctx->stream);
+  return launch_ray_step(ctx->rays, gx, gx + m, p, maps, stream);
 }
 
 }  // namespace hrt
@@ -807,6 +836,7 @@ hrt_status hrt_ray_step_adjoint(const hrt_rays* rays, const float* grad_x, const
   if (bar->n_rays != rays->n_rays) return fail(HRT_ERR_INVALID_ARG, "ray counts differ");
   static thread_local RayStepParams p;
   HRT_TRY(build_ray_params(*geom, chi_from, chi_to, a_ref, omega_m, p));
+  set_tiles(*geom, rays->n_rays, p);
   return launch_ray_step_adjoint(*rays, grad_x, grad_y, p, *bar, gx_bar, gy_bar, node_bar, drift_bar, as_stream(stream));
 }
 
@@ -1045,6 +1075,7 @@ hrt_status hrt_workspace_bytes(const hrt_config* cfg, int64_t n_rays, size_t* by
 hrt_status hrt_destroy(hrt_ctx* ctx) {
   if (!ctx) return HRT_OK;
   cudaStream_t s = ctx->stream;
+  if (ctx->ray_stream) cudaStreamSynchronize(ctx->ray_stream);
   cudaStreamSynchronize(s);
   for (auto& v : ctx->phases)
     for (auto& ev : v) {
@@ -1062,7 +1093,14 @@ hrt_status hrt_destroy(hrt_ctx* ctx) {
   device_free(ctx->rays.A, s);
   device_free(ctx->rays.B, s);
   device_free(ctx->maps, s);
+  device_free(ctx->corr_w, s);
+  device_free(ctx->corr_wb, s);
+  device_free(ctx->corr_x, s);
+  device_free(ctx->corr_table, s);
   cudaStreamSynchronize(s);
+  if (ctx->ev_fields) cudaEventDestroy(ctx->ev_fields);
+  if (ctx->ev_rays) cudaEventDestroy(ctx->ev_rays);
+  if (ctx->ray_stream) cudaStreamDestroy(ctx->ray_stream);
   cudaGetLastError();
   delete ctx;
   return HRT_OK;
@@ -1078,6 +1116,9 @@ hrt_status hrt_create(const hrt_config* cfg, void* stream, hrt_ctx** out) {
   ctx->stream = as_stream(stream);
   const int64_t n = cfg->n_mesh, m = n * n * n, np = cfg->n_side * cfg->n_side * cfg->n_side;
   hrt_status s = hrt_pm_create(n, cfg->box, cfg->ray_fields, stream, &ctx->pm);
+  if (s == HRT_OK) s = cuda_status(cudaStreamCreateWithFlags(&ctx->ray_stream, cudaStreamNonBlocking), "ray stream");
+  if (s == HRT_OK) s = cuda_status(cudaEventCreateWithFlags(&ctx->ev_fields, cudaEventDisableTiming), "event");
+  if (s == HRT_OK) s = cuda_status(cudaEventCreateWithFlags(&ctx->ev_rays, cudaEventDisableTiming), "event");
   if (s == HRT_OK) s = device_alloc(reinterpret_cast<void**>(&ctx->disp), 3 * np * sizeof(float), ctx->stream, "disp");
   if (s == HRT_OK) s = device_alloc(reinterpret_cast<void**>(&ctx->mom), 3 * np * sizeof(float), ctx->stream, "mom");
   if (s == HRT_OK) s = device_alloc(reinterpret_cast<void**>(&ctx->rho), m * sizeof(float), ctx->stream, "rho");
@@ -1157,8 +1198,18 @@ hrt_status hrt_step(hrt_ctx* ctx, double a_next, int32_t source) {
   hrt_status s = HRT_OK;
   PhaseScope whole(ctx, 6);
   if (ctx->rays.n_rays > 0 && a_next < ctx->a) {
-    PhaseScope ps(ctx, 0);
-    s = ctx_ray_step(ctx, c.chi(ctx->a), c.chi(a_next), ctx->a, source);
+    if (ctx->profiling) {
+      // serialised on the context stream so that each phase has its own time
+      PhaseScope ps(ctx, 0);
+      s = ctx_ray_step(ctx, c.chi(ctx->a), c.chi(a_next), ctx->a, source, ctx->stream);
+    } else {
+      // the ray step runs on the ray stream beside the particle update; the next force waits for it
+      s = cuda_status(cudaEventRecord(ctx->ev_fields, ctx->stream), "record fields");
+      if (s == HRT_OK) s = cuda_status(cudaStreamWaitEvent(ctx->ray_stream, ctx->ev_fields, 0), "wait fields");
+      if (s == HRT_OK) s = ctx_ray_step(ctx, c.chi(ctx->a), c.chi(a_next), ctx->a, source, ctx->ray_stream);
+      if (s == HRT_OK) s = cuda_status(cudaEventRecord(ctx->ev_rays, ctx->ray_stream), "record rays");
+      if (s == HRT_OK) ctx->rays_pending = true;
+    }
     if (s != HRT_OK) return ctx_mark(ctx, s);
   }
   const double a_half = 0.5 * (ctx->a + a_next);
@@ -1173,6 +1224,44 @@ hrt_status hrt_step(hrt_ctx* ctx, double a_next, int32_t source) {
   ctx->a = a_next;
   ctx->a_mom = a_half;
   return ctx_mark(ctx, ctx_solve(ctx));
+}
+
+hrt_status hrt_set_ray_correction(hrt_ctx* ctx, const float* params) {
+  HRT_TRY(ctx_guard(ctx));
+  if (ctx->cfg.ray_fields != 2) return fail(HRT_ERR_STATE, "a ray correction needs ray_fields == 2");
+  cudaStream_t st = ctx->stream;
+  if (!params) {
+    device_free(ctx->corr_w, st);
+    device_free(ctx->corr_wb, st);
+    device_free(ctx->corr_x, st);
+    device_free(ctx->corr_table, st);
+    ctx->corr_w = ctx->corr_table = ctx->corr_x = nullptr;
+    ctx->corr_wb = nullptr;
+    return HRT_OK;
+  }
+  if (!ctx->corr_w) {
+    float *w = nullptr, *x = nullptr, *t = nullptr;
+    void* wb = nullptr;
+    hrt_status s = device_alloc(reinterpret_cast<void**>(&w), kMlpParams * sizeof(float), st, "correction");
+    if (s == HRT_OK) s = device_alloc(&wb, kMlpParams * 2, st, "correction bf16");
+    if (s == HRT_OK) s = device_alloc(reinterpret_cast<void**>(&x), 3 * kCorrectionRows * sizeof(float), st, "inputs");
+    if (s == HRT_OK) s = device_alloc(reinterpret_cast<void**>(&t), kCorrectionRows * sizeof(float), st, "table");
+    if (s != HRT_OK) {
+      device_free(w, st);
+      device_free(wb, st);
+      device_free(x, st);
+      device_free(t, st);
+      return s;
+    }
+    ctx->corr_w = w;
+    ctx->corr_wb = wb;
+    ctx->corr_x = x;
+    ctx->corr_table = t;
+  }
+  hrt_status s = cuda_status(cudaMemcpyAsync(ctx->corr_w, params, kMlpParams * sizeof(float),
+                                             cudaMemcpyDeviceToDevice, st), "copy correction");
+  if (s == HRT_OK) s = launch_to_bf16(ctx->corr_w, ctx->corr_wb, st);
+  return ctx_mark(ctx, s);
 }
 
 hrt_status hrt_sync_particles(hrt_ctx* ctx) {
@@ -1191,7 +1280,7 @@ hrt_status hrt_step_static(hrt_ctx* ctx, double chi_from, double chi_to, int32_t
   if (!ctx->cfg.static_mode) return fail(HRT_ERR_STATE, "hrt_step_static needs the static mode");
   if (!ctx->have_particles) return fail(HRT_ERR_STATE, "no lens particles");
   if (ctx->rays.n_rays == 0) return fail(HRT_ERR_STATE, "no rays");
-  return ctx_mark(ctx, ctx_ray_step(ctx, chi_from, chi_to, 0.0, source));
+  return ctx_mark(ctx, ctx_ray_step(ctx, chi_from, chi_to, 0.0, source, ctx->stream));
 }
 
 hrt_status hrt_drift_free(hrt_ctx* ctx, double chi_from, double chi_to) {

@@ -1,5 +1,5 @@
 // Load callback of the batched complex-to-real FFT that turns the density spectrum into the gradient spectra on
-// the fly (the fused k-space step of the Poisson solve, Sec. 2 Poisson equation and Sec. 4.2 deconvolution).
+// the fly (the fused k-space step of the Poisson solve, Sec. 2 Poisson equation and Sec. 5.2 deconvolution).
 //
 // Compiled separately to LTO IR (compute_100, C++ linkage: the form cuFFT's JIT link resolves by name) and linked
 // into cuFFT's own kernels at plan time (cufftXtSetJITCallback).  cuFFT

@@ -181,16 +181,16 @@ __device__ __forceinline__ float learned_g(const KspaceSet& s, float kmag) {
   return __ldg(s.g + i) * (1.f - w) + __ldg(s.g + i + 1) * w;
 }
 
-__device__ __forceinline__ void kspace_element(const float2* __restrict__ rho_hat, int n, float kf, float scale,
-                                               int64_t elems, const KspaceSet& a, const KspaceSet& b, int ix,
-                                               int iy, int iz, int64_t e) {
+// One half-spectrum element: v = rho_hat[e] at integer frequency (ix, iy, iz) -> the gradient spectra of both sets.
+__device__ __forceinline__ void kspace_element(float2 v, int n, float kf, float scale, int64_t elems,
+                                               const KspaceSet& a, const KspaceSet& b, int ix, int iy, int iz,
+                                               int64_t e) {
   const int half = n >> 1;
   const int nx = ix < half ? ix : ix - n;
   const int ny = iy < half ? iy : iy - n;
   const int nz = iz;
   const float kx = kf * nx, ky = kf * ny, kz = kf * nz;
   const float k2 = kx * kx + ky * ky + kz * kz;
-  const float2 v = rho_hat[e];
   const float dx = (nx == -half) ? 0.f : kx;
   const float dy = (ny == -half) ? 0.f : ky;
   const float dz = (nz == half) ? 0.f : kz;
@@ -212,18 +212,34 @@ __device__ __forceinline__ void kspace_element(const float2* __restrict__ rho_ha
   }
 }
 
-// Grid: x over rows (ix, iy) in groups of blockDim.y, y over chunks of blockDim.x along kz in [0, n/2).  The
-// Nyquist column kz = n/2 is done by the thread that holds kz = 0, so no thread of the grid is idle.
+// Grid: x over rows (ix, iy) in groups of blockDim.y; y over chunks of kKspacePer * blockDim.x along kz in
+// [0, n/2).  Each thread loads its kKspacePer elements (strided by blockDim.x, so every load is coalesced)
+// before computing, to keep several loads in flight; the Nyquist column kz = n/2 is done by the thread that
+// holds kz = 0.
+constexpr int kKspacePer = 4;
+
 __global__ void __launch_bounds__(256) kspace_kernel(const float2* __restrict__ rho_hat, int n, int nzc, float kf,
                                                      float scale, int64_t elems, KspaceSet a, KspaceSet b) {
-  const int iz = blockIdx.y * blockDim.x + threadIdx.x;
   const unsigned row = blockIdx.x * blockDim.y + threadIdx.y;
-  if (iz >= nzc - 1 || row >= static_cast<unsigned>(n) * static_cast<unsigned>(n)) return;
+  if (row >= static_cast<unsigned>(n) * static_cast<unsigned>(n)) return;
   const int ix = static_cast<int>(row / static_cast<unsigned>(n));
   const int iy = static_cast<int>(row - static_cast<unsigned>(ix) * n);
-  const int64_t e = static_cast<int64_t>(row) * nzc + iz;
-  kspace_element(rho_hat, n, kf, scale, elems, a, b, ix, iy, iz, e);
-  if (iz == 0) kspace_element(rho_hat, n, kf, scale, elems, a, b, ix, iy, nzc - 1, e + nzc - 1);
+  const int64_t e0 = static_cast<int64_t>(row) * nzc;
+  const int z0 = blockIdx.y * (blockDim.x * kKspacePer) + threadIdx.x;
+  float2 v[kKspacePer];
+#pragma unroll
+  for (int j = 0; j < kKspacePer; ++j) {
+    const int iz = z0 + j * blockDim.x;
+    v[j] = iz < nzc - 1 ? __ldg(rho_hat + e0 + iz) : make_float2(0.f, 0.f);
+  }
+  const bool nyquist = z0 == 0;
+  const float2 vn = nyquist ? __ldg(rho_hat + e0 + nzc - 1) : make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < kKspacePer; ++j) {
+    const int iz = z0 + j * blockDim.x;
+    if (iz < nzc - 1) kspace_element(v[j], n, kf, scale, elems, a, b, ix, iy, iz, e0 + iz);
+  }
+  if (nyquist) kspace_element(vn, n, kf, scale, elems, a, b, ix, iy, nzc - 1, e0 + nzc - 1);
 }
 
 __global__ void set_callback_info_kernel(KspaceCallbackInfo* dst, KspaceCallbackInfo v) { *dst = v; }
@@ -275,7 +291,7 @@ hrt_status launch_kspace(const void* rho_hat, int64_t n, double box, double pref
   KspaceSet b = make_set(tab_b, fb, n_b, out_b);
   dim3 block(64, 4);
   dim3 grid(static_cast<unsigned>((n * n + block.y - 1) / block.y),
-            static_cast<unsigned>((nzc - 1 + block.x - 1) / block.x));
+            static_cast<unsigned>((nzc - 1 + block.x * kKspacePer - 1) / (block.x * kKspacePer)));
   kspace_kernel<<<grid, block, 0, s>>>(static_cast<const float2*>(rho_hat), static_cast<int>(n),
                                        static_cast<int>(nzc), static_cast<float>(2.0 * M_PI / box),
                                        static_cast<float>(scale), elems, a, b);

@@ -1,10 +1,10 @@
 // Learned force correction: a 3 -> 64 -> 64 -> 64 -> 1 multilayer perceptron g(|k| cell, a, ln N_mesh) that
 // multiplies the Green's function of the ray gradient fields (the analogue of the paper's force-sharpening
-// factor k/k^2 -> (k/k^2) g, Sec. 5.2), evaluated once per step on a 1D table of |k|.
+// factor k/k^2 -> (k/k^2) g, Sec. 6.2), evaluated once per step on a 1D table of |k|.
 //
 // Forward: one warp per 16 table rows; BF16 weights and activations, FP32 accumulation on the tensor cores
-// (mma.sync m16n8k16), SiLU hidden activations in FP32, output g = 1 + y.  Backward (training): FP32 kernel
-// per block of rows, weight gradients reduced in shared memory then added to the global FP32 accumulators.
+// (mma.sync m16n8k16), SiLU hidden activations in FP32, output g = 1 + y.  Backward (training): FP32 matrix
+// products on tiles of 32 rows in shared memory, one global atomic per parameter per tile.
 // Adam update of the FP32 master weights, which are also rounded to the BF16 copy used by the forward.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -124,82 +124,141 @@ __global__ void __launch_bounds__(32 * kWarps) mlp_forward_kernel(const float* _
   }
 }
 
-// Backward in FP32 (the BF16-rounded weights, as in the forward): one thread per row recomputes the forward in
-// FP32 from the BF16 weights, back-propagates dL/dg, and adds its weight gradients to block-shared accumulators.
-__global__ void __launch_bounds__(64) mlp_backward_kernel(const float* __restrict__ x, int rows,
-                                                          const __nv_bfloat16* __restrict__ wb,
-                                                          const float* __restrict__ wf,
-                                                          const float* __restrict__ gbar, float* __restrict__ grad) {
-  extern __shared__ float smem[];  // [kParams] weights, [kParams] gradient accumulators
-  float* w = smem;
-  float* acc = smem + kParams;
-  for (int i = threadIdx.x; i < kParams; i += blockDim.x) {
-    const bool is_bias = (i >= kOffB1 && i < kOffW2) || (i >= kOffB2 && i < kOffW3) || (i >= kOffB3 && i < kOffW4) ||
-                         i == kOffB4;
-    w[i] = is_bias ? wf[i] : __bfloat162float(wb[i]);
-    acc[i] = 0.f;
+// Backward in FP32 (the BF16-rounded weights, as in the forward; FP32 activations) on a tile of kBwdRows rows
+// per block, as matrix products in shared memory: the forward is recomputed layer by layer (Z = H W^T + b),
+// then D3 = (gbar W4) o silu'(Z3), dW3 = D3^T H2, D2 = (D3 W3) o silu'(Z2), ... Thread mappings keep every
+// shared access conflict-free: lane = row for the layer products (activation tiles padded to kLd columns, the
+// weight row a warp-uniform broadcast), lane = input column k for the weight gradients.  Each block adds its
+// tile's gradient with one global atomic per parameter.
+constexpr int kBwdRows = 32, kBwdThreads = 256, kLd = kH + 1;
+constexpr int kBwdSmemFloats = kH * 3 + kH + 2 * (kH * kH + kH) + kH + kBwdRows * 4 + 8 * kBwdRows * kLd;
+
+__global__ void __launch_bounds__(kBwdThreads) mlp_backward_kernel(const float* __restrict__ x, int rows,
+                                                                   const __nv_bfloat16* __restrict__ wb,
+                                                                   const float* __restrict__ wf,
+                                                                   const float* __restrict__ gbar,
+                                                                   float* __restrict__ grad) {
+  extern __shared__ float sm[];
+  float* W1 = sm;                 // [64][3]
+  float* B1 = W1 + kH * 3;        // [64]
+  float* W2 = B1 + kH;            // [64][64] (row n = output neuron)
+  float* B2 = W2 + kH * kH;
+  float* W3 = B2 + kH;
+  float* B3 = W3 + kH * kH;
+  float* W4 = B3 + kH;            // [64]
+  float* X = W4 + kH;             // [rows][3]
+  float* GY = X + kBwdRows * 3;   // [rows]
+  float* H1 = GY + kBwdRows;      // [rows][kLd] activations
+  float* H2 = H1 + kBwdRows * kLd;
+  float* H3 = H2 + kBwdRows * kLd;
+  float* S1 = H3 + kBwdRows * kLd;  // silu'(Z)
+  float* S2 = S1 + kBwdRows * kLd;
+  float* S3 = S2 + kBwdRows * kLd;
+  float* D = S3 + kBwdRows * kLd;   // deltas, ping-pong
+  float* E = D + kBwdRows * kLd;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int row0 = blockIdx.x * kBwdRows;
+  for (int i = tid; i < kH * 3; i += kBwdThreads) W1[i] = __bfloat162float(wb[kOffW1 + (i / 3) * kIn + i % 3]);
+  for (int i = tid; i < kH * kH; i += kBwdThreads) {
+    W2[i] = __bfloat162float(wb[kOffW2 + i]);
+    W3[i] = __bfloat162float(wb[kOffW3 + i]);
+  }
+  for (int i = tid; i < kH; i += kBwdThreads) {
+    B1[i] = wf[kOffB1 + i];
+    B2[i] = wf[kOffB2 + i];
+    B3[i] = wf[kOffB3 + i];
+    W4[i] = __bfloat162float(wb[kOffW4 + i]);
+  }
+  for (int i = tid; i < kBwdRows * 3; i += kBwdThreads) {
+    const int r = row0 + i / 3;
+    X[i] = r < rows ? x[static_cast<int64_t>(r) * 3 + i % 3] : 0.f;
+  }
+  for (int i = tid; i < kBwdRows; i += kBwdThreads) GY[i] = row0 + i < rows ? gbar[row0 + i] : 0.f;
+  __syncthreads();
+  // forward recomputation; lane = row, warp -> output neurons n = warp + 8 i
+  for (int i = 0; i < kH / 8; ++i) {
+    const int n = warp + 8 * i;
+    const float z = B1[n] + W1[n * 3] * X[lane * 3] + W1[n * 3 + 1] * X[lane * 3 + 1] + W1[n * 3 + 2] * X[lane * 3 + 2];
+    H1[lane * kLd + n] = silu(z);
+    S1[lane * kLd + n] = silu_grad(z);
   }
   __syncthreads();
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row < rows) {
-    const float gy = gbar[row];
-    if (gy != 0.f) {
-      float in[3] = {x[row * 3], x[row * 3 + 1], x[row * 3 + 2]};
-      float z1[kH], z2[kH], z3[kH], h1[kH], h2[kH], h3[kH];
-      for (int n = 0; n < kH; ++n) {
-        float s = w[kOffB1 + n];
-        for (int k = 0; k < 3; ++k) s += w[kOffW1 + n * kIn + k] * in[k];
-        z1[n] = s;
-        h1[n] = silu(s);
+  for (int i = 0; i < kH / 8; ++i) {
+    const int n = warp + 8 * i;
+    float z = B2[n];
+    for (int k = 0; k < kH; ++k) z += W2[n * kH + k] * H1[lane * kLd + k];
+    H2[lane * kLd + n] = silu(z);
+    S2[lane * kLd + n] = silu_grad(z);
+  }
+  __syncthreads();
+  for (int i = 0; i < kH / 8; ++i) {
+    const int n = warp + 8 * i;
+    float z = B3[n];
+    for (int k = 0; k < kH; ++k) z += W3[n * kH + k] * H2[lane * kLd + k];
+    H3[lane * kLd + n] = silu(z);
+    S3[lane * kLd + n] = silu_grad(z);
+  }
+  __syncthreads();
+  // output layer: dW4, db4 and D3 = gbar W4 o silu'(Z3)
+  if (tid < kH) {
+    float s = 0.f;
+    for (int r = 0; r < kBwdRows; ++r) s += GY[r] * H3[r * kLd + tid];
+    atomicAdd(grad + kOffW4 + tid, s);
+  } else if (tid == kH) {
+    float s = 0.f;
+    for (int r = 0; r < kBwdRows; ++r) s += GY[r];
+    atomicAdd(grad + kOffB4, s);
+  }
+  for (int i = 0; i < kH / 8; ++i) {
+    const int n = warp + 8 * i;
+    D[lane * kLd + n] = GY[lane] * W4[n] * S3[lane * kLd + n];
+  }
+  __syncthreads();
+  // hidden layers 3 and 2: dW = D^T H_in, db = sum_r D, E = (D W) o silu'(Z_in)
+  const float* h_in[2] = {H2, H1};
+  const float* s_in[2] = {S2, S1};
+  const float* w_l[2] = {W3, W2};
+  const int off_w[2] = {kOffW3, kOffW2}, off_b[2] = {kOffB3, kOffB2};
+  for (int l = 0; l < 2; ++l) {
+    const float* hin = h_in[l];
+    {
+      const int k = tid & (kH - 1);
+      for (int i = 0; i < kH / 4; ++i) {
+        const int n = (tid >> 6) + 4 * i;
+        float s = 0.f;
+        for (int r = 0; r < kBwdRows; ++r) s += D[r * kLd + n] * hin[r * kLd + k];
+        atomicAdd(grad + off_w[l] + n * kH + k, s);
       }
-      for (int n = 0; n < kH; ++n) {
-        float s = w[kOffB2 + n];
-        for (int k = 0; k < kH; ++k) s += w[kOffW2 + n * kH + k] * h1[k];
-        z2[n] = s;
-        h2[n] = silu(s);
-      }
-      for (int n = 0; n < kH; ++n) {
-        float s = w[kOffB3 + n];
-        for (int k = 0; k < kH; ++k) s += w[kOffW3 + n * kH + k] * h2[k];
-        z3[n] = s;
-        h3[n] = silu(s);
-      }
-      // output layer
-      atomicAdd(&acc[kOffB4], gy);
-      float d3[kH];
-      for (int k = 0; k < kH; ++k) {
-        atomicAdd(&acc[kOffW4 + k], gy * h3[k]);
-        d3[k] = gy * w[kOffW4 + k] * silu_grad(z3[k]);
-      }
-      float d2[kH];
-      for (int k = 0; k < kH; ++k) d2[k] = 0.f;
-      for (int n = 0; n < kH; ++n) {
-        atomicAdd(&acc[kOffB3 + n], d3[n]);
-        for (int k = 0; k < kH; ++k) {
-          atomicAdd(&acc[kOffW3 + n * kH + k], d3[n] * h2[k]);
-          d2[k] += w[kOffW3 + n * kH + k] * d3[n];
-        }
-      }
-      for (int k = 0; k < kH; ++k) d2[k] *= silu_grad(z2[k]);
-      float d1[kH];
-      for (int k = 0; k < kH; ++k) d1[k] = 0.f;
-      for (int n = 0; n < kH; ++n) {
-        atomicAdd(&acc[kOffB2 + n], d2[n]);
-        for (int k = 0; k < kH; ++k) {
-          atomicAdd(&acc[kOffW2 + n * kH + k], d2[n] * h1[k]);
-          d1[k] += w[kOffW2 + n * kH + k] * d2[n];
-        }
-      }
-      for (int n = 0; n < kH; ++n) {
-        const float dn = d1[n] * silu_grad(z1[n]);
-        atomicAdd(&acc[kOffB1 + n], dn);
-        for (int k = 0; k < 3; ++k) atomicAdd(&acc[kOffW1 + n * kIn + k], dn * in[k]);
+      if (tid < kH) {
+        float s = 0.f;
+        for (int r = 0; r < kBwdRows; ++r) s += D[r * kLd + tid];
+        atomicAdd(grad + off_b[l] + tid, s);
       }
     }
+    const float* w = w_l[l];
+    for (int i = 0; i < kH / 8; ++i) {
+      const int k = warp + 8 * i;
+      float s = 0.f;
+      for (int n = 0; n < kH; ++n) s += D[lane * kLd + n] * w[n * kH + k];
+      E[lane * kLd + k] = s * s_in[l][lane * kLd + k];
+    }
+    __syncthreads();
+    float* t = D;
+    D = E;
+    E = t;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kParams; i += blockDim.x)
-    if (acc[i] != 0.f) atomicAdd(grad + i, acc[i]);
+  // first layer: dW1 = D1^T X, db1 = sum_r D1
+  if (tid < kH * 3) {
+    const int n = tid / 3, k = tid % 3;
+    float s = 0.f;
+    for (int r = 0; r < kBwdRows; ++r) s += D[r * kLd + n] * X[r * 3 + k];
+    atomicAdd(grad + kOffW1 + n * kIn + k, s);
+  } else if (tid < kH * 4) {
+    const int n = tid - kH * 3;
+    float s = 0.f;
+    for (int r = 0; r < kBwdRows; ++r) s += D[r * kLd + n];
+    atomicAdd(grad + kOffB1 + n, s);
+  }
 }
 
 // Adam step on the FP32 master weights (bias-corrected), then the BF16 copy; padding columns stay zero.
@@ -236,10 +295,10 @@ hrt_status launch_mlp_forward(const float* x, int rows, const void* wb, const fl
 
 hrt_status launch_mlp_backward(const float* x, int rows, const void* wb, const float* wf, const float* gbar,
                                float* grad, cudaStream_t s) {
-  const int smem = 2 * kParams * static_cast<int>(sizeof(float));
+  const int smem = kBwdSmemFloats * static_cast<int>(sizeof(float));
   HRT_CUDA(cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  mlp_backward_kernel<<<(rows + 63) / 64, 64, smem, s>>>(x, rows, static_cast<const __nv_bfloat16*>(wb), wf, gbar,
-                                                         grad);
+  mlp_backward_kernel<<<(rows + kBwdRows - 1) / kBwdRows, kBwdThreads, smem, s>>>(
+      x, rows, static_cast<const __nv_bfloat16*>(wb), wf, gbar, grad);
   HRT_LAUNCHED("mlp_backward_kernel");
   return HRT_OK;
 }
@@ -257,6 +316,22 @@ hrt_status launch_adam(float* wf, void* wb, const float* grad, float* m, float* 
 hrt_status launch_to_bf16(const float* wf, void* wb, cudaStream_t s) {
   to_bf16_kernel<<<(kParams + 255) / 256, 256, 0, s>>>(wf, static_cast<__nv_bfloat16*>(wb));
   HRT_LAUNCHED("to_bf16_kernel");
+  return HRT_OK;
+}
+
+// Inputs of the correction table at one scale factor: row i = (i dx, a, ln N_mesh), dx = |k|max cell / (rows - 1).
+__global__ void correction_inputs_kernel(float* __restrict__ x, int rows, double dx, float a, float ln_n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows) return;
+  x[3 * i] = static_cast<float>(i * dx);
+  x[3 * i + 1] = a;
+  x[3 * i + 2] = ln_n;
+}
+
+hrt_status launch_correction_inputs(float* x, int rows, double dx, double a, double ln_n, cudaStream_t s) {
+  correction_inputs_kernel<<<(rows + 255) / 256, 256, 0, s>>>(x, rows, dx, static_cast<float>(a),
+                                                              static_cast<float>(ln_n));
+  HRT_LAUNCHED("correction_inputs_kernel");
   return HRT_OK;
 }
 

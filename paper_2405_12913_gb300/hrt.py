@@ -87,6 +87,7 @@ _SIGS = {
     "hrt_init_rays": ([_P, _P, _I64], C.c_int),
     "hrt_step": ([_P, _D, _I32], C.c_int),
     "hrt_sync_particles": ([_P], C.c_int),
+    "hrt_set_ray_correction": ([_P, _P], C.c_int),
     "hrt_step_static": ([_P, _D, _D, _I32], C.c_int),
     "hrt_drift_free": ([_P, _D, _D], C.c_int),
     "hrt_read_rays": ([_P, _P, _P, _P, _P], C.c_int),
@@ -535,6 +536,12 @@ class Context:
 
     def hrt_step(self, a_next: float, source: int = -1):
         _check(_lib.hrt_step(self._h, a_next, source), "hrt_step")
+
+    def hrt_set_ray_correction(self, params: torch.Tensor | None):
+        """Learned ray-force correction (float32 MLP parameters on the device), or None for the plain kernel."""
+        if params is not None and params.numel() != MLP_PARAMS:
+            raise ValueError(f"params must hold {MLP_PARAMS} values")
+        _check(_lib.hrt_set_ray_correction(self._h, _ptr(params, torch.float32, "params")), "hrt_set_ray_correction")
 
     def hrt_sync_particles(self):
         _check(_lib.hrt_sync_particles(self._h), "hrt_sync_particles")

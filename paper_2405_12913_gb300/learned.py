@@ -1,6 +1,6 @@
 """Learned correction of the coarse-mesh ray force, trained on the method's own coarse/fine mesh pairs.
 
-The paper sharpens the PM force with a trained factor g in k/k^2 -> (k/k^2) g (Sec. 5.2).  Here g = 1 + MLP(|k| cell,
+The paper sharpens the PM force with a trained factor g in k/k^2 -> (k/k^2) g (Sec. 6.2).  Here g = 1 + MLP(|k| cell,
 a, ln N_mesh) multiplies the Green's function of the ray gradient fields of a coarse mesh (the particles keep the
 plain force), and is trained so that the convergence power spectrum of the coarse run matches that of a run with
 the same initial conditions on a mesh four times finer.  The plain kernel (g = 1) is both the fallback and the
@@ -129,9 +129,21 @@ def _noise(seed: int, n: int) -> torch.Tensor:
 
 def plain_run(S: PairSpec, n_mesh: int, seed: int, record_spectra: bool = False):
     """Plain HRT run on an n_mesh^3 mesh (context API): returns (kappa map, [density spectra per reverse step])."""
+    kappa, spectra, _ = run(S, n_mesh, seed, record_spectra=record_spectra)
+    return kappa, spectra
+
+
+def run(S: PairSpec, n_mesh: int, seed: int, params: torch.Tensor | None = None, record_spectra: bool = False,
+        timed: bool = False):
+    """HRT run on an n_mesh^3 mesh through the context API, with the learned ray correction ``params`` (None:
+    plain).  Returns (kappa map, [density spectra per reverse step], milliseconds of the reverse co-evolution
+    steps (CUDA events on the context's stream) or None)."""
     cfg = hrt.make_config(n_mesh, S.box, S.n_side, S.omega_m, S.h, S.n_s, S.sigma8, S.deconv_p, S.smooth_cells,
-                          1.0, S.observer, n_sources=1)
+                          1.0, S.observer, n_sources=1, ray_fields=0 if params is None else 2,
+                          ray_deconv_p=S.deconv_p, ray_smooth_cells=S.smooth_cells)
     ctx = hrt.Context(cfg)
+    if params is not None:
+        ctx.hrt_set_ray_correction(params)
     ctx.hrt_init_particles_zeldovich(_noise(seed, S.n_side).reshape(-1), S.a_init)
     for a in S.forward_grid[1:]:
         ctx.hrt_step(a)
@@ -139,13 +151,22 @@ def plain_run(S: PairSpec, n_mesh: int, seed: int, record_spectra: bool = False)
     ctx.hrt_init_rays(_theta0(S))
     spectra = []
     rg = S.reverse_grid
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)] if timed else None
+    if timed:
+        torch.cuda.synchronize()
+        ev[0].record()
     for n in range(S.n_reverse):
         if record_spectra:
             spectra.append(_ctx_density_spectrum(ctx, S, n_mesh, rg[n]))
         ctx.hrt_step(rg[n + 1], 0 if n + 1 == S.n_reverse else -1)
+    ms = None
+    if timed:
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1])
     kappa = ctx.hrt_read_maps(0)[0].clone()
     ctx.close()
-    return kappa, spectra
+    return kappa, spectra, ms
 
 
 def _ctx_density_spectrum(ctx, S, n_mesh, a):
@@ -294,6 +315,36 @@ def evaluate(S, trainer, mlp, seeds, fine, spectra, plain_p, sel):
             "plain_err_per_bin": ep.mean(axis=0).tolist(), "learned_err_per_bin": el.mean(axis=0).tolist()}
 
 
+def compare(S: PairSpec, params: torch.Tensor, seeds, log=print):
+    """The learned form against the plain one at equal cost and against the fine mesh: per held-out seed, the
+    coarse plain, coarse learned and fine plain runs; P(ell) relative errors of both coarse forms against the
+    fine run (bins with ell <= S.ell_cut), and the reverse co-evolution rate (particles + rays, sim-steps/s)
+    of each form, timed with CUDA events (the first seed's runs are an untimed warm-up of plans and memory)."""
+    rates = {"coarse_plain": [], "coarse_learned": [], "fine_plain": []}
+    err_plain, err_learned = [], []
+    for i, s in enumerate([seeds[0]] + list(seeds)):
+        kf, _, mf = run(S, S.n_fine, s, timed=True)
+        kc, _, mc = run(S, S.n_coarse, s, timed=True)
+        kl, _, ml = run(S, S.n_coarse, s, params=params, timed=True)
+        if i == 0:
+            continue
+        ell, pf, cnt = power(S, kf)
+        sel = _bins(S, ell, cnt)
+        err_plain.append(np.abs(power(S, kc)[1][sel] / pf[sel] - 1.0))
+        err_learned.append(np.abs(power(S, kl)[1][sel] / pf[sel] - 1.0))
+        for k, ms in (("fine_plain", mf), ("coarse_plain", mc), ("coarse_learned", ml)):
+            rates[k].append(S.n_reverse / (ms * 1e-3))
+        log(f"seed {s}: plain err {err_plain[-1].mean():.4f} learned err {err_learned[-1].mean():.4f}; "
+            f"sim-steps/s fine {rates['fine_plain'][-1]:.1f} coarse {rates['coarse_plain'][-1]:.1f} "
+            f"learned {rates['coarse_learned'][-1]:.1f}")
+    ep, el = np.array(err_plain), np.array(err_learned)
+    return {"seeds": list(seeds), "n_pix": S.n_pix, "bins": int(ep.shape[1]),
+            "sim_steps_per_s": {k: float(np.median(v)) for k, v in rates.items()},
+            "plain_mean_rel_err": float(ep.mean()), "plain_max_rel_err": float(ep.max()),
+            "learned_mean_rel_err": float(el.mean()), "learned_max_rel_err": float(el.max()),
+            "plain_err_per_bin": ep.mean(axis=0).tolist(), "learned_err_per_bin": el.mean(axis=0).tolist()}
+
+
 def main():
     ap = argparse.ArgumentParser(description="train and evaluate the learned ray-force correction")
     ap.add_argument("--train-seeds", type=int, default=16)
@@ -302,12 +353,25 @@ def main():
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--n-pix", type=int, default=1024)
     ap.add_argument("--out", default=None, help="write the trained FP32 parameters (.npy) here")
+    ap.add_argument("--compare-n-pix", type=int, default=4096,
+                    help="rays per side of the learned/plain/fine comparison on the held-out seeds (0: skip)")
+    ap.add_argument("--params", default=None, help="skip training: compare with these parameters (.npy)")
     a = ap.parse_args()
     S = replace(PairSpec(), n_pix=a.n_pix)
-    mlp, res = train(S, range(a.train_seeds), range(100, 100 + a.test_seeds), a.iters, a.lr)
-    if a.out:
-        np.save(a.out, mlp.state())
-    print(json.dumps({k: v for k, v in res.items() if k != "history"}))
+    test = list(range(100, 100 + a.test_seeds))
+    out = {}
+    if a.params:
+        w = torch.tensor(np.load(a.params), dtype=torch.float32, device="cuda")
+    else:
+        mlp, res = train(S, range(a.train_seeds), test, a.iters, a.lr, log=lambda m: print(m, flush=True))
+        if a.out:
+            np.save(a.out, mlp.state())
+        w = mlp.w
+        out["training"] = {k: v for k, v in res.items() if k != "history"}
+        out["training"]["loss_first_last"] = [res["history"][0], res["history"][-1]]
+    if a.compare_n_pix:
+        out["comparison"] = compare(replace(S, n_pix=a.compare_n_pix), w, test, log=lambda m: print(m, flush=True))
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":

@@ -111,3 +111,44 @@ def test_trained_correction_beats_plain_kernel_on_held_out_seeds(hrt):
     mlp, res = learned.train(S, train_seeds=range(4), test_seeds=range(100, 102), iters=40, lr=3e-3, log=lambda s: None)
     assert res["history"][-1] < 0.5 * res["history"][0]
     assert res["learned_mean_rel_err"] < 0.7 * res["plain_mean_rel_err"], res
+
+
+def test_context_correction_matches_ray_trainer(hrt):
+    """hrt_step with a correction set evaluates g at each step's a inside the context; its kappa equals the
+    trainer's ray-only re-trace on the stored density spectra with the same network, and differs from the
+    plain kernel's."""
+    from dataclasses import replace
+
+    from paper_2405_12913_gb300 import learned
+    S = replace(learned.PairSpec(), n_side=32, n_coarse=32, n_fine=64, box=64.0, n_forward=6, n_reverse=4,
+                a_min=0.7, n_pix=64, fov_deg=4.0, nbins=6)
+    mlp = learned.MLP(seed=3)
+    rng = np.random.default_rng(9)
+    w = mlp.w.cpu().numpy()
+    w[-65:] = rng.standard_normal(65) * 0.05          # output layer: g != 1
+    mlp.w.copy_(torch.tensor(w))
+    hrt.hrt_mlp_to_bf16(mlp.w, mlp.wb)
+    k_plain, spectra = learned.plain_run(S, S.n_coarse, 7, record_spectra=True)
+    k_ref, _ = learned.RayTrainer(S).forward(mlp, spectra, keep=False)
+    k_ctx, _, _ = learned.run(S, S.n_coarse, 7, params=mlp.w)
+    scale = k_ref.abs().max().item()
+    assert (k_ctx - k_ref).abs().max().item() <= 1e-4 * scale
+    assert (k_ctx - k_plain).abs().max().item() > 1e-3 * scale
+
+
+def test_context_correction_needs_ray_fields_and_resets(hrt):
+    from dataclasses import replace
+
+    from paper_2405_12913_gb300 import learned
+    S = replace(learned.PairSpec(), n_side=16, n_coarse=32, box=64.0, n_forward=4, n_reverse=3, a_min=0.7,
+                n_pix=32, fov_deg=4.0)
+    w = torch.zeros(hrt.MLP_PARAMS, device="cuda")
+    cfg = hrt.make_config(32, S.box, S.n_side, observer=S.observer, ray_fields=0)
+    ctx = hrt.Context(cfg)
+    with pytest.raises(hrt.HRTError):
+        ctx.hrt_set_ray_correction(w)
+    ctx.close()
+    # g = 1 exactly (zero output layer) on the separately filtered ray fields reproduces the plain run
+    k_plain, _, _ = learned.run(S, 32, 5)
+    k_one, _, _ = learned.run(S, 32, 5, params=w)
+    assert torch.allclose(k_one, k_plain, rtol=0, atol=1e-5 * k_plain.abs().max().item())

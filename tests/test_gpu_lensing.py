@@ -54,7 +54,7 @@ def test_point_mass_deflection_matches_oracle(hrt):
     # spec parity target: deflection within 1e-4 relative of the FP64 oracle
     assert rel[b > 1.0].max() < 1e-4, rel[b > 1.0].max()
     assert np.median(rel) < 1e-5
-    # and the physics: against the Born integral of the exact periodic field above 4 cells (Sec. 5.1), over
+    # and the physics: against the Born integral of the exact periodic field above 4 cells (Sec. 6.1), over
     # all azimuths.  Errors are normalised by the single-lens deflection; the 3D-mesh filter leaves up to ~2 %
     # along the mesh axes near 4 cells (median 0.5 %), falling to < 0.1 % median beyond 10 cells.
     sel = np.flatnonzero(b > 4.0)[::53]

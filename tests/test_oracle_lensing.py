@@ -1,4 +1,4 @@
-"""Pins of the oracle's lensing end to end: point-mass lens (Sec. 5.1) and the convergence power spectrum."""
+"""Pins of the oracle's lensing end to end: point-mass lens (Sec. 6.1) and the convergence power spectrum."""
 import math
 import os
 
@@ -14,7 +14,7 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 def test_einstein_radius_worked_example():
-    # Sec. 5.1: M = 1.3e15 Msun at chi_l = 350 Mpc/h, chi_s = 850 Mpc/h gives theta_E = 1.8'.
+    # Sec. 6.1: M = 1.3e15 Msun at chi_l = 350 Mpc/h, chi_s = 850 Mpc/h gives theta_E = 1.8'.
     row = np.loadtxt(os.path.join(GOLDEN, "point_mass_einstein_radius.txt"))
     m_sun, chi_l, chi_s, h, theta_e_arcmin = row
     m = m_sun * h  # Msun -> Msun/h
@@ -47,12 +47,12 @@ def test_point_mass_deflection_matches_born_ewald_above_threshold(point_mass_run
     # deflection points away from the lens direction on the sky: alpha parallel to +theta0 / |theta0|
     cosang = (alpha * th).sum(axis=1) / (np.linalg.norm(alpha, axis=1) * np.linalg.norm(th, axis=1))
     assert cosang[above].min() > 0.999
-    # inside the threshold the mesh suppresses the deflection (Sec. 5.1)
+    # inside the threshold the mesh suppresses the deflection (Sec. 6.1)
     assert np.all(np.linalg.norm(alpha[b < 1.0], axis=1) < np.linalg.norm(born[b < 1.0], axis=1))
 
 
 def test_born_ewald_matches_closed_form_with_periodic_images(point_mass_run):
-    # Eq. "pointmass_analytic" with the periodic image sum of Appendix C (and the uniform background of the
+    # Eq. "pointmass_analytic" with the periodic image sum of Appendix D (and the uniform background of the
     # zero-mean FFT potential): alpha = (chi_s - chi_l)/chi_s 4GM/c^2 sum_m (b - m)/|b - m|^2 - (pi/L^2) b.
     pmc, th, alpha, born, b = point_mass_run
     bvec = th * pmc.chi_lens
