@@ -140,7 +140,7 @@ def algorithmic_bytes(W):
     return {
         "cic_scatter": 3 * 4 * npart + mesh,                 # positions read + density written
         "kspace": spec + 3 * spec,                           # density spectrum read + 3 gradient spectra written
-        "kick_drift": 3 * mesh + 2 * 2 * 3 * 4 * npart,      # 3 fields read + disp, mom read and written
+        "kick_drift": 4 * mesh + 2 * 2 * 3 * 4 * npart,      # 3 fields read, density written, disp/mom r+w
         "ray_step": 2 * rays * (16 + 8 + 16 + 16),           # ray state read and written (slab reads extra)
         "fft_r2c": mesh + spec,
         "fft_c2r": 3 * (spec + mesh),

@@ -373,10 +373,12 @@ __device__ void half_backward(const RayStepParams& p, int j0, int j1, double thx
   const float inv_cell = static_cast<float>(1.0 / p.cell);
   const float* f[2] = {gx, gy};
   float* fb[2] = {gbx, gby};
+  const int lane = threadIdx.x & 31;
   for (int j = j0; j < j1; ++j) {
     float cwb = 0.f, cwrb = 0.f, chib = 0.f;
+    NodeCols c{};
+    float t[2][4][2] = {};  // field cotangent per field, (x, y) corner and z plane
     if (active) {
-      NodeCols c;
       node_cols(p, j, bx, fbx, by, fby, tx, ty, c);
       const float cw = p.cw[j], cwr = p.cwr[j];
       float fbar_x = 0.f, fbar_y = 0.f, fbar_z = 0.f;
@@ -391,9 +393,8 @@ __device__ void half_backward(const RayStepParams& p, int j0, int j1, double thx
                             al * c.fx * uy + bex * uy - bey * c.fx, al * c.fx * c.fy + bex * c.fy + bey * c.fx};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const float t0 = (1.f - c.fz) * q[k], t1 = c.fz * q[k];
-          if (t0 != 0.f) atomicAdd(fb[a] + c.r[k] + c.iz, t0);
-          if (t1 != 0.f) atomicAdd(fb[a] + c.r[k] + c.jz, t1);
+          t[a][k][0] = (1.f - c.fz) * q[k];
+          t[a][k][1] = c.fz * q[k];
         }
         // cotangent of the fractional position (the mixed second derivatives couple the J terms)
         fbar_x += al * o.dx + bey * o.sxy;
@@ -407,6 +408,35 @@ __device__ void half_backward(const RayStepParams& p, int j0, int j1, double thx
       thb[0] += fbar_x * r_over_cell;
       thb[1] += fbar_y * r_over_cell;
       chib = (fbar_x * tx + fbar_y * ty + fbar_z) * inv_cell;
+    }
+    // Neighbouring rays of a warp mostly share the node's mesh cell: lanes with the same cell that follow
+    // each other form a segment, the segment's cotangents are summed by a segmented shuffle reduction and its
+    // first lane issues the 16 atomics (a cell that reappears later in the warp starts a new segment).
+    const long long key = active ? static_cast<long long>(c.r[0] + c.iz) : -1ll - lane;
+    const long long prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool head = lane == 0 || prev != key;
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const unsigned above = lane == 31 ? 0u : heads & (0xffffffffu << (lane + 1));
+    const int seg_end = above ? __ffs(above) - 2 : 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1)
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int z = 0; z < 2; ++z) {
+            const float u = __shfl_down_sync(0xffffffffu, t[a][k][z], d);
+            if (lane + d <= seg_end) t[a][k][z] += u;
+          }
+    if (head && active) {
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (t[a][k][0] != 0.f) atomicAdd(fb[a] + c.r[k] + c.iz, t[a][k][0]);
+          if (t[a][k][1] != 0.f) atomicAdd(fb[a] + c.r[k] + c.jz, t[a][k][1]);
+        }
     }
     // block reduction of the node cotangents into shared memory
     for (int o = 16; o > 0; o >>= 1) {
