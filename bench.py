@@ -33,7 +33,7 @@ KERNEL_SOURCES = {
     "ray_step": ["ray_kernels.cu", "mesh_kernels.h"],
     "kick_drift": ["mesh_kernels.cu"],
     "cic_scatter": ["mesh_kernels.cu"],
-    "kspace": ["mesh_kernels.cu"],
+    "kspace": ["mesh_kernels.cu", "xpass_kernels.cu"],
 }
 
 
@@ -197,10 +197,11 @@ def run_gpu(args, W, world, rank, local):
         for _ in range(k):
             if pos == len(grid) - 1:
                 reset()
+                launches += 3  # CIC scatter, k-space pass, ray initialisation
                 pos = 0
             n = pos + 1
             ctx.hrt_step(grid[n], slots.get(n, -1))
-            launches += 4
+            launches += 3  # ray step, kick-drift-deposit, k-space pass (x-pass on the split path)
             pos = n
         return pos, launches
 

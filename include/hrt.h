@@ -148,6 +148,13 @@ hrt_status hrt_pm_destroy(hrt_pm* pm); /* NULL is fine; synchronises the stream 
  * k-space kernel.  Returns HRT_ERR_CUDA if cuFFT refuses the callback. */
 hrt_status hrt_pm_set_fused(hrt_pm* pm, int32_t on);
 
+/* Split path of hrt_pm_solve (on by default for n = 256, 512, 1024): batched 2D (y, z) cuFFT plans over the
+ * x-planes and one x-pass kernel between them that does the forward FFT along x, the k-space step of
+ * hrt_kspace_gradient and the inverse FFTs along x, so that no 3D spectrum is written or read twice.  Same
+ * results as the 3D path (FP32 rounding of a different FFT order).  on = 0 returns to 3D cuFFT plans and the
+ * separate k-space kernel.  HRT_ERR_INVALID_ARG for other mesh sides. */
+hrt_status hrt_pm_set_split(hrt_pm* pm, int32_t on);
+
 /* grad[3][n^3] <- gradient of phi from rho[n^3] (rho is overwritten as FFT scratch);
  * ray_grad[2][n^3] (only if the object has ray fields; else pass NULL) with the ray filter. */
 hrt_status hrt_pm_solve(hrt_pm* pm, float* rho, double pref, const hrt_filter* f, float* grad,
@@ -318,7 +325,8 @@ hrt_status hrt_mlp_to_bf16(const float* w_f32, void* w_bf16, void* stream);
 hrt_status hrt_kspace_table_adjoint(const void* gbar_hat, int32_t n_comp, const void* rho_hat, int64_t n, double box,
                                     double pref, const hrt_filter* f, float* table_bar, void* stream);
 
-/* Copies the density half spectrum of the last hrt_pm_solve into out (complex64 [n][n][n/2+1]). */
+/* Copies the density half spectrum of the last hrt_pm_solve into out (complex64 [n][n][n/2+1]); HRT_ERR_STATE
+ * if that solve took the split path (see hrt_pm_set_split), which never forms the 3D spectrum. */
 hrt_status hrt_pm_density_spectrum(hrt_pm* pm, void* out);
 
 /* fields[n_out][n^3] <- gradient fields from a stored density half spectrum rho_hat (not modified): the k-space

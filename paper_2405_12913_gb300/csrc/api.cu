@@ -17,6 +17,7 @@
 #include "kspace_callback.h"
 #include "mesh_kernels.h"
 #include "mlp.h"
+#include "xpass.h"
 
 extern "C" const unsigned char hrt_kspace_callback_fatbin[];
 extern "C" const size_t hrt_kspace_callback_fatbin_size;
@@ -259,11 +260,22 @@ struct hrt_pm {
   bool have_cb3 = false, have_cb2 = false;
   hrt::KspaceCallbackInfo* cb_info = nullptr;  // device: [0] particle fields, [1] ray fields
   size_t work_bytes = 0;
+  // split path (the default where supported): batched 2D (y, z) plans on rows padded to xpass_row(n), and the
+  // x-pass kernel between them (forward x-FFT, k-space step, inverse x-FFTs)
+  bool split = false;
+  cufftHandle r2c2d = 0, c2r2d = 0;
+  bool have_r2c2d = false, have_c2r2d = false;
+  float2* xtw = nullptr;    // x-FFT twiddles
+  bool last_split = false;  // rho_hat holds the (y, z)-transformed density of the split path
 };
 
 namespace hrt {
 
 static size_t spectrum_bytes(int64_t n) { return static_cast<size_t>(n) * n * (n / 2 + 1) * sizeof(float2); }
+// Bytes of one spectrum buffer: the half spectrum, or the padded split layout where the split path exists.
+static size_t spectrum_alloc(int64_t n) {
+  return xpass_supported(n) ? static_cast<size_t>(n) * n * xpass_row(n) * sizeof(float2) : spectrum_bytes(n);
+}
 
 static bool fusable(int64_t n) { return n >= 8 && n <= 1024 && (n & (n - 1)) == 0; }
 
@@ -294,6 +306,35 @@ static void pm_set_work(hrt_pm* pm) {
     cufftSetWorkArea(pm->c2r_cb2, pm->work);
     cufftSetStream(pm->c2r_cb2, pm->stream);
   }
+  for (int i = 0; i < 2; ++i) {
+    if (!(i == 0 ? pm->have_r2c2d : pm->have_c2r2d)) continue;
+    cufftHandle p = i == 0 ? pm->r2c2d : pm->c2r2d;
+    cufftSetWorkArea(p, pm->work);
+    cufftSetStream(p, pm->stream);
+  }
+}
+
+// Batched 2D (y, z) plans over the n x-planes, spectra rows padded to xpass_row(n), and the x-FFT twiddles.
+static hrt_status pm_make_split(hrt_pm* pm, size_t* work) {
+  const long long n = pm->n, nzp = xpass_row(pm->n);
+  long long dims[2] = {n, n}, real_embed[2] = {n, n}, spec_embed[2] = {n, nzp};
+  size_t w1 = 0, w2 = 0;
+  HRT_CUFFT(cufftCreate(&pm->r2c2d));
+  pm->have_r2c2d = true;
+  HRT_CUFFT(cufftSetAutoAllocation(pm->r2c2d, 0));
+  HRT_CUFFT(cufftMakePlanMany64(pm->r2c2d, 2, dims, real_embed, 1, n * n, spec_embed, 1, n * nzp, CUFFT_R2C, n, &w1));
+  HRT_CUFFT(cufftCreate(&pm->c2r2d));
+  pm->have_c2r2d = true;
+  HRT_CUFFT(cufftSetAutoAllocation(pm->c2r2d, 0));
+  HRT_CUFFT(cufftMakePlanMany64(pm->c2r2d, 2, dims, spec_embed, 1, n * nzp, real_embed, 1, n * n, CUFFT_C2R, n, &w2));
+  *work = std::max(w1, w2);
+  std::vector<float2> tw;
+  xpass_twiddles(pm->n, tw);
+  HRT_TRY(device_alloc(reinterpret_cast<void**>(&pm->xtw), tw.size() * sizeof(float2), pm->stream, "twiddles"));
+  HRT_CUDA(cudaMemcpyAsync(pm->xtw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, pm->stream));
+  // the host vector must outlive the copy
+  HRT_CUDA(cudaStreamSynchronize(pm->stream));
+  return HRT_OK;
 }
 
 static hrt_status pm_make(int64_t n, double box, int32_t n_ray, cudaStream_t s, hrt_pm* pm) {
@@ -312,10 +353,16 @@ static hrt_status pm_make(int64_t n, double box, int32_t n_ray, cudaStream_t s, 
   HRT_CUFFT(cufftSetAutoAllocation(pm->c2r, 0));
   HRT_CUFFT(cufftMakePlanMany64(pm->c2r, 3, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, 1, &w2));
   pm->work_bytes = std::max(w1, w2);
+  if (xpass_supported(n)) {
+    size_t w3 = 0;
+    HRT_TRY(pm_make_split(pm, &w3));
+    pm->work_bytes = std::max(pm->work_bytes, w3);
+    pm->split = true;
+  }
   HRT_TRY(device_alloc(&pm->work, pm->work_bytes, s, "cuFFT work area"));
   pm_set_work(pm);
-  HRT_TRY(device_alloc(&pm->rho_hat, spectrum_bytes(n), s, "rho_hat"));
-  HRT_TRY(device_alloc(&pm->grad_hat, spectrum_bytes(n) * (3 + n_ray), s, "gradient spectra"));
+  HRT_TRY(device_alloc(&pm->rho_hat, spectrum_alloc(n), s, "rho_hat"));
+  HRT_TRY(device_alloc(&pm->grad_hat, spectrum_alloc(n) * (3 + n_ray), s, "gradient spectra"));
   return HRT_OK;
 }
 
@@ -356,6 +403,9 @@ static void pm_release(hrt_pm* pm) {
   if (pm->have_c2r) cufftDestroy(pm->c2r);
   if (pm->have_cb3) cufftDestroy(pm->c2r_cb3);
   if (pm->have_cb2) cufftDestroy(pm->c2r_cb2);
+  if (pm->have_r2c2d) cufftDestroy(pm->r2c2d);
+  if (pm->have_c2r2d) cufftDestroy(pm->c2r2d);
+  device_free(pm->xtw, pm->stream);
   device_free(pm->work, pm->stream);
   device_free(pm->rho_hat, pm->stream);
   device_free(pm->grad_hat, pm->stream);
@@ -414,6 +464,42 @@ static hrt_status pm_solve(hrt_pm* pm, float* rho, double pref, const hrt_filter
   if (rays) HRT_TRY(check_filter(fr));
   HRT_TRY(pm_tables(pm, *f, &pm->tab_a, &pm->key_a));
   if (rays) HRT_TRY(pm_tables(pm, *fr, &pm->tab_b, &pm->key_b));
+  pm->last_split = pm->split && !pm->fused;
+  if (pm->last_split) {
+    const int64_t n = pm->n;
+    const size_t sp = spectrum_alloc(n);
+    char* gh = static_cast<char*>(pm->grad_hat);
+    {
+      PhaseScope ps(pc, 3);
+      HRT_CUFFT(cufftExecR2C(pm->r2c2d, rho, static_cast<cufftComplex*>(pm->rho_hat)));
+    }
+    auto set = [&](const float* tab, const hrt_filter& flt, int n_out, char* out) {
+      XpassSet x{};
+      x.wxy = tab;
+      x.wz = tab + n;
+      x.g = flt.g_table;
+      x.g_nk = flt.g_nk;
+      x.g_inv_dk = flt.g_table ? static_cast<float>((flt.g_nk - 1) / flt.g_kmax) : 0.f;
+      x.n_out = n_out;
+      x.out = reinterpret_cast<float2*>(out);
+      return x;
+    };
+    const XpassSet xa = set(pm->tab_a, *f, 3, gh);
+    const XpassSet xb = rays ? set(pm->tab_b, *fr, pm->n_ray, gh + 3 * sp) : XpassSet{};
+    {
+      PhaseScope ps(pc, 4);
+      HRT_TRY(launch_xpass(pm->rho_hat, n, pm->box, pref, pm->xtw, xa, xb, pm->stream));
+    }
+    if (before_fields) HRT_CUDA(cudaStreamWaitEvent(pm->stream, before_fields, 0));
+    PhaseScope ps(pc, 5);
+    const size_t mb = static_cast<size_t>(n) * n * n;
+    for (int j = 0; j < 3; ++j)
+      HRT_CUFFT(cufftExecC2R(pm->c2r2d, reinterpret_cast<cufftComplex*>(gh + j * sp), grad + j * mb));
+    if (rays)
+      for (int j = 0; j < pm->n_ray; ++j)
+        HRT_CUFFT(cufftExecC2R(pm->c2r2d, reinterpret_cast<cufftComplex*>(gh + (3 + j) * sp), ray_grad + j * mb));
+    return HRT_OK;
+  }
   {
     PhaseScope ps(pc, 3);
     HRT_CUFFT(cufftExecR2C(pm->r2c, rho, static_cast<cufftComplex*>(pm->rho_hat)));
@@ -659,6 +745,13 @@ hrt_status hrt_pm_set_fused(hrt_pm* pm, int32_t on) {
   if (!pm) return fail(HRT_ERR_INVALID_ARG, "pm is NULL");
   if (on) HRT_TRY(pm_build_fused(pm));
   pm->fused = on != 0;
+  return HRT_OK;
+}
+
+hrt_status hrt_pm_set_split(hrt_pm* pm, int32_t on) {
+  if (!pm) return fail(HRT_ERR_INVALID_ARG, "pm is NULL");
+  if (on && !pm->have_r2c2d) return fail(HRT_ERR_INVALID_ARG, "the split path needs a mesh side of 256, 512 or 1024");
+  pm->split = on != 0;
   return HRT_OK;
 }
 
@@ -1040,6 +1133,8 @@ hrt_status hrt_pm_forward_fft(hrt_pm* pm, const float* real, void* out) {
 
 hrt_status hrt_pm_density_spectrum(hrt_pm* pm, void* out) {
   if (!pm || !out) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  if (pm->last_split)
+    return fail(HRT_ERR_STATE, "the last solve took the split path, which keeps no 3D spectrum (hrt_pm_set_split 0)");
   return cuda_status(cudaMemcpyAsync(out, pm->rho_hat, spectrum_bytes(pm->n), cudaMemcpyDeviceToDevice, pm->stream),
                      "copy density spectrum");
 }
@@ -1065,7 +1160,7 @@ hrt_status hrt_workspace_bytes(const hrt_config* cfg, int64_t n_rays, size_t* by
   if (!bytes || n_rays < 0) return fail(HRT_ERR_INVALID_ARG, "bad arguments");
   const size_t n = cfg->n_mesh, mesh = n * n * n * sizeof(float), np = cfg->n_side * cfg->n_side * cfg->n_side;
   size_t b = 6 * np * sizeof(float) + mesh * (4 + cfg->ray_fields);
-  b += spectrum_bytes(cfg->n_mesh) * (1 + 3 + cfg->ray_fields) + 2 * spectrum_bytes(cfg->n_mesh);  // + cuFFT work
+  b += spectrum_alloc(cfg->n_mesh) * (1 + 3 + cfg->ray_fields) + 2 * spectrum_bytes(cfg->n_mesh);  // + cuFFT work
   b += static_cast<size_t>(n_rays) * (2 * sizeof(double) + 10 * sizeof(float));
   b += static_cast<size_t>(n_rays) * 4 * sizeof(float) * cfg->n_sources;
   *bytes = b;

@@ -73,6 +73,7 @@ _SIGS = {
     "hrt_pm_destroy": ([_P], C.c_int),
     "hrt_pm_solve": ([_P, _P, _D, _P, _P, _P, _P], C.c_int),
     "hrt_pm_set_fused": ([_P, _I32], C.c_int),
+    "hrt_pm_set_split": ([_P, _I32], C.c_int),
     "hrt_rays_init": ([_P, _P, _P], C.c_int),
     "hrt_ray_step": ([_P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
     "hrt_ray_drift_free": ([_P, _D, _D, _P], C.c_int),
@@ -282,6 +283,9 @@ class PM:
 
     def set_fused(self, on: bool):
         _check(_lib.hrt_pm_set_fused(self._h, int(on)), "hrt_pm_set_fused")
+
+    def set_split(self, on: bool):
+        _check(_lib.hrt_pm_set_split(self._h, int(on)), "hrt_pm_set_split")
 
     def close(self):
         if self._h:

@@ -299,3 +299,34 @@ def test_invalid_arguments_enqueue_nothing(hrt):
     with pytest.raises(hrt.HRTError):
         hrt.hrt_ray_drift_free(rays, 0.0, 10.0)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("n", [256, 1024])
+def test_pm_split_path_matches_3d_path(hrt, n):
+    # batched 2D (y, z) plans + the x-pass kernel against 3D plans + the k-space kernel, for the particle fields
+    # and for separately filtered ray fields with a learned table; the two differ by FP32 FFT rounding only
+    box, pref = 1000.0 * n / 1024, 0.45
+    g = torch.Generator(device="cuda").manual_seed(n)
+    rho = 1.0 + 0.5 * torch.randn(n, n, n, device="cuda", generator=g)
+    kmax = math.sqrt(3.0) * math.pi * n / box * 1.0001
+    gt = torch.linspace(1.3, 0.8, 512, device="cuda")
+    f = hrt.make_filter(4.0, box / n)
+    fr = hrt.make_filter(4.0, box / n, gt, kmax)
+    out = {}
+    for split in (False, True):
+        pm = hrt.PM(n, box, n_ray_fields=2)
+        pm.set_split(split)
+        grad = torch.empty(3, n, n, n, device="cuda")
+        rgrad = torch.empty(2, n, n, n, device="cuda")
+        pm.solve(rho.clone(), pref, f, grad, fr, rgrad)
+        torch.cuda.synchronize()
+        out[split] = (grad, rgrad)
+        if split:
+            with pytest.raises(hrt.HRTError):
+                pm.density_spectrum(torch.empty(n, n, n // 2 + 1, dtype=torch.complex64, device="cuda"))
+        pm.close()
+    for k in range(2):
+        for j in range(out[False][k].shape[0]):
+            ref = out[False][k][j]
+            err = (out[True][k][j] - ref).abs().max().item()
+            assert err <= 2e-5 * ref.abs().max().item(), (k, j, err, ref.abs().max().item())
