@@ -260,7 +260,7 @@ struct hrt_pm {
   bool have_cb3 = false, have_cb2 = false;
   hrt::KspaceCallbackInfo* cb_info = nullptr;  // device: [0] particle fields, [1] ray fields
   size_t work_bytes = 0;
-  // split path (the default where supported): batched 2D (y, z) plans on rows padded to xpass_row(n), and the
+  // split path (the default where supported): batched 2D (y, z) plans over the x-planes, and the
   // x-pass kernel between them (forward x-FFT, k-space step, inverse x-FFTs)
   bool split = false;
   cufftHandle r2c2d = 0, c2r2d = 0;

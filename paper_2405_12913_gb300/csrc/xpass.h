@@ -26,7 +26,7 @@ struct XpassSet {
 
 // Mesh sides the x-pass supports (n = 32 R1 with R1 in {8, 16, 32}).
 bool xpass_supported(int64_t n);
-// Padded length of a kz row of the split layout: n/2 + 8 P with P = 1024 / n (a whole number of tiles).
+// Length of a kz row of the split layout (the half spectrum's n/2 + 1).
 int64_t xpass_row(int64_t n);
 // Twiddle table of the x-FFT for side n: [R1][32] forward factors exp(-2 pi i l k1 / n), then [32][32] inverse
 // factors exp(+2 pi i n1 (lane mod R1) / n); FP64 on the host, rounded to float.

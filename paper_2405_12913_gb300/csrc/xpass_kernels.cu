@@ -12,9 +12,8 @@
 // pencil (ky, kz) the y and z components are d_y V and d_z V with V = IFFT_x(i c X), so a filter set needs two
 // inverse transforms (V and the x component) for its three outputs.
 //
-// Tiles: a CTA of 8 warps owns the pencils (ky, kz0 .. kz0 + 8P - 1) for all x: rows of 64 contiguous bytes in
-// the [x][ky][kz] spectra, whose rows are padded to n/2 + 8P entries (the last tile holds only the Nyquist
-// column kz = n/2).  Persistent CTAs; the next tile is copied into the second shared buffer with cp.async while
+// Tiles: a CTA of 8 warps owns the pencils (ky, kz0 .. kz0 + 8P - 1) for all x: rows of 8P contiguous complex
+// values in the [x][ky][kz] half spectra (the last tile holds only the Nyquist column kz = n/2).  Persistent CTAs; the next tile is copied into the second shared buffer with cp.async while
 // the current one is transformed.
 #include <cuda_runtime.h>
 
@@ -191,29 +190,46 @@ __device__ __forceinline__ void inverse_x(float2 (&u)[32], float2* T, int col0, 
   DftPencils<R1, true, P>::run(u);
 }
 
-// u[k2] = d(kx) i c(k) X[k2] at kx = k1 + R1 k2 for one filter set (d = d_x of each kx when with_dx, else 1):
-// the same arithmetic as the k-space kernel (c = Green's function x per-axis filter factors x learned g).
+// c(k) = Green's function x per-axis filter factors x learned g at kx = k1 + R1 k2 (the k-space kernel's factor).
 template <int R1>
+__device__ __forceinline__ float filter_c(const XpassSet& s, const float* wx, int n, int k1, int k2, float kf,
+                                          float scale, float k2yz, float cyz) {
+  const int kx = k1 + R1 * k2;
+  const int nx = kx < (n >> 1) ? kx : kx - n;
+  const float kxf = kf * nx;
+  const float kk = kxf * kxf + k2yz;
+  const float green = kk > 0.f ? __fdividef(scale, kk) : 0.f;
+  float c = green * wx[kx] * cyz;
+  if (s.g != nullptr) c *= learned_factor(s, sqrtf(kk));
+  return c;
+}
+
+__device__ __forceinline__ float dx_of(int kx, int n, float kf) {
+  const int nx = kx < (n >> 1) ? kx : kx - n;
+  return nx == -(n >> 1) ? 0.f : kf * nx;
+}
+
+// u[k2] = d(kx) Y[k2] at kx = k1 + R1 k2, with Y = i c X: computed here from X (PRE false) or given in X
+// (PRE true); d = d_x of each kx when with_dx, else 1.
+template <int R1, bool PRE>
 __device__ __forceinline__ void filtered(const float2 (&X)[32], float2 (&u)[32], const XpassSet& s,
                                          const float* wx, int n, int k1, float kf, float scale, float k2yz,
                                          float cyz, bool with_dx) {
-  const int half = n >> 1;
 #pragma unroll
   for (int k2 = 0; k2 < 32; ++k2) {
-    const int kx = k1 + R1 * k2;
-    const int nx = kx < half ? kx : kx - n;
-    const float kxf = kf * nx;
-    const float kk = kxf * kxf + k2yz;
-    const float green = kk > 0.f ? scale / kk : 0.f;
-    const float c = green * wx[kx] * cyz * learned_factor(s, sqrtf(kk));
-    const float d = with_dx ? (nx == -half ? 0.f : kxf) : 1.f;
-    u[k2] = make_float2(-d * c * X[k2].y, d * c * X[k2].x);
+    const float d = with_dx ? dx_of(k1 + R1 * k2, n, kf) : 1.f;
+    if (PRE) {
+      u[k2] = make_float2(d * X[k2].x, d * X[k2].y);
+    } else {
+      const float c = d * filter_c<R1>(s, wx, n, k1, k2, kf, scale, k2yz, cyz);
+      u[k2] = make_float2(-c * X[k2].y, c * X[k2].x);
+    }
   }
 }
 
-// The gradient spectra of one filter set for the tile: the x component, then V = IFFT_x(i c X) scaled by d_y
-// and d_z; each component is written to the tile's rows and stored by the whole CTA.
-template <int R1>
+// The gradient spectra of one filter set for the tile: the x component, then V = IFFT_x(i c X), stored once
+// scaled by d_y and once by d_z; each transform's result is written to the tile's rows and stored by the CTA.
+template <int R1, bool PRE>
 __device__ __forceinline__ void one_set(const XpassSet& s, const float* wx, const float2 (&X)[32], float2* T,
                                         const TileGeom& g, int col0, int k1, int lane, bool busy, int n, int nzp,
                                         float kf, float scale, int kz, float k2yz, float dy, int64_t plane,
@@ -223,7 +239,7 @@ __device__ __forceinline__ void one_set(const XpassSet& s, const float* wx, cons
   const float cyz = __ldg(s.wxy + g.ky) * __ldg(s.wz + kz);
   float2 u[32];
   if (busy) {
-    filtered<R1>(X, u, s, wx, n, k1, kf, scale, k2yz, cyz, true);
+    filtered<R1, PRE>(X, u, s, wx, n, k1, kf, scale, k2yz, cyz, true);
     inverse_x<R1>(u, T, col0, twi, lane);
 #pragma unroll
     for (int p = 0; p < P; ++p)
@@ -234,32 +250,33 @@ __device__ __forceinline__ void one_set(const XpassSet& s, const float* wx, cons
   store_tile<TK, LD>(s.out, n, nzp, g, T);
   __syncthreads();
   if (busy) {
-    filtered<R1>(X, u, s, wx, n, k1, kf, scale, k2yz, cyz, false);
+    filtered<R1, PRE>(X, u, s, wx, n, k1, kf, scale, k2yz, cyz, false);
     inverse_x<R1>(u, T, col0, twi, lane);
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+      for (int j = 0; j < R1; ++j) T[(lane + 32 * j) * LD + col0 + p] = u[p * R1 + j];
   }
-#pragma unroll
-  for (int comp = 1; comp < 3; ++comp) {
-    if (comp >= s.n_out) break;
-    if (busy) {
-#pragma unroll
-      for (int p = 0; p < P; ++p) {
-        // d_y or d_z of pencil col0 + p (lane l holds the x rows of all P pencils here)
-        const int kzp = min(g.kz0 + col0 + p, half);
-        const float d = comp == 1 ? dy : (kzp == half ? 0.f : kf * kzp);
-#pragma unroll
-        for (int j = 0; j < R1; ++j) {
-          const float2 v = u[p * R1 + j];
-          T[(lane + 32 * j) * LD + col0 + p] = make_float2(d * v.x, d * v.y);
-        }
-      }
+  __syncthreads();
+  // y and z components in one pass over V: d_y is the tile's, d_z each column's
+  float2* out_y = s.out + plane;
+  float2* out_z = s.n_out > 2 ? s.out + 2 * plane : nullptr;
+  for (int e = threadIdx.x; e < n * TK; e += blockDim.x) {
+    const int x = e / TK, c = e - x * TK;
+    if (c >= g.width) continue;
+    const float2 v = T[x * LD + c];
+    const int64_t o = (static_cast<int64_t>(x) * n + g.ky) * nzp + g.kz0 + c;
+    out_y[o] = make_float2(dy * v.x, dy * v.y);
+    if (out_z) {
+      const int kzc = g.kz0 + c;
+      const float dz = kzc == half ? 0.f : kf * kzc;
+      out_z[o] = make_float2(dz * v.x, dz * v.y);
     }
-    __syncthreads();
-    store_tile<TK, LD>(s.out + comp * plane, n, nzp, g, T);
-    __syncthreads();
   }
+  __syncthreads();
 }
 
-template <int R1>
+template <int R1, bool TWO>
 __global__ void __launch_bounds__(kXWarps * 32, 1)
     xpass_kernel(const float2* __restrict__ in, int n, int nzc, int nzp, int kz_tiles, float kf, float scale,
                  const float2* __restrict__ tw, XpassSet a, XpassSet b) {
@@ -275,7 +292,7 @@ __global__ void __launch_bounds__(kXWarps * 32, 1)
   for (int i = tid; i < R1 * 32 + 32 * 32; i += blockDim.x) sm[i] = tw[i];
   for (int i = tid; i < n; i += blockDim.x) {
     wxa[i] = __ldg(a.wxy + i);
-    wxb[i] = b.n_out > 0 ? __ldg(b.wxy + i) : 0.f;
+    wxb[i] = TWO ? __ldg(b.wxy + i) : 0.f;
   }
   const int n_tiles = n * kz_tiles;
   const int64_t plane = static_cast<int64_t>(n) * n * nzp;
@@ -324,8 +341,21 @@ __global__ void __launch_bounds__(kXWarps * 32, 1)
     const float kyf = kf * ny, kzf = kf * kz;
     const float k2yz = kyf * kyf + kzf * kzf;
     const float dy = ny == -half ? 0.f : kyf;
-    one_set<R1>(a, wxa, X, T, g, col0, k1, lane, busy, n, nzp, kf, scale, kz, k2yz, dy, plane, twi);
-    if (b.n_out > 0) one_set<R1>(b, wxb, X, T, g, col0, k1, lane, busy, n, nzp, kf, scale, kz, k2yz, dy, plane, twi);
+    if (TWO) {
+      one_set<R1, false>(a, wxa, X, T, g, col0, k1, lane, busy, n, nzp, kf, scale, kz, k2yz, dy, plane, twi);
+      one_set<R1, false>(b, wxb, X, T, g, col0, k1, lane, busy, n, nzp, kf, scale, kz, k2yz, dy, plane, twi);
+    } else {
+      // one filter set: Y = i c X once, in place
+      if (busy) {
+        const float cyz = __ldg(a.wxy + g.ky) * __ldg(a.wz + kz);
+#pragma unroll
+        for (int k2 = 0; k2 < 32; ++k2) {
+          const float c = filter_c<R1>(a, wxa, n, k1, k2, kf, scale, k2yz, cyz);
+          X[k2] = make_float2(-c * X[k2].y, c * X[k2].x);
+        }
+      }
+      one_set<R1, true>(a, wxa, X, T, g, col0, k1, lane, busy, n, nzp, kf, scale, kz, k2yz, dy, plane, twi);
+    }
     cur ^= 1;
   }
   cp_async_wait<0>();
@@ -335,7 +365,7 @@ __global__ void __launch_bounds__(kXWarps * 32, 1)
 
 bool xpass_supported(int64_t n) { return n == 256 || n == 512 || n == 1024; }
 
-int64_t xpass_row(int64_t n) { return n / 2 + kXWarps * (1024 / n); }
+int64_t xpass_row(int64_t n) { return n / 2 + 1; }
 
 void xpass_twiddles(int64_t n, std::vector<float2>& tw) {
   const int r1 = static_cast<int>(n / 32);
@@ -354,7 +384,7 @@ void xpass_twiddles(int64_t n, std::vector<float2>& tw) {
     }
 }
 
-template <int R1>
+template <int R1, bool TWO>
 static hrt_status launch_r1(const void* in, int64_t n, double box, double pref, const float2* tw,
                             const XpassSet& a, const XpassSet& b, cudaStream_t s) {
   constexpr int P = 32 / R1, LD = kXWarps * P + 1;
@@ -365,12 +395,12 @@ static hrt_status launch_r1(const void* in, int64_t n, double box, double pref, 
   int dev = 0, sms = 0;
   HRT_CUDA(cudaGetDevice(&dev));
   HRT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  HRT_CUDA(cudaFuncSetAttribute(xpass_kernel<R1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  HRT_CUDA(cudaFuncSetAttribute(xpass_kernel<R1, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(smem)));
   const int tiles = static_cast<int>(n) * kz_tiles;
   const int grid = std::min(tiles, sms);
   const double scale = -pref / (static_cast<double>(n) * n * n);
-  xpass_kernel<R1><<<grid, kXWarps * 32, smem, s>>>(static_cast<const float2*>(in), static_cast<int>(n), nzc, nzp,
+  xpass_kernel<R1, TWO><<<grid, kXWarps * 32, smem, s>>>(static_cast<const float2*>(in), static_cast<int>(n), nzc, nzp,
                                                     kz_tiles, static_cast<float>(2.0 * M_PI / box),
                                                     static_cast<float>(scale), tw, a, b);
   HRT_LAUNCHED("xpass_kernel");
@@ -379,10 +409,11 @@ static hrt_status launch_r1(const void* in, int64_t n, double box, double pref, 
 
 hrt_status launch_xpass(const void* in, int64_t n, double box, double pref, const float2* tw, const XpassSet& a,
                         const XpassSet& b, cudaStream_t s) {
+  const bool two = b.n_out > 0;
   switch (n) {
-    case 256: return launch_r1<8>(in, n, box, pref, tw, a, b, s);
-    case 512: return launch_r1<16>(in, n, box, pref, tw, a, b, s);
-    case 1024: return launch_r1<32>(in, n, box, pref, tw, a, b, s);
+    case 256: return two ? launch_r1<8, true>(in, n, box, pref, tw, a, b, s) : launch_r1<8, false>(in, n, box, pref, tw, a, b, s);
+    case 512: return two ? launch_r1<16, true>(in, n, box, pref, tw, a, b, s) : launch_r1<16, false>(in, n, box, pref, tw, a, b, s);
+    case 1024: return two ? launch_r1<32, true>(in, n, box, pref, tw, a, b, s) : launch_r1<32, false>(in, n, box, pref, tw, a, b, s);
     default: return fail(HRT_ERR_INVALID_ARG, "x-pass needs a mesh side of 256, 512 or 1024");
   }
 }
