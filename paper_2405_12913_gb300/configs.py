@@ -123,6 +123,12 @@ COSMO_1024_SCALED = CosmoWorkload(name="cosmo_1024_recipe_at_128p_256m_512r", n_
                                   box=1000.0, a_init=0.02, n_forward=64, a_min=1.0 / 3.0, n_reverse=64, n_pix=512,
                                   fov_deg=10.0, source_steps=(32, 48, 64))
 
+# The 1024^3 recipe at half the side, same cell size (256^3 particles, 512^3 mesh, 500 Mpc/h box, 1024^2 rays over
+# 10 deg): a case of a few GB on the device for detailed counters of the full-size kernels.
+COSMO_512_HALF = CosmoWorkload(name="cosmo_256p_512m_1024r", n_side=256, n_mesh=512, box=500.0, a_init=0.02,
+                               n_forward=64, a_min=1.0 / 3.0, n_reverse=64, n_pix=1024, fov_deg=10.0,
+                               source_steps=(32, 48, 64))
+
 # Small case the FP64 oracle runs in seconds: mesh 60 (not a power of two), 20^3 particles (a ragged last
 # block), 60^2 rays, 8 forward and 8 reverse steps.
 COSMO_TINY = CosmoWorkload(name="cosmo_20p_60m_60r", n_side=20, n_mesh=60, box=120.0, a_init=0.05, n_forward=8,
@@ -137,5 +143,5 @@ COSMO_GRAD = CosmoWorkload(name="grad_8p_16m_16r", n_side=8, n_mesh=16, box=32.0
 COSMO_GRAD_256 = CosmoWorkload(name="grad_128p_256m_512r", n_side=128, n_mesh=256, box=256.0, a_init=0.02,
                                n_forward=32, a_min=0.5, n_reverse=16, n_pix=512, fov_deg=3.5, source_steps=(16,))
 
-WORKLOADS = {w.name: w for w in (POINT_MASS, COSMO_256, COSMO_1024, COSMO_1024_SCALED, COSMO_TINY,
+WORKLOADS = {w.name: w for w in (POINT_MASS, COSMO_256, COSMO_1024, COSMO_1024_SCALED, COSMO_512_HALF, COSMO_TINY,
                                          COSMO_GRAD, COSMO_GRAD_256)}
