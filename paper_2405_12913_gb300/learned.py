@@ -345,6 +345,38 @@ def compare(S: PairSpec, params: torch.Tensor, seeds, log=print):
             "plain_err_per_bin": ep.mean(axis=0).tolist(), "learned_err_per_bin": el.mean(axis=0).tolist()}
 
 
+def ell_within(ell, rel, tol: float = 0.01) -> float:
+    """Largest bin ell up to which every bin's relative error is within tol (0 if the first bin is not)."""
+    last = 0.0
+    for e, r in zip(ell, rel):
+        if not r <= tol:
+            break
+        last = float(e)
+    return last
+
+
+def ladder(S: PairSpec, params: torch.Tensor | None, seed: int, meshes=(256, 512, 768), log=print):
+    """Accuracy against speed on one held-out seed: for each coarse mesh the plain form (and at S.n_coarse the
+    learned form, if params are given) against the plain S.n_fine run: reverse co-evolution sim-steps/s, mean and
+    largest P(ell) error over the bins with ell <= S.ell_cut, and the ell up to which every bin is within 1 %."""
+    run(S, S.n_fine, seed)  # warm-up of plans and memory
+    kf, _, mf = run(S, S.n_fine, seed, timed=True)
+    ell, pf, cnt = power(S, kf)
+    sel = _bins(S, ell, cnt)
+    rows = [{"mesh": S.n_fine, "form": "plain", "sim_steps_per_s": S.n_reverse / (mf * 1e-3)}]
+    forms = [(m, None) for m in meshes] + ([(S.n_coarse, params)] if params is not None else [])
+    for m, w in forms:
+        run(S, m, seed, params=w)
+        k, _, ms = run(S, m, seed, params=w, timed=True)
+        rel = np.abs(power(S, k)[1][sel] / pf[sel] - 1.0)
+        row = {"mesh": m, "form": "learned" if w is not None else "plain",
+               "sim_steps_per_s": S.n_reverse / (ms * 1e-3), "mean_rel_err": float(rel.mean()),
+               "max_rel_err": float(rel.max()), "ell_within_1pct": ell_within(ell[sel], rel)}
+        rows.append(row)
+        log(str(row))
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser(description="train and evaluate the learned ray-force correction")
     ap.add_argument("--train-seeds", type=int, default=16)

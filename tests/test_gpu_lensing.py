@@ -121,3 +121,30 @@ def test_cosmological_coevolution_matches_oracle(hrt):
     alpha_o = theta0 - res.rays["theta"].numpy()
     alpha = theta0 - th
     assert np.abs(alpha - alpha_o).max() <= 1e-4 * np.abs(alpha_o).max()
+
+
+def test_cosmo_1024_recipe_at_128p_matches_oracle_fixture(hrt):
+    # The 1024^3 workload's recipe (box 1 Gpc/h, 64 + 64 steps, 10 deg field, sources z = 0.5, 1, 2) scaled to
+    # 128^3 particles / 256^3 mesh / 512^2 rays, against the FP64 oracle's outputs stored by
+    # tests/golden/make_cosmo_1024_recipe_128p.py: kappa P(ell) within 1e-3 in every bin, deflections within
+    # 1e-4 of the largest, maps within 1e-3 of the kappa rms at sampled pixels, particles within 1e-3 cell.
+    import os
+    from paper_2405_12913_gb300.configs import COSMO_1024_SCALED as W
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "cosmo_1024_recipe_128p.npz"))
+    noise = synthetic.white_noise(W.seed, W.n_side)
+    theta0 = synthetic.pixel_grid(W.n_pix, W.fov_deg * synthetic.DEGREE)
+    disp_1, mom_1, maps, th, pk = _cosmo_gpu(hrt, W, noise, theta0)
+    ip, ir = g["particle_index"], g["ray_index"]
+    cell = W.box / W.n_mesh
+    assert np.abs(disp_1[:, ip].T - g["disp"]).max() < 1e-3 * cell
+    assert np.abs(mom_1[:, ip].T - g["mom"]).max() < 1e-3 * float(g["mom_absmax"])
+    for s in W.source_steps:
+        err = np.abs(maps[s][:, ir] - g[f"maps_{s}"]).max()
+        assert err <= 1e-3 * float(g[f"kappa_rms_{s}"]), (s, err, float(g[f"kappa_rms_{s}"]))
+        ell, p, cnt = pk[s]
+        assert np.array_equal(cnt, g[f"count_{s}"])
+        ok = cnt > 0
+        rel = np.abs(p[ok] / g[f"power_{s}"][ok] - 1.0)
+        assert rel.max() <= 1e-3, (s, rel.max())
+    err = np.abs(th[ir] - g["theta"]).max()
+    assert err <= 1e-4 * float(g["alpha_absmax"]), (err, float(g["alpha_absmax"]))
