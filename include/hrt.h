@@ -389,6 +389,25 @@ hrt_status hrt_step(hrt_ctx* ctx, double a_next, int32_t source);
  * restores the plain ray kernel.  Takes effect at the next force evaluation (the next hrt_step). */
 hrt_status hrt_set_ray_correction(hrt_ctx* ctx, const float* params);
 
+/* Fixed learned correction of the ray force: g_table[nk] (device float32, copied) sampled uniformly on
+ * |k| in [0, kmax], multiplying the Green's function of the ray fields (linear interpolation, 1 beyond kmax),
+ * the same at every step; the a-independent form of hrt_set_ray_correction, which it replaces (and vice
+ * versa).  Needs ray_fields == 2 (HRT_ERR_STATE otherwise).  g_table == NULL removes it.  Takes effect at the
+ * next force evaluation. */
+hrt_status hrt_set_ray_kernel_table(hrt_ctx* ctx, const float* g_table, int32_t nk, double kmax);
+
+/* Checkpoint and resume of a context.  hrt_state_bytes gives the size of the state of the context as it is
+ * now (particles, rays, maps); hrt_save_state writes it into caller device memory buf (a header, then the
+ * displacements and momenta, the ray angles, momenta, A and B, and the maps) and synchronises the stream;
+ * HRT_ERR_INVALID_ARG if bytes is too small, HRT_ERR_STATE without particles.  hrt_load_state restores such a
+ * state into a context of the same particle and mesh sides (HRT_ERR_INVALID_ARG otherwise), reallocating its
+ * rays, and recomputes the PM force at the saved scale factor from the particles, so that stepping on gives
+ * the run that was saved (up to the rounding order of the deposit).  The learned correction and the profiling
+ * state are not part of it. */
+hrt_status hrt_state_bytes(hrt_ctx* ctx, size_t* bytes);
+hrt_status hrt_save_state(hrt_ctx* ctx, void* buf, size_t bytes);
+hrt_status hrt_load_state(hrt_ctx* ctx, const void* buf, size_t bytes);
+
 /* Kick the momenta from their time to the current a with the current force (synchronise). */
 hrt_status hrt_sync_particles(hrt_ctx* ctx);
 

@@ -209,6 +209,10 @@ struct hrt_ctx {
   void* corr_wb = nullptr;
   float* corr_x = nullptr;
   float* corr_table = nullptr;
+  // fixed learned table of the ray fields (NULL: none); exclusive with the network above
+  float* ray_table = nullptr;
+  int32_t ray_table_nk = 0;
+  double ray_table_kmax = 0.0;
 };
 
 namespace hrt {
@@ -575,6 +579,10 @@ static hrt_status ctx_solve(hrt_ctx* ctx) {
     fr.g_table = ctx->corr_table;
     fr.g_nk = kCorrectionRows;
     fr.g_kmax = kCorrectionKmaxCell / cell;
+  } else if (ctx->ray_table) {
+    fr.g_table = ctx->ray_table;
+    fr.g_nk = ctx->ray_table_nk;
+    fr.g_kmax = ctx->ray_table_kmax;
   }
   cudaEvent_t wait = ctx->rays_pending ? ctx->ev_rays : nullptr;
   ctx->rays_pending = false;
@@ -1192,6 +1200,7 @@ hrt_status hrt_destroy(hrt_ctx* ctx) {
   device_free(ctx->corr_wb, s);
   device_free(ctx->corr_x, s);
   device_free(ctx->corr_table, s);
+  device_free(ctx->ray_table, s);
   cudaStreamSynchronize(s);
   if (ctx->ev_fields) cudaEventDestroy(ctx->ev_fields);
   if (ctx->ev_rays) cudaEventDestroy(ctx->ev_rays);
@@ -1429,6 +1438,128 @@ hrt_status hrt_read_grad(hrt_ctx* ctx, float* grad) {
   if (!ctx->have_particles) return fail(HRT_ERR_STATE, "no force yet");
   const size_t n = ctx->cfg.n_mesh;
   return ctx_mark(ctx, cuda_status(cudaMemcpyAsync(grad, ctx->grad, 3 * n * n * n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream), "read grad"));
+}
+
+hrt_status hrt_set_ray_kernel_table(hrt_ctx* ctx, const float* g, int32_t nk, double kmax) {
+  HRT_TRY(ctx_guard(ctx));
+  if (ctx->cfg.ray_fields != 2) return fail(HRT_ERR_STATE, "a ray kernel table needs ray_fields == 2");
+  cudaStream_t st = ctx->stream;
+  device_free(ctx->ray_table, st);
+  ctx->ray_table = nullptr;
+  ctx->ray_table_nk = 0;
+  if (!g) return HRT_OK;
+  if (nk < 2 || !(kmax > 0.0) || !std::isfinite(kmax)) return fail(HRT_ERR_INVALID_ARG, "table needs nk >= 2, kmax > 0");
+  float* t = nullptr;
+  HRT_TRY(device_alloc(reinterpret_cast<void**>(&t), static_cast<size_t>(nk) * sizeof(float), st, "ray table"));
+  hrt_status s = cuda_status(cudaMemcpyAsync(t, g, static_cast<size_t>(nk) * sizeof(float), cudaMemcpyDeviceToDevice, st),
+                             "copy ray table");
+  if (s != HRT_OK) {
+    device_free(t, st);
+    return ctx_mark(ctx, s);
+  }
+  // the network-based correction and a fixed table are exclusive
+  if (ctx->corr_w) HRT_TRY(hrt_set_ray_correction(ctx, nullptr));
+  ctx->ray_table = t;
+  ctx->ray_table_nk = nk;
+  ctx->ray_table_kmax = kmax;
+  return HRT_OK;
+}
+
+// ---- checkpoint / resume: a header, then the particle and ray state and the maps, in caller device memory
+namespace hrt {
+struct StateHeader {
+  uint64_t magic;
+  int64_t n_side, n_mesh, n_rays;
+  int32_t n_sources, have_particles;
+  double a, a_mom;
+  uint64_t bytes;
+};
+constexpr uint64_t kStateMagic = 0x3154415453545248ull;  // "HRTSTAT1"
+
+static size_t state_bytes(const hrt_ctx* ctx) {
+  const size_t np = static_cast<size_t>(ctx->cfg.n_side * ctx->cfg.n_side * ctx->cfg.n_side);
+  const size_t r = static_cast<size_t>(ctx->rays.n_rays);
+  const size_t maps = ctx->maps ? 4 * r * static_cast<size_t>(ctx->cfg.n_sources) : 0;
+  return 256 + 6 * np * sizeof(float) + r * (2 * sizeof(double) + 10 * sizeof(float)) + maps * sizeof(float);
+}
+}  // namespace hrt
+
+hrt_status hrt_state_bytes(hrt_ctx* ctx, size_t* bytes) {
+  HRT_TRY(ctx_guard(ctx));
+  if (!bytes) return fail(HRT_ERR_INVALID_ARG, "bytes is NULL");
+  *bytes = state_bytes(ctx);
+  return HRT_OK;
+}
+
+hrt_status hrt_save_state(hrt_ctx* ctx, void* buf, size_t bytes) {
+  HRT_TRY(ctx_guard(ctx));
+  if (!buf) return fail(HRT_ERR_INVALID_ARG, "buffer is NULL");
+  if (!ctx->have_particles) return fail(HRT_ERR_STATE, "no particles to save");
+  const size_t need = state_bytes(ctx);
+  if (bytes < need) return fail(HRT_ERR_INVALID_ARG, "state needs %zu bytes, buffer has %zu", need, bytes);
+  StateHeader h{kStateMagic, ctx->cfg.n_side, ctx->cfg.n_mesh, ctx->rays.n_rays, ctx->maps ? ctx->cfg.n_sources : 0,
+                1, ctx->a, ctx->a_mom, need};
+  const size_t np3 = 3 * static_cast<size_t>(ctx->cfg.n_side * ctx->cfg.n_side * ctx->cfg.n_side);
+  const size_t r = static_cast<size_t>(ctx->rays.n_rays);
+  cudaStream_t st = ctx->stream;
+  char* p = static_cast<char*>(buf);
+  hrt_status s = cuda_status(cudaMemcpyAsync(p, &h, sizeof(h), cudaMemcpyHostToDevice, st), "save header");
+  p += 256;
+  auto put = [&](const void* src, size_t n) {
+    if (s == HRT_OK && n) s = cuda_status(cudaMemcpyAsync(p, src, n, cudaMemcpyDeviceToDevice, st), "save state");
+    p += n;
+  };
+  put(ctx->disp, np3 * sizeof(float));
+  put(ctx->mom, np3 * sizeof(float));
+  put(ctx->rays.theta, 2 * r * sizeof(double));
+  put(ctx->rays.eta, 2 * r * sizeof(float));
+  put(ctx->rays.A, 4 * r * sizeof(float));
+  put(ctx->rays.B, 4 * r * sizeof(float));
+  if (ctx->maps) put(ctx->maps, 4 * r * static_cast<size_t>(ctx->cfg.n_sources) * sizeof(float));
+  // the header copy reads host memory on the stream: wait before it goes out of scope
+  if (s == HRT_OK) s = cuda_status(cudaStreamSynchronize(st), "save state");
+  return ctx_mark(ctx, s);
+}
+
+hrt_status hrt_load_state(hrt_ctx* ctx, const void* buf, size_t bytes) {
+  HRT_TRY(ctx_guard(ctx));
+  if (!buf || bytes < 256) return fail(HRT_ERR_INVALID_ARG, "state buffer is NULL or too small");
+  StateHeader h{};
+  cudaStream_t st = ctx->stream;
+  HRT_TRY(ctx_mark(ctx, cuda_status(cudaMemcpyAsync(&h, buf, sizeof(h), cudaMemcpyDeviceToHost, st), "load header")));
+  HRT_TRY(ctx_mark(ctx, cuda_status(cudaStreamSynchronize(st), "load header")));
+  if (h.magic != kStateMagic) return fail(HRT_ERR_INVALID_ARG, "not a saved HRT state");
+  if (h.n_side != ctx->cfg.n_side || h.n_mesh != ctx->cfg.n_mesh)
+    return fail(HRT_ERR_INVALID_ARG, "saved state is for %lld particles per side and mesh %lld",
+                static_cast<long long>(h.n_side), static_cast<long long>(h.n_mesh));
+  if (h.bytes > bytes) return fail(HRT_ERR_INVALID_ARG, "state buffer shorter than the saved state");
+  if (h.n_sources > ctx->cfg.n_sources) return fail(HRT_ERR_INVALID_ARG, "saved state has more source planes");
+  if (!(h.a > 0.0 && h.a <= 1.0) || !(h.a_mom > 0.0 && h.a_mom <= 1.0)) return fail(HRT_ERR_INVALID_ARG, "bad scale factors");
+  const size_t np3 = 3 * static_cast<size_t>(h.n_side * h.n_side * h.n_side);
+  const size_t r = static_cast<size_t>(h.n_rays);
+  const char* p = static_cast<const char*>(buf) + 256;
+  hrt_status s = HRT_OK;
+  auto get = [&](void* dst, size_t n) {
+    if (s == HRT_OK && n) s = cuda_status(cudaMemcpyAsync(dst, p, n, cudaMemcpyDeviceToDevice, st), "load state");
+    p += n;
+  };
+  get(ctx->disp, np3 * sizeof(float));
+  get(ctx->mom, np3 * sizeof(float));
+  if (s != HRT_OK) return ctx_mark(ctx, s);
+  if (r > 0) {
+    // reallocates the ray state and the maps for r rays (initialised from the saved angles, then overwritten)
+    HRT_TRY(hrt_init_rays(ctx, reinterpret_cast<const double*>(p), static_cast<int64_t>(r)));
+    get(ctx->rays.theta, 2 * r * sizeof(double));
+    get(ctx->rays.eta, 2 * r * sizeof(float));
+    get(ctx->rays.A, 4 * r * sizeof(float));
+    get(ctx->rays.B, 4 * r * sizeof(float));
+    if (h.n_sources > 0 && ctx->maps) get(ctx->maps, 4 * r * static_cast<size_t>(h.n_sources) * sizeof(float));
+  }
+  if (s != HRT_OK) return ctx_mark(ctx, s);
+  ctx->a = ctx->cfg.static_mode ? 1.0 : h.a;
+  ctx->a_mom = ctx->cfg.static_mode ? 1.0 : h.a_mom;
+  ctx->have_particles = true;
+  return ctx_mark(ctx, ctx_force(ctx));
 }
 
 hrt_status hrt_ctx_kappa_power(hrt_ctx* ctx, int32_t source, int64_t m, double dtheta, int32_t nbins, double ell_min,

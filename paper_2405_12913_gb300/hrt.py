@@ -89,6 +89,10 @@ _SIGS = {
     "hrt_step": ([_P, _D, _I32], C.c_int),
     "hrt_sync_particles": ([_P], C.c_int),
     "hrt_set_ray_correction": ([_P, _P], C.c_int),
+    "hrt_set_ray_kernel_table": ([_P, _P, _I32, C.c_double], C.c_int),
+    "hrt_state_bytes": ([_P, _P], C.c_int),
+    "hrt_save_state": ([_P, _P, C.c_size_t], C.c_int),
+    "hrt_load_state": ([_P, _P, C.c_size_t], C.c_int),
     "hrt_step_static": ([_P, _D, _D, _I32], C.c_int),
     "hrt_drift_free": ([_P, _D, _D], C.c_int),
     "hrt_read_rays": ([_P, _P, _P, _P, _P], C.c_int),
@@ -546,6 +550,26 @@ class Context:
         if params is not None and params.numel() != MLP_PARAMS:
             raise ValueError(f"params must hold {MLP_PARAMS} values")
         _check(_lib.hrt_set_ray_correction(self._h, _ptr(params, torch.float32, "params")), "hrt_set_ray_correction")
+
+    def hrt_set_ray_kernel_table(self, table: torch.Tensor | None, kmax: float = 0.0):
+        """Fixed learned table of the ray fields over |k| in [0, kmax] (float32 on the device), or None."""
+        _check(_lib.hrt_set_ray_kernel_table(self._h, _ptr(table, torch.float32, "table"),
+                                             0 if table is None else table.numel(), kmax), "hrt_set_ray_kernel_table")
+
+    def hrt_state_bytes(self) -> int:
+        n = C.c_size_t()
+        _check(_lib.hrt_state_bytes(self._h, C.byref(n)), "hrt_state_bytes")
+        return n.value
+
+    def hrt_save_state(self) -> torch.Tensor:
+        """The context's state in a new device byte tensor (synchronises the stream)."""
+        buf = torch.empty(self.hrt_state_bytes(), dtype=torch.uint8, device="cuda")
+        _check(_lib.hrt_save_state(self._h, _ptr(buf, torch.uint8, "buf"), buf.numel()), "hrt_save_state")
+        return buf
+
+    def hrt_load_state(self, buf: torch.Tensor):
+        _check(_lib.hrt_load_state(self._h, _ptr(buf, torch.uint8, "buf"), buf.numel()), "hrt_load_state")
+        self.n_rays = int(self.hrt_ctx_rays().n_rays)
 
     def hrt_sync_particles(self):
         _check(_lib.hrt_sync_particles(self._h), "hrt_sync_particles")

@@ -159,3 +159,43 @@ def test_context_correction_needs_ray_fields_and_resets(hrt):
     scale = k_plain.abs().max().item()
     assert (diff > 1e-5 * scale).float().mean().item() <= 2e-3  # rare cell-face crossings, as above
     assert diff.median().item() <= 1e-6 * scale
+
+
+def test_context_fixed_ray_table_matches_ray_trainer(hrt):
+    # hrt_set_ray_kernel_table: a fixed g(|k|) on the ray fields, against the trainer's re-trace with the same
+    # table at every step
+    from dataclasses import replace
+
+    from paper_2405_12913_gb300 import learned
+    S = replace(learned.PairSpec(), n_side=32, n_coarse=32, n_fine=64, box=64.0, n_forward=6, n_reverse=4,
+                a_min=0.7, n_pix=64, fov_deg=4.0, nbins=6)
+    table = torch.linspace(1.4, 0.9, learned.N_TABLE, device="cuda")
+
+    class Fixed:
+        def table(self, x):
+            return table
+
+    k_plain, spectra = learned.plain_run(S, S.n_coarse, 11, record_spectra=True)
+    tr = learned.RayTrainer(S)
+    k_ref, _ = tr.forward(Fixed(), spectra, keep=False)
+    cfg = hrt.make_config(S.n_coarse, S.box, S.n_side, S.omega_m, S.h, S.n_s, S.sigma8, S.deconv_p,
+                          S.smooth_cells, 1.0, S.observer, n_sources=1, ray_fields=2, ray_deconv_p=S.deconv_p,
+                          ray_smooth_cells=S.smooth_cells)
+    ctx = hrt.Context(cfg)
+    ctx.hrt_set_ray_kernel_table(table, tr.kmax)
+    ctx.hrt_init_particles_zeldovich(learned._noise(11, S.n_side).reshape(-1), S.a_init)
+    for a in S.forward_grid[1:]:
+        ctx.hrt_step(a)
+    ctx.hrt_sync_particles()
+    ctx.hrt_init_rays(learned._theta0(S))
+    rg = S.reverse_grid
+    for n in range(S.n_reverse):
+        ctx.hrt_step(rg[n + 1], 0 if n + 1 == S.n_reverse else -1)
+    k_ctx = ctx.hrt_read_maps(0)[0].clone()
+    ctx.hrt_set_ray_kernel_table(None)
+    ctx.close()
+    scale = k_ref.abs().max().item()
+    diff = (k_ctx - k_ref).abs()
+    assert (diff > 1e-4 * scale).float().mean().item() <= 2e-3  # rare cell-face crossings
+    assert diff.median().item() <= 1e-6 * scale
+    assert (k_ctx - k_plain).abs().max().item() > 1e-3 * scale
