@@ -355,23 +355,29 @@ def ell_within(ell, rel, tol: float = 0.01) -> float:
     return last
 
 
-def ladder(S: PairSpec, params: torch.Tensor | None, seed: int, meshes=(256, 512, 768), log=print):
+def ladder(S: PairSpec, params: torch.Tensor | None, seed: int, meshes=(256, 512, 768), cuts=None, log=print):
     """Accuracy against speed on one held-out seed: for each coarse mesh the plain form (and at S.n_coarse the
-    learned form, if params are given) against the plain S.n_fine run: reverse co-evolution sim-steps/s, mean and
-    largest P(ell) error over the bins with ell <= S.ell_cut, and the ell up to which every bin is within 1 %."""
+    learned form, if params are given) against the plain S.n_fine run: reverse co-evolution sim-steps/s, and
+    for each ell cut (default S.ell_cut) the mean and largest P(ell) error over the bins with ell <= cut and the
+    ell up to which every bin is within 1 %."""
+    cuts = tuple(cuts) if cuts else (S.ell_cut,)
     run(S, S.n_fine, seed)  # warm-up of plans and memory
     kf, _, mf = run(S, S.n_fine, seed, timed=True)
     ell, pf, cnt = power(S, kf)
-    sel = _bins(S, ell, cnt)
     rows = [{"mesh": S.n_fine, "form": "plain", "sim_steps_per_s": S.n_reverse / (mf * 1e-3)}]
     forms = [(m, None) for m in meshes] + ([(S.n_coarse, params)] if params is not None else [])
     for m, w in forms:
         run(S, m, seed, params=w)
         k, _, ms = run(S, m, seed, params=w, timed=True)
-        rel = np.abs(power(S, k)[1][sel] / pf[sel] - 1.0)
+        p = power(S, k)[1]
         row = {"mesh": m, "form": "learned" if w is not None else "plain",
-               "sim_steps_per_s": S.n_reverse / (ms * 1e-3), "mean_rel_err": float(rel.mean()),
-               "max_rel_err": float(rel.max()), "ell_within_1pct": ell_within(ell[sel], rel)}
+               "sim_steps_per_s": S.n_reverse / (ms * 1e-3), "errors": {}}
+        for cut in cuts:
+            sel = (cnt > 0) & (ell <= cut)
+            rel = np.abs(p[sel] / pf[sel] - 1.0)
+            row["errors"][f"ell_le_{cut:g}"] = {"bins": int(sel.sum()), "mean_rel_err": float(rel.mean()),
+                                                "max_rel_err": float(rel.max()),
+                                                "ell_within_1pct": ell_within(ell[sel], rel)}
         rows.append(row)
         log(str(row))
     return rows
@@ -388,8 +394,11 @@ def main():
     ap.add_argument("--compare-n-pix", type=int, default=4096,
                     help="rays per side of the learned/plain/fine comparison on the held-out seeds (0: skip)")
     ap.add_argument("--params", default=None, help="skip training: compare with these parameters (.npy)")
+    ap.add_argument("--ell-cut", type=float, default=PairSpec.ell_cut, help="largest bin ell in the training loss")
+    ap.add_argument("--ladder-n-pix", type=int, default=0,
+                    help="rays per side of the accuracy-vs-speed ladder on the first held-out seed (0: skip)")
     a = ap.parse_args()
-    S = replace(PairSpec(), n_pix=a.n_pix)
+    S = replace(PairSpec(), n_pix=a.n_pix, ell_cut=a.ell_cut)
     test = list(range(100, 100 + a.test_seeds))
     out = {}
     if a.params:
@@ -403,6 +412,9 @@ def main():
         out["training"]["loss_first_last"] = [res["history"][0], res["history"][-1]]
     if a.compare_n_pix:
         out["comparison"] = compare(replace(S, n_pix=a.compare_n_pix), w, test, log=lambda m: print(m, flush=True))
+    if a.ladder_n_pix:
+        out["ladder"] = ladder(replace(S, n_pix=a.ladder_n_pix), w, test[0],
+                               cuts=sorted({a.ell_cut, PairSpec.ell_cut}), log=lambda m: print(m, flush=True))
     print(json.dumps(out))
 
 
