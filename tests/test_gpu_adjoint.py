@@ -328,3 +328,57 @@ def test_deflection_loss_gradient_matches_central_differences(hrt):
 
     assert float(om.grad) == pytest.approx(_tiny_fd(oracle_loss, W.omega_m), rel=1e-3)
     sim.close()
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_pm_solve_adjoint_dot_product_at_256(hrt, split):
+    # the PM solve is linear in rho: <PM rho, gbar> = <rho, PM^T gbar> at any size (here 256^3, the
+    # differentiation workload's mesh; the forward solve on the split and on the 3D path)
+    n, box, pref = 256, 256.0, 0.9
+    g = torch.Generator(device="cuda").manual_seed(7)
+    rho = torch.randn(n ** 3, device="cuda", generator=g)
+    gbar = torch.randn(3, n ** 3, device="cuda", generator=g)
+    pm = hrt.PM(n, box)
+    pm.set_split(split)
+    f = hrt.make_filter(4.0, box / n)
+    grad = torch.empty(3, n ** 3, device="cuda")
+    pm.solve(rho.clone(), pref, f, grad)
+    rb = torch.empty(n ** 3, device="cuda")
+    pm.solve_adjoint(gbar.clone(), pref, f, rb)
+    lhs = float((grad.double() * gbar.double()).sum())
+    rhs = float((rho.double() * rb.double()).sum())
+    assert lhs == pytest.approx(rhs, rel=1e-5), (lhs, rhs)
+    pm.close()
+
+
+def test_power_loss_gradient_at_128p_256m_matches_central_differences(hrt):
+    # the differentiation workload (128^3 white-noise modes, 256^3 mesh, 512^2 rays, checkpoint every 4 steps):
+    # loss = sum over the log ell bins of (P(ell) - P_target(ell))^2; the adjoint's derivative along a random
+    # noise direction against central differences with eps = 1e-3.  kappa jumps where line-of-sight samples
+    # cross cell faces (measured spread of the differences over eps = 1e-4 .. 3e-3: about 2 %), hence 3 %.
+    from paper_2405_12913_gb300 import autodiff
+    from paper_2405_12913_gb300.configs import COSMO_GRAD_256 as W
+    noise = _cuda(synthetic.white_noise(W.seed, W.n_side)).reshape(-1)
+    theta0 = torch.tensor(synthetic.pixel_grid(W.n_pix, W.fov_deg * synthetic.DEGREE))
+    lmin, lmax = W.ell_range
+    sim = autodiff.DiffSim(W, theta0, checkpoint_every=4)
+    om = torch.tensor(W.omega_m, dtype=torch.float64)
+
+    def loss(wn, target, scale):
+        kap, _ = autodiff.HRTKappa.apply(wn, om, sim)
+        p = autodiff.KappaPower.apply(kap[0], W.n_pix, W.dtheta, W.nbins, lmin, lmax)
+        return ((p - target) ** 2).sum() / scale
+
+    with torch.no_grad():
+        kap, _ = autodiff.HRTKappa.apply(noise, om, sim)
+        target = 0.8 * autodiff.KappaPower.apply(kap[0], W.n_pix, W.dtheta, W.nbins, lmin, lmax)
+    scale = float((target ** 2).sum())
+    w = noise.clone().requires_grad_(True)
+    loss(w, target, scale).backward()
+    d = _cuda(synthetic.gaussian_field(74, (W.n_side ** 3,)))
+    ad = float((w.grad.double() * d.double()).sum())
+    eps = 1e-3
+    with torch.no_grad():
+        fd = (float(loss(noise + eps * d, target, scale)) - float(loss(noise - eps * d, target, scale))) / (2 * eps)
+    assert ad == pytest.approx(fd, rel=3e-2), (ad, fd)
+    sim.close()
