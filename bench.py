@@ -104,6 +104,28 @@ class ClockSampler:
                 "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
 
 
+# ----------------------------------------------------------------------------------------------- replicas
+def replica_seed(W, rank: int) -> int:
+    """Each rank runs an independent replica of the workload on its own seed."""
+    return W.seed + rank
+
+
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time (the job's time); `device` is the rank's device ("cpu" under gloo)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(steps: int, ms_max: float, world: int) -> float:
+    """Whole-job sim-steps/s: every rank did `steps` steps, the job took the slowest rank's time."""
+    return world * steps / (ms_max / 1e3)
+
+
 # ----------------------------------------------------------------------------------------------- helpers
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -170,7 +192,7 @@ def run_gpu(args, W, world, rank, local):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    seed = W.seed + rank
+    seed = replica_seed(W, rank)
     cfg = hrt.make_config(W.n_mesh, W.box, W.n_side, W.omega_m, W.h, W.n_s, W.sigma8, W.deconv_p, W.smooth_cells,
                           W.samples_per_cell, W.observer, n_sources=len(W.source_steps))
     ctx = hrt.Context(cfg)
@@ -219,14 +241,8 @@ def run_gpu(args, W, world, rank, local):
     t1.record(stream)
     barrier()
     clk = clocks.stop()
-    ms = t0.elapsed_time(t1)
-    ms_max = ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * args.steps / (ms_max / 1e3)
+    ms_max = max_over_ranks(t0.elapsed_time(t1), world, dev)
+    value = replica_rate(args.steps, ms_max, world)
 
     # per-phase timing pass (CUDA events on the context stream around each kernel of the step)
     reset()
@@ -278,13 +294,8 @@ def run_gpu(args, W, world, rank, local):
         d2h += 4
         e1.record(stream)
         barrier()
-        e_ms = e0.elapsed_time(e1)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": world * args.steps / (e_ms / 1e3), "unit": UNIT,
+        e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        e2e = {"value": replica_rate(args.steps, e_ms, world), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps)}
 
     # roofline of the dominant kernel of this library (by time in the phase pass)
