@@ -264,39 +264,52 @@ def _bins(S: PairSpec, ell, cnt):
     return (cnt > 0) & (ell <= S.ell_cut)
 
 
-def train(S: PairSpec, train_seeds, test_seeds, iters: int = 60, lr: float = 2e-3, log=print):
+def train(S: PairSpec, train_seeds, test_seeds, iters: int = 60, lr: float = 2e-3, log=print, meshes=None):
+    """Adam on the MLP parameters: loss = mean over coarse meshes and training seeds of sum over the bins with
+    ell <= S.ell_cut of (P_coarse / P_fine - 1)^2, each coarse mesh paired with the S.n_fine run of the same ICs
+    (meshes: the coarse sides, default S.n_coarse; ln N_mesh is an input, so one network serves them all)."""
+    meshes = tuple(meshes) if meshes else (S.n_coarse,)
     t0 = time.time()
     fine, spectra, plain_p = {}, {}, {}
     for s in list(train_seeds) + list(test_seeds):
         kf, _ = plain_run(S, S.n_fine, s)
         ell, pf, cnt = power(S, kf)
-        kc, sp = plain_run(S, S.n_coarse, s, record_spectra=True)
-        _, pc, _ = power(S, kc)
-        fine[s], spectra[s], plain_p[s] = pf, sp, pc
+        fine[s] = pf
+        for m in meshes:
+            kc, sp = plain_run(S, m, s, record_spectra=True)
+            spectra[(m, s)], plain_p[(m, s)] = sp, power(S, kc)[1]
     sel = _bins(S, ell, cnt)
-    log(f"paired runs: {len(fine)} seeds in {time.time() - t0:.1f} s")
-    trainer = RayTrainer(S)
+    log(f"paired runs: {len(fine)} seeds x {len(meshes)} meshes in {time.time() - t0:.1f} s")
+    trainers = {m: RayTrainer(replace(S, n_coarse=m)) for m in meshes}
     mlp = MLP(seed=0)
     history = []
+    norm = len(train_seeds) * len(meshes)
+    lmin, lmax = S.ell_range
     for it in range(iters):
         grad = torch.zeros(hrt.MLP_PARAMS, device="cuda")
         loss = 0.0
-        for s in train_seeds:
-            kappa, saved = trainer.forward(mlp, spectra[s], keep=True)
-            _, p, _ = power(S, kappa)
-            r = p / fine[s] - 1.0
-            loss += float((r[sel] ** 2).sum()) / len(train_seeds)
-            p_bar = np.where(sel, 2.0 * r / fine[s], 0.0) / len(train_seeds)
-            kb = torch.empty_like(kappa)
-            lmin, lmax = S.ell_range
-            hrt.hrt_kappa_power_adjoint(kappa, S.n_pix, S.dtheta, S.nbins, lmin, lmax, p_bar, kb)
-            trainer.backward(mlp, spectra[s], saved, kb, grad)
-            del saved
+        for m in meshes:
+            for s in train_seeds:
+                kappa, saved = trainers[m].forward(mlp, spectra[(m, s)], keep=True)
+                _, p, _ = power(S, kappa)
+                r = p / fine[s] - 1.0
+                loss += float((r[sel] ** 2).sum()) / norm
+                p_bar = np.where(sel, 2.0 * r / fine[s], 0.0) / norm
+                kb = torch.empty_like(kappa)
+                hrt.hrt_kappa_power_adjoint(kappa, S.n_pix, S.dtheta, S.nbins, lmin, lmax, p_bar, kb)
+                trainers[m].backward(mlp, spectra[(m, s)], saved, kb, grad)
+                del saved
         mlp.adam(grad, lr)
         history.append(loss)
         if it % 10 == 0 or it == iters - 1:
             log(f"iter {it:3d} loss {loss:.4e} ({time.time() - t0:.1f} s)")
-    result = evaluate(S, trainer, mlp, test_seeds, fine, spectra, plain_p, sel)
+    per_mesh = {m: evaluate(S, trainers[m], mlp, test_seeds, fine, {s: spectra[(m, s)] for s in test_seeds},
+                            {s: plain_p[(m, s)] for s in test_seeds}, sel) for m in meshes}
+    result = dict(per_mesh[meshes[0]]) if len(meshes) == 1 else {
+        "per_mesh": per_mesh,
+        **{k: float(np.mean([r[k] for r in per_mesh.values()])) for k in
+           ("plain_mean_rel_err", "learned_mean_rel_err", "plain_max_rel_err", "learned_max_rel_err")}}
+    result["meshes"] = list(meshes)
     result["history"] = history
     result["train_seconds"] = time.time() - t0
     return mlp, result
@@ -355,9 +368,10 @@ def ell_within(ell, rel, tol: float = 0.01) -> float:
     return last
 
 
-def ladder(S: PairSpec, params: torch.Tensor | None, seed: int, meshes=(256, 512, 768), cuts=None, log=print):
-    """Accuracy against speed on one held-out seed: for each coarse mesh the plain form (and at S.n_coarse the
-    learned form, if params are given) against the plain S.n_fine run: reverse co-evolution sim-steps/s, and
+def ladder(S: PairSpec, params: torch.Tensor | None, seed: int, meshes=(256, 512, 768), cuts=None, log=print,
+           learned_meshes=None, learned_forms=None):
+    """Accuracy against speed on one held-out seed: for each coarse mesh the plain form, and the learned forms
+    (learned_forms: (mesh, parameters, name); else params at learned_meshes) against the plain S.n_fine run: reverse co-evolution sim-steps/s, and
     for each ell cut (default S.ell_cut) the mean and largest P(ell) error over the bins with ell <= cut and the
     ell up to which every bin is within 1 %."""
     cuts = tuple(cuts) if cuts else (S.ell_cut,)
@@ -365,12 +379,17 @@ def ladder(S: PairSpec, params: torch.Tensor | None, seed: int, meshes=(256, 512
     kf, _, mf = run(S, S.n_fine, seed, timed=True)
     ell, pf, cnt = power(S, kf)
     rows = [{"mesh": S.n_fine, "form": "plain", "sim_steps_per_s": S.n_reverse / (mf * 1e-3)}]
-    forms = [(m, None) for m in meshes] + ([(S.n_coarse, params)] if params is not None else [])
-    for m, w in forms:
+    lm = tuple(learned_meshes) if learned_meshes else (S.n_coarse,)
+    forms = [(m, None, "plain") for m in meshes]
+    if learned_forms:  # [(mesh, params, name)]
+        forms += list(learned_forms)
+    elif params is not None:
+        forms += [(m, params, "learned") for m in lm]
+    for m, w, name in forms:
         run(S, m, seed, params=w)
         k, _, ms = run(S, m, seed, params=w, timed=True)
         p = power(S, k)[1]
-        row = {"mesh": m, "form": "learned" if w is not None else "plain",
+        row = {"mesh": m, "form": name,
                "sim_steps_per_s": S.n_reverse / (ms * 1e-3), "errors": {}}
         for cut in cuts:
             sel = (cnt > 0) & (ell <= cut)
@@ -395,6 +414,7 @@ def main():
                     help="rays per side of the learned/plain/fine comparison on the held-out seeds (0: skip)")
     ap.add_argument("--params", default=None, help="skip training: compare with these parameters (.npy)")
     ap.add_argument("--ell-cut", type=float, default=PairSpec.ell_cut, help="largest bin ell in the training loss")
+    ap.add_argument("--meshes", default=None, help="coarse mesh sides to train on, e.g. 256,512 (default 256)")
     ap.add_argument("--ladder-n-pix", type=int, default=0,
                     help="rays per side of the accuracy-vs-speed ladder on the first held-out seed (0: skip)")
     a = ap.parse_args()
@@ -404,7 +424,9 @@ def main():
     if a.params:
         w = torch.tensor(np.load(a.params), dtype=torch.float32, device="cuda")
     else:
-        mlp, res = train(S, range(a.train_seeds), test, a.iters, a.lr, log=lambda m: print(m, flush=True))
+        meshes = tuple(int(x) for x in a.meshes.split(",")) if a.meshes else None
+        mlp, res = train(S, range(a.train_seeds), test, a.iters, a.lr, log=lambda m: print(m, flush=True),
+                         meshes=meshes)
         if a.out:
             np.save(a.out, mlp.state())
         w = mlp.w
@@ -414,7 +436,8 @@ def main():
         out["comparison"] = compare(replace(S, n_pix=a.compare_n_pix), w, test, log=lambda m: print(m, flush=True))
     if a.ladder_n_pix:
         out["ladder"] = ladder(replace(S, n_pix=a.ladder_n_pix), w, test[0],
-                               cuts=sorted({a.ell_cut, PairSpec.ell_cut}), log=lambda m: print(m, flush=True))
+                               cuts=sorted({a.ell_cut, PairSpec.ell_cut}), log=lambda m: print(m, flush=True),
+                               learned_meshes=tuple(int(x) for x in a.meshes.split(",")) if a.meshes else None)
     print(json.dumps(out))
 
 
