@@ -364,6 +364,11 @@ def learned_comparison(seed=100):
 
 
 # ----------------------------------------------------------------------------------------------- oracle (CPU)
+# The bounded sample of the workload the FP64 oracle steps through (particles per side, mesh side, rays per side):
+# about a second of host work per step, extrapolated linearly in the work units to the full size.
+ORACLE_SAMPLE = (128, 256, 512)
+
+
 def oracle_sample(W, n_side, n_mesh, n_pix, seed=7):
     """Times one reverse sim-step of the FP64 oracle on a scaled copy of the workload (same box and field of
     view; particles, mesh and rays reduced), and extrapolates linearly in the work units to the full size.
@@ -417,7 +422,7 @@ def oracle_sample(W, n_side, n_mesh, n_pix, seed=7):
 def run_reference(args, W, rank):
     if rank != 0:
         return None
-    sizes = (32, 64, 128)  # n_side, n_mesh, n_pix per sampled step
+    sizes = ORACLE_SAMPLE  # n_side, n_mesh, n_pix per sampled step
     for _ in range(args.warmup):
         oracle_sample(W, *sizes)
     per = []
@@ -453,7 +458,7 @@ def main():
     if world == 1 and not args.no_learned:
         line["learned"] = learned_comparison()
     if world == 1 and not args.no_cpu_baseline:
-        full, desc, threads = oracle_sample(W, 128, 256, 512)
+        full, desc, threads = oracle_sample(W, *ORACLE_SAMPLE)
         line["cpu_baseline"] = {"value": 1.0 / full, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": desc}
     print(json.dumps(line))
