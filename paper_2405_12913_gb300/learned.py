@@ -3,8 +3,9 @@
 The paper sharpens the PM force with a trained factor g in k/k^2 -> (k/k^2) g (Sec. 6.2).  Here g = 1 + MLP(|k| cell,
 a, ln N_mesh) multiplies the Green's function of the ray gradient fields of a coarse mesh (the particles keep the
 plain force), and is trained so that the convergence power spectrum of the coarse run matches that of a run with
-the same initial conditions on a mesh four times finer.  The plain kernel (g = 1) is both the fallback and the
-judge: ``evaluate`` reports the P(ell) error of both forms against the fine run on held-out seeds.
+the same initial conditions on a mesh four times finer.  The plain kernel (g = 1) is the fallback and the
+yardstick: ``evaluate``, ``compare`` and ``ladder`` report the P(ell) error of both forms against the fine run on
+held-out seeds.
 
 Training uses only libhrt kernels: the tensor-core MLP forward, the ray-step and k-space-table adjoints, the FP32
 MLP backward and an Adam kernel.  The particles do not depend on g, so the density spectrum of each reverse step is
