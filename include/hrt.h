@@ -408,6 +408,13 @@ hrt_status hrt_state_bytes(hrt_ctx* ctx, size_t* bytes);
 hrt_status hrt_save_state(hrt_ctx* ctx, void* buf, size_t bytes);
 hrt_status hrt_load_state(hrt_ctx* ctx, const void* buf, size_t bytes);
 
+/* One co-evolution step as hrt_step, with the rays' readout accumulated instead of written: map `source` (>= 0)
+ * += weight * (kappa, gamma1, gamma2, omega) of the rays at the end of the step.  Called at every reverse step
+ * with weight = n_g(chi_n), it builds the observable O = sum_n n_g(chi_n) O_n of a source distribution n_g
+ * (Eq. obs_accum); the weights are the caller's, normalised as it chooses.  Maps start at zero after
+ * hrt_init_rays.  HRT_ERR_INVALID_ARG for source < 0 or a non-finite weight. */
+hrt_status hrt_step_accumulate(hrt_ctx* ctx, double a_next, int32_t source, double weight);
+
 /* Kick the momenta from their time to the current a with the current force (synchronise). */
 hrt_status hrt_sync_particles(hrt_ctx* ctx);
 

@@ -117,6 +117,8 @@ static hrt_status build_ray_params(const hrt_ray_geom& g, double chi_from, doubl
   const double d1_ref = a_ref > 0.0 ? cosmo.D1(a_ref) : 1.0;
   p.n = static_cast<int>(g.n);
   p.tile_w = 0;
+  p.map_accumulate = 0;
+  p.map_weight = 1.f;
   p.cell = cell;
   p.box = g.box;
   p.obs_x = g.observer[0];
@@ -612,7 +614,7 @@ static hrt_ray_geom ctx_geom(const hrt_config& c) {
 }
 
 static hrt_status ctx_ray_step(hrt_ctx* ctx, double chi_from, double chi_to, double a_ref, int32_t source,
-                               cudaStream_t stream) {
+                               cudaStream_t stream, double weight = 1.0, bool accumulate = false) {
   const hrt_config& c = ctx->cfg;
   if (source >= c.n_sources) return fail(HRT_ERR_INVALID_ARG, "source %d out of range", source);
   static thread_local RayStepParams p;
@@ -622,6 +624,8 @@ static hrt_status ctx_ray_step(hrt_ctx* ctx, double chi_from, double chi_to, dou
   if (w * w == ctx->rays.n_rays) g.image_width = w;
   HRT_TRY(build_ray_params(g, chi_from, chi_to, a_ref, c.cosmo.omega_m, p));
   set_tiles(g, ctx->rays.n_rays, p);
+  p.map_accumulate = accumulate ? 1 : 0;
+  p.map_weight = static_cast<float>(weight);
   const int64_t m = c.n_mesh * c.n_mesh * c.n_mesh;
   const float* gx = ctx->ray_grad ? ctx->ray_grad : ctx->grad;
   float* maps = source >= 0 ? ctx->maps + static_cast<int64_t>(source) * 4 * ctx->rays.n_rays : nullptr;
@@ -1293,7 +1297,19 @@ hrt_status hrt_init_rays(hrt_ctx* ctx, const double* theta0, int64_t n_rays) {
   return HRT_OK;
 }
 
-hrt_status hrt_step(hrt_ctx* ctx, double a_next, int32_t source) {
+namespace hrt {
+static hrt_status ctx_step(hrt_ctx* ctx, double a_next, int32_t source, double weight, bool accumulate);
+}
+
+hrt_status hrt_step(hrt_ctx* ctx, double a_next, int32_t source) { return ctx_step(ctx, a_next, source, 1.0, false); }
+
+hrt_status hrt_step_accumulate(hrt_ctx* ctx, double a_next, int32_t source, double weight) {
+  if (source < 0) return fail(HRT_ERR_INVALID_ARG, "accumulation needs a map (source >= 0)");
+  if (!std::isfinite(weight)) return fail(HRT_ERR_INVALID_ARG, "weight must be finite");
+  return ctx_step(ctx, a_next, source, weight, true);
+}
+
+hrt_status hrt::ctx_step(hrt_ctx* ctx, double a_next, int32_t source, double weight, bool accumulate) {
   HRT_TRY(ctx_guard(ctx));
   if (ctx->cfg.static_mode) return fail(HRT_ERR_STATE, "hrt_step needs the expanding mode");
   if (!ctx->have_particles) return fail(HRT_ERR_STATE, "no particles");
@@ -1305,12 +1321,13 @@ hrt_status hrt_step(hrt_ctx* ctx, double a_next, int32_t source) {
     if (ctx->profiling) {
       // serialised on the context stream so that each phase has its own time
       PhaseScope ps(ctx, 0);
-      s = ctx_ray_step(ctx, c.chi(ctx->a), c.chi(a_next), ctx->a, source, ctx->stream);
+      s = ctx_ray_step(ctx, c.chi(ctx->a), c.chi(a_next), ctx->a, source, ctx->stream, weight, accumulate);
     } else {
       // the ray step runs on the ray stream beside the particle update; the next force waits for it
       s = cuda_status(cudaEventRecord(ctx->ev_fields, ctx->stream), "record fields");
       if (s == HRT_OK) s = cuda_status(cudaStreamWaitEvent(ctx->ray_stream, ctx->ev_fields, 0), "wait fields");
-      if (s == HRT_OK) s = ctx_ray_step(ctx, c.chi(ctx->a), c.chi(a_next), ctx->a, source, ctx->ray_stream);
+      if (s == HRT_OK)
+        s = ctx_ray_step(ctx, c.chi(ctx->a), c.chi(a_next), ctx->a, source, ctx->ray_stream, weight, accumulate);
       if (s == HRT_OK) s = cuda_status(cudaEventRecord(ctx->ev_rays, ctx->ray_stream), "record rays");
       if (s == HRT_OK) ctx->rays_pending = true;
     }

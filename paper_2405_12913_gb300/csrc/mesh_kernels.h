@@ -39,6 +39,8 @@ struct RayStepParams {
   int n1, n2;            // nodes of the first and second half shell (after the force window)
   int n;                 // mesh cells per side
   int tile_w;            // > 0: rays form an image tile_w pixels wide, walked in 16 x 8 tiles
+  int map_accumulate;    // readout: 0 writes the observables, 1 adds map_weight times them
+  float map_weight;
   float drift;           // (chi_to - chi_from) / (c chi_mid^2), float32 copy for A
   double drift_d;        // the same in FP64 for theta
   double ref_r[2];       // reference radius of each half shell for the FP64 base position

@@ -153,10 +153,19 @@ __global__ void __launch_bounds__(128) ray_step_kernel(double2* __restrict__ the
   if (maps != nullptr) {
     float k, g1, g2, om;
     readout(A, k, g1, g2, om);
-    maps[r] = k;
-    maps[r + nr] = g1;
-    maps[r + 2 * nr] = g2;
-    maps[r + 3 * nr] = om;
+    if (p.map_accumulate) {
+      // O = sum_n n_g(chi_n) O_n (Eq. obs_accum): this step's observables with the caller's weight
+      const float w = p.map_weight;
+      maps[r] += w * k;
+      maps[r + nr] += w * g1;
+      maps[r + 2 * nr] += w * g2;
+      maps[r + 3 * nr] += w * om;
+    } else {
+      maps[r] = k;
+      maps[r + nr] = g1;
+      maps[r + 2 * nr] = g2;
+      maps[r + 3 * nr] = om;
+    }
   }
 }
 

@@ -89,6 +89,7 @@ _SIGS = {
     "hrt_step": ([_P, _D, _I32], C.c_int),
     "hrt_sync_particles": ([_P], C.c_int),
     "hrt_set_ray_correction": ([_P, _P], C.c_int),
+    "hrt_step_accumulate": ([_P, C.c_double, _I32, C.c_double], C.c_int),
     "hrt_set_ray_kernel_table": ([_P, _P, _I32, C.c_double], C.c_int),
     "hrt_state_bytes": ([_P, _P], C.c_int),
     "hrt_save_state": ([_P, _P, C.c_size_t], C.c_int),
@@ -570,6 +571,10 @@ class Context:
     def hrt_load_state(self, buf: torch.Tensor):
         _check(_lib.hrt_load_state(self._h, _ptr(buf, torch.uint8, "buf"), buf.numel()), "hrt_load_state")
         self.n_rays = int(self.hrt_ctx_rays().n_rays)
+
+    def hrt_step_accumulate(self, a_next: float, source: int, weight: float):
+        """hrt_step with map `source` += weight x the observables at the end of the step (Eq. obs_accum)."""
+        _check(_lib.hrt_step_accumulate(self._h, a_next, source, weight), "hrt_step_accumulate")
 
     def hrt_sync_particles(self):
         _check(_lib.hrt_sync_particles(self._h), "hrt_sync_particles")
