@@ -180,6 +180,72 @@ def zeldovich(noise: np.ndarray, box: float, om: float, h: float, ns: float, sig
     return d1 * psi, (a_init ** 2 * e1 * f1 * d1) * psi
 
 
+def _derivative_factors(n: int, box: float):
+    """k_j with the derivative of the j-Nyquist plane set to zero (as for the first-order displacement), and k^2."""
+    kf = 2.0 * math.pi / box
+    nx, ny, nz = _wavevectors(n, box)
+    half = n // 2
+    d = []
+    for nj, last in ((nx, False), (ny, False), (nz, True)):
+        nyq = (nj == half) if last else (nj == -half)
+        d.append(torch.where(nyq, torch.zeros_like(nj), nj).double() * kf)
+    k2 = (kf * nx.double()) ** 2 + (kf * ny.double()) ** 2 + (kf * nz.double()) ** 2
+    return d, k2
+
+
+def lpt_fields(delta: torch.Tensor, box: float):
+    """First- and second-order Lagrangian displacement fields at unit growth from a real density contrast
+    delta (n, n, n) on the particle lattice (2LPT):
+
+      Psi1 = -grad phi1,  lap phi1 = delta;
+      Psi2 = grad phi2,   lap phi2 = sum_{i<j} (phi1_ii phi1_jj - phi1_ij^2),
+
+    so that x = q + D1 Psi1 + D2 Psi2 with D2 < 0.  Derivatives are spectral; the derivative factor of a
+    Nyquist plane is zero (second derivatives are products of two first-derivative factors).
+
+    Returns (psi1, psi2) as (n^3, 3) float64 tensors."""
+    n = delta.shape[0]
+    d, k2 = _derivative_factors(n, box)
+    inv_k2 = torch.where(k2 > 0, 1.0 / torch.where(k2 > 0, k2, torch.ones_like(k2)), torch.zeros_like(k2))
+    delta_hat = torch.fft.rfftn(torch.as_tensor(delta, dtype=torch.float64))
+    phi1_hat = -delta_hat * inv_k2
+    psi1 = torch.stack([torch.fft.irfftn(-1j * d[j] * phi1_hat, s=(n, n, n)).reshape(-1) for j in range(3)], 1)
+    # phi1_ij = F^-1[(i d_i)(i d_j) phi1_hat]
+    hess = {(i, j): torch.fft.irfftn(-d[i] * d[j] * phi1_hat, s=(n, n, n)) for i in range(3) for j in range(i, 3)}
+    src = torch.zeros((n, n, n), dtype=torch.float64)
+    for i in range(3):
+        for j in range(i + 1, 3):
+            src = src + hess[(i, i)] * hess[(j, j)] - hess[(i, j)] ** 2
+    phi2_hat = -torch.fft.rfftn(src) * inv_k2
+    psi2 = torch.stack([torch.fft.irfftn(1j * d[j] * phi2_hat, s=(n, n, n)).reshape(-1) for j in range(3)], 1)
+    return psi1, psi2
+
+
+def lpt2(noise: np.ndarray, box: float, om: float, h: float, ns: float, sigma8: float, a_init: float):
+    """Second-order Lagrangian (2LPT) displacement and momentum of the lattice particles at a_init from white noise
+    (n,n,n): x = q + D1 Psi1 + D2 Psi2, p = a^2 E (f1 D1 Psi1 + f2 D2 Psi2), with the linear density of
+    ``zeldovich`` and D2 = -(3/7) D1^2 Omega_m(a)^(-1/143), f2 = 2 Omega_m(a)^(6/11).
+
+    Returns (disp, mom) as (n^3, 3) float64 tensors."""
+    n = noise.shape[0]
+    amp = cosmo.power_amplitude(om, h, ns, sigma8)
+    v_cell = (box / n) ** 3
+    w_hat = torch.fft.rfftn(torch.as_tensor(noise, dtype=torch.float64))
+    _, k2 = _derivative_factors(n, box)
+    pk = torch.as_tensor(cosmo.linear_power(torch.sqrt(k2).numpy(), om, h, ns, amp))
+    delta_hat = torch.where(k2 > 0, w_hat * torch.sqrt(pk / v_cell), torch.zeros_like(w_hat))
+    psi1, psi2 = lpt_fields(torch.fft.irfftn(delta_hat, s=(n, n, n)), box)
+    d1 = cosmo.growth_D1(a_init, om)
+    f1 = cosmo.growth_f(a_init, om)
+    e = cosmo.E(a_init, om)
+    om_a = om / (a_init ** 3 * e * e)
+    d2 = -3.0 / 7.0 * d1 * d1 * om_a ** (-1.0 / 143.0)
+    f2 = 2.0 * om_a ** (6.0 / 11.0)
+    disp = d1 * psi1 + d2 * psi2
+    mom = a_init ** 2 * e * (f1 * d1 * psi1 + f2 * d2 * psi2)
+    return disp, mom
+
+
 def matter_power(rho: torch.Tensor, box: float, nbins: int):
     """Spherically averaged power of delta = rho - 1 in linear k bins of width k_f (test utility).
 

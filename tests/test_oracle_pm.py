@@ -197,3 +197,57 @@ def test_low_k_power_grows_as_growth_factor_squared():
     ratio = p1 / p0 / (cosmo.growth_D1(0.1, c.omega_m) / cosmo.growth_D1(0.02, c.omega_m)) ** 2
     assert ratio[0] == pytest.approx(1.0, rel=0.02)
     assert np.all(np.diff(ratio) < 0.0) and ratio.max() < 1.02
+
+
+def _waves(n, box, amps):
+    """delta = sum_axis A_axis cos(k q_axis) on the particle lattice, k = 2 pi 2 / box."""
+    k = 2.0 * math.pi * 2 / box
+    q = pm.lattice(n, box).numpy()
+    delta = sum(a * np.cos(k * q[:, ax]) for ax, a in amps.items())
+    return delta.reshape(n, n, n), q, k
+
+
+def test_lpt_single_plane_wave_has_no_second_order_term():
+    # one-dimensional motion: Zel'dovich is exact, the 2LPT source vanishes
+    n, box = 16, 32.0
+    delta, q, k = _waves(n, box, {1: 0.3})
+    psi1, psi2 = pm.lpt_fields(torch.tensor(delta), box)
+    assert np.abs(psi2.numpy()).max() < 1e-14
+    # Psi1 = -grad phi1 with phi1 = -(A / k^2) cos(k y): Psi1_y = -(A / k) sin(k y), div Psi1 = -delta
+    assert np.allclose(psi1[:, 1].numpy(), -(0.3 / k) * np.sin(k * q[:, 1]), atol=1e-13)
+    assert np.abs(psi1[:, [0, 2]].numpy()).max() < 1e-14
+
+
+@pytest.mark.parametrize("axes", [(0, 1), (0, 2)])
+def test_lpt_two_orthogonal_waves_closed_form(axes):
+    # phi1 = -(A cos kx + B cos ky) / k^2: the source is A B cos kx cos ky, phi2 = -A B cos kx cos ky / (2 k^2),
+    # Psi2 = grad phi2 = (A B / (2 k)) (sin kx cos ky, cos kx sin ky); the (0, 2) case runs through the rfft axis
+    n, box = 16, 32.0
+    a, b = 0.2, 0.35
+    delta, q, k = _waves(n, box, {axes[0]: a, axes[1]: b})
+    _, psi2 = pm.lpt_fields(torch.tensor(delta), box)
+    u, v = k * q[:, axes[0]], k * q[:, axes[1]]
+    want = np.zeros((n ** 3, 3))
+    want[:, axes[0]] = a * b / (2 * k) * np.sin(u) * np.cos(v)
+    want[:, axes[1]] = a * b / (2 * k) * np.cos(u) * np.sin(v)
+    assert np.allclose(psi2.numpy(), want, atol=1e-13)
+
+
+def test_lpt_second_order_is_quadratic_and_eds_assembly():
+    n, box = 16, 64.0
+    noise = synthetic.white_noise(41, n)
+    d = synthetic.gaussian_field(42, (n, n, n), 0.05)
+    p1, p2 = pm.lpt_fields(torch.tensor(d), box)
+    q1, q2 = pm.lpt_fields(torch.tensor(2.0 * d), box)
+    assert np.allclose(q1.numpy(), 2.0 * p1.numpy(), rtol=0, atol=1e-14)
+    assert np.allclose(q2.numpy(), 4.0 * p2.numpy(), rtol=0, atol=1e-14)
+    # Einstein-de Sitter: D1 = a, f1 = 1, D2 = -(3/7) a^2, f2 = 2, E = a^-3/2
+    a = 0.05
+    disp, mom = pm.lpt2(noise, box, 1.0, 0.7, 0.96, 0.8, a)
+    dz, mz = pm.zeldovich(noise, box, 1.0, 0.7, 0.96, 0.8, a)
+    psi1 = dz / a
+    psi2 = (disp - dz) / (-3.0 / 7.0 * a * a)
+    e = a ** -1.5
+    assert np.allclose(mom.numpy(), (a * a * e * (a * psi1 + 2.0 * (-3.0 / 7.0) * a * a * psi2)).numpy(), rtol=1e-10,
+                       atol=1e-14)
+    assert np.abs(psi2.numpy()).max() > 0
