@@ -233,6 +233,15 @@ typedef struct hrt_cosmology {
 hrt_status hrt_ic_zeldovich(const float* noise, int64_t n_side, double box, const hrt_cosmology* cosmo,
                             double a_init, float* disp, float* mom, void* stream);
 
+/* Second-order Lagrangian ICs (the paper's IC scheme, Sec. 6.2): from the same white noise and linear density
+ * as hrt_ic_zeldovich, x = q + D1 Psi1 + D2 Psi2 and p = a^2 E (f1 D1 Psi1 + f2 D2 Psi2), where Psi1 is the
+ * Zel'dovich displacement at unit growth, Psi2 = grad phi2 with lap phi2 = sum_{i<j} (phi1_ii phi1_jj -
+ * phi1_ij^2) (spectral derivatives, zero on Nyquist planes), D2 = -(3/7) D1^2 Omega_m(a)^(-1/143) and
+ * f2 = 2 Omega_m(a)^(6/11).  Same layouts as hrt_ic_zeldovich; allocates 6 n_side^3 floats of scratch for the
+ * call. */
+hrt_status hrt_ic_2lpt(const float* noise, int64_t n_side, double box, const hrt_cosmology* cosmo, double a_init,
+                       float* disp, float* mom, void* stream);
+
 /* ------------------------------------------------------------------------------------------------------
  * Adjoints (reverse mode).  Each call is the vector-Jacobian product of the forward call of the same name:
  * given cotangents of the outputs it returns (or accumulates, where stated) the cotangents of the inputs and
@@ -367,6 +376,10 @@ hrt_status hrt_workspace_bytes(const hrt_config* cfg, int64_t n_rays, size_t* by
 
 /* Particles from Zel'dovich ICs (noise[n_side^3] device float32) at a_init, then the PM force at a_init. */
 hrt_status hrt_init_particles_zeldovich(hrt_ctx* ctx, const float* noise, double a_init);
+
+/* Particles from second-order Lagrangian (2LPT) ICs (noise as for hrt_init_particles_zeldovich; see
+ * hrt_ic_2lpt), then the PM force at a_init. */
+hrt_status hrt_init_particles_2lpt(hrt_ctx* ctx, const float* noise, double a_init);
 
 /* Particles from caller state (copied) at scale factor a (momentum synchronised at a), then the force. */
 hrt_status hrt_init_particles(hrt_ctx* ctx, const float* disp, const float* mom, double a);

@@ -885,6 +885,58 @@ hrt_status hrt_ic_zeldovich(const float* noise, int64_t n_side, double box, cons
   return st;
 }
 
+hrt_status hrt_ic_2lpt(const float* noise, int64_t n_side, double box, const hrt_cosmology* cosmo, double a_init,
+                       float* disp, float* mom, void* stream) {
+  HRT_TRY(check_mesh(n_side, box));
+  if (!noise || !cosmo || !disp || !mom) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  if (!(a_init > 0.0 && a_init <= 1.0) || !(cosmo->omega_m > 0.0 && cosmo->omega_m <= 1.0))
+    return fail(HRT_ERR_INVALID_ARG, "bad cosmology");
+  cudaStream_t s = as_stream(stream);
+  const int64_t n = n_side, np = n * n * n;
+  // growth factors: first order from the host cosmology, second order by the fits exact for Omega_m = 1
+  Cosmo c(cosmo->omega_m);
+  const double d1 = c.D1(a_init), f1 = c.f(a_init), e = c.E(a_init);
+  const double om_a = cosmo->omega_m / (a_init * a_init * a_init * e * e);
+  const double d2 = -3.0 / 7.0 * d1 * d1 * std::pow(om_a, -1.0 / 143.0);
+  const double f2 = 2.0 * std::pow(om_a, 6.0 / 11.0);
+  const double pfac = a_init * a_init * e;
+  const std::vector<double> t64 = ic_table64(n, box, cosmo, a_init, nullptr);
+  std::vector<float> table(t64.size());
+  for (size_t i = 0; i < t64.size(); ++i) table[i] = static_cast<float>(t64[i] / d1);  // unit growth
+  hrt_pm tmp;
+  hrt_status st = pm_make(n, box, 0, s, &tmp);
+  float* tab = nullptr;
+  float* h = nullptr;  // six real fields: the Hessian of phi1, then the source (field 0) and Psi2 (fields 1..3)
+  if (st == HRT_OK) st = upload(table, &tab, s, "IC table");
+  if (st == HRT_OK) st = device_alloc(reinterpret_cast<void**>(&h), 6 * np * sizeof(float), s, "2LPT fields");
+  const size_t sb = spectrum_bytes(n);
+  char* gh = static_cast<char*>(tmp.grad_hat);
+  auto c2r3 = [&](float* out) {
+    for (int j = 0; j < 3 && st == HRT_OK; ++j)
+      st = cufft_status(cufftExecC2R(tmp.c2r, reinterpret_cast<cufftComplex*>(gh + j * sb), out + j * np), "2LPT C2R");
+  };
+  if (st == HRT_OK)
+    st = cufft_status(cufftExecR2C(tmp.r2c, const_cast<float*>(noise), static_cast<cufftComplex*>(tmp.rho_hat)), "IC R2C");
+  // Psi1 at unit growth into disp
+  if (st == HRT_OK) st = launch_ic_kspace(tmp.rho_hat, n, box, tab, tmp.grad_hat, s);
+  c2r3(disp);
+  // Hessian of phi1 (two sets of three), then the source in field 0
+  for (int set = 0; set < 2 && st == HRT_OK; ++set) {
+    st = launch_ic_hessian(tmp.rho_hat, n, box, tab, set, tmp.grad_hat, s);
+    c2r3(h + 3 * set * np);
+  }
+  if (st == HRT_OK) st = launch_lpt2_source(h, np, h, s);
+  if (st == HRT_OK) st = cufft_status(cufftExecR2C(tmp.r2c, h, static_cast<cufftComplex*>(tmp.rho_hat)), "2LPT R2C");
+  if (st == HRT_OK) st = launch_lpt2_kspace(tmp.rho_hat, n, box, tmp.grad_hat, s);
+  c2r3(h + np);
+  if (st == HRT_OK)
+    st = launch_lpt_combine(disp, h + np, 3 * np, d1, d2, pfac * f1 * d1, pfac * f2 * d2, disp, mom, s);
+  device_free(tab, s);
+  device_free(h, s);
+  pm_release(&tmp);
+  return st;
+}
+
 // ---------------------------------------------------------------------------------------------------------
 // Adjoints
 // ---------------------------------------------------------------------------------------------------------
@@ -1246,6 +1298,17 @@ hrt_status hrt_init_particles_zeldovich(hrt_ctx* ctx, const float* noise, double
   if (ctx->cfg.static_mode) return fail(HRT_ERR_STATE, "Zel'dovich ICs need the expanding mode");
   hrt_status s = hrt_ic_zeldovich(noise, ctx->cfg.n_side, ctx->cfg.box, &ctx->cfg.cosmo, a_init, ctx->disp,
                                   ctx->mom, ctx->stream);
+  if (s != HRT_OK) return ctx_mark(ctx, s);
+  ctx->a = ctx->a_mom = a_init;
+  ctx->have_particles = true;
+  return ctx_mark(ctx, ctx_force(ctx));
+}
+
+hrt_status hrt_init_particles_2lpt(hrt_ctx* ctx, const float* noise, double a_init) {
+  HRT_TRY(ctx_guard(ctx));
+  if (ctx->cfg.static_mode) return fail(HRT_ERR_STATE, "2LPT ICs need the expanding mode");
+  hrt_status s = hrt_ic_2lpt(noise, ctx->cfg.n_side, ctx->cfg.box, &ctx->cfg.cosmo, a_init, ctx->disp, ctx->mom,
+                             ctx->stream);
   if (s != HRT_OK) return ctx_mark(ctx, s);
   ctx->a = ctx->a_mom = a_init;
   ctx->have_particles = true;

@@ -423,6 +423,113 @@ hrt_status launch_ic_kspace(const void* w_hat, int64_t n, double box, const floa
   return HRT_OK;
 }
 
+// ---------------------------------------------------------------------------------------------------------
+// Second-order Lagrangian ICs (2LPT): with c = table(|n|^2) = sqrt(P / V_cell) / k^2 / n^3 (unit growth), the
+// Hessian spectra of phi1 are d_i d_j c w_hat (set 0: xx, yy, zz; set 1: xy, xz, yz); the source
+// S = sum_{i<j} (phi1_ii phi1_jj - phi1_ij^2) is formed in real space; Psi2 = grad phi2 with lap phi2 = S is
+// -i d_j S_hat / (k^2 n^3).  Derivative factors are zero on their Nyquist planes.
+// ---------------------------------------------------------------------------------------------------------
+__global__ void ic_hessian_kernel(const float2* __restrict__ w_hat, int n, int nzc, float kf,
+                                  const float* __restrict__ table, int64_t elems, int set, float2* __restrict__ out) {
+  const int iz = blockIdx.y * blockDim.x + threadIdx.x;
+  const int64_t row = static_cast<int64_t>(blockIdx.x) * blockDim.y + threadIdx.y;
+  if (iz >= nzc || row >= static_cast<int64_t>(n) * n) return;
+  const int ix = static_cast<int>(row / n);
+  const int iy = static_cast<int>(row - static_cast<int64_t>(ix) * n);
+  const int half = n >> 1;
+  const int nx = ix < half ? ix : ix - n, ny = iy < half ? iy : iy - n, nz = iz;
+  const int64_t e = row * nzc + iz;
+  const float c = __ldg(table + (nx * nx + ny * ny + nz * nz));
+  const float2 v = w_hat[e];
+  const float dx = (nx == -half) ? 0.f : kf * nx;
+  const float dy = (ny == -half) ? 0.f : kf * ny;
+  const float dz = (nz == half) ? 0.f : kf * nz;
+  const float f0 = set == 0 ? dx * dx : dx * dy;
+  const float f1 = set == 0 ? dy * dy : dx * dz;
+  const float f2 = set == 0 ? dz * dz : dy * dz;
+  out[e] = make_float2(f0 * c * v.x, f0 * c * v.y);
+  out[e + elems] = make_float2(f1 * c * v.x, f1 * c * v.y);
+  out[e + 2 * elems] = make_float2(f2 * c * v.x, f2 * c * v.y);
+}
+
+hrt_status launch_ic_hessian(const void* w_hat, int64_t n, double box, const float* table, int set, void* out,
+                             cudaStream_t s) {
+  const int64_t nzc = n / 2 + 1;
+  dim3 block(64, 4);
+  dim3 grid(static_cast<unsigned>((n * n + 3) / 4), static_cast<unsigned>((nzc + 63) / 64));
+  ic_hessian_kernel<<<grid, block, 0, s>>>(static_cast<const float2*>(w_hat), static_cast<int>(n),
+                                           static_cast<int>(nzc), static_cast<float>(2.0 * M_PI / box), table,
+                                           n * n * nzc, set, static_cast<float2*>(out));
+  HRT_LAUNCHED("ic_hessian_kernel");
+  return HRT_OK;
+}
+
+// h: six fields of m values (xx, yy, zz, xy, xz, yz); out may alias h (field xx).
+__global__ void lpt2_source_kernel(const float* h, int64_t m, float* out) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= m) return;
+  const float xx = h[i], yy = h[i + m], zz = h[i + 2 * m], xy = h[i + 3 * m], xz = h[i + 4 * m], yz = h[i + 5 * m];
+  out[i] = (xx * yy - xy * xy) + (xx * zz - xz * xz) + (yy * zz - yz * yz);
+}
+
+hrt_status launch_lpt2_source(const float* h, int64_t m, float* out, cudaStream_t s) {
+  lpt2_source_kernel<<<blocks_for(m, 256), 256, 0, s>>>(h, m, out);
+  HRT_LAUNCHED("lpt2_source_kernel");
+  return HRT_OK;
+}
+
+__global__ void lpt2_kspace_kernel(const float2* __restrict__ s_hat, int n, int nzc, float kf, float inv_n3,
+                                   int64_t elems, float2* __restrict__ out) {
+  const int iz = blockIdx.y * blockDim.x + threadIdx.x;
+  const int64_t row = static_cast<int64_t>(blockIdx.x) * blockDim.y + threadIdx.y;
+  if (iz >= nzc || row >= static_cast<int64_t>(n) * n) return;
+  const int ix = static_cast<int>(row / n);
+  const int iy = static_cast<int>(row - static_cast<int64_t>(ix) * n);
+  const int half = n >> 1;
+  const int nx = ix < half ? ix : ix - n, ny = iy < half ? iy : iy - n, nz = iz;
+  const int64_t e = row * nzc + iz;
+  const float k2 = kf * kf * static_cast<float>(nx * nx + ny * ny + nz * nz);
+  const float c = k2 > 0.f ? inv_n3 / k2 : 0.f;
+  const float2 v = s_hat[e];
+  const float2 base = make_float2(c * v.y, -c * v.x);  // -i S_hat / (k^2 n^3)
+  const float dx = (nx == -half) ? 0.f : kf * nx;
+  const float dy = (ny == -half) ? 0.f : kf * ny;
+  const float dz = (nz == half) ? 0.f : kf * nz;
+  out[e] = make_float2(dx * base.x, dx * base.y);
+  out[e + elems] = make_float2(dy * base.x, dy * base.y);
+  out[e + 2 * elems] = make_float2(dz * base.x, dz * base.y);
+}
+
+hrt_status launch_lpt2_kspace(const void* s_hat, int64_t n, double box, void* out, cudaStream_t s) {
+  const int64_t nzc = n / 2 + 1;
+  dim3 block(64, 4);
+  dim3 grid(static_cast<unsigned>((n * n + 3) / 4), static_cast<unsigned>((nzc + 63) / 64));
+  lpt2_kspace_kernel<<<grid, block, 0, s>>>(static_cast<const float2*>(s_hat), static_cast<int>(n),
+                                            static_cast<int>(nzc), static_cast<float>(2.0 * M_PI / box),
+                                            static_cast<float>(1.0 / (static_cast<double>(n) * n * n)), n * n * nzc,
+                                            static_cast<float2*>(out));
+  HRT_LAUNCHED("lpt2_kspace_kernel");
+  return HRT_OK;
+}
+
+// disp = d1 psi1 + d2 psi2, mom = c1 psi1 + c2 psi2 (disp may alias psi1).
+__global__ void lpt_combine_kernel(const float* psi1, const float* __restrict__ psi2, int64_t m, float d1, float d2,
+                                   float c1, float c2, float* disp, float* __restrict__ mom) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= m) return;
+  const float a = psi1[i], b = psi2[i];
+  disp[i] = d1 * a + d2 * b;
+  mom[i] = c1 * a + c2 * b;
+}
+
+hrt_status launch_lpt_combine(const float* psi1, const float* psi2, int64_t m, double d1, double d2, double c1,
+                              double c2, float* disp, float* mom, cudaStream_t s) {
+  lpt_combine_kernel<<<blocks_for(m, 256), 256, 0, s>>>(psi1, psi2, m, static_cast<float>(d1), static_cast<float>(d2),
+                                                        static_cast<float>(c1), static_cast<float>(c2), disp, mom);
+  HRT_LAUNCHED("lpt_combine_kernel");
+  return HRT_OK;
+}
+
 __global__ void scale_copy_kernel(const float* __restrict__ in, float* __restrict__ out, float ratio, int64_t m) {
   int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i < m) out[i] = ratio * in[i];

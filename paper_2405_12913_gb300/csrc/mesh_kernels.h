@@ -32,6 +32,15 @@ hrt_status launch_ic_kspace(const void* w_hat, int64_t n, double box, const floa
 
 hrt_status launch_scale_copy(const float* in, float* out, double ratio, int64_t m, cudaStream_t s);
 
+// Second-order Lagrangian ICs (2LPT): Hessian spectra of phi1 (set 0: xx, yy, zz; set 1: xy, xz, yz) from the
+// unit-growth IC table, the real-space source, the spectra of Psi2 and the final combination.
+hrt_status launch_ic_hessian(const void* w_hat, int64_t n, double box, const float* table, int set, void* out,
+                             cudaStream_t s);
+hrt_status launch_lpt2_source(const float* h, int64_t m, float* out, cudaStream_t s);
+hrt_status launch_lpt2_kspace(const void* s_hat, int64_t n, double box, void* out, cudaStream_t s);
+hrt_status launch_lpt_combine(const float* psi1, const float* psi2, int64_t m, double d1, double d2, double c1,
+                              double c2, float* disp, float* mom, cudaStream_t s);
+
 // ---- rays ----
 constexpr int kMaxRayNodes = 1024;
 

@@ -80,6 +80,8 @@ _SIGS = {
     "hrt_ray_readout": ([_P, _P, _P], C.c_int),
     "hrt_kappa_power": ([_P, _I64, _D, _I32, _D, _D, _P, _P, _P, _P], C.c_int),
     "hrt_ic_zeldovich": ([_P, _I64, _D, _P, _D, _P, _P, _P], C.c_int),
+    "hrt_ic_2lpt": ([_P, _I64, _D, _P, _D, _P, _P, _P], C.c_int),
+    "hrt_init_particles_2lpt": ([_P, _P, _D], C.c_int),
     "hrt_create": ([_P, _P, _P], C.c_int),
     "hrt_destroy": ([_P], C.c_int),
     "hrt_workspace_bytes": ([_P, _I64, _P], C.c_int),
@@ -437,6 +439,14 @@ def hrt_ic_table(n_side, box, omega_m, h, n_s, sigma8, a_init):
     return t, ratio.value
 
 
+def hrt_ic_2lpt(noise: torch.Tensor, n_side: int, box: float, omega_m: float, h: float, n_s: float, sigma8: float,
+                a_init: float, disp: torch.Tensor, mom: torch.Tensor, stream=None):
+    c = hrt_cosmology(omega_m, h, n_s, sigma8)
+    _check(_lib.hrt_ic_2lpt(_ptr(noise, torch.float32, "noise"), n_side, box, C.byref(c), a_init,
+                            _ptr(disp, torch.float32, "disp"), _ptr(mom, torch.float32, "mom"), _stream(stream)),
+           "hrt_ic_2lpt")
+
+
 def hrt_ic_zeldovich_adjoint(noise, n_side, box, omega_m, h, n_s, sigma8, a_init, disp_bar, mom_bar, disp, noise_bar,
                              want_table=True, stream=None):
     import numpy as np
@@ -534,6 +544,10 @@ class Context:
     def hrt_init_particles_zeldovich(self, noise: torch.Tensor, a_init: float):
         _check(_lib.hrt_init_particles_zeldovich(self._h, _ptr(noise, torch.float32, "noise"), a_init),
                "hrt_init_particles_zeldovich")
+
+    def hrt_init_particles_2lpt(self, noise: torch.Tensor, a_init: float):
+        _check(_lib.hrt_init_particles_2lpt(self._h, _ptr(noise, torch.float32, "noise"), a_init),
+               "hrt_init_particles_2lpt")
 
     def hrt_init_particles(self, disp: torch.Tensor, mom: torch.Tensor, a: float):
         _check(_lib.hrt_init_particles(self._h, _ptr(disp, torch.float32, "disp"), _ptr(mom, torch.float32, "mom"), a),

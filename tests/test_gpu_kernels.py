@@ -330,3 +330,31 @@ def test_pm_split_path_matches_3d_path(hrt, n):
             ref = out[False][k][j]
             err = (out[True][k][j] - ref).abs().max().item()
             assert err <= 2e-5 * ref.abs().max().item(), (k, j, err, ref.abs().max().item())
+
+
+def test_2lpt_ics_match_oracle(hrt):
+    n, box, a = 32, 128.0, 0.1
+    noise = synthetic.white_noise(12, n)
+    disp = torch.empty(3, n ** 3, device="cuda")
+    mom = torch.empty(3, n ** 3, device="cuda")
+    hrt.hrt_ic_2lpt(_cuda(noise), n, box, 0.3, 0.7, 0.96, 0.8, a, disp, mom)
+    d_w, m_w = opm.lpt2(noise, box, 0.3, 0.7, 0.96, 0.8, a)
+    assert np.abs(disp.cpu().double().numpy() - d_w.numpy().T).max() <= 2e-5 * np.abs(d_w.numpy()).max()
+    assert np.abs(mom.cpu().double().numpy() - m_w.numpy().T).max() <= 2e-5 * np.abs(m_w.numpy()).max()
+    # the second-order part alone (2LPT minus Zel'dovich) to 1e-3 of its size
+    dz = torch.empty_like(disp)
+    mz = torch.empty_like(mom)
+    hrt.hrt_ic_zeldovich(_cuda(noise), n, box, 0.3, 0.7, 0.96, 0.8, a, dz, mz)
+    dz_w, _ = opm.zeldovich(noise, box, 0.3, 0.7, 0.96, 0.8, a)
+    second = (disp - dz).cpu().double().numpy()
+    second_w = (d_w - dz_w).numpy().T
+    assert np.abs(second_w).max() > 1e-3 * np.abs(d_w.numpy()).max()
+    assert np.abs(second - second_w).max() <= 1e-3 * np.abs(second_w).max()
+    # the context entry point gives the same particles
+    cfg = hrt.make_config(2 * n, box, n, 0.3, 0.7, 0.96, 0.8, observer=(0.5 * box, 0.5 * box, 0.0))
+    ctx = hrt.Context(cfg)
+    ctx.hrt_init_particles_2lpt(_cuda(noise).reshape(-1), a)
+    cd, cm, a_pos, a_mom = ctx.hrt_read_particles()
+    assert a_pos == a_mom == a
+    assert torch.equal(cd.reshape(3, -1), disp) and torch.equal(cm.reshape(3, -1), mom)
+    ctx.close()
