@@ -70,6 +70,70 @@ def interp_xy(gx: torch.Tensor, gy: torch.Tensor, X: torch.Tensor, box: float):
     return val, T
 
 
+def interp_grad3(g3, X: torch.Tensor, box: float):
+    """Trilinear values of the three gradient fields g3 = (gx, gy, gz) at box points X (n, 3) and their
+    derivatives along the three box axes.
+
+    Returns (val (n, 3), D (n, 3, 3)) with D[:, c, b] = d g_c / d x_b (on a cell face the lower cell is used)."""
+    n_mesh = g3[0].shape[0]
+    cell = box / n_mesh
+    u = torch.remainder(X, box) / cell
+    i0 = torch.floor(u)
+    f = u - i0
+    i0 = i0.to(torch.int64) % n_mesh
+    val = torch.zeros(X.shape[0], 3, dtype=torch.float64)
+    D = torch.zeros(X.shape[0], 3, 3, dtype=torch.float64)
+    flat = [g.reshape(-1) for g in g3]
+    for corner in _CORNERS:
+        w = [f[:, ax] if corner[ax] else 1 - f[:, ax] for ax in range(3)]
+        dw = [(1.0 if corner[ax] else -1.0) / cell for ax in range(3)]
+        idx = (((i0[:, 0] + corner[0]) % n_mesh) * n_mesh + (i0[:, 1] + corner[1]) % n_mesh) * n_mesh \
+            + (i0[:, 2] + corner[2]) % n_mesh
+        for comp in range(3):
+            v = flat[comp][idx]
+            val[:, comp] += w[0] * w[1] * w[2] * v
+            D[:, comp, 0] += dw[0] * w[1] * w[2] * v
+            D[:, comp, 1] += w[0] * dw[1] * w[2] * v
+            D[:, comp, 2] += w[0] * w[1] * dw[2] * v
+    return val, D
+
+
+def replica_frame(X: torch.Tensor, replicas, box: float, n_mesh: int):
+    """Light-cone tiling: the unwrapped sky point X (n, 3) lies in replica k = floor(X_z / box); with
+    u = X mod box, sky axis a maps to box axis perm[k, a] at sign[k, a] u_a + shift[k, perm[k, a]] cell (mod box).
+
+    Returns (box points (n, 3), perm (n, 3), sign (n, 3) float64)."""
+    perm_t, sign_t, shift_t = (torch.as_tensor(x, dtype=torch.int64) for x in replicas)
+    k = torch.floor(X[:, 2] / box).to(torch.int64)
+    if (k < 0).any() or (k >= perm_t.shape[0]).any():
+        raise ValueError("a point lies outside the replicas")
+    perm, sign, shift = perm_t[k], sign_t[k].double(), shift_t[k].double()
+    cell = box / n_mesh
+    u = torch.remainder(X, box)
+    Xb = torch.zeros_like(X)
+    for a in range(3):
+        dst = perm[:, a]
+        vals = torch.remainder(sign[:, a] * u[:, a] + torch.gather(shift, 1, dst[:, None])[:, 0] * cell, box)
+        Xb.scatter_(1, dst[:, None], vals[:, None])
+    return Xb, perm, sign
+
+
+def tiled_gradient(g3, X: torch.Tensor, replicas, box: float):
+    """Transverse gradient of the tiled potential phi(M_k X) seen along the sky directions x, y, and its
+    derivative: val_a = sign_a g_{perm a}, T_ab = sign_a sign_b d g_{perm a} / d x_{perm b} at the box point."""
+    Xb, perm, sign = replica_frame(X, replicas, box, g3[0].shape[0])
+    v3, D3 = interp_grad3(g3, Xb, box)
+    n = X.shape[0]
+    val = torch.zeros(n, 2, dtype=torch.float64)
+    T = torch.zeros(n, 2, 2, dtype=torch.float64)
+    rows = torch.arange(n)
+    for a in range(2):
+        val[:, a] = sign[:, a] * v3[rows, perm[:, a]]
+        for b in range(2):
+            T[:, a, b] = sign[:, a] * sign[:, b] * D3[rows, perm[:, a], perm[:, b]]
+    return val, T
+
+
 def ray_points(theta: torch.Tensor, chi: float, observer) -> torch.Tensor:
     """3D comoving points X(theta, chi) = O + (chi theta_x, chi theta_y, chi) (unwrapped), shape (n, 3)."""
     r = chi
@@ -80,11 +144,12 @@ def ray_points(theta: torch.Tensor, chi: float, observer) -> torch.Tensor:
     return X
 
 
-def half_kick(theta, gx, gy, box, observer, chis, h, weight_fn, window=None):
+def half_kick(theta, gx, gy, box, observer, chis, h, weight_fn, window=None, gz=None, replicas=None):
     """Kick K = sum_j c_j grad_perp phi(X(theta, chi_j)) and its Jacobian J = sum_j c_j r_j T_j.
 
     ``weight_fn(chi)`` is the time-correction factor g(chi); c_j = -(2/c) h r_j g(chi_j).  Nodes outside
-    ``window = (chi_lo, chi_hi)`` do not contribute."""
+    ``window = (chi_lo, chi_hi)`` do not contribute.  With ``replicas`` = (perm, sign, shift) the light cone is
+    tiled by rotated and translated replicas (``replica_frame``), which needs the third field gz."""
     K = torch.zeros(theta.shape[0], 2, dtype=torch.float64)
     J = torch.zeros(theta.shape[0], 2, 2, dtype=torch.float64)
     for chi in chis:
@@ -92,27 +157,31 @@ def half_kick(theta, gx, gy, box, observer, chis, h, weight_fn, window=None):
             continue
         r = chi
         c = -(2.0 / C_LIGHT) * h * r * weight_fn(chi)
-        val, T = interp_xy(gx, gy, ray_points(theta, chi, observer), box)
+        X = ray_points(theta, chi, observer)
+        if replicas is None:
+            val, T = interp_xy(gx, gy, X, box)
+        else:
+            val, T = tiled_gradient((gx, gy, gz), X, replicas, box)
         K += c * val
         J += (c * r) * T
     return K, J
 
 
 def ray_step(state: dict, gx, gy, box: float, observer, chi_n: float, chi_n1: float,
-             samples_per_cell: float, weight_fn, window=None) -> dict:
+             samples_per_cell: float, weight_fn, window=None, gz=None, replicas=None) -> dict:
     """One KDK step with the A/B recursion over the shell [chi_n, chi_n1] (Alg. 1 order)."""
     cell = box / gx.shape[0]
     theta, eta, A, B = state["theta"], state["eta"], state["A"], state["B"]
     chi_h = 0.5 * (chi_n + chi_n1)
     chis, h = half_shell_nodes(chi_n, chi_h, samples_per_cell, cell)
-    K, J = half_kick(theta, gx, gy, box, observer, chis, h, weight_fn, window)
+    K, J = half_kick(theta, gx, gy, box, observer, chis, h, weight_fn, window, gz, replicas)
     eta = eta + K
     B = B + J @ A
     d = (chi_n1 - chi_n) / (C_LIGHT * chi_h * chi_h)
     theta = theta + d * eta
     A = A + d * B
     chis, h = half_shell_nodes(chi_h, chi_n1, samples_per_cell, cell)
-    K, J = half_kick(theta, gx, gy, box, observer, chis, h, weight_fn, window)
+    K, J = half_kick(theta, gx, gy, box, observer, chis, h, weight_fn, window, gz, replicas)
     eta = eta + K
     B = B + J @ A
     return dict(theta=theta, eta=eta, A=A, B=B)

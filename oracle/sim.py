@@ -109,8 +109,9 @@ class ReverseResult:
 
 def run_reverse(part: Particles, grads, a_grid, box: float, n_mesh: int, c: Cosmo, flt: Filter,
                 theta0: torch.Tensor, observer, source_steps, samples_per_cell: float = 1.0,
-                move_particles: bool = True) -> ReverseResult:
-    """Reverse co-evolution along the decreasing ``a_grid`` (a_grid[0] == part.a_x, normally 1)."""
+                move_particles: bool = True, replicas=None) -> ReverseResult:
+    """Reverse co-evolution along the decreasing ``a_grid`` (a_grid[0] == part.a_x, normally 1); with
+    ``replicas`` = (perm, sign, shift) the rays cross a light cone tiled by rotated, translated replicas."""
     om = c.omega_m
     state = rays.init_state(theta0)
     res = ReverseResult(part, grads, state)
@@ -118,7 +119,7 @@ def run_reverse(part: Particles, grads, a_grid, box: float, n_mesh: int, c: Cosm
         a_n, a_n1 = a_grid[n], a_grid[n + 1]
         chi_n, chi_n1 = cosmo.chi_of_a(a_n, om), cosmo.chi_of_a(a_n1, om)
         state = rays.ray_step(state, grads[0], grads[1], box, observer, chi_n, chi_n1, samples_per_cell,
-                              growth_weight(a_n, om))
+                              growth_weight(a_n, om), gz=grads[2], replicas=replicas)
         if (n + 1) in source_steps:
             res.maps[n + 1] = rays.observables(state["A"])
             res.thetas[n + 1] = state["theta"].clone()

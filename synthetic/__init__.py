@@ -81,3 +81,23 @@ def sample_indices(seed: int, n_total: int, n_sample: int) -> np.ndarray:
     """Sorted distinct indices in ``[0, n_total)`` for spot checks of large outputs."""
     rng = np.random.default_rng(seed)
     return np.sort(rng.choice(n_total, size=min(n_sample, n_total), replace=False))
+
+
+def replica_transforms(seed: int, n_replicas: int, n_mesh: int):
+    """Random proper axis rotations and whole-cell translations of the box replicas that tile a light cone.
+
+    Returns (perm, sign, shift) int32 arrays of shape (n_replicas, 3): sky axis a of replica k maps to box axis
+    perm[k, a] with sign sign[k, a] (det = +1: a rotation by multiples of 90 degrees), and box axis b is
+    translated by shift[k, b] cells in [0, n_mesh)."""
+    rng = np.random.default_rng(seed)
+    perms = [(0, 1, 2), (1, 2, 0), (2, 0, 1), (0, 2, 1), (2, 1, 0), (1, 0, 2)]
+    parity = [1, 1, 1, -1, -1, -1]
+    perm = np.zeros((n_replicas, 3), np.int32)
+    sign = np.zeros((n_replicas, 3), np.int32)
+    for k in range(n_replicas):
+        i = int(rng.integers(len(perms)))
+        s = rng.choice([-1, 1], size=2)
+        perm[k] = perms[i]
+        sign[k] = (s[0], s[1], parity[i] * s[0] * s[1])
+    shift = rng.integers(0, n_mesh, size=(n_replicas, 3)).astype(np.int32)
+    return perm, sign, shift

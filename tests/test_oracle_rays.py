@@ -177,3 +177,40 @@ def test_free_drift_is_exact_for_constant_momentum():
         xm = 0.5 * (x0 + x1)
         th = th + st["eta"] * (x1 - x0) / (C_LIGHT * xm * xm)
     assert torch.allclose(th, want, rtol=1e-7)
+
+
+def _tiling_fields(n, seed):
+    return [torch.tensor(synthetic.gaussian_field(seed + c, (n, n, n))) for c in range(3)]
+
+
+def test_tiling_with_identity_replicas_is_the_plain_gather():
+    n, box = 16, 32.0
+    g = _tiling_fields(n, 300)
+    rng = np.random.default_rng(301)
+    X = torch.tensor(rng.uniform(0, 1, (500, 3)) * [box, box, 3 * box])
+    ident = (np.tile([0, 1, 2], (3, 1)), np.ones((3, 3), np.int32), np.zeros((3, 3), np.int32))
+    val, T = rays.tiled_gradient(g, X, ident, box)
+    val0, T0 = rays.interp_xy(g[0], g[1], X, box)
+    assert torch.allclose(val, val0, rtol=0, atol=1e-14) and torch.allclose(T, T0, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [5, 6, 7])
+def test_tiling_equals_the_gather_of_explicitly_rotated_fields(seed):
+    # phi_k(X) = phi(M X): its sky-frame gradient on the mesh is g'_a[i] = sign_a g_{perm a}[M(i)], with
+    # M(i)[perm a] = sign_a i_a + shift[perm a] (mod n); the plain gather of g' must equal the tiled gather of g
+    n, box = 16, 32.0
+    g = _tiling_fields(n, 310 + seed)
+    perm, sign, shift = synthetic.replica_transforms(seed, 1, n)
+    p, s, sh = perm[0], sign[0], shift[0]
+    idx = np.indices((n, n, n)).reshape(3, -1)
+    b = np.zeros_like(idx)
+    for a in range(3):
+        b[p[a]] = (s[a] * idx[a] + sh[p[a]]) % n
+    flat = (b[0] * n + b[1]) * n + b[2]
+    gp = [torch.tensor(s[a] * g[p[a]].reshape(-1).numpy()[flat].reshape(n, n, n)) for a in range(3)]
+    rng = np.random.default_rng(320 + seed)
+    X = torch.tensor(rng.uniform(0, 1, (800, 3)) * box)  # replica 0 (0 <= z < box)
+    val, T = rays.tiled_gradient(g, X, (perm, sign, shift), box)
+    val_p, T_p = rays.interp_xy(gp[0], gp[1], X, box)
+    assert torch.allclose(val, val_p, rtol=0, atol=1e-12)
+    assert torch.allclose(T, T_p, rtol=0, atol=1e-11)
