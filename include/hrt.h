@@ -186,6 +186,15 @@ typedef struct hrt_ray_geom {
   double window_hi;
   int64_t image_width;       /* > 0: ray r is pixel (r % W, r / W) of an image W pixels wide; the kernel
                                 then walks the rays in 16 x 8 pixel tiles (thread order only, same results) */
+  /* Light-cone tiling (hrt_ray_step_tiled; 0 replicas: none).  Replica k is the slab observer_z + chi in
+   * [k box, (k+1) box); with u = X mod box, sky axis a maps to box axis replica_perm[k][a] at
+   * replica_sign[k][a] u_a + replica_shift[k][replica_perm[k][a]] cells (mod box), i.e. the snapshot is rotated
+   * by multiples of 90 degrees and translated by whole cells (host arrays, read during the call, at most 64
+   * replicas). */
+  int32_t n_replicas;
+  const int32_t* replica_perm;   /* [n_replicas][3], a permutation of 0, 1, 2 */
+  const int32_t* replica_sign;   /* [n_replicas][3], +1 or -1 */
+  const int32_t* replica_shift;  /* [n_replicas][3], cells in [0, n) */
 } hrt_ray_geom;
 
 /* One KDK step of every ray through the shell [chi_from, chi_to] with the A/B recursion, Alg. 1 order
@@ -202,6 +211,15 @@ typedef struct hrt_ray_geom {
 hrt_status hrt_ray_step(const hrt_rays* rays, const float* grad_x, const float* grad_y,
                         const hrt_ray_geom* geom, double chi_from, double chi_to, double a_ref,
                         double omega_m, float* maps, void* stream);
+
+/* hrt_ray_step through a light cone tiled by rotated and translated box replicas (geom->n_replicas >= 1; see
+ * hrt_ray_geom and the tiling of Sec. 6.2): grad_x, grad_y, grad_z are the three gradient fields of the box, of
+ * which each node reads the two that its replica turns into the sky x and y directions.
+ * HRT_ERR_INVALID_ARG if a line-of-sight node falls outside the replicas or a replica is malformed.  (The
+ * ray-step adjoint does not support tiling.) */
+hrt_status hrt_ray_step_tiled(const hrt_rays* rays, const float* grad_x, const float* grad_y, const float* grad_z,
+                              const hrt_ray_geom* geom, double chi_from, double chi_to, double a_ref, double omega_m,
+                              float* maps, void* stream);
 
 /* Exact drift with no force over [chi_from, chi_to] (chi_from > 0): theta += eta (1/chi_from -
  * 1/chi_to)/c, A += B (1/chi_from - 1/chi_to)/c.  Used where the potential is known to vanish. */
@@ -401,6 +419,10 @@ hrt_status hrt_step(hrt_ctx* ctx, double a_next, int32_t source);
  * particle force stays plain.  Needs ray_fields == 2 (HRT_ERR_STATE otherwise).  params == NULL
  * restores the plain ray kernel.  Takes effect at the next force evaluation (the next hrt_step). */
 hrt_status hrt_set_ray_correction(hrt_ctx* ctx, const float* params);
+
+/* Light-cone tiling of the context's rays (see hrt_ray_geom): n replicas with their [n][3] axis, sign and
+ * shift tables (host, copied); n = 0 removes it.  Needs ray_fields == 0 (HRT_ERR_STATE otherwise). */
+hrt_status hrt_set_replicas(hrt_ctx* ctx, int32_t n, const int32_t* perm, const int32_t* sign, const int32_t* shift);
 
 /* Fixed learned correction of the ray force: g_table[nk] (device float32, copied) sampled uniformly on
  * |k| in [0, kmax], multiplying the Green's function of the ray fields (linear interpolation, 1 beyond kmax),

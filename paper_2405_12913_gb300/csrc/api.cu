@@ -119,6 +119,25 @@ static hrt_status build_ray_params(const hrt_ray_geom& g, double chi_from, doubl
   p.tile_w = 0;
   p.map_accumulate = 0;
   p.map_weight = 1.f;
+  p.tiled = g.n_replicas > 0 ? 1 : 0;
+  if (p.tiled) {
+    if (g.n_replicas > kMaxReplicas || !g.replica_perm || !g.replica_sign || !g.replica_shift)
+      return fail(HRT_ERR_INVALID_ARG, "tiling needs 1..%d replicas with their perm, sign and shift tables", kMaxReplicas);
+    for (int k = 0; k < g.n_replicas; ++k) {
+      int seen = 0;
+      for (int a = 0; a < 3; ++a) {
+        const int ax = g.replica_perm[3 * k + a], sg = g.replica_sign[3 * k + a], sh = g.replica_shift[3 * k + a];
+        if (ax < 0 || ax > 2 || (sg != 1 && sg != -1) || sh < 0 || sh >= g.n)
+          return fail(HRT_ERR_INVALID_ARG, "replica %d: bad axis, sign or shift", k);
+        seen |= 1 << ax;
+        p.rperm[k][a] = static_cast<signed char>(ax);
+        p.rsign[k][a] = static_cast<signed char>(sg);
+      }
+      if (seen != 7) return fail(HRT_ERR_INVALID_ARG, "replica %d: the axes are not a permutation", k);
+      p.rshift[k][0] = g.replica_shift[3 * k + g.replica_perm[3 * k]];
+      p.rshift[k][1] = g.replica_shift[3 * k + g.replica_perm[3 * k + 1]];
+    }
+  }
   p.cell = cell;
   p.box = g.box;
   p.obs_x = g.observer[0];
@@ -150,6 +169,16 @@ static hrt_status build_ray_params(const hrt_ray_geom& g, double chi_from, doubl
       if (cwr64) cwr64[total] = c * r / cell;
       if (chi64) chi64[total] = chi;
       double uz = (g.observer[2] + chi) / cell;
+      if (p.tiled) {
+        // replica of the node and its line-of-sight coordinate on the replica's box axis
+        const double zu = g.observer[2] + chi;
+        const int k = static_cast<int>(std::floor(zu / g.box));
+        if (k < 0 || k >= g.n_replicas)
+          return fail(HRT_ERR_INVALID_ARG, "line-of-sight node at chi = %g is outside the %d replicas", chi, g.n_replicas);
+        const int ax = g.replica_perm[3 * k + 2];
+        uz = (g.replica_sign[3 * k + 2] * (zu - k * g.box)) / cell + g.replica_shift[3 * k + ax];
+        p.rep[total] = static_cast<unsigned char>(k);
+      }
       uz -= g.n * std::floor(uz / g.n);
       double fl = std::floor(uz);
       int kz = static_cast<int>(fl);
@@ -211,6 +240,8 @@ struct hrt_ctx {
   void* corr_wb = nullptr;
   float* corr_x = nullptr;
   float* corr_table = nullptr;
+  // light-cone tiling (empty: none): [n][3] perm, sign, shift
+  std::vector<int32_t> rep_perm, rep_sign, rep_shift;
   // fixed learned table of the ray fields (NULL: none); exclusive with the network above
   float* ray_table = nullptr;
   int32_t ray_table_nk = 0;
@@ -602,8 +633,14 @@ static hrt_status ctx_force(hrt_ctx* ctx) {
 }
 
 
-static hrt_ray_geom ctx_geom(const hrt_config& c) {
+static hrt_ray_geom ctx_geom(const hrt_config& c, const hrt_ctx* ctx = nullptr) {
   hrt_ray_geom g{};
+  if (ctx && !ctx->rep_perm.empty()) {
+    g.n_replicas = static_cast<int32_t>(ctx->rep_perm.size() / 3);
+    g.replica_perm = ctx->rep_perm.data();
+    g.replica_sign = ctx->rep_sign.data();
+    g.replica_shift = ctx->rep_shift.data();
+  }
   g.n = c.n_mesh;
   g.box = c.box;
   std::memcpy(g.observer, c.observer, sizeof(g.observer));
@@ -618,7 +655,7 @@ static hrt_status ctx_ray_step(hrt_ctx* ctx, double chi_from, double chi_to, dou
   const hrt_config& c = ctx->cfg;
   if (source >= c.n_sources) return fail(HRT_ERR_INVALID_ARG, "source %d out of range", source);
   static thread_local RayStepParams p;
-  hrt_ray_geom g = ctx_geom(c);
+  hrt_ray_geom g = ctx_geom(c, ctx);
   // rays that fill a square image are walked in tiles (a thread-order choice; any ray set is valid)
   const int64_t w = static_cast<int64_t>(std::llround(std::sqrt(static_cast<double>(ctx->rays.n_rays))));
   if (w * w == ctx->rays.n_rays) g.image_width = w;
@@ -629,7 +666,8 @@ static hrt_status ctx_ray_step(hrt_ctx* ctx, double chi_from, double chi_to, dou
   const int64_t m = c.n_mesh * c.n_mesh * c.n_mesh;
   const float* gx = ctx->ray_grad ? ctx->ray_grad : ctx->grad;
   float* maps = source >= 0 ? ctx->maps + static_cast<int64_t>(source) * 4 * ctx->rays.n_rays : nullptr;
-  return launch_ray_step(ctx->rays, gx, gx + m, p, maps, stream);
+  // a tiled light cone reads all three particle gradient fields (ray_fields == 0 is checked when it is set)
+  return launch_ray_step(ctx->rays, gx, gx + m, p, maps, stream, p.tiled ? ctx->grad + 2 * m : nullptr);
 }
 
 }  // namespace hrt
@@ -787,10 +825,27 @@ hrt_status hrt_ray_step(const hrt_rays* rays, const float* grad_x, const float* 
   if (!std::isfinite(chi_from) || !std::isfinite(chi_to) || !(a_ref >= 0.0) || a_ref > 1.0)
     return fail(HRT_ERR_INVALID_ARG, "bad step range");
   if (a_ref > 0.0 && !(omega_m > 0.0 && omega_m <= 1.0)) return fail(HRT_ERR_INVALID_ARG, "bad omega_m");
+  if (geom->n_replicas > 0)
+    return fail(HRT_ERR_INVALID_ARG, "a tiled light cone needs all three gradient components: hrt_ray_step_tiled");
   static thread_local RayStepParams p;
   HRT_TRY(build_ray_params(*geom, chi_from, chi_to, a_ref, omega_m, p));
   set_tiles(*geom, rays->n_rays, p);
   return launch_ray_step(*rays, grad_x, grad_y, p, maps, as_stream(stream));
+}
+
+hrt_status hrt_ray_step_tiled(const hrt_rays* rays, const float* grad_x, const float* grad_y, const float* grad_z,
+                              const hrt_ray_geom* geom, double chi_from, double chi_to, double a_ref, double omega_m,
+                              float* maps, void* stream) {
+  HRT_TRY(check_rays(rays));
+  if (!geom || !grad_x || !grad_y || !grad_z) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  if (geom->n_replicas < 1) return fail(HRT_ERR_INVALID_ARG, "tiling needs at least one replica");
+  if (!std::isfinite(chi_from) || !std::isfinite(chi_to) || !(a_ref >= 0.0) || a_ref > 1.0)
+    return fail(HRT_ERR_INVALID_ARG, "bad step range");
+  if (a_ref > 0.0 && !(omega_m > 0.0 && omega_m <= 1.0)) return fail(HRT_ERR_INVALID_ARG, "bad omega_m");
+  static thread_local RayStepParams p;
+  HRT_TRY(build_ray_params(*geom, chi_from, chi_to, a_ref, omega_m, p));
+  set_tiles(*geom, rays->n_rays, p);
+  return launch_ray_step(*rays, grad_x, grad_y, p, maps, as_stream(stream), grad_z);
 }
 
 hrt_status hrt_ray_drift_free(const hrt_rays* rays, double chi_from, double chi_to, void* stream) {
@@ -991,6 +1046,7 @@ hrt_status hrt_ray_step_adjoint(const hrt_rays* rays, const float* grad_x, const
   if (!geom || !grad_x || !grad_y || !gx_bar || !gy_bar || !node_bar || !drift_bar)
     return fail(HRT_ERR_INVALID_ARG, "NULL argument");
   if (bar->n_rays != rays->n_rays) return fail(HRT_ERR_INVALID_ARG, "ray counts differ");
+  if (geom->n_replicas > 0) return fail(HRT_ERR_INVALID_ARG, "the ray-step adjoint does not support a tiled light cone");
   static thread_local RayStepParams p;
   HRT_TRY(build_ray_params(*geom, chi_from, chi_to, a_ref, omega_m, p));
   set_tiles(*geom, rays->n_rays, p);
@@ -1518,6 +1574,32 @@ hrt_status hrt_read_grad(hrt_ctx* ctx, float* grad) {
   if (!ctx->have_particles) return fail(HRT_ERR_STATE, "no force yet");
   const size_t n = ctx->cfg.n_mesh;
   return ctx_mark(ctx, cuda_status(cudaMemcpyAsync(grad, ctx->grad, 3 * n * n * n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream), "read grad"));
+}
+
+hrt_status hrt_set_replicas(hrt_ctx* ctx, int32_t n, const int32_t* perm, const int32_t* sign, const int32_t* shift) {
+  HRT_TRY(ctx_guard(ctx));
+  if (n == 0) {
+    ctx->rep_perm.clear();
+    ctx->rep_sign.clear();
+    ctx->rep_shift.clear();
+    return HRT_OK;
+  }
+  if (ctx->cfg.ray_fields != 0) return fail(HRT_ERR_STATE, "light-cone tiling uses the particle fields (ray_fields == 0)");
+  if (n < 0 || n > kMaxReplicas || !perm || !sign || !shift)
+    return fail(HRT_ERR_INVALID_ARG, "tiling needs 1..%d replicas with their perm, sign and shift tables", kMaxReplicas);
+  // validate through the node-table builder (one empty shell at the observer's replica)
+  hrt_ray_geom g = ctx_geom(ctx->cfg);
+  g.n_replicas = n;
+  g.replica_perm = perm;
+  g.replica_sign = sign;
+  g.replica_shift = shift;
+  static thread_local RayStepParams p;
+  g.window_lo = g.window_hi = 0.0;
+  HRT_TRY(build_ray_params(g, 1.0, 2.0, 0.0, ctx->cfg.cosmo.omega_m, p));
+  ctx->rep_perm.assign(perm, perm + 3 * n);
+  ctx->rep_sign.assign(sign, sign + 3 * n);
+  ctx->rep_shift.assign(shift, shift + 3 * n);
+  return HRT_OK;
 }
 
 hrt_status hrt_set_ray_kernel_table(hrt_ctx* ctx, const float* g, int32_t nk, double kmax) {

@@ -43,6 +43,7 @@ hrt_status launch_lpt_combine(const float* psi1, const float* psi2, int64_t m, d
 
 // ---- rays ----
 constexpr int kMaxRayNodes = 1024;
+constexpr int kMaxReplicas = 64;
 
 struct RayStepParams {
   int n1, n2;            // nodes of the first and second half shell (after the force window)
@@ -58,12 +59,20 @@ struct RayStepParams {
   float dr[kMaxRayNodes];   // (r_j - ref_r) / cell
   float cw[kMaxRayNodes];   // c_j
   float cwr[kMaxRayNodes];  // c_j r_j / cell
-  int kz[kMaxRayNodes];     // lower z node of the sample
-  float fz[kMaxRayNodes];   // z fraction of the sample
+  int kz[kMaxRayNodes];     // lower node of the sample along the line-of-sight box axis (z without tiling)
+  float fz[kMaxRayNodes];   // its fraction
+  // light-cone tiling (tiled != 0): replica of each node, and per replica the box axis and sign of the sky
+  // axes and the translation (cells) of the box axes that receive sky x and y
+  int tiled;
+  unsigned char rep[kMaxRayNodes];
+  signed char rperm[kMaxReplicas][3];
+  signed char rsign[kMaxReplicas][3];
+  int rshift[kMaxReplicas][2];
 };
 
+// gz (the third gradient component) is read only when p.tiled.
 hrt_status launch_ray_step(const hrt_rays& rays, const float* gx, const float* gy, const RayStepParams& p,
-                           float* maps, cudaStream_t s);
+                           float* maps, cudaStream_t s, const float* gz = nullptr);
 hrt_status launch_ray_drift_free(const hrt_rays& rays, double d, cudaStream_t s);
 hrt_status launch_ray_readout(const hrt_rays& rays, float* maps, cudaStream_t s);
 hrt_status launch_rays_init(const hrt_rays& rays, const double* theta0, cudaStream_t s);

@@ -94,6 +94,99 @@ __device__ __forceinline__ HalfKick half_kick(const RayStepParams& p, int j0, in
   return h;
 }
 
+// Cell and fraction on a box axis of a sky coordinate (cell i_s, fraction f_s) under sign sgn and a translation
+// of sh cells: u -> sgn u + sh (mod n); a flipped point on a cell face stays on the face (lower cell).
+__device__ __forceinline__ void box_axis(int i_s, float f_s, int sgn, int sh, int n, int& ib, float& fb) {
+  if (sgn > 0) {
+    ib = i_s + sh;
+    fb = f_s;
+  } else if (f_s > 0.f) {
+    ib = sh - i_s - 1;
+    fb = 1.f - f_s;
+  } else {
+    ib = sh - i_s;
+    fb = 0.f;
+  }
+  ib %= n;
+  if (ib < 0) ib += n;
+}
+
+__device__ __forceinline__ int pick(int axis, int a, int b, int c) { return axis == 0 ? a : (axis == 1 ? b : c); }
+__device__ __forceinline__ float pickf(int axis, float a, float b, float c) { return axis == 0 ? a : (axis == 1 ? b : c); }
+
+// Trilinear value of field f at box cell (ix, iy, iz) + (fx, fy, fz) and its derivatives (per cell) along
+// the three box axes.
+__device__ __forceinline__ void trilinear3(const float* __restrict__ f, int64_t r00, int64_t r01, int64_t r10,
+                                           int64_t r11, int iz, int jz, float fx, float fy, float fz, float& v,
+                                           float& dX, float& dY, float& dZ) {
+  const float a00 = __ldg(f + r00 + iz), a01 = __ldg(f + r01 + iz), a10 = __ldg(f + r10 + iz), a11 = __ldg(f + r11 + iz);
+  const float z00 = __ldg(f + r00 + jz) - a00, z01 = __ldg(f + r01 + jz) - a01, z10 = __ldg(f + r10 + jz) - a10,
+              z11 = __ldg(f + r11 + jz) - a11;
+  const float e00 = a00 + fz * z00, e01 = a01 + fz * z01, e10 = a10 + fz * z10, e11 = a11 + fz * z11;
+  const float h0 = e01 - e00, h1 = e11 - e10;
+  const float g0 = e00 + fy * h0, g1 = e10 + fy * h1;
+  v = g0 + fx * (g1 - g0);
+  dX = g1 - g0;
+  dY = h0 + fx * (h1 - h0);
+  const float q0 = z00 + fy * (z01 - z00), q1 = z10 + fy * (z11 - z10);
+  dZ = q0 + fx * (q1 - q0);
+}
+
+// Half kick through a light cone tiled by rotated and translated replicas: each node is mapped into its
+// replica's box frame; the sky gradient component a is sign_a times field perm_a there, and its derivative along
+// sky axis b is sign_a sign_b times the box derivative along perm_b.
+__device__ __forceinline__ HalfKick half_kick_tiled(const RayStepParams& p, int j0, int j1, double th_x, double th_y,
+                                                    double ref_r, const float* __restrict__ gx,
+                                                    const float* __restrict__ gy, const float* __restrict__ gz) {
+  HalfKick h{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (j1 <= j0) return h;
+  const int n = p.n;
+  int bx, by;
+  float fbx, fby;
+  base_position(p.obs_x, ref_r, th_x, p.cell, n, bx, fbx);
+  base_position(p.obs_y, ref_r, th_y, p.cell, n, by, fby);
+  const float tx = static_cast<float>(th_x), ty = static_cast<float>(th_y);
+  const int64_t nn = n;
+  for (int j = j0; j < j1; ++j) {
+    const float dr = p.dr[j];
+    int ix, iy;
+    float fx, fy;
+    node_axis(bx, fbx, dr * tx, n, ix, fx);
+    node_axis(by, fby, dr * ty, n, iy, fy);
+    const int R = p.rep[j];
+    const int p0 = p.rperm[R][0], p1 = p.rperm[R][1];
+    const int s0 = p.rsign[R][0], s1 = p.rsign[R][1];
+    int c0, c1;
+    float q0, q1;
+    box_axis(ix, fx, s0, p.rshift[R][0], n, c0, q0);
+    box_axis(iy, fy, s1, p.rshift[R][1], n, c1, q1);
+    const int c2 = p.kz[j];
+    const float q2 = p.fz[j];
+    // box-frame cell and fraction per box axis (axis p0 from sky x, p1 from sky y, the other from the line of sight)
+    const int jx_ = pick(0 == p0 ? 0 : (0 == p1 ? 1 : 2), c0, c1, c2), jy_ = pick(1 == p0 ? 0 : (1 == p1 ? 1 : 2), c0, c1, c2),
+              jz_ = pick(2 == p0 ? 0 : (2 == p1 ? 1 : 2), c0, c1, c2);
+    const float gfx = pickf(0 == p0 ? 0 : (0 == p1 ? 1 : 2), q0, q1, q2), gfy = pickf(1 == p0 ? 0 : (1 == p1 ? 1 : 2), q0, q1, q2),
+                gfz = pickf(2 == p0 ? 0 : (2 == p1 ? 1 : 2), q0, q1, q2);
+    const int kx = jx_ + 1 == n ? 0 : jx_ + 1, ky = jy_ + 1 == n ? 0 : jy_ + 1, kz2 = jz_ + 1 == n ? 0 : jz_ + 1;
+    const int64_t r00 = (jx_ * nn + jy_) * nn, r01 = (jx_ * nn + ky) * nn, r10 = (kx * nn + jy_) * nn,
+                  r11 = (kx * nn + ky) * nn;
+    const float* fa = p0 == 0 ? gx : (p0 == 1 ? gy : gz);
+    const float* fb = p1 == 0 ? gx : (p1 == 1 ? gy : gz);
+    float va, aX, aY, aZ, vb, bX, bY, bZ;
+    trilinear3(fa, r00, r01, r10, r11, jz_, kz2, gfx, gfy, gfz, va, aX, aY, aZ);
+    trilinear3(fb, r00, r01, r10, r11, jz_, kz2, gfx, gfy, gfz, vb, bX, bY, bZ);
+    const float ss = static_cast<float>(s0 * s1);
+    const float c = p.cw[j], cr = p.cwr[j];
+    h.kx += c * (s0 * va);
+    h.ky += c * (s1 * vb);
+    h.j00 += cr * pickf(p0, aX, aY, aZ);
+    h.j01 += cr * (ss * pickf(p1, aX, aY, aZ));
+    h.j10 += cr * (ss * pickf(p0, bX, bY, bZ));
+    h.j11 += cr * pickf(p1, bX, bY, bZ);
+  }
+  return h;
+}
+
 __device__ __forceinline__ void readout(const float4 A, float& kappa, float& g1, float& g2, float& om) {
   float c1 = 0.5f * (A.x + A.w), c2 = 0.5f * (A.y - A.z), c3 = 0.5f * (A.w - A.x), c4 = 0.5f * (A.y + A.z);
   kappa = 1.f - c1;
@@ -102,11 +195,12 @@ __device__ __forceinline__ void readout(const float4 A, float& kappa, float& g1,
   g2 = -c4 + c3 * om;
 }
 
+template <bool TILED>
 __global__ void __launch_bounds__(128) ray_step_kernel(double2* __restrict__ theta, float2* __restrict__ eta,
                                                        float4* __restrict__ Amat, float4* __restrict__ Bmat,
                                                        int64_t nr, const float* __restrict__ gx,
                                                        const float* __restrict__ gy, const __grid_constant__ RayStepParams p,
-                                                       float* __restrict__ maps) {
+                                                       float* __restrict__ maps, const float* __restrict__ gz) {
   int64_t r;
   if (p.tile_w > 0) {
     // 16 x 8 pixel tiles in row-major tile order; a warp covers 16 x 2 neighbouring pixels
@@ -122,7 +216,8 @@ __global__ void __launch_bounds__(128) ray_step_kernel(double2* __restrict__ the
   float2 et = eta[r];
   float4 A = Amat[r], B = Bmat[r];
 
-  HalfKick h = half_kick(p, 0, p.n1, th.x, th.y, p.ref_r[0], gx, gy);
+  HalfKick h = TILED ? half_kick_tiled(p, 0, p.n1, th.x, th.y, p.ref_r[0], gx, gy, gz)
+                     : half_kick(p, 0, p.n1, th.x, th.y, p.ref_r[0], gx, gy);
   et.x += h.kx;
   et.y += h.ky;
   // B += J A (row-major 2x2: x = 11, y = 12, z = 21, w = 22)
@@ -138,7 +233,8 @@ __global__ void __launch_bounds__(128) ray_step_kernel(double2* __restrict__ the
   A.y += p.drift * B.y;
   A.z += p.drift * B.z;
   A.w += p.drift * B.w;
-  h = half_kick(p, p.n1, p.n1 + p.n2, th.x, th.y, p.ref_r[1], gx, gy);
+  h = TILED ? half_kick_tiled(p, p.n1, p.n1 + p.n2, th.x, th.y, p.ref_r[1], gx, gy, gz)
+            : half_kick(p, p.n1, p.n1 + p.n2, th.x, th.y, p.ref_r[1], gx, gy);
   et.x += h.kx;
   et.y += h.ky;
   B.x += h.j00 * A.x + h.j01 * A.z;
@@ -170,11 +266,13 @@ __global__ void __launch_bounds__(128) ray_step_kernel(double2* __restrict__ the
 }
 
 hrt_status launch_ray_step(const hrt_rays& rays, const float* gx, const float* gy, const RayStepParams& p,
-                           float* maps, cudaStream_t s) {
+                           float* maps, cudaStream_t s, const float* gz) {
   if (rays.n_rays == 0) return HRT_OK;
-  ray_step_kernel<<<blocks_for(rays.n_rays, 128), 128, 0, s>>>(
+  if (p.tiled && !gz) return fail(HRT_ERR_INVALID_ARG, "light-cone tiling needs the third gradient component");
+  auto* kernel = p.tiled ? ray_step_kernel<true> : ray_step_kernel<false>;
+  kernel<<<blocks_for(rays.n_rays, 128), 128, 0, s>>>(
       reinterpret_cast<double2*>(rays.theta), reinterpret_cast<float2*>(rays.eta),
-      reinterpret_cast<float4*>(rays.A), reinterpret_cast<float4*>(rays.B), rays.n_rays, gx, gy, p, maps);
+      reinterpret_cast<float4*>(rays.A), reinterpret_cast<float4*>(rays.B), rays.n_rays, gx, gy, p, maps, gz);
   HRT_LAUNCHED("ray_step_kernel");
   return HRT_OK;
 }

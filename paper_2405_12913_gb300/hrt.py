@@ -38,7 +38,8 @@ class hrt_rays(C.Structure):
 class hrt_ray_geom(C.Structure):
     _fields_ = [("n", C.c_int64), ("box", C.c_double), ("observer", C.c_double * 3),
                 ("samples_per_cell", C.c_double), ("window_lo", C.c_double), ("window_hi", C.c_double),
-                ("image_width", C.c_int64)]
+                ("image_width", C.c_int64), ("n_replicas", C.c_int32), ("replica_perm", C.c_void_p),
+                ("replica_sign", C.c_void_p), ("replica_shift", C.c_void_p)]
 
 
 class hrt_cosmology(C.Structure):
@@ -76,6 +77,8 @@ _SIGS = {
     "hrt_pm_set_split": ([_P, _I32], C.c_int),
     "hrt_rays_init": ([_P, _P, _P], C.c_int),
     "hrt_ray_step": ([_P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
+    "hrt_ray_step_tiled": ([_P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
+    "hrt_set_replicas": ([_P, _I32, _P, _P, _P], C.c_int),
     "hrt_ray_drift_free": ([_P, _D, _D, _P], C.c_int),
     "hrt_ray_readout": ([_P, _P, _P], C.c_int),
     "hrt_kappa_power": ([_P, _I64, _D, _I32, _D, _D, _P, _P, _P, _P], C.c_int),
@@ -325,9 +328,15 @@ class RayState:
 
 
 def make_geom(n: int, box: float, observer, samples_per_cell: float = 1.0, window=(-1e300, 1e300),
-              image_width: int = 0) -> hrt_ray_geom:
+              image_width: int = 0, replicas=None) -> hrt_ray_geom:
+    """Ray geometry; ``replicas`` = (perm, sign, shift) [k][3] integer arrays tile the light cone."""
     g = hrt_ray_geom()
     g.image_width = image_width
+    if replicas is not None:
+        import numpy as np
+        g._tables = [np.ascontiguousarray(t, dtype=np.int32) for t in replicas]  # kept alive with the struct
+        g.n_replicas = g._tables[0].shape[0]
+        g.replica_perm, g.replica_sign, g.replica_shift = (t.ctypes.data for t in g._tables)
     g.n, g.box = n, box
     for i in range(3):
         g.observer[i] = observer[i]
@@ -348,6 +357,16 @@ def hrt_ray_step(rays: RayState, grad_x: torch.Tensor, grad_y: torch.Tensor, geo
     _check(_lib.hrt_ray_step(C.byref(r), _ptr(grad_x, torch.float32, "grad_x"), _ptr(grad_y, torch.float32, "grad_y"),
                              C.byref(geom), chi_from, chi_to, a_ref, omega_m, _ptr(maps, torch.float32, "maps"),
                              _stream(stream)), "hrt_ray_step")
+
+
+def hrt_ray_step_tiled(rays: RayState, grad: torch.Tensor, geom: hrt_ray_geom, chi_from: float, chi_to: float,
+                       a_ref: float = 0.0, omega_m: float = 0.3, maps: torch.Tensor | None = None, stream=None):
+    """hrt_ray_step through the tiled light cone of geom; grad holds the three gradient fields [3][n^3]."""
+    r = rays.c()
+    g = grad.reshape(3, -1)
+    _check(_lib.hrt_ray_step_tiled(C.byref(r), _ptr(g[0], torch.float32, "grad_x"), _ptr(g[1], torch.float32, "grad_y"),
+                                   _ptr(g[2], torch.float32, "grad_z"), C.byref(geom), chi_from, chi_to, a_ref, omega_m,
+                                   _ptr(maps, torch.float32, "maps"), _stream(stream)), "hrt_ray_step_tiled")
 
 
 def hrt_ray_drift_free(rays: RayState, chi_from: float, chi_to: float, stream=None):
@@ -565,6 +584,16 @@ class Context:
         if params is not None and params.numel() != MLP_PARAMS:
             raise ValueError(f"params must hold {MLP_PARAMS} values")
         _check(_lib.hrt_set_ray_correction(self._h, _ptr(params, torch.float32, "params")), "hrt_set_ray_correction")
+
+    def hrt_set_replicas(self, replicas=None):
+        """Light-cone tiling: (perm, sign, shift) [k][3] integer arrays, or None to remove it."""
+        if replicas is None:
+            _check(_lib.hrt_set_replicas(self._h, 0, None, None, None), "hrt_set_replicas")
+            return
+        import numpy as np
+        t = [np.ascontiguousarray(x, dtype=np.int32) for x in replicas]
+        _check(_lib.hrt_set_replicas(self._h, t[0].shape[0], t[0].ctypes.data, t[1].ctypes.data, t[2].ctypes.data),
+               "hrt_set_replicas")
 
     def hrt_set_ray_kernel_table(self, table: torch.Tensor | None, kmax: float = 0.0):
         """Fixed learned table of the ray fields over |k| in [0, kmax] (float32 on the device), or None."""

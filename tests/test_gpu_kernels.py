@@ -358,3 +358,77 @@ def test_2lpt_ics_match_oracle(hrt):
     assert a_pos == a_mom == a
     assert torch.equal(cd.reshape(3, -1), disp) and torch.equal(cm.reshape(3, -1), mom)
     ctx.close()
+
+
+def _smooth_grads3(n, box, seed):
+    # the three gradient components of a smooth random potential (a handful of low Fourier modes)
+    rng = np.random.default_rng(seed)
+    g = np.arange(n) * box / n
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    out = [np.zeros((n, n, n)) for _ in range(3)]
+    for _ in range(6):
+        m = rng.integers(-3, 4, size=3)
+        k = 2 * math.pi * m / box
+        a, ph = rng.normal() * 3e3, rng.uniform(0, 2 * math.pi)
+        arg = k[0] * X + k[1] * Y + k[2] * Z + ph
+        for c in range(3):
+            out[c] += -a * k[c] * np.sin(arg)
+    return out
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_tiled_ray_step_matches_oracle(hrt, seed):
+    # light cone tiled by six rotated, translated replicas; the shells cross the replica boundaries at
+    # observer_z + chi = 192 and 288
+    n, box = 48, 96.0
+    obs = (30.3, 61.7, 5.0)
+    g3 = _smooth_grads3(n, box, seed)
+    reps = synthetic.replica_transforms(seed, 6, n)
+    theta0 = synthetic.pixel_grid(32, 0.3)
+    rays = hrt.RayState(theta0.shape[0])
+    hrt.hrt_rays_init(rays, _cuda(theta0, torch.float64))
+    geom = hrt.make_geom(n, box, obs, 1.0, image_width=32, replicas=reps)
+    grad = _cuda(np.stack(g3))
+    maps = torch.empty(4, theta0.shape[0], device="cuda")
+    st = orays.init_state(torch.tensor(theta0))
+    t3 = [torch.tensor(x) for x in g3]
+    for (c0, c1) in [(150.0, 210.0), (210.0, 300.0)]:
+        hrt.hrt_ray_step_tiled(rays, grad, geom, c0, c1, 0.0, 0.3, maps)
+        st = orays.ray_step(st, t3[0], t3[1], box, obs, c0, c1, 1.0, lambda chi: 1.0, gz=t3[2], replicas=reps)
+    th = rays.theta.cpu().numpy()
+    dth, dth_w = th - theta0, st["theta"].numpy() - theta0
+    scale = np.abs(dth_w).max()
+    assert scale > 1e-6
+    assert np.abs(dth - dth_w).max() <= 1e-4 * scale
+    assert np.abs(rays.eta.cpu().double().numpy() - st["eta"].numpy()).max() <= 1e-4 * np.abs(st["eta"].numpy()).max()
+    assert np.abs(rays.A.cpu().double().numpy().reshape(-1, 2, 2) - st["A"].numpy()).max() <= 2e-6
+    B_w = st["B"].numpy()
+    assert np.abs(rays.B.cpu().double().numpy().reshape(-1, 2, 2) - B_w).max() <= 1e-4 * np.abs(B_w).max()
+    k, g1, g2, om = orays.observables(st["A"])
+    got = maps.cpu().double().numpy()
+    for i, w in enumerate((k, g1, g2, om)):
+        assert np.abs(got[i] - w.numpy()).max() <= 2e-6
+
+
+def test_tiled_ray_step_with_identity_replicas_is_the_plain_step(hrt):
+    n, box = 48, 96.0
+    obs = (30.3, 61.7, 5.0)
+    g3 = _smooth_grads3(n, box, 23)
+    ident = (np.tile([0, 1, 2], (6, 1)), np.ones((6, 3), np.int32), np.zeros((6, 3), np.int32))
+    theta0 = _cuda(synthetic.pixel_grid(32, 0.3), torch.float64)
+    a_rays, b_rays = hrt.RayState(theta0.shape[0]), hrt.RayState(theta0.shape[0])
+    hrt.hrt_rays_init(a_rays, theta0)
+    hrt.hrt_rays_init(b_rays, theta0)
+    grad = _cuda(np.stack(g3))
+    plain = hrt.make_geom(n, box, obs, 1.0, image_width=32)
+    tiled = hrt.make_geom(n, box, obs, 1.0, image_width=32, replicas=ident)
+    hrt.hrt_ray_step(a_rays, grad[0], grad[1], plain, 150.0, 300.0, 0.0, 0.3)
+    hrt.hrt_ray_step_tiled(b_rays, grad, tiled, 150.0, 300.0, 0.0, 0.3)
+    d = (a_rays.theta - theta0).abs().max().item()
+    assert (b_rays.theta - a_rays.theta).abs().max().item() <= 1e-6 * d
+    assert (b_rays.A - a_rays.A).abs().max().item() <= 1e-6
+    with pytest.raises(hrt.HRTError):  # the plain step refuses a tiled geometry
+        hrt.hrt_ray_step(a_rays, grad[0], grad[1], tiled, 150.0, 300.0, 0.0, 0.3)
+    short = hrt.make_geom(n, box, obs, 1.0, replicas=tuple(t[:2] for t in ident))
+    with pytest.raises(hrt.HRTError):  # nodes beyond the last replica
+        hrt.hrt_ray_step_tiled(b_rays, grad, short, 150.0, 300.0, 0.0, 0.3)

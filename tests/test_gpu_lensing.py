@@ -67,10 +67,12 @@ def test_point_mass_deflection_matches_oracle(hrt):
     assert np.median(err[far]) < 0.001 and err[far].max() < 0.01
 
 
-def _cosmo_gpu(hrt, W, noise, theta0):
+def _cosmo_gpu(hrt, W, noise, theta0, replicas=None):
     cfg = hrt.make_config(W.n_mesh, W.box, W.n_side, W.omega_m, W.h, W.n_s, W.sigma8, W.deconv_p, W.smooth_cells,
                           W.samples_per_cell, W.observer, n_sources=len(W.source_steps))
     ctx = hrt.Context(cfg)
+    if replicas is not None:
+        ctx.hrt_set_replicas(replicas)
     ctx.hrt_init_particles_zeldovich(torch.tensor(noise, dtype=torch.float32, device="cuda"), W.a_init)
     for a in W.forward_grid[1:]:
         ctx.hrt_step(a)
@@ -245,3 +247,38 @@ def test_accumulated_source_distribution_matches_oracle(hrt):
     assert np.array_equal(cnt, cnt_o)
     ok = cnt_o > 0
     assert np.allclose(p[ok], p_o[ok], rtol=1e-3), np.abs(p[ok] / p_o[ok] - 1).max()
+
+
+def test_tiled_light_cone_run_matches_oracle(hrt):
+    # the co-evolution run with the rays crossing 16 rotated, translated replicas of the box
+    from paper_2405_12913_gb300.configs import COSMO_TINY as W
+    reps = synthetic.replica_transforms(31, 16, W.n_mesh)
+    noise = synthetic.white_noise(W.seed, W.n_side)
+    theta0 = synthetic.pixel_grid(W.n_pix, W.fov_deg * synthetic.DEGREE)
+    _, _, maps, th, pk = _cosmo_gpu(hrt, W, noise, theta0, replicas=reps)
+    c = sim.Cosmo(W.omega_m, W.h, W.n_s, W.sigma8)
+    flt = sim.Filter(W.deconv_p, W.smooth_cells)
+    part = sim.initial_particles(noise, W.box, c, W.a_init)
+    part, grads = sim.run_forward(part, W.forward_grid, W.box, W.n_mesh, c, flt)
+    res = sim.run_reverse(part, grads, W.reverse_grid, W.box, W.n_mesh, c, flt, torch.tensor(theta0), W.observer,
+                          set(W.source_steps), W.samples_per_cell, replicas=reps)
+    lmin, lmax = W.ell_range
+    for s in W.source_steps:
+        want = np.stack([res.maps[s][i].numpy() for i in range(4)])
+        rms = want[0].std()
+        err = np.abs(maps[s] - want)
+        # kappa jumps where a line-of-sight sample crosses a cell face: allow a rare pixel
+        assert (err > 1e-3 * rms).mean() <= 2e-3 and np.median(err) <= 1e-4 * rms, (s, err.max(), rms)
+        ell_o, p_o, cnt_o = opow.kappa_power(want[0].reshape(W.n_pix, W.n_pix), W.dtheta, W.nbins, lmin, lmax)
+        ell, p, cnt = pk[s]
+        assert np.array_equal(cnt, cnt_o)
+        ok = cnt_o > 0
+        assert np.allclose(p[ok], p_o[ok], rtol=1e-3), np.abs(p[ok] / p_o[ok] - 1).max()
+    alpha_o = theta0 - res.rays["theta"].numpy()
+    assert np.abs((theta0 - th) - alpha_o).max() <= 1e-4 * np.abs(alpha_o).max()
+    # a tiled light cone reads the particle fields: not available with separately filtered ray fields
+    cfg2 = hrt.make_config(W.n_mesh, W.box, W.n_side, observer=W.observer, ray_fields=2)
+    ctx2 = hrt.Context(cfg2)
+    with pytest.raises(hrt.HRTError):
+        ctx2.hrt_set_replicas(reps)
+    ctx2.close()
