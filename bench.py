@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--workload", default="cosmo_512p_1024m_2048r")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-next", action="store_true",
+                   help="skip the timings of the widened rows (tiled light cone, accumulated sources, 2LPT ICs)")
     p.add_argument("--no-learned", action="store_true",
                    help="skip the learned-correction comparison (coarse learned vs coarse plain vs fine plain)")
     return p.parse_args()
@@ -308,6 +310,7 @@ def run_gpu(args, W, world, rank, local):
     phase_summary = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1],
                          "algo_GBps": (algo[k] / (v[0] / max(v[1], 1) / 1e3) / 1e9) if k in algo and v[1] else None}
                      for k, v in phases.items()}
+    extra = None if args.no_next else next_rows(args, W, ctx, reset, grid, slots, run_steps, stream, seed)
     ctx.close()
     if world > 1:
         import torch.distributed as dist
@@ -328,9 +331,58 @@ def run_gpu(args, W, world, rank, local):
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "traffic": recorded_traffic(dom, W.name), "algorithmic_bytes": algo[dom]},
         "phases": phase_summary,
+        "next_rows": extra,
         "e2e": e2e,
     }
     return line
+
+
+# ----------------------------------------------------------------------------------------------- widened rows
+def next_rows(args, W, ctx, reset, grid, slots, run_steps, stream, seed):
+    """Timings of the rows beyond the measured step, on the same workload and context: the ray step through a
+    light cone tiled by rotated, translated replicas against the plain one (phase timing), the step with the
+    accumulating readout of a source distribution, and 2LPT against Zel'dovich initial conditions."""
+    import numpy as np
+    import torch
+    import synthetic
+    from paper_2405_12913_gb300 import hrt
+    steps = min(16, len(grid) - 1)
+    out = {"steps": steps}
+    # tiled light cone: enough replicas for the deepest node
+    from paper_2405_12913_gb300.hrt import hrt_cosmo_eval
+    n_rep = int(math.floor((W.observer[2] + hrt_cosmo_eval(W.omega_m, W.a_min)[1]) / W.box)) + 2
+    ctx.hrt_set_replicas(synthetic.replica_transforms(seed, n_rep, W.n_mesh))
+    reset()
+    ctx.hrt_ctx_set_profiling(True)
+    run_steps(steps, 0)
+    ph = ctx.hrt_ctx_phase_times()
+    ctx.hrt_ctx_set_profiling(False)
+    ctx.hrt_set_replicas(None)
+    out["tiled_ray_step_ms"] = ph["ray_step"][0] / max(ph["ray_step"][1], 1)
+    out["replicas"] = n_rep
+    # accumulated source distribution: every reverse step adds n_g(chi_n) O_n
+    reset()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for n in range(1, steps + 1):
+        ctx.hrt_step_accumulate(grid[n], 0, 1.0 / steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["accumulate_step_ms"] = e0.elapsed_time(e1) / steps
+    # initial conditions on the particle lattice
+    noise = torch.from_numpy(synthetic.white_noise(seed, W.n_side).astype(np.float32)).cuda().reshape(-1)
+    disp = torch.empty(3, W.n_side ** 3, device="cuda")
+    mom = torch.empty_like(disp)
+    for name, fn in (("zeldovich", hrt.hrt_ic_zeldovich), ("2lpt", hrt.hrt_ic_2lpt)):
+        fn(noise, W.n_side, W.box, W.omega_m, W.h, W.n_s, W.sigma8, W.a_init, disp, mom)  # plans and memory
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn(noise, W.n_side, W.box, W.omega_m, W.h, W.n_s, W.sigma8, W.a_init, disp, mom)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[f"ic_{name}_ms"] = e0.elapsed_time(e1)
+    return out
 
 
 # ----------------------------------------------------------------------------------------------- learned form
