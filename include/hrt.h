@@ -229,6 +229,61 @@ hrt_status hrt_ray_drift_free(const hrt_rays* rays, double chi_from, double chi_
 hrt_status hrt_ray_readout(const hrt_rays* rays, float* maps, void* stream);
 
 /* ------------------------------------------------------------------------------------------------------
+ * Ray-mesh kick operator (Sec. 5.2 "kick on a 2D ray mesh", Sec. 5.3 "adaptive ray mesh", App. C): the
+ * paper's own way of evaluating the kick of Eq. "kick", an alternative to the direct line-of-sight gather of
+ * hrt_ray_step.  For a half shell [chi_a, chi_b) (either orientation):
+ *   lambda_lim = max(2 cell / (|chi_a| + |chi_b|), mu)              (Eq. "reslim")
+ *   x2d = iota lambda_lim, N = smallest power of two >= ceil(m_pix mu / x2d + p_min / iota)   (App. C);
+ * the ray mesh holds N x N nodes at the angles ((i - N/2) x2d, (j - N/2) x2d).  Every 3D node of a plane
+ * z = kz cell with min(chi_a, chi_b) <= chi = z - O_z < max(chi_a, chi_b), chi > 0 (and inside the geometry's
+ * window), with its transverse periodic images, is projected to the angle (X_xy - O_xy) / chi and carries
+ * -(2/c) chi g(chi) (d_x phi, d_y phi) times its line-of-sight extent (+cell, or -cell for a shell walked
+ * towards the observer) and its solid angle over the ray-mesh cell's, cell^2 / (chi^2 x2d^2).  These values
+ * are CIC-deposited; the mesh is then multiplied in 2D Fourier space by
+ * sinc(k_x x2d / 2)^-4 sinc(k_y x2d / 2)^-4 exp(-(k_x^2 + k_y^2) lambda_lim^2 / 2) (the deconvolution of
+ * both CIC steps and the Gaussian smoothing of Sec. 5.2), and the kick at a ray is the bilinear interpolation
+ * of the mesh at its angle (zero outside the mesh), with dK/dtheta the derivative of that interpolant.
+ * g(chi) is the growth correction of Eq. "kick" with a_ref (a_ref <= 0: g = 1).  The line of sight is the z
+ * axis of the periodically replicated box; light-cone tiling (n_replicas != 0) is not supported
+ * (HRT_ERR_INVALID_ARG), and samples_per_cell and image_width of the geometry are not used.  Computed in
+ * float32: the 3D-to-mesh positions start from an FP64 base per 8 x 32 block of mesh nodes; the ray angles
+ * stay FP64.
+ * ------------------------------------------------------------------------------------------------------ */
+typedef struct hrt_raymesh_config {
+  double iota;      /* accuracy parameter, 0 < iota <= 1 (smaller: finer ray mesh)                      */
+  double p_min;     /* minimum padding width in units of lambda_lim, >= 0                                */
+  double mu;        /* pixel size of the ray image, rad, > 0                                             */
+  int64_t m_pix;    /* pixels across the image, >= 1                                                     */
+  int64_t n2d_max;  /* largest ray-mesh side accepted (0: 8192, at most 32768); a shell that needs a
+                       larger mesh gives HRT_ERR_INVALID_ARG                                              */
+} hrt_raymesh_config;
+
+/* Workspace of the ray-mesh kick: cuFFT plans by mesh side and two device meshes (one per half shell),
+ * grown on demand.  Not thread-safe; one stream at a time. */
+typedef struct hrt_raymesh hrt_raymesh;
+
+/* lambda_lim, x2d and N of the half shell [chi_a, chi_b) on a mesh of cell size cell (host only). */
+hrt_status hrt_raymesh_geometry(const hrt_raymesh_config* cfg, double chi_a, double chi_b, double cell,
+                                double* lambda_lim_host, double* x2d_host, int64_t* n2d_host);
+hrt_status hrt_raymesh_create(const hrt_raymesh_config* cfg, hrt_raymesh** out);
+hrt_status hrt_raymesh_destroy(hrt_raymesh* rm);  /* NULL is fine; synchronises the device */
+
+/* The filtered ray mesh of one half shell into mesh (device, caller-owned, N x N x 2 float32 with
+ * mesh[(i N + j) 2 + c] the component c at node (i, j); N from hrt_raymesh_geometry).  grad_x, grad_y: the
+ * transverse gradient fields [n][n][n] (x, y, z; z fastest), device float32.  HRT_ERR_INVALID_ARG for a bad
+ * geometry or configuration, more than 512 planes in the shell, or a ray-mesh cell wider than 64 mesh cells. */
+hrt_status hrt_raymesh_kick(hrt_raymesh* rm, const float* grad_x, const float* grad_y, const hrt_ray_geom* geom,
+                            double chi_a, double chi_b, double a_ref, double omega_m, float* mesh, void* stream);
+
+/* One KDK ray step over [chi_from, chi_to] in the order of Alg. 1 (as hrt_ray_step) whose half kicks over
+ * [chi_from, chi_mid) and [chi_mid, chi_to) come from their ray meshes; the drift is that of hrt_ray_step.
+ * maps (device float32 [4][n_rays], or NULL) receives kappa, gamma1, gamma2, omega.  Errors as
+ * hrt_raymesh_kick. */
+hrt_status hrt_raymesh_ray_step(hrt_raymesh* rm, const hrt_rays* rays, const float* grad_x, const float* grad_y,
+                                const hrt_ray_geom* geom, double chi_from, double chi_to, double a_ref,
+                                double omega_m, float* maps, void* stream);
+
+/* ------------------------------------------------------------------------------------------------------
  * Convergence power spectrum: P(ell) = <|FFT2(kappa) dtheta^2|^2>_bin / (m dtheta)^2 over nbins log bins
  * in [ell_min, ell_max) (bin b = floor(nbins ln(ell/ell_min)/ln(ell_max/ell_min) + 1e-9), the 1e-9 placing
  * exact edges in the upper bin), ell = 2 pi |n| / (m dtheta).  Outputs the mean ell, mean power and mode
@@ -423,6 +478,13 @@ hrt_status hrt_set_ray_correction(hrt_ctx* ctx, const float* params);
 /* Light-cone tiling of the context's rays (see hrt_ray_geom): n replicas with their [n][3] axis, sign and
  * shift tables (host, copied); n = 0 removes it.  Needs ray_fields == 0 (HRT_ERR_STATE otherwise). */
 hrt_status hrt_set_replicas(hrt_ctx* ctx, int32_t n, const int32_t* perm, const int32_t* sign, const int32_t* shift);
+
+/* Kick operator of the context's rays: cfg != NULL switches to the ray-mesh kick of hrt_raymesh_ray_step
+ * (configuration copied; the context owns its workspace), cfg == NULL back to the direct line-of-sight
+ * gather.  The ray mesh reads the same 3D fields as the direct gather (the ray fields when ray_fields == 2).
+ * HRT_ERR_STATE with light-cone tiling; HRT_ERR_INVALID_ARG for a bad configuration.  Takes effect at the
+ * next ray step. */
+hrt_status hrt_set_ray_mesh(hrt_ctx* ctx, const hrt_raymesh_config* cfg);
 
 /* Fixed learned correction of the ray force: g_table[nk] (device float32, copied) sampled uniformly on
  * |k| in [0, kmax], multiplying the Green's function of the ray fields (linear interpolation, 1 beyond kmax),

@@ -49,10 +49,11 @@ def shell_planes(chi_a: float, chi_b: float, cell: float, observer_z: float):
 
 
 def mesh_kick(gx: torch.Tensor, gy: torch.Tensor, box: float, observer, chi_a: float, chi_b: float, weight_fn,
-              mu: float, m_pix: int, iota: float, p_min: float, filtered: bool = True):
+              mu: float, m_pix: int, iota: float, p_min: float, filtered: bool = True, window=None):
     """The filtered kick of the half shell on its ray mesh: returns (K (2, N, N) float64 tensor, x2d, N), with
     K[c, i, j] the component c at the angle ((i - N/2) x2d, (j - N/2) x2d).  ``filtered=False`` returns the CIC
-    deposit before the deconvolution and smoothing."""
+    deposit before the deconvolution and smoothing; planes outside ``window = (chi_lo, chi_hi)`` do not
+    contribute."""
     n = gx.shape[0]
     cell = box / n
     lam, x2d, n2d = geometry(chi_a, chi_b, cell, mu, m_pix, iota, p_min)
@@ -62,6 +63,8 @@ def mesh_kick(gx: torch.Tensor, gy: torch.Tensor, box: float, observer, chi_a: f
     gxn, gyn = gx.numpy(), gy.numpy()
     idx = np.arange(n) * cell
     for kz, chi in shell_planes(chi_a, chi_b, cell, observer[2]):
+        if window is not None and not (window[0] <= chi < window[1]):
+            continue
         r = chi
         w = -(2.0 / C_LIGHT) * r * weight_fn(chi) * sgn * cell * cell * cell / (r * r * x2d * x2d)
         iz = kz % n
@@ -134,18 +137,18 @@ def gather(K: torch.Tensor, x2d: float, theta: torch.Tensor):
 
 
 def ray_step(state: dict, gx, gy, box: float, observer, chi_n: float, chi_n1: float, weight_fn, mu: float,
-             m_pix: int, iota: float, p_min: float) -> dict:
+             m_pix: int, iota: float, p_min: float, window=None) -> dict:
     """One KDK step with the A/B recursion (Alg. 1 order) whose two half kicks come from ray meshes."""
     theta, eta, A, B = state["theta"], state["eta"], state["A"], state["B"]
     chi_h = 0.5 * (chi_n + chi_n1)
-    K1, x1, _ = mesh_kick(gx, gy, box, observer, chi_n, chi_h, weight_fn, mu, m_pix, iota, p_min)
+    K1, x1, _ = mesh_kick(gx, gy, box, observer, chi_n, chi_h, weight_fn, mu, m_pix, iota, p_min, window=window)
     val, T = gather(K1, x1, theta)
     eta = eta + val
     B = B + T @ A
     d = (chi_n1 - chi_n) / (C_LIGHT * chi_h * chi_h)
     theta = theta + d * eta
     A = A + d * B
-    K2, x2, _ = mesh_kick(gx, gy, box, observer, chi_h, chi_n1, weight_fn, mu, m_pix, iota, p_min)
+    K2, x2, _ = mesh_kick(gx, gy, box, observer, chi_h, chi_n1, weight_fn, mu, m_pix, iota, p_min, window=window)
     val, T = gather(K2, x2, theta)
     eta = eta + val
     B = B + T @ A

@@ -24,7 +24,7 @@ import numpy as np
 import torch
 
 from . import cosmology as cosmo
-from . import pm, rays
+from . import pm, rays, raymesh
 from .units import C_LIGHT, G_NEWTON
 
 
@@ -109,17 +109,22 @@ class ReverseResult:
 
 def run_reverse(part: Particles, grads, a_grid, box: float, n_mesh: int, c: Cosmo, flt: Filter,
                 theta0: torch.Tensor, observer, source_steps, samples_per_cell: float = 1.0,
-                move_particles: bool = True, replicas=None) -> ReverseResult:
+                move_particles: bool = True, replicas=None, ray_mesh=None) -> ReverseResult:
     """Reverse co-evolution along the decreasing ``a_grid`` (a_grid[0] == part.a_x, normally 1); with
-    ``replicas`` = (perm, sign, shift) the rays cross a light cone tiled by rotated, translated replicas."""
+    ``replicas`` = (perm, sign, shift) the rays cross a light cone tiled by rotated, translated replicas; with
+    ``ray_mesh`` = (mu, m_pix, iota, p_min) the kicks come from the ray mesh of Sec. 5.2 (``raymesh``)."""
     om = c.omega_m
     state = rays.init_state(theta0)
     res = ReverseResult(part, grads, state)
     for n in range(len(a_grid) - 1):
         a_n, a_n1 = a_grid[n], a_grid[n + 1]
         chi_n, chi_n1 = cosmo.chi_of_a(a_n, om), cosmo.chi_of_a(a_n1, om)
-        state = rays.ray_step(state, grads[0], grads[1], box, observer, chi_n, chi_n1, samples_per_cell,
-                              growth_weight(a_n, om), gz=grads[2], replicas=replicas)
+        if ray_mesh is None:
+            state = rays.ray_step(state, grads[0], grads[1], box, observer, chi_n, chi_n1, samples_per_cell,
+                                  growth_weight(a_n, om), gz=grads[2], replicas=replicas)
+        else:
+            state = raymesh.ray_step(state, grads[0], grads[1], box, observer, chi_n, chi_n1,
+                                     growth_weight(a_n, om), *ray_mesh)
         if (n + 1) in source_steps:
             res.maps[n + 1] = rays.observables(state["A"])
             res.thetas[n + 1] = state["theta"].clone()

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhrt.so")
-SOURCES = ["api.cu", "mesh_kernels.cu", "ray_kernels.cu", "cosmo.cpp", "noalloc.cu", "adjoint_kernels.cu", "mlp_kernels.cu", "xpass_kernels.cu"]
+SOURCES = ["api.cu", "mesh_kernels.cu", "ray_kernels.cu", "cosmo.cpp", "noalloc.cu", "adjoint_kernels.cu", "mlp_kernels.cu", "xpass_kernels.cu", "raymesh.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "--expt-relaxed-constexpr"]
 
@@ -66,7 +66,7 @@ def _callback_blob() -> str:
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES + ["kspace_callback.cu"]]
-    srcs += [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
+    srcs += [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     srcs.append(os.path.join(os.path.dirname(HERE), "include", "hrt.h"))
     if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(s) for s in srcs):
         return LIB

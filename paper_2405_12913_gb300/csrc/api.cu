@@ -17,6 +17,7 @@
 #include "kspace_callback.h"
 #include "mesh_kernels.h"
 #include "mlp.h"
+#include "raymesh.h"
 #include "xpass.h"
 
 extern "C" const unsigned char hrt_kspace_callback_fatbin[];
@@ -242,6 +243,8 @@ struct hrt_ctx {
   float* corr_table = nullptr;
   // light-cone tiling (empty: none): [n][3] perm, sign, shift
   std::vector<int32_t> rep_perm, rep_sign, rep_shift;
+  // ray-mesh kick operator of Sec. 5.2 (NULL: the direct line-of-sight gather)
+  hrt_raymesh* raymesh = nullptr;
   // fixed learned table of the ray fields (NULL: none); exclusive with the network above
   float* ray_table = nullptr;
   int32_t ray_table_nk = 0;
@@ -666,6 +669,9 @@ static hrt_status ctx_ray_step(hrt_ctx* ctx, double chi_from, double chi_to, dou
   const int64_t m = c.n_mesh * c.n_mesh * c.n_mesh;
   const float* gx = ctx->ray_grad ? ctx->ray_grad : ctx->grad;
   float* maps = source >= 0 ? ctx->maps + static_cast<int64_t>(source) * 4 * ctx->rays.n_rays : nullptr;
+  if (ctx->raymesh)
+    return raymesh_step(ctx->raymesh, ctx->rays, gx, gx + m, g, chi_from, chi_to, a_ref, c.cosmo.omega_m, maps,
+                        accumulate ? 1 : 0, static_cast<float>(weight), stream);
   // a tiled light cone reads all three particle gradient fields (ray_fields == 0 is checked when it is set)
   return launch_ray_step(ctx->rays, gx, gx + m, p, maps, stream, p.tiled ? ctx->grad + 2 * m : nullptr);
 }
@@ -1298,6 +1304,7 @@ hrt_status hrt_destroy(hrt_ctx* ctx) {
       cudaEventDestroy(ev.second);
     }
   hrt_pm_destroy(ctx->pm);
+  hrt_raymesh_destroy(ctx->raymesh);
   device_free(ctx->disp, s);
   device_free(ctx->mom, s);
   device_free(ctx->rho, s);
@@ -1585,6 +1592,7 @@ hrt_status hrt_set_replicas(hrt_ctx* ctx, int32_t n, const int32_t* perm, const 
     return HRT_OK;
   }
   if (ctx->cfg.ray_fields != 0) return fail(HRT_ERR_STATE, "light-cone tiling uses the particle fields (ray_fields == 0)");
+  if (ctx->raymesh) return fail(HRT_ERR_STATE, "the ray-mesh kick does not support light-cone tiling");
   if (n < 0 || n > kMaxReplicas || !perm || !sign || !shift)
     return fail(HRT_ERR_INVALID_ARG, "tiling needs 1..%d replicas with their perm, sign and shift tables", kMaxReplicas);
   // validate through the node-table builder (one empty shell at the observer's replica)
@@ -1599,6 +1607,18 @@ hrt_status hrt_set_replicas(hrt_ctx* ctx, int32_t n, const int32_t* perm, const 
   ctx->rep_perm.assign(perm, perm + 3 * n);
   ctx->rep_sign.assign(sign, sign + 3 * n);
   ctx->rep_shift.assign(shift, shift + 3 * n);
+  return HRT_OK;
+}
+
+hrt_status hrt_set_ray_mesh(hrt_ctx* ctx, const hrt_raymesh_config* cfg) {
+  HRT_TRY(ctx_guard(ctx));
+  if (cfg && !ctx->rep_perm.empty()) return fail(HRT_ERR_STATE, "the ray-mesh kick does not support light-cone tiling");
+  hrt_raymesh* rm = nullptr;
+  if (cfg) HRT_TRY(hrt_raymesh_create(cfg, &rm));
+  if (ctx->ray_stream) cudaStreamSynchronize(ctx->ray_stream);
+  cudaStreamSynchronize(ctx->stream);
+  hrt_raymesh_destroy(ctx->raymesh);
+  ctx->raymesh = rm;
   return HRT_OK;
 }
 

@@ -12,6 +12,7 @@
 
 #include "common.h"
 #include "mesh_kernels.h"
+#include "readout.cuh"
 
 namespace hrt {
 
@@ -185,14 +186,6 @@ __device__ __forceinline__ HalfKick half_kick_tiled(const RayStepParams& p, int 
     h.j11 += cr * pickf(p1, bX, bY, bZ);
   }
   return h;
-}
-
-__device__ __forceinline__ void readout(const float4 A, float& kappa, float& g1, float& g2, float& om) {
-  float c1 = 0.5f * (A.x + A.w), c2 = 0.5f * (A.y - A.z), c3 = 0.5f * (A.w - A.x), c4 = 0.5f * (A.y + A.z);
-  kappa = 1.f - c1;
-  om = c2 / c1;
-  g1 = c3 + c4 * om;
-  g2 = -c4 + c3 * om;
 }
 
 template <bool TILED>

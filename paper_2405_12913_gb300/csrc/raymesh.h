@@ -1,0 +1,16 @@
+// The ray-mesh kick operator (raymesh.cu): the context's hook into it.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.h"
+
+namespace hrt {
+
+// One KDK ray step over [chi_from, chi_to] whose two half kicks come from ray meshes (hrt_raymesh_ray_step);
+// maps == nullptr skips the readout, accumulate != 0 adds weight times the observables.
+hrt_status raymesh_step(hrt_raymesh* rm, const hrt_rays& rays, const float* grad_x, const float* grad_y,
+                        const hrt_ray_geom& g, double chi_from, double chi_to, double a_ref, double omega_m,
+                        float* maps, int accumulate, float weight, cudaStream_t s);
+
+}  // namespace hrt

@@ -42,6 +42,11 @@ class hrt_ray_geom(C.Structure):
                 ("replica_sign", C.c_void_p), ("replica_shift", C.c_void_p)]
 
 
+class hrt_raymesh_config(C.Structure):
+    _fields_ = [("iota", C.c_double), ("p_min", C.c_double), ("mu", C.c_double), ("m_pix", C.c_int64),
+                ("n2d_max", C.c_int64)]
+
+
 class hrt_cosmology(C.Structure):
     _fields_ = [("omega_m", C.c_double), ("h", C.c_double), ("n_s", C.c_double), ("sigma8", C.c_double)]
 
@@ -79,6 +84,12 @@ _SIGS = {
     "hrt_ray_step": ([_P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
     "hrt_ray_step_tiled": ([_P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
     "hrt_set_replicas": ([_P, _I32, _P, _P, _P], C.c_int),
+    "hrt_raymesh_geometry": ([_P, _D, _D, _D, _P, _P, _P], C.c_int),
+    "hrt_raymesh_create": ([_P, _P], C.c_int),
+    "hrt_raymesh_destroy": ([_P], C.c_int),
+    "hrt_raymesh_kick": ([_P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
+    "hrt_raymesh_ray_step": ([_P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
+    "hrt_set_ray_mesh": ([_P, _P], C.c_int),
     "hrt_ray_drift_free": ([_P, _D, _D, _P], C.c_int),
     "hrt_ray_readout": ([_P, _P, _P], C.c_int),
     "hrt_kappa_power": ([_P, _I64, _D, _I32, _D, _D, _P, _P, _P, _P], C.c_int),
@@ -369,6 +380,56 @@ def hrt_ray_step_tiled(rays: RayState, grad: torch.Tensor, geom: hrt_ray_geom, c
                                    _ptr(maps, torch.float32, "maps"), _stream(stream)), "hrt_ray_step_tiled")
 
 
+def make_raymesh_config(iota: float, p_min: float, mu: float, m_pix: int, n2d_max: int = 0) -> hrt_raymesh_config:
+    return hrt_raymesh_config(iota, p_min, mu, m_pix, n2d_max)
+
+
+def hrt_raymesh_geometry(cfg: hrt_raymesh_config, chi_a: float, chi_b: float, cell: float):
+    """(lambda_lim, x2d, N) of the ray mesh of the half shell [chi_a, chi_b)."""
+    lam, x2d, n2d = C.c_double(), C.c_double(), C.c_int64()
+    _check(_lib.hrt_raymesh_geometry(C.byref(cfg), chi_a, chi_b, cell, C.byref(lam), C.byref(x2d), C.byref(n2d)),
+           "hrt_raymesh_geometry")
+    return lam.value, x2d.value, n2d.value
+
+
+class RayMesh:
+    """Owner of an ``hrt_raymesh`` workspace (ray-mesh kick operator)."""
+
+    def __init__(self, cfg: hrt_raymesh_config):
+        self.cfg = cfg
+        self._h = C.c_void_p()
+        _check(_lib.hrt_raymesh_create(C.byref(cfg), C.byref(self._h)), "hrt_raymesh_create")
+
+    def hrt_raymesh_kick(self, grad_x, grad_y, geom: hrt_ray_geom, chi_a: float, chi_b: float, a_ref: float = 0.0,
+                         omega_m: float = 0.3, stream=None) -> torch.Tensor:
+        """The filtered ray mesh of one half shell as a (N, N, 2) float32 device tensor."""
+        _, _, n2d = hrt_raymesh_geometry(self.cfg, chi_a, chi_b, geom.box / geom.n)
+        out = torch.empty(n2d, n2d, 2, dtype=torch.float32, device=grad_x.device)
+        _check(_lib.hrt_raymesh_kick(self._h, _ptr(grad_x, torch.float32, "grad_x"), _ptr(grad_y, torch.float32, "grad_y"),
+                                     C.byref(geom), chi_a, chi_b, a_ref, omega_m, _ptr(out, torch.float32, "mesh"),
+                                     _stream(stream)), "hrt_raymesh_kick")
+        return out
+
+    def hrt_raymesh_ray_step(self, rays: RayState, grad_x, grad_y, geom: hrt_ray_geom, chi_from: float, chi_to: float,
+                             a_ref: float = 0.0, omega_m: float = 0.3, maps: torch.Tensor | None = None, stream=None):
+        r = rays.c()
+        _check(_lib.hrt_raymesh_ray_step(self._h, C.byref(r), _ptr(grad_x, torch.float32, "grad_x"),
+                                         _ptr(grad_y, torch.float32, "grad_y"), C.byref(geom), chi_from, chi_to, a_ref,
+                                         omega_m, _ptr(maps, torch.float32, "maps"), _stream(stream)),
+               "hrt_raymesh_ray_step")
+
+    def close(self):
+        if self._h:
+            _lib.hrt_raymesh_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def hrt_ray_drift_free(rays: RayState, chi_from: float, chi_to: float, stream=None):
     r = rays.c()
     _check(_lib.hrt_ray_drift_free(C.byref(r), chi_from, chi_to, _stream(stream)), "hrt_ray_drift_free")
@@ -594,6 +655,10 @@ class Context:
         t = [np.ascontiguousarray(x, dtype=np.int32) for x in replicas]
         _check(_lib.hrt_set_replicas(self._h, t[0].shape[0], t[0].ctypes.data, t[1].ctypes.data, t[2].ctypes.data),
                "hrt_set_replicas")
+
+    def hrt_set_ray_mesh(self, cfg: hrt_raymesh_config | None):
+        """Ray-mesh kick operator for the context's rays (a ``make_raymesh_config``), or None for the direct gather."""
+        _check(_lib.hrt_set_ray_mesh(self._h, None if cfg is None else C.byref(cfg)), "hrt_set_ray_mesh")
 
     def hrt_set_ray_kernel_table(self, table: torch.Tensor | None, kmax: float = 0.0):
         """Fixed learned table of the ray fields over |k| in [0, kmax] (float32 on the device), or None."""

@@ -101,3 +101,20 @@ def test_binding_refuses_to_load_without_library(tmp_path):
         (pkg / fn).write_text(open(os.path.join(ROOT, "paper_2405_12913_gb300", fn)).read())
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
     assert r.returncode != 0 and "is not built" in r.stderr
+
+
+def test_host_raymesh_geometry_matches_oracle(lib):
+    """The ray-mesh size rule of App. C on the host equals the oracle's, and bad configurations are refused
+    before any device work."""
+    from oracle import raymesh
+    for chi_a, chi_b, cell, mu, m, iota, p in ((150.5, 181.3, 2.0, 0.001, 100, 0.5, 8), (181.3, 150.5, 2.0, 0.001, 100, 0.5, 8),
+                                               (1000.0, 1010.0, 2.0, 0.003, 100, 1.0, 4), (30.0, 60.0, 0.98, 8.5e-5, 2048, 0.5, 256),
+                                               (3000.0, 3050.0, 0.98, 8.5e-5, 2048, 0.5, 256), (10.0, 12.0, 3.125, 3e-4, 403, 0.25, 32)):
+        want = raymesh.geometry(chi_a, chi_b, cell, mu, m, iota, p)
+        got = lib.hrt_raymesh_geometry(lib.make_raymesh_config(iota, p, mu, m, 32768), chi_a, chi_b, cell)
+        assert got[2] == want[2] and got[0] == pytest.approx(want[0], rel=1e-15) and got[1] == pytest.approx(want[1], rel=1e-15)
+    for bad in ((0.0, 8, 0.001, 64), (1.5, 8, 0.001, 64), (0.5, -1, 0.001, 64), (0.5, 8, 0.0, 64), (0.5, 8, 0.001, 0)):
+        with pytest.raises(lib.HRTError):
+            lib.RayMesh(lib.make_raymesh_config(*bad))
+    with pytest.raises(lib.HRTError):   # an 8192^2 mesh against a limit of 1024
+        lib.hrt_raymesh_geometry(lib.make_raymesh_config(0.5, 8, 1e-3, 4096, 1024), 1000.0, 1010.0, 2.0)

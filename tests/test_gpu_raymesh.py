@@ -1,0 +1,220 @@
+"""The ray-mesh kick operator (Sec. 5.2, Sec. 5.3, App. C) on the GPU against the FP64 oracle: the filtered mesh of
+one half shell, one KDK ray step with the A/B recursion, and a full co-evolution run of the context; then the
+operator on the point-mass lens against the Born integral of the exact periodic field."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synthetic
+from oracle import power as opow
+from oracle import raymesh, sim
+from oracle.units import C_LIGHT, G_NEWTON
+
+pytestmark = pytest.mark.gpu
+
+BOX, N = 64.0, 32
+OBS = (0.31 * BOX, 0.58 * BOX, 0.7)
+
+
+@pytest.fixture(scope="module")
+def hrt():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_12913_gb300 import hrt as h
+    return h
+
+
+def _fields(seed, scale=1.0):
+    g = torch.Generator().manual_seed(seed)
+    gx = scale * torch.randn(N, N, N, generator=g, dtype=torch.float64)
+    gy = scale * torch.randn(N, N, N, generator=g, dtype=torch.float64)
+    return gx.float(), gy.float()
+
+
+# (chi_a, chi_b, mu, m_pix, iota, p_min, a_ref, window)
+KICKS = [
+    (150.5, 181.3, 0.004, 40, 0.5, 8, 0.0, None),
+    (181.3, 150.5, 0.004, 40, 0.5, 8, 0.0, None),          # towards the observer
+    (150.5, 181.3, 0.003, 64, 0.25, 16, 0.0, None),
+    (40.2, 71.9, 0.003, 50, 1.0, 4, 0.8, None),            # near the observer, growth correction
+    (900.0, 1000.0, 0.0025, 64, 0.5, 8, 0.6, None),        # pixel-limited lambda_lim
+    (150.5, 181.3, 0.004, 40, 0.5, 8, 0.0, (160.0, 171.0)),  # static-lens window
+    (150.6, 150.65, 0.004, 40, 0.5, 8, 0.0, None),         # no plane: zero mesh
+]
+
+
+@pytest.mark.parametrize("case", range(len(KICKS)))
+def test_raymesh_kick_matches_oracle(hrt, case):
+    ca, cb, mu, m_pix, iota, p_min, a_ref, window = KICKS[case]
+    gx, gy = _fields(10 + case)
+    om = 0.3
+    wfn = sim.growth_weight(a_ref, om) if a_ref > 0 else (lambda chi: 1.0)
+    K, x2d, n2d = raymesh.mesh_kick(gx.double(), gy.double(), BOX, OBS, ca, cb, wfn, mu, m_pix, iota, p_min,
+                                    window=window)
+    cfg = hrt.make_raymesh_config(iota, p_min, mu, m_pix)
+    lam, x2d_g, n2d_g = hrt.hrt_raymesh_geometry(cfg, ca, cb, BOX / N)
+    assert n2d_g == n2d and x2d_g == pytest.approx(x2d, rel=1e-15)
+    rm = hrt.RayMesh(cfg)
+    geom = hrt.make_geom(N, BOX, OBS, window=window if window else (-1e300, 1e300))
+    out = rm.hrt_raymesh_kick(gx.cuda().reshape(-1), gy.cuda().reshape(-1), geom, ca, cb, a_ref, om)
+    torch.cuda.synchronize()
+    got = out.permute(2, 0, 1).double().cpu()
+    rm.close()
+    scale = float(K.abs().max())
+    if scale == 0.0:
+        assert float(got.abs().max()) == 0.0
+        return
+    err = float((got - K).abs().max())
+    # float32 deposit (~3e-6 relative) and float32 FFTs of an N^2 mesh
+    assert err <= 3e-5 * scale, (err / scale, n2d)
+
+
+@pytest.mark.parametrize("case", [0, 1, 3, 4])
+def test_raymesh_ray_step_matches_oracle(hrt, case):
+    ca, cb, mu, m_pix, iota, p_min, a_ref, _ = KICKS[case]
+    gx, gy = _fields(30 + case, 3e3)
+    om = 0.3
+    wfn = sim.growth_weight(a_ref, om) if a_ref > 0 else (lambda chi: 1.0)
+    rng = np.random.default_rng(case)
+    n = 4096
+    half = 0.5 * m_pix * mu
+    th0 = torch.tensor(rng.uniform(-1.2 * half, 1.2 * half, size=(n, 2)))   # some rays beyond the image
+    eta0 = torch.tensor(rng.normal(0, 2e-5, size=(n, 2))).float().double()
+    A0 = torch.tensor(rng.normal(0, 1, size=(n, 2, 2))).float().double()
+    B0 = torch.tensor(rng.normal(0, 1e-2, size=(n, 2, 2))).float().double()
+    st = dict(theta=th0.clone(), eta=eta0.clone(), A=A0.clone(), B=B0.clone())
+    want = raymesh.ray_step(st, gx.double(), gy.double(), BOX, OBS, ca, cb, wfn, mu, m_pix, iota, p_min)
+
+    rays = hrt.RayState(n)
+    rays.theta.copy_(th0.cuda())
+    rays.eta.copy_(eta0.float().cuda())
+    rays.A.copy_(A0.reshape(n, 4).float().cuda())
+    rays.B.copy_(B0.reshape(n, 4).float().cuda())
+    maps = torch.zeros(4, n, dtype=torch.float32, device="cuda")
+    rm = hrt.RayMesh(hrt.make_raymesh_config(iota, p_min, mu, m_pix))
+    rm.hrt_raymesh_ray_step(rays, gx.cuda().reshape(-1), gy.cuda().reshape(-1), hrt.make_geom(N, BOX, OBS), ca, cb,
+                            a_ref, om, maps)
+    torch.cuda.synchronize()
+    rm.close()
+    th = rays.theta.cpu()
+    deta = rays.eta.double().cpu() - eta0
+    dB = rays.B.double().cpu().reshape(n, 2, 2) - B0
+    d_eta_o = want["eta"] - eta0
+    d_B_o = want["B"] - B0
+    assert float(d_eta_o.abs().max()) > 1e-6 and float(d_B_o.abs().max()) > 1e-3   # the kicks matter
+    # the bilinear derivative jumps on ray-mesh cell faces: allow a rare ray on the other side of one
+    bad_eta = ((deta - d_eta_o).abs().max(dim=1).values > 1e-4 * float(d_eta_o.abs().max())).sum()
+    bad_B = ((dB - d_B_o).abs().amax(dim=(1, 2)) > 1e-4 * float(d_B_o.abs().max())).sum()
+    assert int(bad_eta) == 0 and int(bad_B) <= 2, (int(bad_eta), int(bad_B))
+    dth_o = want["theta"] - th0
+    assert float((th - want["theta"]).abs().max()) <= 1e-4 * float(dth_o.abs().max()) + 1e-15
+    A = rays.A.double().cpu().reshape(n, 2, 2)
+    assert float((A - want["A"]).abs().max()) <= 1e-6
+    k_o = 1.0 - 0.5 * (want["A"][:, 0, 0] + want["A"][:, 1, 1])
+    assert float((maps[0].double().cpu() - k_o).abs().max()) <= 1e-6
+
+
+def test_raymesh_rejects_bad_configurations(hrt):
+    from paper_2405_12913_gb300.hrt import HRTError
+    with pytest.raises(HRTError):
+        hrt.RayMesh(hrt.make_raymesh_config(0.0, 8, 0.001, 64))
+    with pytest.raises(HRTError):
+        hrt.RayMesh(hrt.make_raymesh_config(0.5, -1, 0.001, 64))
+    cfg = hrt.make_raymesh_config(0.5, 8, 1e-3, 4096, n2d_max=1024)
+    assert hrt.hrt_raymesh_geometry(hrt.make_raymesh_config(0.5, 8, 1e-3, 4096), 1000.0, 1010.0, 2.0)[2] == 8192
+    with pytest.raises(HRTError):      # needs an 8192^2 mesh
+        hrt.hrt_raymesh_geometry(cfg, 1000.0, 1010.0, 2.0)
+    rm = hrt.RayMesh(hrt.make_raymesh_config(0.5, 8, 0.004, 40))
+    gx, gy = _fields(1)
+    geom = hrt.make_geom(N, BOX, OBS, replicas=(np.array([[0, 1, 2]]), np.array([[1, 1, 1]]), np.array([[0, 0, 0]])))
+    with pytest.raises(HRTError):      # no light-cone tiling
+        rm.hrt_raymesh_kick(gx.cuda().reshape(-1), gy.cuda().reshape(-1), geom, 150.5, 181.3)
+    rm.close()
+
+
+def test_context_run_with_the_ray_mesh_matches_oracle(hrt):
+    """The small cosmological co-evolution with the context's kick operator switched to the ray mesh, against
+    the oracle's reverse run with the ray-mesh kick."""
+    from paper_2405_12913_gb300.configs import COSMO_TINY as W
+    rm_args = (W.dtheta, W.n_pix, 0.5, 8.0)
+    noise = synthetic.white_noise(W.seed, W.n_side)
+    theta0 = synthetic.pixel_grid(W.n_pix, W.fov_deg * synthetic.DEGREE)
+    cfg = hrt.make_config(W.n_mesh, W.box, W.n_side, W.omega_m, W.h, W.n_s, W.sigma8, W.deconv_p, W.smooth_cells,
+                          W.samples_per_cell, W.observer, n_sources=len(W.source_steps))
+    ctx = hrt.Context(cfg)
+    ctx.hrt_set_ray_mesh(hrt.make_raymesh_config(rm_args[2], rm_args[3], rm_args[0], rm_args[1]))
+    ctx.hrt_init_particles_zeldovich(torch.tensor(noise, dtype=torch.float32, device="cuda"), W.a_init)
+    for a in W.forward_grid[1:]:
+        ctx.hrt_step(a)
+    ctx.hrt_sync_particles()
+    ctx.hrt_init_rays(torch.tensor(theta0, device="cuda"))
+    slots = {s: i for i, s in enumerate(W.source_steps)}
+    for n, a in enumerate(W.reverse_grid[1:], start=1):
+        ctx.hrt_step(a, slots.get(n, -1))
+    maps = {s: ctx.hrt_read_maps(i).cpu().double().numpy() for s, i in slots.items()}
+    th = ctx.hrt_read_rays()[0].cpu().numpy()
+    lmin, lmax = W.ell_range
+    pk = {s: ctx.hrt_ctx_kappa_power(i, W.n_pix, W.dtheta, W.nbins, lmin, lmax) for s, i in slots.items()}
+    ctx.close()
+
+    c = sim.Cosmo(W.omega_m, W.h, W.n_s, W.sigma8)
+    flt = sim.Filter(W.deconv_p, W.smooth_cells)
+    part = sim.initial_particles(noise, W.box, c, W.a_init)
+    part, grads = sim.run_forward(part, W.forward_grid, W.box, W.n_mesh, c, flt)
+    res = sim.run_reverse(part, grads, W.reverse_grid, W.box, W.n_mesh, c, flt, torch.tensor(theta0), W.observer,
+                          set(W.source_steps), W.samples_per_cell, ray_mesh=rm_args)
+    for s in W.source_steps:
+        kap_o = res.maps[s][0].numpy()
+        rms = kap_o.std()
+        assert rms > 1e-4
+        for i in range(4):
+            err = np.abs(maps[s][i] - res.maps[s][i].numpy())
+            assert (err > 1e-3 * rms).mean() <= 2e-3 and np.median(err) <= 1e-4 * rms, (s, i, err.max() / rms)
+        ell_o, p_o, cnt_o = opow.kappa_power(kap_o.reshape(W.n_pix, W.n_pix), W.dtheta, W.nbins, lmin, lmax)
+        ell, p, cnt = pk[s]
+        assert np.array_equal(cnt, cnt_o)
+        ok = cnt_o > 0
+        assert np.allclose(p[ok], p_o[ok], rtol=1e-3), np.abs(p[ok] / p_o[ok] - 1).max()
+    alpha_o = theta0 - res.rays["theta"].numpy()
+    assert np.abs((theta0 - th) - alpha_o).max() <= 1e-4 * np.abs(alpha_o).max()
+
+
+def test_point_mass_with_the_ray_mesh_against_born_integral(hrt):
+    """Sec. 6.1 with the paper's kick operator: the 3D field carries only the CIC deconvolution (the ray mesh does
+    the smoothing, at lambda_lim); deflections above 4 cells against the Born integral of the exact periodic
+    field, normalised by the single-lens deflection."""
+    from paper_2405_12913_gb300.configs import POINT_MASS as W
+    theta0 = synthetic.polar_impact_grid(W.n_radial, W.n_azimuth, W.b_min_cells, W.b_max_cells, W.cell, W.chi_lens)
+    half = W.b_max_cells * W.cell / W.chi_lens
+    mu = 0.1 * W.cell / W.chi_lens
+    m_pix = int(math.ceil(2 * half / mu))
+    cfg = hrt.make_config(W.n_mesh, W.box, 1, deconv_p=W.deconv_p, smooth_cells=0.0,
+                          samples_per_cell=W.samples_per_cell, observer=W.observer, static_mode=True,
+                          static_pref=W.static_pref, n_sources=1)
+    ctx = hrt.Context(cfg)
+    ctx.hrt_set_ray_mesh(hrt.make_raymesh_config(0.5, 32.0, mu, m_pix))
+    lens = torch.tensor([[W.lens_position[0]], [W.lens_position[1]], [W.lens_position[2]]], dtype=torch.float32,
+                        device="cuda")
+    ctx.hrt_init_particles(lens, torch.zeros_like(lens), 1.0)
+    ctx.hrt_init_rays(torch.tensor(theta0, device="cuda"))
+    chis = W.chi_grid
+    for i in range(W.n_steps):
+        ctx.hrt_step_static(chis[i], chis[i + 1], -1)
+    ctx.hrt_drift_free(chis[-1], W.chi_source)
+    th = ctx.hrt_read_rays()[0].cpu().numpy()
+    ctx.close()
+    alpha = theta0 - th
+    b = W.chi_lens * np.hypot(theta0[:, 0], theta0[:, 1]) / W.cell
+    pmc = sim.PointMass(W.n_mesh, W.box, W.mass, W.chi_lens, W.chi_source, W.n_steps, W.deconv_p, 0.0,
+                        W.samples_per_cell)
+    sel = np.flatnonzero(b > 4.0)[::53]
+    born = sim.point_mass_born_ewald(pmc, theta0[sel], 300)
+    lever = (W.chi_source - W.chi_lens) / W.chi_source * 4 * G_NEWTON * W.mass / C_LIGHT ** 2
+    err = np.linalg.norm(alpha[sel] - born, axis=1) / (lever / (b[sel] * W.cell))
+    far = b[sel] > 10.0
+    print("ray mesh point mass: median %.4f max %.4f; beyond 10 cells median %.4f max %.4f"
+          % (np.median(err), err.max(), np.median(err[far]), err[far].max()))
+    assert np.median(err) < 0.01 and err.max() < 0.05
+    assert np.median(err[far]) < 0.005
