@@ -50,6 +50,8 @@ def parse():
                    help="skip the timings of the widened rows (tiled light cone, accumulated sources, 2LPT ICs)")
     p.add_argument("--no-learned", action="store_true",
                    help="skip the learned-correction comparison (coarse learned vs coarse plain vs fine plain)")
+    p.add_argument("--kick", default="direct", choices=["direct", "mesh"],
+                   help="kick operator of the rays: the direct line-of-sight gather or the ray mesh of Sec. 5.2")
     return p.parse_args()
 
 
@@ -155,6 +157,26 @@ def recorded_traffic(kernel: str, workload: str):
     return d.get("dram_bytes_per_launch")
 
 
+# the ray mesh with the paper's hyper-parameters (iota = 0.5, p_min = 256; App. C) and the image's pixel size
+RAYMESH_IOTA, RAYMESH_P_MIN = 0.5, 256.0
+
+
+def raymesh_config(hrt, W):
+    return hrt.make_raymesh_config(RAYMESH_IOTA, RAYMESH_P_MIN, W.dtheta, W.n_pix)
+
+
+def raymesh_sides(hrt, W):
+    """Smallest and largest ray-mesh side over the half shells of the reverse grid."""
+    from paper_2405_12913_gb300.hrt import hrt_cosmo_eval
+    chis = [hrt_cosmo_eval(W.omega_m, a)[1] for a in W.reverse_grid]
+    sides = []
+    for a, b in zip(chis[:-1], chis[1:]):
+        m = 0.5 * (a + b)
+        for lo, hi in ((a, m), (m, b)):
+            sides.append(hrt.hrt_raymesh_geometry(raymesh_config(hrt, W), lo, hi, W.box / W.n_mesh)[2])
+    return min(sides), max(sides)
+
+
 def algorithmic_bytes(W):
     """Algorithmic HBM bytes per launch (one read or write per element)."""
     mesh = W.n_mesh ** 3 * 4
@@ -209,10 +231,18 @@ def run_gpu(args, W, world, rank, local):
     disp0, mom0, _, _ = ctx.hrt_read_particles()
     grid = W.reverse_grid
     slots = {s: i for i, s in enumerate(W.source_steps)}
+    # own kernels per ray step: the direct gather is one launch; the ray mesh is, per half shell, the projection
+    # and the filter (around cuFFT's transforms), then the ray kernel
+    ray_launches = 1
+    if args.kick == "mesh":
+        ctx.hrt_set_ray_mesh(raymesh_config(hrt, W))
+        ray_launches = 5
 
     def reset():
         ctx.hrt_init_particles(disp0, mom0, 1.0)
         ctx.hrt_init_rays(theta0)
+
+    reset.state = (disp0, mom0, theta0)
 
     def run_steps(k, start=0):
         """k reverse steps continuing at reverse index `start`, cycling through the reverse grid."""
@@ -225,7 +255,7 @@ def run_gpu(args, W, world, rank, local):
                 pos = 0
             n = pos + 1
             ctx.hrt_step(grid[n], slots.get(n, -1))
-            launches += 3  # ray step, kick-drift-deposit, k-space pass (x-pass on the split path)
+            launches += 2 + ray_launches  # ray step, kick-drift-deposit, k-space pass (x-pass on the split path)
             pos = n
         return pos, launches
 
@@ -302,7 +332,9 @@ def run_gpu(args, W, world, rank, local):
 
     # roofline of the dominant kernel of this library (by time in the phase pass)
     algo = algorithmic_bytes(W)
-    own = {k: phases[k] for k in ("ray_step", "kick_drift", "cic_scatter", "kspace")}
+    if args.kick == "mesh":
+        algo.pop("ray_step")   # the ray-mesh phase is mesh builds and FFTs, not the ray-state traffic
+    own = {k: phases[k] for k in ("ray_step", "kick_drift", "cic_scatter", "kspace") if k in algo}
     dom = max(own, key=lambda k: own[k][0])
     t_ms, cnt = own[dom]
     peak, peak_kind = measured_peaks()
@@ -325,6 +357,8 @@ def run_gpu(args, W, world, rank, local):
         "config": {"workload": W.name, "n_particles": W.n_side ** 3, "n_mesh": W.n_mesh, "box_mpc_h": W.box,
                    "n_rays": W.n_rays, "fov_deg": W.fov_deg, "reverse_steps": W.n_reverse,
                    "timed_steps_start_at_a": 1.0, "parallelism": f"replicas{world}",
+                   "kick": ("ray mesh (iota %g, p_min %g)" % (RAYMESH_IOTA, RAYMESH_P_MIN)
+                            if args.kick == "mesh" else "direct line-of-sight gather"),
                    "l2": "inputs larger than L2 (4.3 GB mesh per field)"},
         "clocks": clk, "gpu_launches": launches,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -341,13 +375,15 @@ def run_gpu(args, W, world, rank, local):
 def next_rows(args, W, ctx, reset, grid, slots, run_steps, stream, seed):
     """Timings of the rows beyond the measured step, on the same workload and context: the ray step through a
     light cone tiled by rotated, translated replicas against the plain one (phase timing), the step with the
-    accumulating readout of a source distribution, and 2LPT against Zel'dovich initial conditions."""
+    accumulating readout of a source distribution, the ray-mesh kick operator against the direct gather
+    (ray-step time and kappa power of full reverse runs), and 2LPT against Zel'dovich initial conditions."""
     import numpy as np
     import torch
     import synthetic
     from paper_2405_12913_gb300 import hrt
     steps = min(16, len(grid) - 1)
     out = {"steps": steps}
+    ctx.hrt_set_ray_mesh(None)   # the rows below start from the direct gather
     # tiled light cone: enough replicas for the deepest node
     from paper_2405_12913_gb300.hrt import hrt_cosmo_eval
     n_rep = int(math.floor((W.observer[2] + hrt_cosmo_eval(W.omega_m, W.a_min)[1]) / W.box)) + 2
@@ -370,6 +406,53 @@ def next_rows(args, W, ctx, reset, grid, slots, run_steps, stream, seed):
     e1.record(stream)
     torch.cuda.synchronize()
     out["accumulate_step_ms"] = e0.elapsed_time(e1) / steps
+    # the paper's ray-mesh kick operator against the direct gather: full reverse runs from a = 1 on the same
+    # particles, ray-step phase time and the kappa power spectra of every source plane
+    lmin, lmax = W.ell_range
+    runs = {}
+    for name, cfg in (("direct", None), ("mesh", raymesh_config(hrt, W))):
+        ctx.hrt_set_ray_mesh(cfg)
+        reset()
+        ctx.hrt_ctx_set_profiling(True)
+        run_steps(len(grid) - 1, 0)
+        ph = ctx.hrt_ctx_phase_times()
+        ctx.hrt_ctx_set_profiling(False)
+        pk = {s: ctx.hrt_ctx_kappa_power(i, W.n_pix, W.dtheta, W.nbins, lmin, lmax) for s, i in slots.items()}
+        runs[name] = (ph["ray_step"][0] / max(ph["ray_step"][1], 1), pk)
+    ctx.hrt_set_ray_mesh(None)
+    # the paper's arrangement: the rays' 3D fields carry only the CIC deconvolution and the ray mesh does the
+    # smoothing (separately filtered ray fields in a second context on the same particles)
+    cfg2 = hrt.make_config(W.n_mesh, W.box, W.n_side, W.omega_m, W.h, W.n_s, W.sigma8, W.deconv_p, W.smooth_cells,
+                           W.samples_per_cell, W.observer, n_sources=len(W.source_steps), ray_fields=2,
+                           ray_deconv_p=W.deconv_p, ray_smooth_cells=0.0)
+    ctx2 = hrt.Context(cfg2)
+    ctx2.hrt_set_ray_mesh(raymesh_config(hrt, W))
+    ctx2.hrt_init_particles(*reset.state[:2], 1.0)
+    ctx2.hrt_init_rays(reset.state[2])
+    ctx2.hrt_ctx_set_profiling(True)
+    for n in range(1, len(grid)):
+        ctx2.hrt_step(grid[n], slots.get(n, -1))
+    ph = ctx2.hrt_ctx_phase_times()
+    pk = {s: ctx2.hrt_ctx_kappa_power(i, W.n_pix, W.dtheta, W.nbins, lmin, lmax) for s, i in slots.items()}
+    runs["mesh_unsmoothed_3d"] = (ph["ray_step"][0] / max(ph["ray_step"][1], 1), pk)
+    ctx2.close()
+    cmp = {"iota": RAYMESH_IOTA, "p_min": RAYMESH_P_MIN, "ray_mesh_sides": list(raymesh_sides(hrt, W)),
+           "forms": {"direct": "direct gather of the 3D fields (Gaussian of 1 cell)",
+                     "mesh": "ray mesh over the same fields (3D Gaussian and 2D Gaussian at lambda_lim)",
+                     "mesh_unsmoothed_3d": "ray mesh over 3D fields without the Gaussian (the paper's arrangement)"},
+           "ray_step_ms": {k: v[0] for k, v in runs.items()}, "sources": {}}
+    for s in W.source_steps:
+        ell, p_d, cnt = runs["direct"][1][s]
+        ok = cnt > 0
+        e = ell[ok]
+        row = {"ell": [round(float(x), 1) for x in e]}
+        for name in ("mesh", "mesh_unsmoothed_3d"):
+            ratio = runs[name][1][s][1][ok] / p_d[ok]
+            row[f"power_ratio_{name}_over_direct"] = [round(float(x), 4) for x in ratio]
+            for cut in (1200, 3000):
+                row[f"{name}_max_dev_ell_le_{cut}"] = float(np.abs(ratio[e <= cut] - 1).max()) if (e <= cut).any() else None
+        cmp["sources"][str(s)] = row
+    out["kick_operators"] = cmp
     # initial conditions on the particle lattice
     noise = torch.from_numpy(synthetic.white_noise(seed, W.n_side).astype(np.float32)).cuda().reshape(-1)
     disp = torch.empty(3, W.n_side ** 3, device="cuda")

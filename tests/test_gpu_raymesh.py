@@ -216,5 +216,6 @@ def test_point_mass_with_the_ray_mesh_against_born_integral(hrt):
     far = b[sel] > 10.0
     print("ray mesh point mass: median %.4f max %.4f; beyond 10 cells median %.4f max %.4f"
           % (np.median(err), err.max(), np.median(err[far]), err[far].max()))
-    assert np.median(err) < 0.01 and err.max() < 0.05
-    assert np.median(err[far]) < 0.005
+    # the largest errors lie along the mesh axes at 4-12 cells, where the unsmoothed 3D force is anisotropic
+    assert np.median(err) < 0.002 and err.max() < 0.04
+    assert np.median(err[far]) < 0.001
