@@ -60,7 +60,9 @@ def mesh_kick(gx: torch.Tensor, gy: torch.Tensor, box: float, observer, chi_a: f
     sgn = 1.0 if chi_b >= chi_a else -1.0
     mesh = np.zeros((2, n2d, n2d))
     half_extent = 0.5 * n2d * x2d
-    gxn, gyn = gx.numpy(), gy.numpy()
+    # any n^3 array-like whose z planes [:, :, iz] can be read serves (only the shell's planes are read)
+    gxn = gx.numpy() if torch.is_tensor(gx) else gx
+    gyn = gy.numpy() if torch.is_tensor(gy) else gy
     idx = np.arange(n) * cell
     for kz, chi in shell_planes(chi_a, chi_b, cell, observer[2]):
         if window is not None and not (window[0] <= chi < window[1]):
@@ -76,16 +78,21 @@ def mesh_kick(gx: torch.Tensor, gy: torch.Tensor, box: float, observer, chi_a: f
         a1 = math.floor((observer[0] + reach) / box)
         b0 = math.floor((observer[1] - reach) / box)
         b1 = math.floor((observer[1] + reach) / box)
+        flat, wx_all, wy_all = [], [], []
         for ia in range(a0, a1 + 1):
-            tx = (idx + ia * box - observer[0]) / r
+            ux = ((idx + ia * box - observer[0]) / r) / x2d + n2d / 2
+            selx = np.flatnonzero((ux > -1) & (ux < n2d))     # node columns whose CIC weights reach the mesh
             for ib in range(b0, b1 + 1):
-                ty = (idx + ib * box - observer[1]) / r
-                ux = tx / x2d + n2d / 2
-                uy = ty / x2d + n2d / 2
-                ix = np.floor(ux).astype(np.int64)
-                iy = np.floor(uy).astype(np.int64)
-                fx = ux - ix
-                fy = uy - iy
+                uy = ((idx + ib * box - observer[1]) / r) / x2d + n2d / 2
+                sely = np.flatnonzero((uy > -1) & (uy < n2d))
+                if selx.size == 0 or sely.size == 0:
+                    continue
+                ix = np.floor(ux[selx]).astype(np.int64)
+                iy = np.floor(uy[sely]).astype(np.int64)
+                fx = ux[selx] - ix
+                fy = uy[sely] - iy
+                vxs = vx[np.ix_(selx, sely)]
+                vys = vy[np.ix_(selx, sely)]
                 for dx in (0, 1):
                     wxv = fx if dx else 1 - fx
                     jx = ix + dx
@@ -95,10 +102,13 @@ def mesh_kick(gx: torch.Tensor, gy: torch.Tensor, box: float, observer, chi_a: f
                         jy = iy + dy
                         oky = (jy >= 0) & (jy < n2d)
                         ww = np.outer(wxv * okx, wyv * oky)
-                        JX = np.broadcast_to(np.clip(jx, 0, n2d - 1)[:, None], ww.shape)
-                        JY = np.broadcast_to(np.clip(jy, 0, n2d - 1)[None, :], ww.shape)
-                        np.add.at(mesh[0], (JX, JY), ww * vx)
-                        np.add.at(mesh[1], (JX, JY), ww * vy)
+                        flat.append((np.clip(jx, 0, n2d - 1)[:, None] * n2d + np.clip(jy, 0, n2d - 1)[None, :]).ravel())
+                        wx_all.append((ww * vxs).ravel())
+                        wy_all.append((ww * vys).ravel())
+        if flat:
+            f = np.concatenate(flat)
+            mesh[0] += np.bincount(f, np.concatenate(wx_all), minlength=n2d * n2d).reshape(n2d, n2d)
+            mesh[1] += np.bincount(f, np.concatenate(wy_all), minlength=n2d * n2d).reshape(n2d, n2d)
     if not filtered:
         return torch.tensor(mesh), x2d, n2d
     # deconvolution and smoothing on the ray mesh

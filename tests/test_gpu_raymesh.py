@@ -219,3 +219,68 @@ def test_point_mass_with_the_ray_mesh_against_born_integral(hrt):
     # the largest errors lie along the mesh axes at 4-12 cells, where the unsmoothed 3D force is anisotropic
     assert np.median(err) < 0.002 and err.max() < 0.04
     assert np.median(err[far]) < 0.001
+
+
+class _Planes:
+    """An n^3 field that is zero except on the listed z planes; the oracle reads only planes [:, :, iz]."""
+
+    def __init__(self, n, planes):
+        self.shape = (n, n, n)
+        self.planes = planes
+        self.zero = np.zeros((n, n), dtype=np.float32)
+
+    def __getitem__(self, key):
+        return self.planes.get(key[2], self.zero)
+
+
+def test_raymesh_ray_step_at_the_bench_size(hrt):
+    """The last reverse step of the 1024^3 workload in the bench's ray-mesh configuration (2048^2 rays over 10 deg,
+    iota 0.5, p_min 256: two 2048^2 ray meshes over 1024^3 gradient fields), random fields on the shell's planes:
+    4096 sampled rays against the oracle step."""
+    from paper_2405_12913_gb300.configs import COSMO_1024 as W
+    om = W.omega_m
+    n, box = W.n_mesh, W.box
+    a0, a1 = W.reverse_grid[-2], W.reverse_grid[-1]
+    chi0, chi1 = hrt.hrt_cosmo_eval(om, a0)[1], hrt.hrt_cosmo_eval(om, a1)[1]
+    cell = box / n
+    kzs = sorted({k % n for k, _ in raymesh.shell_planes(chi0, chi1, cell, W.observer[2])})
+    rng = np.random.default_rng(7)
+    px = {k: rng.normal(0, 3e3, size=(n, n)).astype(np.float32) for k in kzs}
+    py = {k: rng.normal(0, 3e3, size=(n, n)).astype(np.float32) for k in kzs}
+    gx = torch.zeros(n, n, n, dtype=torch.float32, device="cuda")
+    gy = torch.zeros_like(gx)
+    for k in kzs:
+        gx[:, :, k] = torch.from_numpy(px[k]).cuda()
+        gy[:, :, k] = torch.from_numpy(py[k]).cuda()
+    theta0 = synthetic.pixel_grid(W.n_pix, W.fov_deg * synthetic.DEGREE)
+    nr = theta0.shape[0]
+    g = torch.Generator().manual_seed(3)
+    eta0 = (2e-5 * torch.randn(nr, 2, generator=g)).float()
+    A0 = (torch.eye(2).reshape(1, 4) + 0.05 * torch.randn(nr, 4, generator=g)).float()
+    B0 = (1e-2 * torch.randn(nr, 4, generator=g)).float()
+    rays = hrt.RayState(nr)
+    rays.theta.copy_(torch.from_numpy(theta0).cuda())
+    rays.eta.copy_(eta0.cuda())
+    rays.A.copy_(A0.cuda())
+    rays.B.copy_(B0.cuda())
+    rm = hrt.RayMesh(hrt.make_raymesh_config(0.5, 256.0, W.dtheta, W.n_pix))
+    rm.hrt_raymesh_ray_step(rays, gx.reshape(-1), gy.reshape(-1), hrt.make_geom(n, box, W.observer), chi0, chi1,
+                            a0, om)
+    torch.cuda.synchronize()
+    rm.close()
+    del gx, gy
+    idx = synthetic.sample_indices(11, nr, 4096)
+    st = dict(theta=torch.from_numpy(theta0[idx]), eta=eta0[idx].double(), A=A0[idx].double().reshape(-1, 2, 2),
+              B=B0[idx].double().reshape(-1, 2, 2))
+    e0, b0 = st["eta"].clone(), st["B"].clone()
+    want = raymesh.ray_step(st, _Planes(n, px), _Planes(n, py), box, W.observer, chi0, chi1,
+                            sim.growth_weight(a0, om), W.dtheta, W.n_pix, 0.5, 256.0)
+    deta = rays.eta[idx].double().cpu() - e0
+    dB = rays.B[idx].double().cpu().reshape(-1, 2, 2) - b0
+    d_eta_o, d_B_o = want["eta"] - e0, want["B"] - b0
+    assert float(d_eta_o.abs().max()) > 1e-7 and float(d_B_o.abs().max()) > 1e-4
+    bad_eta = ((deta - d_eta_o).abs().max(dim=1).values > 1e-4 * float(d_eta_o.abs().max())).sum()
+    bad_B = ((dB - d_B_o).abs().amax(dim=(1, 2)) > 1e-4 * float(d_B_o.abs().max())).sum()
+    assert int(bad_eta) == 0 and int(bad_B) <= 2, (int(bad_eta), int(bad_B))
+    dth = rays.theta[idx].cpu() - want["theta"]
+    assert float(dth.abs().max()) <= 1e-4 * float((want["theta"] - torch.from_numpy(theta0[idx])).abs().max()) + 1e-15
