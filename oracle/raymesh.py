@@ -48,12 +48,34 @@ def shell_planes(chi_a: float, chi_b: float, cell: float, observer_z: float):
     return out
 
 
+def plane_fields(g3, kz: int, replicas):
+    """Sky-frame transverse gradient (g_x, g_y) on the node plane of sky index kz (>= 0) of a light cone tiled by
+    replicas (perm, sign, shift): the plane lies in replica k = kz // n, whose sky axis a maps to box axis
+    perm[k, a] at node (sign[k, a] i_a + shift[k, perm[k, a]]) mod n; the sky components are
+    sign[k, a] g_{perm[k, a]} there (the tiling of ``rays.replica_frame`` restricted to mesh nodes)."""
+    n = g3[0].shape[0]
+    perm, sign, shift = (np.asarray(t) for t in replicas)
+    k = kz // n
+    if kz < 0 or k >= perm.shape[0]:
+        raise ValueError("a node plane lies outside the replicas")
+    p, sg, sh = perm[k], sign[k], shift[k]
+    ii = np.arange(n)
+    b = [None, None, None]
+    b[p[0]] = ((sg[0] * ii + sh[p[0]]) % n)[:, None]
+    b[p[1]] = ((sg[1] * ii + sh[p[1]]) % n)[None, :]
+    b[p[2]] = (sg[2] * (kz % n) + sh[p[2]]) % n
+    g = [x.numpy() if torch.is_tensor(x) else x for x in g3]
+    return sg[0] * g[p[0]][b[0], b[1], b[2]], sg[1] * g[p[1]][b[0], b[1], b[2]]
+
+
 def mesh_kick(gx: torch.Tensor, gy: torch.Tensor, box: float, observer, chi_a: float, chi_b: float, weight_fn,
-              mu: float, m_pix: int, iota: float, p_min: float, filtered: bool = True, window=None):
+              mu: float, m_pix: int, iota: float, p_min: float, filtered: bool = True, window=None, gz=None,
+              replicas=None):
     """The filtered kick of the half shell on its ray mesh: returns (K (2, N, N) float64 tensor, x2d, N), with
     K[c, i, j] the component c at the angle ((i - N/2) x2d, (j - N/2) x2d).  ``filtered=False`` returns the CIC
     deposit before the deconvolution and smoothing; planes outside ``window = (chi_lo, chi_hi)`` do not
-    contribute."""
+    contribute.  With ``replicas`` = (perm, sign, shift) the light cone is tiled by rotated, translated box
+    replicas (``plane_fields``, which needs the third field gz)."""
     n = gx.shape[0]
     cell = box / n
     lam, x2d, n2d = geometry(chi_a, chi_b, cell, mu, m_pix, iota, p_min)
@@ -69,9 +91,13 @@ def mesh_kick(gx: torch.Tensor, gy: torch.Tensor, box: float, observer, chi_a: f
             continue
         r = chi
         w = -(2.0 / C_LIGHT) * r * weight_fn(chi) * sgn * cell * cell * cell / (r * r * x2d * x2d)
-        iz = kz % n
-        vx = gxn[:, :, iz] * w
-        vy = gyn[:, :, iz] * w
+        if replicas is None:
+            iz = kz % n
+            vx = gxn[:, :, iz] * w
+            vy = gyn[:, :, iz] * w
+        else:
+            px, py = plane_fields((gx, gy, gz), kz, replicas)
+            vx, vy = px * w, py * w
         # transverse images that can land on the mesh
         reach = (half_extent + x2d) * r + cell
         a0 = math.floor((observer[0] - reach) / box)
@@ -147,18 +173,20 @@ def gather(K: torch.Tensor, x2d: float, theta: torch.Tensor):
 
 
 def ray_step(state: dict, gx, gy, box: float, observer, chi_n: float, chi_n1: float, weight_fn, mu: float,
-             m_pix: int, iota: float, p_min: float, window=None) -> dict:
+             m_pix: int, iota: float, p_min: float, window=None, gz=None, replicas=None) -> dict:
     """One KDK step with the A/B recursion (Alg. 1 order) whose two half kicks come from ray meshes."""
     theta, eta, A, B = state["theta"], state["eta"], state["A"], state["B"]
     chi_h = 0.5 * (chi_n + chi_n1)
-    K1, x1, _ = mesh_kick(gx, gy, box, observer, chi_n, chi_h, weight_fn, mu, m_pix, iota, p_min, window=window)
+    K1, x1, _ = mesh_kick(gx, gy, box, observer, chi_n, chi_h, weight_fn, mu, m_pix, iota, p_min, window=window,
+                          gz=gz, replicas=replicas)
     val, T = gather(K1, x1, theta)
     eta = eta + val
     B = B + T @ A
     d = (chi_n1 - chi_n) / (C_LIGHT * chi_h * chi_h)
     theta = theta + d * eta
     A = A + d * B
-    K2, x2, _ = mesh_kick(gx, gy, box, observer, chi_h, chi_n1, weight_fn, mu, m_pix, iota, p_min, window=window)
+    K2, x2, _ = mesh_kick(gx, gy, box, observer, chi_h, chi_n1, weight_fn, mu, m_pix, iota, p_min, window=window,
+                          gz=gz, replicas=replicas)
     val, T = gather(K2, x2, theta)
     eta = eta + val
     B = B + T @ A

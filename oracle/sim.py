@@ -124,7 +124,7 @@ def run_reverse(part: Particles, grads, a_grid, box: float, n_mesh: int, c: Cosm
                                   growth_weight(a_n, om), gz=grads[2], replicas=replicas)
         else:
             state = raymesh.ray_step(state, grads[0], grads[1], box, observer, chi_n, chi_n1,
-                                     growth_weight(a_n, om), *ray_mesh)
+                                     growth_weight(a_n, om), *ray_mesh, gz=grads[2], replicas=replicas)
         if (n + 1) in source_steps:
             res.maps[n + 1] = rays.observables(state["A"])
             res.thetas[n + 1] = state["theta"].clone()

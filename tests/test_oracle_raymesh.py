@@ -218,3 +218,51 @@ def test_filter_on_a_mesh_periodic_mode_at_mesh_nodes():
                                             + torch.sin(2 * kb * CELL * MX - kb * CELL * MY + 0.9))))
     assert torch.allclose(K[0], want_x, atol=1e-9 * abs(w))
     assert torch.allclose(K[1], want_y, atol=1e-9 * abs(w))
+
+
+def _g3(seed):
+    g = torch.Generator().manual_seed(seed)
+    return [torch.randn(N, N, N, generator=g, dtype=torch.float64) for _ in range(3)]
+
+
+def _rotated(g3, perm, sign, shift):
+    """Sky-frame mesh arrays g'_a[i] = sign_a g_{perm a}[M(i)], M(i)[perm a] = sign_a i_a + shift[perm a] (mod n),
+    built on the whole mesh at once (independently of the oracle's per-plane map)."""
+    n = g3[0].shape[0]
+    idx = np.indices((n, n, n)).reshape(3, -1)
+    b = np.zeros_like(idx)
+    for a in range(3):
+        b[perm[a]] = (sign[a] * idx[a] + shift[perm[a]]) % n
+    flat = (b[0] * n + b[1]) * n + b[2]
+    return [torch.tensor(sign[a] * g3[perm[a]].reshape(-1).numpy()[flat].reshape(n, n, n)) for a in range(3)]
+
+
+def test_tiled_mesh_with_identity_replicas_is_the_plain_mesh():
+    g3 = _g3(40)
+    ident = (np.tile([0, 1, 2], (12, 1)), np.ones((12, 3), np.int32), np.zeros((12, 3), np.int32))
+    args = (BOX, OBS, CHI_A, CHI_B, G, 0.002, 40, 0.5, 8)
+    K, _, _ = raymesh.mesh_kick(g3[0], g3[1], *args)
+    Kt, _, _ = raymesh.mesh_kick(g3[0], g3[1], *args, gz=g3[2], replicas=ident)
+    assert torch.equal(K, Kt)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_tiled_mesh_is_the_sum_of_plain_meshes_of_rotated_fields(seed):
+    """A shell that spans two replicas: its mesh equals the plain meshes of the two sub-shells, each over the
+    explicitly rotated and translated arrays of its replica (the kick is linear in the field)."""
+    import synthetic
+    g3 = _g3(50 + seed)
+    perm, sign, shift = synthetic.replica_transforms(seed, 12, N)
+    # replica k holds the sky planes kz with kz // N == k; the shell [150.5, 181.3) with O_z = 0.7 spans planes
+    # 76..90, i.e. replicas 4 (kz < 80) and 5
+    edge = 80 * CELL - OBS[2]
+    args = (BOX, OBS)
+    tail = (G, 0.002, 40, 0.5, 8)
+    Kt, x2d, n2d = raymesh.mesh_kick(g3[0], g3[1], *args, CHI_A, CHI_B, *tail, gz=g3[2], replicas=(perm, sign, shift))
+    parts = []
+    for k, (lo, hi) in ((4, (CHI_A, edge)), (5, (edge, CHI_B))):
+        r = _rotated(g3, perm[k], sign[k], shift[k])
+        parts.append(raymesh.mesh_kick(r[0], r[1], *args, CHI_A, CHI_B, *tail, window=(lo, hi))[0])
+    assert torch.allclose(Kt, parts[0] + parts[1], rtol=0, atol=1e-12 * float(Kt.abs().max()))
+    # and the tiling matters
+    assert float((Kt - raymesh.mesh_kick(g3[0], g3[1], *args, CHI_A, CHI_B, *tail)[0]).abs().max()) > 0.1 * float(Kt.abs().max())
