@@ -244,8 +244,10 @@ hrt_status hrt_ray_readout(const hrt_rays* rays, float* maps, void* stream);
  * both CIC steps and the Gaussian smoothing of Sec. 5.2), and the kick at a ray is the bilinear interpolation
  * of the mesh at its angle (zero outside the mesh), with dK/dtheta the derivative of that interpolant.
  * g(chi) is the growth correction of Eq. "kick" with a_ref (a_ref <= 0: g = 1).  The line of sight is the z
- * axis of the periodically replicated box; light-cone tiling (n_replicas != 0) is not supported
- * (HRT_ERR_INVALID_ARG), and samples_per_cell and image_width of the geometry are not used.  Computed in
+ * axis of the periodically replicated box, or, through the _tiled calls, of a light cone tiled by rotated and
+ * translated replicas (hrt_ray_geom): the plane z = kz cell lies in replica floor(kz / n), and its node (i, j)
+ * reads the box node that the replica's map gives for sky node (i, j, kz mod n), with the sky components
+ * sign_a grad_{perm a} there.  samples_per_cell and image_width of the geometry are not used.  Computed in
  * float32: the 3D-to-mesh positions start from an FP64 base per 8 x 32 block of mesh nodes; the ray angles
  * stay FP64.
  * ------------------------------------------------------------------------------------------------------ */
@@ -274,6 +276,12 @@ hrt_status hrt_raymesh_destroy(hrt_raymesh* rm);  /* NULL is fine; synchronises 
  * geometry or configuration, more than 512 planes in the shell, or a ray-mesh cell wider than 64 mesh cells. */
 hrt_status hrt_raymesh_kick(hrt_raymesh* rm, const float* grad_x, const float* grad_y, const hrt_ray_geom* geom,
                             double chi_a, double chi_b, double a_ref, double omega_m, float* mesh, void* stream);
+/* hrt_raymesh_kick through a tiled light cone (geom->n_replicas >= 1): grad_z is the third gradient field.
+ * HRT_ERR_INVALID_ARG also if a plane falls outside the replicas or a replica is malformed.  The untiled calls
+ * refuse a geometry with replicas. */
+hrt_status hrt_raymesh_kick_tiled(hrt_raymesh* rm, const float* grad_x, const float* grad_y, const float* grad_z,
+                                  const hrt_ray_geom* geom, double chi_a, double chi_b, double a_ref, double omega_m,
+                                  float* mesh, void* stream);
 
 /* One KDK ray step over [chi_from, chi_to] in the order of Alg. 1 (as hrt_ray_step) whose half kicks over
  * [chi_from, chi_mid) and [chi_mid, chi_to) come from their ray meshes; the drift is that of hrt_ray_step.
@@ -282,6 +290,9 @@ hrt_status hrt_raymesh_kick(hrt_raymesh* rm, const float* grad_x, const float* g
 hrt_status hrt_raymesh_ray_step(hrt_raymesh* rm, const hrt_rays* rays, const float* grad_x, const float* grad_y,
                                 const hrt_ray_geom* geom, double chi_from, double chi_to, double a_ref,
                                 double omega_m, float* maps, void* stream);
+hrt_status hrt_raymesh_ray_step_tiled(hrt_raymesh* rm, const hrt_rays* rays, const float* grad_x, const float* grad_y,
+                                      const float* grad_z, const hrt_ray_geom* geom, double chi_from, double chi_to,
+                                      double a_ref, double omega_m, float* maps, void* stream);
 
 /* ------------------------------------------------------------------------------------------------------
  * Convergence power spectrum: P(ell) = <|FFT2(kappa) dtheta^2|^2>_bin / (m dtheta)^2 over nbins log bins
@@ -481,9 +492,9 @@ hrt_status hrt_set_replicas(hrt_ctx* ctx, int32_t n, const int32_t* perm, const 
 
 /* Kick operator of the context's rays: cfg != NULL switches to the ray-mesh kick of hrt_raymesh_ray_step
  * (configuration copied; the context owns its workspace), cfg == NULL back to the direct line-of-sight
- * gather.  The ray mesh reads the same 3D fields as the direct gather (the ray fields when ray_fields == 2).
- * HRT_ERR_STATE with light-cone tiling; HRT_ERR_INVALID_ARG for a bad configuration.  Takes effect at the
- * next ray step. */
+ * gather.  The ray mesh reads the same 3D fields as the direct gather (the ray fields when ray_fields == 2; all
+ * three particle fields through a tiled light cone, hrt_set_replicas).  HRT_ERR_INVALID_ARG for a bad
+ * configuration.  Takes effect at the next ray step. */
 hrt_status hrt_set_ray_mesh(hrt_ctx* ctx, const hrt_raymesh_config* cfg);
 
 /* Fixed learned correction of the ray force: g_table[nk] (device float32, copied) sampled uniformly on

@@ -670,8 +670,8 @@ static hrt_status ctx_ray_step(hrt_ctx* ctx, double chi_from, double chi_to, dou
   const float* gx = ctx->ray_grad ? ctx->ray_grad : ctx->grad;
   float* maps = source >= 0 ? ctx->maps + static_cast<int64_t>(source) * 4 * ctx->rays.n_rays : nullptr;
   if (ctx->raymesh)
-    return raymesh_step(ctx->raymesh, ctx->rays, gx, gx + m, g, chi_from, chi_to, a_ref, c.cosmo.omega_m, maps,
-                        accumulate ? 1 : 0, static_cast<float>(weight), stream);
+    return raymesh_step(ctx->raymesh, ctx->rays, gx, gx + m, p.tiled ? ctx->grad + 2 * m : nullptr, g, chi_from,
+                        chi_to, a_ref, c.cosmo.omega_m, maps, accumulate ? 1 : 0, static_cast<float>(weight), stream);
   // a tiled light cone reads all three particle gradient fields (ray_fields == 0 is checked when it is set)
   return launch_ray_step(ctx->rays, gx, gx + m, p, maps, stream, p.tiled ? ctx->grad + 2 * m : nullptr);
 }
@@ -1593,7 +1593,6 @@ hrt_status hrt_set_replicas(hrt_ctx* ctx, int32_t n, const int32_t* perm, const 
     return HRT_OK;
   }
   if (ctx->cfg.ray_fields != 0) return fail(HRT_ERR_STATE, "light-cone tiling uses the particle fields (ray_fields == 0)");
-  if (ctx->raymesh) return fail(HRT_ERR_STATE, "the ray-mesh kick does not support light-cone tiling");
   if (n < 0 || n > kMaxReplicas || !perm || !sign || !shift)
     return fail(HRT_ERR_INVALID_ARG, "tiling needs 1..%d replicas with their perm, sign and shift tables", kMaxReplicas);
   // validate through the node-table builder (one empty shell at the observer's replica)
@@ -1613,7 +1612,6 @@ hrt_status hrt_set_replicas(hrt_ctx* ctx, int32_t n, const int32_t* perm, const 
 
 hrt_status hrt_set_ray_mesh(hrt_ctx* ctx, const hrt_raymesh_config* cfg) {
   HRT_TRY(ctx_guard(ctx));
-  if (cfg && !ctx->rep_perm.empty()) return fail(HRT_ERR_STATE, "the ray-mesh kick does not support light-cone tiling");
   hrt_raymesh* rm = nullptr;
   if (cfg) HRT_TRY(hrt_raymesh_create(cfg, &rm));
   if (ctx->ray_stream) cudaStreamSynchronize(ctx->ray_stream);

@@ -24,6 +24,7 @@
 
 #include "common.h"
 #include "cosmo.h"
+#include "mesh_kernels.h"
 #include "raymesh.h"
 #include "readout.cuh"
 
@@ -41,10 +42,20 @@ constexpr int kTileX = 8, kTileY = 32;  // ray-mesh nodes per CTA (x rows, y col
 constexpr double kMaxCellsPerMeshCell = 64.0;
 constexpr float kPif = 3.14159265358979f;
 
+// Light-cone tiling: where a replica's sky axes x, y and z land in the box (field of the sky components, box
+// stride, sign and translation in cells).
+struct ReplicaMap {
+  int64_t str_x, str_y, str_z;
+  int sh_x, sh_y, sh_z;
+  signed char sg_x, sg_y, sg_z;
+  unsigned char c_x, c_y;
+};
+
 struct ProjectParams {
   int n;         // 3D mesh side
   int n2d;       // ray-mesh side
   int n_planes;
+  int tiled;     // 0: the periodic box; 1: replicas (rep, rmap)
   int kz[kMaxMeshPlanes];        // plane index on the z axis, wrapped into [0, n)
   float w[kMaxMeshPlanes];       // -(2/c) r g(chi) (+-cell) cell^2 / (r^2 x2d^2)
   float pf[kMaxMeshPlanes];      // P = r x2d / cell (3D cells per ray-mesh cell)
@@ -52,6 +63,8 @@ struct ProjectParams {
   double p[kMaxMeshPlanes];      // P in FP64 for the CTA base
   double qx[kMaxMeshPlanes];     // position of ray-mesh node 0 in 3D cells: (O - r (N/2) x2d) / cell
   double qy[kMaxMeshPlanes];
+  unsigned char rep[kMaxMeshPlanes];  // replica of each plane (tiled)
+  ReplicaMap rmap[kMaxReplicas];
 };
 
 __device__ __forceinline__ int wrap(int i, int n) {
@@ -60,8 +73,13 @@ __device__ __forceinline__ int wrap(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
+// Box index along the box axis that receives a sky axis: i -> sgn i + sh (mod n).
+__device__ __forceinline__ int box_index(int i, int sgn, int sh, int n) { return wrap(sgn > 0 ? i + sh : sh - i, n); }
+
+template <bool TILED>
 __global__ void __launch_bounds__(kTileX * kTileY) raymesh_project_kernel(const float* __restrict__ gx,
                                                                          const float* __restrict__ gy,
+                                                                         const float* __restrict__ gz,
                                                                          const __grid_constant__ ProjectParams p,
                                                                          float2* __restrict__ mesh) {
   __shared__ int2 s_base[kMaxMeshPlanes];
@@ -87,22 +105,38 @@ __global__ void __launch_bounds__(kTileX * kTileY) raymesh_project_kernel(const 
     const int ilo = static_cast<int>(floorf(fx - P)), ihi = static_cast<int>(ceilf(fx + P));
     const int jlo = static_cast<int>(floorf(fy - P)), jhi = static_cast<int>(ceilf(fy + P));
     const int bx = s_base[q].x, by = s_base[q].y, kz = p.kz[q];
+    // sky-frame fields of the plane: the box itself, or the replica's rotated and translated view of it
+    const float* fxp = gx;
+    const float* fyp = gy;
+    float cx = 1.f, cy = 1.f;
+    int64_t zoff = kz;
+    const ReplicaMap* m = nullptr;
+    if (TILED) {
+      m = &p.rmap[p.rep[q]];
+      fxp = m->c_x == 0 ? gx : (m->c_x == 1 ? gy : gz);
+      fyp = m->c_y == 0 ? gx : (m->c_y == 1 ? gy : gz);
+      cx = m->sg_x;
+      cy = m->sg_y;
+      zoff = box_index(kz, m->sg_z, m->sh_z, n) * m->str_z;
+    }
     float sx = 0.f, sy = 0.f;
     for (int i = ilo; i <= ihi; ++i) {
       const float wx = 1.f - fabsf(static_cast<float>(i) - fx) * inv;
       if (wx <= 0.f) continue;
-      const int64_t row = static_cast<int64_t>(wrap(bx + i, n)) * nn;
+      const int xs = wrap(bx + i, n);
+      const int64_t row = TILED ? box_index(xs, m->sg_x, m->sh_x, n) * m->str_x + zoff : static_cast<int64_t>(xs) * nn;
       for (int j = jlo; j <= jhi; ++j) {
         const float wy = 1.f - fabsf(static_cast<float>(j) - fy) * inv;
         if (wy <= 0.f) continue;
-        const int64_t idx = (row + wrap(by + j, n)) * nn + kz;
+        const int ys = wrap(by + j, n);
+        const int64_t idx = TILED ? row + box_index(ys, m->sg_y, m->sh_y, n) * m->str_y : (row + ys) * nn + kz;
         const float ww = wx * wy;
-        sx += ww * __ldg(gx + idx);
-        sy += ww * __ldg(gy + idx);
+        sx += ww * __ldg(fxp + idx);
+        sy += ww * __ldg(fyp + idx);
       }
     }
-    kx += p.w[q] * sx;
-    ky += p.w[q] * sy;
+    kx += p.w[q] * cx * sx;
+    ky += p.w[q] * cy * sy;
   }
   mesh[static_cast<int64_t>(mx) * p.n2d + my] = make_float2(kx, ky);
 }
@@ -282,6 +316,37 @@ static hrt_status plane_table(const hrt_ray_geom& g, double chi_a, double chi_b,
   p.n = static_cast<int>(g.n);
   p.n2d = static_cast<int>(n2d);
   p.n_planes = 0;
+  p.tiled = g.n_replicas > 0 ? 1 : 0;
+  if (p.tiled) {
+    if (g.n_replicas > kMaxReplicas || !g.replica_perm || !g.replica_sign || !g.replica_shift)
+      return fail(HRT_ERR_INVALID_ARG, "tiling needs 1..%d replicas with their perm, sign and shift tables", kMaxReplicas);
+    const int64_t nn = g.n;
+    auto stride = [nn](int b) { return b == 0 ? nn * nn : (b == 1 ? nn : int64_t{1}); };
+    for (int k = 0; k < g.n_replicas; ++k) {
+      const int32_t* pm = g.replica_perm + 3 * k;
+      const int32_t* sg = g.replica_sign + 3 * k;
+      const int32_t* sh = g.replica_shift + 3 * k;
+      int seen = 0;
+      for (int a = 0; a < 3; ++a) {
+        if (pm[a] < 0 || pm[a] > 2 || (sg[a] != 1 && sg[a] != -1) || sh[a] < 0 || sh[a] >= g.n)
+          return fail(HRT_ERR_INVALID_ARG, "replica %d: bad axis, sign or shift", k);
+        seen |= 1 << pm[a];
+      }
+      if (seen != 7) return fail(HRT_ERR_INVALID_ARG, "replica %d: the axes are not a permutation", k);
+      ReplicaMap& m = p.rmap[k];
+      m.c_x = static_cast<unsigned char>(pm[0]);
+      m.c_y = static_cast<unsigned char>(pm[1]);
+      m.str_x = stride(pm[0]);
+      m.str_y = stride(pm[1]);
+      m.str_z = stride(pm[2]);
+      m.sg_x = static_cast<signed char>(sg[0]);
+      m.sg_y = static_cast<signed char>(sg[1]);
+      m.sg_z = static_cast<signed char>(sg[2]);
+      m.sh_x = sh[pm[0]];
+      m.sh_y = sh[pm[1]];
+      m.sh_z = sh[pm[2]];
+    }
+  }
   const int64_t k0 = static_cast<int64_t>(std::ceil((oz + lo) / cell)) - 1;
   const int64_t k1 = static_cast<int64_t>(std::ceil((oz + hi) / cell));
   for (int64_t kz = k0; kz <= k1; ++kz) {
@@ -301,7 +366,15 @@ static hrt_status plane_table(const hrt_ray_geom& g, double chi_a, double chi_b,
     const double qy = (g.observer[1] - r * (0.5 * n2d) * x2d) / cell;
     // the CTA bases qx + m0 P must stay well inside the int range
     if (std::fabs(qx) + n2d * P > 1.0e9 || std::fabs(qy) + n2d * P > 1.0e9) return fail(HRT_ERR_INVALID_ARG, "ray mesh too far from the box");
+    int64_t rep = 0;
+    if (p.tiled) {
+      // the plane z = kz cell lies in replica floor(kz / n)
+      rep = kz >= 0 ? kz / g.n : -1;
+      if (rep < 0 || rep >= g.n_replicas)
+        return fail(HRT_ERR_INVALID_ARG, "mesh plane at chi = %g is outside the %d replicas", chi, g.n_replicas);
+    }
     const int q = p.n_planes++;
+    p.rep[q] = static_cast<unsigned char>(rep);
     int64_t kzw = kz % g.n;
     if (kzw < 0) kzw += g.n;
     p.kz[q] = static_cast<int>(kzw);
@@ -315,10 +388,11 @@ static hrt_status plane_table(const hrt_ray_geom& g, double chi_a, double chi_b,
   return HRT_OK;
 }
 
-static hrt_status check_geom(const hrt_ray_geom* g) {
+static hrt_status check_geom(const hrt_ray_geom* g, bool tiled) {
   if (!g) return fail(HRT_ERR_INVALID_ARG, "geometry is NULL");
   if (g->n < 2 || g->n > 8192 || !(g->box > 0.0)) return fail(HRT_ERR_INVALID_ARG, "bad mesh or box");
-  if (g->n_replicas != 0) return fail(HRT_ERR_INVALID_ARG, "the ray-mesh kick does not support light-cone tiling");
+  if (!tiled && g->n_replicas != 0) return fail(HRT_ERR_INVALID_ARG, "a tiled geometry needs the tiled call (three fields)");
+  if (tiled && g->n_replicas < 1) return fail(HRT_ERR_INVALID_ARG, "the tiled call needs n_replicas >= 1");
   return HRT_OK;
 }
 
@@ -347,9 +421,9 @@ static hrt_status plan_for(hrt_raymesh* rm, int64_t n2d, cudaStream_t s, cufftHa
 
 // Builds the filtered ray mesh of the half shell [chi_a, chi_b) in rm->mesh[h]; view.k == nullptr when the
 // shell holds no plane.
-static hrt_status build_mesh(hrt_raymesh* rm, int h, const float* gx, const float* gy, const hrt_ray_geom& g,
-                             double chi_a, double chi_b, double a_ref, double omega_m, cudaStream_t s,
-                             MeshView& view) {
+static hrt_status build_mesh(hrt_raymesh* rm, int h, const float* gx, const float* gy, const float* gz,
+                             const hrt_ray_geom& g, double chi_a, double chi_b, double a_ref, double omega_m,
+                             cudaStream_t s, MeshView& view) {
   static thread_local ProjectParams p;
   double lam, x2d;
   int64_t n2d;
@@ -362,7 +436,12 @@ static hrt_status build_mesh(hrt_raymesh* rm, int h, const float* gx, const floa
   HRT_TRY(ensure_mesh(rm, h, n2d * n2d, s));
   float2* mesh = rm->mesh[h];
   const dim3 grid(static_cast<unsigned>((n2d + kTileY - 1) / kTileY), static_cast<unsigned>((n2d + kTileX - 1) / kTileX));
-  raymesh_project_kernel<<<grid, kTileX * kTileY, 0, s>>>(gx, gy, p, mesh);
+  if (p.tiled) {
+    if (!gz) return fail(HRT_ERR_INVALID_ARG, "light-cone tiling needs the third gradient component");
+    raymesh_project_kernel<true><<<grid, kTileX * kTileY, 0, s>>>(gx, gy, gz, p, mesh);
+  } else {
+    raymesh_project_kernel<false><<<grid, kTileX * kTileY, 0, s>>>(gx, gy, gz, p, mesh);
+  }
   HRT_LAUNCHED("raymesh_project_kernel");
   cufftHandle plan;
   HRT_TRY(plan_for(rm, n2d, s, plan));
@@ -381,14 +460,14 @@ static hrt_status build_mesh(hrt_raymesh* rm, int h, const float* gx, const floa
   return HRT_OK;
 }
 
-hrt_status raymesh_step(hrt_raymesh* rm, const hrt_rays& rays, const float* gx, const float* gy,
+hrt_status raymesh_step(hrt_raymesh* rm, const hrt_rays& rays, const float* gx, const float* gy, const float* gz,
                         const hrt_ray_geom& g, double chi_from, double chi_to, double a_ref, double omega_m,
                         float* maps, int accumulate, float weight, cudaStream_t s) {
   const double chi_mid = 0.5 * (chi_from + chi_to);
   if (!(chi_mid > 0.0)) return fail(HRT_ERR_INVALID_ARG, "shell midpoint must be at chi > 0");
   RayMeshParams p{};
-  HRT_TRY(build_mesh(rm, 0, gx, gy, g, chi_from, chi_mid, a_ref, omega_m, s, p.m[0]));
-  HRT_TRY(build_mesh(rm, 1, gx, gy, g, chi_mid, chi_to, a_ref, omega_m, s, p.m[1]));
+  HRT_TRY(build_mesh(rm, 0, gx, gy, gz, g, chi_from, chi_mid, a_ref, omega_m, s, p.m[0]));
+  HRT_TRY(build_mesh(rm, 1, gx, gy, gz, g, chi_mid, chi_to, a_ref, omega_m, s, p.m[1]));
   p.drift_d = (chi_to - chi_from) / (kCLight * chi_mid * chi_mid);
   p.drift = static_cast<float>(p.drift_d);
   p.map_accumulate = accumulate;
@@ -399,6 +478,33 @@ hrt_status raymesh_step(hrt_raymesh* rm, const hrt_rays& rays, const float* gx, 
       reinterpret_cast<float4*>(rays.B), rays.n_rays, p, maps);
   HRT_LAUNCHED("raymesh_ray_kernel");
   return HRT_OK;
+}
+
+static hrt_status kick_call(hrt_raymesh* rm, const float* grad_x, const float* grad_y, const float* grad_z,
+                            const hrt_ray_geom* geom, double chi_a, double chi_b, double a_ref, double omega_m,
+                            float* mesh, void* stream) {
+  if (!rm || !grad_x || !grad_y || !mesh) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  HRT_TRY(check_geom(geom, grad_z != nullptr));
+  if (!(omega_m > 0.0 && omega_m <= 1.0)) return fail(HRT_ERR_INVALID_ARG, "omega_m must be in (0, 1]");
+  cudaStream_t s = as_stream(stream);
+  MeshView v{};
+  HRT_TRY(build_mesh(rm, 0, grad_x, grad_y, grad_z, *geom, chi_a, chi_b, a_ref, omega_m, s, v));
+  const size_t bytes = static_cast<size_t>(v.n2d) * v.n2d * sizeof(float2);
+  if (v.k == nullptr) return cuda_status(cudaMemsetAsync(mesh, 0, bytes, s), "clear ray mesh");
+  return cuda_status(cudaMemcpyAsync(mesh, v.k, bytes, cudaMemcpyDeviceToDevice, s), "copy ray mesh");
+}
+
+static hrt_status step_call(hrt_raymesh* rm, const hrt_rays* rays, const float* grad_x, const float* grad_y,
+                            const float* grad_z, const hrt_ray_geom* geom, double chi_from, double chi_to,
+                            double a_ref, double omega_m, float* maps, void* stream) {
+  if (!rm || !grad_x || !grad_y) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  if (!rays) return fail(HRT_ERR_INVALID_ARG, "rays is NULL");
+  if (rays->n_rays < 0 || (rays->n_rays > 0 && (!rays->theta || !rays->eta || !rays->A || !rays->B)))
+    return fail(HRT_ERR_INVALID_ARG, "bad ray state");
+  HRT_TRY(check_geom(geom, grad_z != nullptr));
+  if (!(omega_m > 0.0 && omega_m <= 1.0)) return fail(HRT_ERR_INVALID_ARG, "omega_m must be in (0, 1]");
+  return raymesh_step(rm, *rays, grad_x, grad_y, grad_z, *geom, chi_from, chi_to, a_ref, omega_m, maps, 0, 1.f,
+                      as_stream(stream));
 }
 
 }  // namespace hrt
@@ -437,28 +543,27 @@ hrt_status hrt_raymesh_destroy(hrt_raymesh* rm) {
 
 hrt_status hrt_raymesh_kick(hrt_raymesh* rm, const float* grad_x, const float* grad_y, const hrt_ray_geom* geom,
                             double chi_a, double chi_b, double a_ref, double omega_m, float* mesh, void* stream) {
-  if (!rm || !grad_x || !grad_y || !mesh) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
-  HRT_TRY(check_geom(geom));
-  if (!(omega_m > 0.0 && omega_m <= 1.0)) return fail(HRT_ERR_INVALID_ARG, "omega_m must be in (0, 1]");
-  cudaStream_t s = as_stream(stream);
-  MeshView v{};
-  HRT_TRY(build_mesh(rm, 0, grad_x, grad_y, *geom, chi_a, chi_b, a_ref, omega_m, s, v));
-  const size_t bytes = static_cast<size_t>(v.n2d) * v.n2d * sizeof(float2);
-  if (v.k == nullptr) return cuda_status(cudaMemsetAsync(mesh, 0, bytes, s), "clear ray mesh");
-  return cuda_status(cudaMemcpyAsync(mesh, v.k, bytes, cudaMemcpyDeviceToDevice, s), "copy ray mesh");
+  return kick_call(rm, grad_x, grad_y, nullptr, geom, chi_a, chi_b, a_ref, omega_m, mesh, stream);
+}
+
+hrt_status hrt_raymesh_kick_tiled(hrt_raymesh* rm, const float* grad_x, const float* grad_y, const float* grad_z,
+                                  const hrt_ray_geom* geom, double chi_a, double chi_b, double a_ref, double omega_m,
+                                  float* mesh, void* stream) {
+  if (!grad_z) return fail(HRT_ERR_INVALID_ARG, "grad_z is NULL");
+  return kick_call(rm, grad_x, grad_y, grad_z, geom, chi_a, chi_b, a_ref, omega_m, mesh, stream);
 }
 
 hrt_status hrt_raymesh_ray_step(hrt_raymesh* rm, const hrt_rays* rays, const float* grad_x, const float* grad_y,
                                 const hrt_ray_geom* geom, double chi_from, double chi_to, double a_ref,
                                 double omega_m, float* maps, void* stream) {
-  if (!rm || !grad_x || !grad_y) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
-  if (!rays) return fail(HRT_ERR_INVALID_ARG, "rays is NULL");
-  if (rays->n_rays < 0 || (rays->n_rays > 0 && (!rays->theta || !rays->eta || !rays->A || !rays->B)))
-    return fail(HRT_ERR_INVALID_ARG, "bad ray state");
-  HRT_TRY(check_geom(geom));
-  if (!(omega_m > 0.0 && omega_m <= 1.0)) return fail(HRT_ERR_INVALID_ARG, "omega_m must be in (0, 1]");
-  return raymesh_step(rm, *rays, grad_x, grad_y, *geom, chi_from, chi_to, a_ref, omega_m, maps, 0, 1.f,
-                      as_stream(stream));
+  return step_call(rm, rays, grad_x, grad_y, nullptr, geom, chi_from, chi_to, a_ref, omega_m, maps, stream);
+}
+
+hrt_status hrt_raymesh_ray_step_tiled(hrt_raymesh* rm, const hrt_rays* rays, const float* grad_x, const float* grad_y,
+                                      const float* grad_z, const hrt_ray_geom* geom, double chi_from, double chi_to,
+                                      double a_ref, double omega_m, float* maps, void* stream) {
+  if (!grad_z) return fail(HRT_ERR_INVALID_ARG, "grad_z is NULL");
+  return step_call(rm, rays, grad_x, grad_y, grad_z, geom, chi_from, chi_to, a_ref, omega_m, maps, stream);
 }
 
 }  // extern "C"

@@ -89,6 +89,8 @@ _SIGS = {
     "hrt_raymesh_destroy": ([_P], C.c_int),
     "hrt_raymesh_kick": ([_P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
     "hrt_raymesh_ray_step": ([_P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
+    "hrt_raymesh_kick_tiled": ([_P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
+    "hrt_raymesh_ray_step_tiled": ([_P, _P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
     "hrt_set_ray_mesh": ([_P, _P], C.c_int),
     "hrt_ray_drift_free": ([_P, _D, _D, _P], C.c_int),
     "hrt_ray_readout": ([_P, _P, _P], C.c_int),
@@ -401,22 +403,35 @@ class RayMesh:
         _check(_lib.hrt_raymesh_create(C.byref(cfg), C.byref(self._h)), "hrt_raymesh_create")
 
     def hrt_raymesh_kick(self, grad_x, grad_y, geom: hrt_ray_geom, chi_a: float, chi_b: float, a_ref: float = 0.0,
-                         omega_m: float = 0.3, stream=None) -> torch.Tensor:
-        """The filtered ray mesh of one half shell as a (N, N, 2) float32 device tensor."""
+                         omega_m: float = 0.3, stream=None, grad_z=None) -> torch.Tensor:
+        """The filtered ray mesh of one half shell as a (N, N, 2) float32 device tensor (``grad_z`` and a geometry
+        with replicas: through the tiled light cone)."""
         _, _, n2d = hrt_raymesh_geometry(self.cfg, chi_a, chi_b, geom.box / geom.n)
         out = torch.empty(n2d, n2d, 2, dtype=torch.float32, device=grad_x.device)
-        _check(_lib.hrt_raymesh_kick(self._h, _ptr(grad_x, torch.float32, "grad_x"), _ptr(grad_y, torch.float32, "grad_y"),
-                                     C.byref(geom), chi_a, chi_b, a_ref, omega_m, _ptr(out, torch.float32, "mesh"),
-                                     _stream(stream)), "hrt_raymesh_kick")
+        gx, gy = _ptr(grad_x, torch.float32, "grad_x"), _ptr(grad_y, torch.float32, "grad_y")
+        if grad_z is None:
+            _check(_lib.hrt_raymesh_kick(self._h, gx, gy, C.byref(geom), chi_a, chi_b, a_ref, omega_m,
+                                         _ptr(out, torch.float32, "mesh"), _stream(stream)), "hrt_raymesh_kick")
+        else:
+            _check(_lib.hrt_raymesh_kick_tiled(self._h, gx, gy, _ptr(grad_z, torch.float32, "grad_z"), C.byref(geom),
+                                               chi_a, chi_b, a_ref, omega_m, _ptr(out, torch.float32, "mesh"),
+                                               _stream(stream)), "hrt_raymesh_kick_tiled")
         return out
 
     def hrt_raymesh_ray_step(self, rays: RayState, grad_x, grad_y, geom: hrt_ray_geom, chi_from: float, chi_to: float,
-                             a_ref: float = 0.0, omega_m: float = 0.3, maps: torch.Tensor | None = None, stream=None):
+                             a_ref: float = 0.0, omega_m: float = 0.3, maps: torch.Tensor | None = None, stream=None,
+                             grad_z=None):
         r = rays.c()
-        _check(_lib.hrt_raymesh_ray_step(self._h, C.byref(r), _ptr(grad_x, torch.float32, "grad_x"),
-                                         _ptr(grad_y, torch.float32, "grad_y"), C.byref(geom), chi_from, chi_to, a_ref,
-                                         omega_m, _ptr(maps, torch.float32, "maps"), _stream(stream)),
-               "hrt_raymesh_ray_step")
+        gx, gy = _ptr(grad_x, torch.float32, "grad_x"), _ptr(grad_y, torch.float32, "grad_y")
+        if grad_z is None:
+            _check(_lib.hrt_raymesh_ray_step(self._h, C.byref(r), gx, gy, C.byref(geom), chi_from, chi_to, a_ref,
+                                             omega_m, _ptr(maps, torch.float32, "maps"), _stream(stream)),
+                   "hrt_raymesh_ray_step")
+        else:
+            _check(_lib.hrt_raymesh_ray_step_tiled(self._h, C.byref(r), gx, gy, _ptr(grad_z, torch.float32, "grad_z"),
+                                                   C.byref(geom), chi_from, chi_to, a_ref, omega_m,
+                                                   _ptr(maps, torch.float32, "maps"), _stream(stream)),
+                   "hrt_raymesh_ray_step_tiled")
 
     def close(self):
         if self._h:

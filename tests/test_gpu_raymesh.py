@@ -116,6 +116,30 @@ def test_raymesh_ray_step_matches_oracle(hrt, case):
     assert float((maps[0].double().cpu() - k_o).abs().max()) <= 1e-6
 
 
+@pytest.mark.parametrize("seed", [1, 2])
+def test_tiled_raymesh_kick_matches_oracle(hrt, seed):
+    """The filtered mesh of half shells that cross replica boundaries of a tiled light cone."""
+    g = torch.Generator().manual_seed(60 + seed)
+    g3 = [torch.randn(N, N, N, generator=g, dtype=torch.float64).float() for _ in range(3)]
+    reps = synthetic.replica_transforms(seed, 12, N)
+    cfg = hrt.make_raymesh_config(0.5, 8, 0.004, 40)
+    rm = hrt.RayMesh(cfg)
+    geom = hrt.make_geom(N, BOX, OBS, replicas=reps)
+    for ca, cb in ((120.3, 141.0), (141.0, 120.3), (300.2, 400.9)):
+        K, _, _ = raymesh.mesh_kick(g3[0].double(), g3[1].double(), BOX, OBS, ca, cb, lambda chi: 1.0, 0.004, 40,
+                                    0.5, 8, gz=g3[2].double(), replicas=reps)
+        out = rm.hrt_raymesh_kick(g3[0].cuda().reshape(-1), g3[1].cuda().reshape(-1), geom, ca, cb,
+                                  grad_z=g3[2].cuda().reshape(-1))
+        torch.cuda.synchronize()
+        err = float((out.permute(2, 0, 1).double().cpu() - K).abs().max())
+        assert err <= 3e-5 * float(K.abs().max()), (ca, cb, err / float(K.abs().max()))
+    # a plane beyond the last replica is refused
+    with pytest.raises(hrt.HRTError):
+        rm.hrt_raymesh_kick(g3[0].cuda().reshape(-1), g3[1].cuda().reshape(-1), geom, 700.0, 800.0,
+                            grad_z=g3[2].cuda().reshape(-1))
+    rm.close()
+
+
 def test_raymesh_rejects_bad_configurations(hrt):
     from paper_2405_12913_gb300.hrt import HRTError
     with pytest.raises(HRTError):
@@ -134,17 +158,22 @@ def test_raymesh_rejects_bad_configurations(hrt):
     rm.close()
 
 
-def test_context_run_with_the_ray_mesh_matches_oracle(hrt):
+@pytest.mark.parametrize("tiled", [False, True])
+def test_context_run_with_the_ray_mesh_matches_oracle(hrt, tiled):
     """The small cosmological co-evolution with the context's kick operator switched to the ray mesh, against
-    the oracle's reverse run with the ray-mesh kick."""
+    the oracle's reverse run with the ray-mesh kick; also through a light cone tiled by 16 rotated, translated
+    replicas."""
     from paper_2405_12913_gb300.configs import COSMO_TINY as W
     rm_args = (W.dtheta, W.n_pix, 0.5, 8.0)
+    reps = synthetic.replica_transforms(31, 16, W.n_mesh) if tiled else None
     noise = synthetic.white_noise(W.seed, W.n_side)
     theta0 = synthetic.pixel_grid(W.n_pix, W.fov_deg * synthetic.DEGREE)
     cfg = hrt.make_config(W.n_mesh, W.box, W.n_side, W.omega_m, W.h, W.n_s, W.sigma8, W.deconv_p, W.smooth_cells,
                           W.samples_per_cell, W.observer, n_sources=len(W.source_steps))
     ctx = hrt.Context(cfg)
     ctx.hrt_set_ray_mesh(hrt.make_raymesh_config(rm_args[2], rm_args[3], rm_args[0], rm_args[1]))
+    if tiled:
+        ctx.hrt_set_replicas(reps)
     ctx.hrt_init_particles_zeldovich(torch.tensor(noise, dtype=torch.float32, device="cuda"), W.a_init)
     for a in W.forward_grid[1:]:
         ctx.hrt_step(a)
@@ -164,7 +193,7 @@ def test_context_run_with_the_ray_mesh_matches_oracle(hrt):
     part = sim.initial_particles(noise, W.box, c, W.a_init)
     part, grads = sim.run_forward(part, W.forward_grid, W.box, W.n_mesh, c, flt)
     res = sim.run_reverse(part, grads, W.reverse_grid, W.box, W.n_mesh, c, flt, torch.tensor(theta0), W.observer,
-                          set(W.source_steps), W.samples_per_cell, ray_mesh=rm_args)
+                          set(W.source_steps), W.samples_per_cell, replicas=reps, ray_mesh=rm_args)
     for s in W.source_steps:
         kap_o = res.maps[s][0].numpy()
         rms = kap_o.std()
