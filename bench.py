@@ -161,11 +161,12 @@ def recorded_traffic(kernel: str, workload: str):
 RAYMESH_IOTA, RAYMESH_P_MIN = 0.5, 256.0
 
 
-def raymesh_config(hrt, W):
-    return hrt.make_raymesh_config(RAYMESH_IOTA, RAYMESH_P_MIN, W.dtheta, W.n_pix)
+def raymesh_config(hrt, W, iota=None, p_min=None):
+    return hrt.make_raymesh_config(RAYMESH_IOTA if iota is None else iota, RAYMESH_P_MIN if p_min is None else p_min,
+                                   W.dtheta, W.n_pix)
 
 
-def raymesh_sides(hrt, W):
+def raymesh_sides(hrt, W, iota=None, p_min=None):
     """Smallest and largest ray-mesh side over the half shells of the reverse grid."""
     from paper_2405_12913_gb300.hrt import hrt_cosmo_eval
     chis = [hrt_cosmo_eval(W.omega_m, a)[1] for a in W.reverse_grid]
@@ -173,7 +174,7 @@ def raymesh_sides(hrt, W):
     for a, b in zip(chis[:-1], chis[1:]):
         m = 0.5 * (a + b)
         for lo, hi in ((a, m), (m, b)):
-            sides.append(hrt.hrt_raymesh_geometry(raymesh_config(hrt, W), lo, hi, W.box / W.n_mesh)[2])
+            sides.append(hrt.hrt_raymesh_geometry(raymesh_config(hrt, W, iota, p_min), lo, hi, W.box / W.n_mesh)[2])
     return min(sides), max(sides)
 
 
@@ -426,27 +427,36 @@ def next_rows(args, W, ctx, reset, grid, slots, run_steps, stream, seed):
                            W.samples_per_cell, W.observer, n_sources=len(W.source_steps), ray_fields=2,
                            ray_deconv_p=W.deconv_p, ray_smooth_cells=0.0)
     ctx2 = hrt.Context(cfg2)
-    ctx2.hrt_set_ray_mesh(raymesh_config(hrt, W))
-    ctx2.hrt_init_particles(*reset.state[:2], 1.0)
-    ctx2.hrt_init_rays(reset.state[2])
-    ctx2.hrt_ctx_set_profiling(True)
-    for n in range(1, len(grid)):
-        ctx2.hrt_step(grid[n], slots.get(n, -1))
-    ph = ctx2.hrt_ctx_phase_times()
-    pk = {s: ctx2.hrt_ctx_kappa_power(i, W.n_pix, W.dtheta, W.nbins, lmin, lmax) for s, i in slots.items()}
-    runs["mesh_unsmoothed_3d"] = (ph["ray_step"][0] / max(ph["ray_step"][1], 1), pk)
+    # the hyper-parameters of the paper's ray-mesh tests (App. C): (iota, p_min) = (1, 4), (1, 256), (0.5, 256),
+    # and a finer (0.25, 256)
+    sweep = ((RAYMESH_IOTA, RAYMESH_P_MIN), (1.0, 4.0), (1.0, 256.0), (0.25, 256.0))
+    sides = {"mesh": list(raymesh_sides(hrt, W))}
+    for iota, p_min in sweep:
+        ctx2.hrt_set_ray_mesh(raymesh_config(hrt, W, iota, p_min))
+        ctx2.hrt_init_particles(*reset.state[:2], 1.0)
+        ctx2.hrt_init_rays(reset.state[2])
+        ctx2.hrt_ctx_set_profiling(True)
+        for n in range(1, len(grid)):
+            ctx2.hrt_step(grid[n], slots.get(n, -1))
+        ph = ctx2.hrt_ctx_phase_times()
+        ctx2.hrt_ctx_set_profiling(False)
+        pk = {s: ctx2.hrt_ctx_kappa_power(i, W.n_pix, W.dtheta, W.nbins, lmin, lmax) for s, i in slots.items()}
+        name = "mesh_unsmoothed_3d" if (iota, p_min) == sweep[0] else f"mesh_unsmoothed_3d_iota{iota:g}_p{p_min:g}"
+        runs[name] = (ph["ray_step"][0] / max(ph["ray_step"][1], 1), pk)
+        sides[name] = list(raymesh_sides(hrt, W, iota, p_min))
     ctx2.close()
-    cmp = {"iota": RAYMESH_IOTA, "p_min": RAYMESH_P_MIN, "ray_mesh_sides": list(raymesh_sides(hrt, W)),
+    cmp = {"iota": RAYMESH_IOTA, "p_min": RAYMESH_P_MIN, "ray_mesh_sides": sides,
            "forms": {"direct": "direct gather of the 3D fields (Gaussian of 1 cell)",
                      "mesh": "ray mesh over the same fields (3D Gaussian and 2D Gaussian at lambda_lim)",
-                     "mesh_unsmoothed_3d": "ray mesh over 3D fields without the Gaussian (the paper's arrangement)"},
+                     "mesh_unsmoothed_3d": "ray mesh over 3D fields without the Gaussian (the paper's arrangement)",
+                     "mesh_unsmoothed_3d_iota*_p*": "the same with other (iota, p_min)"},
            "ray_step_ms": {k: v[0] for k, v in runs.items()}, "sources": {}}
     for s in W.source_steps:
         ell, p_d, cnt = runs["direct"][1][s]
         ok = cnt > 0
         e = ell[ok]
         row = {"ell": [round(float(x), 1) for x in e]}
-        for name in ("mesh", "mesh_unsmoothed_3d"):
+        for name in [k for k in runs if k != "direct"]:
             ratio = runs[name][1][s][1][ok] / p_d[ok]
             row[f"power_ratio_{name}_over_direct"] = [round(float(x), 4) for x in ratio]
             for cut in (1200, 3000):
