@@ -407,6 +407,18 @@ def next_rows(args, W, ctx, reset, grid, slots, run_steps, stream, seed):
     e1.record(stream)
     torch.cuda.synchronize()
     out["accumulate_step_ms"] = e0.elapsed_time(e1) / steps
+    # kappa power spectrum of one source map: a synchronous call (2D R2C plan, transform, binning, bins to the
+    # host), timed on the host clock
+    import time
+    lmin, lmax = W.ell_range
+    kmap = ctx.hrt_read_maps(0)[0].contiguous()
+    hrt.hrt_kappa_power(kmap, W.n_pix, W.dtheta, W.nbins, lmin, lmax)
+    torch.cuda.synchronize()
+    reps_p = 10
+    t_p = time.perf_counter()
+    for _ in range(reps_p):
+        hrt.hrt_kappa_power(kmap, W.n_pix, W.dtheta, W.nbins, lmin, lmax)
+    out["kappa_power_call_ms"] = (time.perf_counter() - t_p) * 1e3 / reps_p
     # the paper's ray-mesh kick operator against the direct gather: full reverse runs from a = 1 on the same
     # particles, ray-step phase time and the kappa power spectra of every source plane
     lmin, lmax = W.ell_range
