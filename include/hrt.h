@@ -490,6 +490,35 @@ hrt_status hrt_set_ray_correction(hrt_ctx* ctx, const float* params);
  * shift tables (host, copied); n = 0 removes it.  Needs ray_fields == 0 (HRT_ERR_STATE otherwise). */
 hrt_status hrt_set_replicas(hrt_ctx* ctx, int32_t n, const int32_t* perm, const int32_t* sign, const int32_t* shift);
 
+/* Adjoints of the ray-mesh kick (untiled geometries).  The mesh geometry (lambda_lim, x2d, N, the plane set) is
+ * held fixed: derivatives are taken with respect to the fields, the ray state and the plane weights
+ * w_p = -(2/c) chi_p g(chi_p) (+-cell) cell^2 / (chi_p^2 x2d^2), not with respect to the discretisation.
+ *
+ * hrt_raymesh_kick_adjoint: transpose of hrt_raymesh_kick.  mesh_bar (device, N x N x 2 float32, layout of
+ * hrt_raymesh_kick's output) is dL/dK of the filtered mesh; gx_bar, gy_bar (device [n^3] float32) accumulate
+ * dL/d(grad_x), dL/d(grad_y); plane_bar_host (host, >= 512 doubles, or NULL) accumulates dL/dw_p for the
+ * shell's planes in the order of hrt_raymesh_step_planes.  grad_x, grad_y are the forward's fields (for dL/dw_p).
+ * Synchronises the stream. */
+hrt_status hrt_raymesh_kick_adjoint(hrt_raymesh* rm, const float* grad_x, const float* grad_y, const float* mesh_bar,
+                                    const hrt_ray_geom* geom, double chi_a, double chi_b, double a_ref, double omega_m,
+                                    float* gx_bar, float* gy_bar, double* plane_bar_host, void* stream);
+
+/* hrt_raymesh_ray_step_adjoint: transpose of hrt_raymesh_ray_step (without the readout).  rays hold the state
+ * before the step (unchanged); bar holds on entry the cotangents of the state after it and on return those of
+ * the state before it; gx_bar, gy_bar accumulate the field cotangents; plane_bar_host ([2][512] doubles, or NULL)
+ * accumulates dL/dw_p of the two half shells' planes; drift_bar_host[0] (or NULL) accumulates dL/dd for the drift
+ * coefficient d = (chi_to - chi_from) / (c chi_mid^2).  Synchronises the stream. */
+hrt_status hrt_raymesh_ray_step_adjoint(hrt_raymesh* rm, const hrt_rays* rays, const float* grad_x, const float* grad_y,
+                                        const hrt_ray_geom* geom, double chi_from, double chi_to, double a_ref,
+                                        double omega_m, const hrt_rays* bar, float* gx_bar, float* gy_bar,
+                                        double* plane_bar_host, double* drift_bar_host, void* stream);
+
+/* Host: the planes of a ray-mesh step, per half shell h the count n_h, chi_host[h * 512 + q] and the FP64
+ * weight w_host[h * 512 + q], and the drift coefficient. */
+hrt_status hrt_raymesh_step_planes(const hrt_raymesh_config* cfg, const hrt_ray_geom* geom, double chi_from,
+                                   double chi_to, double a_ref, double omega_m, int32_t* n1_host, int32_t* n2_host,
+                                   double* chi_host, double* w_host, double* drift_host);
+
 /* Kick operator of the context's rays: cfg != NULL switches to the ray-mesh kick of hrt_raymesh_ray_step
  * (configuration copied; the context owns its workspace), cfg == NULL back to the direct line-of-sight
  * gather.  The ray mesh reads the same 3D fields as the direct gather (the ray fields when ray_fields == 2; all

@@ -33,6 +33,9 @@ struct hrt_raymesh {
   std::map<int64_t, cufftHandle> plans;  // C2C n2d x n2d plans by side
   float2* mesh[2] = {nullptr, nullptr};  // one mesh per half shell
   int64_t cap[2] = {0, 0};               // elements allocated
+  float2* mesh_bar[2] = {nullptr, nullptr};  // adjoint: cotangents of the meshes
+  int64_t cap_bar[2] = {0, 0};
+  double* acc = nullptr;                 // adjoint: drift and plane-weight cotangents (1 + 2 * 512 doubles)
 };
 
 namespace hrt {
@@ -267,6 +270,196 @@ __global__ void __launch_bounds__(256) raymesh_ray_kernel(double2* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------------------------------------
+// Adjoint (reverse mode).  The filter is a real, even multiplier in Fourier space, so the filtered mesh is a
+// self-adjoint linear map of the deposit and its transpose is the same filter.  The transpose of the projection
+// is a gather per 3D node: the bilinear interpolation of the mesh cotangent at the node's projected angle,
+// summed over its periodic images and times the plane weight.  The mesh geometry (lambda_lim, x2d, N) is held
+// fixed: it is a discretisation choice, not a function of the fields.
+// ---------------------------------------------------------------------------------------------------------
+
+// Position of an angle on a mesh with its corner values (the forward's arithmetic).
+struct MeshPos {
+  bool inside;
+  int ix, iy;
+  float fx, fy;
+  float2 v00, v01, v10, v11;
+};
+
+__device__ __forceinline__ MeshPos mesh_locate(const MeshView& m, double thx, double thy) {
+  MeshPos c{};
+  c.inside = false;
+  if (m.k == nullptr) return c;
+  const double half = 0.5 * m.n2d;
+  const double ux = thx * m.inv_x2d + half, uy = thy * m.inv_x2d + half;
+  if (!(ux > -1.0 && ux < m.n2d && uy > -1.0 && uy < m.n2d)) return c;
+  const double flx = floor(ux), fly = floor(uy);
+  c.inside = true;
+  c.ix = static_cast<int>(flx);
+  c.iy = static_cast<int>(fly);
+  c.fx = static_cast<float>(ux - flx);
+  c.fy = static_cast<float>(uy - fly);
+  c.v00 = corner(m, c.ix, c.iy);
+  c.v01 = corner(m, c.ix, c.iy + 1);
+  c.v10 = corner(m, c.ix + 1, c.iy);
+  c.v11 = corner(m, c.ix + 1, c.iy + 1);
+  return c;
+}
+
+__device__ __forceinline__ void corner_add(float2* __restrict__ mbar, int n2d, int i, int j, float a, float b) {
+  if (i < 0 || i >= n2d || j < 0 || j >= n2d) return;
+  atomicAdd(mbar + static_cast<int64_t>(i) * n2d + j, make_float2(a, b));
+}
+
+// Transpose of one half kick at c: the kick's cotangent Kb and the cotangent Jb of dK/dtheta (J as in MeshKick,
+// J[c][b] = dK_c / dtheta_b) go to the mesh cotangent through the bilinear and derivative weights, and to the
+// angle cotangent thb through J^T Kb and the cross derivative d^2 K / dtheta_x dtheta_y.
+__device__ __forceinline__ void mesh_kick_backward(const MeshView& m, float2* __restrict__ mbar, const MeshPos& c,
+                                                   const float Kb[2], const float Jb[2][2], float thb[2]) {
+  if (!c.inside) return;
+  const float s = static_cast<float>(m.inv_x2d);
+  const float gx = 1.f - c.fx, gy = 1.f - c.fy, fx = c.fx, fy = c.fy;
+  const float j00 = s * (gy * (c.v10.x - c.v00.x) + fy * (c.v11.x - c.v01.x));
+  const float j01 = s * (gx * (c.v01.x - c.v00.x) + fx * (c.v11.x - c.v10.x));
+  const float j10 = s * (gy * (c.v10.y - c.v00.y) + fy * (c.v11.y - c.v01.y));
+  const float j11 = s * (gx * (c.v01.y - c.v00.y) + fx * (c.v11.y - c.v10.y));
+  const float hx = s * s * (c.v11.x - c.v10.x - c.v01.x + c.v00.x);
+  const float hy = s * s * (c.v11.y - c.v10.y - c.v01.y + c.v00.y);
+  thb[0] += j00 * Kb[0] + j10 * Kb[1] + Jb[0][1] * hx + Jb[1][1] * hy;
+  thb[1] += j01 * Kb[0] + j11 * Kb[1] + Jb[0][0] * hx + Jb[1][0] * hy;
+  // corner (di, dj): value weight w, weights dJx, dJy of J[.][0] and J[.][1]
+  const float w[4] = {gx * gy, gx * fy, fx * gy, fx * fy};
+  const float dx[4] = {-s * gy, -s * fy, s * gy, s * fy};
+  const float dy[4] = {-s * gx, s * gx, -s * fx, s * fx};
+  for (int k = 0; k < 4; ++k) {
+    const float a = Kb[0] * w[k] + Jb[0][0] * dx[k] + Jb[0][1] * dy[k];
+    const float b = Kb[1] * w[k] + Jb[1][0] * dx[k] + Jb[1][1] * dy[k];
+    corner_add(mbar, m.n2d, c.ix + (k >> 1), c.iy + (k & 1), a, b);
+  }
+}
+
+__device__ __forceinline__ void block_sum_add(double v, double* __restrict__ out) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(out, v);
+}
+
+__global__ void __launch_bounds__(256) raymesh_ray_adjoint_kernel(
+    const double2* __restrict__ theta, const float2* __restrict__ eta, const float4* __restrict__ Amat,
+    const float4* __restrict__ Bmat, int64_t nr, const __grid_constant__ RayMeshParams p,
+    double2* __restrict__ theta_bar, float2* __restrict__ eta_bar, float4* __restrict__ A_bar,
+    float4* __restrict__ B_bar, float2* __restrict__ mbar0, float2* __restrict__ mbar1, double* __restrict__ drift_bar) {
+  const int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const bool active = r < nr;
+  double db = 0.0;
+  if (active) {
+    const double2 th0 = theta[r];
+    const float2 et0 = eta[r];
+    const float4 A0v = Amat[r], B0v = Bmat[r];
+    const float A0[2][2] = {{A0v.x, A0v.y}, {A0v.z, A0v.w}};
+    const float B0[2][2] = {{B0v.x, B0v.y}, {B0v.z, B0v.w}};
+    // forward recompute (the arithmetic of raymesh_ray_kernel)
+    const MeshKick h1 = mesh_kick(p.m[0], th0.x, th0.y);
+    const float J1[2][2] = {{h1.j00, h1.j01}, {h1.j10, h1.j11}};
+    const float eta1[2] = {et0.x + h1.kx, et0.y + h1.ky};
+    float B1[2][2], A1[2][2];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) B1[a][b] = B0[a][b] + (J1[a][0] * A0[0][b] + J1[a][1] * A0[1][b]);
+    const double th1x = th0.x + p.drift_d * static_cast<double>(eta1[0]);
+    const double th1y = th0.y + p.drift_d * static_cast<double>(eta1[1]);
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) A1[a][b] = A0[a][b] + p.drift * B1[a][b];
+    const MeshKick h2 = mesh_kick(p.m[1], th1x, th1y);
+    const float J2[2][2] = {{h2.j00, h2.j01}, {h2.j10, h2.j11}};
+    // backward
+    const double2 thbv = theta_bar[r];
+    const float2 etbv = eta_bar[r];
+    const float4 Abv = A_bar[r], Bbv = B_bar[r];
+    float Ab[2][2] = {{Abv.x, Abv.y}, {Abv.z, Abv.w}};
+    float Bb[2][2] = {{Bbv.x, Bbv.y}, {Bbv.z, Bbv.w}};
+    float etb[2] = {etbv.x, etbv.y};
+    float thb[2] = {static_cast<float>(thbv.x), static_cast<float>(thbv.y)};
+    float Jb[2][2];
+    // B2 = B1 + J2 A1 and eta2 = eta1 + K2(theta1)
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) Jb[a][b] = Bb[a][0] * A1[b][0] + Bb[a][1] * A1[b][1];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) Ab[a][b] += J2[0][a] * Bb[0][b] + J2[1][a] * Bb[1][b];
+    mesh_kick_backward(p.m[1], mbar1, mesh_locate(p.m[1], th1x, th1y), etb, Jb, thb);
+    // A1 = A0 + d B1, theta1 = theta0 + d eta1
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) {
+        Bb[a][b] += p.drift * Ab[a][b];
+        db += static_cast<double>(Ab[a][b]) * B1[a][b];
+      }
+    etb[0] += static_cast<float>(p.drift_d) * thb[0];
+    etb[1] += static_cast<float>(p.drift_d) * thb[1];
+    db += static_cast<double>(thb[0]) * eta1[0] + static_cast<double>(thb[1]) * eta1[1];
+    // B1 = B0 + J1 A0 and eta1 = eta0 + K1(theta0)
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) Jb[a][b] = Bb[a][0] * A0[b][0] + Bb[a][1] * A0[b][1];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) Ab[a][b] += J1[0][a] * Bb[0][b] + J1[1][a] * Bb[1][b];
+    mesh_kick_backward(p.m[0], mbar0, mesh_locate(p.m[0], th0.x, th0.y), etb, Jb, thb);
+    theta_bar[r] = make_double2(thb[0], thb[1]);
+    eta_bar[r] = make_float2(etb[0], etb[1]);
+    A_bar[r] = make_float4(Ab[0][0], Ab[0][1], Ab[1][0], Ab[1][1]);
+    B_bar[r] = make_float4(Bb[0][0], Bb[0][1], Bb[1][0], Bb[1][1]);
+  }
+  block_sum_add(db, drift_bar);
+}
+
+// Transpose of the projection (untiled): one thread per 3D node (i, j) of plane blockIdx.z.  It adds
+// w_p * S to the field cotangents, where S is the bilinear interpolation of the (filtered) mesh cotangent at the
+// node's projected angle, summed over the node's periodic images, and adds g . S to dL/dw_p.
+__global__ void __launch_bounds__(256) raymesh_project_adjoint_kernel(const float* __restrict__ gx,
+                                                                     const float* __restrict__ gy,
+                                                                     const __grid_constant__ ProjectParams p,
+                                                                     const float2* __restrict__ mbar,
+                                                                     float* __restrict__ gxb, float* __restrict__ gyb,
+                                                                     double* __restrict__ plane_bar) {
+  const int q = blockIdx.z;
+  const int i = blockIdx.y * kTileX + threadIdx.x / kTileY, j = blockIdx.x * kTileY + threadIdx.x % kTileY;
+  const int n = p.n, n2d = p.n2d;
+  double part = 0.0;
+  if (i < n && j < n) {
+    const double P = p.p[q], inv = 1.0 / P;
+    // u = (node + image n - Q) / P on each axis; the images whose u reaches (-1, n2d)
+    const double ux0 = (i - p.qx[q]) * inv, uy0 = (j - p.qy[q]) * inv, step = n * inv;
+    const int ia0 = static_cast<int>(ceil((-1.0 - ux0) / step)), ia1 = static_cast<int>(floor((n2d - ux0) / step));
+    const int ib0 = static_cast<int>(ceil((-1.0 - uy0) / step)), ib1 = static_cast<int>(floor((n2d - uy0) / step));
+    float sx = 0.f, sy = 0.f;
+    for (int ia = ia0; ia <= ia1; ++ia) {
+      const double ux = ux0 + ia * step;
+      if (!(ux > -1.0 && ux < n2d)) continue;
+      const double flx = floor(ux);
+      const int mx = static_cast<int>(flx);
+      const float fx = static_cast<float>(ux - flx);
+      for (int ib = ib0; ib <= ib1; ++ib) {
+        const double uy = uy0 + ib * step;
+        if (!(uy > -1.0 && uy < n2d)) continue;
+        const double fly = floor(uy);
+        const int my = static_cast<int>(fly);
+        const float fy = static_cast<float>(uy - fly);
+        const float w[4] = {(1.f - fx) * (1.f - fy), (1.f - fx) * fy, fx * (1.f - fy), fx * fy};
+        for (int k = 0; k < 4; ++k) {
+          const int a = mx + (k >> 1), b = my + (k & 1);
+          if (a < 0 || a >= n2d || b < 0 || b >= n2d) continue;
+          const float2 v = __ldg(mbar + static_cast<int64_t>(a) * n2d + b);
+          sx += w[k] * v.x;
+          sy += w[k] * v.y;
+        }
+      }
+    }
+    if (sx != 0.f || sy != 0.f) {
+      const int64_t idx = (static_cast<int64_t>(i) * n + j) * n + p.kz[q];
+      atomicAdd(gxb + idx, p.w[q] * sx);
+      atomicAdd(gyb + idx, p.w[q] * sy);
+      part = static_cast<double>(__ldg(gx + idx)) * sx + static_cast<double>(__ldg(gy + idx)) * sy;
+    }
+  }
+  block_sum_add(part, plane_bar + q);
+}
+
+// ---------------------------------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------------------------------
 
@@ -306,7 +499,8 @@ static hrt_status geometry(const hrt_raymesh_config& c, double chi_a, double chi
 // Plane table of the half shell (FP64 on the host): the node planes z = kz cell with
 // min(chi_a, chi_b) <= chi = z - O_z < max(chi_a, chi_b), chi > 0, inside the geometry's window.
 static hrt_status plane_table(const hrt_ray_geom& g, double chi_a, double chi_b, double a_ref, double omega_m,
-                              double x2d, int64_t n2d, ProjectParams& p) {
+                              double x2d, int64_t n2d, ProjectParams& p, double* w64 = nullptr,
+                              double* chi64 = nullptr) {
   const double cell = g.box / g.n;
   const double lo = std::min(chi_a, chi_b), hi = std::max(chi_a, chi_b);
   const double sgn = chi_b >= chi_a ? 1.0 : -1.0;
@@ -378,7 +572,10 @@ static hrt_status plane_table(const hrt_ray_geom& g, double chi_a, double chi_b,
     int64_t kzw = kz % g.n;
     if (kzw < 0) kzw += g.n;
     p.kz[q] = static_cast<int>(kzw);
-    p.w[q] = static_cast<float>(-(2.0 / kCLight) * r * gw * sgn * cell * cell * cell / (r * r * x2d * x2d));
+    const double wq = -(2.0 / kCLight) * r * gw * sgn * cell * cell * cell / (r * r * x2d * x2d);
+    p.w[q] = static_cast<float>(wq);
+    if (w64) w64[q] = wq;
+    if (chi64) chi64[q] = chi;
     p.pf[q] = static_cast<float>(P);
     p.inv_p[q] = static_cast<float>(1.0 / P);
     p.p[q] = P;
@@ -419,6 +616,24 @@ static hrt_status plan_for(hrt_raymesh* rm, int64_t n2d, cudaStream_t s, cufftHa
   return cufft_check(cufftSetStream(plan, s), "set stream");
 }
 
+// In place: C2C forward, the deconvolution and smoothing (with the 1 / N^2 of the inverse), C2C inverse.  The
+// same operation is its own transpose (real, even multiplier).
+static hrt_status filter_mesh(hrt_raymesh* rm, float2* mesh, int64_t n2d, cudaStream_t s) {
+  cufftHandle plan;
+  HRT_TRY(plan_for(rm, n2d, s, plan));
+  auto* c = reinterpret_cast<cufftComplex*>(mesh);
+  HRT_TRY(cufft_check(cufftExecC2C(plan, c, c, CUFFT_FORWARD), "forward"));
+  const int64_t total = n2d * n2d;
+  const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((total + 255) / 256, 152 * 16));
+  int lg = 0;
+  while ((int64_t{1} << lg) < n2d) ++lg;
+  raymesh_filter_kernel<<<blocks, 256, 0, s>>>(mesh, lg,
+                                               static_cast<float>(1.0 / (rm->cfg.iota * rm->cfg.iota)),
+                                               static_cast<float>(1.0 / static_cast<double>(total)));
+  HRT_LAUNCHED("raymesh_filter_kernel");
+  return cufft_check(cufftExecC2C(plan, c, c, CUFFT_INVERSE), "inverse");
+}
+
 // Builds the filtered ray mesh of the half shell [chi_a, chi_b) in rm->mesh[h]; view.k == nullptr when the
 // shell holds no plane.
 static hrt_status build_mesh(hrt_raymesh* rm, int h, const float* gx, const float* gy, const float* gz,
@@ -443,19 +658,7 @@ static hrt_status build_mesh(hrt_raymesh* rm, int h, const float* gx, const floa
     raymesh_project_kernel<false><<<grid, kTileX * kTileY, 0, s>>>(gx, gy, gz, p, mesh);
   }
   HRT_LAUNCHED("raymesh_project_kernel");
-  cufftHandle plan;
-  HRT_TRY(plan_for(rm, n2d, s, plan));
-  auto* c = reinterpret_cast<cufftComplex*>(mesh);
-  HRT_TRY(cufft_check(cufftExecC2C(plan, c, c, CUFFT_FORWARD), "forward"));
-  const int64_t total = n2d * n2d;
-  const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((total + 255) / 256, 152 * 16));
-  int lg = 0;
-  while ((int64_t{1} << lg) < n2d) ++lg;
-  raymesh_filter_kernel<<<blocks, 256, 0, s>>>(mesh, lg,
-                                               static_cast<float>(1.0 / (rm->cfg.iota * rm->cfg.iota)),
-                                               static_cast<float>(1.0 / static_cast<double>(total)));
-  HRT_LAUNCHED("raymesh_filter_kernel");
-  HRT_TRY(cufft_check(cufftExecC2C(plan, c, c, CUFFT_INVERSE), "inverse"));
+  HRT_TRY(filter_mesh(rm, mesh, n2d, s));
   view.k = mesh;
   return HRT_OK;
 }
@@ -477,6 +680,115 @@ hrt_status raymesh_step(hrt_raymesh* rm, const hrt_rays& rays, const float* gx, 
       reinterpret_cast<double2*>(rays.theta), reinterpret_cast<float2*>(rays.eta), reinterpret_cast<float4*>(rays.A),
       reinterpret_cast<float4*>(rays.B), rays.n_rays, p, maps);
   HRT_LAUNCHED("raymesh_ray_kernel");
+  return HRT_OK;
+}
+
+static hrt_status ensure_bar(hrt_raymesh* rm, int h, int64_t elems, cudaStream_t s) {
+  if (!rm->acc) HRT_TRY(device_alloc(reinterpret_cast<void**>(&rm->acc), (1 + 2 * kMaxMeshPlanes) * sizeof(double), s, "adjoint sums"));
+  if (rm->cap_bar[h] >= elems) return HRT_OK;
+  if (rm->mesh_bar[h]) {
+    cudaFreeAsync(rm->mesh_bar[h], s);
+    rm->mesh_bar[h] = nullptr;
+    rm->cap_bar[h] = 0;
+  }
+  HRT_TRY(device_alloc(reinterpret_cast<void**>(&rm->mesh_bar[h]), static_cast<size_t>(elems) * sizeof(float2), s, "ray-mesh cotangent"));
+  rm->cap_bar[h] = elems;
+  return HRT_OK;
+}
+
+// Transpose of filter + projection for one half shell: mbar (filtered-mesh cotangent, overwritten) to the field
+// cotangents and dL/dw_p (device, per plane).
+static hrt_status shell_adjoint(hrt_raymesh* rm, const float* gx, const float* gy, const ProjectParams& p,
+                                float2* mbar, float* gxb, float* gyb, double* plane_bar, cudaStream_t s) {
+  if (p.n_planes == 0) return HRT_OK;
+  HRT_TRY(filter_mesh(rm, mbar, p.n2d, s));
+  const dim3 grid(static_cast<unsigned>((p.n + kTileY - 1) / kTileY), static_cast<unsigned>((p.n + kTileX - 1) / kTileX),
+                  static_cast<unsigned>(p.n_planes));
+  raymesh_project_adjoint_kernel<<<grid, kTileX * kTileY, 0, s>>>(gx, gy, p, mbar, gxb, gyb, plane_bar);
+  HRT_LAUNCHED("raymesh_project_adjoint_kernel");
+  return HRT_OK;
+}
+
+static hrt_status read_sums(hrt_raymesh* rm, double* host, size_t count, cudaStream_t s) {
+  HRT_TRY(cuda_status(cudaMemcpyAsync(host, rm->acc, count * sizeof(double), cudaMemcpyDeviceToHost, s), "adjoint sums"));
+  return cuda_status(cudaStreamSynchronize(s), "adjoint sync");
+}
+
+static hrt_status kick_adjoint_call(hrt_raymesh* rm, const float* gx, const float* gy, const float* mesh_bar,
+                                    const hrt_ray_geom* geom, double chi_a, double chi_b, double a_ref,
+                                    double omega_m, float* gxb, float* gyb, double* plane_bar_host, void* stream) {
+  if (!rm || !gx || !gy || !mesh_bar || !gxb || !gyb) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  HRT_TRY(check_geom(geom, false));
+  if (!(omega_m > 0.0 && omega_m <= 1.0)) return fail(HRT_ERR_INVALID_ARG, "omega_m must be in (0, 1]");
+  cudaStream_t s = as_stream(stream);
+  static thread_local ProjectParams p;
+  double lam, x2d;
+  int64_t n2d;
+  HRT_TRY(geometry(rm->cfg, chi_a, chi_b, geom->box / geom->n, lam, x2d, n2d));
+  HRT_TRY(plane_table(*geom, chi_a, chi_b, a_ref, omega_m, x2d, n2d, p));
+  HRT_TRY(ensure_bar(rm, 0, n2d * n2d, s));
+  HRT_TRY(cuda_status(cudaMemsetAsync(rm->acc, 0, (1 + 2 * kMaxMeshPlanes) * sizeof(double), s), "clear sums"));
+  HRT_TRY(cuda_status(cudaMemcpyAsync(rm->mesh_bar[0], mesh_bar, static_cast<size_t>(n2d) * n2d * sizeof(float2),
+                                      cudaMemcpyDeviceToDevice, s), "copy mesh cotangent"));
+  HRT_TRY(shell_adjoint(rm, gx, gy, p, rm->mesh_bar[0], gxb, gyb, rm->acc + 1, s));
+  std::vector<double> h(1 + kMaxMeshPlanes);
+  HRT_TRY(read_sums(rm, h.data(), h.size(), s));
+  if (plane_bar_host)
+    for (int q = 0; q < p.n_planes; ++q) plane_bar_host[q] += h[1 + q];
+  return HRT_OK;
+}
+
+static hrt_status step_adjoint_call(hrt_raymesh* rm, const hrt_rays* rays, const float* gx, const float* gy,
+                                    const hrt_ray_geom* geom, double chi_from, double chi_to, double a_ref,
+                                    double omega_m, const hrt_rays* bar, float* gxb, float* gyb,
+                                    double* plane_bar_host, double* drift_bar_host, void* stream) {
+  if (!rm || !gx || !gy || !gxb || !gyb || !rays || !bar) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  if (rays->n_rays < 0 || bar->n_rays != rays->n_rays ||
+      (rays->n_rays > 0 && (!rays->theta || !rays->eta || !rays->A || !rays->B || !bar->theta || !bar->eta ||
+                            !bar->A || !bar->B)))
+    return fail(HRT_ERR_INVALID_ARG, "bad ray state or cotangent");
+  HRT_TRY(check_geom(geom, false));
+  if (!(omega_m > 0.0 && omega_m <= 1.0)) return fail(HRT_ERR_INVALID_ARG, "omega_m must be in (0, 1]");
+  const double chi_mid = 0.5 * (chi_from + chi_to);
+  if (!(chi_mid > 0.0)) return fail(HRT_ERR_INVALID_ARG, "shell midpoint must be at chi > 0");
+  cudaStream_t s = as_stream(stream);
+  RayMeshParams rp{};
+  HRT_TRY(build_mesh(rm, 0, gx, gy, nullptr, *geom, chi_from, chi_mid, a_ref, omega_m, s, rp.m[0]));
+  HRT_TRY(build_mesh(rm, 1, gx, gy, nullptr, *geom, chi_mid, chi_to, a_ref, omega_m, s, rp.m[1]));
+  rp.drift_d = (chi_to - chi_from) / (kCLight * chi_mid * chi_mid);
+  rp.drift = static_cast<float>(rp.drift_d);
+  for (int h = 0; h < 2; ++h) {
+    const int64_t e = static_cast<int64_t>(rp.m[h].n2d) * rp.m[h].n2d;
+    HRT_TRY(ensure_bar(rm, h, e, s));
+    HRT_TRY(cuda_status(cudaMemsetAsync(rm->mesh_bar[h], 0, static_cast<size_t>(e) * sizeof(float2), s), "clear cotangent"));
+  }
+  HRT_TRY(cuda_status(cudaMemsetAsync(rm->acc, 0, (1 + 2 * kMaxMeshPlanes) * sizeof(double), s), "clear sums"));
+  if (rays->n_rays > 0) {
+    raymesh_ray_adjoint_kernel<<<blocks_for(rays->n_rays, 256), 256, 0, s>>>(
+        reinterpret_cast<const double2*>(rays->theta), reinterpret_cast<const float2*>(rays->eta),
+        reinterpret_cast<const float4*>(rays->A), reinterpret_cast<const float4*>(rays->B), rays->n_rays, rp,
+        reinterpret_cast<double2*>(bar->theta), reinterpret_cast<float2*>(bar->eta), reinterpret_cast<float4*>(bar->A),
+        reinterpret_cast<float4*>(bar->B), rm->mesh_bar[0], rm->mesh_bar[1], rm->acc);
+    HRT_LAUNCHED("raymesh_ray_adjoint_kernel");
+  }
+  static thread_local ProjectParams p;
+  const double lo[2] = {chi_from, chi_mid}, hi[2] = {chi_mid, chi_to};
+  int counts[2] = {0, 0};
+  for (int h = 0; h < 2; ++h) {
+    if (rp.m[h].k == nullptr) continue;
+    double lam, x2d;
+    int64_t n2d;
+    HRT_TRY(geometry(rm->cfg, lo[h], hi[h], geom->box / geom->n, lam, x2d, n2d));
+    HRT_TRY(plane_table(*geom, lo[h], hi[h], a_ref, omega_m, x2d, n2d, p));
+    counts[h] = p.n_planes;
+    HRT_TRY(shell_adjoint(rm, gx, gy, p, rm->mesh_bar[h], gxb, gyb, rm->acc + 1 + h * kMaxMeshPlanes, s));
+  }
+  std::vector<double> sums(1 + 2 * kMaxMeshPlanes);
+  HRT_TRY(read_sums(rm, sums.data(), sums.size(), s));
+  if (drift_bar_host) drift_bar_host[0] += sums[0];
+  if (plane_bar_host)
+    for (int h = 0; h < 2; ++h)
+      for (int q = 0; q < counts[h]; ++q) plane_bar_host[h * kMaxMeshPlanes + q] += sums[1 + h * kMaxMeshPlanes + q];
   return HRT_OK;
 }
 
@@ -564,6 +876,45 @@ hrt_status hrt_raymesh_ray_step_tiled(hrt_raymesh* rm, const hrt_rays* rays, con
                                       double a_ref, double omega_m, float* maps, void* stream) {
   if (!grad_z) return fail(HRT_ERR_INVALID_ARG, "grad_z is NULL");
   return step_call(rm, rays, grad_x, grad_y, grad_z, geom, chi_from, chi_to, a_ref, omega_m, maps, stream);
+}
+
+hrt_status hrt_raymesh_kick_adjoint(hrt_raymesh* rm, const float* grad_x, const float* grad_y, const float* mesh_bar,
+                                    const hrt_ray_geom* geom, double chi_a, double chi_b, double a_ref, double omega_m,
+                                    float* gx_bar, float* gy_bar, double* plane_bar_host, void* stream) {
+  return kick_adjoint_call(rm, grad_x, grad_y, mesh_bar, geom, chi_a, chi_b, a_ref, omega_m, gx_bar, gy_bar,
+                           plane_bar_host, stream);
+}
+
+hrt_status hrt_raymesh_ray_step_adjoint(hrt_raymesh* rm, const hrt_rays* rays, const float* grad_x, const float* grad_y,
+                                        const hrt_ray_geom* geom, double chi_from, double chi_to, double a_ref,
+                                        double omega_m, const hrt_rays* bar, float* gx_bar, float* gy_bar,
+                                        double* plane_bar_host, double* drift_bar_host, void* stream) {
+  return step_adjoint_call(rm, rays, grad_x, grad_y, geom, chi_from, chi_to, a_ref, omega_m, bar, gx_bar, gy_bar,
+                           plane_bar_host, drift_bar_host, stream);
+}
+
+hrt_status hrt_raymesh_step_planes(const hrt_raymesh_config* cfg, const hrt_ray_geom* geom, double chi_from,
+                                   double chi_to, double a_ref, double omega_m, int32_t* n1_host, int32_t* n2_host,
+                                   double* chi_host, double* w_host, double* drift_host) {
+  if (!cfg || !n1_host || !n2_host || !chi_host || !w_host || !drift_host) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  HRT_TRY(check_geom(geom, false));
+  if (!(omega_m > 0.0 && omega_m <= 1.0)) return fail(HRT_ERR_INVALID_ARG, "omega_m must be in (0, 1]");
+  const double chi_mid = 0.5 * (chi_from + chi_to);
+  if (!(chi_mid > 0.0)) return fail(HRT_ERR_INVALID_ARG, "shell midpoint must be at chi > 0");
+  static thread_local ProjectParams p;
+  const double lo[2] = {chi_from, chi_mid}, hi[2] = {chi_mid, chi_to};
+  int32_t* counts[2] = {n1_host, n2_host};
+  const double cell = geom->box / geom->n;
+  for (int h = 0; h < 2; ++h) {
+    double lam, x2d;
+    int64_t n2d;
+    HRT_TRY(geometry(*cfg, lo[h], hi[h], cell, lam, x2d, n2d));
+    HRT_TRY(plane_table(*geom, lo[h], hi[h], a_ref, omega_m, x2d, n2d, p, w_host + h * kMaxMeshPlanes,
+                        chi_host + h * kMaxMeshPlanes));
+    *counts[h] = p.n_planes;
+  }
+  drift_host[0] = (chi_to - chi_from) / (kCLight * chi_mid * chi_mid);
+  return HRT_OK;
 }
 
 }  // extern "C"

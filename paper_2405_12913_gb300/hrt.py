@@ -90,6 +90,9 @@ _SIGS = {
     "hrt_raymesh_kick": ([_P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
     "hrt_raymesh_ray_step": ([_P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
     "hrt_raymesh_kick_tiled": ([_P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
+    "hrt_raymesh_kick_adjoint": ([_P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P, _P, _P], C.c_int),
+    "hrt_raymesh_ray_step_adjoint": ([_P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P, _P, _P, _P, _P], C.c_int),
+    "hrt_raymesh_step_planes": ([_P, _P, _D, _D, _D, _D, _P, _P, _P, _P, _P], C.c_int),
     "hrt_raymesh_ray_step_tiled": ([_P, _P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
     "hrt_set_ray_mesh": ([_P, _P], C.c_int),
     "hrt_ray_drift_free": ([_P, _D, _D, _P], C.c_int),
@@ -394,6 +397,18 @@ def hrt_raymesh_geometry(cfg: hrt_raymesh_config, chi_a: float, chi_b: float, ce
     return lam.value, x2d.value, n2d.value
 
 
+def hrt_raymesh_step_planes(cfg: hrt_raymesh_config, geom: hrt_ray_geom, chi_from: float, chi_to: float,
+                            a_ref: float, omega_m: float):
+    """Planes of a ray-mesh step: ([n1, n2], chi [2][512], w [2][512], drift) (numpy, FP64)."""
+    import numpy as np
+    n1, n2 = C.c_int32(), C.c_int32()
+    chi, w, d = np.zeros(1024), np.zeros(1024), np.zeros(1)
+    _check(_lib.hrt_raymesh_step_planes(C.byref(cfg), C.byref(geom), chi_from, chi_to, a_ref, omega_m, C.byref(n1),
+                                        C.byref(n2), chi.ctypes.data, w.ctypes.data, d.ctypes.data),
+           "hrt_raymesh_step_planes")
+    return [n1.value, n2.value], chi.reshape(2, 512), w.reshape(2, 512), float(d[0])
+
+
 class RayMesh:
     """Owner of an ``hrt_raymesh`` workspace (ray-mesh kick operator)."""
 
@@ -432,6 +447,36 @@ class RayMesh:
                                                    C.byref(geom), chi_from, chi_to, a_ref, omega_m,
                                                    _ptr(maps, torch.float32, "maps"), _stream(stream)),
                    "hrt_raymesh_ray_step_tiled")
+
+    def hrt_raymesh_kick_adjoint(self, grad_x, grad_y, mesh_bar: torch.Tensor, geom: hrt_ray_geom, chi_a: float,
+                                 chi_b: float, a_ref: float, omega_m: float, gx_bar: torch.Tensor, gy_bar: torch.Tensor,
+                                 stream=None):
+        """Accumulates dL/dgrad into gx_bar, gy_bar; returns dL/dw_p of the shell's planes (numpy)."""
+        import numpy as np
+        pb = np.zeros(512)
+        _check(_lib.hrt_raymesh_kick_adjoint(self._h, _ptr(grad_x, torch.float32, "grad_x"),
+                                             _ptr(grad_y, torch.float32, "grad_y"),
+                                             _ptr(mesh_bar, torch.float32, "mesh_bar"), C.byref(geom), chi_a, chi_b,
+                                             a_ref, omega_m, _ptr(gx_bar, torch.float32, "gx_bar"),
+                                             _ptr(gy_bar, torch.float32, "gy_bar"), pb.ctypes.data, _stream(stream)),
+               "hrt_raymesh_kick_adjoint")
+        return pb
+
+    def hrt_raymesh_ray_step_adjoint(self, rays: RayState, grad_x, grad_y, geom: hrt_ray_geom, chi_from: float,
+                                     chi_to: float, a_ref: float, omega_m: float, bar: RayState, gx_bar, gy_bar,
+                                     stream=None):
+        """bar: post-step cotangent in, pre-step cotangent out; returns (dL/dw [2][512] numpy, dL/d drift)."""
+        import numpy as np
+        pb = np.zeros(2 * 512)
+        db = np.zeros(1)
+        r, b = rays.c(), bar.c()
+        _check(_lib.hrt_raymesh_ray_step_adjoint(self._h, C.byref(r), _ptr(grad_x, torch.float32, "grad_x"),
+                                                 _ptr(grad_y, torch.float32, "grad_y"), C.byref(geom), chi_from,
+                                                 chi_to, a_ref, omega_m, C.byref(b),
+                                                 _ptr(gx_bar, torch.float32, "gx_bar"),
+                                                 _ptr(gy_bar, torch.float32, "gy_bar"), pb.ctypes.data, db.ctypes.data,
+                                                 _stream(stream)), "hrt_raymesh_ray_step_adjoint")
+        return pb.reshape(2, 512), float(db[0])
 
     def close(self):
         if self._h:

@@ -313,3 +313,108 @@ def test_raymesh_ray_step_at_the_bench_size(hrt):
     assert int(bad_eta) == 0 and int(bad_B) <= 2, (int(bad_eta), int(bad_B))
     dth = rays.theta[idx].cpu() - want["theta"]
     assert float(dth.abs().max()) <= 1e-4 * float((want["theta"] - torch.from_numpy(theta0[idx])).abs().max()) + 1e-15
+
+
+def test_raymesh_kick_adjoint_is_the_transpose(hrt):
+    """<kick(g), K_bar> = <g, kick^T(K_bar)> for the linear map from the gradient fields to the filtered mesh of a
+    half shell, and sum_p w_p dL/dw_p = L (L is linear in the plane weights)."""
+    gx, gy = _fields(70)
+    om, a_ref = 0.3, 0.8
+    for ca, cb, mu, m_pix, iota, p_min in ((150.5, 181.3, 0.004, 40, 0.5, 8), (181.3, 150.5, 0.003, 64, 0.25, 16),
+                                           (40.2, 71.9, 0.003, 50, 1.0, 4)):
+        cfg = hrt.make_raymesh_config(iota, p_min, mu, m_pix)
+        rm = hrt.RayMesh(cfg)
+        geom = hrt.make_geom(N, BOX, OBS)
+        gxd, gyd = gx.cuda().reshape(-1), gy.cuda().reshape(-1)
+        K = rm.hrt_raymesh_kick(gxd, gyd, geom, ca, cb, a_ref, om)
+        g = torch.Generator(device="cuda").manual_seed(5)
+        Kb = torch.randn(K.shape, generator=g, device="cuda")
+        gxb = torch.zeros_like(gxd)
+        gyb = torch.zeros_like(gyd)
+        pb = rm.hrt_raymesh_kick_adjoint(gxd, gyd, Kb, geom, ca, cb, a_ref, om, gxb, gyb)
+        torch.cuda.synchronize()
+        lhs = float((K.double() * Kb.double()).sum())
+        rhs = float((gxd.double() * gxb.double()).sum() + (gyd.double() * gyb.double()).sum())
+        assert abs(lhs - rhs) <= 1e-4 * abs(lhs), (lhs, rhs)
+        n, chi, w, _ = hrt.hrt_raymesh_step_planes(cfg, geom, ca, cb, a_ref, om)
+        # the step's first half shell [ca, (ca + cb) / 2) is not this kick's shell: list this shell's planes
+        planes = raymesh.shell_planes(ca, cb, BOX / N, OBS[2])
+        wq = np.array([-(2.0 / C_LIGHT) * c * sim.growth_weight(a_ref, om)(c) * (1 if cb >= ca else -1) * (BOX / N) ** 3
+                       / (c * c * hrt.hrt_raymesh_geometry(cfg, ca, cb, BOX / N)[1] ** 2) for _, c in planes])
+        assert abs(float((wq * pb[:len(planes)]).sum()) - lhs) <= 1e-4 * abs(lhs)
+        rm.close()
+
+
+@pytest.mark.parametrize("case", [0, 3])
+def test_raymesh_ray_step_adjoint_matches_oracle_derivative(hrt, case):
+    """<bar_after, J v> from central differences of the FP64 oracle step along a direction v of the state and the
+    fields, against <J^T bar_after, v> from the GPU adjoint; and per plane, w_p dL/dw_p equals the plane's share
+    of <g, g_bar>."""
+    ca, cb, mu, m_pix, iota, p_min, a_ref, _ = KICKS[case]
+    om = 0.3
+    wfn = sim.growth_weight(a_ref, om) if a_ref > 0 else (lambda chi: 1.0)
+    gx, gy = _fields(80 + case, 3e3)
+    rng = np.random.default_rng(90 + case)
+    n = 2048
+    half = 0.5 * m_pix * mu
+    th0 = torch.tensor(rng.uniform(-half, half, size=(n, 2)))
+    eta0 = torch.tensor(rng.normal(0, 2e-5, size=(n, 2))).float().double()
+    A0 = torch.tensor(rng.normal(0, 1, size=(n, 2, 2))).float().double()
+    B0 = torch.tensor(rng.normal(0, 1e-2, size=(n, 2, 2))).float().double()
+    # cotangent of the state after the step and a direction for the state before it and the fields
+    wb = {k: torch.tensor(rng.normal(0, 1, size=s)) for k, s in (("theta", (n, 2)), ("eta", (n, 2)), ("A", (n, 2, 2)),
+                                                                 ("B", (n, 2, 2)))}
+    wb["theta"] *= 1e3
+    v = {k: torch.tensor(rng.normal(0, 1, size=s)) for k, s in (("theta", (n, 2)), ("eta", (n, 2)), ("A", (n, 2, 2)),
+                                                                ("B", (n, 2, 2)))}
+    v["theta"] *= 1e-6
+    v["eta"] *= 1e-3
+    vgx = torch.tensor(rng.normal(0, 1, size=(N, N, N))) * 30.0
+    vgy = torch.tensor(rng.normal(0, 1, size=(N, N, N))) * 30.0
+
+    def L(eps, part):
+        st = dict(theta=th0.clone(), eta=eta0.clone(), A=A0.clone(), B=B0.clone())
+        gxe, gye = gx.double(), gy.double()
+        if part == "g":
+            gxe, gye = gxe + eps * vgx, gye + eps * vgy
+        else:
+            st[part] = st[part] + eps * v[part]
+        out = raymesh.ray_step(st, gxe, gye, BOX, OBS, ca, cb, wfn, mu, m_pix, iota, p_min)
+        return sum(float((wb[k] * out[k]).sum()) for k in wb)
+
+    eps = 1e-4
+    jvp = {part: (L(eps, part) - L(-eps, part)) / (2 * eps) for part in ("theta", "eta", "A", "B", "g")}
+
+    rays = hrt.RayState(n)
+    rays.theta.copy_(th0.cuda())
+    rays.eta.copy_(eta0.float().cuda())
+    rays.A.copy_(A0.reshape(n, 4).float().cuda())
+    rays.B.copy_(B0.reshape(n, 4).float().cuda())
+    bar = hrt.RayState(n)
+    bar.theta.copy_(wb["theta"].cuda())
+    bar.eta.copy_(wb["eta"].float().cuda())
+    bar.A.copy_(wb["A"].reshape(n, 4).float().cuda())
+    bar.B.copy_(wb["B"].reshape(n, 4).float().cuda())
+    gxd, gyd = gx.cuda().reshape(-1), gy.cuda().reshape(-1)
+    gxb, gyb = torch.zeros_like(gxd), torch.zeros_like(gyd)
+    cfg = hrt.make_raymesh_config(iota, p_min, mu, m_pix)
+    rm = hrt.RayMesh(cfg)
+    geom = hrt.make_geom(N, BOX, OBS)
+    pb, _ = rm.hrt_raymesh_ray_step_adjoint(rays, gxd, gyd, geom, ca, cb, a_ref, om, bar, gxb, gyb)
+    torch.cuda.synchronize()
+    rm.close()
+    vjp = {"theta": float((bar.theta.cpu() * v["theta"]).sum()), "eta": float((bar.eta.double().cpu() * v["eta"]).sum()),
+           "A": float((bar.A.double().cpu().reshape(n, 2, 2) * v["A"]).sum()),
+           "B": float((bar.B.double().cpu().reshape(n, 2, 2) * v["B"]).sum()),
+           "g": float((gxb.double().cpu() * vgx.reshape(-1)).sum()) + float((gyb.double().cpu() * vgy.reshape(-1)).sum())}
+    for part in jvp:
+        assert abs(vjp[part] - jvp[part]) <= 2e-3 * abs(jvp[part]), (part, vjp[part], jvp[part])
+    # plane weights: w_p dL/dw_p = sum over the plane's nodes of g . g_bar
+    counts, chi, w, _ = hrt.hrt_raymesh_step_planes(cfg, geom, ca, cb, a_ref, om)
+    gbx, gby = gxb.double().cpu().reshape(N, N, N), gyb.double().cpu().reshape(N, N, N)
+    g64x, g64y = gx.double().reshape(N, N, N), gy.double().reshape(N, N, N)
+    for h in range(2):
+        for q in range(counts[h]):
+            kz = int(round((chi[h, q] + OBS[2]) / (BOX / N))) % N
+            share = float((g64x[:, :, kz] * gbx[:, :, kz]).sum() + (g64y[:, :, kz] * gby[:, :, kz]).sum())
+            assert abs(w[h, q] * pb[h, q] - share) <= 1e-4 * (abs(share) + 1e-30) + 1e-9 * float(np.abs(pb).max() * np.abs(w).max())
