@@ -40,7 +40,10 @@ class Step:
 class DiffSim:
     """Forward run with checkpoints and its adjoint for one workload (see ``configs.CosmoWorkload``)."""
 
-    def __init__(self, W, theta0: torch.Tensor, checkpoint_every: int = 4):
+    def __init__(self, W, theta0: torch.Tensor, checkpoint_every: int = 4, ray_mesh=None):
+        """``ray_mesh``: an ``hrt.make_raymesh_config`` to kick the rays on the ray mesh of Sec. 5.2 (the adjoint then
+        holds the mesh geometry of each half shell fixed: dL/dOmega_m acts through the plane weights and the
+        drift coefficients, not through lambda_lim), or None for the direct line-of-sight gather."""
         self.W = W
         self.k = max(1, int(checkpoint_every))
         n, L = W.n_mesh, W.box
@@ -52,6 +55,8 @@ class DiffSim:
         self.theta0 = theta0.to(device="cuda", dtype=torch.float64).contiguous()
         self.n_rays = self.theta0.shape[0]
         self.n_slots = len(W.source_steps)
+        self.rm_cfg = ray_mesh
+        self.rm = hrt.RayMesh(ray_mesh) if ray_mesh is not None else None
 
     # ------------------------------------------------------------------------------------------- plan
     def plan(self):
@@ -101,7 +106,11 @@ class DiffSim:
         if step.kind == "R":
             chi0, chi1 = hrt.hrt_cosmo_eval(om, step.a_x)[1], hrt.hrt_cosmo_eval(om, step.a_next)[1]
             out = maps[step.slot] if (maps is not None and step.slot >= 0) else None
-            hrt.hrt_ray_step(st["rays"], st["g"][0], st["g"][1], self.geom, chi0, chi1, step.a_x, om, out)
+            if self.rm is not None:
+                self.rm.hrt_raymesh_ray_step(st["rays"], st["g"][0], st["g"][1], self.geom, chi0, chi1, step.a_x, om,
+                                             out)
+            else:
+                hrt.hrt_ray_step(st["rays"], st["g"][0], st["g"][1], self.geom, chi0, chi1, step.a_x, om, out)
         if step.kind == "S":
             hrt.hrt_particle_kick_drift(st["g"], self.n, self.L, self.ns, st["d"], st["m"], K, 0.0)
             return
@@ -163,6 +172,7 @@ class DiffSim:
         node_bar = torch.zeros(n_steps, 3, hrt.MAX_RAY_NODES, dtype=torch.float64, device="cuda")
         drift_bar = torch.zeros(n_steps, dtype=torch.float64, device="cuda")
         pref_bar = np.zeros(n_steps)
+        plane_bar = np.zeros((n_steps, 2, 512))
         starts = sorted(self.checkpoints)
         for s0 in reversed(starts):
             s1 = min(s0 + self.k, n_steps)
@@ -190,8 +200,14 @@ class DiffSim:
                                                         rho_bar, d_bar, m_bar, g_bar, coef_bar[i])
                 if step.kind == "R":
                     chi0, chi1 = hrt.hrt_cosmo_eval(om, step.a_x)[1], hrt.hrt_cosmo_eval(om, step.a_next)[1]
-                    hrt.hrt_ray_step_adjoint(ps["rays"], ps["g"][0], ps["g"][1], self.geom, chi0, chi1, step.a_x, om,
-                                             r_bar, g_bar[0], g_bar[1], node_bar[i], drift_bar[i:i + 1])
+                    if self.rm is not None:
+                        plane_bar[i], db = self.rm.hrt_raymesh_ray_step_adjoint(
+                            ps["rays"], ps["g"][0], ps["g"][1], self.geom, chi0, chi1, step.a_x, om, r_bar, g_bar[0],
+                            g_bar[1])
+                        drift_bar[i] += db
+                    else:
+                        hrt.hrt_ray_step_adjoint(ps["rays"], ps["g"][0], ps["g"][1], self.geom, chi0, chi1, step.a_x,
+                                                 om, r_bar, g_bar[0], g_bar[1], node_bar[i], drift_bar[i:i + 1])
                 pref = 1.5 * om / step.a_x
                 pref_bar[i] = hrt.hrt_dot(g_bar, ps["g"]) / pref
                 rho_bar = torch.empty(self.m, device="cuda")
@@ -202,10 +218,10 @@ class DiffSim:
         table_bar, ratio_bar = hrt.hrt_ic_zeldovich_adjoint(self.noise, self.ns, self.L, om, W.h, W.n_s, W.sigma8,
                                                             W.a_init, d_bar, m_bar, self.d0, noise_bar)
         om_bar = self._omega_chain(coef_bar.cpu().numpy(), node_bar.cpu().numpy(), drift_bar.cpu().numpy(),
-                                   pref_bar, table_bar, ratio_bar)
+                                   pref_bar, table_bar, ratio_bar, plane_bar)
         return noise_bar, om_bar
 
-    def _omega_chain(self, coef_bar, node_bar, drift_bar, pref_bar, table_bar, ratio_bar) -> float:
+    def _omega_chain(self, coef_bar, node_bar, drift_bar, pref_bar, table_bar, ratio_bar, plane_bar) -> float:
         W, om, e = self.W, self.om, _EPS_OM
         total = 0.0
         for i, step in enumerate(self.steps):
@@ -213,7 +229,19 @@ class DiffSim:
             km, dm = self.coefficients(step, om - e)
             total += coef_bar[i, 0] * (kp - km) / (2 * e) + coef_bar[i, 1] * (dp - dm) / (2 * e)
             total += pref_bar[i] * 1.5 / step.a_x
-            if step.kind == "R":
+            if step.kind == "R" and self.rm is not None:
+                # plane weights at the nominal geometry: w is proportional to g(chi_p) / x2d^2, x2d held fixed
+                hi, lo = self._mesh_coefficients(step, om + e), self._mesh_coefficients(step, om - e)
+                x2d0 = self._mesh_coefficients(step, om)[2]
+                if hi[0] != lo[0] or not np.array_equal(hi[1], lo[1]):
+                    raise RuntimeError("a ray-mesh plane changes half shell within the Omega_m difference step")
+                for h in range(2):
+                    k = hi[0][h]
+                    wp = hi[3][h, :k] * (hi[2][h] / x2d0[h]) ** 2
+                    wm = lo[3][h, :k] * (lo[2][h] / x2d0[h]) ** 2
+                    total += float(plane_bar[i, h, :k] @ ((wp - wm) / (2 * e)))
+                total += drift_bar[i] * (hi[4] - lo[4]) / (2 * e)
+            elif step.kind == "R":
                 hi = self._ray_coefficients(step, om + e)
                 lo = self._ray_coefficients(step, om - e)
                 if hi[0] != lo[0]:
@@ -233,8 +261,19 @@ class DiffSim:
         n1, n2, cw, cwr, chi, d = hrt.hrt_ray_step_coefficients(self.geom, chi0, chi1, step.a_x, om)
         return n1 + n2, cw, cwr, chi, d
 
+    def _mesh_coefficients(self, step: Step, om: float):
+        """(plane counts, plane chi [2][512], x2d per half shell, FP64 plane weights [2][512], drift)."""
+        chi0, chi1 = hrt.hrt_cosmo_eval(om, step.a_x)[1], hrt.hrt_cosmo_eval(om, step.a_next)[1]
+        counts, chi, w, d = hrt.hrt_raymesh_step_planes(self.rm_cfg, self.geom, chi0, chi1, step.a_x, om)
+        mid = 0.5 * (chi0 + chi1)
+        cell = self.L / self.n
+        x2d = [hrt.hrt_raymesh_geometry(self.rm_cfg, a, b, cell)[1] for a, b in ((chi0, mid), (mid, chi1))]
+        return counts, np.round(chi, 9), x2d, w, d
+
     def close(self):
         self.pm.close()
+        if self.rm is not None:
+            self.rm.close()
 
 
 class HRTKappa(torch.autograd.Function):

@@ -382,3 +382,53 @@ def test_power_loss_gradient_at_128p_256m_matches_central_differences(hrt):
         fd = (float(loss(noise + eps * d, target, scale)) - float(loss(noise - eps * d, target, scale))) / (2 * eps)
     assert ad == pytest.approx(fd, rel=3e-2), (ad, fd)
     sim.close()
+
+
+def _oracle_run_mesh(W, noise, theta0, om, rm_args):
+    c = osim.Cosmo(om, W.h, W.n_s, W.sigma8)
+    flt = osim.Filter(W.deconv_p, W.smooth_cells)
+    part = osim.initial_particles(noise, W.box, c, W.a_init)
+    part, grads = osim.run_forward(part, W.forward_grid, W.box, W.n_mesh, c, flt)
+    res = osim.run_reverse(part, grads, W.reverse_grid, W.box, W.n_mesh, c, flt, theta0, W.observer,
+                           set(W.source_steps), W.samples_per_cell, ray_mesh=rm_args)
+    return torch.stack([res.maps[s][0] for s in W.source_steps]), res.rays["theta"]
+
+
+def test_ray_mesh_end_to_end_gradient_matches_oracle_differences(hrt):
+    """The differentiable simulation with the ray-mesh kick: the noise gradient of a loss on the kappa maps and
+    the final angles against FP64 central differences of the oracle run with the ray-mesh kick (tiny steps that
+    resolve the pieces of the piecewise-smooth kappa)."""
+    from paper_2405_12913_gb300 import autodiff
+    from paper_2405_12913_gb300.configs import COSMO_GRAD as W
+    rm_args = (W.dtheta, W.n_pix, 0.5, 8.0)
+    noise = synthetic.white_noise(W.seed + 3, W.n_side)
+    theta0 = torch.tensor(synthetic.pixel_grid(W.n_pix, W.fov_deg * synthetic.DEGREE))
+    kbar = synthetic.gaussian_field(77, (len(W.source_steps), W.n_rays))
+    tb = synthetic.gaussian_field(78, (W.n_rays, 2))
+    om0 = W.omega_m + 1.234e-6
+    sim = autodiff.DiffSim(W, theta0, checkpoint_every=2,
+                           ray_mesh=hrt.make_raymesh_config(rm_args[2], rm_args[3], rm_args[0], rm_args[1]))
+    w = _cuda(noise).reshape(-1).requires_grad_(True)
+    om = torch.tensor(om0, dtype=torch.float64, requires_grad=True)
+    kap, th = autodiff.HRTKappa.apply(w, om, sim)
+    loss = (kap.double() * _cuda(kbar, torch.float64)).sum() + 1e4 * ((th - theta0.cuda()) * _cuda(tb, torch.float64)).sum()
+    loss.backward()
+    direction = synthetic.gaussian_field(79, (W.n_side ** 3,))
+    ad = float((w.grad.cpu().double() * torch.tensor(direction)).sum())
+
+    def oracle_loss(wn, omv):
+        with torch.no_grad():
+            k, t = _oracle_run_mesh(W, wn, theta0, omv, rm_args)
+            return float((k * torch.tensor(kbar)).sum() + 1e4 * ((t - theta0) * torch.tensor(tb)).sum())
+
+    k_o, _ = _oracle_run_mesh(W, torch.tensor(noise), theta0, om0, rm_args)
+    assert np.abs(kap.detach().cpu().numpy() - k_o.numpy()).max() <= 1e-3 * k_o.abs().max()
+    d = torch.tensor(direction).reshape(noise.shape)
+    fds = _piecewise_fd(lambda e: oracle_loss(torch.tensor(noise) + e * d, om0), 0.0)
+    assert sum(abs(ad - v) <= 2e-3 * abs(v) for v in fds) >= 2, (ad, fds)
+    # Omega_m: the adjoint holds each half shell's ray-mesh geometry fixed, the differences move it with the
+    # comoving distances of the shell boundaries
+    fds_om = _piecewise_fd(lambda x: oracle_loss(torch.tensor(noise), x), om0)
+    print("ray-mesh dL/dOmega_m: adjoint %.6g, oracle differences %s" % (float(om.grad), fds_om))
+    assert sum(abs(float(om.grad) - v) <= 2e-2 * abs(v) for v in fds_om) >= 2, (float(om.grad), fds_om)
+    sim.close()
