@@ -152,6 +152,10 @@ def test_raymesh_rejects_bad_configurations(hrt):
         hrt.hrt_raymesh_geometry(cfg, 1000.0, 1010.0, 2.0)
     rm = hrt.RayMesh(hrt.make_raymesh_config(0.5, 8, 0.004, 40))
     gx, gy = _fields(1)
+    big = hrt.RayMesh(hrt.make_raymesh_config(1.0, 0, 1.0, 1))   # a ray-mesh cell of ~160 mesh cells at chi = 300
+    with pytest.raises(HRTError):
+        big.hrt_raymesh_kick(gx.cuda().reshape(-1), gy.cuda().reshape(-1), hrt.make_geom(N, BOX, OBS), 300.0, 310.0)
+    big.close()
     geom = hrt.make_geom(N, BOX, OBS, replicas=(np.array([[0, 1, 2]]), np.array([[1, 1, 1]]), np.array([[0, 0, 0]])))
     with pytest.raises(HRTError):      # no light-cone tiling
         rm.hrt_raymesh_kick(gx.cuda().reshape(-1), gy.cuda().reshape(-1), geom, 150.5, 181.3)
