@@ -360,7 +360,7 @@ def run_gpu(args, W, world, rank, local):
                    "timed_steps_start_at_a": 1.0, "parallelism": f"replicas{world}",
                    "kick": ("ray mesh (iota %g, p_min %g)" % (RAYMESH_IOTA, RAYMESH_P_MIN)
                             if args.kick == "mesh" else "direct line-of-sight gather"),
-                   "l2": "inputs larger than L2 (4.3 GB mesh per field)"},
+                   "l2": "inputs larger than L2 (%.2g GB mesh per field)" % (W.n_mesh ** 3 * 4 / 1e9)},
         "clocks": clk, "gpu_launches": launches,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
