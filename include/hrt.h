@@ -519,6 +519,24 @@ hrt_status hrt_raymesh_step_planes(const hrt_raymesh_config* cfg, const hrt_ray_
                                    double chi_to, double a_ref, double omega_m, int32_t* n1_host, int32_t* n2_host,
                                    double* chi_host, double* w_host, double* drift_host);
 
+/* Reverse mode of a whole run (the adjoint method named as future work in Sec. 7).  hrt_set_checkpointing(ctx,
+ * k) with k >= 1 makes the context record the run that starts at the next hrt_init_particles_zeldovich: the
+ * noise, the steps (hrt_step, hrt_step_accumulate, hrt_sync_particles), the initial ray angles
+ * (hrt_init_rays) and, every k steps, a checkpoint of the particles and rays (device memory: 24 B per particle
+ * + 48 B per ray per checkpoint, freed by the next call or hrt_destroy); k = 0 stops recording and frees it.
+ * hrt_adjoint then returns the gradient of a loss L with respect to the white noise and Omega_m, given
+ * kappa_bar (device float32 [n_sources][n_rays], dL/dkappa of the maps as they are at the end of the run, or
+ * NULL) and theta_bar (device FP64 [n_rays][2], dL/dtheta of the final ray angles, or NULL): noise_bar (device
+ * float32 [n_side^3]) receives dL/dnoise and *omega_bar_host (or NULL) dL/dOmega_m.  It recomputes each
+ * segment of k steps from its checkpoint (transient device memory: k pre-step states of particles, rays and
+ * the three fields) and runs the adjoint calls above in reverse.  Supported: Zel'dovich ICs, ray steps on the
+ * particle fields (ray_fields == 0), untiled, with the direct gather or the ray mesh (R29); 2LPT or given
+ * initial particles, loaded states, static-lens steps, free drifts, tiling and ray fields make the record
+ * unusable (HRT_ERR_STATE with the reason).  Synchronises the context's stream. */
+hrt_status hrt_set_checkpointing(hrt_ctx* ctx, int32_t every);
+hrt_status hrt_adjoint(hrt_ctx* ctx, const float* kappa_bar, const double* theta_bar, float* noise_bar,
+                       double* omega_bar_host);
+
 /* Kick operator of the context's rays: cfg != NULL switches to the ray-mesh kick of hrt_raymesh_ray_step
  * (configuration copied; the context owns its workspace), cfg == NULL back to the direct line-of-sight
  * gather.  The ray mesh reads the same 3D fields as the direct gather (the ray fields when ray_fields == 2; all

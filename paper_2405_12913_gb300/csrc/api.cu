@@ -13,6 +13,7 @@
 
 #include "adjoint.h"
 #include "common.h"
+#include "context.h"
 #include "cosmo.h"
 #include "kspace_callback.h"
 #include "mesh_kernels.h"
@@ -68,7 +69,7 @@ hrt_status device_alloc(void** p, size_t bytes, cudaStream_t stream, const char*
   return cuda_status(cudaMallocAsync(p, bytes, stream), what);
 }
 
-static void device_free(void* p, cudaStream_t s) {
+void device_free(void* p, cudaStream_t s) {
   if (p) cudaFreeAsync(p, s);
 }
 
@@ -212,44 +213,8 @@ static hrt_status check_rays(const hrt_rays* r) {
 }  // namespace hrt
 
 // ---------------------------------------------------------------------------------------------------------
-// Context
+// Context (the struct is in context.h)
 // ---------------------------------------------------------------------------------------------------------
-struct hrt_ctx {
-  hrt_config cfg{};
-  cudaStream_t stream = nullptr;
-  bool poisoned = false;
-  hrt_pm* pm = nullptr;
-  float* disp = nullptr;
-  float* mom = nullptr;
-  float* rho = nullptr;
-  float* grad = nullptr;
-  float* ray_grad = nullptr;
-  bool have_particles = false;
-  double a = 1.0, a_mom = 1.0;
-  hrt_rays rays{};
-  float* maps = nullptr;
-  int64_t maps_rays = 0;
-  bool profiling = false;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> phases[8];
-  // second stream for the ray step, which overlaps the particle update of the same step (both only read
-  // the force fields); ev_fields: fields ready, ev_rays: ray step done (the next C2R waits for it)
-  cudaStream_t ray_stream = nullptr;
-  cudaEvent_t ev_fields = nullptr, ev_rays = nullptr;
-  bool rays_pending = false;
-  // learned ray-force correction (NULL: plain)
-  float* corr_w = nullptr;
-  void* corr_wb = nullptr;
-  float* corr_x = nullptr;
-  float* corr_table = nullptr;
-  // light-cone tiling (empty: none): [n][3] perm, sign, shift
-  std::vector<int32_t> rep_perm, rep_sign, rep_shift;
-  // ray-mesh kick operator of Sec. 5.2 (NULL: the direct line-of-sight gather)
-  hrt_raymesh* raymesh = nullptr;
-  // fixed learned table of the ray fields (NULL: none); exclusive with the network above
-  float* ray_table = nullptr;
-  int32_t ray_table_nk = 0;
-  double ray_table_kmax = 0.0;
-};
 
 namespace hrt {
 
@@ -589,7 +554,7 @@ static hrt_status ctx_mark(hrt_ctx* ctx, hrt_status s) {
   return s;
 }
 
-static hrt_filter ctx_filter(const hrt_config& c, bool ray) {
+hrt_filter ctx_filter(const hrt_config& c, bool ray) {
   hrt_filter f{};
   const double cell = c.box / c.n_mesh;
   f.deconv_p = ray ? c.ray_deconv_p : c.deconv_p;
@@ -636,7 +601,7 @@ static hrt_status ctx_force(hrt_ctx* ctx) {
 }
 
 
-static hrt_ray_geom ctx_geom(const hrt_config& c, const hrt_ctx* ctx = nullptr) {
+hrt_ray_geom ctx_geom(const hrt_config& c, const hrt_ctx* ctx) {
   hrt_ray_geom g{};
   if (ctx && !ctx->rep_perm.empty()) {
     g.n_replicas = static_cast<int32_t>(ctx->rep_perm.size() / 3);
@@ -1303,6 +1268,7 @@ hrt_status hrt_destroy(hrt_ctx* ctx) {
       cudaEventDestroy(ev.first);
       cudaEventDestroy(ev.second);
     }
+  tape_free(ctx);
   hrt_pm_destroy(ctx->pm);
   hrt_raymesh_destroy(ctx->raymesh);
   device_free(ctx->disp, s);
@@ -1361,6 +1327,7 @@ hrt_status hrt_init_particles_zeldovich(hrt_ctx* ctx, const float* noise, double
   if (ctx->cfg.static_mode) return fail(HRT_ERR_STATE, "Zel'dovich ICs need the expanding mode");
   hrt_status s = hrt_ic_zeldovich(noise, ctx->cfg.n_side, ctx->cfg.box, &ctx->cfg.cosmo, a_init, ctx->disp,
                                   ctx->mom, ctx->stream);
+  if (s == HRT_OK) s = tape_on_ics(ctx, noise, a_init);
   if (s != HRT_OK) return ctx_mark(ctx, s);
   ctx->a = ctx->a_mom = a_init;
   ctx->have_particles = true;
@@ -1370,6 +1337,7 @@ hrt_status hrt_init_particles_zeldovich(hrt_ctx* ctx, const float* noise, double
 hrt_status hrt_init_particles_2lpt(hrt_ctx* ctx, const float* noise, double a_init) {
   HRT_TRY(ctx_guard(ctx));
   if (ctx->cfg.static_mode) return fail(HRT_ERR_STATE, "2LPT ICs need the expanding mode");
+  tape_invalidate(ctx, "the adjoint starts from Zel'dovich initial conditions");
   hrt_status s = hrt_ic_2lpt(noise, ctx->cfg.n_side, ctx->cfg.box, &ctx->cfg.cosmo, a_init, ctx->disp, ctx->mom,
                              ctx->stream);
   if (s != HRT_OK) return ctx_mark(ctx, s);
@@ -1381,6 +1349,7 @@ hrt_status hrt_init_particles_2lpt(hrt_ctx* ctx, const float* noise, double a_in
 hrt_status hrt_init_particles(hrt_ctx* ctx, const float* disp, const float* mom, double a) {
   HRT_TRY(ctx_guard(ctx));
   if (!disp || !mom || !(a > 0.0 && a <= 1.0)) return fail(HRT_ERR_INVALID_ARG, "bad particle arguments");
+  tape_invalidate(ctx, "the adjoint starts from Zel'dovich initial conditions");
   const size_t bytes = 3 * static_cast<size_t>(ctx->cfg.n_side * ctx->cfg.n_side * ctx->cfg.n_side) * sizeof(float);
   hrt_status s = cuda_status(cudaMemcpyAsync(ctx->disp, disp, bytes, cudaMemcpyDeviceToDevice, ctx->stream), "copy disp");
   if (s == HRT_OK) s = cuda_status(cudaMemcpyAsync(ctx->mom, mom, bytes, cudaMemcpyDeviceToDevice, ctx->stream), "copy mom");
@@ -1412,6 +1381,7 @@ hrt_status hrt_init_rays(hrt_ctx* ctx, const double* theta0, int64_t n_rays) {
   if (s == HRT_OK && ctx->maps)
     s = cuda_status(cudaMemsetAsync(ctx->maps, 0, 4 * n_rays * ctx->cfg.n_sources * sizeof(float), st), "maps memset");
   if (s == HRT_OK) s = launch_rays_init(r, theta0, st);
+  if (s == HRT_OK) s = tape_on_rays(ctx, theta0, n_rays);
   if (s != HRT_OK) {
     device_free(r.theta, st);
     device_free(r.eta, st);
@@ -1440,6 +1410,10 @@ hrt_status hrt::ctx_step(hrt_ctx* ctx, double a_next, int32_t source, double wei
   if (ctx->cfg.static_mode) return fail(HRT_ERR_STATE, "hrt_step needs the expanding mode");
   if (!ctx->have_particles) return fail(HRT_ERR_STATE, "no particles");
   if (!(a_next > 0.0 && a_next <= 1.0) || a_next == ctx->a) return fail(HRT_ERR_INVALID_ARG, "bad a_next");
+  if (ctx->tape) {
+    const char kind = (ctx->rays.n_rays > 0 && a_next < ctx->a) ? 'R' : 'F';
+    HRT_TRY(ctx_mark(ctx, tape_on_step(ctx, kind, a_next, source, weight, accumulate)));
+  }
   Cosmo c(ctx->cfg.cosmo.omega_m);
   hrt_status s = HRT_OK;
   PhaseScope whole(ctx, 6);
@@ -1517,6 +1491,7 @@ hrt_status hrt_sync_particles(hrt_ctx* ctx) {
   if (!ctx->have_particles) return fail(HRT_ERR_STATE, "no particles");
   if (ctx->cfg.static_mode || ctx->a_mom == ctx->a) return HRT_OK;
   Cosmo c(ctx->cfg.cosmo.omega_m);
+  HRT_TRY(ctx_mark(ctx, tape_on_step(ctx, 'S', ctx->a, -1, 1.0, false)));
   hrt_status s = launch_kick_drift(ctx->grad, ctx->cfg.n_mesh, ctx->cfg.box, ctx->cfg.n_side, ctx->disp, ctx->mom,
                                    c.kick(ctx->a_mom, ctx->a), 0.0, ctx->stream);
   if (s == HRT_OK) ctx->a_mom = ctx->a;
@@ -1528,12 +1503,14 @@ hrt_status hrt_step_static(hrt_ctx* ctx, double chi_from, double chi_to, int32_t
   if (!ctx->cfg.static_mode) return fail(HRT_ERR_STATE, "hrt_step_static needs the static mode");
   if (!ctx->have_particles) return fail(HRT_ERR_STATE, "no lens particles");
   if (ctx->rays.n_rays == 0) return fail(HRT_ERR_STATE, "no rays");
+  tape_invalidate(ctx, "static-lens steps are not differentiated");
   return ctx_mark(ctx, ctx_ray_step(ctx, chi_from, chi_to, 0.0, source, ctx->stream));
 }
 
 hrt_status hrt_drift_free(hrt_ctx* ctx, double chi_from, double chi_to) {
   HRT_TRY(ctx_guard(ctx));
   if (ctx->rays.n_rays == 0) return fail(HRT_ERR_STATE, "no rays");
+  tape_invalidate(ctx, "free drifts are not differentiated");
   return ctx_mark(ctx, hrt_ray_drift_free(&ctx->rays, chi_from, chi_to, ctx->stream));
 }
 
@@ -1596,7 +1573,7 @@ hrt_status hrt_set_replicas(hrt_ctx* ctx, int32_t n, const int32_t* perm, const 
   if (n < 0 || n > kMaxReplicas || !perm || !sign || !shift)
     return fail(HRT_ERR_INVALID_ARG, "tiling needs 1..%d replicas with their perm, sign and shift tables", kMaxReplicas);
   // validate through the node-table builder (one empty shell at the observer's replica)
-  hrt_ray_geom g = ctx_geom(ctx->cfg);
+  hrt_ray_geom g = ctx_geom(ctx->cfg, nullptr);
   g.n_replicas = n;
   g.replica_perm = perm;
   g.replica_sign = sign;
@@ -1608,6 +1585,27 @@ hrt_status hrt_set_replicas(hrt_ctx* ctx, int32_t n, const int32_t* perm, const 
   ctx->rep_sign.assign(sign, sign + 3 * n);
   ctx->rep_shift.assign(shift, shift + 3 * n);
   return HRT_OK;
+}
+
+hrt_status hrt_set_checkpointing(hrt_ctx* ctx, int32_t every) {
+  HRT_TRY(ctx_guard(ctx));
+  if (every < 0) return fail(HRT_ERR_INVALID_ARG, "checkpoint interval must be >= 0");
+  tape_free(ctx);
+  if (every > 0) {
+    ctx->tape = new (std::nothrow) Tape;
+    if (!ctx->tape) return fail(HRT_ERR_OOM, "tape");
+    ctx->tape->every = every;
+  }
+  return HRT_OK;
+}
+
+hrt_status hrt_adjoint(hrt_ctx* ctx, const float* kappa_bar, const double* theta_bar, float* noise_bar,
+                       double* omega_bar_host) {
+  HRT_TRY(ctx_guard(ctx));
+  if (ctx->ray_stream) cudaStreamSynchronize(ctx->ray_stream);
+  hrt_status s = tape_adjoint(ctx, kappa_bar, theta_bar, noise_bar, omega_bar_host);
+  if (s == HRT_OK) s = cuda_status(cudaStreamSynchronize(ctx->stream), "adjoint sync");
+  return ctx_mark(ctx, s);
 }
 
 hrt_status hrt_set_ray_mesh(hrt_ctx* ctx, const hrt_raymesh_config* cfg) {
@@ -1704,6 +1702,7 @@ hrt_status hrt_save_state(hrt_ctx* ctx, void* buf, size_t bytes) {
 
 hrt_status hrt_load_state(hrt_ctx* ctx, const void* buf, size_t bytes) {
   HRT_TRY(ctx_guard(ctx));
+  tape_invalidate(ctx, "a loaded state is not differentiated");
   if (!buf || bytes < 256) return fail(HRT_ERR_INVALID_ARG, "state buffer is NULL or too small");
   StateHeader h{};
   cudaStream_t st = ctx->stream;

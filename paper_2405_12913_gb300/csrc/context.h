@@ -1,0 +1,106 @@
+// Internal: the context object behind hrt_ctx (api.cu) and the record of a run that its adjoint replays
+// (tape.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <utility>
+#include <vector>
+
+#include "common.h"
+
+namespace hrt {
+
+// One recorded step of a context: 'F' particles only, 'S' the synchronising kick, 'R' rays and particles.
+struct TapeStep {
+  char kind;
+  double a_x, a_next, a_p;  // position time before and after, momentum time before
+  int slot;                 // map written after a ray step (-1: none)
+  double weight;            // readout weight when accumulating
+  bool accumulate;
+  bool mesh;                // the rays were kicked on the ray mesh ...
+  hrt_raymesh_config mesh_cfg;  // ... of this configuration
+};
+
+// State before a step, kept every `every` steps.
+struct TapeCheckpoint {
+  float* disp = nullptr;
+  float* mom = nullptr;
+  hrt_rays rays{};  // theta == nullptr: no rays yet
+};
+
+struct Tape {
+  int every = 0;
+  bool valid = false;           // a run from Zel'dovich ICs is being recorded
+  const char* invalid_why = "no Zel'dovich initial conditions recorded";
+  double a_init = 0.0;
+  float* noise = nullptr;       // copy of the white noise
+  float* disp0 = nullptr;       // displacements of the ICs
+  double* theta0 = nullptr;     // initial ray angles
+  int64_t n_rays = 0;
+  int rays_start = -1;          // index of the first step with rays
+  std::vector<TapeStep> steps;
+  std::map<int, TapeCheckpoint> checkpoints;
+};
+
+void device_free(void* p, cudaStream_t s);
+
+}  // namespace hrt
+
+struct hrt_ctx {
+  hrt_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool poisoned = false;
+  hrt_pm* pm = nullptr;
+  float* disp = nullptr;
+  float* mom = nullptr;
+  float* rho = nullptr;
+  float* grad = nullptr;
+  float* ray_grad = nullptr;
+  bool have_particles = false;
+  double a = 1.0, a_mom = 1.0;
+  hrt_rays rays{};
+  float* maps = nullptr;
+  int64_t maps_rays = 0;
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> phases[8];
+  // second stream for the ray step, which overlaps the particle update of the same step (both only read
+  // the force fields); ev_fields: fields ready, ev_rays: ray step done (the next C2R waits for it)
+  cudaStream_t ray_stream = nullptr;
+  cudaEvent_t ev_fields = nullptr, ev_rays = nullptr;
+  bool rays_pending = false;
+  // learned ray-force correction (NULL: plain)
+  float* corr_w = nullptr;
+  void* corr_wb = nullptr;
+  float* corr_x = nullptr;
+  float* corr_table = nullptr;
+  // light-cone tiling (empty: none): [n][3] perm, sign, shift
+  std::vector<int32_t> rep_perm, rep_sign, rep_shift;
+  // ray-mesh kick operator of Sec. 5.2 (NULL: the direct line-of-sight gather)
+  hrt_raymesh* raymesh = nullptr;
+  // record of the run for hrt_adjoint (NULL: not recording)
+  hrt::Tape* tape = nullptr;
+  // fixed learned table of the ray fields (NULL: none); exclusive with the network above
+  float* ray_table = nullptr;
+  int32_t ray_table_nk = 0;
+  double ray_table_kmax = 0.0;
+};
+
+namespace hrt {
+
+hrt_filter ctx_filter(const hrt_config& c, bool ray);
+hrt_ray_geom ctx_geom(const hrt_config& c, const hrt_ctx* ctx);
+
+// Recording hooks (tape.cu); each is a no-op without a tape.
+hrt_status tape_on_ics(hrt_ctx* ctx, const float* noise, double a_init);
+hrt_status tape_on_rays(hrt_ctx* ctx, const double* theta0, int64_t n_rays);
+hrt_status tape_on_step(hrt_ctx* ctx, char kind, double a_next, int slot, double weight, bool accumulate);
+void tape_invalidate(hrt_ctx* ctx, const char* why);
+void tape_free(hrt_ctx* ctx);
+// Gradients of a recorded run (hrt_adjoint).
+hrt_status tape_adjoint(hrt_ctx* ctx, const float* kappa_bar, const double* theta_bar, float* noise_bar,
+                        double* omega_bar);
+
+}  // namespace hrt

@@ -663,6 +663,8 @@ static hrt_status build_mesh(hrt_raymesh* rm, int h, const float* gx, const floa
   return HRT_OK;
 }
 
+const hrt_raymesh_config& raymesh_config_of(const hrt_raymesh* rm) { return rm->cfg; }
+
 hrt_status raymesh_step(hrt_raymesh* rm, const hrt_rays& rays, const float* gx, const float* gy, const float* gz,
                         const hrt_ray_geom& g, double chi_from, double chi_to, double a_ref, double omega_m,
                         float* maps, int accumulate, float weight, cudaStream_t s) {

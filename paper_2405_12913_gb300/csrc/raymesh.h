@@ -14,4 +14,7 @@ hrt_status raymesh_step(hrt_raymesh* rm, const hrt_rays& rays, const float* grad
                         const float* grad_z, const hrt_ray_geom& g, double chi_from, double chi_to, double a_ref, double omega_m,
                         float* maps, int accumulate, float weight, cudaStream_t s);
 
+// The configuration a workspace was created with.
+const hrt_raymesh_config& raymesh_config_of(const hrt_raymesh* rm);
+
 }  // namespace hrt

@@ -95,6 +95,8 @@ _SIGS = {
     "hrt_raymesh_step_planes": ([_P, _P, _D, _D, _D, _D, _P, _P, _P, _P, _P], C.c_int),
     "hrt_raymesh_ray_step_tiled": ([_P, _P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
     "hrt_set_ray_mesh": ([_P, _P], C.c_int),
+    "hrt_set_checkpointing": ([_P, _I32], C.c_int),
+    "hrt_adjoint": ([_P, _P, _P, _P, _P], C.c_int),
     "hrt_ray_drift_free": ([_P, _D, _D, _P], C.c_int),
     "hrt_ray_readout": ([_P, _P, _P], C.c_int),
     "hrt_kappa_power": ([_P, _I64, _D, _I32, _D, _D, _P, _P, _P, _P], C.c_int),
@@ -715,6 +717,19 @@ class Context:
         t = [np.ascontiguousarray(x, dtype=np.int32) for x in replicas]
         _check(_lib.hrt_set_replicas(self._h, t[0].shape[0], t[0].ctypes.data, t[1].ctypes.data, t[2].ctypes.data),
                "hrt_set_replicas")
+
+    def hrt_set_checkpointing(self, every: int):
+        """Record the run from the next Zel'dovich ICs for hrt_adjoint (checkpoint every `every` steps; 0: off)."""
+        _check(_lib.hrt_set_checkpointing(self._h, every), "hrt_set_checkpointing")
+
+    def hrt_adjoint(self, kappa_bar: torch.Tensor | None, theta_bar: torch.Tensor | None = None):
+        """(dL/dnoise float32 device tensor, dL/dOmega_m) of the recorded run for the map and angle cotangents."""
+        noise_bar = torch.empty(self.cfg.n_side ** 3, dtype=torch.float32, device="cuda")
+        om = C.c_double()
+        _check(_lib.hrt_adjoint(self._h, _ptr(kappa_bar, torch.float32, "kappa_bar"),
+                                _ptr(theta_bar, torch.float64, "theta_bar"), _ptr(noise_bar, torch.float32, "noise_bar"),
+                                C.byref(om)), "hrt_adjoint")
+        return noise_bar, om.value
 
     def hrt_set_ray_mesh(self, cfg: hrt_raymesh_config | None):
         """Ray-mesh kick operator for the context's rays (a ``make_raymesh_config``), or None for the direct gather."""

@@ -457,3 +457,51 @@ def test_ray_mesh_end_to_end_gradient_matches_oracle_differences(hrt, monkeypatc
     assert sum(abs(float(om.grad) - v) <= 2e-3 * abs(v) for v in fds_fixed) >= 2, (float(om.grad), fds_fixed)
     assert sum(abs(float(om.grad) - v) <= 2e-2 * abs(v) for v in fds_om) >= 2, (float(om.grad), fds_om)
     sim.close()
+
+
+@pytest.mark.parametrize("mesh", [False, True])
+def test_context_adjoint_matches_the_differentiable_simulation(hrt, mesh):
+    """hrt_adjoint of a recorded context run (checkpoints every 2 steps) against autodiff.DiffSim on the same
+    run: the same adjoint calls sequenced natively, so the gradients agree to the rounding of the atomics."""
+    from paper_2405_12913_gb300 import autodiff
+    from paper_2405_12913_gb300.configs import COSMO_GRAD as W
+    rm_cfg = hrt.make_raymesh_config(0.5, 8.0, W.dtheta, W.n_pix) if mesh else None
+    noise = synthetic.white_noise(W.seed + 4, W.n_side)
+    theta0 = torch.tensor(synthetic.pixel_grid(W.n_pix, W.fov_deg * synthetic.DEGREE))
+    kbar = _cuda(synthetic.gaussian_field(81, (len(W.source_steps), W.n_rays)))
+    tb = _cuda(synthetic.gaussian_field(82, (W.n_rays, 2)), torch.float64) * 1e4
+    # the context, recording its run
+    cfg = hrt.make_config(W.n_mesh, W.box, W.n_side, W.omega_m, W.h, W.n_s, W.sigma8, W.deconv_p, W.smooth_cells,
+                          W.samples_per_cell, W.observer, n_sources=len(W.source_steps))
+    ctx = hrt.Context(cfg)
+    ctx.hrt_set_checkpointing(2)
+    if mesh:
+        ctx.hrt_set_ray_mesh(rm_cfg)
+    ctx.hrt_init_particles_zeldovich(_cuda(noise).reshape(-1), W.a_init)
+    for a in W.forward_grid[1:]:
+        ctx.hrt_step(a)
+    ctx.hrt_sync_particles()
+    ctx.hrt_init_rays(theta0.cuda())
+    slots = {s: i for i, s in enumerate(W.source_steps)}
+    for n, a in enumerate(W.reverse_grid[1:], start=1):
+        ctx.hrt_step(a, slots.get(n, -1))
+    kap_ctx = torch.stack([ctx.hrt_read_maps(i)[0] for i in range(len(W.source_steps))])
+    nb_ctx, om_ctx = ctx.hrt_adjoint(kbar.contiguous(), tb.contiguous())
+    torch.cuda.synchronize()
+    # the differentiable simulation
+    sim = autodiff.DiffSim(W, theta0, checkpoint_every=3, ray_mesh=rm_cfg)
+    w = _cuda(noise).reshape(-1).requires_grad_(True)
+    om = torch.tensor(W.omega_m, dtype=torch.float64, requires_grad=True)
+    kap, th = autodiff.HRTKappa.apply(w, om, sim)
+    ((kap.double() * kbar.double()).sum() + ((th - theta0.cuda()) * tb).sum()).backward()
+    assert float((kap_ctx - kap).abs().max()) <= 1e-4 * float(kap.abs().max())
+    g_ctx, g_sim = nb_ctx.double().cpu(), w.grad.double().cpu()
+    rel = float((g_ctx - g_sim).norm() / g_sim.norm())
+    assert rel < 1e-3, rel
+    assert om_ctx == pytest.approx(float(om.grad), rel=1e-3), (om_ctx, float(om.grad))
+    # a run that cannot be differentiated is refused with the reason
+    ctx.hrt_drift_free(1000.0, 1100.0)
+    with pytest.raises(hrt.HRTError):
+        ctx.hrt_adjoint(kbar.contiguous())
+    sim.close()
+    ctx.close()
