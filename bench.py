@@ -475,6 +475,7 @@ def next_rows(args, W, ctx, reset, grid, slots, run_steps, stream, seed):
                 row[f"{name}_max_dev_ell_le_{cut}"] = float(np.abs(ratio[e <= cut] - 1).max()) if (e <= cut).any() else None
         cmp["sources"][str(s)] = row
     out["kick_operators"] = cmp
+    out["adjoint"] = adjoint_timing(hrt, seed)
     # initial conditions on the particle lattice
     noise = torch.from_numpy(synthetic.white_noise(seed, W.n_side).astype(np.float32)).cuda().reshape(-1)
     disp = torch.empty(3, W.n_side ** 3, device="cuda")
@@ -487,6 +488,44 @@ def next_rows(args, W, ctx, reset, grid, slots, run_steps, stream, seed):
         e1.record(stream)
         torch.cuda.synchronize()
         out[f"ic_{name}_ms"] = e0.elapsed_time(e1)
+    return out
+
+
+def adjoint_timing(hrt, seed):
+    """Gradient of a kappa-map loss with respect to the white noise and Omega_m by the context's native adjoint
+    on the differentiation workload (128^3 particles, 256^3 mesh, 512^2 rays, 32 + 16 steps, checkpoint every
+    4 steps): wall-clock of the recorded forward run and of hrt_adjoint."""
+    import time
+    import numpy as np
+    import torch
+    import synthetic
+    from paper_2405_12913_gb300.configs import COSMO_GRAD_256 as G
+    cfg = hrt.make_config(G.n_mesh, G.box, G.n_side, G.omega_m, G.h, G.n_s, G.sigma8, G.deconv_p, G.smooth_cells,
+                          G.samples_per_cell, G.observer, n_sources=len(G.source_steps))
+    ctx = hrt.Context(cfg)
+    ctx.hrt_set_checkpointing(4)
+    noise = torch.from_numpy(synthetic.white_noise(seed, G.n_side).astype(np.float32)).cuda().reshape(-1)
+    theta0 = torch.from_numpy(synthetic.pixel_grid(G.n_pix, G.fov_deg * synthetic.DEGREE)).cuda()
+    kbar = torch.from_numpy(synthetic.gaussian_field(seed + 1, (len(G.source_steps), G.n_rays)).astype(np.float32)).cuda()
+    slots = {s: i for i, s in enumerate(G.source_steps)}
+    out = {"workload": G.name, "checkpoint_every": 4}
+    for rep in range(2):   # the first pass creates plans and memory pools
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.hrt_init_particles_zeldovich(noise, G.a_init)
+        for a in G.forward_grid[1:]:
+            ctx.hrt_step(a)
+        ctx.hrt_sync_particles()
+        ctx.hrt_init_rays(theta0)
+        for n, a in enumerate(G.reverse_grid[1:], start=1):
+            ctx.hrt_step(a, slots.get(n, -1))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        _, om_bar = ctx.hrt_adjoint(kbar)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        out.update({"forward_s": t1 - t0, "adjoint_s": t2 - t1, "dL_dOmega_m": om_bar})
+    ctx.close()
     return out
 
 
