@@ -488,6 +488,23 @@ def next_rows(args, W, ctx, reset, grid, slots, run_steps, stream, seed):
         e1.record(stream)
         torch.cuda.synchronize()
         out[f"ic_{name}_ms"] = e0.elapsed_time(e1)
+    # the CIC deposit: plain reductions against warp-aggregated ones, on the ICs (a_init) and on the particles
+    # at a = 1 (clustered)
+    rho = torch.empty(W.n_mesh ** 3, device="cuda")
+    hrt.hrt_ic_zeldovich(noise, W.n_side, W.box, W.omega_m, W.h, W.n_s, W.sigma8, W.a_init, disp, mom)
+    states = {"a_init": disp, "a_1": reset.state[0]}
+    dep = {}
+    for tag, d in states.items():
+        for name, fn in (("plain", hrt.hrt_cic_scatter), ("warp_aggregated", hrt.hrt_cic_scatter_warp_aggregated)):
+            times = []
+            for _ in range(5):
+                e0.record(stream)
+                fn(d, W.n_side, W.n_mesh, W.box, rho)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            dep[f"{tag}_{name}_ms"] = sorted(times)[2]
+    out["cic_deposit"] = dep
     return out
 
 

@@ -79,6 +79,13 @@ hrt_status hrt_cosmo_power_amplitude(double omega_m, double h, double n_s, doubl
 hrt_status hrt_cic_scatter(const float* disp, int64_t n_side, int64_t n, double box, float* rho,
                            void* stream);
 
+/* hrt_cic_scatter with warp-aggregated atomics: lanes of a warp whose targets coincide combine their weights
+ * (__match_any_sync) and one of them adds the sum.  The same result up to rounding; kept as the measured
+ * alternative to the plain reductions (lattice-ordered particles rarely share a target within a warp).  Needs
+ * n_side a power of two >= 32 (HRT_ERR_INVALID_ARG otherwise). */
+hrt_status hrt_cic_scatter_warp_aggregated(const float* disp, int64_t n_side, int64_t n, double box, float* rho,
+                                           void* stream);
+
 /* Fused particle update of the leapfrog (nbody_reverse_step of Alg. 1): CIC-interpolate the three gradient
  * fields grad[3][n^3] (d_x phi, d_y phi, d_z phi) at q + disp, then p -= grad phi * kick and
  * disp += p * drift.  kick and drift are the signed FP64 time integrals (K, Dr above; drift = 0 for a

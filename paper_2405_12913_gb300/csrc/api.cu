@@ -692,6 +692,14 @@ hrt_status hrt_cosmo_power_amplitude(double omega_m, double h, double n_s, doubl
   return HRT_OK;
 }
 
+hrt_status hrt_cic_scatter_warp_aggregated(const float* disp, int64_t n_side, int64_t n, double box, float* rho,
+                                           void* stream) {
+  HRT_TRY(check_mesh(n, box));
+  HRT_TRY(check_particles(n_side, n));
+  if (!disp || !rho) return fail(HRT_ERR_INVALID_ARG, "NULL buffer");
+  return launch_cic_scatter_warp(disp, n_side, n, box, rho, as_stream(stream));
+}
+
 hrt_status hrt_cic_scatter(const float* disp, int64_t n_side, int64_t n, double box, float* rho, void* stream) {
   HRT_TRY(check_mesh(n, box));
   HRT_TRY(check_particles(n_side, n));

@@ -127,6 +127,62 @@ __global__ void __launch_bounds__(256) cic_scatter_kernel(const float* __restric
   deposit_cic(rho, L.n, ix, iy, iz, fx, fy, fz, mass);
 }
 
+// The same deposit with warp-aggregated atomics, the form that pays off when many particles of a warp share a
+// target: lanes whose pair (or first cell) coincides find each other with __match_any_sync, the lowest lane
+// of each group adds the group's sum.  Kept as the measured alternative to plain reductions: in lattice (brick)
+// order few lanes of a warp share a target at 2 mesh cells per particle spacing, so the matching and the shuffles
+// cost more than the atomics they save.
+__device__ __forceinline__ void deposit_pair_warp(float* __restrict__ rho, size_t col, int iz, int jz, float w0,
+                                                  float w1) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const bool vec = (jz == iz + 1 && (iz & 1) == 0);
+  const unsigned long long addr = reinterpret_cast<unsigned long long>(rho + col + iz);
+  const unsigned grp = __match_any_sync(full, vec ? addr : (addr | (1ull << 63)));
+  float s0 = w0, s1 = w1;
+  if (__any_sync(full, __popc(grp) > 1)) {
+    for (int l = 0; l < 32; ++l) {
+      const float v0 = __shfl_sync(full, w0, l), v1 = __shfl_sync(full, w1, l);
+      if (l != lane && ((grp >> l) & 1u)) {
+        s0 += v0;
+        s1 += v1;
+      }
+    }
+  }
+  if (lane != __ffs(grp) - 1) return;
+  if (vec) {
+    atomicAdd(reinterpret_cast<float2*>(rho + col + iz), make_float2(s0, s1));
+  } else {
+    atomicAdd(rho + col + iz, s0);
+    atomicAdd(rho + col + jz, s1);
+  }
+}
+
+// Brick mode only (every warp full, as the warp intrinsics above need).
+__global__ void __launch_bounds__(256) cic_scatter_warp_kernel(const float* __restrict__ disp, int64_t np, Lattice L,
+                                                               float mass, float* __restrict__ rho) {
+  int64_t p;
+  int qi, qj, qk;
+  particle_of_thread(L, p, qi, qj, qk);
+  int ix, iy, iz;
+  float fx, fy, fz;
+  cic_axis(qi * L.ratio, __ldg(disp + p) * L.inv_cell, L.n, ix, fx);
+  cic_axis(qj * L.ratio, __ldg(disp + np + p) * L.inv_cell, L.n, iy, fy);
+  cic_axis(qk * L.ratio, __ldg(disp + 2 * np + p) * L.inv_cell, L.n, iz, fz);
+  const int n = L.n;
+  const int jx = wrap_next(ix, n), jy = wrap_next(iy, n), jz = wrap_next(iz, n);
+  const float wx0 = (1.f - fx) * mass, wx1 = fx * mass;
+  const float wy0 = 1.f - fy, wy1 = fy, wz0 = 1.f - fz, wz1 = fz;
+  const size_t c00 = static_cast<size_t>(static_cast<unsigned>(ix * n + iy)) * n;
+  const size_t c01 = static_cast<size_t>(static_cast<unsigned>(ix * n + jy)) * n;
+  const size_t c10 = static_cast<size_t>(static_cast<unsigned>(jx * n + iy)) * n;
+  const size_t c11 = static_cast<size_t>(static_cast<unsigned>(jx * n + jy)) * n;
+  deposit_pair_warp(rho, c00, iz, jz, wx0 * wy0 * wz0, wx0 * wy0 * wz1);
+  deposit_pair_warp(rho, c01, iz, jz, wx0 * wy1 * wz0, wx0 * wy1 * wz1);
+  deposit_pair_warp(rho, c10, iz, jz, wx1 * wy0 * wz0, wx1 * wy0 * wz1);
+  deposit_pair_warp(rho, c11, iz, jz, wx1 * wy1 * wz0, wx1 * wy1 * wz1);
+}
+
 static Lattice make_lattice(int64_t n_side, int64_t n, double box) {
   Lattice L{static_cast<int>(n_side), static_cast<int>(n / n_side), static_cast<int>(n), static_cast<float>(n / box),
             0, 0, 0, 0};
@@ -142,6 +198,17 @@ static Lattice make_lattice(int64_t n_side, int64_t n, double box) {
 
 static float particle_mass(int64_t n_side, int64_t n) {
   return static_cast<float>(static_cast<double>(n) * n * n / (static_cast<double>(n_side) * n_side * n_side));
+}
+
+hrt_status launch_cic_scatter_warp(const float* disp, int64_t n_side, int64_t n, double box, float* rho,
+                                   cudaStream_t s) {
+  if (!brick_ok(n_side)) return fail(HRT_ERR_INVALID_ARG, "the warp-aggregated deposit needs n_side a power of two >= 32");
+  const int64_t np = n_side * n_side * n_side;
+  HRT_CUDA(cudaMemsetAsync(rho, 0, static_cast<size_t>(n) * n * n * sizeof(float), s));
+  cic_scatter_warp_kernel<<<particle_grid(n_side, 256), 256, 0, s>>>(disp, np, make_lattice(n_side, n, box),
+                                                                     particle_mass(n_side, n), rho);
+  HRT_LAUNCHED("cic_scatter_warp_kernel");
+  return HRT_OK;
 }
 
 hrt_status launch_cic_scatter(const float* disp, int64_t n_side, int64_t n, double box, float* rho,

@@ -9,6 +9,9 @@
 
 namespace hrt {
 
+// The same deposit with warp-aggregated atomics (n_side a power of two >= 32).
+hrt_status launch_cic_scatter_warp(const float* disp, int64_t n_side, int64_t n, double box, float* rho,
+                                   cudaStream_t s);
 hrt_status launch_cic_scatter(const float* disp, int64_t n_side, int64_t n, double box, float* rho,
                               cudaStream_t s);
 

@@ -71,6 +71,7 @@ _SIGS = {
     "hrt_cosmo_a_of_chi": ([_D, _D, _P], C.c_int),
     "hrt_cosmo_power_amplitude": ([_D, _D, _D, _D, _P], C.c_int),
     "hrt_cic_scatter": ([_P, _I64, _I64, _D, _P, _P], C.c_int),
+    "hrt_cic_scatter_warp_aggregated": ([_P, _I64, _I64, _D, _P, _P], C.c_int),
     "hrt_particle_kick_drift": ([_P, _I64, _D, _I64, _P, _P, _D, _D, _P], C.c_int),
     "hrt_particle_kick_drift_deposit": ([_P, _I64, _D, _I64, _P, _P, _D, _D, _P, _P], C.c_int),
     "hrt_kspace_gradient": ([_P, _I64, _D, _D, _P, _I32, _P, _P, _I32, _P, _P], C.c_int),
@@ -238,6 +239,13 @@ def make_filter(deconv_p: float = 0.0, smooth: float = 0.0, g_table: torch.Tenso
 def hrt_cic_scatter(disp: torch.Tensor, n_side: int, n: int, box: float, rho: torch.Tensor, stream=None):
     _check(_lib.hrt_cic_scatter(_ptr(disp, torch.float32, "disp"), n_side, n, box, _ptr(rho, torch.float32, "rho"),
                                 _stream(stream)), "hrt_cic_scatter")
+
+
+def hrt_cic_scatter_warp_aggregated(disp: torch.Tensor, n_side: int, n: int, box: float, rho: torch.Tensor,
+                                    stream=None):
+    _check(_lib.hrt_cic_scatter_warp_aggregated(_ptr(disp, torch.float32, "disp"), n_side, n, box,
+                                                _ptr(rho, torch.float32, "rho"), _stream(stream)),
+           "hrt_cic_scatter_warp_aggregated")
 
 
 def hrt_particle_kick_drift(grad: torch.Tensor, n: int, box: float, n_side: int, disp: torch.Tensor,

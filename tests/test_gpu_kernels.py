@@ -432,3 +432,28 @@ def test_tiled_ray_step_with_identity_replicas_is_the_plain_step(hrt):
     short = hrt.make_geom(n, box, obs, 1.0, replicas=tuple(t[:2] for t in ident))
     with pytest.raises(hrt.HRTError):  # nodes beyond the last replica
         hrt.hrt_ray_step_tiled(b_rays, grad, short, 150.0, 300.0, 0.0, 0.3)
+
+
+def test_warp_aggregated_deposit_matches_the_plain_deposit(hrt):
+    # clustered displacements (many particles of a warp in the same cells) and scattered ones
+    n_side, n, box = 64, 128, 100.0
+    g = torch.Generator(device="cuda").manual_seed(3)
+    i = torch.arange(n_side, device="cuda", dtype=torch.float32) * (box / n_side)
+    q = torch.stack(torch.meshgrid(i, i, i, indexing="ij")).reshape(3, -1)
+    for scale in (0.3, 8.0, -1.0):
+        if scale > 0:
+            disp = (scale * torch.randn(3, n_side ** 3, generator=g, device="cuda")).contiguous()
+        else:
+            # collapse onto 8 points: most lanes of a warp share their targets
+            c = torch.floor(q / (box / 2)) * (box / 2) + box / 4
+            disp = (c - q + 0.01 * torch.randn(3, n_side ** 3, generator=g, device="cuda")).contiguous()
+        rho0 = torch.empty(n ** 3, device="cuda")
+        rho1 = torch.empty_like(rho0)
+        hrt.hrt_cic_scatter(disp, n_side, n, box, rho0)
+        hrt.hrt_cic_scatter_warp_aggregated(disp, n_side, n, box, rho1)
+        torch.cuda.synchronize()
+        assert torch.allclose(rho0, rho1, rtol=1e-5, atol=1e-5 * float(rho0.abs().max()))
+        assert abs(float(rho0.double().sum()) - n ** 3) < 1e-3 * n ** 3
+    with pytest.raises(hrt.HRTError):
+        hrt.hrt_cic_scatter_warp_aggregated(torch.zeros(3, 24 ** 3, device="cuda"), 24, 48, 100.0,
+                                            torch.empty(48 ** 3, device="cuda"))
