@@ -526,6 +526,14 @@ hrt_status hrt_raymesh_step_planes(const hrt_raymesh_config* cfg, const hrt_ray_
                                    double chi_to, double a_ref, double omega_m, int32_t* n1_host, int32_t* n2_host,
                                    double* chi_host, double* w_host, double* drift_host);
 
+/* Storage order of the context's particles: every `every` particle steps (hrt_step, hrt_step_accumulate) the
+ * context re-sorts its particles by mesh cell (a counting sort by z-row segments of 32 cells) before the
+ * kick-drift-deposit, so that neighbouring threads gather from and deposit into neighbouring cells also after
+ * clustering has spread lattice neighbours apart; 0 keeps lattice order (the default after hrt_create is 4).
+ * Only the storage order changes: every read-out (hrt_read_particles, hrt_save_state) is in lattice order.
+ * Extra device memory once sorting starts: 32 B per particle and 4 B per 32 mesh cells. */
+hrt_status hrt_set_particle_sort(hrt_ctx* ctx, int32_t every);
+
 /* Reverse mode of a whole run (the adjoint method named as future work in Sec. 7).  hrt_set_checkpointing(ctx,
  * k) with k >= 1 makes the context record the run that starts at the next hrt_init_particles_zeldovich: the
  * noise, the steps (hrt_step, hrt_step_accumulate, hrt_sync_particles), the initial ray angles

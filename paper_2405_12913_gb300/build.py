@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhrt.so")
-SOURCES = ["api.cu", "mesh_kernels.cu", "ray_kernels.cu", "cosmo.cpp", "noalloc.cu", "adjoint_kernels.cu", "mlp_kernels.cu", "xpass_kernels.cu", "raymesh.cu", "tape.cu"]
+SOURCES = ["api.cu", "mesh_kernels.cu", "ray_kernels.cu", "cosmo.cpp", "noalloc.cu", "adjoint_kernels.cu", "mlp_kernels.cu", "xpass_kernels.cu", "raymesh.cu", "tape.cu", "sort_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "--expt-relaxed-constexpr"]
 

@@ -554,6 +554,53 @@ static hrt_status ctx_mark(hrt_ctx* ctx, hrt_status s) {
   return s;
 }
 
+const int32_t* ctx_order(const hrt_ctx* ctx) { return ctx->order_cur >= 0 ? ctx->order_buf[ctx->order_cur] : nullptr; }
+
+hrt_status ctx_particles_lattice(hrt_ctx* ctx, float* disp_out, float* mom_out) {
+  const int64_t np = ctx->cfg.n_side * ctx->cfg.n_side * ctx->cfg.n_side;
+  const int32_t* order = ctx_order(ctx);
+  if (order) {
+    if (disp_out) HRT_TRY(launch_unsort(ctx->disp, order, np, disp_out, ctx->stream));
+    if (mom_out) HRT_TRY(launch_unsort(ctx->mom, order, np, mom_out, ctx->stream));
+    return HRT_OK;
+  }
+  const size_t bytes = 3 * static_cast<size_t>(np) * sizeof(float);
+  if (disp_out) HRT_CUDA(cudaMemcpyAsync(disp_out, ctx->disp, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (mom_out) HRT_CUDA(cudaMemcpyAsync(mom_out, ctx->mom, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  return HRT_OK;
+}
+
+// Re-sorts the particles by cell (counting sort by z-row segments): the storage order changes, the particles
+// do not.
+static hrt_status ctx_sort(hrt_ctx* ctx) {
+  const hrt_config& c = ctx->cfg;
+  const int64_t np = c.n_side * c.n_side * c.n_side;
+  cudaStream_t st = ctx->stream;
+  if (!ctx->disp_alt) {
+    HRT_TRY(device_alloc(reinterpret_cast<void**>(&ctx->disp_alt), 3 * np * sizeof(float), st, "sorted particles"));
+    HRT_TRY(device_alloc(reinterpret_cast<void**>(&ctx->mom_alt), 3 * np * sizeof(float), st, "sorted particles"));
+    HRT_TRY(device_alloc(reinterpret_cast<void**>(&ctx->order_buf[0]), np * sizeof(int32_t), st, "particle order"));
+    HRT_TRY(device_alloc(reinterpret_cast<void**>(&ctx->order_buf[1]), np * sizeof(int32_t), st, "particle order"));
+    HRT_TRY(device_alloc(reinterpret_cast<void**>(&ctx->sort_scratch),
+                         (particle_sort_counts(c.n_mesh) + 2 * np) * sizeof(int32_t), st, "sort scratch"));
+  }
+  const int dst = ctx->order_cur == 0 ? 1 : 0;
+  int32_t* counts = ctx->sort_scratch;
+  int32_t* keys = counts + particle_sort_counts(c.n_mesh);
+  HRT_TRY(launch_particle_sort(ctx->disp, ctx->mom, ctx_order(ctx), c.n_side, c.n_mesh, c.box, ctx->disp_alt,
+                               ctx->mom_alt, ctx->order_buf[dst], counts, keys, keys + np, st));
+  std::swap(ctx->disp, ctx->disp_alt);
+  std::swap(ctx->mom, ctx->mom_alt);
+  ctx->order_cur = dst;
+  return HRT_OK;
+}
+
+// Back to lattice order (new particles).
+static void ctx_lattice_order(hrt_ctx* ctx) {
+  ctx->order_cur = -1;
+  ctx->steps_since_sort = 0;
+}
+
 hrt_filter ctx_filter(const hrt_config& c, bool ray) {
   hrt_filter f{};
   const double cell = c.box / c.n_mesh;
@@ -595,7 +642,7 @@ static hrt_status ctx_force(hrt_ctx* ctx) {
   const hrt_config& c = ctx->cfg;
   {
     PhaseScope ps(ctx, 2);
-    HRT_TRY(launch_cic_scatter(ctx->disp, c.n_side, c.n_mesh, c.box, ctx->rho, ctx->stream));
+    HRT_TRY(launch_cic_scatter(ctx->disp, c.n_side, c.n_mesh, c.box, ctx->rho, ctx->stream, ctx_order(ctx)));
   }
   return ctx_solve(ctx);
 }
@@ -1277,6 +1324,11 @@ hrt_status hrt_destroy(hrt_ctx* ctx) {
       cudaEventDestroy(ev.second);
     }
   tape_free(ctx);
+  device_free(ctx->disp_alt, s);
+  device_free(ctx->mom_alt, s);
+  device_free(ctx->order_buf[0], s);
+  device_free(ctx->order_buf[1], s);
+  device_free(ctx->sort_scratch, s);
   hrt_pm_destroy(ctx->pm);
   hrt_raymesh_destroy(ctx->raymesh);
   device_free(ctx->disp, s);
@@ -1310,6 +1362,7 @@ hrt_status hrt_create(const hrt_config* cfg, void* stream, hrt_ctx** out) {
   hrt_ctx* ctx = new (std::nothrow) hrt_ctx();
   if (!ctx) return fail(HRT_ERR_OOM, "host allocation");
   ctx->cfg = *cfg;
+  ctx->sort_every = 4;
   ctx->stream = as_stream(stream);
   const int64_t n = cfg->n_mesh, m = n * n * n, np = cfg->n_side * cfg->n_side * cfg->n_side;
   hrt_status s = hrt_pm_create(n, cfg->box, cfg->ray_fields, stream, &ctx->pm);
@@ -1337,6 +1390,7 @@ hrt_status hrt_init_particles_zeldovich(hrt_ctx* ctx, const float* noise, double
                                   ctx->mom, ctx->stream);
   if (s == HRT_OK) s = tape_on_ics(ctx, noise, a_init);
   if (s != HRT_OK) return ctx_mark(ctx, s);
+  ctx_lattice_order(ctx);
   ctx->a = ctx->a_mom = a_init;
   ctx->have_particles = true;
   return ctx_mark(ctx, ctx_force(ctx));
@@ -1349,6 +1403,7 @@ hrt_status hrt_init_particles_2lpt(hrt_ctx* ctx, const float* noise, double a_in
   hrt_status s = hrt_ic_2lpt(noise, ctx->cfg.n_side, ctx->cfg.box, &ctx->cfg.cosmo, a_init, ctx->disp, ctx->mom,
                              ctx->stream);
   if (s != HRT_OK) return ctx_mark(ctx, s);
+  ctx_lattice_order(ctx);
   ctx->a = ctx->a_mom = a_init;
   ctx->have_particles = true;
   return ctx_mark(ctx, ctx_force(ctx));
@@ -1362,6 +1417,7 @@ hrt_status hrt_init_particles(hrt_ctx* ctx, const float* disp, const float* mom,
   hrt_status s = cuda_status(cudaMemcpyAsync(ctx->disp, disp, bytes, cudaMemcpyDeviceToDevice, ctx->stream), "copy disp");
   if (s == HRT_OK) s = cuda_status(cudaMemcpyAsync(ctx->mom, mom, bytes, cudaMemcpyDeviceToDevice, ctx->stream), "copy mom");
   if (s != HRT_OK) return ctx_mark(ctx, s);
+  ctx_lattice_order(ctx);
   ctx->a = ctx->a_mom = ctx->cfg.static_mode ? 1.0 : a;
   ctx->have_particles = true;
   return ctx_mark(ctx, ctx_force(ctx));
@@ -1444,11 +1500,17 @@ hrt_status hrt::ctx_step(hrt_ctx* ctx, double a_next, int32_t source, double wei
   }
   const double a_half = 0.5 * (ctx->a + a_next);
   const double kick = c.kick(ctx->a_mom, a_half), drift = c.drift(ctx->a, a_next);
+  if (ctx->sort_every > 0 && ++ctx->steps_since_sort >= ctx->sort_every) {
+    PhaseScope ps(ctx, 7);
+    s = ctx_sort(ctx);
+    if (s != HRT_OK) return ctx_mark(ctx, s);
+    ctx->steps_since_sort = 0;
+  }
   {
     // kick, drift and the CIC deposit of the drifted particles (the density of the next force) in one pass
     PhaseScope ps(ctx, 1);
     s = launch_kick_drift(ctx->grad, ctx->cfg.n_mesh, ctx->cfg.box, ctx->cfg.n_side, ctx->disp, ctx->mom, kick,
-                          drift, ctx->stream, ctx->rho);
+                          drift, ctx->stream, ctx->rho, ctx_order(ctx));
   }
   if (s != HRT_OK) return ctx_mark(ctx, s);
   ctx->a = a_next;
@@ -1501,7 +1563,7 @@ hrt_status hrt_sync_particles(hrt_ctx* ctx) {
   Cosmo c(ctx->cfg.cosmo.omega_m);
   HRT_TRY(ctx_mark(ctx, tape_on_step(ctx, 'S', ctx->a, -1, 1.0, false)));
   hrt_status s = launch_kick_drift(ctx->grad, ctx->cfg.n_mesh, ctx->cfg.box, ctx->cfg.n_side, ctx->disp, ctx->mom,
-                                   c.kick(ctx->a_mom, ctx->a), 0.0, ctx->stream);
+                                   c.kick(ctx->a_mom, ctx->a), 0.0, ctx->stream, nullptr, ctx_order(ctx));
   if (s == HRT_OK) ctx->a_mom = ctx->a;
   return ctx_mark(ctx, s);
 }
@@ -1552,10 +1614,7 @@ hrt_status hrt_read_maps(hrt_ctx* ctx, int32_t source, float* kappa, float* gamm
 hrt_status hrt_read_particles(hrt_ctx* ctx, float* disp, float* mom, double* a_host, double* a_mom_host) {
   HRT_TRY(ctx_guard(ctx));
   if (!ctx->have_particles) return fail(HRT_ERR_STATE, "no particles");
-  const size_t bytes = 3 * static_cast<size_t>(ctx->cfg.n_side * ctx->cfg.n_side * ctx->cfg.n_side) * sizeof(float);
-  hrt_status s = HRT_OK;
-  if (disp) s = cuda_status(cudaMemcpyAsync(disp, ctx->disp, bytes, cudaMemcpyDeviceToDevice, ctx->stream), "read disp");
-  if (s == HRT_OK && mom) s = cuda_status(cudaMemcpyAsync(mom, ctx->mom, bytes, cudaMemcpyDeviceToDevice, ctx->stream), "read mom");
+  hrt_status s = ctx_particles_lattice(ctx, disp, mom);
   if (a_host) *a_host = ctx->a;
   if (a_mom_host) *a_mom_host = ctx->a_mom;
   return ctx_mark(ctx, s);
@@ -1592,6 +1651,14 @@ hrt_status hrt_set_replicas(hrt_ctx* ctx, int32_t n, const int32_t* perm, const 
   ctx->rep_perm.assign(perm, perm + 3 * n);
   ctx->rep_sign.assign(sign, sign + 3 * n);
   ctx->rep_shift.assign(shift, shift + 3 * n);
+  return HRT_OK;
+}
+
+hrt_status hrt_set_particle_sort(hrt_ctx* ctx, int32_t every) {
+  HRT_TRY(ctx_guard(ctx));
+  if (every < 0) return fail(HRT_ERR_INVALID_ARG, "sort interval must be >= 0");
+  ctx->sort_every = every;
+  ctx->steps_since_sort = 0;
   return HRT_OK;
 }
 
@@ -1696,8 +1763,9 @@ hrt_status hrt_save_state(hrt_ctx* ctx, void* buf, size_t bytes) {
     if (s == HRT_OK && n) s = cuda_status(cudaMemcpyAsync(p, src, n, cudaMemcpyDeviceToDevice, st), "save state");
     p += n;
   };
-  put(ctx->disp, np3 * sizeof(float));
-  put(ctx->mom, np3 * sizeof(float));
+  // particles in lattice order
+  if (s == HRT_OK) s = ctx_particles_lattice(ctx, reinterpret_cast<float*>(p), reinterpret_cast<float*>(p) + np3);
+  p += 2 * np3 * sizeof(float);
   put(ctx->rays.theta, 2 * r * sizeof(double));
   put(ctx->rays.eta, 2 * r * sizeof(float));
   put(ctx->rays.A, 4 * r * sizeof(float));
@@ -1711,6 +1779,7 @@ hrt_status hrt_save_state(hrt_ctx* ctx, void* buf, size_t bytes) {
 hrt_status hrt_load_state(hrt_ctx* ctx, const void* buf, size_t bytes) {
   HRT_TRY(ctx_guard(ctx));
   tape_invalidate(ctx, "a loaded state is not differentiated");
+  ctx_lattice_order(ctx);
   if (!buf || bytes < 256) return fail(HRT_ERR_INVALID_ARG, "state buffer is NULL or too small");
   StateHeader h{};
   cudaStream_t st = ctx->stream;

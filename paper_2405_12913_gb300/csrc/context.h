@@ -82,6 +82,15 @@ struct hrt_ctx {
   hrt_raymesh* raymesh = nullptr;
   // record of the run for hrt_adjoint (NULL: not recording)
   hrt::Tape* tape = nullptr;
+  // particles stored in cell order, re-sorted every sort_every particle steps (0: never): slot i of disp and mom
+  // holds lattice particle order_buf[order_cur][i] (order_cur < 0: lattice order)
+  int32_t* order_buf[2] = {nullptr, nullptr};
+  int order_cur = -1;
+  float* disp_alt = nullptr;
+  float* mom_alt = nullptr;
+  int32_t* sort_scratch = nullptr;
+  int32_t sort_every = 0;
+  int32_t steps_since_sort = 0;
   // fixed learned table of the ray fields (NULL: none); exclusive with the network above
   float* ray_table = nullptr;
   int32_t ray_table_nk = 0;
@@ -91,6 +100,10 @@ struct hrt_ctx {
 namespace hrt {
 
 hrt_filter ctx_filter(const hrt_config& c, bool ray);
+// The slot -> lattice index map of the context's particles (nullptr: lattice order).
+const int32_t* ctx_order(const hrt_ctx* ctx);
+// The context's particles in lattice order into disp_out, mom_out ([3][np] device, either may be NULL).
+hrt_status ctx_particles_lattice(hrt_ctx* ctx, float* disp_out, float* mom_out);
 hrt_ray_geom ctx_geom(const hrt_config& c, const hrt_ctx* ctx);
 
 // Recording hooks (tape.cu); each is a no-op without a tape.

@@ -40,6 +40,9 @@ struct Lattice {
   float inv_cell;
   int brick_mode;
   int lbx, lby, lbz;  // log2 of the brick counts per axis (brick mode)
+  // particles stored in cell order: slot i holds lattice particle order[i] (nullptr: lattice order)
+  const int32_t* order;
+  int64_t n_particles;
 };
 
 __device__ __forceinline__ void morton_decode(unsigned code, int lbx, int lby, int lbz, int& bx, int& by, int& bz) {
@@ -54,6 +57,18 @@ __device__ __forceinline__ void morton_decode(unsigned code, int lbx, int lby, i
 }
 
 __device__ __forceinline__ bool particle_of_thread(const Lattice& L, int64_t& p, int& qi, int& qj, int& qk) {
+  if (L.order) {
+    // one thread per storage slot; the lattice site comes from the slot's particle index
+    p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (p >= L.n_particles) return false;
+    const unsigned lag = static_cast<unsigned>(__ldg(L.order + p));
+    const unsigned ns = static_cast<unsigned>(L.n_side);
+    qk = static_cast<int>(lag % ns);
+    const unsigned row = lag / ns;
+    qj = static_cast<int>(row % ns);
+    qi = static_cast<int>(row / ns);
+    return true;
+  }
   if (L.brick_mode) {
     int bx, by, bz;
     morton_decode(blockIdx.x, L.lbx, L.lby, L.lbz, bx, by, bz);
@@ -80,7 +95,8 @@ static inline int ilog2_exact(int64_t v) {
 
 static inline bool brick_ok(int64_t n_side) { return n_side >= 32 && ilog2_exact(n_side) >= 0; }
 
-static inline dim3 particle_grid(int64_t n_side, int threads) {
+static inline dim3 particle_grid(int64_t n_side, int threads, const int32_t* order = nullptr) {
+  if (order) return dim3(static_cast<unsigned>((n_side * n_side * n_side + threads - 1) / threads), 1);
   if (brick_ok(n_side) && threads == 256) return dim3(static_cast<unsigned>(n_side * n_side * n_side / 256), 1);
   return dim3(static_cast<unsigned>(n_side * n_side), static_cast<unsigned>((n_side + threads - 1) / threads));
 }
@@ -183,9 +199,9 @@ __global__ void __launch_bounds__(256) cic_scatter_warp_kernel(const float* __re
   deposit_pair_warp(rho, c11, iz, jz, wx1 * wy1 * wz0, wx1 * wy1 * wz1);
 }
 
-static Lattice make_lattice(int64_t n_side, int64_t n, double box) {
+static Lattice make_lattice(int64_t n_side, int64_t n, double box, const int32_t* order = nullptr) {
   Lattice L{static_cast<int>(n_side), static_cast<int>(n / n_side), static_cast<int>(n), static_cast<float>(n / box),
-            0, 0, 0, 0};
+            0, 0, 0, 0, order, n_side * n_side * n_side};
   if (brick_ok(n_side)) {
     const int l = ilog2_exact(n_side);
     L.brick_mode = 1;
@@ -212,13 +228,13 @@ hrt_status launch_cic_scatter_warp(const float* disp, int64_t n_side, int64_t n,
 }
 
 hrt_status launch_cic_scatter(const float* disp, int64_t n_side, int64_t n, double box, float* rho,
-                              cudaStream_t s) {
+                              cudaStream_t s, const int32_t* order) {
   int64_t np = n_side * n_side * n_side;
   size_t mesh_bytes = static_cast<size_t>(n) * n * n * sizeof(float);
   HRT_CUDA(cudaMemsetAsync(rho, 0, mesh_bytes, s));
   if (np == 0) return HRT_OK;
-  cic_scatter_kernel<<<particle_grid(n_side, 256), 256, 0, s>>>(disp, np, make_lattice(n_side, n, box),
-                                                                particle_mass(n_side, n), rho);
+  cic_scatter_kernel<<<particle_grid(n_side, 256, order), 256, 0, s>>>(disp, np, make_lattice(n_side, n, box, order),
+                                                                       particle_mass(n_side, n), rho);
   HRT_LAUNCHED("cic_scatter_kernel");
   return HRT_OK;
 }
@@ -432,13 +448,13 @@ __global__ void __launch_bounds__(256) kick_drift_kernel(const float* __restrict
 }
 
 hrt_status launch_kick_drift(const float* grad, int64_t n, double box, int64_t n_side, float* disp, float* mom,
-                             double kick, double drift, cudaStream_t s, float* rho_out) {
+                             double kick, double drift, cudaStream_t s, float* rho_out, const int32_t* order) {
   int64_t np = n_side * n_side * n_side;
   int64_t m = n * n * n;
   if (rho_out) HRT_CUDA(cudaMemsetAsync(rho_out, 0, static_cast<size_t>(m) * sizeof(float), s));
   if (np == 0) return HRT_OK;
-  const Lattice L = make_lattice(n_side, n, box);
-  const dim3 grid = particle_grid(n_side, 256);
+  const Lattice L = make_lattice(n_side, n, box, order);
+  const dim3 grid = particle_grid(n_side, 256, order);
   if (rho_out) {
     kick_drift_kernel<true><<<grid, 256, 0, s>>>(grad, grad + m, grad + 2 * m, L, np, disp, mom,
                                                  static_cast<float>(kick), static_cast<float>(drift),

@@ -1,4 +1,5 @@
-// Launch wrappers of the mesh kernels (mesh_kernels.cu) and the ray kernels (ray_kernels.cu).
+// Launch wrappers of the mesh kernels (mesh_kernels.cu), the particle sort (sort_kernels.cu) and the ray kernels
+// (ray_kernels.cu).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -12,8 +13,21 @@ namespace hrt {
 // The same deposit with warp-aggregated atomics (n_side a power of two >= 32).
 hrt_status launch_cic_scatter_warp(const float* disp, int64_t n_side, int64_t n, double box, float* rho,
                                    cudaStream_t s);
+// order (or nullptr): particles stored in cell order, slot i holding lattice particle order[i].
 hrt_status launch_cic_scatter(const float* disp, int64_t n_side, int64_t n, double box, float* rho,
-                              cudaStream_t s);
+                              cudaStream_t s, const int32_t* order = nullptr);
+
+// Counting sort of the particles by z-row segments of 32 mesh cells (row-major): slot i of the output holds the
+// particle that the key order puts there; disp, mom are [3][np] in slot order, order the slot -> lattice index
+// map (nullptr: lattice order, read in the rows-of-sites order).  Writes disp_out, mom_out, order_out; counts
+// (n^3 / 32 + 1 ints) and keys, ranks (np ints each) are scratch.
+hrt_status launch_particle_sort(const float* disp, const float* mom, const int32_t* order, int64_t n_side, int64_t n,
+                                double box, float* disp_out, float* mom_out, int32_t* order_out, int32_t* counts,
+                                int32_t* keys, int32_t* ranks, cudaStream_t s);
+// Size (ints) of the counts scratch of launch_particle_sort for mesh side n.
+int64_t particle_sort_counts(int64_t n);
+// Slot order back to lattice order: out[:, order[i]] = in[:, i] for [3][np] arrays.
+hrt_status launch_unsort(const float* in, const int32_t* order, int64_t np, float* out, cudaStream_t s);
 
 void filter_tables(int64_t n, double box, const hrt_filter& f, std::vector<float>& wxy, std::vector<float>& wz);
 
@@ -28,7 +42,8 @@ struct KspaceCallbackInfo;
 hrt_status launch_set_callback_info(KspaceCallbackInfo* dst, const KspaceCallbackInfo& v, cudaStream_t s);
 
 hrt_status launch_kick_drift(const float* grad, int64_t n, double box, int64_t n_side, float* disp, float* mom,
-                             double kick, double drift, cudaStream_t s, float* rho_out = nullptr);
+                             double kick, double drift, cudaStream_t s, float* rho_out = nullptr,
+                             const int32_t* order = nullptr);
 
 hrt_status launch_ic_kspace(const void* w_hat, int64_t n, double box, const float* table, void* out,
                             cudaStream_t s);

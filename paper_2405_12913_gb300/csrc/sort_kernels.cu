@@ -1,0 +1,185 @@
+// Counting sort of the particles by mesh cell (z-row segments of 32 cells, row-major), so that a warp's
+// particles gather from and deposit into neighbouring cells also after clustering has scattered lattice
+// neighbours over many lines.  The particles keep their Lagrangian displacements; a slot -> lattice index map
+// (order) says which lattice site each storage slot holds.
+//
+// key(i) = (ix n + iy) ceil(n / 32) + iz / 32 of the cell the particle in slot i sits in; its rank within the
+// key comes from an atomic counter, the key offsets from an exclusive scan of the counters (three passes: block
+// sums, one-block scan of the block sums, block scans plus offsets), and a scatter moves displacements,
+// momenta and the lattice index to offset + rank.  The order within a key depends on the atomics.
+#include <cuda_runtime.h>
+
+#include "common.h"
+#include "mesh_kernels.h"
+
+namespace hrt {
+
+namespace {
+
+constexpr int kSeg = 32;           // cells per key along z
+constexpr int kScanThreads = 256;  // threads per scan block, 4 counters each
+constexpr int kScanItems = 4 * kScanThreads;
+
+__device__ __forceinline__ int cell_of(int q_node, float d_cells, int n) {
+  int i = q_node + static_cast<int>(floorf(d_cells));
+  if (static_cast<unsigned>(i) >= static_cast<unsigned>(n)) {
+    i %= n;
+    if (i < 0) i += n;
+  }
+  return i;
+}
+
+__global__ void sort_key_kernel(const float* __restrict__ disp, const int32_t* __restrict__ order, int64_t np,
+                                int n_side, int ratio, int n, int nseg, float inv_cell, int32_t* __restrict__ counts,
+                                int32_t* __restrict__ keys, int32_t* __restrict__ ranks) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= np) return;
+  const unsigned lag = order ? static_cast<unsigned>(__ldg(order + i)) : static_cast<unsigned>(i);
+  const unsigned ns = static_cast<unsigned>(n_side);
+  const int qk = static_cast<int>(lag % ns), qj = static_cast<int>((lag / ns) % ns), qi = static_cast<int>(lag / ns / ns);
+  const int ix = cell_of(qi * ratio, __ldg(disp + i) * inv_cell, n);
+  const int iy = cell_of(qj * ratio, __ldg(disp + np + i) * inv_cell, n);
+  const int iz = cell_of(qk * ratio, __ldg(disp + 2 * np + i) * inv_cell, n);
+  const int32_t key = (ix * n + iy) * nseg + iz / kSeg;
+  keys[i] = key;
+  ranks[i] = atomicAdd(counts + key, 1);
+}
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* sh, int& total) {
+  // warp-level inclusive scan, then the warp totals
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    int w = lane < nw ? sh[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) sh[lane] = w;
+  }
+  __syncthreads();
+  total = sh[(blockDim.x >> 5) - 1];
+  const int before = (warp > 0 ? sh[warp - 1] : 0) + x - v;
+  __syncthreads();
+  return before;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(const int32_t* __restrict__ counts, int64_t T,
+                                                                 int32_t* __restrict__ block_sums) {
+  __shared__ int sh[32];
+  const int64_t base = blockIdx.x * static_cast<int64_t>(kScanItems) + 4 * threadIdx.x;
+  int v = 0;
+  for (int k = 0; k < 4; ++k)
+    if (base + k < T) v += counts[base + k];
+  int total;
+  block_exclusive_scan(v, sh, total);
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// One block: exclusive scan of the block sums in place (each thread a contiguous chunk).
+__global__ void __launch_bounds__(1024) scan_block_sums_kernel(int32_t* __restrict__ sums, int nb) {
+  __shared__ int sh[32];
+  const int chunk = (nb + blockDim.x - 1) / blockDim.x;
+  const int lo = threadIdx.x * chunk, hi = min(nb, lo + chunk);
+  int v = 0;
+  for (int i = lo; i < hi; ++i) v += sums[i];
+  int total;
+  int run = block_exclusive_scan(v, sh, total);
+  for (int i = lo; i < hi; ++i) {
+    const int c = sums[i];
+    sums[i] = run;
+    run += c;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(int32_t* __restrict__ counts, int64_t T,
+                                                                  const int32_t* __restrict__ block_sums) {
+  __shared__ int sh[32];
+  const int64_t base = blockIdx.x * static_cast<int64_t>(kScanItems) + 4 * threadIdx.x;
+  int c[4], v = 0;
+  for (int k = 0; k < 4; ++k) {
+    c[k] = base + k < T ? counts[base + k] : 0;
+    v += c[k];
+  }
+  int total;
+  int run = block_exclusive_scan(v, sh, total) + block_sums[blockIdx.x];
+  for (int k = 0; k < 4; ++k)
+    if (base + k < T) {
+      counts[base + k] = run;
+      run += c[k];
+    }
+}
+
+__global__ void sort_scatter_kernel(const float* __restrict__ disp, const float* __restrict__ mom,
+                                    const int32_t* __restrict__ order, int64_t np, const int32_t* __restrict__ offsets,
+                                    const int32_t* __restrict__ keys, const int32_t* __restrict__ ranks,
+                                    float* __restrict__ disp_out, float* __restrict__ mom_out,
+                                    int32_t* __restrict__ order_out) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= np) return;
+  const int64_t d = static_cast<int64_t>(offsets[keys[i]]) + ranks[i];
+  for (int c = 0; c < 3; ++c) {
+    disp_out[c * np + d] = disp[c * np + i];
+    mom_out[c * np + d] = mom[c * np + i];
+  }
+  order_out[d] = order ? order[i] : static_cast<int32_t>(i);
+}
+
+__global__ void unsort_kernel(const float* __restrict__ in, const int32_t* __restrict__ order, int64_t np,
+                              float* __restrict__ out) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= np) return;
+  const int64_t p = order[i];
+  for (int c = 0; c < 3; ++c) out[c * np + p] = in[c * np + i];
+}
+
+}  // namespace
+
+hrt_status launch_particle_sort(const float* disp, const float* mom, const int32_t* order, int64_t n_side, int64_t n,
+                                double box, float* disp_out, float* mom_out, int32_t* order_out, int32_t* counts,
+                                int32_t* keys, int32_t* ranks, cudaStream_t s) {
+  const int64_t np = n_side * n_side * n_side;
+  if (np == 0) return HRT_OK;
+  if (np > INT32_MAX) return fail(HRT_ERR_INVALID_ARG, "too many particles for the sort");
+  const int nseg = static_cast<int>((n + kSeg - 1) / kSeg);
+  const int64_t T = n * n * nseg;
+  const int64_t nb = (T + kScanItems - 1) / kScanItems;
+  // counters, then the block sums after them
+  HRT_CUDA(cudaMemsetAsync(counts, 0, static_cast<size_t>(T) * sizeof(int32_t), s));
+  sort_key_kernel<<<blocks_for(np, 256), 256, 0, s>>>(disp, order, np, static_cast<int>(n_side),
+                                                      static_cast<int>(n / n_side), static_cast<int>(n), nseg,
+                                                      static_cast<float>(n / box), counts, keys, ranks);
+  HRT_LAUNCHED("sort_key_kernel");
+  int32_t* sums = counts + T;
+  scan_sums_kernel<<<static_cast<unsigned>(nb), kScanThreads, 0, s>>>(counts, T, sums);
+  HRT_LAUNCHED("scan_sums_kernel");
+  scan_block_sums_kernel<<<1, 1024, 0, s>>>(sums, static_cast<int>(nb));
+  HRT_LAUNCHED("scan_block_sums_kernel");
+  scan_apply_kernel<<<static_cast<unsigned>(nb), kScanThreads, 0, s>>>(counts, T, sums);
+  HRT_LAUNCHED("scan_apply_kernel");
+  sort_scatter_kernel<<<blocks_for(np, 256), 256, 0, s>>>(disp, mom, order, np, counts, keys, ranks, disp_out, mom_out,
+                                                          order_out);
+  HRT_LAUNCHED("sort_scatter_kernel");
+  return HRT_OK;
+}
+
+int64_t particle_sort_counts(int64_t n) {
+  const int64_t T = n * n * ((n + kSeg - 1) / kSeg);
+  return T + (T + kScanItems - 1) / kScanItems;
+}
+
+hrt_status launch_unsort(const float* in, const int32_t* order, int64_t np, float* out, cudaStream_t s) {
+  if (np == 0) return HRT_OK;
+  unsort_kernel<<<blocks_for(np, 256), 256, 0, s>>>(in, order, np, out);
+  HRT_LAUNCHED("unsort_kernel");
+  return HRT_OK;
+}
+
+}  // namespace hrt

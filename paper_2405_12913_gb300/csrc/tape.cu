@@ -173,8 +173,7 @@ hrt_status tape_on_step(hrt_ctx* ctx, char kind, double a_next, int slot, double
     TapeCheckpoint c;
     hrt_status st = device_alloc(reinterpret_cast<void**>(&c.disp), np3 * sizeof(float), s, "checkpoint");
     if (st == HRT_OK) st = device_alloc(reinterpret_cast<void**>(&c.mom), np3 * sizeof(float), s, "checkpoint");
-    if (st == HRT_OK) st = copy_floats(c.disp, ctx->disp, np3, s);
-    if (st == HRT_OK) st = copy_floats(c.mom, ctx->mom, np3, s);
+    if (st == HRT_OK) st = ctx_particles_lattice(ctx, c.disp, c.mom);
     if (st == HRT_OK && t.rays_start >= 0 && idx >= t.rays_start) {
       st = alloc_rays(c.rays, t.n_rays, s);
       if (st == HRT_OK) st = copy_rays(c.rays, ctx->rays, s);

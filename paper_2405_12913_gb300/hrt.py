@@ -97,6 +97,7 @@ _SIGS = {
     "hrt_raymesh_ray_step_tiled": ([_P, _P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
     "hrt_set_ray_mesh": ([_P, _P], C.c_int),
     "hrt_set_checkpointing": ([_P, _I32], C.c_int),
+    "hrt_set_particle_sort": ([_P, _I32], C.c_int),
     "hrt_adjoint": ([_P, _P, _P, _P, _P], C.c_int),
     "hrt_ray_drift_free": ([_P, _D, _D, _P], C.c_int),
     "hrt_ray_readout": ([_P, _P, _P], C.c_int),
@@ -726,6 +727,10 @@ class Context:
         _check(_lib.hrt_set_replicas(self._h, t[0].shape[0], t[0].ctypes.data, t[1].ctypes.data, t[2].ctypes.data),
                "hrt_set_replicas")
 
+    def hrt_set_particle_sort(self, every: int):
+        """Re-sort the particles by mesh cell every `every` particle steps (0: keep lattice order)."""
+        _check(_lib.hrt_set_particle_sort(self._h, every), "hrt_set_particle_sort")
+
     def hrt_set_checkpointing(self, every: int):
         """Record the run from the next Zel'dovich ICs for hrt_adjoint (checkpoint every `every` steps; 0: off)."""
         _check(_lib.hrt_set_checkpointing(self._h, every), "hrt_set_checkpointing")
@@ -816,7 +821,7 @@ class Context:
                                         p.data_ptr(), cnt.data_ptr()), "hrt_ctx_kappa_power")
         return ell.numpy(), p.numpy(), cnt.numpy()
 
-    PHASES = ("ray_step", "kick_drift", "cic_scatter", "fft_r2c", "kspace", "fft_c2r", "step", "unused")
+    PHASES = ("ray_step", "kick_drift", "cic_scatter", "fft_r2c", "kspace", "fft_c2r", "step", "particle_sort")
 
     def hrt_ctx_set_profiling(self, on: bool):
         _check(_lib.hrt_ctx_set_profiling(self._h, int(on)), "hrt_ctx_set_profiling")
@@ -825,7 +830,7 @@ class Context:
         ms = (C.c_double * 8)()
         cnt = (C.c_int64 * 8)()
         _check(_lib.hrt_ctx_phase_times(self._h, ms, cnt), "hrt_ctx_phase_times")
-        return {name: (ms[i], cnt[i]) for i, name in enumerate(self.PHASES[:7])}
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(self.PHASES)}
 
     def hrt_ctx_rays(self) -> hrt_rays:
         r = hrt_rays()

@@ -282,3 +282,38 @@ def test_tiled_light_cone_run_matches_oracle(hrt):
     with pytest.raises(hrt.HRTError):
         ctx2.hrt_set_replicas(reps)
     ctx2.close()
+
+
+def test_particle_sort_leaves_the_run_unchanged(hrt):
+    # the cell-order storage of the particles (re-sorted every step here) against lattice order: the same run up
+    # to the rounding order of the deposit
+    from paper_2405_12913_gb300.configs import COSMO_TINY as W
+    noise = synthetic.white_noise(W.seed, W.n_side)
+    theta0 = synthetic.pixel_grid(W.n_pix, W.fov_deg * synthetic.DEGREE)
+    out = []
+    for every in (0, 1, 3):
+        cfg = hrt.make_config(W.n_mesh, W.box, W.n_side, W.omega_m, W.h, W.n_s, W.sigma8, W.deconv_p, W.smooth_cells,
+                              W.samples_per_cell, W.observer, n_sources=len(W.source_steps))
+        ctx = hrt.Context(cfg)
+        ctx.hrt_set_particle_sort(every)
+        ctx.hrt_init_particles_zeldovich(torch.tensor(noise, dtype=torch.float32, device="cuda"), W.a_init)
+        for a in W.forward_grid[1:]:
+            ctx.hrt_step(a)
+        ctx.hrt_sync_particles()
+        ctx.hrt_init_rays(torch.tensor(theta0, device="cuda"))
+        for n, a in enumerate(W.reverse_grid[1:], start=1):
+            ctx.hrt_step(a, 0 if n == W.n_reverse else -1)
+        d, m, _, _ = ctx.hrt_read_particles()
+        k = ctx.hrt_read_maps(0)[0]
+        # a saved state holds lattice order too
+        buf = ctx.hrt_save_state()
+        np3 = 3 * W.n_side ** 3
+        saved = buf[256:256 + 4 * np3].view(torch.float32)
+        out.append((d.cpu().double(), m.cpu().double(), k.cpu().double(), saved.cpu().double()))
+        ctx.close()
+    cell = W.box / W.n_mesh
+    for d, m, k, saved in out[1:]:
+        assert float((d - out[0][0]).abs().max()) < 1e-4 * cell
+        assert float((m - out[0][1]).abs().max()) < 1e-4 * float(out[0][1].abs().max())
+        assert float((k - out[0][2]).abs().max()) < 1e-3 * float(out[0][2].std())
+        assert torch.equal(saved, d.reshape(-1))
