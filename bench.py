@@ -50,6 +50,8 @@ def parse():
                    help="skip the timings of the widened rows (tiled light cone, accumulated sources, 2LPT ICs)")
     p.add_argument("--no-learned", action="store_true",
                    help="skip the learned-correction comparison (coarse learned vs coarse plain vs fine plain)")
+    p.add_argument("--sort-every", type=int, default=None,
+                   help="re-sort the particles by mesh cell every K particle steps (default: the library's, 4; 0: never)")
     p.add_argument("--kick", default="direct", choices=["direct", "mesh"],
                    help="kick operator of the rays: the direct line-of-sight gather or the ray mesh of Sec. 5.2")
     return p.parse_args()
@@ -221,6 +223,8 @@ def run_gpu(args, W, world, rank, local):
     cfg = hrt.make_config(W.n_mesh, W.box, W.n_side, W.omega_m, W.h, W.n_s, W.sigma8, W.deconv_p, W.smooth_cells,
                           W.samples_per_cell, W.observer, n_sources=len(W.source_steps))
     ctx = hrt.Context(cfg)
+    if args.sort_every is not None:
+        ctx.hrt_set_particle_sort(args.sort_every)
     noise = torch.from_numpy(synthetic.white_noise(seed, W.n_side).astype(np.float32)).to(dev)
     theta0_h = torch.from_numpy(synthetic.pixel_grid(W.n_pix, W.fov_deg * synthetic.DEGREE))
     theta0 = theta0_h.to(dev)
@@ -239,9 +243,14 @@ def run_gpu(args, W, world, rank, local):
         ctx.hrt_set_ray_mesh(raymesh_config(hrt, W))
         ray_launches = 5
 
+    # the context re-sorts its particles every sort_every particle steps after new particles (5 own launches)
+    sort_every = 4 if args.sort_every is None else args.sort_every
+    since_sort = [0]
+
     def reset():
         ctx.hrt_init_particles(disp0, mom0, 1.0)
         ctx.hrt_init_rays(theta0)
+        since_sort[0] = 0
 
     reset.state = (disp0, mom0, theta0)
 
@@ -257,6 +266,10 @@ def run_gpu(args, W, world, rank, local):
             n = pos + 1
             ctx.hrt_step(grid[n], slots.get(n, -1))
             launches += 2 + ray_launches  # ray step, kick-drift-deposit, k-space pass (x-pass on the split path)
+            since_sort[0] += 1
+            if sort_every > 0 and since_sort[0] >= sort_every:
+                launches += 5  # cell keys, three scan passes, scatter
+                since_sort[0] = 0
             pos = n
         return pos, launches
 
@@ -358,6 +371,7 @@ def run_gpu(args, W, world, rank, local):
         "config": {"workload": W.name, "n_particles": W.n_side ** 3, "n_mesh": W.n_mesh, "box_mpc_h": W.box,
                    "n_rays": W.n_rays, "fov_deg": W.fov_deg, "reverse_steps": W.n_reverse,
                    "timed_steps_start_at_a": 1.0, "parallelism": f"replicas{world}",
+                   "particle_sort_every": sort_every,
                    "kick": ("ray mesh (iota %g, p_min %g)" % (RAYMESH_IOTA, RAYMESH_P_MIN)
                             if args.kick == "mesh" else "direct line-of-sight gather"),
                    "l2": "inputs larger than L2 (%.2g GB mesh per field)" % (W.n_mesh ** 3 * 4 / 1e9)},
