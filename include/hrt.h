@@ -531,7 +531,7 @@ hrt_status hrt_raymesh_step_planes(const hrt_raymesh_config* cfg, const hrt_ray_
  * kick-drift-deposit, so that neighbouring threads gather from and deposit into neighbouring cells also after
  * clustering has spread lattice neighbours apart; 0 keeps lattice order (the default after hrt_create is 4).
  * Only the storage order changes: every read-out (hrt_read_particles, hrt_save_state) is in lattice order.
- * Extra device memory once sorting starts: 32 B per particle and 4 B per 32 mesh cells. */
+ * Extra device memory once sorting starts: 44 B per particle and 4 B per 32 mesh cells. */
 hrt_status hrt_set_particle_sort(hrt_ctx* ctx, int32_t every);
 
 /* Reverse mode of a whole run (the adjoint method named as future work in Sec. 7).  hrt_set_checkpointing(ctx,

@@ -582,13 +582,13 @@ static hrt_status ctx_sort(hrt_ctx* ctx) {
     HRT_TRY(device_alloc(reinterpret_cast<void**>(&ctx->order_buf[0]), np * sizeof(int32_t), st, "particle order"));
     HRT_TRY(device_alloc(reinterpret_cast<void**>(&ctx->order_buf[1]), np * sizeof(int32_t), st, "particle order"));
     HRT_TRY(device_alloc(reinterpret_cast<void**>(&ctx->sort_scratch),
-                         (particle_sort_counts(c.n_mesh) + 2 * np) * sizeof(int32_t), st, "sort scratch"));
+                         (particle_sort_counts(c.n_mesh) + 3 * np) * sizeof(int32_t), st, "sort scratch"));
   }
   const int dst = ctx->order_cur == 0 ? 1 : 0;
   int32_t* counts = ctx->sort_scratch;
   int32_t* keys = counts + particle_sort_counts(c.n_mesh);
   HRT_TRY(launch_particle_sort(ctx->disp, ctx->mom, ctx_order(ctx), c.n_side, c.n_mesh, c.box, ctx->disp_alt,
-                               ctx->mom_alt, ctx->order_buf[dst], counts, keys, keys + np, st));
+                               ctx->mom_alt, ctx->order_buf[dst], counts, keys, keys + np, keys + 2 * np, st));
   std::swap(ctx->disp, ctx->disp_alt);
   std::swap(ctx->mom, ctx->mom_alt);
   ctx->order_cur = dst;

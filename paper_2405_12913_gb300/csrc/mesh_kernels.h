@@ -20,10 +20,10 @@ hrt_status launch_cic_scatter(const float* disp, int64_t n_side, int64_t n, doub
 // Counting sort of the particles by z-row segments of 32 mesh cells (row-major): slot i of the output holds the
 // particle that the key order puts there; disp, mom are [3][np] in slot order, order the slot -> lattice index
 // map (nullptr: lattice order, read in the rows-of-sites order).  Writes disp_out, mom_out, order_out; counts
-// (n^3 / 32 + 1 ints) and keys, ranks (np ints each) are scratch.
+// (particle_sort_counts(n) ints) and keys, ranks, src (np ints each) are scratch.
 hrt_status launch_particle_sort(const float* disp, const float* mom, const int32_t* order, int64_t n_side, int64_t n,
                                 double box, float* disp_out, float* mom_out, int32_t* order_out, int32_t* counts,
-                                int32_t* keys, int32_t* ranks, cudaStream_t s);
+                                int32_t* keys, int32_t* ranks, int32_t* src, cudaStream_t s);
 // Size (ints) of the counts scratch of launch_particle_sort for mesh side n.
 int64_t particle_sort_counts(int64_t n);
 // Slot order back to lattice order: out[:, order[i]] = in[:, i] for [3][np] arrays.

@@ -5,8 +5,9 @@
 //
 // key(i) = (ix n + iy) ceil(n / 32) + iz / 32 of the cell the particle in slot i sits in; its rank within the
 // key comes from an atomic counter, the key offsets from an exclusive scan of the counters (three passes: block
-// sums, one-block scan of the block sums, block scans plus offsets), and a scatter moves displacements,
-// momenta and the lattice index to offset + rank.  The order within a key depends on the atomics.
+// sums, one-block scan of the block sums, block scans plus offsets).  Each destination offset + rank then learns
+// its source slot, and a gather moves displacements, momenta and the lattice index there (coalesced writes).
+// The order within a key depends on the atomics.
 #include <cuda_runtime.h>
 
 #include "common.h"
@@ -117,19 +118,27 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(int32_t* __res
     }
 }
 
-__global__ void sort_scatter_kernel(const float* __restrict__ disp, const float* __restrict__ mom,
-                                    const int32_t* __restrict__ order, int64_t np, const int32_t* __restrict__ offsets,
-                                    const int32_t* __restrict__ keys, const int32_t* __restrict__ ranks,
-                                    float* __restrict__ disp_out, float* __restrict__ mom_out,
-                                    int32_t* __restrict__ order_out) {
+// Destination slot of every particle, stored as the source of every destination (a 4-byte scattered write per
+// particle), so that the move below writes its six arrays coalesced and reads them scattered.
+__global__ void sort_invert_kernel(int64_t np, const int32_t* __restrict__ offsets, const int32_t* __restrict__ keys,
+                                   const int32_t* __restrict__ ranks, int32_t* __restrict__ src) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= np) return;
-  const int64_t d = static_cast<int64_t>(offsets[keys[i]]) + ranks[i];
+  src[static_cast<int64_t>(offsets[keys[i]]) + ranks[i]] = static_cast<int32_t>(i);
+}
+
+__global__ void sort_gather_kernel(const float* __restrict__ disp, const float* __restrict__ mom,
+                                   const int32_t* __restrict__ order, int64_t np, const int32_t* __restrict__ src,
+                                   float* __restrict__ disp_out, float* __restrict__ mom_out,
+                                   int32_t* __restrict__ order_out) {
+  const int64_t d = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (d >= np) return;
+  const int64_t i = src[d];
   for (int c = 0; c < 3; ++c) {
-    disp_out[c * np + d] = disp[c * np + i];
-    mom_out[c * np + d] = mom[c * np + i];
+    disp_out[c * np + d] = __ldg(disp + c * np + i);
+    mom_out[c * np + d] = __ldg(mom + c * np + i);
   }
-  order_out[d] = order ? order[i] : static_cast<int32_t>(i);
+  order_out[d] = order ? __ldg(order + i) : static_cast<int32_t>(i);
 }
 
 __global__ void unsort_kernel(const float* __restrict__ in, const int32_t* __restrict__ order, int64_t np,
@@ -144,7 +153,7 @@ __global__ void unsort_kernel(const float* __restrict__ in, const int32_t* __res
 
 hrt_status launch_particle_sort(const float* disp, const float* mom, const int32_t* order, int64_t n_side, int64_t n,
                                 double box, float* disp_out, float* mom_out, int32_t* order_out, int32_t* counts,
-                                int32_t* keys, int32_t* ranks, cudaStream_t s) {
+                                int32_t* keys, int32_t* ranks, int32_t* src, cudaStream_t s) {
   const int64_t np = n_side * n_side * n_side;
   if (np == 0) return HRT_OK;
   if (np > INT32_MAX) return fail(HRT_ERR_INVALID_ARG, "too many particles for the sort");
@@ -164,9 +173,10 @@ hrt_status launch_particle_sort(const float* disp, const float* mom, const int32
   HRT_LAUNCHED("scan_block_sums_kernel");
   scan_apply_kernel<<<static_cast<unsigned>(nb), kScanThreads, 0, s>>>(counts, T, sums);
   HRT_LAUNCHED("scan_apply_kernel");
-  sort_scatter_kernel<<<blocks_for(np, 256), 256, 0, s>>>(disp, mom, order, np, counts, keys, ranks, disp_out, mom_out,
-                                                          order_out);
-  HRT_LAUNCHED("sort_scatter_kernel");
+  sort_invert_kernel<<<blocks_for(np, 256), 256, 0, s>>>(np, counts, keys, ranks, src);
+  HRT_LAUNCHED("sort_invert_kernel");
+  sort_gather_kernel<<<blocks_for(np, 256), 256, 0, s>>>(disp, mom, order, np, src, disp_out, mom_out, order_out);
+  HRT_LAUNCHED("sort_gather_kernel");
   return HRT_OK;
 }
 
