@@ -392,6 +392,18 @@ hrt_status hrt_ic_zeldovich_adjoint(const float* noise, int64_t n_side, double b
                                     double a_init, const float* disp_bar, const float* mom_bar, const float* disp,
                                     float* noise_bar, double* table_bar_host, double* ratio_bar_host, void* stream);
 
+/* Transpose of hrt_ic_2lpt (R21: x = q + D1 Psi1 + D2 Psi2, p = c1 Psi1 + c2 Psi2 with c1 = a^2 E f1 D1 and
+ * c2 = a^2 E f2 D2): noise_bar[n_side^3] <- dL/dnoise given disp_bar, mom_bar, the cotangents of its outputs.
+ * table_bar_host (size as hrt_ic_table, or NULL) receives dL/dt for the unit-growth transfer t(|n|^2) =
+ * T(|n|^2) / D1(a_init), and coef_bar_host (4 doubles, or NULL) dL/d(D1, D2, c1, c2) of the combine; both
+ * depend on Omega_m (hrt_ic_table, hrt_ic_2lpt_coefficients).  Recomputes the forward fields (device memory:
+ * about 60 B per particle plus 2 spectra).  Synchronises the stream. */
+hrt_status hrt_ic_2lpt_adjoint(const float* noise, int64_t n_side, double box, const hrt_cosmology* cosmo,
+                               double a_init, const float* disp_bar, const float* mom_bar, float* noise_bar,
+                               double* table_bar_host, double* coef_bar_host, void* stream);
+/* (D1, D2, c1, c2) of hrt_ic_2lpt's combine at a_init (host). */
+hrt_status hrt_ic_2lpt_coefficients(const hrt_cosmology* cosmo, double a_init, double* out_host);
+
 /* out_host = sum_i a[i] b[i] in FP64 over m float32 elements (synchronises). */
 hrt_status hrt_dot(const float* a, const float* b, int64_t m, double* out_host, void* stream);
 
@@ -544,10 +556,10 @@ hrt_status hrt_set_particle_sort(hrt_ctx* ctx, int32_t every);
  * NULL) and theta_bar (device FP64 [n_rays][2], dL/dtheta of the final ray angles, or NULL): noise_bar (device
  * float32 [n_side^3]) receives dL/dnoise and *omega_bar_host (or NULL) dL/dOmega_m.  It recomputes each
  * segment of k steps from its checkpoint (transient device memory: k pre-step states of particles, rays and
- * the three fields) and runs the adjoint calls above in reverse.  Supported: Zel'dovich ICs, ray steps on the
- * particle fields (ray_fields == 0), untiled, with the direct gather or the ray mesh (R29); 2LPT or given
- * initial particles, loaded states, static-lens steps, free drifts, tiling and ray fields make the record
- * unusable (HRT_ERR_STATE with the reason).  Synchronises the context's stream. */
+ * the three fields) and runs the adjoint calls above in reverse.  Supported: Zel'dovich or 2LPT ICs, ray steps
+ * on the particle fields (ray_fields == 0), untiled, with the direct gather or the ray mesh; given initial
+ * particles, loaded states, static-lens steps, free drifts, tiling and ray fields make the record unusable
+ * (HRT_ERR_STATE with the reason).  Synchronises the context's stream. */
 hrt_status hrt_set_checkpointing(hrt_ctx* ctx, int32_t every);
 hrt_status hrt_adjoint(hrt_ctx* ctx, const float* kappa_bar, const double* theta_bar, float* noise_bar,
                        double* omega_bar_host);

@@ -23,6 +23,10 @@ hrt_status launch_power_adjoint_weight(void* spec, int64_t m, double dtheta, int
                                        const double* wbin_dev, cudaStream_t s);
 hrt_status launch_ic_adjoint(const void* in, const void* w_hat, int64_t n, double box, const float* table, void* out,
                              double* table_bar, cudaStream_t s);
+hrt_status launch_lpt2_kspace_adjoint(const void* in, int64_t n, double box, void* out, cudaStream_t s);
+hrt_status launch_lpt2_source_adjoint(float* h, const float* sb, int64_t m, cudaStream_t s);
+hrt_status launch_ic_hessian_adjoint(const void* in, const void* w_hat, int64_t n, double box, const float* table,
+                                     int set, void* out, double* table_bar, cudaStream_t s);
 hrt_status launch_axpy(const float* x, float* y, double alpha, int64_t m, cudaStream_t s);
 hrt_status launch_dot(const float* a, const float* b, int64_t m, double* out, cudaStream_t s);
 

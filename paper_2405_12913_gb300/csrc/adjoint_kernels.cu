@@ -645,6 +645,117 @@ hrt_status launch_ic_adjoint(const void* in, const void* w_hat, int64_t n, doubl
 }
 
 // ---------------------------------------------------------------------------------------------------------
+// 2LPT adjoint pieces.  The forward (hrt_ic_2lpt) is, at unit growth, with w_hat = R2C(noise) and t = T / D1:
+//   Psi1_j = C2R(i t d_j w_hat),  H_ab = C2R(t d_a d_b w_hat),  S = sum_{a<b} (H_aa H_bb - H_ab^2),
+//   Psi2_j = C2R(-i d_j R2C(S) / (k^2 n^3)).
+// Each C2R(M R2C(.)) with a Hermitian multiplier M has the transpose C2R(conj(M) R2C(.)).
+// ---------------------------------------------------------------------------------------------------------
+
+// out = sum_j (i d_j / (k^2 n^3)) in_j (the transpose of the Psi2 step, into the spectrum of S_bar).
+__global__ void lpt2_kspace_adjoint_kernel(const float2* __restrict__ in, int n, int nzc, float kf, float inv_n3,
+                                           int64_t elems, float2* __restrict__ out) {
+  const int iz = blockIdx.y * blockDim.x + threadIdx.x;
+  const int64_t row = static_cast<int64_t>(blockIdx.x) * blockDim.y + threadIdx.y;
+  if (iz >= nzc || row >= static_cast<int64_t>(n) * n) return;
+  const int ix = static_cast<int>(row / n);
+  const int iy = static_cast<int>(row - static_cast<int64_t>(ix) * n);
+  const int half = n >> 1;
+  const int nx = ix < half ? ix : ix - n, ny = iy < half ? iy : iy - n, nz = iz;
+  const int64_t e = row * nzc + iz;
+  const float k2 = kf * kf * static_cast<float>(nx * nx + ny * ny + nz * nz);
+  const float c = k2 > 0.f ? inv_n3 / k2 : 0.f;
+  const float d[3] = {(nx == -half) ? 0.f : kf * nx, (ny == -half) ? 0.f : kf * ny, (nz == half) ? 0.f : kf * nz};
+  float2 acc = make_float2(0.f, 0.f);
+  for (int j = 0; j < 3; ++j) {
+    const float2 v = in[e + j * elems];
+    const float cd = c * d[j];  // i cd v
+    acc.x -= cd * v.y;
+    acc.y += cd * v.x;
+  }
+  out[e] = acc;
+}
+
+hrt_status launch_lpt2_kspace_adjoint(const void* in, int64_t n, double box, void* out, cudaStream_t s) {
+  const int64_t nzc = n / 2 + 1;
+  dim3 block(64, 4);
+  dim3 grid(static_cast<unsigned>((n * n + 3) / 4), static_cast<unsigned>((nzc + 63) / 64));
+  lpt2_kspace_adjoint_kernel<<<grid, block, 0, s>>>(static_cast<const float2*>(in), static_cast<int>(n),
+                                                    static_cast<int>(nzc), static_cast<float>(2.0 * M_PI / box),
+                                                    static_cast<float>(1.0 / (static_cast<double>(n) * n * n)),
+                                                    n * n * nzc, static_cast<float2*>(out));
+  HRT_LAUNCHED("lpt2_kspace_adjoint_kernel");
+  return HRT_OK;
+}
+
+// In place: h holds the six Hessian fields (xx, yy, zz, xy, xz, yz) and receives their cotangents for the
+// source cotangent sb: d S / d H_aa = sum of the other two diagonal fields, d S / d H_ab = -2 H_ab.
+__global__ void lpt2_source_adjoint_kernel(float* __restrict__ h, const float* __restrict__ sb, int64_t m) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= m) return;
+  const float xx = h[i], yy = h[i + m], zz = h[i + 2 * m], xy = h[i + 3 * m], xz = h[i + 4 * m], yz = h[i + 5 * m];
+  const float b = sb[i];
+  h[i] = b * (yy + zz);
+  h[i + m] = b * (xx + zz);
+  h[i + 2 * m] = b * (xx + yy);
+  h[i + 3 * m] = -2.f * b * xy;
+  h[i + 4 * m] = -2.f * b * xz;
+  h[i + 5 * m] = -2.f * b * yz;
+}
+
+hrt_status launch_lpt2_source_adjoint(float* h, const float* sb, int64_t m, cudaStream_t s) {
+  lpt2_source_adjoint_kernel<<<blocks_for(m, 256), 256, 0, s>>>(h, sb, m);
+  HRT_LAUNCHED("lpt2_source_adjoint_kernel");
+  return HRT_OK;
+}
+
+// out += sum_j t f_j in_j for the Hessian set (0: xx, yy, zz; 1: xy, xz, yz) with f_j the product of the two
+// derivative factors, and table_bar[|n|^2] += sum_j f_j Re(conj(in_j) w_hat) (half-spectrum weight 2 off the
+// kz = 0 and Nyquist planes).
+__global__ void ic_hessian_adjoint_kernel(const float2* __restrict__ in, const float2* __restrict__ w_hat, int n,
+                                          int nzc, float kf, const float* __restrict__ table, int set, int64_t elems,
+                                          float2* __restrict__ out, double* __restrict__ table_bar) {
+  const int iz = blockIdx.y * blockDim.x + threadIdx.x;
+  const int64_t row = static_cast<int64_t>(blockIdx.x) * blockDim.y + threadIdx.y;
+  if (iz >= nzc || row >= static_cast<int64_t>(n) * n) return;
+  const int ix = static_cast<int>(row / n);
+  const int iy = static_cast<int>(row - static_cast<int64_t>(ix) * n);
+  const int half = n >> 1;
+  const int nx = ix < half ? ix : ix - n, ny = iy < half ? iy : iy - n, nz = iz;
+  const int64_t e = row * nzc + iz;
+  const int n2 = nx * nx + ny * ny + nz * nz;
+  const float t = __ldg(table + n2);
+  const float dx = (nx == -half) ? 0.f : kf * nx;
+  const float dy = (ny == -half) ? 0.f : kf * ny;
+  const float dz = (nz == half) ? 0.f : kf * nz;
+  const float f[3] = {set == 0 ? dx * dx : dx * dy, set == 0 ? dy * dy : dx * dz, set == 0 ? dz * dz : dy * dz};
+  const float2 wv = w_hat[e];
+  float2 acc = out[e];
+  double tb = 0.0;
+  const double wkz = (iz == 0 || iz == half) ? 1.0 : 2.0;
+  for (int j = 0; j < 3; ++j) {
+    const float2 v = in[e + j * elems];
+    acc.x += t * f[j] * v.x;
+    acc.y += t * f[j] * v.y;
+    tb += wkz * f[j] * (static_cast<double>(v.x) * wv.x + static_cast<double>(v.y) * wv.y);
+  }
+  out[e] = acc;
+  if (table_bar != nullptr && tb != 0.0) atomicAdd(table_bar + n2, tb);
+}
+
+hrt_status launch_ic_hessian_adjoint(const void* in, const void* w_hat, int64_t n, double box, const float* table,
+                                     int set, void* out, double* table_bar, cudaStream_t s) {
+  const int64_t nzc = n / 2 + 1;
+  dim3 block(64, 4);
+  dim3 grid(static_cast<unsigned>((n * n + 3) / 4), static_cast<unsigned>((nzc + 63) / 64));
+  ic_hessian_adjoint_kernel<<<grid, block, 0, s>>>(static_cast<const float2*>(in), static_cast<const float2*>(w_hat),
+                                                   static_cast<int>(n), static_cast<int>(nzc),
+                                                   static_cast<float>(2.0 * M_PI / box), table, set, n * n * nzc,
+                                                   static_cast<float2*>(out), table_bar);
+  HRT_LAUNCHED("ic_hessian_adjoint_kernel");
+  return HRT_OK;
+}
+
+// ---------------------------------------------------------------------------------------------------------
 // FP64 dot product of two float32 arrays (coefficient cotangents such as dL/dpref = <g_bar, g> / pref).
 // ---------------------------------------------------------------------------------------------------------
 __global__ void dot_kernel(const float* __restrict__ a, const float* __restrict__ b, int64_t m, double* __restrict__ out) {

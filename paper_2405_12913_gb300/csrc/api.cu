@@ -1150,6 +1150,119 @@ hrt_status hrt_ic_table(int64_t n_side, double box, const hrt_cosmology* cosmo, 
   return HRT_OK;
 }
 
+// Growth factors of the 2LPT combine (R21): disp = d1 Psi1 + d2 Psi2, mom = c1 Psi1 + c2 Psi2.
+static void lpt2_coefficients(const hrt_cosmology& cosmo, double a_init, double& d1, double& d2, double& c1, double& c2) {
+  Cosmo c(cosmo.omega_m);
+  d1 = c.D1(a_init);
+  const double f1 = c.f(a_init), e = c.E(a_init);
+  const double om_a = cosmo.omega_m / (a_init * a_init * a_init * e * e);
+  d2 = -3.0 / 7.0 * d1 * d1 * std::pow(om_a, -1.0 / 143.0);
+  const double f2 = 2.0 * std::pow(om_a, 6.0 / 11.0);
+  const double pfac = a_init * a_init * e;
+  c1 = pfac * f1 * d1;
+  c2 = pfac * f2 * d2;
+}
+
+hrt_status hrt_ic_2lpt_coefficients(const hrt_cosmology* cosmo, double a_init, double* out_host) {
+  if (!cosmo || !out_host || !(a_init > 0.0 && a_init <= 1.0) || !(cosmo->omega_m > 0.0 && cosmo->omega_m <= 1.0))
+    return fail(HRT_ERR_INVALID_ARG, "bad arguments");
+  lpt2_coefficients(*cosmo, a_init, out_host[0], out_host[1], out_host[2], out_host[3]);
+  return HRT_OK;
+}
+
+hrt_status hrt_ic_2lpt_adjoint(const float* noise, int64_t n_side, double box, const hrt_cosmology* cosmo,
+                               double a_init, const float* disp_bar, const float* mom_bar, float* noise_bar,
+                               double* table_bar_host, double* coef_bar_host, void* stream) {
+  HRT_TRY(check_mesh(n_side, box));
+  if (!noise || !cosmo || !disp_bar || !mom_bar || !noise_bar) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  if (!(a_init > 0.0 && a_init <= 1.0) || !(cosmo->omega_m > 0.0 && cosmo->omega_m <= 1.0))
+    return fail(HRT_ERR_INVALID_ARG, "bad cosmology");
+  cudaStream_t s = as_stream(stream);
+  const int64_t n = n_side, np = n * n * n;
+  double d1, d2, c1, c2;
+  lpt2_coefficients(*cosmo, a_init, d1, d2, c1, c2);
+  const std::vector<double> t64 = ic_table64(n, box, cosmo, a_init, nullptr);
+  std::vector<float> table(t64.size());
+  for (size_t i = 0; i < t64.size(); ++i) table[i] = static_cast<float>(t64[i] / d1);  // unit growth, as the forward
+  const size_t nt = table.size();
+  hrt_pm tmp;
+  hrt_status st = pm_make(n, box, 0, s, &tmp);
+  float *tab = nullptr, *psi1 = nullptr, *psi2 = nullptr, *h = nullptr, *sf = nullptr;
+  void *w_hat = nullptr, *acc = nullptr;
+  double* dbuf = nullptr;  // [0..3] combine coefficient cotangents, [4..] table cotangent
+  if (st == HRT_OK) st = upload(table, &tab, s, "IC table");
+  if (st == HRT_OK) st = device_alloc(reinterpret_cast<void**>(&psi1), 3 * np * sizeof(float), s, "Psi1");
+  if (st == HRT_OK) st = device_alloc(reinterpret_cast<void**>(&psi2), 3 * np * sizeof(float), s, "Psi2");
+  if (st == HRT_OK) st = device_alloc(reinterpret_cast<void**>(&h), 6 * np * sizeof(float), s, "Hessian");
+  if (st == HRT_OK) st = device_alloc(reinterpret_cast<void**>(&sf), np * sizeof(float), s, "source");
+  const size_t sb = spectrum_bytes(n);
+  if (st == HRT_OK) st = device_alloc(&w_hat, sb, s, "noise spectrum");
+  if (st == HRT_OK) st = device_alloc(&acc, sb, s, "noise_bar spectrum");
+  if (st == HRT_OK) st = device_alloc(reinterpret_cast<void**>(&dbuf), (4 + nt) * sizeof(double), s, "cotangents");
+  if (st == HRT_OK) st = cuda_status(cudaMemsetAsync(dbuf, 0, (4 + nt) * sizeof(double), s), "memset");
+  char* gh = static_cast<char*>(tmp.grad_hat);
+  auto c2r3 = [&](float* out) {
+    for (int j = 0; j < 3 && st == HRT_OK; ++j)
+      st = cufft_status(cufftExecC2R(tmp.c2r, reinterpret_cast<cufftComplex*>(gh + j * sb), out + j * np), "2LPT C2R");
+  };
+  auto r2c3 = [&](const float* in) {
+    for (int j = 0; j < 3 && st == HRT_OK; ++j)
+      st = cufft_status(cufftExecR2C(tmp.r2c, const_cast<float*>(in + j * np), reinterpret_cast<cufftComplex*>(gh + j * sb)),
+                        "2LPT adj R2C");
+  };
+  // forward recompute: Psi1, the Hessian, the source and Psi2 at unit growth
+  if (st == HRT_OK) st = cufft_status(cufftExecR2C(tmp.r2c, const_cast<float*>(noise), static_cast<cufftComplex*>(w_hat)), "IC R2C");
+  if (st == HRT_OK) st = launch_ic_kspace(w_hat, n, box, tab, tmp.grad_hat, s);
+  c2r3(psi1);
+  for (int set = 0; set < 2 && st == HRT_OK; ++set) {
+    st = launch_ic_hessian(w_hat, n, box, tab, set, tmp.grad_hat, s);
+    c2r3(h + 3 * set * np);
+  }
+  if (st == HRT_OK) st = launch_lpt2_source(h, np, sf, s);
+  if (st == HRT_OK) st = cufft_status(cufftExecR2C(tmp.r2c, sf, static_cast<cufftComplex*>(tmp.rho_hat)), "2LPT R2C");
+  if (st == HRT_OK) st = launch_lpt2_kspace(tmp.rho_hat, n, box, tmp.grad_hat, s);
+  c2r3(psi2);
+  // combine coefficients: d(disp, mom)/d(d1, d2, c1, c2)
+  if (st == HRT_OK) st = launch_dot(disp_bar, psi1, 3 * np, dbuf, s);
+  if (st == HRT_OK) st = launch_dot(disp_bar, psi2, 3 * np, dbuf + 1, s);
+  if (st == HRT_OK) st = launch_dot(mom_bar, psi1, 3 * np, dbuf + 2, s);
+  if (st == HRT_OK) st = launch_dot(mom_bar, psi2, 3 * np, dbuf + 3, s);
+  // Psi1_bar = d1 disp_bar + c1 mom_bar, Psi2_bar = d2 disp_bar + c2 mom_bar (over the forward fields)
+  if (st == HRT_OK) st = launch_lpt_combine(disp_bar, mom_bar, 3 * np, d1, c1, d2, c2, psi1, psi2, s);
+  // Psi1 part of the noise cotangent (the Zel'dovich transpose at unit growth)
+  r2c3(psi1);
+  if (st == HRT_OK) st = launch_ic_adjoint(tmp.grad_hat, w_hat, n, box, tab, acc, table_bar_host ? dbuf + 4 : nullptr, s);
+  // Psi2 -> source cotangent -> Hessian cotangents (in place) -> noise cotangent
+  r2c3(psi2);
+  if (st == HRT_OK) st = launch_lpt2_kspace_adjoint(tmp.grad_hat, n, box, tmp.rho_hat, s);
+  if (st == HRT_OK) st = cufft_status(cufftExecC2R(tmp.c2r, static_cast<cufftComplex*>(tmp.rho_hat), sf), "2LPT adj C2R");
+  if (st == HRT_OK) st = launch_lpt2_source_adjoint(h, sf, np, s);
+  for (int set = 0; set < 2 && st == HRT_OK; ++set) {
+    r2c3(h + 3 * set * np);
+    if (st == HRT_OK)
+      st = launch_ic_hessian_adjoint(tmp.grad_hat, w_hat, n, box, tab, set, acc, table_bar_host ? dbuf + 4 : nullptr, s);
+  }
+  if (st == HRT_OK) st = cufft_status(cufftExecC2R(tmp.c2r, static_cast<cufftComplex*>(acc), noise_bar), "IC adj C2R");
+  std::vector<double> hb(4 + nt);
+  if (st == HRT_OK) st = cuda_status(cudaMemcpyAsync(hb.data(), dbuf, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "copy");
+  if (st == HRT_OK) st = cuda_status(cudaStreamSynchronize(s), "sync");
+  device_free(tab, s);
+  device_free(psi1, s);
+  device_free(psi2, s);
+  device_free(h, s);
+  device_free(sf, s);
+  device_free(w_hat, s);
+  device_free(acc, s);
+  device_free(dbuf, s);
+  pm_release(&tmp);
+  if (st != HRT_OK) return st;
+  if (coef_bar_host)
+    for (int k = 0; k < 4; ++k) coef_bar_host[k] = hb[k];
+  if (table_bar_host)
+    for (size_t i = 0; i < nt; ++i) table_bar_host[i] = hb[4 + i];
+  return HRT_OK;
+}
+
 hrt_status hrt_ic_zeldovich_adjoint(const float* noise, int64_t n_side, double box, const hrt_cosmology* cosmo,
                                     double a_init, const float* disp_bar, const float* mom_bar, const float* disp,
                                     float* noise_bar, double* table_bar_host, double* ratio_bar_host, void* stream) {
@@ -1388,7 +1501,7 @@ hrt_status hrt_init_particles_zeldovich(hrt_ctx* ctx, const float* noise, double
   if (ctx->cfg.static_mode) return fail(HRT_ERR_STATE, "Zel'dovich ICs need the expanding mode");
   hrt_status s = hrt_ic_zeldovich(noise, ctx->cfg.n_side, ctx->cfg.box, &ctx->cfg.cosmo, a_init, ctx->disp,
                                   ctx->mom, ctx->stream);
-  if (s == HRT_OK) s = tape_on_ics(ctx, noise, a_init);
+  if (s == HRT_OK) s = tape_on_ics(ctx, noise, a_init, false);
   if (s != HRT_OK) return ctx_mark(ctx, s);
   ctx_lattice_order(ctx);
   ctx->a = ctx->a_mom = a_init;
@@ -1399,9 +1512,9 @@ hrt_status hrt_init_particles_zeldovich(hrt_ctx* ctx, const float* noise, double
 hrt_status hrt_init_particles_2lpt(hrt_ctx* ctx, const float* noise, double a_init) {
   HRT_TRY(ctx_guard(ctx));
   if (ctx->cfg.static_mode) return fail(HRT_ERR_STATE, "2LPT ICs need the expanding mode");
-  tape_invalidate(ctx, "the adjoint starts from Zel'dovich initial conditions");
   hrt_status s = hrt_ic_2lpt(noise, ctx->cfg.n_side, ctx->cfg.box, &ctx->cfg.cosmo, a_init, ctx->disp, ctx->mom,
                              ctx->stream);
+  if (s == HRT_OK) s = tape_on_ics(ctx, noise, a_init, true);
   if (s != HRT_OK) return ctx_mark(ctx, s);
   ctx_lattice_order(ctx);
   ctx->a = ctx->a_mom = a_init;
@@ -1412,7 +1525,7 @@ hrt_status hrt_init_particles_2lpt(hrt_ctx* ctx, const float* noise, double a_in
 hrt_status hrt_init_particles(hrt_ctx* ctx, const float* disp, const float* mom, double a) {
   HRT_TRY(ctx_guard(ctx));
   if (!disp || !mom || !(a > 0.0 && a <= 1.0)) return fail(HRT_ERR_INVALID_ARG, "bad particle arguments");
-  tape_invalidate(ctx, "the adjoint starts from Zel'dovich initial conditions");
+  tape_invalidate(ctx, "the adjoint starts from initial conditions drawn from white noise");
   const size_t bytes = 3 * static_cast<size_t>(ctx->cfg.n_side * ctx->cfg.n_side * ctx->cfg.n_side) * sizeof(float);
   hrt_status s = cuda_status(cudaMemcpyAsync(ctx->disp, disp, bytes, cudaMemcpyDeviceToDevice, ctx->stream), "copy disp");
   if (s == HRT_OK) s = cuda_status(cudaMemcpyAsync(ctx->mom, mom, bytes, cudaMemcpyDeviceToDevice, ctx->stream), "copy mom");

@@ -34,8 +34,9 @@ struct TapeCheckpoint {
 struct Tape {
   int every = 0;
   bool valid = false;           // a run from Zel'dovich ICs is being recorded
-  const char* invalid_why = "no Zel'dovich initial conditions recorded";
+  const char* invalid_why = "no initial conditions from white noise recorded";
   double a_init = 0.0;
+  bool lpt2 = false;            // 2LPT (else Zel'dovich) initial conditions
   float* noise = nullptr;       // copy of the white noise
   float* disp0 = nullptr;       // displacements of the ICs
   double* theta0 = nullptr;     // initial ray angles
@@ -107,7 +108,7 @@ hrt_status ctx_particles_lattice(hrt_ctx* ctx, float* disp_out, float* mom_out);
 hrt_ray_geom ctx_geom(const hrt_config& c, const hrt_ctx* ctx);
 
 // Recording hooks (tape.cu); each is a no-op without a tape.
-hrt_status tape_on_ics(hrt_ctx* ctx, const float* noise, double a_init);
+hrt_status tape_on_ics(hrt_ctx* ctx, const float* noise, double a_init, bool lpt2);
 hrt_status tape_on_rays(hrt_ctx* ctx, const double* theta0, int64_t n_rays);
 hrt_status tape_on_step(hrt_ctx* ctx, char kind, double a_next, int slot, double weight, bool accumulate);
 void tape_invalidate(hrt_ctx* ctx, const char* why);

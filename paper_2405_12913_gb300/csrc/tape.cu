@@ -85,7 +85,7 @@ void tape_clear(Tape& t, cudaStream_t s) {
   t.checkpoints.clear();
   t.steps.clear();
   t.valid = false;
-  t.invalid_why = "no Zel'dovich initial conditions recorded";
+  t.invalid_why = "no initial conditions from white noise recorded";
   t.n_rays = 0;
   t.rays_start = -1;
 }
@@ -126,7 +126,7 @@ void tape_invalidate(hrt_ctx* ctx, const char* why) {
   }
 }
 
-hrt_status tape_on_ics(hrt_ctx* ctx, const float* noise, double a_init) {
+hrt_status tape_on_ics(hrt_ctx* ctx, const float* noise, double a_init, bool lpt2) {
   if (!ctx->tape) return HRT_OK;
   Tape& t = *ctx->tape;
   cudaStream_t s = ctx->stream;
@@ -137,6 +137,7 @@ hrt_status tape_on_ics(hrt_ctx* ctx, const float* noise, double a_init) {
   HRT_TRY(copy_floats(t.noise, noise, np, s));
   HRT_TRY(copy_floats(t.disp0, ctx->disp, 3 * np, s));
   t.a_init = a_init;
+  t.lpt2 = lpt2;
   t.valid = true;
   return HRT_OK;
 }
@@ -389,9 +390,13 @@ hrt_status tape_adjoint(hrt_ctx* ctx, const float* kappa_bar, const double* thet
   HRT_TRY(hrt_cic_scatter_adjoint(rho_bar, t.disp0, cfg.n_side, n, cfg.box, d_bar, s));
   const int64_t ntab = 3 * (cfg.n_side / 2) * (cfg.n_side / 2) + 1;
   std::vector<double> table_bar(ntab, 0.0);
-  double ratio_bar = 0.0;
-  HRT_TRY(hrt_ic_zeldovich_adjoint(t.noise, cfg.n_side, cfg.box, &cfg.cosmo, t.a_init, d_bar, m_bar, t.disp0,
-                                   noise_bar, table_bar.data(), &ratio_bar, s));
+  double ratio_bar = 0.0, lpt_bar[4] = {0.0, 0.0, 0.0, 0.0};
+  if (t.lpt2)
+    HRT_TRY(hrt_ic_2lpt_adjoint(t.noise, cfg.n_side, cfg.box, &cfg.cosmo, t.a_init, d_bar, m_bar, noise_bar,
+                                table_bar.data(), lpt_bar, s));
+  else
+    HRT_TRY(hrt_ic_zeldovich_adjoint(t.noise, cfg.n_side, cfg.box, &cfg.cosmo, t.a_init, d_bar, m_bar, t.disp0,
+                                     noise_bar, table_bar.data(), &ratio_bar, s));
   if (!omega_bar) return HRT_OK;
 
   // Omega_m: FP64 central differences of the host coefficients, weighted by their cotangents
@@ -472,8 +477,17 @@ hrt_status tape_adjoint(hrt_ctx* ctx, const float* kappa_bar, const double* thet
   cm.omega_m = om - e;
   HRT_TRY(hrt_ic_table(cfg.n_side, cfg.box, &cp, t.a_init, tp.data(), &rp));
   HRT_TRY(hrt_ic_table(cfg.n_side, cfg.box, &cm, t.a_init, tm.data(), &rm));
-  for (int64_t j = 0; j < ntab; ++j) total += table_bar[j] * (tp[j] - tm[j]) / (2 * e);
-  total += ratio_bar * (rp - rm) / (2 * e);
+  if (t.lpt2) {
+    // the 2LPT transfer is the table at unit growth, and the combine has its own growth coefficients
+    double gp[4], gm[4];
+    HRT_TRY(hrt_ic_2lpt_coefficients(&cp, t.a_init, gp));
+    HRT_TRY(hrt_ic_2lpt_coefficients(&cm, t.a_init, gm));
+    for (int64_t j = 0; j < ntab; ++j) total += table_bar[j] * (tp[j] / gp[0] - tm[j] / gm[0]) / (2 * e);
+    for (int k = 0; k < 4; ++k) total += lpt_bar[k] * (gp[k] - gm[k]) / (2 * e);
+  } else {
+    for (int64_t j = 0; j < ntab; ++j) total += table_bar[j] * (tp[j] - tm[j]) / (2 * e);
+    total += ratio_bar * (rp - rm) / (2 * e);
+  }
   *omega_bar = total;
   return HRT_OK;
 }

@@ -104,6 +104,8 @@ _SIGS = {
     "hrt_kappa_power": ([_P, _I64, _D, _I32, _D, _D, _P, _P, _P, _P], C.c_int),
     "hrt_ic_zeldovich": ([_P, _I64, _D, _P, _D, _P, _P, _P], C.c_int),
     "hrt_ic_2lpt": ([_P, _I64, _D, _P, _D, _P, _P, _P], C.c_int),
+    "hrt_ic_2lpt_adjoint": ([_P, _I64, _D, _P, _D, _P, _P, _P, _P, _P, _P], C.c_int),
+    "hrt_ic_2lpt_coefficients": ([_P, _D, _P], C.c_int),
     "hrt_init_particles_2lpt": ([_P, _P, _D], C.c_int),
     "hrt_create": ([_P, _P, _P], C.c_int),
     "hrt_destroy": ([_P], C.c_int),
@@ -596,6 +598,27 @@ def hrt_ic_2lpt(noise: torch.Tensor, n_side: int, box: float, omega_m: float, h:
     _check(_lib.hrt_ic_2lpt(_ptr(noise, torch.float32, "noise"), n_side, box, C.byref(c), a_init,
                             _ptr(disp, torch.float32, "disp"), _ptr(mom, torch.float32, "mom"), _stream(stream)),
            "hrt_ic_2lpt")
+
+
+def hrt_ic_2lpt_adjoint(noise, n_side, box, omega_m, h, n_s, sigma8, a_init, disp_bar, mom_bar, noise_bar, stream=None):
+    """Fills noise_bar; returns (dL/d unit-growth table, dL/d(D1, D2, c1, c2)) as numpy arrays."""
+    import numpy as np
+    c = hrt_cosmology(omega_m, h, n_s, sigma8)
+    tb = np.zeros(3 * (n_side // 2) ** 2 + 1)
+    cb = np.zeros(4)
+    _check(_lib.hrt_ic_2lpt_adjoint(_ptr(noise, torch.float32, "noise"), n_side, box, C.byref(c), a_init,
+                                    _ptr(disp_bar, torch.float32, "disp_bar"), _ptr(mom_bar, torch.float32, "mom_bar"),
+                                    _ptr(noise_bar, torch.float32, "noise_bar"), tb.ctypes.data, cb.ctypes.data,
+                                    _stream(stream)), "hrt_ic_2lpt_adjoint")
+    return tb, cb
+
+
+def hrt_ic_2lpt_coefficients(omega_m, h, n_s, sigma8, a_init):
+    import numpy as np
+    c = hrt_cosmology(omega_m, h, n_s, sigma8)
+    out = np.zeros(4)
+    _check(_lib.hrt_ic_2lpt_coefficients(C.byref(c), a_init, out.ctypes.data), "hrt_ic_2lpt_coefficients")
+    return out
 
 
 def hrt_ic_zeldovich_adjoint(noise, n_side, box, omega_m, h, n_s, sigma8, a_init, disp_bar, mom_bar, disp, noise_bar,

@@ -195,6 +195,33 @@ def test_ic_adjoint_matches_autograd(hrt):
     _close(nb.cpu().numpy(), w.grad.numpy().reshape(-1), 3e-5)
 
 
+def test_2lpt_adjoint_matches_autograd(hrt):
+    n, box, a = 16, 64.0, 0.1
+    noise = synthetic.white_noise(65, n)
+    dbar = synthetic.gaussian_field(66, (3, n ** 3))
+    mbar = synthetic.gaussian_field(67, (3, n ** 3))
+    nb = torch.empty(n ** 3, device="cuda")
+    tb, cb = hrt.hrt_ic_2lpt_adjoint(_cuda(noise), n, box, 0.3, 0.7, 0.96, 0.8, a, _cuda(dbar), _cuda(mbar), nb)
+    w = torch.tensor(noise, requires_grad=True)
+    d, mm = opm.lpt2(w, box, 0.3, 0.7, 0.96, 0.8, a)
+    ((d * torch.tensor(dbar.T)).sum() + (mm * torch.tensor(mbar.T)).sum()).backward()
+    _close(nb.cpu().numpy(), w.grad.numpy().reshape(-1), 3e-5)
+    # the second-order part is not negligible here: the first-order (Zel'dovich) transpose alone differs
+    nz = torch.empty(n ** 3, device="cuda")
+    disp = torch.empty(3, n ** 3, device="cuda")
+    mom = torch.empty(3, n ** 3, device="cuda")
+    hrt.hrt_ic_zeldovich(_cuda(noise), n, box, 0.3, 0.7, 0.96, 0.8, a, disp, mom)
+    hrt.hrt_ic_zeldovich_adjoint(_cuda(noise), n, box, 0.3, 0.7, 0.96, 0.8, a, _cuda(dbar), _cuda(mbar), disp, nz)
+    assert float((nz - nb).abs().max()) > 1e-3 * float(nb.abs().max())
+    # the combine coefficients' cotangents: L is linear in them, so sum_k c_k dL/dc_k = L
+    disp2 = torch.empty(3, n ** 3, device="cuda")
+    mom2 = torch.empty(3, n ** 3, device="cuda")
+    hrt.hrt_ic_2lpt(_cuda(noise), n, box, 0.3, 0.7, 0.96, 0.8, a, disp2, mom2)
+    L = float((disp2.double() * _cuda(dbar).double()).sum() + (mom2.double() * _cuda(mbar).double()).sum())
+    coefs = hrt.hrt_ic_2lpt_coefficients(0.3, 0.7, 0.96, 0.8, a)
+    assert abs(float(coefs @ cb) - L) <= 1e-4 * abs(L)
+
+
 def _oracle_run(W, noise, theta0, om):
     c = osim.Cosmo(om, W.h, W.n_s, W.sigma8)
     flt = osim.Filter(W.deconv_p, W.smooth_cells)
@@ -504,4 +531,38 @@ def test_context_adjoint_matches_the_differentiable_simulation(hrt, mesh):
     with pytest.raises(hrt.HRTError):
         ctx.hrt_adjoint(kbar.contiguous())
     sim.close()
+    ctx.close()
+
+
+def test_context_adjoint_from_2lpt_ics_matches_central_differences(hrt):
+    """The recorded context run from 2LPT initial conditions: the noise gradient of a loss on the final ray angles
+    (continuous in the noise) against central differences of the same context run."""
+    from paper_2405_12913_gb300.configs import COSMO_GRAD as W
+    noise = _cuda(synthetic.white_noise(W.seed + 5, W.n_side)).reshape(-1)
+    theta0 = torch.tensor(synthetic.pixel_grid(W.n_pix, W.fov_deg * synthetic.DEGREE)).cuda()
+    tb = _cuda(synthetic.gaussian_field(83, (W.n_rays, 2)), torch.float64) * 1e4
+    cfg = hrt.make_config(W.n_mesh, W.box, W.n_side, W.omega_m, W.h, W.n_s, W.sigma8, W.deconv_p, W.smooth_cells,
+                          W.samples_per_cell, W.observer, n_sources=len(W.source_steps))
+    ctx = hrt.Context(cfg)
+    ctx.hrt_set_checkpointing(2)
+
+    def run(w):
+        ctx.hrt_init_particles_2lpt(w, W.a_init)
+        for a in W.forward_grid[1:]:
+            ctx.hrt_step(a)
+        ctx.hrt_sync_particles()
+        ctx.hrt_init_rays(theta0)
+        for a in W.reverse_grid[1:]:
+            ctx.hrt_step(a)
+        th = ctx.hrt_read_rays()[0]
+        return float(((th - theta0) * tb).sum())
+
+    run(noise)
+    nb, om_bar = ctx.hrt_adjoint(None, tb.contiguous())
+    direction = _cuda(synthetic.gaussian_field(84, (W.n_side ** 3,)))
+    ad = float((nb.double() * direction.double()).sum())
+    eps = 1e-3
+    fd = (run(noise + eps * direction) - run(noise - eps * direction)) / (2 * eps)
+    assert ad == pytest.approx(fd, rel=1e-2), (ad, fd)
+    assert np.isfinite(om_bar)
     ctx.close()
