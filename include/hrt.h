@@ -222,8 +222,8 @@ hrt_status hrt_ray_step(const hrt_rays* rays, const float* grad_x, const float* 
 /* hrt_ray_step through a light cone tiled by rotated and translated box replicas (geom->n_replicas >= 1; see
  * hrt_ray_geom and the tiling of Sec. 6.2): grad_x, grad_y, grad_z are the three gradient fields of the box, of
  * which each node reads the two that its replica turns into the sky x and y directions.
- * HRT_ERR_INVALID_ARG if a line-of-sight node falls outside the replicas or a replica is malformed.  (The
- * ray-step adjoint does not support tiling.) */
+ * HRT_ERR_INVALID_ARG if a line-of-sight node falls outside the replicas or a replica is malformed.  Its
+ * adjoint is hrt_ray_step_tiled_adjoint. */
 hrt_status hrt_ray_step_tiled(const hrt_rays* rays, const float* grad_x, const float* grad_y, const float* grad_z,
                               const hrt_ray_geom* geom, double chi_from, double chi_to, double a_ref, double omega_m,
                               float* maps, void* stream);
@@ -368,6 +368,14 @@ hrt_status hrt_pm_solve_adjoint(hrt_pm* pm, float* grad_bar, double pref, const 
 hrt_status hrt_ray_step_adjoint(const hrt_rays* rays, const float* grad_x, const float* grad_y, const hrt_ray_geom* geom,
                                 double chi_from, double chi_to, double a_ref, double omega_m, const hrt_rays* bar,
                                 float* gx_bar, float* gy_bar, double* node_bar, double* drift_bar, void* stream);
+
+/* hrt_ray_step_adjoint through a tiled light cone (geom->n_replicas >= 1, as hrt_ray_step_tiled): grad_z is the
+ * third gradient field and gz_bar its cotangent; each node's cotangents go to the two box fields its replica
+ * turns into the sky x and y directions. */
+hrt_status hrt_ray_step_tiled_adjoint(const hrt_rays* rays, const float* grad_x, const float* grad_y,
+                                      const float* grad_z, const hrt_ray_geom* geom, double chi_from, double chi_to,
+                                      double a_ref, double omega_m, const hrt_rays* bar, float* gx_bar, float* gy_bar,
+                                      float* gz_bar, double* node_bar, double* drift_bar, void* stream);
 
 /* FP64 node table of a ray step as the kernels use it (host): counts of the two half shells and, per kept
  * node, c_j, c_j r_j / cell and chi_j, plus the drift coefficient.  Arrays hold at least 1024 entries. */
@@ -557,8 +565,9 @@ hrt_status hrt_set_particle_sort(hrt_ctx* ctx, int32_t every);
  * float32 [n_side^3]) receives dL/dnoise and *omega_bar_host (or NULL) dL/dOmega_m.  It recomputes each
  * segment of k steps from its checkpoint (transient device memory: k pre-step states of particles, rays and
  * the three fields) and runs the adjoint calls above in reverse.  Supported: Zel'dovich or 2LPT ICs, ray steps
- * on the particle fields (ray_fields == 0), untiled, with the direct gather or the ray mesh; given initial
- * particles, loaded states, static-lens steps, free drifts, tiling and ray fields make the record unusable
+ * on the particle fields (ray_fields == 0) with the direct gather (also through a tiled light cone) or the
+ * ray mesh (untiled); given initial particles, loaded states, static-lens steps, free drifts, ray fields, the
+ * ray mesh through a tiled light cone and replicas changed during the run make the record unusable
  * (HRT_ERR_STATE with the reason).  Synchronises the context's stream. */
 hrt_status hrt_set_checkpointing(hrt_ctx* ctx, int32_t every);
 hrt_status hrt_adjoint(hrt_ctx* ctx, const float* kappa_bar, const double* theta_bar, float* noise_bar,

@@ -16,9 +16,10 @@ hrt_status launch_kick_drift_adjoint(const float* grad, int64_t n, double box, i
                                      cudaStream_t s);
 hrt_status launch_kspace_adjoint(const void* in, int n_in, int64_t n, double box, double pref, const float* tab,
                                  const hrt_filter* f, void* out, bool accumulate, cudaStream_t s);
+// gz, gbz: the third field and its cotangent, read and written only for a tiled step (p.tiled).
 hrt_status launch_ray_step_adjoint(const hrt_rays& rays, const float* gx, const float* gy, const RayStepParams& p,
                                    const hrt_rays& bar, float* gbx, float* gby, double* node_bar, double* drift_bar,
-                                   cudaStream_t s);
+                                   cudaStream_t s, const float* gz = nullptr, float* gbz = nullptr);
 hrt_status launch_power_adjoint_weight(void* spec, int64_t m, double dtheta, int nbins, double ell_min, double ell_max,
                                        const double* wbin_dev, cudaStream_t s);
 hrt_status launch_ic_adjoint(const void* in, const void* w_hat, int64_t n, double box, const float* table, void* out,

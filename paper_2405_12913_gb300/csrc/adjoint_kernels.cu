@@ -452,12 +452,208 @@ __device__ void half_backward(const RayStepParams& p, int j0, int j1, double thx
   }
 }
 
+// ---- light-cone tiling (the forward's half_kick_tiled): the node's sky-frame cell and fraction per sky axis map
+// to a box axis through the replica's axis permutation, sign and translation.
+__device__ __forceinline__ void box_axis_t(int i_s, float f_s, int sgn, int sh, int n, int& ib, float& fb) {
+  if (sgn > 0) {
+    ib = i_s + sh;
+    fb = f_s;
+  } else if (f_s > 0.f) {
+    ib = sh - i_s - 1;
+    fb = 1.f - f_s;
+  } else {
+    ib = sh - i_s;
+    fb = 0.f;
+  }
+  ib %= n;
+  if (ib < 0) ib += n;
+}
+
+// Box-frame columns of tiled node j (as node_cols), the replica's axes p[3] (box axis of sky x, y, line of
+// sight) and signs sg[3].
+__device__ __forceinline__ void node_cols_tiled(const RayStepParams& p, int j, int bx, float fbx, int by, float fby,
+                                                float tx, float ty, NodeCols& c, int pa[3], int sg[3]) {
+  const int n = p.n;
+  int ix, iy;
+  float fx, fy;
+  axis_split(bx, fbx + p.dr[j] * tx, n, ix, fx);
+  axis_split(by, fby + p.dr[j] * ty, n, iy, fy);
+  const int R = p.rep[j];
+  pa[0] = p.rperm[R][0];
+  pa[1] = p.rperm[R][1];
+  pa[2] = 3 - pa[0] - pa[1];
+  sg[0] = p.rsign[R][0];
+  sg[1] = p.rsign[R][1];
+  sg[2] = p.rsign[R][2];
+  int cb[3];
+  float fb[3];
+  box_axis_t(ix, fx, sg[0], p.rshift[R][0], n, cb[pa[0]], fb[pa[0]]);
+  box_axis_t(iy, fy, sg[1], p.rshift[R][1], n, cb[pa[1]], fb[pa[1]]);
+  cb[pa[2]] = p.kz[j];
+  fb[pa[2]] = p.fz[j];
+  c.fx = fb[0];
+  c.fy = fb[1];
+  c.fz = fb[2];
+  c.iz = cb[2];
+  c.jz = nxt(cb[2], n);
+  const int jx = nxt(cb[0], n), jy = nxt(cb[1], n);
+  const int64_t nn = n;
+  c.r[0] = (cb[0] * nn + cb[1]) * nn;
+  c.r[1] = (cb[0] * nn + jy) * nn;
+  c.r[2] = (jx * nn + cb[1]) * nn;
+  c.r[3] = (jx * nn + jy) * nn;
+}
+
+__device__ __forceinline__ float nf_d(const NodeField& o, int a) { return a == 0 ? o.dx : (a == 1 ? o.dy : o.dz); }
+// mixed second derivative along box axes a != b (zero for a == b: the interpolant is linear per axis)
+__device__ __forceinline__ float nf_s(const NodeField& o, int a, int b) {
+  if (a == b) return 0.f;
+  const int m = a + b;  // 1: xy, 2: xz, 3: yz
+  return m == 1 ? o.sxy : (m == 2 ? o.sxz : o.syz);
+}
+
+__device__ void half_forward_tiled(const RayStepParams& p, int j0, int j1, double thx, double thy, double ref_r,
+                                   const float* __restrict__ gx, const float* __restrict__ gy,
+                                   const float* __restrict__ gz, float K[2], float J[2][2]) {
+  K[0] = K[1] = 0.f;
+  J[0][0] = J[0][1] = J[1][0] = J[1][1] = 0.f;
+  if (j1 <= j0) return;
+  int bx, by;
+  float fbx, fby;
+  base_pos(p.obs_x, ref_r, thx, p.cell, p.n, bx, fbx);
+  base_pos(p.obs_y, ref_r, thy, p.cell, p.n, by, fby);
+  const float tx = static_cast<float>(thx), ty = static_cast<float>(thy);
+  const float* f3[3] = {gx, gy, gz};
+  for (int j = j0; j < j1; ++j) {
+    NodeCols c;
+    int pa[3], sg[3];
+    node_cols_tiled(p, j, bx, fbx, by, fby, tx, ty, c, pa, sg);
+    const NodeField oa = node_field(f3[pa[0]], c), ob = node_field(f3[pa[1]], c);
+    const float ss = static_cast<float>(sg[0] * sg[1]);
+    K[0] += p.cw[j] * (sg[0] * oa.v);
+    K[1] += p.cw[j] * (sg[1] * ob.v);
+    J[0][0] += p.cwr[j] * nf_d(oa, pa[0]);
+    J[0][1] += p.cwr[j] * (ss * nf_d(oa, pa[1]));
+    J[1][0] += p.cwr[j] * (ss * nf_d(ob, pa[0]));
+    J[1][1] += p.cwr[j] * nf_d(ob, pa[1]);
+  }
+}
+
+// Backward of one tiled half kick (as half_backward): the sky components are sign-weighted box fields g_{p0},
+// g_{p1}, and the derivative of sky axis b is sign_b d / d(box axis p_b).
+__device__ void half_backward_tiled(const RayStepParams& p, int j0, int j1, double thx, double thy, double ref_r,
+                                    const float* __restrict__ gx, const float* __restrict__ gy,
+                                    const float* __restrict__ gz, const float Kb[2], const float Jb[2][2],
+                                    float* __restrict__ gbx, float* __restrict__ gby, float* __restrict__ gbz,
+                                    float thb[2], float* __restrict__ sh_nodes, int n_nodes, bool active) {
+  if (j1 <= j0) return;
+  int bx = 0, by = 0;
+  float fbx = 0.f, fby = 0.f;
+  if (active) {
+    base_pos(p.obs_x, ref_r, thx, p.cell, p.n, bx, fbx);
+    base_pos(p.obs_y, ref_r, thy, p.cell, p.n, by, fby);
+  }
+  const float tx = static_cast<float>(thx), ty = static_cast<float>(thy);
+  const float inv_cell = static_cast<float>(1.0 / p.cell);
+  const float* f3[3] = {gx, gy, gz};
+  float* fb3[3] = {gbx, gby, gbz};
+  const int lane = threadIdx.x & 31;
+  for (int j = j0; j < j1; ++j) {
+    float cwb = 0.f, cwrb = 0.f, chib = 0.f;
+    NodeCols c{};
+    int pa[3] = {0, 1, 2}, sg[3] = {1, 1, 1};
+    float t[2][4][2] = {};  // cotangent per sky field (x, y), box (x, y) corner and box z plane
+    if (active) {
+      node_cols_tiled(p, j, bx, fbx, by, fby, tx, ty, c, pa, sg);
+      const float cw = p.cw[j], cwr = p.cwr[j];
+      const float ss = static_cast<float>(sg[0] * sg[1]);
+      const NodeField o[2] = {node_field(f3[pa[0]], c), node_field(f3[pa[1]], c)};
+      // per sky field: value weight al and derivative weights be[box axis]
+      float al[2] = {cw * sg[0] * Kb[0], cw * sg[1] * Kb[1]};
+      float be[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+      be[0][pa[0]] += cwr * Jb[0][0];
+      be[0][pa[1]] += cwr * ss * Jb[0][1];
+      be[1][pa[0]] += cwr * ss * Jb[1][0];
+      be[1][pa[1]] += cwr * Jb[1][1];
+      const float w0[3] = {1.f - c.fx, 1.f - c.fy, 1.f - c.fz}, w1[3] = {c.fx, c.fy, c.fz};
+      float F[3] = {0.f, 0.f, 0.f};  // dL / d(box fraction)
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int z = 0; z < 2; ++z) {
+            const int ax = k >> 1, ay = k & 1;
+            const float wx = ax ? w1[0] : w0[0], wy = ay ? w1[1] : w0[1], wz = z ? w1[2] : w0[2];
+            const float sx = ax ? 1.f : -1.f, sy = ay ? 1.f : -1.f, sz = z ? 1.f : -1.f;
+            t[a][k][z] = al[a] * wx * wy * wz + be[a][0] * sx * wy * wz + be[a][1] * wx * sy * wz + be[a][2] * wx * wy * sz;
+          }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          F[q] += al[a] * nf_d(o[a], q);
+#pragma unroll
+          for (int r = 0; r < 3; ++r) F[q] += be[a][r] * nf_s(o[a], q, r);
+        }
+      }
+      cwb = Kb[0] * sg[0] * o[0].v + Kb[1] * sg[1] * o[1].v;
+      cwrb = Jb[0][0] * nf_d(o[0], pa[0]) + Jb[0][1] * ss * nf_d(o[0], pa[1]) + Jb[1][0] * ss * nf_d(o[1], pa[0]) +
+             Jb[1][1] * nf_d(o[1], pa[1]);
+      const float r_over_cell = static_cast<float>(ref_r / p.cell) + p.dr[j];
+      thb[0] += F[pa[0]] * sg[0] * r_over_cell;
+      thb[1] += F[pa[1]] * sg[1] * r_over_cell;
+      chib = (F[pa[0]] * sg[0] * tx + F[pa[1]] * sg[1] * ty + F[pa[2]] * sg[2]) * inv_cell;
+    }
+    // the warp-segmented reduction of the field cotangents (as half_backward); a segment needs the same cell and
+    // the same replica axes
+    const long long key = active ? static_cast<long long>(c.r[0] + c.iz) * 8 + pa[0] * 3 + pa[1] : -1ll - lane;
+    const long long prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool head = lane == 0 || prev != key;
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const unsigned above = lane == 31 ? 0u : heads & (0xffffffffu << (lane + 1));
+    const int seg_end = above ? __ffs(above) - 2 : 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1)
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int z = 0; z < 2; ++z) {
+            const float u = __shfl_down_sync(0xffffffffu, t[a][k][z], d);
+            if (lane + d <= seg_end) t[a][k][z] += u;
+          }
+    if (head && active) {
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        float* fbp = fb3[pa[a]];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (t[a][k][0] != 0.f) atomicAdd(fbp + c.r[k] + c.iz, t[a][k][0]);
+          if (t[a][k][1] != 0.f) atomicAdd(fbp + c.r[k] + c.jz, t[a][k][1]);
+        }
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      cwb += __shfl_down_sync(0xffffffffu, cwb, o);
+      cwrb += __shfl_down_sync(0xffffffffu, cwrb, o);
+      chib += __shfl_down_sync(0xffffffffu, chib, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(sh_nodes + j, cwb);
+      atomicAdd(sh_nodes + n_nodes + j, cwrb);
+      atomicAdd(sh_nodes + 2 * n_nodes + j, chib);
+    }
+  }
+}
+
+template <bool TILED>
 __global__ void __launch_bounds__(128) ray_step_adjoint_kernel(
     const double2* __restrict__ theta, const float2* __restrict__ eta, const float4* __restrict__ Amat,
     const float4* __restrict__ Bmat, int64_t nr, const float* __restrict__ gx, const float* __restrict__ gy,
     const __grid_constant__ RayStepParams p, double2* __restrict__ theta_bar, float2* __restrict__ eta_bar,
     float4* __restrict__ A_bar, float4* __restrict__ B_bar, float* __restrict__ gbx, float* __restrict__ gby,
-    double* __restrict__ node_bar, double* __restrict__ drift_bar) {
+    double* __restrict__ node_bar, double* __restrict__ drift_bar, const float* __restrict__ gz,
+    float* __restrict__ gbz) {
   extern __shared__ float sh[];  // [3][n_nodes]
   const int n_nodes = p.n1 + p.n2;
   for (int i = threadIdx.x; i < 3 * n_nodes; i += blockDim.x) sh[i] = 0.f;
@@ -481,7 +677,10 @@ __global__ void __launch_bounds__(128) ray_step_adjoint_kernel(
   const float B0[2][2] = {{B0v.x, B0v.y}, {B0v.z, B0v.w}};
   // ---- forward recompute
   float K1[2], J1[2][2], K2[2], J2[2][2];
-  if (active) half_forward(p, 0, p.n1, th0.x, th0.y, p.ref_r[0], gx, gy, K1, J1);
+  if (active) {
+    if (TILED) half_forward_tiled(p, 0, p.n1, th0.x, th0.y, p.ref_r[0], gx, gy, gz, K1, J1);
+    else half_forward(p, 0, p.n1, th0.x, th0.y, p.ref_r[0], gx, gy, K1, J1);
+  }
   float eta1[2] = {et0.x + (active ? K1[0] : 0.f), et0.y + (active ? K1[1] : 0.f)};
   float B1[2][2], A1[2][2];
   for (int a = 0; a < 2; ++a)
@@ -490,7 +689,10 @@ __global__ void __launch_bounds__(128) ray_step_adjoint_kernel(
   const double th1x = th0.x + d * eta1[0], th1y = th0.y + d * eta1[1];
   for (int a = 0; a < 2; ++a)
     for (int b = 0; b < 2; ++b) A1[a][b] = A0[a][b] + p.drift * B1[a][b];
-  if (active) half_forward(p, p.n1, p.n1 + p.n2, th1x, th1y, p.ref_r[1], gx, gy, K2, J2);
+  if (active) {
+    if (TILED) half_forward_tiled(p, p.n1, p.n1 + p.n2, th1x, th1y, p.ref_r[1], gx, gy, gz, K2, J2);
+    else half_forward(p, p.n1, p.n1 + p.n2, th1x, th1y, p.ref_r[1], gx, gy, K2, J2);
+  }
   // ---- backward
   const double2 thbv = active ? theta_bar[r] : make_double2(0.0, 0.0);
   const float2 etbv = active ? eta_bar[r] : make_float2(0.f, 0.f);
@@ -511,7 +713,11 @@ __global__ void __launch_bounds__(128) ray_step_adjoint_kernel(
   Kb[1] = etb[1];
   // second half kick at theta1: half_backward adds dK/dtheta^T K_bar (= J2^T K_bar) and the second-derivative
   // terms of J2 to theta1_bar
-  half_backward(p, p.n1, p.n1 + p.n2, th1x, th1y, p.ref_r[1], gx, gy, Kb, Jb, gbx, gby, thb1, sh, n_nodes, active);
+  if (TILED)
+    half_backward_tiled(p, p.n1, p.n1 + p.n2, th1x, th1y, p.ref_r[1], gx, gy, gz, Kb, Jb, gbx, gby, gbz, thb1, sh,
+                        n_nodes, active);
+  else
+    half_backward(p, p.n1, p.n1 + p.n2, th1x, th1y, p.ref_r[1], gx, gy, Kb, Jb, gbx, gby, thb1, sh, n_nodes, active);
   // A1 = A0 + d B1
   for (int a = 0; a < 2; ++a)
     for (int b = 0; b < 2; ++b) {
@@ -531,7 +737,11 @@ __global__ void __launch_bounds__(128) ray_step_adjoint_kernel(
       for (int b = 0; b < 2; ++b) Ab[a][b] += J1[0][a] * Bb[0][b] + J1[1][a] * Bb[1][b];
   Kb[0] = etb[0];
   Kb[1] = etb[1];
-  half_backward(p, 0, p.n1, th0.x, th0.y, p.ref_r[0], gx, gy, Kb, Jb, gbx, gby, thb0, sh, n_nodes, active);
+  if (TILED)
+    half_backward_tiled(p, 0, p.n1, th0.x, th0.y, p.ref_r[0], gx, gy, gz, Kb, Jb, gbx, gby, gbz, thb0, sh, n_nodes,
+                        active);
+  else
+    half_backward(p, 0, p.n1, th0.x, th0.y, p.ref_r[0], gx, gy, Kb, Jb, gbx, gby, thb0, sh, n_nodes, active);
   if (active) {
     theta_bar[r] = make_double2(thb0[0], thb0[1]);
     eta_bar[r] = make_float2(etb[0], etb[1]);
@@ -546,17 +756,18 @@ __global__ void __launch_bounds__(128) ray_step_adjoint_kernel(
 
 hrt_status launch_ray_step_adjoint(const hrt_rays& rays, const float* gx, const float* gy, const RayStepParams& p,
                                    const hrt_rays& bar, float* gbx, float* gby, double* node_bar, double* drift_bar,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, const float* gz, float* gbz) {
   if (rays.n_rays == 0) return HRT_OK;
+  if (p.tiled && (!gz || !gbz)) return fail(HRT_ERR_INVALID_ARG, "a tiled ray step needs the third field and its cotangent");
   const size_t smem = 3 * static_cast<size_t>(p.n1 + p.n2) * sizeof(float);
+  auto* kernel = p.tiled ? ray_step_adjoint_kernel<true> : ray_step_adjoint_kernel<false>;
   if (smem > 48 * 1024)
-    HRT_CUDA(cudaFuncSetAttribute(ray_step_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(smem)));
-  ray_step_adjoint_kernel<<<blocks_for(rays.n_rays, 128), 128, smem, s>>>(
+    HRT_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  kernel<<<blocks_for(rays.n_rays, 128), 128, smem, s>>>(
       reinterpret_cast<const double2*>(rays.theta), reinterpret_cast<const float2*>(rays.eta),
       reinterpret_cast<const float4*>(rays.A), reinterpret_cast<const float4*>(rays.B), rays.n_rays, gx, gy, p,
       reinterpret_cast<double2*>(bar.theta), reinterpret_cast<float2*>(bar.eta), reinterpret_cast<float4*>(bar.A),
-      reinterpret_cast<float4*>(bar.B), gbx, gby, node_bar, drift_bar);
+      reinterpret_cast<float4*>(bar.B), gbx, gby, node_bar, drift_bar, gz, gbz);
   HRT_LAUNCHED("ray_step_adjoint_kernel");
   return HRT_OK;
 }

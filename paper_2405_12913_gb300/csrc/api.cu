@@ -1072,11 +1072,28 @@ hrt_status hrt_ray_step_adjoint(const hrt_rays* rays, const float* grad_x, const
   if (!geom || !grad_x || !grad_y || !gx_bar || !gy_bar || !node_bar || !drift_bar)
     return fail(HRT_ERR_INVALID_ARG, "NULL argument");
   if (bar->n_rays != rays->n_rays) return fail(HRT_ERR_INVALID_ARG, "ray counts differ");
-  if (geom->n_replicas > 0) return fail(HRT_ERR_INVALID_ARG, "the ray-step adjoint does not support a tiled light cone");
+  if (geom->n_replicas > 0) return fail(HRT_ERR_INVALID_ARG, "a tiled light cone needs hrt_ray_step_tiled_adjoint");
   static thread_local RayStepParams p;
   HRT_TRY(build_ray_params(*geom, chi_from, chi_to, a_ref, omega_m, p));
   set_tiles(*geom, rays->n_rays, p);
   return launch_ray_step_adjoint(*rays, grad_x, grad_y, p, *bar, gx_bar, gy_bar, node_bar, drift_bar, as_stream(stream));
+}
+
+hrt_status hrt_ray_step_tiled_adjoint(const hrt_rays* rays, const float* grad_x, const float* grad_y,
+                                      const float* grad_z, const hrt_ray_geom* geom, double chi_from, double chi_to,
+                                      double a_ref, double omega_m, const hrt_rays* bar, float* gx_bar, float* gy_bar,
+                                      float* gz_bar, double* node_bar, double* drift_bar, void* stream) {
+  HRT_TRY(check_rays(rays));
+  HRT_TRY(check_rays(bar));
+  if (!geom || !grad_x || !grad_y || !grad_z || !gx_bar || !gy_bar || !gz_bar || !node_bar || !drift_bar)
+    return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  if (bar->n_rays != rays->n_rays) return fail(HRT_ERR_INVALID_ARG, "ray counts differ");
+  if (geom->n_replicas < 1) return fail(HRT_ERR_INVALID_ARG, "the tiled adjoint needs n_replicas >= 1");
+  static thread_local RayStepParams p;
+  HRT_TRY(build_ray_params(*geom, chi_from, chi_to, a_ref, omega_m, p));
+  set_tiles(*geom, rays->n_rays, p);
+  return launch_ray_step_adjoint(*rays, grad_x, grad_y, p, *bar, gx_bar, gy_bar, node_bar, drift_bar, as_stream(stream),
+                                 grad_z, gz_bar);
 }
 
 hrt_status hrt_ray_step_coefficients(const hrt_ray_geom* geom, double chi_from, double chi_to, double a_ref,

@@ -22,6 +22,7 @@ struct TapeStep {
   bool accumulate;
   bool mesh;                // the rays were kicked on the ray mesh ...
   hrt_raymesh_config mesh_cfg;  // ... of this configuration
+  bool tiled;               // through the light cone tiled by the tape's replicas
 };
 
 // State before a step, kept every `every` steps.
@@ -44,6 +45,7 @@ struct Tape {
   int rays_start = -1;          // index of the first step with rays
   std::vector<TapeStep> steps;
   std::map<int, TapeCheckpoint> checkpoints;
+  std::vector<int32_t> rep_perm, rep_sign, rep_shift;  // replicas of the tiled steps
 };
 
 void device_free(void* p, cudaStream_t s);

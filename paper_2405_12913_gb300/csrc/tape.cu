@@ -84,6 +84,9 @@ void tape_clear(Tape& t, cudaStream_t s) {
   }
   t.checkpoints.clear();
   t.steps.clear();
+  t.rep_perm.clear();
+  t.rep_sign.clear();
+  t.rep_shift.clear();
   t.valid = false;
   t.invalid_why = "no initial conditions from white noise recorded";
   t.n_rays = 0;
@@ -163,9 +166,24 @@ hrt_status tape_on_step(hrt_ctx* ctx, char kind, double a_next, int slot, double
     tape_invalidate(ctx, "a ray step ran with rays not initialised after the recorded ICs");
     return HRT_OK;
   }
-  if (kind == 'R' && (!ctx->rep_perm.empty() || ctx->cfg.ray_fields != 0)) {
-    tape_invalidate(ctx, "the adjoint supports untiled ray steps on the particle fields only");
+  const bool tiled = kind == 'R' && !ctx->rep_perm.empty();
+  if (kind == 'R' && ctx->cfg.ray_fields != 0) {
+    tape_invalidate(ctx, "the adjoint supports ray steps on the particle fields only");
     return HRT_OK;
+  }
+  if (tiled && ctx->raymesh) {
+    tape_invalidate(ctx, "the ray-mesh kick through a tiled light cone has no adjoint");
+    return HRT_OK;
+  }
+  if (tiled) {
+    if (t.rep_perm.empty()) {
+      t.rep_perm = ctx->rep_perm;
+      t.rep_sign = ctx->rep_sign;
+      t.rep_shift = ctx->rep_shift;
+    } else if (t.rep_perm != ctx->rep_perm || t.rep_sign != ctx->rep_sign || t.rep_shift != ctx->rep_shift) {
+      tape_invalidate(ctx, "the light-cone replicas changed during the recorded run");
+      return HRT_OK;
+    }
   }
   const int idx = static_cast<int>(t.steps.size());
   if (idx % t.every == 0) {
@@ -187,7 +205,7 @@ hrt_status tape_on_step(hrt_ctx* ctx, char kind, double a_next, int slot, double
     }
     t.checkpoints[idx] = c;
   }
-  TapeStep st{kind, ctx->a, a_next, ctx->a_mom, slot, weight, accumulate, ctx->raymesh != nullptr, {}};
+  TapeStep st{kind, ctx->a, a_next, ctx->a_mom, slot, weight, accumulate, ctx->raymesh != nullptr, {}, tiled};
   if (ctx->raymesh) st.mesh_cfg = raymesh_config_of(ctx->raymesh);
   t.steps.push_back(st);
   return HRT_OK;
@@ -241,6 +259,13 @@ hrt_status tape_adjoint(hrt_ctx* ctx, const float* kappa_bar, const double* thet
   const int n_steps = static_cast<int>(t.steps.size()), k = t.every;
   const hrt_filter f = ctx_filter(cfg, false);
   const hrt_ray_geom geom = ctx_geom(cfg, nullptr);
+  hrt_ray_geom geom_tiled = geom;
+  if (!t.rep_perm.empty()) {
+    geom_tiled.n_replicas = static_cast<int32_t>(t.rep_perm.size() / 3);
+    geom_tiled.replica_perm = t.rep_perm.data();
+    geom_tiled.replica_sign = t.rep_sign.data();
+    geom_tiled.replica_shift = t.rep_shift.data();
+  }
   Cosmo cosmo(om);
   auto pref = [&](double a) { return 1.5 * om / a; };
 
@@ -309,6 +334,9 @@ hrt_status tape_adjoint(hrt_ctx* ctx, const float* kappa_bar, const double* thet
         hrt_raymesh* rm;
         HRT_TRY(meshes.get(step.mesh_cfg, &rm));
         HRT_TRY(hrt_raymesh_ray_step(rm, &st.rays, st.g, st.g + m, &geom, chi0, chi1, step.a_x, om, nullptr, s));
+      } else if (step.tiled) {
+        HRT_TRY(hrt_ray_step_tiled(&st.rays, st.g, st.g + m, st.g + 2 * m, &geom_tiled, chi0, chi1, step.a_x, om,
+                                   nullptr, s));
       } else {
         HRT_TRY(hrt_ray_step(&st.rays, st.g, st.g + m, &geom, chi0, chi1, step.a_x, om, nullptr, s));
       }
@@ -373,6 +401,10 @@ hrt_status tape_adjoint(hrt_ctx* ctx, const float* kappa_bar, const double* thet
           HRT_TRY(hrt_raymesh_ray_step_adjoint(rm, &p.rays, p.g, p.g + m, &geom, chi0, chi1, step.a_x, om, &r_bar,
                                                g_bar, g_bar + m, plane_bar.data() + 1024 * static_cast<size_t>(i),
                                                &mesh_drift_bar[i], s));
+        } else if (step.tiled) {
+          HRT_TRY(hrt_ray_step_tiled_adjoint(&p.rays, p.g, p.g + m, p.g + 2 * m, &geom_tiled, chi0, chi1, step.a_x,
+                                             om, &r_bar, g_bar, g_bar + m, g_bar + 2 * m,
+                                             node_bar + 3 * kMaxRayNodes * static_cast<size_t>(i), drift_bar + i, s));
         } else {
           HRT_TRY(hrt_ray_step_adjoint(&p.rays, p.g, p.g + m, &geom, chi0, chi1, step.a_x, om, &r_bar, g_bar,
                                        g_bar + m, node_bar + 3 * kMaxRayNodes * static_cast<size_t>(i),
@@ -458,7 +490,7 @@ hrt_status tape_adjoint(hrt_ctx* ctx, const float* kappa_bar, const double* thet
         cw[sgn].assign(kMaxRayNodes, 0.0);
         cwr[sgn].assign(kMaxRayNodes, 0.0);
         chi[sgn].assign(kMaxRayNodes, 0.0);
-        HRT_TRY(hrt_ray_step_coefficients(&geom, c.chi(step.a_x), c.chi(step.a_next), step.a_x, oms[sgn], &n1[sgn],
+        HRT_TRY(hrt_ray_step_coefficients(step.tiled ? &geom_tiled : &geom, c.chi(step.a_x), c.chi(step.a_next), step.a_x, oms[sgn], &n1[sgn],
                                           &n2[sgn], cw[sgn].data(), cwr[sgn].data(), chi[sgn].data(), &dd[sgn]));
       }
       if (n1[0] + n2[0] != n1[1] + n2[1])

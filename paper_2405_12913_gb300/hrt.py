@@ -132,6 +132,7 @@ _SIGS = {
     "hrt_particle_kick_drift_adjoint": ([_P, _I64, _D, _I64, _P, _P, _D, _D, _P, _P, _P, _P, _P, _P], C.c_int),
     "hrt_pm_solve_adjoint": ([_P, _P, _D, _P, _P, _P, _P], C.c_int),
     "hrt_ray_step_adjoint": ([_P, _P, _P, _P, _D, _D, _D, _D, _P, _P, _P, _P, _P, _P], C.c_int),
+    "hrt_ray_step_tiled_adjoint": ([_P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "hrt_ray_step_coefficients": ([_P, _D, _D, _D, _D, _P, _P, _P, _P, _P, _P], C.c_int),
     "hrt_kappa_power_adjoint": ([_P, _I64, _D, _I32, _D, _D, _P, _P, _P], C.c_int),
     "hrt_ic_table": ([_I64, _D, _P, _D, _P, _P], C.c_int),
@@ -560,6 +561,19 @@ def hrt_ray_step_adjoint(rays: RayState, grad_x, grad_y, geom, chi_from, chi_to,
                                      _ptr(gy_bar, torch.float32, "gy_bar"), _ptr(node_bar, torch.float64, "node_bar"),
                                      _ptr(drift_bar, torch.float64, "drift_bar"), _stream(stream)),
            "hrt_ray_step_adjoint")
+
+
+def hrt_ray_step_tiled_adjoint(rays: RayState, grad, geom, chi_from, chi_to, a_ref, omega_m, bar: RayState, grad_bar,
+                               node_bar, drift_bar, stream=None):
+    """Tiled ray-step adjoint; grad and grad_bar hold the three fields [3][n^3]."""
+    r, b = rays.c(), bar.c()
+    g, gb = grad.reshape(3, -1), grad_bar.reshape(3, -1)
+    _check(_lib.hrt_ray_step_tiled_adjoint(C.byref(r), _ptr(g[0], torch.float32, "grad_x"), _ptr(g[1], torch.float32, "grad_y"),
+                                           _ptr(g[2], torch.float32, "grad_z"), C.byref(geom), chi_from, chi_to, a_ref,
+                                           omega_m, C.byref(b), _ptr(gb[0], torch.float32, "gx_bar"),
+                                           _ptr(gb[1], torch.float32, "gy_bar"), _ptr(gb[2], torch.float32, "gz_bar"),
+                                           _ptr(node_bar, torch.float64, "node_bar"), _ptr(drift_bar, torch.float64, "drift_bar"),
+                                           _stream(stream)), "hrt_ray_step_tiled_adjoint")
 
 
 def hrt_ray_step_coefficients(geom, chi_from, chi_to, a_ref, omega_m):

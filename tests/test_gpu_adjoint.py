@@ -154,6 +154,48 @@ def test_ray_step_adjoint_matches_autograd(hrt, a_ref, c0, c1):
     _close(gyb.cpu().numpy(), fy.grad.numpy().reshape(-1), 2e-4)
 
 
+@pytest.mark.parametrize("seed", [3, 4])
+def test_tiled_ray_step_adjoint_matches_autograd(hrt, seed):
+    # a step across replica boundaries of a light cone tiled by rotated, translated replicas
+    n, box, obs, s = 32, 64.0, (20.3, 41.7, 3.0), 1.0
+    reps = synthetic.replica_transforms(seed, 12, n)
+    g3 = [synthetic.gaussian_field(90 + seed + c, (n, n, n), 3e3) for c in range(3)]
+    theta0 = synthetic.pixel_grid(19, 0.25)
+    a_ref, c0, c1 = 0.75, 100.0, 150.0
+    wfn = osim.growth_weight(a_ref, 0.3)
+    gt = [torch.tensor(g) for g in g3]
+    pre = orays.ray_step(orays.init_state(torch.tensor(theta0)), gt[0], gt[1], box, obs, 60.0, c0, s, wfn, gz=gt[2],
+                         replicas=reps)
+    R = theta0.shape[0]
+    rays = hrt.RayState(R)
+    rays.theta.copy_(pre["theta"])
+    rays.eta.copy_(pre["eta"])
+    rays.A.copy_(pre["A"].reshape(R, 4))
+    rays.B.copy_(pre["B"].reshape(R, 4))
+    cot = {k: synthetic.gaussian_field(70 + i, v.shape) for i, (k, v) in enumerate(pre.items())}
+    cot["theta"] *= 1e3
+    bar = hrt.RayState(R)
+    bar.theta.copy_(torch.tensor(cot["theta"]))
+    bar.eta.copy_(torch.tensor(cot["eta"]))
+    bar.A.copy_(torch.tensor(cot["A"].reshape(R, 4)))
+    bar.B.copy_(torch.tensor(cot["B"].reshape(R, 4)))
+    gb = torch.zeros(3, n ** 3, device="cuda")
+    nb = torch.zeros(3, 1024, dtype=torch.float64, device="cuda")
+    drb = torch.zeros(1, dtype=torch.float64, device="cuda")
+    geom = hrt.make_geom(n, box, obs, s, replicas=reps)
+    hrt.hrt_ray_step_tiled_adjoint(rays, _cuda(np.stack(g3)), geom, c0, c1, a_ref, 0.3, bar, gb, nb, drb)
+    st = {k: v.clone().requires_grad_(True) for k, v in pre.items()}
+    f3 = [torch.tensor(g, requires_grad=True) for g in g3]
+    out = orays.ray_step(st, f3[0], f3[1], box, obs, c0, c1, s, wfn, gz=f3[2], replicas=reps)
+    sum((out[k] * torch.tensor(cot[k])).sum() for k in out).backward()
+    _close(bar.theta.cpu().numpy(), st["theta"].grad.numpy(), 2e-4)
+    _close(bar.eta.cpu().numpy(), st["eta"].grad.numpy(), 2e-4)
+    _close(bar.A.cpu().numpy(), st["A"].grad.numpy().reshape(R, 4), 2e-4)
+    _close(bar.B.cpu().numpy(), st["B"].grad.numpy().reshape(R, 4), 2e-4)
+    for c in range(3):
+        _close(gb[c].cpu().numpy(), f3[c].grad.numpy().reshape(-1), 2e-4)
+
+
 def test_kappa_power_adjoint_matches_autograd(hrt):
     m, dth, nb = 64, 4e-4, 8
     kap = synthetic.gaussian_field(60, (m, m), 0.02)
