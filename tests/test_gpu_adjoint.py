@@ -612,3 +612,64 @@ def test_context_adjoint_from_2lpt_ics_matches_central_differences(hrt):
     assert lo - 0.02 * abs(lo) <= ad <= hi + 0.02 * abs(hi), (ad, fds)
     assert np.isfinite(om_bar)
     ctx.close()
+
+
+@pytest.mark.parametrize("tiling", ["identity", "random"])
+def test_context_adjoint_through_a_tiled_light_cone(hrt, tiling):
+    """A recorded context run through a light cone tiled by 40 box replicas.  Replicas that neither rotate nor
+    shift the box tile it like the periodic images, so that run's gradients equal the untiled run's; random
+    rotations and shifts are checked against central differences of the same context run (their spread, as the
+    angles' derivative has kinks)."""
+    from paper_2405_12913_gb300.configs import COSMO_GRAD as W
+    k = 40
+    if tiling == "identity":
+        reps = (np.tile(np.arange(3, dtype=np.int32), (k, 1)), np.ones((k, 3), np.int32), np.zeros((k, 3), np.int32))
+    else:
+        reps = synthetic.replica_transforms(17, k, W.n_mesh)
+    noise = _cuda(synthetic.white_noise(W.seed + 6, W.n_side)).reshape(-1)
+    theta0 = torch.tensor(synthetic.pixel_grid(W.n_pix, W.fov_deg * synthetic.DEGREE)).cuda()
+    kbar = _cuda(synthetic.gaussian_field(85, (len(W.source_steps), W.n_rays)))
+    tb = _cuda(synthetic.gaussian_field(86, (W.n_rays, 2)), torch.float64) * 1e4
+    cfg = hrt.make_config(W.n_mesh, W.box, W.n_side, W.omega_m, W.h, W.n_s, W.sigma8, W.deconv_p, W.smooth_cells,
+                          W.samples_per_cell, W.observer, n_sources=len(W.source_steps))
+    slots = {s: i for i, s in enumerate(W.source_steps)}
+
+    def run(ctx, w):
+        ctx.hrt_init_particles_zeldovich(w, W.a_init)
+        for a in W.forward_grid[1:]:
+            ctx.hrt_step(a)
+        ctx.hrt_sync_particles()
+        ctx.hrt_init_rays(theta0)
+        for n, a in enumerate(W.reverse_grid[1:], start=1):
+            ctx.hrt_step(a, slots.get(n, -1))
+        kap = torch.stack([ctx.hrt_read_maps(i)[0] for i in range(len(W.source_steps))])
+        th = ctx.hrt_read_rays()[0]
+        return float((kap.double() * kbar.double()).sum() + ((th - theta0) * tb).sum())
+
+    def gradients(replicas):
+        ctx = hrt.Context(cfg)
+        ctx.hrt_set_checkpointing(2)
+        if replicas is not None:
+            ctx.hrt_set_replicas(replicas)
+        loss = run(ctx, noise)
+        nb, om_bar = ctx.hrt_adjoint(kbar.contiguous(), tb.contiguous())
+        return ctx, loss, nb.double(), om_bar
+
+    ctx, loss, nb, om_bar = gradients(reps)
+    assert np.isfinite(om_bar) and bool(torch.isfinite(nb).all())
+    if tiling == "identity":
+        ctx0, loss0, nb0, om0 = gradients(None)
+        ctx0.close()
+        assert loss == pytest.approx(loss0, rel=1e-4, abs=1e-6)
+        rel = float((nb - nb0).norm() / nb0.norm())
+        assert rel < 1e-3, rel
+        assert om_bar == pytest.approx(om0, rel=1e-3)
+    else:
+        direction = _cuda(synthetic.gaussian_field(87, (W.n_side ** 3,)))
+        ad = float((nb * direction.double()).sum())
+        fds = [(run(ctx, noise + e * direction) - run(ctx, noise - e * direction)) / (2 * e)
+               for e in (3e-4, 1e-3, 3e-3)]
+        lo, hi = min(fds), max(fds)
+        print("tiled context adjoint %.6g, central differences %s" % (ad, fds))
+        assert lo - 0.02 * abs(lo) <= ad <= hi + 0.02 * abs(hi), (ad, fds)
+    ctx.close()
