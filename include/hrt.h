@@ -517,7 +517,7 @@ hrt_status hrt_set_ray_correction(hrt_ctx* ctx, const float* params);
  * shift tables (host, copied); n = 0 removes it.  Needs ray_fields == 0 (HRT_ERR_STATE otherwise). */
 hrt_status hrt_set_replicas(hrt_ctx* ctx, int32_t n, const int32_t* perm, const int32_t* sign, const int32_t* shift);
 
-/* Adjoints of the ray-mesh kick (untiled geometries).  The mesh geometry (lambda_lim, x2d, N, the plane set) is
+/* Adjoints of the ray-mesh kick.  The mesh geometry (lambda_lim, x2d, N, the plane set) is
  * held fixed: derivatives are taken with respect to the fields, the ray state and the plane weights
  * w_p = -(2/c) chi_p g(chi_p) (+-cell) cell^2 / (chi_p^2 x2d^2), not with respect to the discretisation.
  *
@@ -539,6 +539,21 @@ hrt_status hrt_raymesh_ray_step_adjoint(hrt_raymesh* rm, const hrt_rays* rays, c
                                         const hrt_ray_geom* geom, double chi_from, double chi_to, double a_ref,
                                         double omega_m, const hrt_rays* bar, float* gx_bar, float* gy_bar,
                                         double* plane_bar_host, double* drift_bar_host, void* stream);
+
+/* The same two transposes through a tiled light cone (geom with n_replicas >= 1; the forwards are
+ * hrt_raymesh_kick_tiled and hrt_raymesh_ray_step_tiled).  A node of a plane in replica k was read from box
+ * field perm[k][a] with sign sign[k][a] for sky component a, at the replica's shifted box node, so its cotangent
+ * goes there: gx_bar, gy_bar and gz_bar (device [n^3] float32, all three required) accumulate the cotangents of
+ * the three box fields.  Other arguments and outputs as in the untiled calls. */
+hrt_status hrt_raymesh_kick_tiled_adjoint(hrt_raymesh* rm, const float* grad_x, const float* grad_y,
+                                          const float* grad_z, const float* mesh_bar, const hrt_ray_geom* geom,
+                                          double chi_a, double chi_b, double a_ref, double omega_m, float* gx_bar,
+                                          float* gy_bar, float* gz_bar, double* plane_bar_host, void* stream);
+hrt_status hrt_raymesh_ray_step_tiled_adjoint(hrt_raymesh* rm, const hrt_rays* rays, const float* grad_x,
+                                              const float* grad_y, const float* grad_z, const hrt_ray_geom* geom,
+                                              double chi_from, double chi_to, double a_ref, double omega_m,
+                                              const hrt_rays* bar, float* gx_bar, float* gy_bar, float* gz_bar,
+                                              double* plane_bar_host, double* drift_bar_host, void* stream);
 
 /* Host: the planes of a ray-mesh step, per half shell h the count n_h, chi_host[h * 512 + q] and the FP64
  * weight w_host[h * 512 + q], and the drift coefficient. */
@@ -565,9 +580,9 @@ hrt_status hrt_set_particle_sort(hrt_ctx* ctx, int32_t every);
  * float32 [n_side^3]) receives dL/dnoise and *omega_bar_host (or NULL) dL/dOmega_m.  It recomputes each
  * segment of k steps from its checkpoint (transient device memory: k pre-step states of particles, rays and
  * the three fields) and runs the adjoint calls above in reverse.  Supported: Zel'dovich or 2LPT ICs, ray steps
- * on the particle fields (ray_fields == 0) with the direct gather (also through a tiled light cone) or the
- * ray mesh (untiled); given initial particles, loaded states, static-lens steps, free drifts, ray fields, the
- * ray mesh through a tiled light cone and replicas changed during the run make the record unusable
+ * on the particle fields (ray_fields == 0) with the direct gather or the ray mesh, untiled or through a tiled
+ * light cone; given initial particles, loaded states, static-lens steps, free drifts, ray fields and replicas
+ * changed during the run make the record unusable
  * (HRT_ERR_STATE with the reason).  Synchronises the context's stream. */
 hrt_status hrt_set_checkpointing(hrt_ctx* ctx, int32_t every);
 hrt_status hrt_adjoint(hrt_ctx* ctx, const float* kappa_bar, const double* theta_bar, float* noise_bar,

@@ -407,14 +407,20 @@ __global__ void __launch_bounds__(256) raymesh_ray_adjoint_kernel(
   block_sum_add(db, drift_bar);
 }
 
-// Transpose of the projection (untiled): one thread per 3D node (i, j) of plane blockIdx.z.  It adds
-// w_p * S to the field cotangents, where S is the bilinear interpolation of the (filtered) mesh cotangent at the
-// node's projected angle, summed over the node's periodic images, and adds g . S to dL/dw_p.
+// Transpose of the projection: one thread per sky-frame 3D node (i, j) of plane blockIdx.z.  S is the bilinear
+// interpolation of the (filtered) mesh cotangent at the node's projected angle, summed over the node's periodic
+// images.  Untiled, the node is the box node and w_p S goes to the (x, y) field cotangents.  Tiled, the node lives
+// in the plane's replica: sky component a was read from box field perm(a) with sign s_a at the replica's box
+// node, so w_p s_a S_a goes to that field's cotangent there.  The dot product of the fields read with S adds to
+// dL/dw_p.
+template <bool TILED>
 __global__ void __launch_bounds__(256) raymesh_project_adjoint_kernel(const float* __restrict__ gx,
                                                                      const float* __restrict__ gy,
+                                                                     const float* __restrict__ gz,
                                                                      const __grid_constant__ ProjectParams p,
                                                                      const float2* __restrict__ mbar,
                                                                      float* __restrict__ gxb, float* __restrict__ gyb,
+                                                                     float* __restrict__ gzb,
                                                                      double* __restrict__ plane_bar) {
   const int q = blockIdx.z;
   const int i = blockIdx.y * kTileX + threadIdx.x / kTileY, j = blockIdx.x * kTileY + threadIdx.x % kTileY;
@@ -449,7 +455,19 @@ __global__ void __launch_bounds__(256) raymesh_project_adjoint_kernel(const floa
         }
       }
     }
-    if (sx != 0.f || sy != 0.f) {
+    if ((sx != 0.f || sy != 0.f) && TILED) {
+      const ReplicaMap& m = p.rmap[p.rep[q]];
+      const int64_t idx = box_index(i, m.sg_x, m.sh_x, n) * m.str_x + box_index(j, m.sg_y, m.sh_y, n) * m.str_y +
+                          box_index(p.kz[q], m.sg_z, m.sh_z, n) * m.str_z;
+      const float* fxp = m.c_x == 0 ? gx : (m.c_x == 1 ? gy : gz);
+      const float* fyp = m.c_y == 0 ? gx : (m.c_y == 1 ? gy : gz);
+      float* bxp = m.c_x == 0 ? gxb : (m.c_x == 1 ? gyb : gzb);
+      float* byp = m.c_y == 0 ? gxb : (m.c_y == 1 ? gyb : gzb);
+      const float tx = m.sg_x * sx, ty = m.sg_y * sy;
+      atomicAdd(bxp + idx, p.w[q] * tx);
+      atomicAdd(byp + idx, p.w[q] * ty);
+      part = static_cast<double>(__ldg(fxp + idx)) * tx + static_cast<double>(__ldg(fyp + idx)) * ty;
+    } else if (sx != 0.f || sy != 0.f) {
       const int64_t idx = (static_cast<int64_t>(i) * n + j) * n + p.kz[q];
       atomicAdd(gxb + idx, p.w[q] * sx);
       atomicAdd(gyb + idx, p.w[q] * sy);
@@ -699,14 +717,16 @@ static hrt_status ensure_bar(hrt_raymesh* rm, int h, int64_t elems, cudaStream_t
 }
 
 // Transpose of filter + projection for one half shell: mbar (filtered-mesh cotangent, overwritten) to the field
-// cotangents and dL/dw_p (device, per plane).
-static hrt_status shell_adjoint(hrt_raymesh* rm, const float* gx, const float* gy, const ProjectParams& p,
-                                float2* mbar, float* gxb, float* gyb, double* plane_bar, cudaStream_t s) {
+// cotangents and dL/dw_p (device, per plane); gz, gzb are read only through a tiled light cone.
+static hrt_status shell_adjoint(hrt_raymesh* rm, const float* gx, const float* gy, const float* gz,
+                                const ProjectParams& p, float2* mbar, float* gxb, float* gyb, float* gzb,
+                                double* plane_bar, cudaStream_t s) {
   if (p.n_planes == 0) return HRT_OK;
   HRT_TRY(filter_mesh(rm, mbar, p.n2d, s));
   const dim3 grid(static_cast<unsigned>((p.n + kTileY - 1) / kTileY), static_cast<unsigned>((p.n + kTileX - 1) / kTileX),
                   static_cast<unsigned>(p.n_planes));
-  raymesh_project_adjoint_kernel<<<grid, kTileX * kTileY, 0, s>>>(gx, gy, p, mbar, gxb, gyb, plane_bar);
+  auto* kernel = p.tiled ? raymesh_project_adjoint_kernel<true> : raymesh_project_adjoint_kernel<false>;
+  kernel<<<grid, kTileX * kTileY, 0, s>>>(gx, gy, gz, p, mbar, gxb, gyb, gzb, plane_bar);
   HRT_LAUNCHED("raymesh_project_adjoint_kernel");
   return HRT_OK;
 }
@@ -716,11 +736,13 @@ static hrt_status read_sums(hrt_raymesh* rm, double* host, size_t count, cudaStr
   return cuda_status(cudaStreamSynchronize(s), "adjoint sync");
 }
 
-static hrt_status kick_adjoint_call(hrt_raymesh* rm, const float* gx, const float* gy, const float* mesh_bar,
-                                    const hrt_ray_geom* geom, double chi_a, double chi_b, double a_ref,
-                                    double omega_m, float* gxb, float* gyb, double* plane_bar_host, void* stream) {
+static hrt_status kick_adjoint_call(hrt_raymesh* rm, const float* gx, const float* gy, const float* gz,
+                                    const float* mesh_bar, const hrt_ray_geom* geom, double chi_a, double chi_b,
+                                    double a_ref, double omega_m, float* gxb, float* gyb, float* gzb,
+                                    double* plane_bar_host, void* stream) {
   if (!rm || !gx || !gy || !mesh_bar || !gxb || !gyb) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
-  HRT_TRY(check_geom(geom, false));
+  if ((gz == nullptr) != (gzb == nullptr)) return fail(HRT_ERR_INVALID_ARG, "grad_z and gz_bar go together");
+  HRT_TRY(check_geom(geom, gz != nullptr));
   if (!(omega_m > 0.0 && omega_m <= 1.0)) return fail(HRT_ERR_INVALID_ARG, "omega_m must be in (0, 1]");
   cudaStream_t s = as_stream(stream);
   static thread_local ProjectParams p;
@@ -732,7 +754,7 @@ static hrt_status kick_adjoint_call(hrt_raymesh* rm, const float* gx, const floa
   HRT_TRY(cuda_status(cudaMemsetAsync(rm->acc, 0, (1 + 2 * kMaxMeshPlanes) * sizeof(double), s), "clear sums"));
   HRT_TRY(cuda_status(cudaMemcpyAsync(rm->mesh_bar[0], mesh_bar, static_cast<size_t>(n2d) * n2d * sizeof(float2),
                                       cudaMemcpyDeviceToDevice, s), "copy mesh cotangent"));
-  HRT_TRY(shell_adjoint(rm, gx, gy, p, rm->mesh_bar[0], gxb, gyb, rm->acc + 1, s));
+  HRT_TRY(shell_adjoint(rm, gx, gy, gz, p, rm->mesh_bar[0], gxb, gyb, gzb, rm->acc + 1, s));
   std::vector<double> h(1 + kMaxMeshPlanes);
   HRT_TRY(read_sums(rm, h.data(), h.size(), s));
   if (plane_bar_host)
@@ -741,22 +763,23 @@ static hrt_status kick_adjoint_call(hrt_raymesh* rm, const float* gx, const floa
 }
 
 static hrt_status step_adjoint_call(hrt_raymesh* rm, const hrt_rays* rays, const float* gx, const float* gy,
-                                    const hrt_ray_geom* geom, double chi_from, double chi_to, double a_ref,
-                                    double omega_m, const hrt_rays* bar, float* gxb, float* gyb,
-                                    double* plane_bar_host, double* drift_bar_host, void* stream) {
+                                    const float* gz, const hrt_ray_geom* geom, double chi_from, double chi_to,
+                                    double a_ref, double omega_m, const hrt_rays* bar, float* gxb, float* gyb,
+                                    float* gzb, double* plane_bar_host, double* drift_bar_host, void* stream) {
   if (!rm || !gx || !gy || !gxb || !gyb || !rays || !bar) return fail(HRT_ERR_INVALID_ARG, "NULL argument");
+  if ((gz == nullptr) != (gzb == nullptr)) return fail(HRT_ERR_INVALID_ARG, "grad_z and gz_bar go together");
   if (rays->n_rays < 0 || bar->n_rays != rays->n_rays ||
       (rays->n_rays > 0 && (!rays->theta || !rays->eta || !rays->A || !rays->B || !bar->theta || !bar->eta ||
                             !bar->A || !bar->B)))
     return fail(HRT_ERR_INVALID_ARG, "bad ray state or cotangent");
-  HRT_TRY(check_geom(geom, false));
+  HRT_TRY(check_geom(geom, gz != nullptr));
   if (!(omega_m > 0.0 && omega_m <= 1.0)) return fail(HRT_ERR_INVALID_ARG, "omega_m must be in (0, 1]");
   const double chi_mid = 0.5 * (chi_from + chi_to);
   if (!(chi_mid > 0.0)) return fail(HRT_ERR_INVALID_ARG, "shell midpoint must be at chi > 0");
   cudaStream_t s = as_stream(stream);
   RayMeshParams rp{};
-  HRT_TRY(build_mesh(rm, 0, gx, gy, nullptr, *geom, chi_from, chi_mid, a_ref, omega_m, s, rp.m[0]));
-  HRT_TRY(build_mesh(rm, 1, gx, gy, nullptr, *geom, chi_mid, chi_to, a_ref, omega_m, s, rp.m[1]));
+  HRT_TRY(build_mesh(rm, 0, gx, gy, gz, *geom, chi_from, chi_mid, a_ref, omega_m, s, rp.m[0]));
+  HRT_TRY(build_mesh(rm, 1, gx, gy, gz, *geom, chi_mid, chi_to, a_ref, omega_m, s, rp.m[1]));
   rp.drift_d = (chi_to - chi_from) / (kCLight * chi_mid * chi_mid);
   rp.drift = static_cast<float>(rp.drift_d);
   for (int h = 0; h < 2; ++h) {
@@ -783,7 +806,7 @@ static hrt_status step_adjoint_call(hrt_raymesh* rm, const hrt_rays* rays, const
     HRT_TRY(geometry(rm->cfg, lo[h], hi[h], geom->box / geom->n, lam, x2d, n2d));
     HRT_TRY(plane_table(*geom, lo[h], hi[h], a_ref, omega_m, x2d, n2d, p));
     counts[h] = p.n_planes;
-    HRT_TRY(shell_adjoint(rm, gx, gy, p, rm->mesh_bar[h], gxb, gyb, rm->acc + 1 + h * kMaxMeshPlanes, s));
+    HRT_TRY(shell_adjoint(rm, gx, gy, gz, p, rm->mesh_bar[h], gxb, gyb, gzb, rm->acc + 1 + h * kMaxMeshPlanes, s));
   }
   std::vector<double> sums(1 + 2 * kMaxMeshPlanes);
   HRT_TRY(read_sums(rm, sums.data(), sums.size(), s));
@@ -883,16 +906,35 @@ hrt_status hrt_raymesh_ray_step_tiled(hrt_raymesh* rm, const hrt_rays* rays, con
 hrt_status hrt_raymesh_kick_adjoint(hrt_raymesh* rm, const float* grad_x, const float* grad_y, const float* mesh_bar,
                                     const hrt_ray_geom* geom, double chi_a, double chi_b, double a_ref, double omega_m,
                                     float* gx_bar, float* gy_bar, double* plane_bar_host, void* stream) {
-  return kick_adjoint_call(rm, grad_x, grad_y, mesh_bar, geom, chi_a, chi_b, a_ref, omega_m, gx_bar, gy_bar,
-                           plane_bar_host, stream);
+  return kick_adjoint_call(rm, grad_x, grad_y, nullptr, mesh_bar, geom, chi_a, chi_b, a_ref, omega_m, gx_bar, gy_bar,
+                           nullptr, plane_bar_host, stream);
+}
+
+hrt_status hrt_raymesh_kick_tiled_adjoint(hrt_raymesh* rm, const float* grad_x, const float* grad_y,
+                                          const float* grad_z, const float* mesh_bar, const hrt_ray_geom* geom,
+                                          double chi_a, double chi_b, double a_ref, double omega_m, float* gx_bar,
+                                          float* gy_bar, float* gz_bar, double* plane_bar_host, void* stream) {
+  if (!grad_z || !gz_bar) return fail(HRT_ERR_INVALID_ARG, "the tiled adjoint needs grad_z and gz_bar");
+  return kick_adjoint_call(rm, grad_x, grad_y, grad_z, mesh_bar, geom, chi_a, chi_b, a_ref, omega_m, gx_bar, gy_bar,
+                           gz_bar, plane_bar_host, stream);
 }
 
 hrt_status hrt_raymesh_ray_step_adjoint(hrt_raymesh* rm, const hrt_rays* rays, const float* grad_x, const float* grad_y,
                                         const hrt_ray_geom* geom, double chi_from, double chi_to, double a_ref,
                                         double omega_m, const hrt_rays* bar, float* gx_bar, float* gy_bar,
                                         double* plane_bar_host, double* drift_bar_host, void* stream) {
-  return step_adjoint_call(rm, rays, grad_x, grad_y, geom, chi_from, chi_to, a_ref, omega_m, bar, gx_bar, gy_bar,
-                           plane_bar_host, drift_bar_host, stream);
+  return step_adjoint_call(rm, rays, grad_x, grad_y, nullptr, geom, chi_from, chi_to, a_ref, omega_m, bar, gx_bar,
+                           gy_bar, nullptr, plane_bar_host, drift_bar_host, stream);
+}
+
+hrt_status hrt_raymesh_ray_step_tiled_adjoint(hrt_raymesh* rm, const hrt_rays* rays, const float* grad_x,
+                                              const float* grad_y, const float* grad_z, const hrt_ray_geom* geom,
+                                              double chi_from, double chi_to, double a_ref, double omega_m,
+                                              const hrt_rays* bar, float* gx_bar, float* gy_bar, float* gz_bar,
+                                              double* plane_bar_host, double* drift_bar_host, void* stream) {
+  if (!grad_z || !gz_bar) return fail(HRT_ERR_INVALID_ARG, "the tiled adjoint needs grad_z and gz_bar");
+  return step_adjoint_call(rm, rays, grad_x, grad_y, grad_z, geom, chi_from, chi_to, a_ref, omega_m, bar, gx_bar,
+                           gy_bar, gz_bar, plane_bar_host, drift_bar_host, stream);
 }
 
 hrt_status hrt_raymesh_step_planes(const hrt_raymesh_config* cfg, const hrt_ray_geom* geom, double chi_from,

@@ -171,10 +171,6 @@ hrt_status tape_on_step(hrt_ctx* ctx, char kind, double a_next, int slot, double
     tape_invalidate(ctx, "the adjoint supports ray steps on the particle fields only");
     return HRT_OK;
   }
-  if (tiled && ctx->raymesh) {
-    tape_invalidate(ctx, "the ray-mesh kick through a tiled light cone has no adjoint");
-    return HRT_OK;
-  }
   if (tiled) {
     if (t.rep_perm.empty()) {
       t.rep_perm = ctx->rep_perm;
@@ -333,7 +329,11 @@ hrt_status tape_adjoint(hrt_ctx* ctx, const float* kappa_bar, const double* thet
       if (step.mesh) {
         hrt_raymesh* rm;
         HRT_TRY(meshes.get(step.mesh_cfg, &rm));
-        HRT_TRY(hrt_raymesh_ray_step(rm, &st.rays, st.g, st.g + m, &geom, chi0, chi1, step.a_x, om, nullptr, s));
+        if (step.tiled)
+          HRT_TRY(hrt_raymesh_ray_step_tiled(rm, &st.rays, st.g, st.g + m, st.g + 2 * m, &geom_tiled, chi0, chi1,
+                                             step.a_x, om, nullptr, s));
+        else
+          HRT_TRY(hrt_raymesh_ray_step(rm, &st.rays, st.g, st.g + m, &geom, chi0, chi1, step.a_x, om, nullptr, s));
       } else if (step.tiled) {
         HRT_TRY(hrt_ray_step_tiled(&st.rays, st.g, st.g + m, st.g + 2 * m, &geom_tiled, chi0, chi1, step.a_x, om,
                                    nullptr, s));
@@ -398,9 +398,14 @@ hrt_status tape_adjoint(hrt_ctx* ctx, const float* kappa_bar, const double* thet
         if (step.mesh) {
           hrt_raymesh* rm;
           HRT_TRY(meshes.get(step.mesh_cfg, &rm));
-          HRT_TRY(hrt_raymesh_ray_step_adjoint(rm, &p.rays, p.g, p.g + m, &geom, chi0, chi1, step.a_x, om, &r_bar,
-                                               g_bar, g_bar + m, plane_bar.data() + 1024 * static_cast<size_t>(i),
-                                               &mesh_drift_bar[i], s));
+          double* pb = plane_bar.data() + 1024 * static_cast<size_t>(i);
+          if (step.tiled)
+            HRT_TRY(hrt_raymesh_ray_step_tiled_adjoint(rm, &p.rays, p.g, p.g + m, p.g + 2 * m, &geom_tiled, chi0, chi1,
+                                                       step.a_x, om, &r_bar, g_bar, g_bar + m, g_bar + 2 * m, pb,
+                                                       &mesh_drift_bar[i], s));
+          else
+            HRT_TRY(hrt_raymesh_ray_step_adjoint(rm, &p.rays, p.g, p.g + m, &geom, chi0, chi1, step.a_x, om, &r_bar,
+                                                 g_bar, g_bar + m, pb, &mesh_drift_bar[i], s));
         } else if (step.tiled) {
           HRT_TRY(hrt_ray_step_tiled_adjoint(&p.rays, p.g, p.g + m, p.g + 2 * m, &geom_tiled, chi0, chi1, step.a_x,
                                              om, &r_bar, g_bar, g_bar + m, g_bar + 2 * m,

@@ -93,6 +93,9 @@ _SIGS = {
     "hrt_raymesh_kick_tiled": ([_P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
     "hrt_raymesh_kick_adjoint": ([_P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P, _P, _P], C.c_int),
     "hrt_raymesh_ray_step_adjoint": ([_P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P, _P, _P, _P, _P], C.c_int),
+    "hrt_raymesh_kick_tiled_adjoint": ([_P, _P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P, _P, _P, _P], C.c_int),
+    "hrt_raymesh_ray_step_tiled_adjoint": ([_P, _P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P, _P, _P, _P, _P, _P],
+                                           C.c_int),
     "hrt_raymesh_step_planes": ([_P, _P, _D, _D, _D, _D, _P, _P, _P, _P, _P], C.c_int),
     "hrt_raymesh_ray_step_tiled": ([_P, _P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P], C.c_int),
     "hrt_set_ray_mesh": ([_P, _P], C.c_int),
@@ -464,32 +467,46 @@ class RayMesh:
 
     def hrt_raymesh_kick_adjoint(self, grad_x, grad_y, mesh_bar: torch.Tensor, geom: hrt_ray_geom, chi_a: float,
                                  chi_b: float, a_ref: float, omega_m: float, gx_bar: torch.Tensor, gy_bar: torch.Tensor,
-                                 stream=None):
-        """Accumulates dL/dgrad into gx_bar, gy_bar; returns dL/dw_p of the shell's planes (numpy)."""
+                                 stream=None, grad_z=None, gz_bar=None):
+        """Accumulates dL/dgrad into gx_bar, gy_bar (and gz_bar through a tiled light cone, with grad_z); returns
+        dL/dw_p of the shell's planes (numpy)."""
         import numpy as np
         pb = np.zeros(512)
-        _check(_lib.hrt_raymesh_kick_adjoint(self._h, _ptr(grad_x, torch.float32, "grad_x"),
-                                             _ptr(grad_y, torch.float32, "grad_y"),
-                                             _ptr(mesh_bar, torch.float32, "mesh_bar"), C.byref(geom), chi_a, chi_b,
-                                             a_ref, omega_m, _ptr(gx_bar, torch.float32, "gx_bar"),
-                                             _ptr(gy_bar, torch.float32, "gy_bar"), pb.ctypes.data, _stream(stream)),
-               "hrt_raymesh_kick_adjoint")
+        gx, gy = _ptr(grad_x, torch.float32, "grad_x"), _ptr(grad_y, torch.float32, "grad_y")
+        mb = _ptr(mesh_bar, torch.float32, "mesh_bar")
+        gxb, gyb = _ptr(gx_bar, torch.float32, "gx_bar"), _ptr(gy_bar, torch.float32, "gy_bar")
+        if grad_z is None:
+            _check(_lib.hrt_raymesh_kick_adjoint(self._h, gx, gy, mb, C.byref(geom), chi_a, chi_b, a_ref, omega_m,
+                                                 gxb, gyb, pb.ctypes.data, _stream(stream)), "hrt_raymesh_kick_adjoint")
+        else:
+            _check(_lib.hrt_raymesh_kick_tiled_adjoint(self._h, gx, gy, _ptr(grad_z, torch.float32, "grad_z"), mb,
+                                                       C.byref(geom), chi_a, chi_b, a_ref, omega_m, gxb, gyb,
+                                                       _ptr(gz_bar, torch.float32, "gz_bar"), pb.ctypes.data,
+                                                       _stream(stream)), "hrt_raymesh_kick_tiled_adjoint")
         return pb
 
     def hrt_raymesh_ray_step_adjoint(self, rays: RayState, grad_x, grad_y, geom: hrt_ray_geom, chi_from: float,
                                      chi_to: float, a_ref: float, omega_m: float, bar: RayState, gx_bar, gy_bar,
-                                     stream=None):
-        """bar: post-step cotangent in, pre-step cotangent out; returns (dL/dw [2][512] numpy, dL/d drift)."""
+                                     stream=None, grad_z=None, gz_bar=None):
+        """bar: post-step cotangent in, pre-step cotangent out; returns (dL/dw [2][512] numpy, dL/d drift).  With
+        grad_z and gz_bar: through a tiled light cone."""
         import numpy as np
         pb = np.zeros(2 * 512)
         db = np.zeros(1)
         r, b = rays.c(), bar.c()
-        _check(_lib.hrt_raymesh_ray_step_adjoint(self._h, C.byref(r), _ptr(grad_x, torch.float32, "grad_x"),
-                                                 _ptr(grad_y, torch.float32, "grad_y"), C.byref(geom), chi_from,
-                                                 chi_to, a_ref, omega_m, C.byref(b),
-                                                 _ptr(gx_bar, torch.float32, "gx_bar"),
-                                                 _ptr(gy_bar, torch.float32, "gy_bar"), pb.ctypes.data, db.ctypes.data,
-                                                 _stream(stream)), "hrt_raymesh_ray_step_adjoint")
+        gx, gy = _ptr(grad_x, torch.float32, "grad_x"), _ptr(grad_y, torch.float32, "grad_y")
+        gxb, gyb = _ptr(gx_bar, torch.float32, "gx_bar"), _ptr(gy_bar, torch.float32, "gy_bar")
+        if grad_z is None:
+            _check(_lib.hrt_raymesh_ray_step_adjoint(self._h, C.byref(r), gx, gy, C.byref(geom), chi_from, chi_to,
+                                                     a_ref, omega_m, C.byref(b), gxb, gyb, pb.ctypes.data,
+                                                     db.ctypes.data, _stream(stream)), "hrt_raymesh_ray_step_adjoint")
+        else:
+            _check(_lib.hrt_raymesh_ray_step_tiled_adjoint(self._h, C.byref(r), gx, gy,
+                                                           _ptr(grad_z, torch.float32, "grad_z"), C.byref(geom),
+                                                           chi_from, chi_to, a_ref, omega_m, C.byref(b), gxb, gyb,
+                                                           _ptr(gz_bar, torch.float32, "gz_bar"), pb.ctypes.data,
+                                                           db.ctypes.data, _stream(stream)),
+                   "hrt_raymesh_ray_step_tiled_adjoint")
         return pb.reshape(2, 512), float(db[0])
 
     def close(self):

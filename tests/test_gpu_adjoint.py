@@ -614,12 +614,13 @@ def test_context_adjoint_from_2lpt_ics_matches_central_differences(hrt):
     ctx.close()
 
 
+@pytest.mark.parametrize("mesh", [False, True])
 @pytest.mark.parametrize("tiling", ["identity", "random"])
-def test_context_adjoint_through_a_tiled_light_cone(hrt, tiling):
-    """A recorded context run through a light cone tiled by 40 box replicas.  Replicas that neither rotate nor
-    shift the box tile it like the periodic images, so that run's gradients equal the untiled run's; random
-    rotations and shifts are checked against central differences of the same context run (their spread, as the
-    angles' derivative has kinks)."""
+def test_context_adjoint_through_a_tiled_light_cone(hrt, tiling, mesh):
+    """A recorded context run through a light cone tiled by 40 box replicas, with the direct gather or the ray
+    mesh.  Replicas that neither rotate nor shift the box tile it like the periodic images, so that run's
+    gradients equal the untiled run's; random rotations and shifts are checked against central differences of the
+    same context run (their spread, as the angles' derivative has kinks)."""
     from paper_2405_12913_gb300.configs import COSMO_GRAD as W
     k = 40
     if tiling == "identity":
@@ -649,6 +650,8 @@ def test_context_adjoint_through_a_tiled_light_cone(hrt, tiling):
     def gradients(replicas):
         ctx = hrt.Context(cfg)
         ctx.hrt_set_checkpointing(2)
+        if mesh:
+            ctx.hrt_set_ray_mesh(hrt.make_raymesh_config(0.5, 8.0, W.dtheta, W.n_pix))
         if replicas is not None:
             ctx.hrt_set_replicas(replicas)
         loss = run(ctx, noise)

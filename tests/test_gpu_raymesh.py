@@ -422,3 +422,113 @@ def test_raymesh_ray_step_adjoint_matches_oracle_derivative(hrt, case):
             kz = int(round((chi[h, q] + OBS[2]) / (BOX / N))) % N
             share = float((g64x[:, :, kz] * gbx[:, :, kz]).sum() + (g64y[:, :, kz] * gby[:, :, kz]).sum())
             assert abs(w[h, q] * pb[h, q] - share) <= 1e-4 * (abs(share) + 1e-30) + 1e-9 * float(np.abs(pb).max() * np.abs(w).max())
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_tiled_raymesh_kick_adjoint_is_the_transpose(hrt, seed):
+    """Through a tiled light cone: <kick(g), K_bar> = <g, kick^T(K_bar)> over the three box fields for half shells
+    that cross replica boundaries, sum_p w_p dL/dw_p = L, and with replicas that neither rotate nor shift the box
+    the transpose equals the untiled one (no cotangent on the z field)."""
+    g = torch.Generator().manual_seed(70 + seed)
+    g3 = [torch.randn(N, N, N, generator=g, dtype=torch.float64).float().cuda().reshape(-1) for _ in range(3)]
+    reps = synthetic.replica_transforms(seed, 12, N)
+    ident = (np.tile(np.arange(3, dtype=np.int32), (12, 1)), np.ones((12, 3), np.int32), np.zeros((12, 3), np.int32))
+    om, a_ref = 0.3, 0.8
+    cfg = hrt.make_raymesh_config(0.5, 8, 0.004, 40)
+    rm = hrt.RayMesh(cfg)
+    for ca, cb in ((110.3, 141.0), (141.0, 110.3), (250.2, 300.9)):
+        geom = hrt.make_geom(N, BOX, OBS, replicas=reps)
+        K = rm.hrt_raymesh_kick(g3[0], g3[1], geom, ca, cb, a_ref, om, grad_z=g3[2])
+        gen = torch.Generator(device="cuda").manual_seed(seed)
+        Kb = torch.randn(K.shape, generator=gen, device="cuda")
+        gb = [torch.zeros_like(g3[0]) for _ in range(3)]
+        pb = rm.hrt_raymesh_kick_adjoint(g3[0], g3[1], Kb, geom, ca, cb, a_ref, om, gb[0], gb[1], grad_z=g3[2],
+                                         gz_bar=gb[2])
+        torch.cuda.synchronize()
+        lhs = float((K.double() * Kb.double()).sum())
+        rhs = sum(float((g3[c].double() * gb[c].double()).sum()) for c in range(3))
+        assert abs(lhs - rhs) <= 1e-4 * abs(lhs), (ca, cb, lhs, rhs)
+        assert float(gb[2].abs().max()) > 0.0
+        planes = raymesh.shell_planes(ca, cb, BOX / N, OBS[2])
+        x2d = hrt.hrt_raymesh_geometry(cfg, ca, cb, BOX / N)[1]
+        wq = np.array([-(2.0 / C_LIGHT) * c * sim.growth_weight(a_ref, om)(c) * (1 if cb >= ca else -1) * (BOX / N) ** 3
+                       / (c * c * x2d ** 2) for _, c in planes])
+        assert abs(float((wq * pb[:len(planes)]).sum()) - lhs) <= 1e-4 * abs(lhs)
+        # identity replicas against the untiled transpose
+        gi = [torch.zeros_like(g3[0]) for _ in range(3)]
+        pbi = rm.hrt_raymesh_kick_adjoint(g3[0], g3[1], Kb, hrt.make_geom(N, BOX, OBS, replicas=ident), ca, cb, a_ref,
+                                          om, gi[0], gi[1], grad_z=g3[2], gz_bar=gi[2])
+        gu = [torch.zeros_like(g3[0]) for _ in range(2)]
+        pbu = rm.hrt_raymesh_kick_adjoint(g3[0], g3[1], Kb, hrt.make_geom(N, BOX, OBS), ca, cb, a_ref, om, gu[0], gu[1])
+        torch.cuda.synchronize()
+        for c in range(2):
+            assert float((gi[c] - gu[c]).abs().max()) <= 1e-5 * float(gu[c].abs().max())
+        assert float(gi[2].abs().max()) == 0.0
+        assert np.allclose(pbi, pbu, rtol=1e-5, atol=1e-12 * np.abs(pbu).max())
+    rm.close()
+
+
+@pytest.mark.parametrize("case", [0, 1])
+def test_tiled_raymesh_ray_step_adjoint_matches_oracle_derivative(hrt, case):
+    """The ray-mesh KDK step through a tiled light cone (a shell across a replica boundary): <bar_after, J v> from
+    central differences of the FP64 oracle step along a direction v of the state and the three fields, against
+    <J^T bar_after, v> from the GPU adjoint."""
+    ca, cb = ((110.3, 141.0), (141.0, 110.3))[case]
+    mu, m_pix, iota, p_min, a_ref, om = 0.004, 40, 0.5, 8, 0.8, 0.3
+    wfn = sim.growth_weight(a_ref, om)
+    reps = synthetic.replica_transforms(5 + case, 12, N)
+    g = torch.Generator().manual_seed(95 + case)
+    g3 = [3e3 * torch.randn(N, N, N, generator=g, dtype=torch.float64).float() for _ in range(3)]
+    rng = np.random.default_rng(96 + case)
+    n = 2048
+    half = 0.5 * m_pix * mu
+    th0 = torch.tensor(rng.uniform(-half, half, size=(n, 2)))
+    eta0 = torch.tensor(rng.normal(0, 2e-5, size=(n, 2))).float().double()
+    A0 = torch.tensor(rng.normal(0, 1, size=(n, 2, 2))).float().double()
+    B0 = torch.tensor(rng.normal(0, 1e-2, size=(n, 2, 2))).float().double()
+    shapes = (("theta", (n, 2)), ("eta", (n, 2)), ("A", (n, 2, 2)), ("B", (n, 2, 2)))
+    wb = {k: torch.tensor(rng.normal(0, 1, size=s)) for k, s in shapes}
+    wb["theta"] *= 1e3
+    v = {k: torch.tensor(rng.normal(0, 1, size=s)) for k, s in shapes}
+    v["theta"] *= 1e-6
+    v["eta"] *= 1e-3
+    vg = [torch.tensor(rng.normal(0, 1, size=(N, N, N))) * 30.0 for _ in range(3)]
+
+    def L(eps, part):
+        st = dict(theta=th0.clone(), eta=eta0.clone(), A=A0.clone(), B=B0.clone())
+        ge = [x.double() for x in g3]
+        if part == "g":
+            ge = [ge[c] + eps * vg[c] for c in range(3)]
+        else:
+            st[part] = st[part] + eps * v[part]
+        out = raymesh.ray_step(st, ge[0], ge[1], BOX, OBS, ca, cb, wfn, mu, m_pix, iota, p_min, gz=ge[2],
+                               replicas=reps)
+        return sum(float((wb[k] * out[k]).sum()) for k in wb)
+
+    eps = 1e-4
+    jvp = {part: (L(eps, part) - L(-eps, part)) / (2 * eps) for part in ("theta", "eta", "A", "B", "g")}
+
+    rays = hrt.RayState(n)
+    rays.theta.copy_(th0.cuda())
+    rays.eta.copy_(eta0.float().cuda())
+    rays.A.copy_(A0.reshape(n, 4).float().cuda())
+    rays.B.copy_(B0.reshape(n, 4).float().cuda())
+    bar = hrt.RayState(n)
+    bar.theta.copy_(wb["theta"].cuda())
+    bar.eta.copy_(wb["eta"].float().cuda())
+    bar.A.copy_(wb["A"].reshape(n, 4).float().cuda())
+    bar.B.copy_(wb["B"].reshape(n, 4).float().cuda())
+    gd = [x.cuda().reshape(-1) for x in g3]
+    gb = [torch.zeros_like(gd[0]) for _ in range(3)]
+    rm = hrt.RayMesh(hrt.make_raymesh_config(iota, p_min, mu, m_pix))
+    geom = hrt.make_geom(N, BOX, OBS, replicas=reps)
+    rm.hrt_raymesh_ray_step_adjoint(rays, gd[0], gd[1], geom, ca, cb, a_ref, om, bar, gb[0], gb[1], grad_z=gd[2],
+                                    gz_bar=gb[2])
+    torch.cuda.synchronize()
+    rm.close()
+    vjp = {"theta": float((bar.theta.cpu() * v["theta"]).sum()), "eta": float((bar.eta.double().cpu() * v["eta"]).sum()),
+           "A": float((bar.A.double().cpu().reshape(n, 2, 2) * v["A"]).sum()),
+           "B": float((bar.B.double().cpu().reshape(n, 2, 2) * v["B"]).sum()),
+           "g": sum(float((gb[c].double().cpu() * vg[c].reshape(-1)).sum()) for c in range(3))}
+    for part in jvp:
+        assert abs(vjp[part] - jvp[part]) <= 2e-3 * abs(jvp[part]), (part, vjp[part], jvp[part])
