@@ -89,6 +89,32 @@ def sinc(x: torch.Tensor) -> torch.Tensor:
     return torch.where(x == 0, torch.ones_like(x), torch.sin(safe) / safe)
 
 
+def gradient_multipliers(nx: torch.Tensor, ny: torch.Tensor, nz: torch.Tensor, n_mesh: int, box: float, pref: float,
+                         deconv_p: float, smooth: float = 0.0, g_of_k=None) -> list[torch.Tensor]:
+    """The factors that map the density spectrum to the spectra of (d_x phi, d_y phi, d_z phi) at integer
+    wavevectors (nx, ny, nz) (signed tensors, broadcastable; Sec. 2 Poisson equation):
+    i d_j(k) G(k) W(k) [g(|k|)], with G = -pref / k^2 (0 at k = 0), the per-axis deconvolution
+    W = prod_i sinc(k_i cell / 2)^(-p) times exp(-k^2 smooth^2 / 2), and d_j = k_j except 0 on a Nyquist plane
+    |n_j| = n_mesh / 2 (a real output)."""
+    cell = box / n_mesh
+    kf = 2.0 * math.pi / box
+    kx, ky, kz = kf * nx.double(), kf * ny.double(), kf * nz.double()
+    k2 = kx * kx + ky * ky + kz * kz
+    green = torch.where(k2 > 0, -pref / torch.where(k2 > 0, k2, torch.ones_like(k2)), torch.zeros_like(k2))
+    window = (sinc(kx * cell / 2) * sinc(ky * cell / 2) * sinc(kz * cell / 2)) ** (-deconv_p)
+    if smooth > 0.0:
+        window = window * torch.exp(-0.5 * k2 * smooth * smooth)
+    phi = green * window
+    if g_of_k is not None:
+        phi = phi * g_of_k(torch.sqrt(k2))
+    half = n_mesh // 2
+    out = []
+    for kj, nj in ((kx, nx), (ky, ny), (kz, nz)):
+        d = torch.where(nj.abs() == half, torch.zeros_like(kj), kj)
+        out.append(phi * (1j * d))
+    return out
+
+
 def poisson_gradient_hat(rho_hat: torch.Tensor, box: float, pref: float, deconv_p: float,
                          smooth: float = 0.0, g_of_k=None) -> list[torch.Tensor]:
     """Three gradient spectra (d_x phi, d_y phi, d_z phi) from the half spectrum of rho (any k = 0 value).
@@ -97,25 +123,24 @@ def poisson_gradient_hat(rho_hat: torch.Tensor, box: float, pref: float, deconv_
     on |k| (tensor) returning a multiplicative correction of the Green's function (the learned force
     correction of the ray fields)."""
     n_mesh = rho_hat.shape[0]
-    cell = box / n_mesh
-    kf = 2.0 * math.pi / box
     nx, ny, nz = _wavevectors(n_mesh, box)
-    kx, ky, kz = kf * nx.double(), kf * ny.double(), kf * nz.double()
-    k2 = kx * kx + ky * ky + kz * kz
-    green = torch.where(k2 > 0, -pref / torch.where(k2 > 0, k2, torch.ones_like(k2)), torch.zeros_like(k2))
-    window = (sinc(kx * cell / 2) * sinc(ky * cell / 2) * sinc(kz * cell / 2)) ** (-deconv_p)
-    if smooth > 0.0:
-        window = window * torch.exp(-0.5 * k2 * smooth * smooth)
-    phi_hat = rho_hat * (green * window)
-    if g_of_k is not None:
-        phi_hat = phi_hat * g_of_k(torch.sqrt(k2))
-    out = []
-    half = n_mesh // 2
-    for kj, nj, last in ((kx, nx, False), (ky, ny, False), (kz, nz, True)):
-        nyq = (nj == half) if last else (nj == -half)
-        d = torch.where(nyq, torch.zeros_like(kj), kj)
-        out.append(phi_hat * (1j * d))
-    return out
+    return [rho_hat * m for m in gradient_multipliers(nx, ny, nz, n_mesh, box, pref, deconv_p, smooth, g_of_k)]
+
+
+def mode_gradient(modes: np.ndarray, amp: np.ndarray, phase: np.ndarray, flat_idx: np.ndarray, n_mesh: int,
+                  box: float, pref: float, deconv_p: float, smooth: float = 0.0) -> list[np.ndarray]:
+    """The gradient fields of poisson_gradient at single mesh nodes, for a density made of cosine modes
+    rho = const + sum_m a_m cos(2 pi (m . x) / n + phi_m) with no Nyquist component: each mode's spectrum sits
+    at +m and -m, where the multipliers are complex conjugates, so its gradient at node x is
+    Re(a_m M_j(m) exp(i (2 pi (m . x) / n + phi_m))).  Nodes are flat indices (i n + j) n + k; returns
+    [d_x phi, d_y phi, d_z phi] at them (float64)."""
+    m = torch.as_tensor(np.asarray(modes, dtype=np.int64))
+    mult = gradient_multipliers(m[:, 0], m[:, 1], m[:, 2], n_mesh, box, pref, deconv_p, smooth)
+    idx = np.asarray(flat_idx, dtype=np.int64)
+    i, j, k = idx // (n_mesh * n_mesh), (idx // n_mesh) % n_mesh, idx % n_mesh
+    t = (np.outer(i, m[:, 0].numpy()) + np.outer(j, m[:, 1].numpy()) + np.outer(k, m[:, 2].numpy())) % n_mesh
+    e = np.exp(1j * (2.0 * math.pi * t / n_mesh + np.asarray(phase)[None, :]))
+    return [np.real(e @ (np.asarray(amp) * mj.numpy())) for mj in mult]
 
 
 def poisson_gradient(rho: torch.Tensor, box: float, pref: float, deconv_p: float, smooth: float = 0.0,

@@ -101,3 +101,58 @@ def replica_transforms(seed: int, n_replicas: int, n_mesh: int):
         sign[k] = (s[0], s[1], parity[i] * s[0] * s[1])
     shift = rng.integers(0, n_mesh, size=(n_replicas, 3)).astype(np.int32)
     return perm, sign, shift
+
+
+def mode_spec(seed: int, n: int, n_modes: int, scale: float) -> dict:
+    """A real periodic field on an ``n^3`` mesh made of cosine modes,
+    ``f(i, j, k) = sum_m a_m cos(2 pi (m . (i, j, k)) / n + phi_m)``: integer mode vectors whose largest component
+    spreads geometrically from 1 to ``n/2 - 1`` (no zero mode, no Nyquist component), amplitudes ``scale N(0, 1)``,
+    phases uniform in ``[0, 2 pi)``.  Evaluate with ``mode_field_values`` or ``mode_field_device``."""
+    rng = np.random.default_rng(seed)
+    top = n // 2 - 1
+    modes = []
+    for t in np.geomspace(1.0, top, n_modes):
+        m = np.round(rng.uniform(-1.0, 1.0, size=3) * t).astype(np.int64)
+        m[rng.integers(3)] = int(round(t)) * (1 if rng.random() < 0.5 else -1)
+        modes.append(np.clip(m, -top, top))
+    return dict(modes=np.array(modes, dtype=np.int64), amp=scale * rng.standard_normal(n_modes),
+                phase=rng.uniform(0.0, 2.0 * np.pi, n_modes))
+
+
+def mode_field_values(spec: dict, n: int, flat_idx: np.ndarray) -> np.ndarray:
+    """The mode field (float64) at flat mesh indices ``(i n + j) n + k``; the phase index ``m . (i, j, k) mod n`` is
+    formed in integers."""
+    idx = np.asarray(flat_idx, dtype=np.int64)
+    i, j, k = idx // (n * n), (idx // n) % n, idx % n
+    out = np.zeros(idx.shape, dtype=np.float64)
+    for m, a, ph in zip(spec["modes"], spec["amp"], spec["phase"]):
+        t = (m[0] * i + m[1] * j + m[2] * k) % n
+        out += a * np.cos(2.0 * np.pi * t / n + ph)
+    return out
+
+
+def mode_field_device(spec: dict, n: int, device, slab: int = 32):
+    """The mode field on the whole mesh as a float32 torch tensor ``(n, n, n)`` on ``device``, built in float64
+    ``slab`` x-planes at a time (the same values as ``mode_field_values``, rounded to float32)."""
+    import torch
+    out = torch.empty(n, n, n, dtype=torch.float32, device=device)
+    jj = torch.arange(n, dtype=torch.int64, device=device).view(1, -1, 1)
+    kk = torch.arange(n, dtype=torch.int64, device=device).view(1, 1, -1)
+    for x0 in range(0, n, slab):
+        ii = torch.arange(x0, min(n, x0 + slab), dtype=torch.int64, device=device).view(-1, 1, 1)
+        acc = torch.zeros(ii.shape[0], n, n, dtype=torch.float64, device=device)
+        for m, a, ph in zip(spec["modes"], spec["amp"], spec["phase"]):
+            t = (int(m[0]) * ii + int(m[1]) * jj + int(m[2]) * kk) % n
+            acc += float(a) * torch.cos(t.double() * (2.0 * np.pi / n) + float(ph))
+        out[x0:x0 + ii.shape[0]] = acc.float()
+    return out
+
+
+def bounded_particle_state(seed: int, n_side: int, disp_max: float, mom_max: float):
+    """Displacements and momenta uniform in ``[-disp_max, disp_max]`` and ``[-mom_max, mom_max]`` per component for
+    an ``n_side^3`` lattice, float32 SoA ``(3, n_side^3)`` each (bounded, so that a particle's reach is known)."""
+    rng = np.random.default_rng(seed)
+    n = n_side ** 3
+    disp = (2.0 * rng.random((3, n), dtype=np.float32) - 1.0) * np.float32(disp_max)
+    mom = (2.0 * rng.random((3, n), dtype=np.float32) - 1.0) * np.float32(mom_max)
+    return disp, mom

@@ -251,3 +251,20 @@ def test_lpt_second_order_is_quadratic_and_eds_assembly():
     assert np.allclose(mom.numpy(), (a * a * e * (a * psi1 + 2.0 * (-3.0 / 7.0) * a * a * psi2)).numpy(), rtol=1e-10,
                        atol=1e-14)
     assert np.abs(psi2.numpy()).max() > 0
+
+
+def test_mode_gradient_matches_the_grid_solve():
+    # the gradient of a cosine-mode density at single nodes (used for spot checks of full-size meshes) against the
+    # FFT solve of the same density on the whole mesh, with deconvolution, smoothing and a mode that reaches the
+    # largest non-Nyquist frequency on one axis
+    n, box, pref = 16, 40.0, 0.7
+    spec = synthetic.mode_spec(3, n, 6, 1.0)
+    assert int(np.abs(spec["modes"]).max()) == n // 2 - 1
+    rho = 1.0 + synthetic.mode_field_values(spec, n, np.arange(n ** 3)).reshape(n, n, n)
+    grid = pm.poisson_gradient(torch.tensor(rho), box, pref, 4.0, 0.8 * box / n)
+    idx = np.arange(n ** 3)
+    want = pm.mode_gradient(spec["modes"], spec["amp"], spec["phase"], idx, n, box, pref, 4.0, 0.8 * box / n)
+    for j in range(3):
+        g = grid[j].reshape(-1).numpy()
+        assert np.abs(g - want[j]).max() <= 1e-12 * np.abs(g).max()
+        assert np.abs(g).max() > 0.0
