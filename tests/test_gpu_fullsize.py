@@ -158,10 +158,13 @@ def test_ray_step_at_the_full_size(hrt, W):
     d_eta_o, d_B_o = want["eta"] - e0, want["B"] - b0
     assert float(d_eta_o.abs().max()) > 1e-7 and float(d_B_o.abs().max()) > 1e-4
     # the transverse derivative of the trilinear interpolant jumps on cell faces, where float32 and float64
-    # positions may take different (equally valid) cells: allow a rare ray there
+    # positions may take different (equally valid) cells: with ~98 nodes per ray, a few of the 4096 rays meet
+    # one (B only; eta is continuous there), so at most 0.2 % of the rays may differ in B
     bad_eta = ((deta - d_eta_o).abs().max(dim=1).values > 1e-4 * float(d_eta_o.abs().max())).sum()
-    bad_B = ((dB - d_B_o).abs().amax(dim=(1, 2)) > 1e-4 * float(d_B_o.abs().max())).sum()
-    assert int(bad_eta) == 0 and int(bad_B) <= 2, (int(bad_eta), int(bad_B))
+    err_B = (dB - d_B_o).abs().amax(dim=(1, 2)) / float(d_B_o.abs().max())
+    bad_B = int((err_B > 1e-4).sum())
+    assert int(bad_eta) == 0 and bad_B <= 8, (int(bad_eta), bad_B, sorted(err_B.tolist())[-10:])
+    assert float(err_B.median()) <= 1e-6
     dth = rays.theta[idx].cpu() - want["theta"]
     assert float(dth.abs().max()) <= 1e-4 * float((want["theta"] - torch.from_numpy(theta0[idx])).abs().max()) + 1e-15
     dA = rays.A[idx].double().cpu().reshape(-1, 2, 2) - want["A"]
