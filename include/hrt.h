@@ -482,7 +482,8 @@ typedef struct hrt_ctx hrt_ctx;
 hrt_status hrt_create(const hrt_config* cfg, void* stream, hrt_ctx** out);
 hrt_status hrt_destroy(hrt_ctx* ctx);  /* NULL is fine; synchronises the context's stream */
 
-/* Device bytes a context of this configuration allocates (plans and buffers), for capacity planning. */
+/* Device bytes a context of this configuration allocates (plans and buffers, with the buffers of the default
+ * particle sort), for capacity planning; the ray mesh and a recorded run for hrt_adjoint come on top. */
 hrt_status hrt_workspace_bytes(const hrt_config* cfg, int64_t n_rays, size_t* bytes_host);
 
 /* Particles from Zel'dovich ICs (noise[n_side^3] device float32) at a_init, then the PM force at a_init. */

@@ -1439,6 +1439,9 @@ hrt_status hrt_workspace_bytes(const hrt_config* cfg, int64_t n_rays, size_t* by
   b += spectrum_alloc(cfg->n_mesh) * (1 + 3 + cfg->ray_fields) + 2 * spectrum_bytes(cfg->n_mesh);  // + cuFFT work
   b += static_cast<size_t>(n_rays) * (2 * sizeof(double) + 10 * sizeof(float));
   b += static_cast<size_t>(n_rays) * 4 * sizeof(float) * cfg->n_sources;
+  // cell-order storage of the particles (on by default): second copies, two order maps, keys, ranks, sources and
+  // the per-segment counters
+  b += np * (6 * sizeof(float) + 5 * sizeof(int32_t)) + static_cast<size_t>(particle_sort_counts(cfg->n_mesh)) * sizeof(int32_t);
   *bytes = b;
   return HRT_OK;
 }
