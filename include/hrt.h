@@ -518,7 +518,8 @@ hrt_status hrt_set_ray_correction(hrt_ctx* ctx, const float* params);
  * shift tables (host, copied); n = 0 removes it.  Needs ray_fields == 0 (HRT_ERR_STATE otherwise). */
 hrt_status hrt_set_replicas(hrt_ctx* ctx, int32_t n, const int32_t* perm, const int32_t* sign, const int32_t* shift);
 
-/* Adjoints of the ray-mesh kick.  The mesh geometry (lambda_lim, x2d, N, the plane set) is
+/* Adjoints of the ray-mesh kick (the kick operator of Sec. 5.2 and App. C, differentiated as the adjoint
+ * method that Sec. 7 names as future work).  The mesh geometry (lambda_lim, x2d, N, the plane set) is
  * held fixed: derivatives are taken with respect to the fields, the ray state and the plane weights
  * w_p = -(2/c) chi_p g(chi_p) (+-cell) cell^2 / (chi_p^2 x2d^2), not with respect to the discretisation.
  *
@@ -541,11 +542,11 @@ hrt_status hrt_raymesh_ray_step_adjoint(hrt_raymesh* rm, const hrt_rays* rays, c
                                         double omega_m, const hrt_rays* bar, float* gx_bar, float* gy_bar,
                                         double* plane_bar_host, double* drift_bar_host, void* stream);
 
-/* The same two transposes through a tiled light cone (geom with n_replicas >= 1; the forwards are
- * hrt_raymesh_kick_tiled and hrt_raymesh_ray_step_tiled).  A node of a plane in replica k was read from box
- * field perm[k][a] with sign sign[k][a] for sky component a, at the replica's shifted box node, so its cotangent
- * goes there: gx_bar, gy_bar and gz_bar (device [n^3] float32, all three required) accumulate the cotangents of
- * the three box fields.  Other arguments and outputs as in the untiled calls. */
+/* The same two transposes through a light cone tiled by box replicas (Sec. 6.2; geom with n_replicas >= 1;
+ * the forwards are hrt_raymesh_kick_tiled and hrt_raymesh_ray_step_tiled).  A node of a plane in replica k was
+ * read from box field perm[k][a] with sign sign[k][a] for sky component a, at the replica's shifted box node, so
+ * its cotangent goes there: gx_bar, gy_bar and gz_bar (device [n^3] float32, all three required) accumulate the
+ * cotangents of the three box fields.  Other arguments and outputs as in the untiled calls. */
 hrt_status hrt_raymesh_kick_tiled_adjoint(hrt_raymesh* rm, const float* grad_x, const float* grad_y,
                                           const float* grad_z, const float* mesh_bar, const hrt_ray_geom* geom,
                                           double chi_a, double chi_b, double a_ref, double omega_m, float* gx_bar,
