@@ -457,3 +457,27 @@ def test_warp_aggregated_deposit_matches_the_plain_deposit(hrt):
     with pytest.raises(hrt.HRTError):
         hrt.hrt_cic_scatter_warp_aggregated(torch.zeros(3, 24 ** 3, device="cuda"), 24, 48, 100.0,
                                             torch.empty(48 ** 3, device="cuda"))
+
+
+def test_empty_ray_sets_are_no_ops(hrt):
+    # zero rays: every ray call (direct and ray-mesh step, free drift, readout and their adjoints) succeeds and
+    # leaves the field and node cotangents at zero
+    n, box = 16, 32.0
+    g = torch.randn(n ** 3, device="cuda")
+    geom = hrt.make_geom(n, box, (3.3, 7.7, 1.0))
+    rays, bar = hrt.RayState(0), hrt.RayState(0)
+    maps = torch.empty(4, 0, device="cuda")
+    hrt.hrt_ray_step(rays, g, g, geom, 10.0, 12.0, 0.8, 0.3, maps)
+    hrt.hrt_ray_drift_free(rays, 12.0, 14.0)
+    hrt.hrt_ray_readout(rays, maps)
+    gb = torch.zeros(n ** 3, device="cuda")
+    nb = torch.zeros(3, 1024, dtype=torch.float64, device="cuda")
+    drb = torch.zeros(1, dtype=torch.float64, device="cuda")
+    hrt.hrt_ray_step_adjoint(rays, g, g, geom, 10.0, 12.0, 0.8, 0.3, bar, gb, gb, nb, drb)
+    rm = hrt.RayMesh(hrt.make_raymesh_config(0.5, 8, 0.004, 40))
+    rm.hrt_raymesh_ray_step(rays, g, g, geom, 10.0, 12.0, 0.8, 0.3)
+    pb, db = rm.hrt_raymesh_ray_step_adjoint(rays, g, g, geom, 10.0, 12.0, 0.8, 0.3, bar, gb, gb)
+    torch.cuda.synchronize()
+    rm.close()
+    assert float(gb.abs().max()) == 0.0 and float(nb.abs().max()) == 0.0 and float(drb.abs().max()) == 0.0
+    assert not np.any(pb) and db == 0.0
