@@ -232,7 +232,8 @@ hrt_status hrt_ray_step_tiled(const hrt_rays* rays, const float* grad_x, const f
  * 1/chi_to)/c, A += B (1/chi_from - 1/chi_to)/c.  Used where the potential is known to vanish. */
 hrt_status hrt_ray_drift_free(const hrt_rays* rays, double chi_from, double chi_to, void* stream);
 
-/* Readout only: maps[4][n_rays] = kappa, gamma1, gamma2, omega from A (Eqs. "obs_first_set"). */
+/* Readout only: maps[4][n_rays] = kappa, gamma1, gamma2, omega from A (Eqs. "obs_first_set"); maps may be NULL
+ * when there are no rays. */
 hrt_status hrt_ray_readout(const hrt_rays* rays, float* maps, void* stream);
 
 /* ------------------------------------------------------------------------------------------------------

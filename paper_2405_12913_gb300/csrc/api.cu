@@ -882,7 +882,7 @@ hrt_status hrt_ray_drift_free(const hrt_rays* rays, double chi_from, double chi_
 
 hrt_status hrt_ray_readout(const hrt_rays* rays, float* maps, void* stream) {
   HRT_TRY(check_rays(rays));
-  if (!maps) return fail(HRT_ERR_INVALID_ARG, "maps is NULL");
+  if (!maps && rays->n_rays > 0) return fail(HRT_ERR_INVALID_ARG, "maps is NULL");
   return launch_ray_readout(*rays, maps, as_stream(stream));
 }
 
