@@ -31,8 +31,14 @@ int64_t xpass_row(int64_t n);
 // Twiddle table of the x-FFT for side n: [R1][32] forward factors exp(-2 pi i l k1 / n), then [32][32] inverse
 // factors exp(+2 pi i n1 (lane mod R1) / n); FP64 on the host, rounded to float.
 void xpass_twiddles(int64_t n, std::vector<float2>& tw);
-// in: the (y, z)-transformed density [x][ky][xpass_row(n)]; tw: device copy of xpass_twiddles(n).
+// Bit the x-pass sets in its error word when a wait for a tile's copy timed out (the kernel then stops early).
+constexpr int kXpassTimeout = 1;
+// Dynamic shared memory of the x-pass for side n (three 64 KB tiles, twiddle and filter tables, barriers).
+size_t xpass_smem_bytes(int64_t n);
+// in: the (y, z)-transformed density [x][ky][xpass_row(n)] (16-byte aligned, as are the outputs); tw: device copy
+// of xpass_twiddles(n); err: device error word (kXpassTimeout is OR-ed into it).  Set a has 2 or 3 outputs, set
+// b none (n_out 0), 2 or 3.
 hrt_status launch_xpass(const void* in, int64_t n, double box, double pref, const float2* tw, const XpassSet& a,
-                        const XpassSet& b, cudaStream_t s);
+                        const XpassSet& b, int* err, cudaStream_t s);
 
 }  // namespace hrt

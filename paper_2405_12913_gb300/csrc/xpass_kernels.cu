@@ -4,22 +4,34 @@
 // inverse x-FFTs of the gradient spectra; batched 2D C2R plans finish the gradient fields.  Together with the 2D
 // plans this reads and writes every spectrum once less than a 3D R2C, a separate k-space kernel and 3D C2Rs.
 //
-// FFT along x (n = 32 R1 points): four-step, x = l + 32 m, k = k1 + R1 k2.  A warp holds 32 complex values per
-// lane: lane l first holds x = l + 32 m of its P = 32 / R1 pencils, does the R1-point DFTs over m in registers,
-// applies the twiddles W_n^(l k1), transposes through its pencils' columns of the shared tile, and does the
-// 32-point DFT over l in registers, so that lane (p, k1) holds X[k1 + R1 k2] for all k2.  The inverse runs the
-// same steps backwards and returns to the first layout.  The gradient spectra are linear in the pencil: for a
-// pencil (ky, kz) the y and z components are d_y V and d_z V with V = IFFT_x(i c X), so a filter set needs two
-// inverse transforms (V and the x component) for its three outputs.
+// Tiles.  The [x][ky][kz] half spectrum (kz rows of n/2 + 1 complex values, as cuFFT writes them) is viewed as n
+// x-planes of F = n (n/2 + 1) consecutive (ky, kz) pencils.  A tile is TK = 8P consecutive pencils of that flat
+// index for all n x-planes: TK x 8 bytes per plane (64 B at n = 1024), which start on a 64-byte boundary in every
+// plane because F is a multiple of TK.  So a tile is one 2D box of a TMA tensor map (inner extent the flat
+// index, outer extent x), with no padding of the rows that cuFFT reads and writes, and every tile is full.  A
+// tile may span two ky rows; each pencil takes its own (ky, kz).
 //
-// Tiles: a CTA of 8 warps owns the pencils (ky, kz0 .. kz0 + 8P - 1) for all x: rows of 8P contiguous complex
-// values in the [x][ky][kz] half spectra (the last tile holds only the Nyquist column kz = n/2).  Persistent CTAs; the next tile is copied into the second shared buffer with cp.async while
-// the current one is transformed.
+// Data movement.  Input tiles arrive by TMA (cp.async.bulk.tensor) into one of two shared buffers, completing on
+// an mbarrier; the next tile is requested while the current one is transformed.  Outputs are written row-wise
+// into a staging buffer and leave by TMA stores (bulk groups), so that no thread issues a global load or store
+// per element.  The buffers carry the TMA swizzle (64 B or 128 B), which spreads a pencil's column over 8 of the
+// 16 eight-byte bank slots of a 128-byte line.
+//
+// FFT along x (n = 32 R1 points), four-step with x = l + 32 m and k = k1 + R1 k2.  A warp owns P = 32 / R1
+// pencils.  Lane l first holds x = l + 32 m of its P pencils (its column of the tile), does the R1-point DFTs
+// over m in registers and applies the twiddles W_n^(l k1); a transpose through the warp's private 8 KB of the
+// (already read) input buffer gives lane (p, k1) the 32 values over l, and a 32-point DFT over l in registers
+// leaves X[k1 + R1 k2] of pencil p in that lane.  The inverse runs the same steps backwards.  The gradient
+// spectra are linear in the pencil: for a pencil (ky, kz) the y and z components are d_y V and d_z V with
+// V = IFFT_x(i c X), so a filter set needs two inverse transforms (V and the x component) for its three outputs.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 #include <vector>
 
 #include "common.h"
@@ -30,6 +42,12 @@ namespace hrt {
 namespace {
 
 constexpr int kXWarps = 8;
+constexpr int kXThreads = kXWarps * 32;
+constexpr int kTileBytes = 64 * 1024;  // TK pencils x n rows x 8 bytes, for every supported n
+// Bounded waits: each mbarrier probe may suspend the thread for up to kWaitHintNs; after kWaitTries probes
+// (about a second) the kernel records kXpassTimeout and returns.
+constexpr uint32_t kWaitHintNs = 20000;
+constexpr int kWaitTries = 1 << 16;
 
 __host__ __device__ constexpr int bit_reverse(int i, int bits) {
   int r = 0;
@@ -118,17 +136,82 @@ struct DftPencils<R1, INV, 0> {
   __device__ __forceinline__ static void run(float2 (&)[32]) {}
 };
 
-// Slot of the transposed element (k1, l) in a pencil's column: the XOR keeps both the row-wise writes and the
-// column-wise reads of a warp on distinct bank pairs (the column stride LD is odd).
-__device__ __forceinline__ int slot(int k1, int l) { return k1 * 32 + (l ^ k1); }
-
-__device__ __forceinline__ void cp_async8(float2* dst, const float2* src) {
-  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+// ---- shared memory, mbarriers and TMA (inline PTX) -------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// True once the barrier's phase with the given parity has completed; false after the bounded number of probes.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int i = 0; i < kWaitTries; ++i) {
+    uint32_t ok = 0;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(kWaitHintNs)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, uint32_t src, int c0, int c1, int c2) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];\n"
+               ::"l"(reinterpret_cast<uint64_t>(map)), "r"(src), "r"(c0), "r"(c1), "r"(c2)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// Waits until every committed store group has finished reading its shared-memory source.
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+// Waits until every committed store group has completed.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+// Orders this thread's generic shared-memory writes before later TMA (async-proxy) accesses.
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// ---- tile geometry ----------------------------------------------------------------------------------------
+// TK = 8P pencils per tile; the tile is stored as NSUB sub-tiles of SUBW columns (rows of PITCH = 8 SUBW bytes,
+// at most 128 so that a TMA swizzle applies): element (row r, column c) sits at sub-tile c / SUBW, row r,
+// 8-byte slot c % SUBW, with the 16-byte chunk index XORed by the swizzle key of the row.
+template <int R1>
+struct Geo {
+  static constexpr int P = 32 / R1;
+  static constexpr int N = 32 * R1;
+  static constexpr int TK = kXWarps * P;
+  static constexpr int SUBW = TK < 16 ? TK : 16;
+  static constexpr int NSUB = TK / SUBW;
+  static constexpr int PITCH = SUBW * 8;
+  static constexpr int SUB_BYTES = N * PITCH;
+  static constexpr int ROWS_PER_BOX = N < 256 ? N : 256;
+  static constexpr int BOXES = N / ROWS_PER_BOX;
+  static_assert(TK * N * 8 == kTileBytes, "a tile is 64 KB");
+  // Swizzle key of row r: address bits [7, 9) (64 B pitch, SWIZZLE_64B) or [7, 10) (128 B, SWIZZLE_128B).
+  __device__ __forceinline__ static int key(int r) { return PITCH == 64 ? (r >> 1) & 3 : r & 7; }
+  // Byte offset of (r, c) within the tile.
+  __device__ __forceinline__ static int offset(int r, int c) {
+    const int sub = c / SUBW, cc = c - sub * SUBW;
+    return sub * SUB_BYTES + r * PITCH + ((cc * 8) ^ (key(r) << 4));
+  }
+};
+
+struct Pencil {
+  int ky, kz;
+};
 
 __device__ __forceinline__ float learned_factor(const XpassSet& s, float kmag) {
   if (s.g == nullptr) return 1.f;
@@ -139,226 +222,315 @@ __device__ __forceinline__ float learned_factor(const XpassSet& s, float kmag) {
   return __ldg(s.g + i) * (1.f - w) + __ldg(s.g + i + 1) * w;
 }
 
-struct TileGeom {
-  int ky, kz0, width;
-};
-
-__device__ __forceinline__ TileGeom tile_geom(int tile, int kz_tiles, int tk, int nzc) {
-  TileGeom t;
-  t.ky = tile / kz_tiles;
-  t.kz0 = (tile - t.ky * kz_tiles) * tk;
-  t.width = min(tk, nzc - t.kz0);
-  return t;
-}
-
-// Copies the tile's valid columns of all n rows into shared memory (8-byte cp.async, TK threads per row).
-template <int TK, int LD>
-__device__ __forceinline__ void load_tile(const float2* __restrict__ in, int n, int nzp, const TileGeom& g,
-                                          float2* dst) {
-  for (int e = threadIdx.x; e < n * TK; e += blockDim.x) {
-    const int x = e / TK, c = e - x * TK;
-    if (c < g.width) cp_async8(dst + x * LD + c, in + (static_cast<int64_t>(x) * n + g.ky) * nzp + g.kz0 + c);
-  }
-}
-
-template <int TK, int LD>
-__device__ __forceinline__ void store_tile(float2* __restrict__ out, int n, int nzp, const TileGeom& g,
-                                           const float2* src) {
-  for (int e = threadIdx.x; e < n * TK; e += blockDim.x) {
-    const int x = e / TK, c = e - x * TK;
-    if (c < g.width) out[(static_cast<int64_t>(x) * n + g.ky) * nzp + g.kz0 + c] = src[x * LD + c];
-  }
-}
-
-// Inverse x-FFT from layout B (lane (p, k1), u[k2] = X[k1 + R1 k2]) to layout A (lane l, u[p R1 + n2] =
-// x[l + 32 n2]) through the warp's columns col0 .. col0 + P - 1 of the tile.
-template <int R1>
-__device__ __forceinline__ void inverse_x(float2 (&u)[32], float2* T, int col0, const float2* twi, int lane) {
-  constexpr int P = 32 / R1, LD = kXWarps * P + 1;
-  dft<32, true, 0>(u);
-#pragma unroll
-  for (int n1 = 1; n1 < 32; ++n1) u[n1] = cmul(u[n1], twi[n1 * 32 + lane]);
-  const int pp = lane / R1, k1 = lane - pp * R1;
-#pragma unroll
-  for (int n1 = 0; n1 < 32; ++n1) T[slot(k1, n1) * LD + col0 + pp] = u[n1];
-  __syncwarp();
-#pragma unroll
-  for (int p = 0; p < P; ++p)
-#pragma unroll
-    for (int j = 0; j < R1; ++j) u[p * R1 + j] = T[slot(j, lane) * LD + col0 + p];
-  __syncwarp();
-  DftPencils<R1, true, P>::run(u);
-}
-
-// c(k) = Green's function x per-axis filter factors x learned g at kx = k1 + R1 k2 (the k-space kernel's factor).
-template <int R1>
-__device__ __forceinline__ float filter_c(const XpassSet& s, const float* wx, int n, int k1, int k2, float kf,
-                                          float scale, float k2yz, float cyz) {
-  const int kx = k1 + R1 * k2;
-  const int nx = kx < (n >> 1) ? kx : kx - n;
-  const float kxf = kf * nx;
-  const float kk = kxf * kxf + k2yz;
-  const float green = kk > 0.f ? __fdividef(scale, kk) : 0.f;
-  float c = green * wx[kx] * cyz;
-  if (s.g != nullptr) c *= learned_factor(s, sqrtf(kk));
-  return c;
-}
-
 __device__ __forceinline__ float dx_of(int kx, int n, float kf) {
   const int nx = kx < (n >> 1) ? kx : kx - n;
   return nx == -(n >> 1) ? 0.f : kf * nx;
 }
 
-// u[k2] = d(kx) Y[k2] at kx = k1 + R1 k2, with Y = i c X: computed here from X (PRE false) or given in X
-// (PRE true); d = d_x of each kx when with_dx, else 1.
+// u[k2] = d(kx) Y[k2] at kx = k1 + R1 k2, with Y = i c X, c = Green's function x per-axis filter factors x learned
+// g (the k-space kernel's factor): computed here from X (PRE false) or already in X (PRE true); d = d_x of each
+// kx for the x component, else 1.
 template <int R1, bool PRE>
 __device__ __forceinline__ void filtered(const float2 (&X)[32], float2 (&u)[32], const XpassSet& s,
-                                         const float* wx, int n, int k1, float kf, float scale, float k2yz,
-                                         float cyz, bool with_dx) {
+                                         const float* wx, int k1, float kf, float scale, float k2yz, float cyz,
+                                         bool with_dx) {
+  constexpr int N = 32 * R1;
 #pragma unroll
   for (int k2 = 0; k2 < 32; ++k2) {
-    const float d = with_dx ? dx_of(k1 + R1 * k2, n, kf) : 1.f;
+    const int kx = k1 + R1 * k2;
+    const float d = with_dx ? dx_of(kx, N, kf) : 1.f;
     if (PRE) {
       u[k2] = make_float2(d * X[k2].x, d * X[k2].y);
     } else {
-      const float c = d * filter_c<R1>(s, wx, n, k1, k2, kf, scale, k2yz, cyz);
+      const int nx = kx < (N >> 1) ? kx : kx - N;
+      const float kxf = kf * nx;
+      const float kk = kxf * kxf + k2yz;
+      float c = kk > 0.f ? __fdividef(scale, kk) : 0.f;
+      c *= wx[kx] * cyz;
+      if (s.g != nullptr) c *= learned_factor(s, sqrtf(kk));
+      c *= d;
       u[k2] = make_float2(-c * X[k2].y, c * X[k2].x);
     }
   }
 }
 
-// The gradient spectra of one filter set for the tile: the x component, then V = IFFT_x(i c X), stored once
-// scaled by d_y and once by d_z; each transform's result is written to the tile's rows and stored by the CTA.
-template <int R1, bool PRE>
-__device__ __forceinline__ void one_set(const XpassSet& s, const float* wx, const float2 (&X)[32], float2* T,
-                                        const TileGeom& g, int col0, int k1, int lane, bool busy, int n, int nzp,
-                                        float kf, float scale, int kz, float k2yz, float dy, int64_t plane,
-                                        const float2* twi) {
-  constexpr int P = 32 / R1, TK = kXWarps * P, LD = TK + 1;
+// The warp's private transpose area: 32 rows q of 32 complex values, slot (q, l) at q * 32 + (l ^ q) (an XOR
+// that keeps both the row-wise writes and the column-wise reads of a warp on 16 distinct 8-byte slots).
+__device__ __forceinline__ float2* tslot(char* priv, int q, int l) {
+  return reinterpret_cast<float2*>(priv + q * 256 + ((l ^ q) << 3));
+}
+
+// Inverse x-FFT from layout B (lane (p, k1), u[k2] = X[k1 + R1 k2]) to layout A (lane l, u[p R1 + n2] =
+// x[l + 32 n2]) through the warp's private area.
+template <int R1>
+__device__ __forceinline__ void inverse_x(float2 (&u)[32], char* priv, const float2* twi, int lane) {
+  constexpr int P = 32 / R1;
+  dft<32, true, 0>(u);
+#pragma unroll
+  for (int n1 = 1; n1 < 32; ++n1) u[n1] = cmul(u[n1], twi[n1 * 32 + lane]);
+#pragma unroll
+  for (int n1 = 0; n1 < 32; ++n1) *tslot(priv, lane, n1) = u[n1];
+  __syncwarp();
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int j = 0; j < R1; ++j) u[p * R1 + j] = *tslot(priv, p * R1 + j, lane);
+  __syncwarp();
+  DftPencils<R1, true, P>::run(u);
+}
+
+// Pencil frequencies and the per-pencil factors of one filter set.
+struct PencilFactors {
+  float k2yz, cyz, dy, dz;
+};
+
+__device__ __forceinline__ PencilFactors pencil_factors(const XpassSet& s, Pencil pc, int n, float kf) {
   const int half = n >> 1;
-  const float cyz = __ldg(s.wxy + g.ky) * __ldg(s.wz + kz);
-  float2 u[32];
-  if (busy) {
-    filtered<R1, PRE>(X, u, s, wx, n, k1, kf, scale, k2yz, cyz, true);
-    inverse_x<R1>(u, T, col0, twi, lane);
-#pragma unroll
-    for (int p = 0; p < P; ++p)
-#pragma unroll
-      for (int j = 0; j < R1; ++j) T[(lane + 32 * j) * LD + col0 + p] = u[p * R1 + j];
-  }
-  __syncthreads();
-  store_tile<TK, LD>(s.out, n, nzp, g, T);
-  __syncthreads();
-  if (busy) {
-    filtered<R1, PRE>(X, u, s, wx, n, k1, kf, scale, k2yz, cyz, false);
-    inverse_x<R1>(u, T, col0, twi, lane);
-#pragma unroll
-    for (int p = 0; p < P; ++p)
-#pragma unroll
-      for (int j = 0; j < R1; ++j) T[(lane + 32 * j) * LD + col0 + p] = u[p * R1 + j];
-  }
-  __syncthreads();
-  // y and z components in one pass over V: d_y is the tile's, d_z each column's
-  float2* out_y = s.out + plane;
-  float2* out_z = s.n_out > 2 ? s.out + 2 * plane : nullptr;
-  for (int e = threadIdx.x; e < n * TK; e += blockDim.x) {
-    const int x = e / TK, c = e - x * TK;
-    if (c >= g.width) continue;
-    const float2 v = T[x * LD + c];
-    const int64_t o = (static_cast<int64_t>(x) * n + g.ky) * nzp + g.kz0 + c;
-    out_y[o] = make_float2(dy * v.x, dy * v.y);
-    if (out_z) {
-      const int kzc = g.kz0 + c;
-      const float dz = kzc == half ? 0.f : kf * kzc;
-      out_z[o] = make_float2(dz * v.x, dz * v.y);
-    }
-  }
-  __syncthreads();
+  const int ny = pc.ky < half ? pc.ky : pc.ky - n;
+  const float kyf = kf * ny, kzf = kf * pc.kz;
+  PencilFactors f;
+  f.k2yz = kyf * kyf + kzf * kzf;
+  f.cyz = __ldg(s.wxy + pc.ky) * __ldg(s.wz + pc.kz);
+  f.dy = ny == -half ? 0.f : kyf;
+  f.dz = pc.kz == half ? 0.f : kzf;
+  return f;
 }
 
 template <int R1, bool TWO>
-__global__ void __launch_bounds__(kXWarps * 32, 1)
-    xpass_kernel(const float2* __restrict__ in, int n, int nzc, int nzp, int kz_tiles, float kf, float scale,
-                 const float2* __restrict__ tw, XpassSet a, XpassSet b) {
-  constexpr int P = 32 / R1, TK = kXWarps * P, LD = TK + 1;
-  extern __shared__ float2 sm[];
-  float2* twf = sm;             // [R1][32]: W_n^(l k1)
-  float2* twi = twf + R1 * 32;  // [32][32]: W_n^(-n1 k1(lane))
+__global__ void __launch_bounds__(kXThreads, 1)
+    xpass_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_constant__ CUtensorMap out_a,
+                 const __grid_constant__ CUtensorMap out_b, int nzc, int n_tiles, float kf, float scale,
+                 const float2* __restrict__ tw, XpassSet a, XpassSet b, int* __restrict__ err) {
+  using G = Geo<R1>;
+  constexpr int P = G::P, N = G::N, TK = G::TK;
+  extern __shared__ unsigned char smem_raw[];
+  // 1024-byte aligned base: the 128-byte swizzle repeats every 1024 bytes and is taken from address bits
+  unsigned char* sm = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+  unsigned char* const ibuf0 = sm;
+  unsigned char* const ibuf1 = sm + kTileBytes;
+  unsigned char* const obuf = sm + 2 * kTileBytes;
+  float2* twf = reinterpret_cast<float2*>(sm + 3 * kTileBytes);  // [R1][32]: W_n^(l k1)
+  float2* twi = twf + R1 * 32;                                     // [32][32]: W_n^(-n1 k1(lane))
   float* wxa = reinterpret_cast<float*>(twi + 32 * 32);
-  float* wxb = wxa + n;
-  float2* const buf0 = reinterpret_cast<float2*>(wxb + n);
-  float2* const buf1 = buf0 + n * LD;
+  float* wxb = wxa + N;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wxb + N);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < R1 * 32 + 32 * 32; i += blockDim.x) sm[i] = tw[i];
-  for (int i = tid; i < n; i += blockDim.x) {
+  for (int i = tid; i < R1 * 32 + 32 * 32; i += kXThreads) twf[i] = tw[i];
+  for (int i = tid; i < N; i += kXThreads) {
     wxa[i] = __ldg(a.wxy + i);
     wxb[i] = TWO ? __ldg(b.wxy + i) : 0.f;
   }
-  const int n_tiles = n * kz_tiles;
-  const int64_t plane = static_cast<int64_t>(n) * n * nzp;
-  const int half = n >> 1;
+  const uint32_t bar0 = smem_u32(bars), bar1 = smem_u32(bars + 1);
+  const uint32_t ib0 = smem_u32(ibuf0), ib1 = smem_u32(ibuf1), ob = smem_u32(obuf);
+  if (tid == 0) {
+    mbar_init(bar0, 1);
+    mbar_init(bar1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+
+  // one thread requests tile t into the input buffer at dst
+  auto request = [&](int t, uint32_t dst, uint32_t bar) {
+    mbar_expect_tx(bar, kTileBytes);
+#pragma unroll
+    for (int s = 0; s < G::NSUB; ++s)
+#pragma unroll
+      for (int bx = 0; bx < G::BOXES; ++bx)
+        tma_load_2d(dst + s * G::SUB_BYTES + bx * G::ROWS_PER_BOX * G::PITCH, &in_map,
+                    2 * (t * TK + s * G::SUBW), bx * G::ROWS_PER_BOX, bar);
+  };
+  // one thread stores the staged tile at src as component comp of the set's output spectra
+  auto store = [&](const CUtensorMap* map, uint32_t src, int t, int comp) {
+#pragma unroll
+    for (int s = 0; s < G::NSUB; ++s)
+#pragma unroll
+      for (int bx = 0; bx < G::BOXES; ++bx)
+        tma_store_3d(map, src + s * G::SUB_BYTES + bx * G::ROWS_PER_BOX * G::PITCH, 2 * (t * TK + s * G::SUBW),
+                     bx * G::ROWS_PER_BOX, comp);
+  };
+
+  // loads requested and not yet consumed, one bit per input buffer (thread 0's bookkeeping, for the exit after
+  // a timed-out wait)
+  uint32_t pending = 0u;
+  if (tid == 0 && static_cast<int>(blockIdx.x) < n_tiles) {
+    request(blockIdx.x, ib0, bar0);
+    pending = 1u;
+  }
   const int col0 = warp * P;
   const int pp = lane / R1, k1 = lane - pp * R1;
-  int cur = 0;
-  if (static_cast<int>(blockIdx.x) < n_tiles)
-    load_tile<TK, LD>(in, n, nzp, tile_geom(blockIdx.x, kz_tiles, TK, nzc), buf0);
-  cp_async_commit();
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int next = tile + gridDim.x;
-    if (next < n_tiles) load_tile<TK, LD>(in, n, nzp, tile_geom(next, kz_tiles, TK, nzc), cur ? buf0 : buf1);
-    cp_async_commit();
-    cp_async_wait<1>();
-    __syncthreads();
-    const TileGeom g = tile_geom(tile, kz_tiles, TK, nzc);
-    float2* T = cur ? buf1 : buf0;
-    const bool busy = col0 < g.width;
-    // ---- forward x-FFT of the warp's pencils: X[k2] = spectrum at kx = k1 + R1 k2 of pencil col0 + pp
-    float2 X[32];
-    if (busy) {
+  // per-lane byte offsets of the warp's columns at rows lane + 32 m (the swizzle key depends on lane only)
+  int coff[P];
 #pragma unroll
-      for (int p = 0; p < P; ++p)
-#pragma unroll
-        for (int m = 0; m < R1; ++m) X[p * R1 + m] = T[(lane + 32 * m) * LD + col0 + p];
-      __syncwarp();
-      DftPencils<R1, false, P>::run(X);
-#pragma unroll
-      for (int p = 0; p < P; ++p)
-#pragma unroll
-        for (int j = 1; j < R1; ++j) X[p * R1 + j] = cmul(X[p * R1 + j], twf[j * 32 + lane]);
-#pragma unroll
-      for (int p = 0; p < P; ++p)
-#pragma unroll
-        for (int j = 0; j < R1; ++j) T[slot(j, lane) * LD + col0 + p] = X[p * R1 + j];
-      __syncwarp();
-#pragma unroll
-      for (int l = 0; l < 32; ++l) X[l] = T[slot(k1, l) * LD + col0 + pp];
-      __syncwarp();
-      dft<32, false, 0>(X);
+  for (int p = 0; p < P; ++p) coff[p] = G::offset(lane, col0 + p);
+  uint32_t parity = 0u;  // bit c: the phase parity to wait for on input buffer c
+  int k = 0;
+  bool ok = true;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++k) {
+    const int cb = k & 1;
+    unsigned char* const ib = cb ? ibuf1 : ibuf0;
+    const uint32_t ibs = cb ? ib1 : ib0;
+    const bool got = mbar_wait(cb ? bar1 : bar0, (parity >> cb) & 1u);
+    parity ^= 1u << cb;
+    if (!__syncthreads_and(got)) {
+      ok = false;
+      break;
     }
-    // pencil frequencies (ky, kz); columns past the tile's width hold no pencil and are not stored
-    const int kz = min(g.kz0 + col0 + pp, half);
-    const int ny = g.ky < half ? g.ky : g.ky - n;
-    const float kyf = kf * ny, kzf = kf * kz;
-    const float k2yz = kyf * kyf + kzf * kzf;
-    const float dy = ny == -half ? 0.f : kyf;
-    if (TWO) {
-      one_set<R1, false>(a, wxa, X, T, g, col0, k1, lane, busy, n, nzp, kf, scale, kz, k2yz, dy, plane, twi);
-      one_set<R1, false>(b, wxb, X, T, g, col0, k1, lane, busy, n, nzp, kf, scale, kz, k2yz, dy, plane, twi);
-    } else {
-      // one filter set: Y = i c X once, in place
-      if (busy) {
-        const float cyz = __ldg(a.wxy + g.ky) * __ldg(a.wz + kz);
+    pending &= ~(1u << cb);
+    // ---- the warp's columns: X[p R1 + m] = x[lane + 32 m] of pencil col0 + p
+    float2 X[32];
 #pragma unroll
-        for (int k2 = 0; k2 < 32; ++k2) {
-          const float c = filter_c<R1>(a, wxa, n, k1, k2, kf, scale, k2yz, cyz);
-          X[k2] = make_float2(-c * X[k2].y, c * X[k2].x);
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+      for (int m = 0; m < R1; ++m)
+        X[p * R1 + m] = *reinterpret_cast<const float2*>(ib + coff[p] + m * 32 * G::PITCH);
+    __syncthreads();  // every column read: the input buffer is now the warps' transpose area
+    char* const priv = reinterpret_cast<char*>(ib) + warp * 8192;
+    // ---- forward x-FFT: X[k2] = spectrum at kx = k1 + R1 k2 of pencil col0 + pp
+    DftPencils<R1, false, P>::run(X);
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+      for (int j = 1; j < R1; ++j) X[p * R1 + j] = cmul(X[p * R1 + j], twf[j * 32 + lane]);
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+      for (int j = 0; j < R1; ++j) *tslot(priv, p * R1 + j, lane) = X[p * R1 + j];
+    __syncwarp();
+#pragma unroll
+    for (int l = 0; l < 32; ++l) X[l] = *tslot(priv, lane, l);
+    __syncwarp();
+    dft<32, false, 0>(X);
+
+    // this lane's pencil in layout B, and the warp's P pencils in layout A (for the d_y, d_z scaling)
+    const int flat0 = tile * TK + col0;
+    const int fb = flat0 + pp;
+    const Pencil pb{fb / nzc, fb - (fb / nzc) * nzc};
+    const PencilFactors fa_b = pencil_factors(a, pb, N, kf);
+    if (!TWO) {
+      // one filter set: Y = i c X once, in place
+      float2 u[32];
+      filtered<R1, false>(X, u, a, wxa, k1, kf, scale, fa_b.k2yz, fa_b.cyz, false);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) X[i] = u[i];
+    }
+    // ---- inverse transforms: per set, the x component, then V (stored as d_y V and d_z V)
+    constexpr int kOutputs = TWO ? 4 : 2;
+#pragma unroll 1
+    for (int w = 0; w < kOutputs; ++w) {
+      const bool second = TWO && w >= 2;
+      const XpassSet& s = second ? b : a;
+      const bool xcomp = (w & 1) == 0;
+      float2 u[32];
+      if (TWO) {
+        const PencilFactors f = second ? pencil_factors(b, pb, N, kf) : fa_b;
+        filtered<R1, false>(X, u, s, second ? wxb : wxa, k1, kf, scale, f.k2yz, f.cyz, xcomp);
+      } else {
+        filtered<R1, true>(X, u, s, wxa, k1, kf, scale, 0.f, 0.f, xcomp);
+      }
+      inverse_x<R1>(u, priv, twi, lane);
+      // staging: every earlier store has read its source, and every warp is done with its transposes
+      if (tid == 0) bulk_wait_read_all();
+      __syncthreads();
+      if (tid == 0 && w == 0) {
+        // the other input buffer's last reader (the previous tile's stores) is done: request the next tile
+        const int next = tile + gridDim.x;
+        if (next < n_tiles) {
+          fence_async_shared();
+          request(next, cb ? ib0 : ib1, cb ? bar0 : bar1);
+          pending |= 1u << (cb ^ 1);
         }
       }
-      one_set<R1, true>(a, wxa, X, T, g, col0, k1, lane, busy, n, nzp, kf, scale, kz, k2yz, dy, plane, twi);
+      const CUtensorMap* map = second ? &out_b : &out_a;
+      if (xcomp) {
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+#pragma unroll
+          for (int m = 0; m < R1; ++m)
+            *reinterpret_cast<float2*>(obuf + coff[p] + m * 32 * G::PITCH) = u[p * R1 + m];
+        fence_async_shared();
+        __syncthreads();
+        if (tid == 0) {
+          store(map, ob, tile, 0);
+          bulk_commit();
+        }
+      } else {
+        // d_y V into the staging buffer, d_z V (three outputs) into the input buffer, whose transposes are done
+        const bool with_z = s.n_out == 3;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          const int f = flat0 + p;
+          const Pencil pc{f / nzc, f - (f / nzc) * nzc};
+          const PencilFactors pf = pencil_factors(s, pc, N, kf);
+#pragma unroll
+          for (int m = 0; m < R1; ++m) {
+            const float2 v = u[p * R1 + m];
+            *reinterpret_cast<float2*>(obuf + coff[p] + m * 32 * G::PITCH) = make_float2(pf.dy * v.x, pf.dy * v.y);
+            if (with_z)
+              *reinterpret_cast<float2*>(ib + coff[p] + m * 32 * G::PITCH) = make_float2(pf.dz * v.x, pf.dz * v.y);
+          }
+        }
+        fence_async_shared();
+        __syncthreads();
+        if (tid == 0) {
+          store(map, ob, tile, 1);
+          if (with_z) store(map, ibs, tile, 2);
+          bulk_commit();
+        }
+        if (TWO && !second) {
+          // set b transposes through the input buffer again: wait until its d_z V store has read it
+          if (tid == 0) bulk_wait_read_all();
+          __syncthreads();
+        }
+      }
     }
-    cur ^= 1;
   }
-  cp_async_wait<0>();
+  if (tid == 0) {
+    bulk_wait_all();
+    if (!ok) {
+      atomicOr(err, kXpassTimeout);
+      // let requested loads land before the block's shared memory goes away (again a bounded wait); the
+      // timed-out buffer's parity was already advanced
+      for (int c = 0; c < 2; ++c)
+        if ((pending >> c) & 1u) mbar_wait(c ? bar1 : bar0, ((parity >> c) & 1u) ^ (c == (k & 1) ? 1u : 0u));
+    }
+  }
+}
+
+using EncodeTiled = PFN_cuTensorMapEncodeTiled_v12000;
+
+hrt_status encoder(EncodeTiled* out) {
+  static std::once_flag once;
+  static EncodeTiled fn = nullptr;
+  static cudaError_t e = cudaSuccess;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q{};
+    void* p = nullptr;
+    e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (e == cudaSuccess && q == cudaDriverEntryPointSuccess) fn = reinterpret_cast<EncodeTiled>(p);
+  });
+  if (!fn) return cuda_status(e == cudaSuccess ? cudaErrorSymbolNotFound : e, "cuTensorMapEncodeTiled entry point");
+  *out = fn;
+  return HRT_OK;
+}
+
+// Tensor map over the [comp][x][flat pencil] spectra: rank 2 (one spectrum) or 3; boxes of (2 SUBW floats) x
+// (rows per box) x 1.
+template <int R1>
+hrt_status make_map(CUtensorMap* map, const void* base, int n, int comps) {
+  using G = Geo<R1>;
+  EncodeTiled enc = nullptr;
+  HRT_TRY(encoder(&enc));
+  const uint64_t flat = static_cast<uint64_t>(n) * (n / 2 + 1);
+  const cuuint64_t dims[3] = {2 * flat, static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(comps)};
+  const cuuint64_t strides[2] = {flat * sizeof(float2), flat * sizeof(float2) * n};
+  const cuuint32_t box[3] = {2 * G::SUBW, G::ROWS_PER_BOX, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, comps > 0 ? 3 : 2, const_cast<void*>(base), dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         G::PITCH == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(HRT_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+  return HRT_OK;
 }
 
 }  // namespace
@@ -384,36 +556,54 @@ void xpass_twiddles(int64_t n, std::vector<float2>& tw) {
     }
 }
 
+size_t xpass_smem_bytes(int64_t n) {
+  const size_t r1 = static_cast<size_t>(n / 32);
+  return 1024 + 3 * static_cast<size_t>(kTileBytes) + (r1 * 32 + 32 * 32) * sizeof(float2) +
+         2 * static_cast<size_t>(n) * sizeof(float) + 2 * sizeof(uint64_t);
+}
+
 template <int R1, bool TWO>
 static hrt_status launch_r1(const void* in, int64_t n, double box, double pref, const float2* tw,
-                            const XpassSet& a, const XpassSet& b, cudaStream_t s) {
-  constexpr int P = 32 / R1, LD = kXWarps * P + 1;
-  const int nzc = static_cast<int>(n / 2 + 1), nzp = static_cast<int>(xpass_row(n));
-  const int kz_tiles = static_cast<int>((n / 2) / (kXWarps * P) + 1);
-  const size_t smem = (static_cast<size_t>(R1) * 32 + 32 * 32) * sizeof(float2) + 2 * n * sizeof(float) +
-                      2 * static_cast<size_t>(n) * LD * sizeof(float2);
+                            const XpassSet& a, const XpassSet& b, int* err, cudaStream_t s) {
+  using G = Geo<R1>;
+  const int nzc = static_cast<int>(n / 2 + 1);
+  const int64_t flat = n * nzc;
+  if (flat % G::TK != 0) return fail(HRT_ERR_INVALID_ARG, "x-pass: pencils per plane not a multiple of the tile");
+  for (const XpassSet* x : {&a, &b})
+    if (x->n_out > 0 && (reinterpret_cast<uintptr_t>(x->out) & 15) != 0)
+      return fail(HRT_ERR_INVALID_ARG, "x-pass: output spectra must be 16-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(in) & 15) != 0) return fail(HRT_ERR_INVALID_ARG, "x-pass: input must be 16-byte aligned");
+  CUtensorMap in_map, map_a, map_b;
+  HRT_TRY(make_map<R1>(&in_map, in, static_cast<int>(n), 0));
+  HRT_TRY(make_map<R1>(&map_a, a.out, static_cast<int>(n), a.n_out));
+  if (TWO) HRT_TRY(make_map<R1>(&map_b, b.out, static_cast<int>(n), b.n_out));
+  else map_b = map_a;
+  const size_t smem = xpass_smem_bytes(n);
   int dev = 0, sms = 0;
   HRT_CUDA(cudaGetDevice(&dev));
   HRT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   HRT_CUDA(cudaFuncSetAttribute(xpass_kernel<R1, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(smem)));
-  const int tiles = static_cast<int>(n) * kz_tiles;
+  const int tiles = static_cast<int>(flat / G::TK);
   const int grid = std::min(tiles, sms);
   const double scale = -pref / (static_cast<double>(n) * n * n);
-  xpass_kernel<R1, TWO><<<grid, kXWarps * 32, smem, s>>>(static_cast<const float2*>(in), static_cast<int>(n), nzc, nzp,
-                                                    kz_tiles, static_cast<float>(2.0 * M_PI / box),
-                                                    static_cast<float>(scale), tw, a, b);
+  xpass_kernel<R1, TWO><<<grid, kXThreads, smem, s>>>(in_map, map_a, map_b, nzc, tiles,
+                                                      static_cast<float>(2.0 * M_PI / box), static_cast<float>(scale),
+                                                      tw, a, b, err);
   HRT_LAUNCHED("xpass_kernel");
   return HRT_OK;
 }
 
 hrt_status launch_xpass(const void* in, int64_t n, double box, double pref, const float2* tw, const XpassSet& a,
-                        const XpassSet& b, cudaStream_t s) {
+                        const XpassSet& b, int* err, cudaStream_t s) {
+  // every set has the x and y components (and z when n_out is 3): the x-pass stores V as d_y V [and d_z V]
+  if (a.n_out < 2 || a.n_out > 3 || b.n_out == 1 || b.n_out < 0 || b.n_out > 3 || !err)
+    return fail(HRT_ERR_INVALID_ARG, "x-pass: bad output sets");
   const bool two = b.n_out > 0;
   switch (n) {
-    case 256: return two ? launch_r1<8, true>(in, n, box, pref, tw, a, b, s) : launch_r1<8, false>(in, n, box, pref, tw, a, b, s);
-    case 512: return two ? launch_r1<16, true>(in, n, box, pref, tw, a, b, s) : launch_r1<16, false>(in, n, box, pref, tw, a, b, s);
-    case 1024: return two ? launch_r1<32, true>(in, n, box, pref, tw, a, b, s) : launch_r1<32, false>(in, n, box, pref, tw, a, b, s);
+    case 256: return two ? launch_r1<8, true>(in, n, box, pref, tw, a, b, err, s) : launch_r1<8, false>(in, n, box, pref, tw, a, b, err, s);
+    case 512: return two ? launch_r1<16, true>(in, n, box, pref, tw, a, b, err, s) : launch_r1<16, false>(in, n, box, pref, tw, a, b, err, s);
+    case 1024: return two ? launch_r1<32, true>(in, n, box, pref, tw, a, b, err, s) : launch_r1<32, false>(in, n, box, pref, tw, a, b, err, s);
     default: return fail(HRT_ERR_INVALID_ARG, "x-pass needs a mesh side of 256, 512 or 1024");
   }
 }

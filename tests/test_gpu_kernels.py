@@ -301,10 +301,12 @@ def test_invalid_arguments_enqueue_nothing(hrt):
     torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("n", [256, 1024])
-def test_pm_split_path_matches_3d_path(hrt, n):
+@pytest.mark.parametrize("n,rays", [(256, True), (256, False), (512, True), (512, False), (1024, True)])
+def test_pm_split_path_matches_3d_path(hrt, n, rays):
     # batched 2D (y, z) plans + the x-pass kernel against 3D plans + the k-space kernel, for the particle fields
-    # and for separately filtered ray fields with a learned table; the two differ by FP32 FFT rounding only
+    # alone (one filter set) and with separately filtered ray fields with a learned table (two sets); the two
+    # paths differ by FP32 FFT rounding only.  Every mesh side of the x-pass: 32 R1 points with R1 = 8, 16, 32
+    # (4, 2 and 1 pencils per warp)
     box, pref = 1000.0 * n / 1024, 0.45
     g = torch.Generator(device="cuda").manual_seed(n)
     rho = 1.0 + 0.5 * torch.randn(n, n, n, device="cuda", generator=g)
@@ -314,18 +316,22 @@ def test_pm_split_path_matches_3d_path(hrt, n):
     fr = hrt.make_filter(4.0, box / n, gt, kmax)
     out = {}
     for split in (False, True):
-        pm = hrt.PM(n, box, n_ray_fields=2)
+        pm = hrt.PM(n, box, n_ray_fields=2 if rays else 0)
         pm.set_split(split)
         grad = torch.empty(3, n, n, n, device="cuda")
-        rgrad = torch.empty(2, n, n, n, device="cuda")
-        pm.solve(rho.clone(), pref, f, grad, fr, rgrad)
+        if rays:
+            rgrad = torch.empty(2, n, n, n, device="cuda")
+            pm.solve(rho.clone(), pref, f, grad, fr, rgrad)
+            out[split] = (grad, rgrad)
+        else:
+            pm.solve(rho.clone(), pref, f, grad)
+            out[split] = (grad,)
         torch.cuda.synchronize()
-        out[split] = (grad, rgrad)
         if split:
             with pytest.raises(hrt.HRTError):
                 pm.density_spectrum(torch.empty(n, n, n // 2 + 1, dtype=torch.complex64, device="cuda"))
         pm.close()
-    for k in range(2):
+    for k in range(len(out[False])):
         for j in range(out[False][k].shape[0]):
             ref = out[False][k][j]
             err = (out[True][k][j] - ref).abs().max().item()
