@@ -271,6 +271,7 @@ struct hrt_pm {
   cufftHandle r2c2d = 0, c2r2d = 0;
   bool have_r2c2d = false, have_c2r2d = false;
   float2* xtw = nullptr;    // x-FFT twiddles
+  int* xerr = nullptr;      // device error word of the x-pass (a timed-out wait for a tile's copy)
   bool last_split = false;  // rho_hat holds the (y, z)-transformed density of the split path
 };
 
@@ -335,6 +336,8 @@ static hrt_status pm_make_split(hrt_pm* pm, size_t* work) {
   *work = std::max(w1, w2);
   std::vector<float2> tw;
   xpass_twiddles(pm->n, tw);
+  HRT_TRY(device_alloc(reinterpret_cast<void**>(&pm->xerr), sizeof(int), pm->stream, "x-pass error word"));
+  HRT_CUDA(cudaMemsetAsync(pm->xerr, 0, sizeof(int), pm->stream));
   HRT_TRY(device_alloc(reinterpret_cast<void**>(&pm->xtw), tw.size() * sizeof(float2), pm->stream, "twiddles"));
   HRT_CUDA(cudaMemcpyAsync(pm->xtw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, pm->stream));
   // the host vector must outlive the copy
@@ -411,6 +414,7 @@ static void pm_release(hrt_pm* pm) {
   if (pm->have_r2c2d) cufftDestroy(pm->r2c2d);
   if (pm->have_c2r2d) cufftDestroy(pm->c2r2d);
   device_free(pm->xtw, pm->stream);
+  device_free(pm->xerr, pm->stream);
   device_free(pm->work, pm->stream);
   device_free(pm->rho_hat, pm->stream);
   device_free(pm->grad_hat, pm->stream);
@@ -493,7 +497,7 @@ static hrt_status pm_solve(hrt_pm* pm, float* rho, double pref, const hrt_filter
     const XpassSet xb = rays ? set(pm->tab_b, *fr, pm->n_ray, gh + 3 * sp) : XpassSet{};
     {
       PhaseScope ps(pc, 4);
-      HRT_TRY(launch_xpass(pm->rho_hat, n, pm->box, pref, pm->xtw, xa, xb, pm->stream));
+      HRT_TRY(launch_xpass(pm->rho_hat, n, pm->box, pref, pm->xtw, xa, xb, pm->xerr, pm->stream));
     }
     if (before_fields) HRT_CUDA(cudaStreamWaitEvent(pm->stream, before_fields, 0));
     PhaseScope ps(pc, 5);
@@ -577,13 +581,34 @@ static hrt_status ctx_sort(hrt_ctx* ctx) {
   const int64_t np = c.n_side * c.n_side * c.n_side;
   cudaStream_t st = ctx->stream;
   if (!ctx->disp_alt) {
-    HRT_TRY(device_alloc(reinterpret_cast<void**>(&ctx->disp_alt), 3 * np * sizeof(float), st, "sorted particles"));
-    HRT_TRY(device_alloc(reinterpret_cast<void**>(&ctx->mom_alt), 3 * np * sizeof(float), st, "sorted particles"));
-    HRT_TRY(device_alloc(reinterpret_cast<void**>(&ctx->order_buf[0]), np * sizeof(int32_t), st, "particle order"));
-    HRT_TRY(device_alloc(reinterpret_cast<void**>(&ctx->order_buf[1]), np * sizeof(int32_t), st, "particle order"));
-    HRT_TRY(device_alloc(reinterpret_cast<void**>(&ctx->sort_scratch),
-                         (particle_sort_counts(c.n_mesh) + 3 * np) * sizeof(int32_t), st, "sort scratch"));
+    // All five buffers or none: they are allocated into locals and handed to the context only together, so
+    // a failed allocation (which leaves the context usable) never leaves a partial set that a later sort
+    // would launch on.
+    float *disp_alt = nullptr, *mom_alt = nullptr;
+    int32_t *order0 = nullptr, *order1 = nullptr, *scratch = nullptr;
+    hrt_status s = device_alloc(reinterpret_cast<void**>(&disp_alt), 3 * np * sizeof(float), st, "sorted particles");
+    if (s == HRT_OK) s = device_alloc(reinterpret_cast<void**>(&mom_alt), 3 * np * sizeof(float), st, "sorted particles");
+    if (s == HRT_OK) s = device_alloc(reinterpret_cast<void**>(&order0), np * sizeof(int32_t), st, "particle order");
+    if (s == HRT_OK) s = device_alloc(reinterpret_cast<void**>(&order1), np * sizeof(int32_t), st, "particle order");
+    if (s == HRT_OK)
+      s = device_alloc(reinterpret_cast<void**>(&scratch), (particle_sort_counts(c.n_mesh) + 3 * np) * sizeof(int32_t),
+                       st, "sort scratch");
+    if (s != HRT_OK) {
+      device_free(disp_alt, st);
+      device_free(mom_alt, st);
+      device_free(order0, st);
+      device_free(order1, st);
+      device_free(scratch, st);
+      return s;
+    }
+    ctx->disp_alt = disp_alt;
+    ctx->mom_alt = mom_alt;
+    ctx->order_buf[0] = order0;
+    ctx->order_buf[1] = order1;
+    ctx->sort_scratch = scratch;
   }
+  if (!ctx->mom_alt || !ctx->order_buf[0] || !ctx->order_buf[1] || !ctx->sort_scratch)
+    return fail(HRT_ERR_STATE, "particle sort buffers are incomplete");
   const int dst = ctx->order_cur == 0 ? 1 : 0;
   int32_t* counts = ctx->sort_scratch;
   int32_t* keys = counts + particle_sort_counts(c.n_mesh);
@@ -1547,8 +1572,8 @@ hrt_status hrt_init_particles(hrt_ctx* ctx, const float* disp, const float* mom,
   if (!disp || !mom || !(a > 0.0 && a <= 1.0)) return fail(HRT_ERR_INVALID_ARG, "bad particle arguments");
   tape_invalidate(ctx, "the adjoint starts from initial conditions drawn from white noise");
   const size_t bytes = 3 * static_cast<size_t>(ctx->cfg.n_side * ctx->cfg.n_side * ctx->cfg.n_side) * sizeof(float);
-  hrt_status s = cuda_status(cudaMemcpyAsync(ctx->disp, disp, bytes, cudaMemcpyDeviceToDevice, ctx->stream), "copy disp");
-  if (s == HRT_OK) s = cuda_status(cudaMemcpyAsync(ctx->mom, mom, bytes, cudaMemcpyDeviceToDevice, ctx->stream), "copy mom");
+  hrt_status s = cuda_status(cudaMemcpyAsync(ctx->disp, disp, bytes, cudaMemcpyDefault, ctx->stream), "copy disp");
+  if (s == HRT_OK) s = cuda_status(cudaMemcpyAsync(ctx->mom, mom, bytes, cudaMemcpyDefault, ctx->stream), "copy mom");
   if (s != HRT_OK) return ctx_mark(ctx, s);
   ctx_lattice_order(ctx);
   ctx->a = ctx->a_mom = ctx->cfg.static_mode ? 1.0 : a;
@@ -1577,8 +1602,11 @@ hrt_status hrt_init_rays(hrt_ctx* ctx, const double* theta0, int64_t n_rays) {
     s = device_alloc(reinterpret_cast<void**>(&ctx->maps), 4 * n_rays * ctx->cfg.n_sources * sizeof(float), st, "maps");
   if (s == HRT_OK && ctx->maps)
     s = cuda_status(cudaMemsetAsync(ctx->maps, 0, 4 * n_rays * ctx->cfg.n_sources * sizeof(float), st), "maps memset");
-  if (s == HRT_OK) s = launch_rays_init(r, theta0, st);
-  if (s == HRT_OK) s = tape_on_rays(ctx, theta0, n_rays);
+  // theta0 may be host or device memory: it is copied into the context first and initialised in place
+  if (s == HRT_OK)
+    s = cuda_status(cudaMemcpyAsync(r.theta, theta0, 2 * n_rays * sizeof(double), cudaMemcpyDefault, st), "theta0");
+  if (s == HRT_OK) s = launch_rays_init(r, r.theta, st);
+  if (s == HRT_OK) s = tape_on_rays(ctx, r.theta, n_rays);
   if (s != HRT_OK) {
     device_free(r.theta, st);
     device_free(r.eta, st);
@@ -1722,10 +1750,10 @@ hrt_status hrt_read_rays(hrt_ctx* ctx, double* theta, float* eta, float* A, floa
   const int64_t r = ctx->rays.n_rays;
   if (r == 0) return fail(HRT_ERR_STATE, "no rays");
   hrt_status s = HRT_OK;
-  if (theta) s = cuda_status(cudaMemcpyAsync(theta, ctx->rays.theta, 2 * r * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream), "read theta");
-  if (s == HRT_OK && eta) s = cuda_status(cudaMemcpyAsync(eta, ctx->rays.eta, 2 * r * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream), "read eta");
-  if (s == HRT_OK && A) s = cuda_status(cudaMemcpyAsync(A, ctx->rays.A, 4 * r * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream), "read A");
-  if (s == HRT_OK && B) s = cuda_status(cudaMemcpyAsync(B, ctx->rays.B, 4 * r * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream), "read B");
+  if (theta) s = cuda_status(cudaMemcpyAsync(theta, ctx->rays.theta, 2 * r * sizeof(double), cudaMemcpyDefault, ctx->stream), "read theta");
+  if (s == HRT_OK && eta) s = cuda_status(cudaMemcpyAsync(eta, ctx->rays.eta, 2 * r * sizeof(float), cudaMemcpyDefault, ctx->stream), "read eta");
+  if (s == HRT_OK && A) s = cuda_status(cudaMemcpyAsync(A, ctx->rays.A, 4 * r * sizeof(float), cudaMemcpyDefault, ctx->stream), "read A");
+  if (s == HRT_OK && B) s = cuda_status(cudaMemcpyAsync(B, ctx->rays.B, 4 * r * sizeof(float), cudaMemcpyDefault, ctx->stream), "read B");
   return ctx_mark(ctx, s);
 }
 
@@ -1738,7 +1766,7 @@ hrt_status hrt_read_maps(hrt_ctx* ctx, int32_t source, float* kappa, float* gamm
   float* dst[4] = {kappa, gamma1, gamma2, omega};
   for (int i = 0; i < 4; ++i)
     if (dst[i]) {
-      hrt_status s = cuda_status(cudaMemcpyAsync(dst[i], base + i * r, r * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream), "read map");
+      hrt_status s = cuda_status(cudaMemcpyAsync(dst[i], base + i * r, r * sizeof(float), cudaMemcpyDefault, ctx->stream), "read map");
       if (s != HRT_OK) return ctx_mark(ctx, s);
     }
   return HRT_OK;
