@@ -50,6 +50,8 @@ def parse():
                    help="skip the timings of the widened rows (tiled light cone, accumulated sources, 2LPT ICs)")
     p.add_argument("--no-learned", action="store_true",
                    help="skip the learned-correction comparison (coarse learned vs coarse plain vs fine plain)")
+    p.add_argument("--no-precision", action="store_true",
+                   help="skip the per-output errors against the stored FP64 oracle outputs (and the FP32-angle ablation)")
     p.add_argument("--sort-every", type=int, default=None,
                    help="re-sort the particles by mesh cell every K particle steps (default: the library's, 4; 0: never)")
     p.add_argument("--kick", default="direct", choices=["direct", "mesh"],
@@ -297,52 +299,46 @@ def run_gpu(args, W, world, rank, local):
     phases = ctx.hrt_ctx_phase_times()
     ctx.hrt_ctx_set_profiling(False)
 
-    # end-to-end through the public API from pinned host buffers
+    # end-to-end through the C ABI with host buffers: the initial state goes in from pinned host memory through
+    # hrt_init_particles / hrt_init_rays (their copies run inside the calls), and every step's result comes back
+    # through hrt_read_rays into a pinned host buffer (the ray angles theta, i.e. the deflections), plus the
+    # convergence map through hrt_read_maps at source-plane steps; all of it inside the timed region
     e2e = None
     if not args.no_e2e:
         disp_h = torch.empty(disp0.shape, dtype=torch.float32, pin_memory=True)
         mom_h = torch.empty(mom0.shape, dtype=torch.float32, pin_memory=True)
         disp_h.copy_(disp0)
         mom_h.copy_(mom0)
-        th_h = theta0_h.pin_memory()
+        th_h = theta0_h.contiguous().pin_memory()
+        theta_out_h = torch.empty(W.n_rays, 2, dtype=torch.float64, pin_memory=True)
         kmaps_h = torch.empty(len(slots), W.n_rays, dtype=torch.float32, pin_memory=True)
-        disp_d = torch.empty_like(disp0)
-        mom_d = torch.empty_like(mom0)
-        th_d = torch.empty_like(theta0)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        disp_d.copy_(disp_h, non_blocking=True)
-        mom_d.copy_(mom_h, non_blocking=True)
-        th_d.copy_(th_h, non_blocking=True)
-        ctx.hrt_init_particles(disp_d, mom_d, 1.0)
-        ctx.hrt_init_rays(th_d)
-        h2d = disp_h.numel() * 4 + mom_h.numel() * 4 + th_h.numel() * 8
-        d2h = 0
-        p = 0
+        h2d = d2h = 0
+        p = len(grid) - 1
         for i in range(args.steps):
             if p == len(grid) - 1:
-                disp_d.copy_(disp_h, non_blocking=True)
-                mom_d.copy_(mom_h, non_blocking=True)
-                ctx.hrt_init_particles(disp_d, mom_d, 1.0)
-                ctx.hrt_init_rays(th_d)
-                h2d += disp_h.numel() * 4 + mom_h.numel() * 4
+                ctx.hrt_init_particles(disp_h, mom_h, 1.0)
+                ctx.hrt_init_rays(th_h)
+                h2d += disp_h.numel() * 4 + mom_h.numel() * 4 + th_h.numel() * 8
                 p = 0
             n = p + 1
             ctx.hrt_step(grid[n], slots.get(n, -1))
+            ctx.hrt_read_rays_into(theta_out_h)
+            d2h += theta_out_h.numel() * 8
             if n in slots:
-                kmaps_h[slots[n]].copy_(ctx.hrt_read_maps(slots[n])[0], non_blocking=True)
+                ctx.hrt_read_maps_into(slots[n], kmaps_h[slots[n]])
                 d2h += W.n_rays * 4
             p = n
-        last = torch.empty(1, dtype=torch.float32, pin_memory=True)
-        last.copy_(ctx.hrt_read_maps(0)[0][:1], non_blocking=True)
-        d2h += 4
         e1.record(stream)
         barrier()
         e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        assert bool(torch.isfinite(theta_out_h).all()), "non-finite ray angles read back"
         e2e = {"value": replica_rate(args.steps, e_ms, world), "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps)}
+               "h2d_bytes_per_step": int(h2d / args.steps), "d2h_bytes_per_step": int(d2h / args.steps),
+               "returned": "ray angles theta every step, kappa maps at source-plane steps"}
 
     # roofline of the dominant kernel of this library (by time in the phase pass)
     algo = algorithmic_bytes(W)
@@ -669,6 +665,57 @@ def run_reference(args, W, rank):
     }
 
 
+def precision_errors():
+    """Per-output error of the GPU path against the FP64 oracle on the 1024^3 workload's recipe scaled to 128^3
+    particles, 256^3 mesh and 512^2 rays (the oracle's outputs are the ones stored by
+    tests/golden/make_cosmo_1024_recipe_128p.py), for the method as built (FP64 ray angles and positions, FP32
+    mesh, FFT and gathers) and for the FP32 ray-angle ablation.  Deflections: |theta - theta_oracle| over the
+    largest deflection; maps: |error| over the rms of the oracle's kappa map; P(ell): relative error per bin."""
+    import numpy as np
+    import torch
+    from paper_2405_12913_gb300 import hrt
+    from paper_2405_12913_gb300.configs import COSMO_1024_SCALED as W
+    import synthetic
+    g = np.load(os.path.join(ROOT, "tests", "golden", "cosmo_1024_recipe_128p.npz"))
+    noise = torch.tensor(synthetic.white_noise(W.seed, W.n_side), dtype=torch.float32, device="cuda")
+    theta0 = torch.tensor(synthetic.pixel_grid(W.n_pix, W.fov_deg * synthetic.DEGREE), device="cuda")
+    slots = {s: i for i, s in enumerate(W.source_steps)}
+    ir = g["ray_index"]
+    lmin, lmax = W.ell_range
+    out = {"workload": W.name, "reference": "FP64 oracle (stored outputs at 4096 sampled rays; all P(ell) bins)"}
+    for bits in (64, 32):
+        cfg = hrt.make_config(W.n_mesh, W.box, W.n_side, W.omega_m, W.h, W.n_s, W.sigma8, W.deconv_p,
+                              W.smooth_cells, W.samples_per_cell, W.observer, n_sources=len(W.source_steps))
+        ctx = hrt.Context(cfg)
+        ctx.hrt_set_ray_theta_bits(bits)
+        ctx.hrt_init_particles_zeldovich(noise, W.a_init)
+        for a in W.forward_grid[1:]:
+            ctx.hrt_step(a)
+        ctx.hrt_init_rays(theta0)
+        for n, a in enumerate(W.reverse_grid[1:], start=1):
+            ctx.hrt_step(a, slots.get(n, -1))
+        th = ctx.hrt_read_rays()[0].cpu().numpy()
+        row = {}
+        d = np.abs(th[ir] - g["theta"]).max(axis=1) / float(g["alpha_absmax"])
+        row["deflection"] = {"max": float(d.max()), "median": float(np.median(d))}
+        for s, i in slots.items():
+            maps = ctx.hrt_read_maps(i).cpu().double().numpy()[:, ir]
+            rms = float(g[f"kappa_rms_{s}"])
+            per = {}
+            for k, name in enumerate(("kappa", "gamma1", "gamma2", "omega")):
+                e = np.abs(maps[k] - g[f"maps_{s}"][k]) / rms
+                per[name] = {"max": float(e.max()), "p99": float(np.quantile(e, 0.99)), "median": float(np.median(e))}
+            _, p, cnt = ctx.hrt_ctx_kappa_power(i, W.n_pix, W.dtheta, W.nbins, lmin, lmax)
+            ok = cnt > 0
+            rel = np.abs(p[ok] / g[f"power_{s}"][ok] - 1.0)
+            per["power_per_bin"] = [float(x) for x in rel]
+            per["power_max"] = float(rel.max())
+            row[f"source_step_{s}"] = per
+        ctx.close()
+        out["fp64_angles" if bits == 64 else "fp32_angles_ablation"] = row
+    return out
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -682,6 +729,8 @@ def main():
     line = run_gpu(args, W, world, rank, local)
     if line is None:
         return 0
+    if world == 1 and not args.no_precision:
+        line["precision"] = precision_errors()
     if world == 1 and not args.no_learned:
         line["learned"] = learned_comparison()
     if world == 1 and not args.no_cpu_baseline:

@@ -133,7 +133,10 @@ hrt_status hrt_kspace_gradient(const void* rho_hat, int64_t n, double box, doubl
  * call before any stream capture.  Each call overwrites the whole array with its own tables before its kernel
  * reads them, so nothing has to start at zero; but every call shares the array, so calls whose work overlaps
  * on the GPU (different streams, or several host threads) race and may read each other's tables: serialise
- * them, e.g. on one stream.  No cudaMalloc, cudaFree or allocating library routine is called. */
+ * them, e.g. on one stream.  No cudaMalloc, cudaFree or allocating library routine is called.  The tables are
+ * staged from a host buffer during the call, so a call made while its stream is being captured into a CUDA
+ * graph returns HRT_ERR_STATE and enqueues nothing.  Invalid arguments (the checks of hrt_kspace_gradient)
+ * return HRT_ERR_INVALID_ARG. */
 hrt_status hrt_kspace_gradient_noalloc(const void* rho_hat, int64_t n, double box, double pref,
                                        const hrt_filter* f, int32_t n_out, void* out, const hrt_filter* f2,
                                        int32_t n_second, void* second, void* stream);
@@ -307,7 +310,9 @@ hrt_status hrt_raymesh_ray_step_tiled(hrt_raymesh* rm, const hrt_rays* rays, con
  * in [ell_min, ell_max) (bin b = floor(nbins ln(ell/ell_min)/ln(ell_max/ell_min) + 1e-9), the 1e-9 placing
  * exact edges in the upper bin), ell = 2 pi |n| / (m dtheta).  Outputs the mean ell, mean power and mode
  * count per bin to host arrays of nbins.  kappa is m x m float32 (m even, 2 <= m <= 16384,
- * 1 <= nbins <= 256).  Synchronises the stream.
+ * 1 <= nbins <= 256).  Synchronises the stream: it first waits for the work already queued on the stream
+ * within the host wait limit (hrt_set_host_wait_limit) and returns HRT_ERR_TIMEOUT, having enqueued nothing,
+ * when that expires; then its own transform and binning run and are waited for.
  * ---------------------------------------------------------------------------------------------------- */
 hrt_status hrt_kappa_power(const float* kappa, int64_t m, double dtheta, int32_t nbins, double ell_min,
                            double ell_max, double* ell_host, double* p_host, int64_t* count_host,
@@ -494,10 +499,11 @@ hrt_status hrt_init_particles_zeldovich(hrt_ctx* ctx, const float* noise, double
  * hrt_ic_2lpt), then the PM force at a_init. */
 hrt_status hrt_init_particles_2lpt(hrt_ctx* ctx, const float* noise, double a_init);
 
-/* Particles from caller state (copied) at scale factor a (momentum synchronised at a), then the force. */
+/* Particles from caller state (copied) at scale factor a (momentum synchronised at a), then the force.  disp and
+ * mom may be device or host memory (stream-ordered copies; pinned host memory keeps the call asynchronous). */
 hrt_status hrt_init_particles(hrt_ctx* ctx, const float* disp, const float* mom, double a);
 
-/* Rays at the observer (copied): theta0[n_rays][2]. */
+/* Rays at the observer (copied): theta0[n_rays][2], in device or host memory. */
 hrt_status hrt_init_rays(hrt_ctx* ctx, const double* theta0, int64_t n_rays);
 
 /* One co-evolution step from the current a to a_next (Alg. 1): if rays exist and a_next < a they are
@@ -634,12 +640,48 @@ hrt_status hrt_step_static(hrt_ctx* ctx, double chi_from, double chi_to, int32_t
 /* Exact force-free drift of the rays (see hrt_ray_drift_free). */
 hrt_status hrt_drift_free(hrt_ctx* ctx, double chi_from, double chi_to);
 
-/* Copies of the context state into caller device buffers (any pointer may be NULL). */
+/* Copies of the context state into caller buffers (any pointer may be NULL), stream-ordered on the context's
+ * stream.  hrt_read_rays and hrt_read_maps accept device or host memory (a pinned host buffer is filled
+ * asynchronously: synchronise the stream before reading it); hrt_read_particles and hrt_read_grad write
+ * device memory only. */
 hrt_status hrt_read_rays(hrt_ctx* ctx, double* theta, float* eta, float* A, float* B);
 hrt_status hrt_read_maps(hrt_ctx* ctx, int32_t source, float* kappa, float* gamma1, float* gamma2,
                          float* omega);
 hrt_status hrt_read_particles(hrt_ctx* ctx, float* disp, float* mom, double* a_host, double* a_mom_host);
 hrt_status hrt_read_grad(hrt_ctx* ctx, float* grad /* [3][n^3] */);
+
+/* Opt-in checks for NaN and infinity (off by default).  With on = 1, hrt_init_particles and hrt_init_rays
+ * scan the state they copied in and return HRT_ERR_NONFINITE before using it (the context then has no
+ * particles, or no rays), and hrt_step / hrt_step_accumulate scan the particle state, the ray state and the
+ * maps after the step and return HRT_ERR_NONFINITE if any value is not finite.  Each check waits for the
+ * context's stream (within the host wait limit), so it costs a synchronisation and a pass over the state.
+ * A kernel that gave up waiting for its own copies is reported here as HRT_ERR_TIMEOUT.  Neither status
+ * poisons the context. */
+hrt_status hrt_set_nonfinite_check(hrt_ctx* ctx, int32_t on);
+
+/* Poisson prefactor of a static lens of total mass `mass` (Msun/h) in a periodic box of side `box` (Mpc/h):
+ * 4 pi G M / box^3 in the library's units ((100 km/s)^2 per (Mpc/h)^2), the value hrt_config.static_pref takes
+ * for the point-mass test (Sec. 6.1; the FFT solve then sees delta = rho / rho_mean - 1).  HRT_ERR_INVALID_ARG
+ * for a non-positive or non-finite mass or box. */
+hrt_status hrt_static_prefactor(double mass, double box, double* pref);
+
+/* Precision ablation of the direct line-of-sight kick: bits = 64 (the default, the method as built) keeps the
+ * ray angles in FP64 and forms each interpolation position from an FP64 cell / fraction split (Alg. 1 ray
+ * state, Sec. 3.1); bits = 32 keeps the angles in FP32 (rounded after every drift) and forms the positions in
+ * FP32, which is what a single-precision build would do.  For measuring what the FP64 parts buy; a recorded run
+ * for hrt_adjoint is invalidated by bits = 32.  HRT_ERR_INVALID_ARG for other values. */
+hrt_status hrt_set_ray_theta_bits(hrt_ctx* ctx, int32_t bits);
+
+/* Host-side fault injection for tests of the error paths: the k-th device allocation of the library from now
+ * (1-based) reports HRT_ERR_OOM as if the device were out of memory; k = 0 turns it off.  The environment
+ * variable HRT_FAIL_ALLOC_AT=k does the same from process start.  Process-wide; HRT_ERR_INVALID_ARG for k < 0. */
+hrt_status hrt_inject_alloc_failure(int64_t k);
+
+/* Process-wide limit, in seconds, of the library's host waits for a stream (hrt_kappa_power and
+ * hrt_ctx_kappa_power waiting for the work already queued, the checks above); seconds <= 0 removes it (the
+ * default).  When a wait exceeds it the call returns HRT_ERR_TIMEOUT; the queued work keeps running and the
+ * call may be repeated.  HRT_ERR_INVALID_ARG for NaN. */
+hrt_status hrt_set_host_wait_limit(double seconds);
 
 /* Power spectrum of the kappa map of `source` (the rays must form an m x m image, m^2 = n_rays). */
 hrt_status hrt_ctx_kappa_power(hrt_ctx* ctx, int32_t source, int64_t m, double dtheta, int32_t nbins,

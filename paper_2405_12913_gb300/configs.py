@@ -9,7 +9,6 @@ import math
 from dataclasses import dataclass, field
 
 DEG = math.pi / 180.0
-G_NEWTON = 4.30091727e-13  # (Mpc/h) (100 km/s)^2 / (Msun/h)
 
 
 @dataclass(frozen=True)
@@ -43,10 +42,6 @@ class PointMassWorkload:
     @property
     def lens_position(self):
         return (0.5 * self.box, 0.5 * self.box, 0.5 * self.box)
-
-    @property
-    def static_pref(self) -> float:
-        return 4.0 * math.pi * G_NEWTON * self.mass / self.box ** 3
 
     @property
     def chi_grid(self):

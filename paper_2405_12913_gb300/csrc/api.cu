@@ -5,10 +5,14 @@
 #include <cufftXt.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "adjoint.h"
@@ -52,14 +56,27 @@ static hrt_status cufft_status(cufftResult r, const char* what) {
 }
 #define HRT_CUFFT(expr) HRT_TRY(::hrt::cufft_status((expr), #expr))
 
+// Host-side allocation-failure injection: the target-th device allocation counted from the last reset reports
+// out-of-memory (0: off).  The environment variable HRT_FAIL_ALLOC_AT sets the first target of the process.
+static std::atomic<long> g_fail_target{-1};
+static std::atomic<long> g_alloc_count{0};
+
+void set_alloc_failure(int64_t k) {
+  g_alloc_count.store(0);
+  g_fail_target.store(static_cast<long>(k));
+}
+
 bool inject_alloc_failure() {
-  static long target = [] {
+  long target = g_fail_target.load();
+  if (target < 0) {
     const char* v = std::getenv("HRT_FAIL_ALLOC_AT");
-    return v ? std::atol(v) : 0L;
-  }();
-  static long count = 0;
+    long t = v ? std::atol(v) : 0L;
+    long expected = -1;
+    g_fail_target.compare_exchange_strong(expected, t < 0 ? 0 : t);
+    target = g_fail_target.load();
+  }
   if (target <= 0) return false;
-  return ++count == target;
+  return g_alloc_count.fetch_add(1) + 1 == target;
 }
 
 hrt_status device_alloc(void** p, size_t bytes, cudaStream_t stream, const char* what) {
@@ -71,6 +88,24 @@ hrt_status device_alloc(void** p, size_t bytes, cudaStream_t stream, const char*
 
 void device_free(void* p, cudaStream_t s) {
   if (p) cudaFreeAsync(p, s);
+}
+
+static std::atomic<double> g_wait_limit{0.0};
+
+hrt_status wait_stream(cudaStream_t s, const char* what) {
+  const double limit = g_wait_limit.load();
+  if (!(limit > 0.0)) return cuda_status(cudaStreamSynchronize(s), what);
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaStreamQuery(s);
+    if (e == cudaSuccess) return HRT_OK;
+    if (e != cudaErrorNotReady) return cuda_status(e, what);
+    const double waited = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (waited > limit)
+      return fail(HRT_ERR_TIMEOUT, "%s: the queued work did not finish within the host wait limit of %g s", what,
+                  limit);
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
 }
 
 // Uploads host floats to a fresh stream-ordered device buffer (the host copy is consumed before return).
@@ -121,6 +156,7 @@ static hrt_status build_ray_params(const hrt_ray_geom& g, double chi_from, doubl
   p.tile_w = 0;
   p.map_accumulate = 0;
   p.map_weight = 1.f;
+  p.theta32 = 0;
   p.tiled = g.n_replicas > 0 ? 1 : 0;
   if (p.tiled) {
     if (g.n_replicas > kMaxReplicas || !g.replica_perm || !g.replica_sign || !g.replica_shift)
@@ -558,6 +594,46 @@ static hrt_status ctx_mark(hrt_ctx* ctx, hrt_status s) {
   return s;
 }
 
+// The opt-in check for NaN and infinity: scans the given arrays on the context's stream (after everything queued
+// so far), waits within the host wait limit and returns HRT_ERR_NONFINITE if any value is not finite.  Also
+// reports a kernel that gave up waiting for its own copies (the x-pass error word) as HRT_ERR_TIMEOUT.
+struct ScanItem {
+  const void* p;
+  int64_t n;
+  bool dbl;
+};
+
+static hrt_status ctx_scan(hrt_ctx* ctx, std::initializer_list<ScanItem> items, const char* what) {
+  if (!ctx->check_finite) return HRT_OK;
+  cudaStream_t st = ctx->stream;
+  HRT_CUDA(cudaMemsetAsync(ctx->finite_flag, 0, sizeof(int), st));
+  for (const ScanItem& it : items) {
+    if (!it.p) continue;
+    if (it.dbl) HRT_TRY(launch_nonfinite_scan(static_cast<const double*>(it.p), it.n, ctx->finite_flag, st));
+    else HRT_TRY(launch_nonfinite_scan(static_cast<const float*>(it.p), it.n, ctx->finite_flag, st));
+  }
+  HRT_TRY(wait_stream(st, what));
+  int flag = 0, xerr = 0;
+  HRT_CUDA(cudaMemcpy(&flag, ctx->finite_flag, sizeof(int), cudaMemcpyDeviceToHost));
+  if (ctx->pm && ctx->pm->xerr) HRT_CUDA(cudaMemcpy(&xerr, ctx->pm->xerr, sizeof(int), cudaMemcpyDeviceToHost));
+  if (xerr) return fail(HRT_ERR_TIMEOUT, "%s: the x-pass gave up waiting for a tile's copy", what);
+  if (flag) return fail(HRT_ERR_NONFINITE, "%s: a NaN or an infinity was found", what);
+  return HRT_OK;
+}
+
+static hrt_status ctx_scan_state(hrt_ctx* ctx, const char* what) {
+  const int64_t np3 = 3 * ctx->cfg.n_side * ctx->cfg.n_side * ctx->cfg.n_side, r = ctx->rays.n_rays;
+  return ctx_scan(ctx,
+                  {{ctx->have_particles ? ctx->disp : nullptr, np3, false},
+                   {ctx->have_particles ? ctx->mom : nullptr, np3, false},
+                   {ctx->rays.theta, 2 * r, true},
+                   {ctx->rays.eta, 2 * r, false},
+                   {ctx->rays.A, 4 * r, false},
+                   {ctx->rays.B, 4 * r, false},
+                   {ctx->maps, 4 * r * ctx->cfg.n_sources, false}},
+                  what);
+}
+
 const int32_t* ctx_order(const hrt_ctx* ctx) { return ctx->order_cur >= 0 ? ctx->order_buf[ctx->order_cur] : nullptr; }
 
 hrt_status ctx_particles_lattice(hrt_ctx* ctx, float* disp_out, float* mom_out) {
@@ -574,9 +650,8 @@ hrt_status ctx_particles_lattice(hrt_ctx* ctx, float* disp_out, float* mom_out) 
   return HRT_OK;
 }
 
-// Re-sorts the particles by cell (counting sort by z-row segments): the storage order changes, the particles
-// do not.
-static hrt_status ctx_sort(hrt_ctx* ctx) {
+// Buffers of the particle sort, allocated on first use.
+static hrt_status ctx_sort_alloc(hrt_ctx* ctx) {
   const hrt_config& c = ctx->cfg;
   const int64_t np = c.n_side * c.n_side * c.n_side;
   cudaStream_t st = ctx->stream;
@@ -607,6 +682,16 @@ static hrt_status ctx_sort(hrt_ctx* ctx) {
     ctx->order_buf[1] = order1;
     ctx->sort_scratch = scratch;
   }
+  return HRT_OK;
+}
+
+// Re-sorts the particles by cell (counting sort by z-row segments): the storage order changes, the particles
+// do not.
+static hrt_status ctx_sort(hrt_ctx* ctx) {
+  const hrt_config& c = ctx->cfg;
+  const int64_t np = c.n_side * c.n_side * c.n_side;
+  cudaStream_t st = ctx->stream;
+  HRT_TRY(ctx_sort_alloc(ctx));
   if (!ctx->mom_alt || !ctx->order_buf[0] || !ctx->order_buf[1] || !ctx->sort_scratch)
     return fail(HRT_ERR_STATE, "particle sort buffers are incomplete");
   const int dst = ctx->order_cur == 0 ? 1 : 0;
@@ -642,6 +727,7 @@ static double ctx_pref(const hrt_ctx* ctx, double a) {
 // evaluated at ctx->a first when a correction is set).
 static hrt_status ctx_solve(hrt_ctx* ctx) {
   const hrt_config& c = ctx->cfg;
+  ctx->force_valid = false;
   hrt_filter f = ctx_filter(c, false), fr = ctx_filter(c, true);
   if (ctx->corr_w) {
     const double cell = c.box / c.n_mesh;
@@ -659,12 +745,16 @@ static hrt_status ctx_solve(hrt_ctx* ctx) {
   }
   cudaEvent_t wait = ctx->rays_pending ? ctx->ev_rays : nullptr;
   ctx->rays_pending = false;
-  return pm_solve(ctx->pm, ctx->rho, ctx_pref(ctx, ctx->a), &f, ctx->grad, &fr, ctx->ray_grad, ctx, wait);
+  ctx->force_valid = false;
+  HRT_TRY(pm_solve(ctx->pm, ctx->rho, ctx_pref(ctx, ctx->a), &f, ctx->grad, &fr, ctx->ray_grad, ctx, wait));
+  ctx->force_valid = true;
+  return HRT_OK;
 }
 
 // CIC deposit of the current particles, then the gradient fields.
 static hrt_status ctx_force(hrt_ctx* ctx) {
   const hrt_config& c = ctx->cfg;
+  ctx->force_valid = false;
   {
     PhaseScope ps(ctx, 2);
     HRT_TRY(launch_cic_scatter(ctx->disp, c.n_side, c.n_mesh, c.box, ctx->rho, ctx->stream, ctx_order(ctx)));
@@ -701,6 +791,7 @@ static hrt_status ctx_ray_step(hrt_ctx* ctx, double chi_from, double chi_to, dou
   if (w * w == ctx->rays.n_rays) g.image_width = w;
   HRT_TRY(build_ray_params(g, chi_from, chi_to, a_ref, c.cosmo.omega_m, p));
   set_tiles(g, ctx->rays.n_rays, p);
+  p.theta32 = ctx->theta32 ? 1 : 0;
   p.map_accumulate = accumulate ? 1 : 0;
   p.map_weight = static_cast<float>(weight);
   const int64_t m = c.n_mesh * c.n_mesh * c.n_mesh;
@@ -918,6 +1009,9 @@ hrt_status hrt_kappa_power(const float* kappa, int64_t m, double dtheta, int32_t
       !(ell_max > ell_min))
     return fail(HRT_ERR_INVALID_ARG, "bad power-spectrum arguments");
   cudaStream_t s = as_stream(stream);
+  // first the work already queued on the stream (e.g. the steps that wrote the map), within the host wait limit;
+  // on expiry nothing has been enqueued and the call can be repeated
+  HRT_TRY(wait_stream(s, "hrt_kappa_power"));
   cufftHandle plan;
   HRT_CUFFT(cufftPlan2d(&plan, static_cast<int>(m), static_cast<int>(m), CUFFT_R2C));
   void* spec = nullptr;
@@ -1499,6 +1593,7 @@ hrt_status hrt_destroy(hrt_ctx* ctx) {
   device_free(ctx->rays.A, s);
   device_free(ctx->rays.B, s);
   device_free(ctx->maps, s);
+  device_free(ctx->finite_flag, s);
   device_free(ctx->corr_w, s);
   device_free(ctx->corr_wb, s);
   device_free(ctx->corr_x, s);
@@ -1574,6 +1669,11 @@ hrt_status hrt_init_particles(hrt_ctx* ctx, const float* disp, const float* mom,
   const size_t bytes = 3 * static_cast<size_t>(ctx->cfg.n_side * ctx->cfg.n_side * ctx->cfg.n_side) * sizeof(float);
   hrt_status s = cuda_status(cudaMemcpyAsync(ctx->disp, disp, bytes, cudaMemcpyDefault, ctx->stream), "copy disp");
   if (s == HRT_OK) s = cuda_status(cudaMemcpyAsync(ctx->mom, mom, bytes, cudaMemcpyDefault, ctx->stream), "copy mom");
+  if (s == HRT_OK && ctx->check_finite) {
+    const int64_t n3 = static_cast<int64_t>(bytes / sizeof(float));
+    s = ctx_scan(ctx, {{ctx->disp, n3, false}, {ctx->mom, n3, false}}, "hrt_init_particles");
+    if (s != HRT_OK) ctx->have_particles = false;  // the force is not computed from a non-finite state
+  }
   if (s != HRT_OK) return ctx_mark(ctx, s);
   ctx_lattice_order(ctx);
   ctx->a = ctx->a_mom = ctx->cfg.static_mode ? 1.0 : a;
@@ -1605,6 +1705,7 @@ hrt_status hrt_init_rays(hrt_ctx* ctx, const double* theta0, int64_t n_rays) {
   // theta0 may be host or device memory: it is copied into the context first and initialised in place
   if (s == HRT_OK)
     s = cuda_status(cudaMemcpyAsync(r.theta, theta0, 2 * n_rays * sizeof(double), cudaMemcpyDefault, st), "theta0");
+  if (s == HRT_OK && ctx->check_finite) s = ctx_scan(ctx, {{r.theta, 2 * n_rays, true}}, "hrt_init_rays");
   if (s == HRT_OK) s = launch_rays_init(r, r.theta, st);
   if (s == HRT_OK) s = tape_on_rays(ctx, r.theta, n_rays);
   if (s != HRT_OK) {
@@ -1634,7 +1735,11 @@ hrt_status hrt::ctx_step(hrt_ctx* ctx, double a_next, int32_t source, double wei
   HRT_TRY(ctx_guard(ctx));
   if (ctx->cfg.static_mode) return fail(HRT_ERR_STATE, "hrt_step needs the expanding mode");
   if (!ctx->have_particles) return fail(HRT_ERR_STATE, "no particles");
+  if (!ctx->force_valid) return fail(HRT_ERR_STATE, "no force: an earlier call failed while computing it");
   if (!(a_next > 0.0 && a_next <= 1.0) || a_next == ctx->a) return fail(HRT_ERR_INVALID_ARG, "bad a_next");
+  // a sort due in this step gets its buffers before anything moves, so that an allocation failure leaves the
+  // state as it was
+  if (ctx->sort_every > 0 && ctx->steps_since_sort + 1 >= ctx->sort_every) HRT_TRY(ctx_sort_alloc(ctx));
   if (ctx->tape) {
     const char kind = (ctx->rays.n_rays > 0 && a_next < ctx->a) ? 'R' : 'F';
     HRT_TRY(ctx_mark(ctx, tape_on_step(ctx, kind, a_next, source, weight, accumulate)));
@@ -1676,7 +1781,9 @@ hrt_status hrt::ctx_step(hrt_ctx* ctx, double a_next, int32_t source, double wei
   if (s != HRT_OK) return ctx_mark(ctx, s);
   ctx->a = a_next;
   ctx->a_mom = a_half;
-  return ctx_mark(ctx, ctx_solve(ctx));
+  s = ctx_solve(ctx);
+  if (s == HRT_OK) s = ctx_scan_state(ctx, "hrt_step");
+  return ctx_mark(ctx, s);
 }
 
 hrt_status hrt_set_ray_correction(hrt_ctx* ctx, const float* params) {
@@ -1721,6 +1828,7 @@ hrt_status hrt_sync_particles(hrt_ctx* ctx) {
   HRT_TRY(ctx_guard(ctx));
   if (!ctx->have_particles) return fail(HRT_ERR_STATE, "no particles");
   if (ctx->cfg.static_mode || ctx->a_mom == ctx->a) return HRT_OK;
+  if (!ctx->force_valid) return fail(HRT_ERR_STATE, "no force: an earlier call failed while computing it");
   Cosmo c(ctx->cfg.cosmo.omega_m);
   HRT_TRY(ctx_mark(ctx, tape_on_step(ctx, 'S', ctx->a, -1, 1.0, false)));
   hrt_status s = launch_kick_drift(ctx->grad, ctx->cfg.n_mesh, ctx->cfg.box, ctx->cfg.n_side, ctx->disp, ctx->mom,
@@ -1734,6 +1842,7 @@ hrt_status hrt_step_static(hrt_ctx* ctx, double chi_from, double chi_to, int32_t
   if (!ctx->cfg.static_mode) return fail(HRT_ERR_STATE, "hrt_step_static needs the static mode");
   if (!ctx->have_particles) return fail(HRT_ERR_STATE, "no lens particles");
   if (ctx->rays.n_rays == 0) return fail(HRT_ERR_STATE, "no rays");
+  if (!ctx->force_valid) return fail(HRT_ERR_STATE, "no force: an earlier call failed while computing it");
   tape_invalidate(ctx, "static-lens steps are not differentiated");
   return ctx_mark(ctx, ctx_ray_step(ctx, chi_from, chi_to, 0.0, source, ctx->stream));
 }
@@ -1784,7 +1893,7 @@ hrt_status hrt_read_particles(hrt_ctx* ctx, float* disp, float* mom, double* a_h
 hrt_status hrt_read_grad(hrt_ctx* ctx, float* grad) {
   HRT_TRY(ctx_guard(ctx));
   if (!grad) return fail(HRT_ERR_INVALID_ARG, "grad is NULL");
-  if (!ctx->have_particles) return fail(HRT_ERR_STATE, "no force yet");
+  if (!ctx->have_particles || !ctx->force_valid) return fail(HRT_ERR_STATE, "no force");
   const size_t n = ctx->cfg.n_mesh;
   return ctx_mark(ctx, cuda_status(cudaMemcpyAsync(grad, ctx->grad, 3 * n * n * n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream), "read grad"));
 }
@@ -1987,6 +2096,43 @@ hrt_status hrt_ctx_kappa_power(hrt_ctx* ctx, int32_t source, int64_t m, double d
   if (m * m != ctx->rays.n_rays) return fail(HRT_ERR_INVALID_ARG, "rays do not form an m x m image");
   const float* kappa = ctx->maps + static_cast<int64_t>(source) * 4 * ctx->rays.n_rays;
   return ctx_mark(ctx, hrt_kappa_power(kappa, m, dtheta, nbins, ell_min, ell_max, ell_host, p_host, count_host, ctx->stream));
+}
+
+hrt_status hrt_set_nonfinite_check(hrt_ctx* ctx, int32_t on) {
+  HRT_TRY(ctx_guard(ctx));
+  if (on && !ctx->finite_flag)
+    HRT_TRY(device_alloc(reinterpret_cast<void**>(&ctx->finite_flag), sizeof(int), ctx->stream, "finite flag"));
+  ctx->check_finite = on != 0;
+  return HRT_OK;
+}
+
+hrt_status hrt_static_prefactor(double mass, double box, double* pref) {
+  if (!pref) return fail(HRT_ERR_INVALID_ARG, "pref is NULL");
+  if (!(mass > 0.0) || !std::isfinite(mass) || !(box > 0.0) || !std::isfinite(box))
+    return fail(HRT_ERR_INVALID_ARG, "mass and box must be positive and finite");
+  // the Poisson equation of a static lens, lap(phi) = 4 pi G rho_mean delta with rho_mean = M / L^3
+  *pref = 4.0 * M_PI * kGNewton * mass / (box * box * box);
+  return HRT_OK;
+}
+
+hrt_status hrt_set_ray_theta_bits(hrt_ctx* ctx, int32_t bits) {
+  HRT_TRY(ctx_guard(ctx));
+  if (bits != 32 && bits != 64) return fail(HRT_ERR_INVALID_ARG, "ray angle bits must be 32 or 64");
+  if (bits == 32) tape_invalidate(ctx, "the FP32 ray-angle ablation is not differentiated");
+  ctx->theta32 = bits == 32;
+  return HRT_OK;
+}
+
+hrt_status hrt_inject_alloc_failure(int64_t k) {
+  if (k < 0) return fail(HRT_ERR_INVALID_ARG, "k must be >= 0");
+  set_alloc_failure(k);
+  return HRT_OK;
+}
+
+hrt_status hrt_set_host_wait_limit(double seconds) {
+  if (std::isnan(seconds)) return fail(HRT_ERR_INVALID_ARG, "the wait limit must be a number");
+  g_wait_limit.store(seconds);
+  return HRT_OK;
 }
 
 hrt_status hrt_ctx_set_profiling(hrt_ctx* ctx, int32_t on) {

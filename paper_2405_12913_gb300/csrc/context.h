@@ -63,6 +63,7 @@ struct hrt_ctx {
   float* grad = nullptr;
   float* ray_grad = nullptr;
   bool have_particles = false;
+  bool force_valid = false;  // grad (and ray_grad) hold the force of the current particles
   double a = 1.0, a_mom = 1.0;
   hrt_rays rays{};
   float* maps = nullptr;
@@ -98,6 +99,10 @@ struct hrt_ctx {
   float* ray_table = nullptr;
   int32_t ray_table_nk = 0;
   double ray_table_kmax = 0.0;
+  // opt-in checks for NaN and infinity (hrt_set_nonfinite_check): device flag of the scans
+  bool theta32 = false;  // FP32 ray-angle ablation of the direct kick (hrt_set_ray_theta_bits)
+  bool check_finite = false;
+  int* finite_flag = nullptr;
 };
 
 namespace hrt {

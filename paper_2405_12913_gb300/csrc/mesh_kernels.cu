@@ -6,6 +6,7 @@
 // so the CIC atomics and gathers hit lines already resident in the 129 MB L2).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -624,5 +625,32 @@ hrt_status launch_scale_copy(const float* in, float* out, double ratio, int64_t 
   HRT_LAUNCHED("scale_copy_kernel");
   return HRT_OK;
 }
+
+// ---------------------------------------------------------------------------------------------------------
+// Non-finite scan (opt-in checks of the context): one warp vote per 32 values, one atomic per warp that saw one.
+// ---------------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void nonfinite_scan_kernel(const T* __restrict__ p, int64_t n, int* __restrict__ flag) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    bad |= !isfinite(p[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+template <typename T>
+static hrt_status scan(const T* p, int64_t n, int* flag, cudaStream_t s) {
+  if (n <= 0) return HRT_OK;
+  int dev = 0, sms = 0;
+  HRT_TRY(cuda_status(cudaGetDevice(&dev), "cudaGetDevice"));
+  HRT_TRY(cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count"));
+  const unsigned grid = std::min<unsigned>(blocks_for(n, 256), static_cast<unsigned>(sms) * 8);
+  nonfinite_scan_kernel<T><<<grid, 256, 0, s>>>(p, n, flag);
+  HRT_LAUNCHED("nonfinite_scan_kernel");
+  return HRT_OK;
+}
+
+hrt_status launch_nonfinite_scan(const float* p, int64_t n, int* flag, cudaStream_t s) { return scan(p, n, flag, s); }
+hrt_status launch_nonfinite_scan(const double* p, int64_t n, int* flag, cudaStream_t s) { return scan(p, n, flag, s); }
 
 }  // namespace hrt

@@ -82,6 +82,9 @@ struct RayStepParams {
   // light-cone tiling (tiled != 0): replica of each node, and per replica the box axis and sign of the sky
   // axes and the translation (cells) of the box axes that receive sky x and y
   int tiled;
+  // precision ablation (0 in the method): 1 keeps the ray angle in FP32 (rounded after each drift) and forms the
+  // interpolation position r theta in FP32 instead of the FP64 cell / fraction split
+  int theta32;
   unsigned char rep[kMaxRayNodes];
   signed char rperm[kMaxReplicas][3];
   signed char rsign[kMaxReplicas][3];

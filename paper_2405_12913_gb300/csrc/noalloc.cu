@@ -11,6 +11,7 @@
 // address; the device address is looked up once per device with cudaGetSymbolAddress and passed to the kernel.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <mutex>
 #include <vector>
 
@@ -59,13 +60,25 @@ extern "C" hrt_status hrt_kspace_gradient_noalloc(const void* rho_hat, int64_t n
   if (n > kNoallocMaxMesh)
     return fail(HRT_ERR_INVALID_ARG, "hrt_kspace_gradient_noalloc: mesh %lld exceeds the fixed table limit %lld",
                 static_cast<long long>(n), static_cast<long long>(kNoallocMaxMesh));
-  if (n < 2 || n % 2 != 0 || !(box > 0.0)) return fail(HRT_ERR_INVALID_ARG, "bad mesh size or box");
-  if (!f || !rho_hat || !out || n_out < 1 || n_out > 3) return fail(HRT_ERR_INVALID_ARG, "bad primary output");
-  if (second && (!f2 || n_second < 1 || n_second > 3)) return fail(HRT_ERR_INVALID_ARG, "bad second output");
-  if (f->g_table && (f->g_nk < 2 || !(f->g_kmax > 0.0))) return fail(HRT_ERR_INVALID_ARG, "bad learned table");
-  if (second && f2->g_table && (f2->g_nk < 2 || !(f2->g_kmax > 0.0)))
-    return fail(HRT_ERR_INVALID_ARG, "bad learned table");
+  // the same argument checks as hrt_kspace_gradient
+  if (n < 2 || n % 2 != 0) return fail(HRT_ERR_INVALID_ARG, "mesh size %lld must be even", static_cast<long long>(n));
+  if (!(box > 0.0) || !std::isfinite(box)) return fail(HRT_ERR_INVALID_ARG, "box must be positive and finite");
+  if (!std::isfinite(pref)) return fail(HRT_ERR_INVALID_ARG, "non-finite prefactor");
+  if (!rho_hat || !out || n_out < 1 || n_out > 3) return fail(HRT_ERR_INVALID_ARG, "bad primary output");
+  if (second && (n_second < 1 || n_second > 3)) return fail(HRT_ERR_INVALID_ARG, "bad second output count");
+  for (const hrt_filter* g : {f, second ? f2 : f}) {
+    if (!g) return fail(HRT_ERR_INVALID_ARG, "filter is NULL");
+    if (!std::isfinite(g->deconv_p) || !(g->smooth >= 0.0) || !std::isfinite(g->smooth))
+      return fail(HRT_ERR_INVALID_ARG, "bad filter");
+    if (g->g_table && (g->g_nk < 2 || !(g->g_kmax > 0.0))) return fail(HRT_ERR_INVALID_ARG, "bad learned table");
+  }
   cudaStream_t s = as_stream(stream);
+  // The tables are staged from host memory at call time; a captured graph would replay a copy from a host
+  // buffer that no longer exists, so calls during stream capture are refused.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  HRT_CUDA(cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(HRT_ERR_STATE, "hrt_kspace_gradient_noalloc cannot be called while the stream is being captured");
   float* tables = nullptr;
   HRT_TRY(table_address(&tables));
   // Host tables, then one copy into the fixed array on the caller's stream.  The copy reads pageable host

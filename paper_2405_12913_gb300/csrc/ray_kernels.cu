@@ -22,7 +22,18 @@ struct HalfKick {
 };
 
 __device__ __forceinline__ void base_position(double obs, double r_ref, double theta, double cell, int n,
-                                              int& i0, float& f0) {
+                                              int& i0, float& f0, int theta32 = 0) {
+  if (theta32) {
+    // the FP32 ablation: the position and its cell split in single precision
+    float uf = (static_cast<float>(obs) + static_cast<float>(r_ref) * static_cast<float>(theta)) / static_cast<float>(cell);
+    uf -= static_cast<float>(n) * floorf(uf / static_cast<float>(n));
+    const float flf = floorf(uf);
+    i0 = static_cast<int>(flf);
+    if (i0 >= n) i0 -= n;
+    if (i0 < 0) i0 += n;
+    f0 = uf - flf;
+    return;
+  }
   double u = (obs + r_ref * theta) / cell;
   u -= n * floor(u / n);
   double fl = floor(u);
@@ -48,8 +59,8 @@ __device__ __forceinline__ HalfKick half_kick(const RayStepParams& p, int j0, in
   const int n = p.n;
   int bx, by;
   float fbx, fby;
-  base_position(p.obs_x, ref_r, th_x, p.cell, n, bx, fbx);
-  base_position(p.obs_y, ref_r, th_y, p.cell, n, by, fby);
+  base_position(p.obs_x, ref_r, th_x, p.cell, n, bx, fbx, p.theta32);
+  base_position(p.obs_y, ref_r, th_y, p.cell, n, by, fby, p.theta32);
   const float tx = static_cast<float>(th_x), ty = static_cast<float>(th_y);
   const int64_t nn = n;
   for (int j = j0; j < j1; ++j) {
@@ -144,8 +155,8 @@ __device__ __forceinline__ HalfKick half_kick_tiled(const RayStepParams& p, int 
   const int n = p.n;
   int bx, by;
   float fbx, fby;
-  base_position(p.obs_x, ref_r, th_x, p.cell, n, bx, fbx);
-  base_position(p.obs_y, ref_r, th_y, p.cell, n, by, fby);
+  base_position(p.obs_x, ref_r, th_x, p.cell, n, bx, fbx, p.theta32);
+  base_position(p.obs_y, ref_r, th_y, p.cell, n, by, fby, p.theta32);
   const float tx = static_cast<float>(th_x), ty = static_cast<float>(th_y);
   const int64_t nn = n;
   for (int j = j0; j < j1; ++j) {
@@ -220,8 +231,14 @@ __global__ void __launch_bounds__(128) ray_step_kernel(double2* __restrict__ the
   B.w += h.j10 * A.y + h.j11 * A.w;
   // drift: theta in FP64, A in float32
   const double d = p.drift_d;
-  th.x += d * static_cast<double>(et.x);
-  th.y += d * static_cast<double>(et.y);
+  if (p.theta32) {
+    const float df = static_cast<float>(d);
+    th.x = static_cast<double>(static_cast<float>(th.x) + df * et.x);
+    th.y = static_cast<double>(static_cast<float>(th.y) + df * et.y);
+  } else {
+    th.x += d * static_cast<double>(et.x);
+    th.y += d * static_cast<double>(et.y);
+  }
   A.x += p.drift * B.x;
   A.y += p.drift * B.y;
   A.z += p.drift * B.z;
@@ -317,8 +334,9 @@ hrt_status launch_ray_readout(const hrt_rays& rays, float* maps, cudaStream_t s)
   return HRT_OK;
 }
 
-__global__ void rays_init_kernel(double2* __restrict__ theta, float2* __restrict__ eta, float4* __restrict__ Amat,
-                                 float4* __restrict__ Bmat, const double2* __restrict__ theta0, int64_t nr) {
+// theta0 may be theta itself (initialisation in place)
+__global__ void rays_init_kernel(double2* theta, float2* __restrict__ eta, float4* __restrict__ Amat,
+                                 float4* __restrict__ Bmat, const double2* theta0, int64_t nr) {
   int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (r >= nr) return;
   theta[r] = theta0[r];

@@ -150,6 +150,11 @@ _SIGS = {
     "hrt_pm_gradient_from_spectrum": ([_P, _P, _D, _P, _I32, _P], C.c_int),
     "hrt_pm_forward_fft": ([_P, _P, _P], C.c_int),
     "hrt_ctx_set_profiling": ([_P, _I32], C.c_int),
+    "hrt_set_nonfinite_check": ([_P, _I32], C.c_int),
+    "hrt_set_host_wait_limit": ([_D], C.c_int),
+    "hrt_inject_alloc_failure": ([_I64], C.c_int),
+    "hrt_set_ray_theta_bits": ([_P, _I32], C.c_int),
+    "hrt_static_prefactor": ([_D, _D, _P], C.c_int),
     "hrt_ctx_phase_times": ([_P, _P, _P], C.c_int),
     "hrt_ctx_rays": ([_P, _P], C.c_int),
 }
@@ -193,12 +198,38 @@ def _ptr(t: torch.Tensor | None, dtype=None, name: str = "tensor") -> int | None
     return t.data_ptr()
 
 
+def _any_ptr(t: torch.Tensor | None, dtype, name: str) -> int | None:
+    """Pointer of a contiguous tensor in device or host memory (for calls that copy with either)."""
+    if t is None:
+        return None
+    if t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor")
+    return t.data_ptr()
+
+
 def _host_ptr(t: torch.Tensor | None, dtype, name: str) -> int | None:
     if t is None:
         return None
     if t.is_cuda or t.dtype != dtype or not t.is_contiguous():
         raise ValueError(f"{name} must be a contiguous host {dtype} tensor")
     return t.data_ptr()
+
+
+def hrt_set_host_wait_limit(seconds: float):
+    """Process-wide limit of the library's host waits for a stream (<= 0: none)."""
+    _check(_lib.hrt_set_host_wait_limit(seconds), "hrt_set_host_wait_limit")
+
+
+def hrt_static_prefactor(mass: float, box: float) -> float:
+    """4 pi G M / box^3: the Poisson prefactor of a static lens of mass M (Msun/h) in a box of side L (Mpc/h)."""
+    out = C.c_double()
+    _check(_lib.hrt_static_prefactor(mass, box, C.byref(out)), "hrt_static_prefactor")
+    return out.value
+
+
+def hrt_inject_alloc_failure(k: int):
+    """Test hook: the k-th device allocation of the library from now reports out-of-memory (0: off)."""
+    _check(_lib.hrt_inject_alloc_failure(k), "hrt_inject_alloc_failure")
 
 
 def status_string(status: int) -> str:
@@ -754,12 +785,22 @@ class Context:
         _check(_lib.hrt_init_particles_2lpt(self._h, _ptr(noise, torch.float32, "noise"), a_init),
                "hrt_init_particles_2lpt")
 
+    def hrt_set_ray_theta_bits(self, bits: int):
+        """64: FP64 ray angles (the method); 32: the FP32 ablation."""
+        _check(_lib.hrt_set_ray_theta_bits(self._h, bits), "hrt_set_ray_theta_bits")
+
+    def hrt_set_nonfinite_check(self, on: bool):
+        _check(_lib.hrt_set_nonfinite_check(self._h, int(bool(on))), "hrt_set_nonfinite_check")
+
     def hrt_init_particles(self, disp: torch.Tensor, mom: torch.Tensor, a: float):
-        _check(_lib.hrt_init_particles(self._h, _ptr(disp, torch.float32, "disp"), _ptr(mom, torch.float32, "mom"), a),
-               "hrt_init_particles")
+        """disp, mom: [3][N_p] float32 in device or host memory (pinned host memory keeps the copy asynchronous)."""
+        _check(_lib.hrt_init_particles(self._h, _any_ptr(disp, torch.float32, "disp"),
+                                       _any_ptr(mom, torch.float32, "mom"), a), "hrt_init_particles")
 
     def hrt_init_rays(self, theta0: torch.Tensor):
-        _check(_lib.hrt_init_rays(self._h, _ptr(theta0, torch.float64, "theta0"), theta0.shape[0]), "hrt_init_rays")
+        """theta0: [R][2] float64 in device or host memory."""
+        _check(_lib.hrt_init_rays(self._h, _any_ptr(theta0, torch.float64, "theta0"), theta0.shape[0]),
+               "hrt_init_rays")
         self.n_rays = theta0.shape[0]
 
     def hrt_step(self, a_next: float, source: int = -1):
@@ -844,6 +885,19 @@ class Context:
         B = torch.empty(r, 4, dtype=torch.float32, device=dev)
         _check(_lib.hrt_read_rays(self._h, th.data_ptr(), eta.data_ptr(), A.data_ptr(), B.data_ptr()), "hrt_read_rays")
         return th, eta, A, B
+
+    def hrt_read_rays_into(self, theta: torch.Tensor | None, eta: torch.Tensor | None = None,
+                           A: torch.Tensor | None = None, B: torch.Tensor | None = None):
+        """Stream-ordered copies of the ray state into caller tensors in device or host memory (None skips)."""
+        _check(_lib.hrt_read_rays(self._h, _any_ptr(theta, torch.float64, "theta"), _any_ptr(eta, torch.float32, "eta"),
+                                  _any_ptr(A, torch.float32, "A"), _any_ptr(B, torch.float32, "B")), "hrt_read_rays")
+
+    def hrt_read_maps_into(self, source: int, kappa: torch.Tensor | None, gamma1: torch.Tensor | None = None,
+                           gamma2: torch.Tensor | None = None, omega: torch.Tensor | None = None):
+        """Stream-ordered copies of the maps of `source` into caller tensors in device or host memory."""
+        _check(_lib.hrt_read_maps(self._h, source, _any_ptr(kappa, torch.float32, "kappa"),
+                                  _any_ptr(gamma1, torch.float32, "gamma1"), _any_ptr(gamma2, torch.float32, "gamma2"),
+                                  _any_ptr(omega, torch.float32, "omega")), "hrt_read_maps")
 
     def hrt_read_maps(self, source: int):
         r = self.n_rays

@@ -307,7 +307,7 @@ def test_end_to_end_gradient_matches_oracle(hrt):
     kbar = synthetic.gaussian_field(70, (len(W.source_steps), W.n_rays))
     om0 = W.omega_m + 1.234e-6  # a generic point (no line-of-sight sample exactly on a cell face)
     # GPU: forward and adjoint through the autograd function (checkpoint every 2 steps)
-    sim = autodiff.DiffSim(W, theta0, checkpoint_every=2)
+    sim = autodiff.ContextSim(W, theta0, checkpoint_every=2)
     w_gpu = _cuda(noise).reshape(-1).requires_grad_(True)
     om_gpu = torch.tensor(om0, dtype=torch.float64, requires_grad=True)
     kap, _ = autodiff.HRTKappa.apply(w_gpu, om_gpu, sim)
@@ -340,7 +340,7 @@ def test_power_loss_gradient_matches_oracle(hrt):
     theta0 = torch.tensor(synthetic.pixel_grid(W.n_pix, W.fov_deg * synthetic.DEGREE))
     lmin, lmax = W.ell_range
     target = torch.tensor(synthetic.gaussian_field(73, (W.nbins,), 1e-9)).abs()
-    sim = autodiff.DiffSim(W, theta0, checkpoint_every=3)
+    sim = autodiff.ContextSim(W, theta0, checkpoint_every=3)
     w = _cuda(noise).reshape(-1).requires_grad_(True)
     om = torch.tensor(W.omega_m, dtype=torch.float64, requires_grad=True)
     kap, _ = autodiff.HRTKappa.apply(w, om, sim)
@@ -372,7 +372,7 @@ def test_deflection_loss_gradient_matches_central_differences(hrt):
     noise = synthetic.white_noise(W.seed + 2, W.n_side)
     theta0 = torch.tensor(synthetic.pixel_grid(W.n_pix, W.fov_deg * synthetic.DEGREE))
     tb = _cuda(synthetic.gaussian_field(75, (W.n_rays, 2)), torch.float64)
-    sim = autodiff.DiffSim(W, theta0, checkpoint_every=2)
+    sim = autodiff.ContextSim(W, theta0, checkpoint_every=2)
 
     def loss(wn, omv):
         _, th = autodiff.HRTKappa.apply(wn, omv, sim)
@@ -430,7 +430,7 @@ def test_power_loss_gradient_at_128p_256m_matches_central_differences(hrt):
     noise = _cuda(synthetic.white_noise(W.seed, W.n_side)).reshape(-1)
     theta0 = torch.tensor(synthetic.pixel_grid(W.n_pix, W.fov_deg * synthetic.DEGREE))
     lmin, lmax = W.ell_range
-    sim = autodiff.DiffSim(W, theta0, checkpoint_every=4)
+    sim = autodiff.ContextSim(W, theta0, checkpoint_every=4)
     om = torch.tensor(W.omega_m, dtype=torch.float64)
 
     def loss(wn, target, scale):
@@ -475,7 +475,7 @@ def test_ray_mesh_end_to_end_gradient_matches_oracle_differences(hrt, monkeypatc
     kbar = synthetic.gaussian_field(77, (len(W.source_steps), W.n_rays))
     tb = synthetic.gaussian_field(78, (W.n_rays, 2))
     om0 = W.omega_m + 1.234e-6
-    sim = autodiff.DiffSim(W, theta0, checkpoint_every=2,
+    sim = autodiff.ContextSim(W, theta0, checkpoint_every=2,
                            ray_mesh=hrt.make_raymesh_config(rm_args[2], rm_args[3], rm_args[0], rm_args[1]))
     w = _cuda(noise).reshape(-1).requires_grad_(True)
     om = torch.tensor(om0, dtype=torch.float64, requires_grad=True)
@@ -530,8 +530,10 @@ def test_ray_mesh_end_to_end_gradient_matches_oracle_differences(hrt, monkeypatc
 
 @pytest.mark.parametrize("mesh", [False, True])
 def test_context_adjoint_matches_the_differentiable_simulation(hrt, mesh):
-    """hrt_adjoint of a recorded context run (checkpoints every 2 steps) against autodiff.DiffSim on the same
-    run: the same adjoint calls sequenced natively, so the gradients agree to the rounding of the atomics."""
+    """hrt_adjoint of a recorded context run (checkpoints every 2 steps) against the same adjoint calls sequenced
+    in Python over the stateless ABI (tests/stateless_adjoint.py, checkpoints every 3 steps, with its own FP64
+    chain for Omega_m): the gradients agree to the rounding of the atomics."""
+    from stateless_adjoint import DiffSim
     from paper_2405_12913_gb300 import autodiff
     from paper_2405_12913_gb300.configs import COSMO_GRAD as W
     rm_cfg = hrt.make_raymesh_config(0.5, 8.0, W.dtheta, W.n_pix) if mesh else None
@@ -558,7 +560,7 @@ def test_context_adjoint_matches_the_differentiable_simulation(hrt, mesh):
     nb_ctx, om_ctx = ctx.hrt_adjoint(kbar.contiguous(), tb.contiguous())
     torch.cuda.synchronize()
     # the differentiable simulation
-    sim = autodiff.DiffSim(W, theta0, checkpoint_every=3, ray_mesh=rm_cfg)
+    sim = DiffSim(W, theta0, checkpoint_every=3, ray_mesh=rm_cfg)
     w = _cuda(noise).reshape(-1).requires_grad_(True)
     om = torch.tensor(W.omega_m, dtype=torch.float64, requires_grad=True)
     kap, th = autodiff.HRTKappa.apply(w, om, sim)

@@ -24,7 +24,7 @@ def hrt():
 def run_point_mass_gpu(hrt, W, theta0):
     cfg = hrt.make_config(W.n_mesh, W.box, 1, deconv_p=W.deconv_p, smooth_cells=W.smooth_cells,
                           samples_per_cell=W.samples_per_cell, observer=W.observer, static_mode=True,
-                          static_pref=W.static_pref, n_sources=1)
+                          static_pref=hrt.hrt_static_prefactor(W.mass, W.box), n_sources=1)
     ctx = hrt.Context(cfg)
     lens = torch.tensor([[W.lens_position[0]], [W.lens_position[1]], [W.lens_position[2]]], dtype=torch.float32,
                         device="cuda")

@@ -225,7 +225,7 @@ def test_point_mass_with_the_ray_mesh_against_born_integral(hrt):
     m_pix = int(math.ceil(2 * half / mu))
     cfg = hrt.make_config(W.n_mesh, W.box, 1, deconv_p=W.deconv_p, smooth_cells=0.0,
                           samples_per_cell=W.samples_per_cell, observer=W.observer, static_mode=True,
-                          static_pref=W.static_pref, n_sources=1)
+                          static_pref=hrt.hrt_static_prefactor(W.mass, W.box), n_sources=1)
     ctx = hrt.Context(cfg)
     ctx.hrt_set_ray_mesh(hrt.make_raymesh_config(0.5, 32.0, mu, m_pix))
     lens = torch.tensor([[W.lens_position[0]], [W.lens_position[1]], [W.lens_position[2]]], dtype=torch.float32,

@@ -56,3 +56,46 @@ def test_noalloc_rejects_meshes_beyond_its_fixed_tables(hrt):
     with pytest.raises(hrt.HRTError) as e:
         hrt.hrt_kspace_gradient_noalloc(x, 4096, 100.0, 1.0, hrt.make_filter(), 3, x)
     assert e.value.status == 1 and "fixed table limit" in str(e.value)
+
+
+def test_noalloc_rejects_what_the_ordinary_entry_point_rejects(hrt):
+    # an infinite box or prefactor, a non-finite deconvolution power and a negative or NaN smoothing length are
+    # refused by both entry points before anything is enqueued
+    n = 8
+    x = torch.zeros(n * n * (n // 2 + 1) * 3, dtype=torch.complex64, device="cuda")
+    good = hrt.make_filter(4.0, 1.0)
+    cases = [
+        (math.inf, 1.0, good),
+        (100.0, math.inf, good),
+        (100.0, math.nan, good),
+        (100.0, 1.0, hrt.make_filter(math.nan, 1.0)),
+        (100.0, 1.0, hrt.make_filter(4.0, -1.0)),
+        (100.0, 1.0, hrt.make_filter(4.0, math.nan)),
+    ]
+    for box, pref, f in cases:
+        for call in (hrt.hrt_kspace_gradient, hrt.hrt_kspace_gradient_noalloc):
+            with pytest.raises(hrt.HRTError) as e:
+                call(x, n, box, pref, f, 3, x)
+            assert e.value.status == 1, (call.__name__, box, pref)
+    torch.cuda.synchronize()
+
+
+def test_noalloc_refuses_a_call_during_stream_capture(hrt):
+    # the tables are staged from a host buffer during the call, which a captured graph could not replay, so a
+    # call on a capturing stream returns HRT_ERR_STATE and enqueues nothing (the captured graph stays empty)
+    n = 8
+    x = torch.zeros(n * n * (n // 2 + 1) * 3, dtype=torch.complex64, device="cuda")
+    f = hrt.make_filter(4.0, 1.0)
+    hrt.hrt_kspace_gradient_noalloc(x, n, 100.0, 1.0, f, 3, x)  # first call on the device: the set-up
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        try:
+            with pytest.raises(hrt.HRTError) as e:
+                hrt.hrt_kspace_gradient_noalloc(x, n, 100.0, 1.0, f, 3, x, stream=s)
+        finally:
+            g.capture_end()
+    assert e.value.status == 4 and "captured" in str(e.value)
+    torch.cuda.synchronize()
