@@ -187,6 +187,33 @@ def ray_step(state: dict, gx, gy, box: float, observer, chi_n: float, chi_n1: fl
     return dict(theta=theta, eta=eta, A=A, B=B)
 
 
+def face_distance(theta: torch.Tensor, box: float, n_mesh: int, observer, chis) -> torch.Tensor:
+    """Smallest distance, in cells, of the transverse coordinates of the line-of-sight nodes X(theta, chi_j) to a
+    cell face, per ray.  The transverse derivative of the trilinear interpolant (the T of dK/dtheta) is piecewise
+    constant and jumps on those faces (reading C12 of the interpolant's derivative, Sec. 4), so a node this close
+    to a face may take either cell in any finite precision.  Distances are invariant under the whole-cell shifts
+    and sign flips of a tiled light cone."""
+    cell = box / n_mesh
+    d = torch.full((theta.shape[0],), math.inf, dtype=torch.float64)
+    for chi in chis:
+        u = torch.remainder(ray_points(theta, chi, observer)[:, :2], box) / cell
+        f = u - torch.floor(u)
+        d = torch.minimum(d, torch.minimum(f, 1.0 - f).amin(dim=1))
+    return d
+
+
+def step_face_distance(theta_n: torch.Tensor, theta_n1: torch.Tensor, box: float, n_mesh: int, observer,
+                       chi_n: float, chi_n1: float, samples_per_cell: float) -> torch.Tensor:
+    """``face_distance`` over the nodes of one ``ray_step``: the first half shell at theta_n, the second at
+    theta_{n+1} (Alg. 1 order)."""
+    cell = box / n_mesh
+    chi_h = 0.5 * (chi_n + chi_n1)
+    first, _ = half_shell_nodes(chi_n, chi_h, samples_per_cell, cell)
+    second, _ = half_shell_nodes(chi_h, chi_n1, samples_per_cell, cell)
+    return torch.minimum(face_distance(theta_n, box, n_mesh, observer, first),
+                         face_distance(theta_n1, box, n_mesh, observer, second))
+
+
 def free_drift(state: dict, chi_a: float, chi_b: float) -> dict:
     """Exact solution of the drift equation d theta / d chi = -eta_EOM / r^2 for constant eta over
     [chi_a, chi_b] (chi_a > 0): theta += eta (1/chi_a - 1/chi_b) / c, A += B (1/chi_a - 1/chi_b) / c."""

@@ -105,29 +105,40 @@ class ReverseResult:
     rays: dict
     maps: dict = field(default_factory=dict)   # source step -> (kappa, g1, g2, omega)
     thetas: dict = field(default_factory=dict)  # source step -> theta
+    face_min: dict = field(default_factory=dict)  # source step -> per ray, nearest approach of a node to a face
 
 
 def run_reverse(part: Particles, grads, a_grid, box: float, n_mesh: int, c: Cosmo, flt: Filter,
                 theta0: torch.Tensor, observer, source_steps, samples_per_cell: float = 1.0,
-                move_particles: bool = True, replicas=None, ray_mesh=None) -> ReverseResult:
+                move_particles: bool = True, replicas=None, ray_mesh=None,
+                face_distance: bool = False) -> ReverseResult:
     """Reverse co-evolution along the decreasing ``a_grid`` (a_grid[0] == part.a_x, normally 1); with
     ``replicas`` = (perm, sign, shift) the rays cross a light cone tiled by rotated, translated replicas; with
-    ``ray_mesh`` = (mu, m_pix, iota, p_min) the kicks come from the ray mesh of Sec. 5.2 (``raymesh``)."""
+    ``ray_mesh`` = (mu, m_pix, iota, p_min) the kicks come from the ray mesh of Sec. 5.2 (``raymesh``).  With
+    ``face_distance`` (direct kick) the result also holds, per source step and ray, the nearest approach of any
+    line-of-sight node so far to a transverse cell face (``rays.face_distance``)."""
     om = c.omega_m
     state = rays.init_state(theta0)
     res = ReverseResult(part, grads, state)
+    nearest = torch.full((theta0.shape[0],), math.inf, dtype=torch.float64) if face_distance else None
     for n in range(len(a_grid) - 1):
         a_n, a_n1 = a_grid[n], a_grid[n + 1]
         chi_n, chi_n1 = cosmo.chi_of_a(a_n, om), cosmo.chi_of_a(a_n1, om)
+        theta_n = state["theta"]
         if ray_mesh is None:
             state = rays.ray_step(state, grads[0], grads[1], box, observer, chi_n, chi_n1, samples_per_cell,
                                   growth_weight(a_n, om), gz=grads[2], replicas=replicas)
+            if nearest is not None:
+                nearest = torch.minimum(nearest, rays.step_face_distance(theta_n, state["theta"], box, n_mesh,
+                                                                         observer, chi_n, chi_n1, samples_per_cell))
         else:
             state = raymesh.ray_step(state, grads[0], grads[1], box, observer, chi_n, chi_n1,
                                      growth_weight(a_n, om), *ray_mesh, gz=grads[2], replicas=replicas)
         if (n + 1) in source_steps:
             res.maps[n + 1] = rays.observables(state["A"])
             res.thetas[n + 1] = state["theta"].clone()
+            if nearest is not None:
+                res.face_min[n + 1] = nearest.clone()
         if move_particles:
             part = particle_step(part, grads, a_n1, om, box)
             grads = pm_force(part, box, n_mesh, 1.5 * om / a_n1, flt)

@@ -2,8 +2,10 @@
 // deconvolution kernel, the fused particle gather + kick + drift, and the Zel'dovich IC helpers.
 //
 // All three mesh passes are bound by HBM bandwidth; the kernels are written for coalesced 4- and 8-byte
-// accesses with the particles in Lagrangian-lattice order (neighbouring threads touch neighbouring cells,
-// so the CIC atomics and gathers hit lines already resident in the 129 MB L2).
+// accesses with neighbouring threads on neighbouring cells, so that the CIC atomics and gathers hit lines already
+// resident in the 129 MB L2.  Particles come in one of two storage orders: fresh particles in Lagrangian-lattice
+// order, walked in Morton-ordered bricks of lattice sites, and the context's particles in cell order (re-sorted
+// by mesh cell every few steps, sort_kernels.cu), where a slot -> lattice-site map gives each thread its site.
 #include <cuda_runtime.h>
 
 #include <algorithm>

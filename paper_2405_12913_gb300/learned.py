@@ -369,6 +369,42 @@ def ell_within(ell, rel, tol: float = 0.01) -> float:
     return last
 
 
+def ladder_seeds(S: PairSpec, seeds, meshes=(256, 512, 768), cuts=None, learned_forms=(), log=print):
+    """``ladder`` on several held-out seeds: per form the median sim-steps/s and, per ell cut, the largest and the
+    mean P(ell) error over the seeds and bins, the largest error per bin over the seeds, the ell up to which every
+    bin is within 1 % on every seed, and whether all bins with ell <= cut are within 1 % on every seed; then, for
+    the plain and the learned forms, the coarsest mesh that meets 1 % in every bin up to each cut on all seeds
+    (None when none does)."""
+    cuts = tuple(cuts) if cuts else (S.ell_cut,)
+    per_seed = [ladder(S, None, s, meshes=meshes, cuts=cuts, log=log, learned_forms=list(learned_forms))
+                for s in seeds]
+    forms = []
+    for i, row in enumerate(per_seed[0]):
+        rows = [ps[i] for ps in per_seed]
+        out = {"mesh": row["mesh"], "form": row["form"],
+               "sim_steps_per_s": float(np.median([r["sim_steps_per_s"] for r in rows]))}
+        if "errors" in row:
+            out["errors"] = {}
+            for key in row["errors"]:
+                errs = [r["errors"][key] for r in rows]
+                per_bin = np.max(np.array([e["per_bin"] for e in errs]), axis=0)
+                out["errors"][key] = {
+                    "bins": errs[0]["bins"], "max_rel_err": float(max(e["max_rel_err"] for e in errs)),
+                    "mean_rel_err": float(np.mean([e["mean_rel_err"] for e in errs])),
+                    "ell_within_1pct_all_seeds": float(min(e["ell_within_1pct"] for e in errs)),
+                    "meets_1pct_all_seeds": bool(per_bin.max() <= 0.01),
+                    "max_rel_err_per_bin": [float(x) for x in per_bin],
+                    "bin_ell": errs[0]["ell"]}
+        forms.append(out)
+    coarsest = {}
+    for key in [f"ell_le_{c:g}" for c in cuts]:
+        for kind in ("plain", "learned"):
+            ok = [f["mesh"] for f in forms if "errors" in f and f["form"].startswith(kind)
+                  and f["errors"][key]["meets_1pct_all_seeds"]]
+            coarsest[f"{kind} {key}"] = min(ok) if ok else None
+    return {"seeds": list(seeds), "forms": forms, "coarsest_mesh_within_1pct": coarsest}
+
+
 def ladder(S: PairSpec, params: torch.Tensor | None, seed: int, meshes=(256, 512, 768), cuts=None, log=print,
            learned_meshes=None, learned_forms=None):
     """Accuracy against speed on one held-out seed: for each coarse mesh the plain form, and the learned forms
@@ -397,7 +433,9 @@ def ladder(S: PairSpec, params: torch.Tensor | None, seed: int, meshes=(256, 512
             rel = np.abs(p[sel] / pf[sel] - 1.0)
             row["errors"][f"ell_le_{cut:g}"] = {"bins": int(sel.sum()), "mean_rel_err": float(rel.mean()),
                                                 "max_rel_err": float(rel.max()),
-                                                "ell_within_1pct": ell_within(ell[sel], rel)}
+                                                "ell_within_1pct": ell_within(ell[sel], rel),
+                                                "per_bin": [float(x) for x in rel],
+                                                "ell": [float(x) for x in ell[sel]]}
         rows.append(row)
         log(str(row))
     return rows

@@ -6,8 +6,10 @@ sizes.  Runs about six minutes on eight cores:
     python tests/golden/make_cosmo_1024_recipe_128p.py
 
 Stored: particles at a = 1 at 4096 sampled indices; per source plane the binned kappa power spectrum (all bins),
-the kappa, gamma1, gamma2, omega maps at 4096 sampled pixels and the rms of the full kappa map; the final ray angles
-at 4096 sampled rays and the largest deflection over all rays.
+the kappa, gamma1, gamma2, omega maps at 4096 sampled pixels, the rms of the full kappa map and, per sampled pixel,
+the nearest approach of any of its line-of-sight nodes so far to a transverse cell face (in cells: where the
+interpolant's derivative jumps); the final ray angles at 4096 sampled rays and the largest deflection over all
+rays.
 """
 import os
 import sys
@@ -39,7 +41,7 @@ def main():
     out = {"particle_index": ip, "disp": part.disp.numpy()[ip], "mom": part.mom.numpy()[ip],
            "mom_absmax": np.abs(part.mom.numpy()).max()}
     res = sim.run_reverse(part, grads, W.reverse_grid, W.box, W.n_mesh, c, flt, torch.tensor(theta0), W.observer,
-                          set(W.source_steps), W.samples_per_cell)
+                          set(W.source_steps), W.samples_per_cell, face_distance=True)
     ir = synthetic.sample_indices(SAMPLE_SEED + 1, W.n_rays, N_SAMPLE)
     out["ray_index"] = ir
     lmin, lmax = W.ell_range
@@ -47,6 +49,7 @@ def main():
         maps = np.stack([res.maps[s][i].numpy() for i in range(4)])
         out[f"maps_{s}"] = maps[:, ir]
         out[f"kappa_rms_{s}"] = maps[0].std()
+        out[f"face_min_{s}"] = res.face_min[s].numpy()[ir]
         ell, p, cnt = opow.kappa_power(maps[0].reshape(W.n_pix, W.n_pix), W.dtheta, W.nbins, lmin, lmax)
         out[f"ell_{s}"], out[f"power_{s}"], out[f"count_{s}"] = ell, p, cnt
     th = res.rays["theta"].numpy()

@@ -158,12 +158,16 @@ def test_ray_step_at_the_full_size(hrt, W):
     d_eta_o, d_B_o = want["eta"] - e0, want["B"] - b0
     assert float(d_eta_o.abs().max()) > 1e-7 and float(d_B_o.abs().max()) > 1e-4
     # the transverse derivative of the trilinear interpolant jumps on cell faces, where float32 and float64
-    # positions may take different (equally valid) cells: with ~98 nodes per ray, a few of the 4096 rays meet
-    # one (B only; eta is continuous there), so at most 0.2 % of the rays may differ in B
+    # positions may take different (equally valid) cells: every ray whose B (or A, below) differs must have a
+    # line-of-sight node, in the oracle's own step, within 1e-5 cell of a transverse face (the float32 position
+    # fraction of the kernel is good to about 1e-6 cell); eta is continuous there and must agree everywhere
+    near = orays.step_face_distance(torch.from_numpy(theta0[idx]), want["theta"], box, n, W.observer, chi0, chi1,
+                                    W.samples_per_cell) < 1e-5
     bad_eta = ((deta - d_eta_o).abs().max(dim=1).values > 1e-4 * float(d_eta_o.abs().max())).sum()
     err_B = (dB - d_B_o).abs().amax(dim=(1, 2)) / float(d_B_o.abs().max())
-    bad_B = int((err_B > 1e-4).sum())
-    assert int(bad_eta) == 0 and bad_B <= 8, (int(bad_eta), bad_B, sorted(err_B.tolist())[-10:])
+    off_face_B = (err_B > 1e-4) & ~near
+    assert int(bad_eta) == 0 and not bool(off_face_B.any()), (int(bad_eta), int((err_B > 1e-4).sum()),
+                                                                sorted(err_B[off_face_B].tolist()))
     assert float(err_B.median()) <= 1e-6
     dth = rays.theta[idx].cpu() - want["theta"]
     assert float(dth.abs().max()) <= 1e-4 * float((want["theta"] - torch.from_numpy(theta0[idx])).abs().max()) + 1e-15
@@ -172,4 +176,5 @@ def test_ray_step_at_the_full_size(hrt, W):
     dA_o = want["A"] - a0_
     err_A = (rays.A[idx].double().cpu().reshape(-1, 2, 2) - a0_ - dA_o).abs().amax(dim=(1, 2)) / float(dA_o.abs().max())
     assert float(dA_o.abs().max()) > 0.0
-    assert int((err_A > 1e-4).sum()) <= 8 and float(err_A.median()) <= 1e-5, sorted(err_A.tolist())[-10:]
+    off_face_A = (err_A > 1e-4) & ~near
+    assert not bool(off_face_A.any()) and float(err_A.median()) <= 1e-5, sorted(err_A[off_face_A].tolist())

@@ -91,6 +91,19 @@ def _cosmo_gpu(hrt, W, noise, theta0, replicas=None):
     return disp_1, mom_1, maps, th, pk
 
 
+# A whole run's GPU and oracle trajectories differ by the accumulated rounding of the angles (a few 1e-6 cell in
+# position); a map pixel beyond tolerance must come from a ray whose line of sight passed within this distance of a
+# transverse cell face in the oracle's run, where the interpolant's derivative jumps.
+FACE_TOL_RUN = 3e-5
+
+
+def _assert_outliers_near_faces(bad, face_min, what):
+    """Every flagged pixel (boolean array) has a line-of-sight node within FACE_TOL_RUN cell of a face."""
+    bad = np.asarray(bad)
+    off = bad & ~(np.asarray(face_min) < FACE_TOL_RUN)
+    assert not off.any(), (what, int(bad.sum()), int(off.sum()), np.asarray(face_min)[off][:5])
+
+
 def test_cosmological_coevolution_matches_oracle(hrt):
     from paper_2405_12913_gb300.configs import COSMO_TINY as W
     noise = synthetic.white_noise(W.seed, W.n_side)
@@ -143,10 +156,10 @@ def test_cosmo_1024_recipe_at_128p_matches_oracle_fixture(hrt):
     assert np.abs(mom_1[:, ip].T - g["mom"]).max() < 1e-3 * float(g["mom_absmax"])
     for s in W.source_steps:
         # the maps jump where a line-of-sight sample crosses a cell face (the interpolant's derivative is piecewise
-        # constant), and the deposit's atomic order varies between runs: allow a rare sampled pixel beyond 1e-3
+        # constant): every sampled pixel beyond 1e-3 of the kappa rms must have passed near a face in the oracle's run
         err = np.abs(maps[s][:, ir] - g[f"maps_{s}"])
         rms = float(g[f"kappa_rms_{s}"])
-        assert (err > 1e-3 * rms).mean() <= 2e-3, (s, (err > 1e-3 * rms).sum(), err.max(), rms)
+        _assert_outliers_near_faces((err > 1e-3 * rms).any(axis=0), g[f"face_min_{s}"], s)
         assert np.median(err) <= 1e-4 * rms, (s, np.median(err), rms)
         ell, p, cnt = pk[s]
         assert np.array_equal(cnt, g[f"count_{s}"])
@@ -195,14 +208,22 @@ def test_save_and_load_state_resume_the_run(hrt):
     th_b = ctx2.hrt_read_rays()[0]
     alpha = (theta0 - th_a).abs().max().item()
     assert (th_b - th_a).abs().max().item() <= 1e-5 * alpha
-    for s, i in slots.items():
-        k_a, k_b = maps_a[s][0], ctx2.hrt_read_maps(i)[0]
-        scale = k_a.abs().max().item()
-        diff = (k_b - k_a).abs()
-        # kappa jumps where a line-of-sight sample crosses a cell face: allow a rare pixel
-        assert (diff > 1e-4 * scale).float().mean().item() <= 2e-3, s
-        assert diff.median().item() <= 1e-5 * scale, s
+    maps_b = {s: ctx2.hrt_read_maps(i)[0].cpu().numpy() for s, i in slots.items()}
     ctx2.close()
+    # kappa jumps where a line-of-sight sample crosses a cell face: every pixel that differs must have passed near
+    # one (the oracle's run of the same workload gives the distances)
+    c = sim.Cosmo(W.omega_m, W.h, W.n_s, W.sigma8)
+    flt = sim.Filter(W.deconv_p, W.smooth_cells)
+    part = sim.initial_particles(synthetic.white_noise(W.seed, W.n_side), W.box, c, W.a_init)
+    part, grads = sim.run_forward(part, W.forward_grid, W.box, W.n_mesh, c, flt)
+    res = sim.run_reverse(part, grads, grid, W.box, W.n_mesh, c, flt, theta0.cpu(), W.observer, set(slots),
+                          W.samples_per_cell, face_distance=True)
+    for s in slots:
+        k_a, k_b = maps_a[s][0].cpu().numpy(), maps_b[s]
+        scale = np.abs(k_a).max()
+        diff = np.abs(k_b - k_a)
+        _assert_outliers_near_faces(diff > 1e-4 * scale, res.face_min[s].numpy(), s)
+        assert np.median(diff) <= 1e-5 * scale, s
 
 
 def test_accumulated_source_distribution_matches_oracle(hrt):
@@ -261,14 +282,16 @@ def test_tiled_light_cone_run_matches_oracle(hrt):
     part = sim.initial_particles(noise, W.box, c, W.a_init)
     part, grads = sim.run_forward(part, W.forward_grid, W.box, W.n_mesh, c, flt)
     res = sim.run_reverse(part, grads, W.reverse_grid, W.box, W.n_mesh, c, flt, torch.tensor(theta0), W.observer,
-                          set(W.source_steps), W.samples_per_cell, replicas=reps)
+                          set(W.source_steps), W.samples_per_cell, replicas=reps, face_distance=True)
     lmin, lmax = W.ell_range
     for s in W.source_steps:
         want = np.stack([res.maps[s][i].numpy() for i in range(4)])
         rms = want[0].std()
         err = np.abs(maps[s] - want)
-        # kappa jumps where a line-of-sight sample crosses a cell face: allow a rare pixel
-        assert (err > 1e-3 * rms).mean() <= 2e-3 and np.median(err) <= 1e-4 * rms, (s, err.max(), rms)
+        # kappa jumps where a line-of-sight sample crosses a cell face: every pixel beyond 1e-3 of the rms must
+        # have passed near one in the oracle's run
+        _assert_outliers_near_faces((err > 1e-3 * rms).any(axis=0), res.face_min[s].numpy(), s)
+        assert np.median(err) <= 1e-4 * rms, (s, err.max(), rms)
         ell_o, p_o, cnt_o = opow.kappa_power(want[0].reshape(W.n_pix, W.n_pix), W.dtheta, W.nbins, lmin, lmax)
         ell, p, cnt = pk[s]
         assert np.array_equal(cnt, cnt_o)

@@ -214,3 +214,38 @@ def test_tiling_equals_the_gather_of_explicitly_rotated_fields(seed):
     val_p, T_p = rays.interp_xy(gp[0], gp[1], X, box)
     assert torch.allclose(val, val_p, rtol=0, atol=1e-12)
     assert torch.allclose(T, T_p, rtol=0, atol=1e-11)
+
+
+def test_face_distance_bounds_the_cells_the_nodes_occupy():
+    # face_distance is the largest observer shift (in cells) that leaves every node of every ray in its cell:
+    # shifts of 0.99 of it along +-x and +-y keep all cells, and one of the four shifts by 1.01 of it moves a node
+    # into the next cell.  Checked ray by ray on random angles, with nodes from a real half shell.
+    from oracle import rays as orays
+    g = torch.Generator().manual_seed(91)
+    box, n_mesh, cell = 100.0, 50, 2.0
+    chis, _ = orays.half_shell_nodes(300.0, 340.0, 1.0, cell)
+    theta = 0.05 * (torch.rand(64, 2, generator=g, dtype=torch.float64) - 0.5)
+    obs = (3.7, 41.2, 0.0)
+    d = orays.face_distance(theta, box, n_mesh, obs, chis)
+    assert float(d.min()) >= 0.0 and float(d.max()) <= 0.5
+
+    def cells(t, o):
+        return torch.stack([torch.floor(torch.remainder(orays.ray_points(t, c, o)[:, :2], box) / cell)
+                            for c in chis])
+
+    for r in range(theta.shape[0]):
+        t = theta[r:r + 1]
+        base = cells(t, obs)
+        moved_past = False
+        for ax in (0, 1):
+            for sgn in (1.0, -1.0):
+                o_in, o_out = list(obs), list(obs)
+                o_in[ax] += sgn * 0.99 * float(d[r]) * cell
+                o_out[ax] += sgn * 1.01 * float(d[r]) * cell
+                assert torch.equal(cells(t, tuple(o_in)), base)
+                moved_past |= not torch.equal(cells(t, tuple(o_out)), base)
+        assert moved_past, r
+    # a node exactly on a face has distance 0, one at a cell centre 0.5
+    on_face = torch.tensor([[0.0, 0.0]], dtype=torch.float64)
+    assert float(orays.face_distance(on_face, box, n_mesh, (4.0, 4.0 + 0.5 * cell, 0.0), [10.0])) == 0.0
+    assert float(orays.face_distance(on_face, box, n_mesh, (3.0, 5.0, 0.0), [10.0])) == pytest.approx(0.5)
