@@ -521,6 +521,14 @@ hrt_status hrt_step(hrt_ctx* ctx, double a_next, int32_t source);
  * restores the plain ray kernel.  Takes effect at the next force evaluation (the next hrt_step). */
 hrt_status hrt_set_ray_correction(hrt_ctx* ctx, const float* params);
 
+/* Learned correction of the particle force (off by default; params = NULL returns to the plain kernel): the same
+ * network form as hrt_set_ray_correction, g(|k| cell, a, ln N_mesh) = 1 + MLP, evaluated on the tensor cores at
+ * each force evaluation's scale factor and multiplying the Green's function of the particle gradient fields
+ * (k/k^2 -> (k/k^2) g, the force sharpening of Sec. 6.2).  The rays read the corrected fields unless the context
+ * has ray fields of its own (ray_fields == 2).  params: device float32 [hrt_mlp_params] (copied).  The plain
+ * kernel stays the fallback and the yardstick; a run with it is not recorded for hrt_adjoint. */
+hrt_status hrt_set_particle_correction(hrt_ctx* ctx, const float* params);
+
 /* Light-cone tiling of the context's rays (see hrt_ray_geom): n replicas with their [n][3] axis, sign and
  * shift tables (host, copied); n = 0 removes it.  Needs ray_fields == 0 (HRT_ERR_STATE otherwise). */
 hrt_status hrt_set_replicas(hrt_ctx* ctx, int32_t n, const int32_t* perm, const int32_t* sign, const int32_t* shift);

@@ -743,6 +743,17 @@ static hrt_status ctx_solve(hrt_ctx* ctx) {
     fr.g_nk = ctx->ray_table_nk;
     fr.g_kmax = ctx->ray_table_kmax;
   }
+  if (ctx->pcorr_w) {
+    // the learned factor of the particle force (read by the rays too when they have no fields of their own)
+    const double cell = c.box / c.n_mesh;
+    HRT_TRY(launch_correction_inputs(ctx->pcorr_x, kCorrectionRows, kCorrectionKmaxCell / (kCorrectionRows - 1),
+                                     ctx->a, std::log(static_cast<double>(c.n_mesh)), ctx->stream));
+    HRT_TRY(launch_mlp_forward(ctx->pcorr_x, kCorrectionRows, ctx->pcorr_wb, ctx->pcorr_w, ctx->pcorr_table,
+                               ctx->stream));
+    f.g_table = ctx->pcorr_table;
+    f.g_nk = kCorrectionRows;
+    f.g_kmax = kCorrectionKmaxCell / cell;
+  }
   cudaEvent_t wait = ctx->rays_pending ? ctx->ev_rays : nullptr;
   ctx->rays_pending = false;
   ctx->force_valid = false;
@@ -1597,6 +1608,10 @@ hrt_status hrt_destroy(hrt_ctx* ctx) {
   device_free(ctx->corr_w, s);
   device_free(ctx->corr_wb, s);
   device_free(ctx->corr_x, s);
+  device_free(ctx->pcorr_w, s);
+  device_free(ctx->pcorr_wb, s);
+  device_free(ctx->pcorr_x, s);
+  device_free(ctx->pcorr_table, s);
   device_free(ctx->corr_table, s);
   device_free(ctx->ray_table, s);
   cudaStreamSynchronize(s);
@@ -1786,42 +1801,57 @@ hrt_status hrt::ctx_step(hrt_ctx* ctx, double a_next, int32_t source, double wei
   return ctx_mark(ctx, s);
 }
 
+namespace hrt {
+// Sets (params != NULL: copies the FP32 parameters, refreshes the BF16 copy) or removes one learned correction
+// network of the context; its buffers are allocated all or none.
+static hrt_status set_correction(hrt_ctx* ctx, const float* params, float*& w, void*& wb, float*& x, float*& t) {
+  cudaStream_t st = ctx->stream;
+  if (!params) {
+    device_free(w, st);
+    device_free(wb, st);
+    device_free(x, st);
+    device_free(t, st);
+    w = t = x = nullptr;
+    wb = nullptr;
+    return HRT_OK;
+  }
+  if (!w) {
+    float *nw = nullptr, *nx = nullptr, *nt = nullptr;
+    void* nwb = nullptr;
+    hrt_status s = device_alloc(reinterpret_cast<void**>(&nw), kMlpParams * sizeof(float), st, "correction");
+    if (s == HRT_OK) s = device_alloc(&nwb, kMlpParams * 2, st, "correction bf16");
+    if (s == HRT_OK) s = device_alloc(reinterpret_cast<void**>(&nx), 3 * kCorrectionRows * sizeof(float), st, "inputs");
+    if (s == HRT_OK) s = device_alloc(reinterpret_cast<void**>(&nt), kCorrectionRows * sizeof(float), st, "table");
+    if (s != HRT_OK) {
+      device_free(nw, st);
+      device_free(nwb, st);
+      device_free(nx, st);
+      device_free(nt, st);
+      return s;
+    }
+    w = nw;
+    wb = nwb;
+    x = nx;
+    t = nt;
+  }
+  hrt_status s = cuda_status(cudaMemcpyAsync(w, params, kMlpParams * sizeof(float), cudaMemcpyDeviceToDevice, st),
+                             "copy correction");
+  if (s == HRT_OK) s = launch_to_bf16(w, wb, st);
+  return ctx_mark(ctx, s);
+}
+}  // namespace hrt
+
 hrt_status hrt_set_ray_correction(hrt_ctx* ctx, const float* params) {
   HRT_TRY(ctx_guard(ctx));
   if (ctx->cfg.ray_fields != 2) return fail(HRT_ERR_STATE, "a ray correction needs ray_fields == 2");
-  cudaStream_t st = ctx->stream;
-  if (!params) {
-    device_free(ctx->corr_w, st);
-    device_free(ctx->corr_wb, st);
-    device_free(ctx->corr_x, st);
-    device_free(ctx->corr_table, st);
-    ctx->corr_w = ctx->corr_table = ctx->corr_x = nullptr;
-    ctx->corr_wb = nullptr;
-    return HRT_OK;
-  }
-  if (!ctx->corr_w) {
-    float *w = nullptr, *x = nullptr, *t = nullptr;
-    void* wb = nullptr;
-    hrt_status s = device_alloc(reinterpret_cast<void**>(&w), kMlpParams * sizeof(float), st, "correction");
-    if (s == HRT_OK) s = device_alloc(&wb, kMlpParams * 2, st, "correction bf16");
-    if (s == HRT_OK) s = device_alloc(reinterpret_cast<void**>(&x), 3 * kCorrectionRows * sizeof(float), st, "inputs");
-    if (s == HRT_OK) s = device_alloc(reinterpret_cast<void**>(&t), kCorrectionRows * sizeof(float), st, "table");
-    if (s != HRT_OK) {
-      device_free(w, st);
-      device_free(wb, st);
-      device_free(x, st);
-      device_free(t, st);
-      return s;
-    }
-    ctx->corr_w = w;
-    ctx->corr_wb = wb;
-    ctx->corr_x = x;
-    ctx->corr_table = t;
-  }
-  hrt_status s = cuda_status(cudaMemcpyAsync(ctx->corr_w, params, kMlpParams * sizeof(float),
-                                             cudaMemcpyDeviceToDevice, st), "copy correction");
-  if (s == HRT_OK) s = launch_to_bf16(ctx->corr_w, ctx->corr_wb, st);
-  return ctx_mark(ctx, s);
+  return set_correction(ctx, params, ctx->corr_w, ctx->corr_wb, ctx->corr_x, ctx->corr_table);
+}
+
+hrt_status hrt_set_particle_correction(hrt_ctx* ctx, const float* params) {
+  HRT_TRY(ctx_guard(ctx));
+  if (ctx->cfg.static_mode) return fail(HRT_ERR_STATE, "a particle-force correction needs the expanding mode");
+  if (params) tape_invalidate(ctx, "a learned particle force is not differentiated");
+  return set_correction(ctx, params, ctx->pcorr_w, ctx->pcorr_wb, ctx->pcorr_x, ctx->pcorr_table);
 }
 
 hrt_status hrt_sync_particles(hrt_ctx* ctx) {

@@ -80,6 +80,11 @@ struct hrt_ctx {
   void* corr_wb = nullptr;
   float* corr_x = nullptr;
   float* corr_table = nullptr;
+  // learned correction of the particle force (NULL: plain), the same network form evaluated per force at a
+  float* pcorr_w = nullptr;
+  void* pcorr_wb = nullptr;
+  float* pcorr_x = nullptr;
+  float* pcorr_table = nullptr;
   // light-cone tiling (empty: none): [n][3] perm, sign, shift
   std::vector<int32_t> rep_perm, rep_sign, rep_shift;
   // ray-mesh kick operator of Sec. 5.2 (NULL: the direct line-of-sight gather)

@@ -142,6 +142,7 @@ hrt_status tape_on_ics(hrt_ctx* ctx, const float* noise, double a_init, bool lpt
   t.a_init = a_init;
   t.lpt2 = lpt2;
   t.valid = true;
+  if (ctx->pcorr_w) tape_invalidate(ctx, "a learned particle force is not differentiated");
   return HRT_OK;
 }
 
@@ -162,6 +163,10 @@ hrt_status tape_on_rays(hrt_ctx* ctx, const double* theta0, int64_t n_rays) {
 hrt_status tape_on_step(hrt_ctx* ctx, char kind, double a_next, int slot, double weight, bool accumulate) {
   if (!ctx->tape || !ctx->tape->valid) return HRT_OK;
   Tape& t = *ctx->tape;
+  if (ctx->pcorr_w) {
+    tape_invalidate(ctx, "a learned particle force is not differentiated");
+    return HRT_OK;
+  }
   if (kind == 'R' && t.rays_start < 0) {
     tape_invalidate(ctx, "a ray step ran with rays not initialised after the recorded ICs");
     return HRT_OK;

@@ -154,6 +154,7 @@ _SIGS = {
     "hrt_set_host_wait_limit": ([_D], C.c_int),
     "hrt_inject_alloc_failure": ([_I64], C.c_int),
     "hrt_set_ray_theta_bits": ([_P, _I32], C.c_int),
+    "hrt_set_particle_correction": ([_P, _P], C.c_int),
     "hrt_static_prefactor": ([_D, _D, _P], C.c_int),
     "hrt_ctx_phase_times": ([_P, _P, _P], C.c_int),
     "hrt_ctx_rays": ([_P, _P], C.c_int),
@@ -811,6 +812,13 @@ class Context:
         if params is not None and params.numel() != MLP_PARAMS:
             raise ValueError(f"params must hold {MLP_PARAMS} values")
         _check(_lib.hrt_set_ray_correction(self._h, _ptr(params, torch.float32, "params")), "hrt_set_ray_correction")
+
+    def hrt_set_particle_correction(self, params: torch.Tensor | None):
+        """Learned particle-force correction (float32 MLP parameters on the device), or None for the plain force."""
+        if params is not None and params.numel() != MLP_PARAMS:
+            raise ValueError(f"params must hold {MLP_PARAMS} values")
+        _check(_lib.hrt_set_particle_correction(self._h, _ptr(params, torch.float32, "params")),
+               "hrt_set_particle_correction")
 
     def hrt_set_replicas(self, replicas=None):
         """Light-cone tiling: (perm, sign, shift) [k][3] integer arrays, or None to remove it."""

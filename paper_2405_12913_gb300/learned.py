@@ -135,16 +135,19 @@ def plain_run(S: PairSpec, n_mesh: int, seed: int, record_spectra: bool = False)
 
 
 def run(S: PairSpec, n_mesh: int, seed: int, params: torch.Tensor | None = None, record_spectra: bool = False,
-        timed: bool = False):
-    """HRT run on an n_mesh^3 mesh through the context API, with the learned ray correction ``params`` (None:
-    plain).  Returns (kappa map, [density spectra per reverse step], milliseconds of the reverse co-evolution
-    steps (CUDA events on the context's stream) or None)."""
+        timed: bool = False, pparams: torch.Tensor | None = None):
+    """HRT run on an n_mesh^3 mesh through the context API, with the learned ray correction ``params`` and the
+    learned particle-force correction ``pparams`` (None: plain; without a ray correction the rays read the
+    particle fields, corrected or not).  Returns (kappa map, [density spectra per reverse step], milliseconds of
+    the reverse co-evolution steps (CUDA events on the context's stream) or None)."""
     cfg = hrt.make_config(n_mesh, S.box, S.n_side, S.omega_m, S.h, S.n_s, S.sigma8, S.deconv_p, S.smooth_cells,
                           1.0, S.observer, n_sources=1, ray_fields=0 if params is None else 2,
                           ray_deconv_p=S.deconv_p, ray_smooth_cells=S.smooth_cells)
     ctx = hrt.Context(cfg)
     if params is not None:
         ctx.hrt_set_ray_correction(params)
+    if pparams is not None:
+        ctx.hrt_set_particle_correction(pparams)
     ctx.hrt_init_particles_zeldovich(_noise(seed, S.n_side).reshape(-1), S.a_init)
     for a in S.forward_grid[1:]:
         ctx.hrt_step(a)
@@ -261,14 +264,131 @@ class RayTrainer:
             mlp.accumulate(self.x[i], tb, grad)
 
 
+class ForceTrainer:
+    """Force matching of the particle correction (the analogue of the trained force sharpening of Sec. 6.2): at
+    snapshots of fine-mesh runs, the coarse-mesh PM force with the learned factor g, interpolated at the
+    particles, against the fine-mesh force there.  Loss per snapshot: sum_p |F_coarse - F_fine|^2 / sum_p
+    |F_fine|^2.  Gradients go through the gather adjoint (``hrt_particle_kick_drift_adjoint``), forward FFTs of
+    the field cotangents and ``hrt_kspace_table_adjoint`` into the MLP; all arithmetic in libhrt kernels."""
+
+    def __init__(self, S: PairSpec, n_coarse: int):
+        self.S, self.n = S, n_coarse
+        self.cell = S.box / n_coarse
+        self.kmax = math.sqrt(3.0) * math.pi / self.cell * 1.0001
+        self.pm = _pm_cache(n_coarse, S.box)
+        self.samples = []
+
+    def _filter(self, table):
+        return hrt.make_filter(self.S.deconv_p, self.S.smooth_cells * self.cell, table, self.kmax)
+
+    def add_seed(self, seed: int, snapshots):
+        """Fine run of the seed (plain force) up to a = 1; at each snapshot a the particles, their fine-mesh force
+        and the coarse density spectrum of the same particles."""
+        S, n = self.S, self.n
+        cfg = hrt.make_config(S.n_fine, S.box, S.n_side, S.omega_m, S.h, S.n_s, S.sigma8, S.deconv_p,
+                              S.smooth_cells, 1.0, S.observer)
+        ctx = hrt.Context(cfg)
+        ctx.hrt_init_particles_zeldovich(_noise(seed, S.n_side).reshape(-1), S.a_init)
+        want = sorted(snapshots)
+        for a in S.forward_grid[1:]:
+            ctx.hrt_step(a)
+            while want and abs(a - want[0]) < 1e-9:
+                disp, _, _, _ = ctx.hrt_read_particles()
+                grad = ctx.hrt_read_grad()
+                f_fine = torch.zeros(3, S.n_side ** 3, device="cuda")
+                hrt.hrt_particle_kick_drift(grad, S.n_fine, S.box, S.n_side, disp.clone(), f_fine, -1.0, 0.0)
+                del grad
+                rho = torch.empty(n ** 3, device="cuda")
+                hrt.hrt_cic_scatter(disp, S.n_side, n, S.box, rho)
+                spec = torch.empty(n, n, n // 2 + 1, dtype=torch.complex64, device="cuda")
+                self.pm.forward_fft(rho, spec)
+                self.samples.append(dict(a=a, disp=disp, f_fine=f_fine, norm=float((f_fine.double() ** 2).sum()),
+                                         spec=spec, x=MLP.inputs(self.kmax, self.cell, a, n)))
+                want.pop(0)
+        ctx.close()
+
+    def loss_and_grad(self, mlp: MLP | None, sample, grad=None):
+        """Relative force error of one snapshot; with grad, adds the MLP parameter gradient."""
+        S, n = self.S, self.n
+        table = mlp.table(sample["x"]) if mlp is not None else torch.ones(N_TABLE, device="cuda")
+        f = self._filter(table)
+        pref = 1.5 * S.omega_m / sample["a"]
+        fields = torch.empty(3, n ** 3, device="cuda")
+        self.pm.gradient_from_spectrum(sample["spec"], pref, f, 3, fields)
+        zeros = torch.zeros(3, S.n_side ** 3, device="cuda")
+        fc = zeros.clone()
+        disp = sample["disp"]
+        hrt.hrt_particle_kick_drift(fields, n, S.box, S.n_side, disp.clone(), fc, -1.0, 0.0)
+        r = fc - sample["f_fine"]
+        loss = float((r.double() ** 2).sum()) / sample["norm"]
+        if grad is not None:
+            m_bar = (2.0 / sample["norm"]) * r
+            g_bar = torch.zeros(3, n ** 3, device="cuda")
+            hrt.hrt_particle_kick_drift_adjoint(fields, n, S.box, S.n_side, disp.clone(), zeros, -1.0, 0.0, None,
+                                                torch.zeros_like(zeros), m_bar.contiguous(), g_bar,
+                                                torch.zeros(2, dtype=torch.float64, device="cuda"))
+            gbar_hat = torch.empty(3, n, n, n // 2 + 1, dtype=torch.complex64, device="cuda")
+            for j in range(3):
+                self.pm.forward_fft(g_bar[j].contiguous(), gbar_hat[j])
+            tb = torch.zeros(N_TABLE, device="cuda")
+            hrt.hrt_kspace_table_adjoint(gbar_hat, 3, sample["spec"], n, S.box, pref, f, tb)
+            mlp.accumulate(sample["x"], tb, grad)
+        return loss
+
+
+def train_particle(S: PairSpec, train_seeds, test_seeds, iters: int = 300, lr: float = 2e-3, log=print,
+                   snapshots=(0.2, 0.4, 0.6, 0.8, 1.0), meshes=None):
+    """Adam on the particle-correction MLP by force matching (ForceTrainer), over the coarse meshes (default
+    S.n_coarse; ln N_mesh is an input, so one network serves them all) and the training seeds' snapshots; returns
+    the network and the relative force errors of the plain and the learned coarse force on the held-out seeds."""
+    meshes = tuple(meshes) if meshes else (S.n_coarse,)
+    t0 = time.time()
+    fg = S.forward_grid
+    snaps = sorted({min(fg[1:], key=lambda a: abs(a - t)) for t in snapshots})
+    trainers = {m: ForceTrainer(S, m) for m in meshes}
+    test = {m: ForceTrainer(S, m) for m in meshes}
+    for m in meshes:
+        for s in train_seeds:
+            trainers[m].add_seed(s, snaps)
+        for s in test_seeds:
+            test[m].add_seed(s, snaps)
+    log(f"force snapshots: {len(train_seeds)} + {len(test_seeds)} seeds x {len(snaps)} times x {len(meshes)} meshes "
+        f"in {time.time() - t0:.1f} s")
+    mlp = MLP(seed=1)
+    history = []
+    norm = sum(len(t.samples) for t in trainers.values())
+    for it in range(iters):
+        grad = torch.zeros(hrt.MLP_PARAMS, device="cuda")
+        loss = 0.0
+        for t in trainers.values():
+            for smp in t.samples:
+                loss += t.loss_and_grad(mlp, smp, grad) / norm
+        grad /= norm
+        mlp.adam(grad, lr)
+        history.append(loss)
+        if it % 25 == 0 or it == iters - 1:
+            log(f"iter {it:3d} force loss {loss:.4e} ({time.time() - t0:.1f} s)")
+    result = {"snapshots": snaps, "meshes": list(meshes), "train_seconds": time.time() - t0,
+              "loss_first_last": [history[0], history[-1]], "held_out": {}}
+    for m, t in test.items():
+        plain = [t.loss_and_grad(None, smp) for smp in t.samples]
+        learned_err = [t.loss_and_grad(mlp, smp) for smp in t.samples]
+        result["held_out"][str(m)] = {"plain_rel_force_err2": float(np.mean(plain)),
+                                      "learned_rel_force_err2": float(np.mean(learned_err))}
+    return mlp, result
+
+
 def _bins(S: PairSpec, ell, cnt):
     return (cnt > 0) & (ell <= S.ell_cut)
 
 
-def train(S: PairSpec, train_seeds, test_seeds, iters: int = 60, lr: float = 2e-3, log=print, meshes=None):
+def train(S: PairSpec, train_seeds, test_seeds, iters: int = 60, lr: float = 2e-3, log=print, meshes=None,
+          batch_seeds: int = 0):
     """Adam on the MLP parameters: loss = mean over coarse meshes and training seeds of sum over the bins with
     ell <= S.ell_cut of (P_coarse / P_fine - 1)^2, each coarse mesh paired with the S.n_fine run of the same ICs
-    (meshes: the coarse sides, default S.n_coarse; ln N_mesh is an input, so one network serves them all)."""
+    (meshes: the coarse sides, default S.n_coarse; ln N_mesh is an input, so one network serves them all).  With
+    batch_seeds > 0 each Adam step uses that many training seeds drawn without replacement (a seeded generator),
+    which keeps the cost of a step bounded at large ray counts while every seed takes part in the training."""
     meshes = tuple(meshes) if meshes else (S.n_coarse,)
     t0 = time.time()
     fine, spectra, plain_p = {}, {}, {}
@@ -284,13 +404,18 @@ def train(S: PairSpec, train_seeds, test_seeds, iters: int = 60, lr: float = 2e-
     trainers = {m: RayTrainer(replace(S, n_coarse=m)) for m in meshes}
     mlp = MLP(seed=0)
     history = []
-    norm = len(train_seeds) * len(meshes)
+    train_seeds = list(train_seeds)
+    per_step = batch_seeds if 0 < batch_seeds < len(train_seeds) else len(train_seeds)
+    pick = np.random.default_rng(12345)
+    norm = per_step * len(meshes)
     lmin, lmax = S.ell_range
     for it in range(iters):
         grad = torch.zeros(hrt.MLP_PARAMS, device="cuda")
         loss = 0.0
+        batch = (train_seeds if per_step == len(train_seeds)
+                 else sorted(pick.choice(train_seeds, size=per_step, replace=False).tolist()))
         for m in meshes:
-            for s in train_seeds:
+            for s in batch:
                 kappa, saved = trainers[m].forward(mlp, spectra[(m, s)], keep=True)
                 _, p, _ = power(S, kappa)
                 r = p / fine[s] - 1.0
@@ -374,7 +499,7 @@ def ladder_seeds(S: PairSpec, seeds, meshes=(256, 512, 768), cuts=None, learned_
     mean P(ell) error over the seeds and bins, the largest error per bin over the seeds, the ell up to which every
     bin is within 1 % on every seed, and whether all bins with ell <= cut are within 1 % on every seed; then, for
     the plain and the learned forms, the coarsest mesh that meets 1 % in every bin up to each cut on all seeds
-    (None when none does)."""
+    (None when none does), per form name."""
     cuts = tuple(cuts) if cuts else (S.ell_cut,)
     per_seed = [ladder(S, None, s, meshes=meshes, cuts=cuts, log=log, learned_forms=list(learned_forms))
                 for s in seeds]
@@ -397,11 +522,12 @@ def ladder_seeds(S: PairSpec, seeds, meshes=(256, 512, 768), cuts=None, learned_
                     "bin_ell": errs[0]["ell"]}
         forms.append(out)
     coarsest = {}
+    names = sorted({f["form"] for f in forms if "errors" in f})
     for key in [f"ell_le_{c:g}" for c in cuts]:
-        for kind in ("plain", "learned"):
-            ok = [f["mesh"] for f in forms if "errors" in f and f["form"].startswith(kind)
-                  and f["errors"][key]["meets_1pct_all_seeds"]]
-            coarsest[f"{kind} {key}"] = min(ok) if ok else None
+        for name in names:
+            ok = [f["mesh"] for f in forms
+                  if f["form"] == name and "errors" in f and f["errors"][key]["meets_1pct_all_seeds"]]
+            coarsest[f"{name}, {key}"] = min(ok) if ok else None
     return {"seeds": list(seeds), "forms": forms, "coarsest_mesh_within_1pct": coarsest}
 
 
@@ -422,9 +548,11 @@ def ladder(S: PairSpec, params: torch.Tensor | None, seed: int, meshes=(256, 512
         forms += list(learned_forms)
     elif params is not None:
         forms += [(m, params, "learned") for m in lm]
-    for m, w, name in forms:
-        run(S, m, seed, params=w)
-        k, _, ms = run(S, m, seed, params=w, timed=True)
+    for form in forms:
+        m, w, name = form[:3]
+        wp = form[3] if len(form) > 3 else None
+        run(S, m, seed, params=w, pparams=wp)
+        k, _, ms = run(S, m, seed, params=w, timed=True, pparams=wp)
         p = power(S, k)[1]
         row = {"mesh": m, "form": name,
                "sim_steps_per_s": S.n_reverse / (ms * 1e-3), "errors": {}}
@@ -456,16 +584,28 @@ def main():
     ap.add_argument("--meshes", default=None, help="coarse mesh sides to train on, e.g. 256,512 (default 256)")
     ap.add_argument("--ladder-n-pix", type=int, default=0,
                     help="rays per side of the accuracy-vs-speed ladder on the first held-out seed (0: skip)")
+    ap.add_argument("--batch-seeds", type=int, default=0,
+                    help="training seeds per Adam step, drawn from the training seeds (0: all)")
+    ap.add_argument("--particle", action="store_true",
+                    help="train the particle-force correction by force matching instead of the ray correction")
     a = ap.parse_args()
     S = replace(PairSpec(), n_pix=a.n_pix, ell_cut=a.ell_cut)
     test = list(range(100, 100 + a.test_seeds))
     out = {}
+    if a.particle:
+        meshes = tuple(int(x) for x in a.meshes.split(",")) if a.meshes else None
+        mlp, res = train_particle(S, range(a.train_seeds), test, a.iters, a.lr, log=lambda m: print(m, flush=True),
+                                  meshes=meshes)
+        if a.out:
+            np.save(a.out, mlp.state())
+        print(json.dumps({"particle_training": res}))
+        return
     if a.params:
         w = torch.tensor(np.load(a.params), dtype=torch.float32, device="cuda")
     else:
         meshes = tuple(int(x) for x in a.meshes.split(",")) if a.meshes else None
         mlp, res = train(S, range(a.train_seeds), test, a.iters, a.lr, log=lambda m: print(m, flush=True),
-                         meshes=meshes)
+                         meshes=meshes, batch_seeds=a.batch_seeds)
         if a.out:
             np.save(a.out, mlp.state())
         w = mlp.w

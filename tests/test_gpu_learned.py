@@ -199,3 +199,54 @@ def test_context_fixed_ray_table_matches_ray_trainer(hrt):
     assert (diff > 1e-4 * scale).float().mean().item() <= 2e-3  # rare cell-face crossings
     assert diff.median().item() <= 1e-6 * scale
     assert (k_ctx - k_plain).abs().max().item() > 1e-3 * scale
+
+
+def test_context_particle_correction_is_the_stateless_solve_with_its_table(hrt):
+    # the particle-force correction of a context: its force fields after the ICs equal the stateless PM solve of
+    # the same density with the network's table at the ICs' scale factor (the same |k| grid as the context's); a
+    # network with a zero output layer is the plain force; a recorded run refuses it
+    from paper_2405_12913_gb300.configs import COSMO_TINY as W
+    from paper_2405_12913_gb300 import learned
+    n, box = W.n_mesh, W.box
+    noise = torch.tensor(synthetic.white_noise(W.seed, W.n_side), dtype=torch.float32, device="cuda").reshape(-1)
+    cfg = hrt.make_config(n, box, W.n_side, W.omega_m, W.h, W.n_s, W.sigma8, W.deconv_p, W.smooth_cells,
+                          W.samples_per_cell, W.observer)
+    plain = hrt.Context(cfg)
+    plain.hrt_init_particles_zeldovich(noise, W.a_init)
+    g_plain = plain.hrt_read_grad().clone()
+    disp, _, _, _ = plain.hrt_read_particles()
+    plain.close()
+    cell = box / n
+    kmax = math.sqrt(3.0) * math.pi / cell * 1.0001
+    for which, p in (("zero output layer", learned.MLP(seed=0).w), ("random", torch.tensor(_params(9), device="cuda"))):
+        ctx = hrt.Context(cfg)
+        ctx.hrt_set_particle_correction(p)
+        ctx.hrt_init_particles_zeldovich(noise, W.a_init)
+        got = ctx.hrt_read_grad()
+        ctx.close()
+        wb = torch.empty(hrt.MLP_PARAMS, dtype=torch.bfloat16, device="cuda")
+        hrt.hrt_mlp_to_bf16(p, wb)
+        table = torch.empty(learned.N_TABLE, device="cuda")
+        hrt.hrt_mlp_forward(learned.MLP.inputs(kmax, cell, W.a_init, n), wb, p, table)
+        rho = torch.empty(n ** 3, device="cuda")
+        hrt.hrt_cic_scatter(disp, W.n_side, n, box, rho)
+        pm = hrt.PM(n, box)
+        want = torch.empty(3, n ** 3, device="cuda")
+        pm.solve(rho, 1.5 * W.omega_m / W.a_init, hrt.make_filter(W.deconv_p, W.smooth_cells * cell, table, kmax), want)
+        pm.close()
+        scale = float(want.abs().max())
+        assert float((got.reshape(3, -1) - want).abs().max()) <= 1e-5 * scale, which
+        if which == "zero output layer":
+            assert float((got - g_plain).abs().max()) <= 1e-5 * scale
+        else:
+            assert float((got - g_plain).abs().max()) > 1e-3 * scale
+    ctx = hrt.Context(cfg)
+    ctx.hrt_set_checkpointing(2)
+    ctx.hrt_set_particle_correction(torch.tensor(_params(9), device="cuda"))
+    ctx.hrt_init_particles_zeldovich(noise, W.a_init)
+    ctx.hrt_step(W.forward_grid[1])
+    with pytest.raises(hrt.HRTError) as e:
+        ctx.hrt_adjoint(None)
+    assert "particle force" in str(e.value)
+    ctx.hrt_set_particle_correction(None)
+    ctx.close()
