@@ -33,7 +33,7 @@ KERNEL_SOURCES = {
     "ray_step": ["ray_kernels.cu", "mesh_kernels.h"],
     "kick_drift": ["mesh_kernels.cu"],
     "cic_scatter": ["mesh_kernels.cu"],
-    "kspace": ["mesh_kernels.cu", "xpass_kernels.cu"],
+    "kspace": ["mesh_kernels.cu", "xpass_kernels.cu", "tma.h"],
 }
 
 
@@ -54,6 +54,9 @@ def parse():
                    help="skip the per-output errors against the stored FP64 oracle outputs (and the FP32-angle ablation)")
     p.add_argument("--sort-every", type=int, default=None,
                    help="re-sort the particles by mesh cell every K particle steps (default: the library's, 4; 0: never)")
+    p.add_argument("--tiled-deposit", type=int, default=0, choices=[0, 1, 2],
+                   help="kick-drift-deposit: 0 per-particle gathers and reductions on z-row order (default), "
+                        "2 shared-memory tiles by TMA on brick order, 1 tiles by row copies")
     p.add_argument("--kick", default="direct", choices=["direct", "mesh"],
                    help="kick operator of the rays: the direct line-of-sight gather or the ray mesh of Sec. 5.2")
     return p.parse_args()
@@ -227,6 +230,8 @@ def run_gpu(args, W, world, rank, local):
     ctx = hrt.Context(cfg)
     if args.sort_every is not None:
         ctx.hrt_set_particle_sort(args.sort_every)
+    if args.tiled_deposit != 0:
+        ctx.hrt_set_tiled_deposit(args.tiled_deposit)
     noise = torch.from_numpy(synthetic.white_noise(seed, W.n_side).astype(np.float32)).to(dev)
     theta0_h = torch.from_numpy(synthetic.pixel_grid(W.n_pix, W.fov_deg * synthetic.DEGREE))
     theta0 = theta0_h.to(dev)
@@ -245,14 +250,15 @@ def run_gpu(args, W, world, rank, local):
         ctx.hrt_set_ray_mesh(raymesh_config(hrt, W))
         ray_launches = 5
 
-    # the context re-sorts its particles every sort_every particle steps after new particles (5 own launches)
+    # the context sorts particles given by the caller at their first step, then every sort_every particle steps
+    # (6 own launches: cell keys, three scan passes, inversion, gather)
     sort_every = 4 if args.sort_every is None else args.sort_every
     since_sort = [0]
 
     def reset():
         ctx.hrt_init_particles(disp0, mom0, 1.0)
         ctx.hrt_init_rays(theta0)
-        since_sort[0] = 0
+        since_sort[0] = sort_every - 1 if sort_every > 0 else 0
 
     reset.state = (disp0, mom0, theta0)
 
@@ -270,7 +276,7 @@ def run_gpu(args, W, world, rank, local):
             launches += 2 + ray_launches  # ray step, kick-drift-deposit, k-space pass (x-pass on the split path)
             since_sort[0] += 1
             if sort_every > 0 and since_sort[0] >= sort_every:
-                launches += 5  # cell keys, three scan passes, scatter
+                launches += 6
                 since_sort[0] = 0
             pos = n
         return pos, launches
@@ -368,6 +374,8 @@ def run_gpu(args, W, world, rank, local):
                    "n_rays": W.n_rays, "fov_deg": W.fov_deg, "reverse_steps": W.n_reverse,
                    "timed_steps_start_at_a": 1.0, "parallelism": f"replicas{world}",
                    "particle_sort_every": sort_every,
+                   "deposit": {0: "per-particle", 1: "shared-memory tiles by row copies",
+                               2: "shared-memory tiles by TMA"}[args.tiled_deposit],
                    "kick": ("ray mesh (iota %g, p_min %g)" % (RAYMESH_IOTA, RAYMESH_P_MIN)
                             if args.kick == "mesh" else "direct line-of-sight gather"),
                    "l2": "inputs larger than L2 (%.2g GB mesh per field)" % (W.n_mesh ** 3 * 4 / 1e9)},

@@ -99,6 +99,19 @@ hrt_status hrt_particle_kick_drift(const float* grad, int64_t n, double box, int
 hrt_status hrt_particle_kick_drift_deposit(const float* grad, int64_t n, double box, int64_t n_side, float* disp,
                                            float* mom, double kick, double drift, float* rho, void* stream);
 
+/* hrt_particle_kick_drift_deposit on particles stored in brick order (the context's sort, hrt_set_particle_sort),
+ * with shared-memory field and density tiles: n a multiple of 32 up to 1024; slot i of disp, mom ([3][n_side^3])
+ * holds lattice particle order[i] (device int32 [n_side^3]); key_start (device int32 [n^3 / 32]) gives the first
+ * slot of every sort key, key = brick * 64 + 8 (ix mod 8) + (iy mod 8) for bricks of 8 x 8 x 32 cells numbered
+ * ((iz / 32) (n / 8) + ix / 8) (n / 8) + iy / 8.  Brick b's block takes slots [key_start[64 b], key_start[64 b +
+ * 64]) (to n_side^3 for the last brick; offsets are clamped into range).  The update of every particle is the
+ * same bit for bit whatever the offsets: a particle outside its block's tile takes the per-particle path; only
+ * the order of the density's float additions differs.  A slot outside every range is not updated. */
+hrt_status hrt_particle_kick_drift_deposit_bricks(const float* grad, int64_t n, double box, int64_t n_side,
+                                                  float* disp, float* mom, const int32_t* order,
+                                                  const int32_t* key_start, double kick, double drift, float* rho,
+                                                  void* stream);
+
 /* k-space filter of the gradient fields (Sec. 5.2 kick operator taken on the 3D mesh):
  *   prod_i sinc(k_i cell/2)^-deconv_p  *  exp(-k^2 smooth^2 / 2)  *  g(|k|)
  * with g the optional learned correction table: g_table[nk] (device, float32) sampled uniformly on
@@ -579,12 +592,28 @@ hrt_status hrt_raymesh_step_planes(const hrt_raymesh_config* cfg, const hrt_ray_
                                    double* chi_host, double* w_host, double* drift_host);
 
 /* Storage order of the context's particles: every `every` particle steps (hrt_step, hrt_step_accumulate) the
- * context re-sorts its particles by mesh cell (a counting sort by z-row segments of 32 cells) before the
- * kick-drift-deposit, so that neighbouring threads gather from and deposit into neighbouring cells also after
- * clustering has spread lattice neighbours apart; 0 keeps lattice order (the default after hrt_create is 4).
- * Only the storage order changes: every read-out (hrt_read_particles, hrt_save_state) is in lattice order.
- * Extra device memory once sorting starts: 44 B per particle and 4 B per 32 mesh cells. */
+ * context re-sorts its particles by mesh cell (a counting sort by z-row segments of 32 cells in row-major order,
+ * grouped into bricks of 8 x 8 x 32 cells while the tiled deposit of hrt_set_tiled_deposit is selected) before
+ * the kick-drift-deposit, so that neighbouring threads gather from and deposit into neighbouring cells also
+ * after clustering has spread lattice neighbours apart; 0 keeps lattice order (the default after hrt_create is
+ * 4).  Particles given by hrt_init_particles or hrt_load_state are sorted at their first step; initial
+ * conditions, still in cell order, wait for the interval.  Only the storage order changes: every read-out
+ * (hrt_read_particles, hrt_save_state) is in lattice order.  Extra device memory once sorting starts: 44 B per
+ * particle and 4 B per 32 mesh cells. */
 hrt_status hrt_set_particle_sort(hrt_ctx* ctx, int32_t every);
+
+/* Kick-drift-deposit of the context (the particle update of Algorithm 1 with the CIC assignment of Sec. 2.2).
+ * mode 0 (the default): one thread per particle, gathers and vector reductions in global memory, particles
+ * sorted by z-row segments.  mode 2: the sort groups its keys into bricks of 8 x 8 x 32 cells (mesh sides that
+ * are multiples of 32 up to 1024), and one block per brick copies the brick's field tile into shared memory (TMA
+ * boxes for tiles inside the mesh, 16-byte row copies for tiles that wrap around it), gathers from it, deposits
+ * into a shared density tile and adds that to the mesh; particles whose stencil left the tile take the
+ * per-particle path.  mode 1: the same with row copies for every tile.  Momenta and displacements come out the
+ * same bit for bit in every mode; the density differs only in the order of its float additions.  The tiled
+ * modes are slower on a GB300 (a measured alternative) and apply from the next sort on.  A wait for a TMA box
+ * that gives up (after about a second) makes the block take the per-particle path and the step return
+ * HRT_ERR_TIMEOUT when the non-finite check is on. */
+hrt_status hrt_set_tiled_deposit(hrt_ctx* ctx, int32_t mode);
 
 /* Reverse mode of a whole run (the adjoint method named as future work in Sec. 7).  hrt_set_checkpointing(ctx,
  * k) with k >= 1 makes the context record the run that starts at the next hrt_init_particles_zeldovich: the

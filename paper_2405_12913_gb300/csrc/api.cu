@@ -307,7 +307,7 @@ struct hrt_pm {
   cufftHandle r2c2d = 0, c2r2d = 0;
   bool have_r2c2d = false, have_c2r2d = false;
   float2* xtw = nullptr;    // x-FFT twiddles
-  int* xerr = nullptr;      // device error word of the x-pass (a timed-out wait for a tile's copy)
+  int* xerr = nullptr;      // device error word of the kernels that wait for TMA copies (x-pass, tiled deposit)
   bool last_split = false;  // rho_hat holds the (y, z)-transformed density of the split path
 };
 
@@ -616,7 +616,7 @@ static hrt_status ctx_scan(hrt_ctx* ctx, std::initializer_list<ScanItem> items, 
   int flag = 0, xerr = 0;
   HRT_CUDA(cudaMemcpy(&flag, ctx->finite_flag, sizeof(int), cudaMemcpyDeviceToHost));
   if (ctx->pm && ctx->pm->xerr) HRT_CUDA(cudaMemcpy(&xerr, ctx->pm->xerr, sizeof(int), cudaMemcpyDeviceToHost));
-  if (xerr) return fail(HRT_ERR_TIMEOUT, "%s: the x-pass gave up waiting for a tile's copy", what);
+  if (xerr) return fail(HRT_ERR_TIMEOUT, "%s: a kernel gave up waiting for a tile's copy", what);
   if (flag) return fail(HRT_ERR_NONFINITE, "%s: a NaN or an infinity was found", what);
   return HRT_OK;
 }
@@ -695,20 +695,27 @@ static hrt_status ctx_sort(hrt_ctx* ctx) {
   if (!ctx->mom_alt || !ctx->order_buf[0] || !ctx->order_buf[1] || !ctx->sort_scratch)
     return fail(HRT_ERR_STATE, "particle sort buffers are incomplete");
   const int dst = ctx->order_cur == 0 ? 1 : 0;
+  // brick keys only for the tiled kick-drift-deposit: the per-particle kernel is faster on z-row order
+  const bool bricks = ctx->tiled_deposit != 0 && particle_bricks_ok(c.n_mesh);
   int32_t* counts = ctx->sort_scratch;
   int32_t* keys = counts + particle_sort_counts(c.n_mesh);
   HRT_TRY(launch_particle_sort(ctx->disp, ctx->mom, ctx_order(ctx), c.n_side, c.n_mesh, c.box, ctx->disp_alt,
-                               ctx->mom_alt, ctx->order_buf[dst], counts, keys, keys + np, keys + 2 * np, st));
+                               ctx->mom_alt, ctx->order_buf[dst], counts, keys, keys + np, keys + 2 * np, st, bricks));
   std::swap(ctx->disp, ctx->disp_alt);
   std::swap(ctx->mom, ctx->mom_alt);
   ctx->order_cur = dst;
+  ctx->sort_bricks = bricks;
+  ctx->sort_first = false;
   return HRT_OK;
 }
 
-// Back to lattice order (new particles).
-static void ctx_lattice_order(hrt_ctx* ctx) {
+// Back to lattice order (new particles).  Initial conditions keep it until the regular sort (lattice order is
+// cell order while the displacements are small); particles given by the caller or a saved state, which may be
+// clustered, are sorted at their first step.
+static void ctx_lattice_order(hrt_ctx* ctx, bool evolved = false) {
   ctx->order_cur = -1;
   ctx->steps_since_sort = 0;
+  ctx->sort_first = evolved;
 }
 
 hrt_filter ctx_filter(const hrt_config& c, bool ray) {
@@ -897,6 +904,19 @@ hrt_status hrt_particle_kick_drift_deposit(const float* grad, int64_t n, double 
   if (!grad || !disp || !mom || !rho) return fail(HRT_ERR_INVALID_ARG, "NULL buffer");
   if (!std::isfinite(kick) || !std::isfinite(drift)) return fail(HRT_ERR_INVALID_ARG, "non-finite coefficient");
   return launch_kick_drift(grad, n, box, n_side, disp, mom, kick, drift, as_stream(stream), rho);
+}
+
+hrt_status hrt_particle_kick_drift_deposit_bricks(const float* grad, int64_t n, double box, int64_t n_side,
+                                                  float* disp, float* mom, const int32_t* order,
+                                                  const int32_t* key_start, double kick, double drift, float* rho,
+                                                  void* stream) {
+  HRT_TRY(check_mesh(n, box));
+  HRT_TRY(check_particles(n_side, n));
+  if (!particle_bricks_ok(n)) return fail(HRT_ERR_INVALID_ARG, "mesh side must be a multiple of 32 up to 1024");
+  if (!grad || !disp || !mom || !rho || !order || !key_start) return fail(HRT_ERR_INVALID_ARG, "NULL buffer");
+  if (!std::isfinite(kick) || !std::isfinite(drift)) return fail(HRT_ERR_INVALID_ARG, "non-finite coefficient");
+  return launch_kick_drift_tiled(grad, n, box, n_side, disp, mom, kick, drift, rho, order, key_start,
+                                 as_stream(stream));
 }
 
 hrt_status hrt_kspace_gradient(const void* rho_hat, int64_t n, double box, double pref, const hrt_filter* f,
@@ -1690,7 +1710,7 @@ hrt_status hrt_init_particles(hrt_ctx* ctx, const float* disp, const float* mom,
     if (s != HRT_OK) ctx->have_particles = false;  // the force is not computed from a non-finite state
   }
   if (s != HRT_OK) return ctx_mark(ctx, s);
-  ctx_lattice_order(ctx);
+  ctx_lattice_order(ctx, true);
   ctx->a = ctx->a_mom = ctx->cfg.static_mode ? 1.0 : a;
   ctx->have_particles = true;
   return ctx_mark(ctx, ctx_force(ctx));
@@ -1754,7 +1774,9 @@ hrt_status hrt::ctx_step(hrt_ctx* ctx, double a_next, int32_t source, double wei
   if (!(a_next > 0.0 && a_next <= 1.0) || a_next == ctx->a) return fail(HRT_ERR_INVALID_ARG, "bad a_next");
   // a sort due in this step gets its buffers before anything moves, so that an allocation failure leaves the
   // state as it was
-  if (ctx->sort_every > 0 && ctx->steps_since_sort + 1 >= ctx->sort_every) HRT_TRY(ctx_sort_alloc(ctx));
+  const bool sort_due =
+      ctx->sort_every > 0 && (ctx->sort_first || ctx->steps_since_sort + 1 >= ctx->sort_every);
+  if (sort_due) HRT_TRY(ctx_sort_alloc(ctx));
   if (ctx->tape) {
     const char kind = (ctx->rays.n_rays > 0 && a_next < ctx->a) ? 'R' : 'F';
     HRT_TRY(ctx_mark(ctx, tape_on_step(ctx, kind, a_next, source, weight, accumulate)));
@@ -1781,17 +1803,26 @@ hrt_status hrt::ctx_step(hrt_ctx* ctx, double a_next, int32_t source, double wei
   }
   const double a_half = 0.5 * (ctx->a + a_next);
   const double kick = c.kick(ctx->a_mom, a_half), drift = c.drift(ctx->a, a_next);
-  if (ctx->sort_every > 0 && ++ctx->steps_since_sort >= ctx->sort_every) {
+  if (sort_due) {
     PhaseScope ps(ctx, 7);
     s = ctx_sort(ctx);
     if (s != HRT_OK) return ctx_mark(ctx, s);
     ctx->steps_since_sort = 0;
+  } else if (ctx->sort_every > 0) {
+    ++ctx->steps_since_sort;
   }
   {
     // kick, drift and the CIC deposit of the drifted particles (the density of the next force) in one pass
     PhaseScope ps(ctx, 1);
-    s = launch_kick_drift(ctx->grad, ctx->cfg.n_mesh, ctx->cfg.box, ctx->cfg.n_side, ctx->disp, ctx->mom, kick,
-                          drift, ctx->stream, ctx->rho, ctx_order(ctx));
+    // brick-sorted particles (the counts scratch of the last sort holds every key's first slot): shared-memory
+    // tiles; otherwise the per-particle gathers and reductions
+    if (ctx->tiled_deposit != 0 && ctx->order_cur >= 0 && ctx->sort_bricks)
+      s = launch_kick_drift_tiled(ctx->grad, ctx->cfg.n_mesh, ctx->cfg.box, ctx->cfg.n_side, ctx->disp, ctx->mom,
+                                  kick, drift, ctx->rho, ctx_order(ctx), ctx->sort_scratch, ctx->stream,
+                                  ctx->tiled_deposit, ctx->pm ? ctx->pm->xerr : nullptr);
+    else
+      s = launch_kick_drift(ctx->grad, ctx->cfg.n_mesh, ctx->cfg.box, ctx->cfg.n_side, ctx->disp, ctx->mom, kick,
+                            drift, ctx->stream, ctx->rho, ctx_order(ctx));
   }
   if (s != HRT_OK) return ctx_mark(ctx, s);
   ctx->a = a_next;
@@ -1962,6 +1993,13 @@ hrt_status hrt_set_particle_sort(hrt_ctx* ctx, int32_t every) {
   return HRT_OK;
 }
 
+hrt_status hrt_set_tiled_deposit(hrt_ctx* ctx, int32_t mode) {
+  HRT_TRY(ctx_guard(ctx));
+  if (mode < 0 || mode > kTilesTma) return fail(HRT_ERR_INVALID_ARG, "tile mode must be 0, 1 or 2");
+  ctx->tiled_deposit = mode;
+  return HRT_OK;
+}
+
 hrt_status hrt_set_checkpointing(hrt_ctx* ctx, int32_t every) {
   HRT_TRY(ctx_guard(ctx));
   if (every < 0) return fail(HRT_ERR_INVALID_ARG, "checkpoint interval must be >= 0");
@@ -2079,7 +2117,7 @@ hrt_status hrt_save_state(hrt_ctx* ctx, void* buf, size_t bytes) {
 hrt_status hrt_load_state(hrt_ctx* ctx, const void* buf, size_t bytes) {
   HRT_TRY(ctx_guard(ctx));
   tape_invalidate(ctx, "a loaded state is not differentiated");
-  ctx_lattice_order(ctx);
+  ctx_lattice_order(ctx, true);
   if (!buf || bytes < 256) return fail(HRT_ERR_INVALID_ARG, "state buffer is NULL or too small");
   StateHeader h{};
   cudaStream_t st = ctx->stream;

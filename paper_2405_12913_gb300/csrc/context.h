@@ -100,6 +100,12 @@ struct hrt_ctx {
   int32_t* sort_scratch = nullptr;
   int32_t sort_every = 0;
   int32_t steps_since_sort = 0;
+  // the sort of the current order used brick keys; the next step sorts whatever the interval (evolved particles)
+  bool sort_bricks = false;
+  bool sort_first = false;
+  // kick-drift-deposit with shared-memory field and density tiles on brick-sorted particles: 0 off (the
+  // default, z-row keys), 1 tiles copied by rows, 2 TMA boxes for the tiles inside the mesh
+  int tiled_deposit = 0;
   // fixed learned table of the ray fields (NULL: none); exclusive with the network above
   float* ray_table = nullptr;
   int32_t ray_table_nk = 0;

@@ -15,6 +15,7 @@
 #include "common.h"
 #include "kspace_callback.h"
 #include "mesh_kernels.h"
+#include "tma.h"
 
 namespace hrt {
 
@@ -104,9 +105,25 @@ static inline dim3 particle_grid(int64_t n_side, int threads, const int32_t* ord
   return dim3(static_cast<unsigned>(n_side * n_side), static_cast<unsigned>((n_side + threads - 1) / threads));
 }
 
-// Adds w0 to cell (col + iz) and w1 to cell (col + jz); z-adjacent pairs starting on an even cell use one
-// 8-byte vector reduction (col is a multiple of the even mesh side, so the address is 8-byte aligned).
-__device__ __forceinline__ void deposit_pair(float* __restrict__ rho, size_t col, int iz, int jz, float w0, float w1) {
+// Adds w0 to cell (col + iz) and w1 to cell (col + jz), jz = iz + 1 or 0 at the periodic wrap.  Mesh sides that
+// are multiples of 4 (col is then a multiple of 4 as well): one 16-byte vector reduction on the aligned group of
+// four cells that holds iz, carrying w1 too unless jz starts the next group (iz mod 4 = 3, the wrap included),
+// which takes a second, predicated one; so a warp issues two reductions per pair of rows whatever the cells of
+// its lanes, where the 8-byte and scalar forms below, taken by lanes of either parity, issue three.  Other sides:
+// z-adjacent pairs starting on an even cell use one 8-byte reduction, the rest two scalar ones.
+__device__ __forceinline__ void deposit_pair(float* __restrict__ rho, size_t col, int iz, int jz, float w0, float w1,
+                                             int n) {
+  if ((n & 3) == 0) {
+    const int s = iz & 3;
+    float4 v;
+    v.x = s == 0 ? w0 : 0.f;
+    v.y = s == 1 ? w0 : (s == 0 ? w1 : 0.f);
+    v.z = s == 2 ? w0 : (s == 1 ? w1 : 0.f);
+    v.w = s == 3 ? w0 : (s == 2 ? w1 : 0.f);
+    atomicAdd(reinterpret_cast<float4*>(rho + col + (iz - s)), v);
+    if (s == 3) atomicAdd(reinterpret_cast<float4*>(rho + col + jz), make_float4(w1, 0.f, 0.f, 0.f));
+    return;
+  }
   if (jz == iz + 1 && (iz & 1) == 0) {
     atomicAdd(reinterpret_cast<float2*>(rho + col + iz), make_float2(w0, w1));
   } else {
@@ -124,10 +141,10 @@ __device__ __forceinline__ void deposit_cic(float* __restrict__ rho, int n, int 
   const size_t c01 = static_cast<size_t>(static_cast<unsigned>(ix * n + jy)) * n;
   const size_t c10 = static_cast<size_t>(static_cast<unsigned>(jx * n + iy)) * n;
   const size_t c11 = static_cast<size_t>(static_cast<unsigned>(jx * n + jy)) * n;
-  deposit_pair(rho, c00, iz, jz, wx0 * wy0 * wz0, wx0 * wy0 * wz1);
-  deposit_pair(rho, c01, iz, jz, wx0 * wy1 * wz0, wx0 * wy1 * wz1);
-  deposit_pair(rho, c10, iz, jz, wx1 * wy0 * wz0, wx1 * wy0 * wz1);
-  deposit_pair(rho, c11, iz, jz, wx1 * wy1 * wz0, wx1 * wy1 * wz1);
+  deposit_pair(rho, c00, iz, jz, wx0 * wy0 * wz0, wx0 * wy0 * wz1, n);
+  deposit_pair(rho, c01, iz, jz, wx0 * wy1 * wz0, wx0 * wy1 * wz1, n);
+  deposit_pair(rho, c10, iz, jz, wx1 * wy0 * wz0, wx1 * wy0 * wz1, n);
+  deposit_pair(rho, c11, iz, jz, wx1 * wy1 * wz0, wx1 * wy1 * wz1, n);
 }
 
 // ---------------------------------------------------------------------------------------------------------
@@ -388,16 +405,20 @@ hrt_status launch_kspace(const void* rho_hat, int64_t n, double box, double pref
 // ---------------------------------------------------------------------------------------------------------
 // Particle gather + kick + drift: one thread per particle.
 // ---------------------------------------------------------------------------------------------------------
-__device__ __forceinline__ float trilinear(const float* __restrict__ f, int64_t r00, int64_t r01, int64_t r10,
-                                           int64_t r11, int iz, int jz, float fx, float fy, float fz) {
-  float c00 = __ldg(f + r00 + iz), c00z = __ldg(f + r00 + jz);
-  float c01 = __ldg(f + r01 + iz), c01z = __ldg(f + r01 + jz);
-  float c10 = __ldg(f + r10 + iz), c10z = __ldg(f + r10 + jz);
-  float c11 = __ldg(f + r11 + iz), c11z = __ldg(f + r11 + jz);
+// Trilinear interpolation of the eight corner values (cYX: lower/upper node along y then x; the z suffix marks
+// the upper node along z).
+__device__ __forceinline__ float trilerp(float c00, float c00z, float c01, float c01z, float c10, float c10z,
+                                         float c11, float c11z, float fx, float fy, float fz) {
   float a00 = c00 + fz * (c00z - c00), a01 = c01 + fz * (c01z - c01);
   float a10 = c10 + fz * (c10z - c10), a11 = c11 + fz * (c11z - c11);
   float b0 = a00 + fy * (a01 - a00), b1 = a10 + fy * (a11 - a10);
   return b0 + fx * (b1 - b0);
+}
+
+__device__ __forceinline__ float trilinear(const float* __restrict__ f, int64_t r00, int64_t r01, int64_t r10,
+                                           int64_t r11, int iz, int jz, float fx, float fy, float fz) {
+  return trilerp(__ldg(f + r00 + iz), __ldg(f + r00 + jz), __ldg(f + r01 + iz), __ldg(f + r01 + jz),
+                 __ldg(f + r10 + iz), __ldg(f + r10 + jz), __ldg(f + r11 + iz), __ldg(f + r11 + jz), fx, fy, fz);
 }
 
 // One thread per particle.  With DEPOSIT the drifted particle is deposited at once into rho (zeroed before
@@ -448,6 +469,249 @@ __global__ void __launch_bounds__(256) kick_drift_kernel(const float* __restrict
     cic_axis(bz, d2 * L.inv_cell, n, iz, fz);
     deposit_cic(rho, n, ix, iy, iz, fx, fy, fz, mass);
   }
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// The kick-drift-deposit on brick-sorted particles: one block per 8 x 8 x 32-cell brick of the sort.  The block
+// copies the fields of its tile (the brick plus one cell of drift and one of stencil on the upper side of each
+// axis, z rounded to 16 bytes: 10 x 10 x 36 cells) into shared memory, gathers from there, and deposits the
+// drifted particles into a density tile of the same box with shared-memory atomics, which it then adds to the
+// mesh with 16-byte vector reductions (all-zero groups skipped).  Tiles inside the mesh arrive by TMA (one 3D
+// box per field, completing on an mbarrier with a bounded wait); tiles that wrap around the periodic boundary,
+// about 5 % of the bricks at 1024^3, by 16-byte cp.async copies of their rows.  A particle whose gather or deposit
+// stencil leaves the tile (it moved below its brick since the sort, or more than a cell above) takes the global
+// path for that part; bricks with fewer than kTileMinParticles particles take the global path entirely.  Every
+// particle's arithmetic is that of kick_drift_kernel, so momenta and displacements are the same bit for bit;
+// the density differs only in the order of its float additions.
+// ---------------------------------------------------------------------------------------------------------
+constexpr int kTileX = kBrickXY + 2, kTileY = kBrickXY + 2, kTileZ = kBrickZ + 4;
+constexpr int kTileCells = kTileX * kTileY * kTileZ;
+constexpr int kFieldStride = (kTileCells + 31) / 32 * 32;  // floats per field tile: 128-byte aligned TMA boxes
+constexpr int kTileQuads = kTileZ / 4;                      // 16-byte groups per tile row
+constexpr int kTileMinParticles = 32;
+constexpr int kTileThreads = 256;
+// three field tiles, the density tile, the mbarrier, and slack for aligning the base to 128 bytes
+constexpr size_t kTileSmem = sizeof(float) * (3 * kFieldStride + kTileCells) + 16 + 128;
+
+// Tensor maps of the three gradient fields (3D, z innermost, boxes of one tile).
+struct FieldMaps {
+  CUtensorMap m[3];
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(gmem) : "memory");
+}
+
+// Offset of tile position (dx, dy, dz) in [0, tile) from tile origin (x0, y0, z0): cells wrap periodically.
+__device__ __forceinline__ int tile_wrap(int v, int n) { return v >= n ? v - n : v; }
+
+__global__ void __launch_bounds__(kTileThreads, 3)
+    kick_drift_tiled_kernel(const __grid_constant__ FieldMaps maps, int use_tma, const float* __restrict__ gx,
+                            const float* __restrict__ gy, const float* __restrict__ gz, Lattice L, int64_t np,
+                            const int32_t* __restrict__ key_start, float* __restrict__ disp, float* __restrict__ mom,
+                            float kick, float drift, float mass, float* __restrict__ rho, int* __restrict__ err) {
+  extern __shared__ unsigned char tile_raw[];
+  float* ft = reinterpret_cast<float*>(tile_raw + ((128 - (tma::smem_u32(tile_raw) & 127)) & 127));
+  // ft: [3][kFieldStride] with [kTileX][kTileY][kTileZ] in each; rt: [kTileX][kTileY][kTileZ]
+  float* rt = ft + 3 * kFieldStride;
+  const uint32_t bar = tma::smem_u32(rt + kTileCells);
+  const int n = L.n, tid = threadIdx.x;
+  const int nb = n / kBrickXY;
+  const unsigned b = blockIdx.x;
+  const int by = static_cast<int>(b % nb), bx = static_cast<int>((b / nb) % nb), bz = static_cast<int>(b / nb / nb);
+  const int x0 = bx * kBrickXY, y0 = by * kBrickXY, z0 = bz * kBrickZ;
+  // the slot range, clamped into [0, np] so that any offsets stay in bounds
+  const int64_t s = min(max(int64_t{__ldg(key_start + static_cast<int64_t>(b) * kBrickKeys)}, int64_t{0}), np);
+  const int64_t e = b + 1 < gridDim.x
+                        ? min(max(int64_t{__ldg(key_start + static_cast<int64_t>(b + 1) * kBrickKeys)}, s), np)
+                        : np;
+  const bool tiled = e - s >= kTileMinParticles;
+  // TMA boxes for tiles inside the mesh, row copies for tiles that wrap
+  const bool by_tma = tiled && use_tma && x0 + kTileX <= n && y0 + kTileY <= n && z0 + kTileZ <= n;
+  if (by_tma) {
+    if (tid == 0) {
+      tma::mbar_init(bar, 1);
+      tma::fence_mbar_init();
+      tma::mbar_expect_tx(bar, 3 * kTileCells * sizeof(float));
+      for (int c = 0; c < 3; ++c) tma::load_3d(tma::smem_u32(ft + c * kFieldStride), &maps.m[c], z0, y0, x0, bar);
+    }
+  }
+  if (tiled) {
+    float4* rt4 = reinterpret_cast<float4*>(rt);
+    for (int i = tid; i < kTileCells / 4; i += kTileThreads) rt4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (tiled && !by_tma) {
+    for (int i = tid; i < 3 * kTileX * kTileY * kTileQuads; i += kTileThreads) {
+      const int r = i / kTileQuads, q = i - r * kTileQuads;
+      const int f = r / (kTileX * kTileY), rem = r - f * (kTileX * kTileY);
+      const int dx = rem / kTileY, dy = rem - dx * kTileY;
+      const float* src = f == 0 ? gx : (f == 1 ? gy : gz);
+      const size_t off = static_cast<size_t>(static_cast<unsigned>(tile_wrap(x0 + dx, n) * n + tile_wrap(y0 + dy, n))) * n +
+                         tile_wrap(z0 + 4 * q, n);
+      cp_async16(ft + f * kFieldStride + rem * kTileZ + 4 * q, src + off);
+    }
+  }
+  // a field tile this thread may read (false after a timed-out wait: the thread takes the global path)
+  bool fields_ok = tiled;
+  const float* gf[3] = {gx, gy, gz};
+  for (int64_t base = s; base < e; base += kTileThreads) {
+    const int64_t p = base + tid;
+    const bool act = p < e;
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f;
+    int qi = 0, qj = 0, qk = 0;
+    if (act) {
+      d0 = disp[p];
+      d1 = disp[p + np];
+      d2 = disp[p + 2 * np];
+      m0 = mom[p];
+      m1 = mom[p + np];
+      m2 = mom[p + 2 * np];
+      const unsigned lag = static_cast<unsigned>(__ldg(L.order + p));
+      const unsigned ns = static_cast<unsigned>(L.n_side);
+      qk = static_cast<int>(lag % ns);
+      const unsigned row = lag / ns;
+      qj = static_cast<int>(row % ns);
+      qi = static_cast<int>(row / ns);
+    }
+    if (tiled && base == s) {
+      if (by_tma) {
+        // the mbarrier was initialised by thread 0 before its loads; the barrier below orders every other
+        // thread's first probe after that
+        __syncthreads();
+        if (!tma::mbar_wait(bar, 0)) {
+          fields_ok = false;
+          atomicOr(err, kTileTimeout);
+        }
+      } else {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+      }
+      __syncthreads();
+    }
+    if (act) {
+      int ix, iy, iz;
+      float fx, fy, fz;
+      const int bxl = qi * L.ratio, byl = qj * L.ratio, bzl = qk * L.ratio;
+      cic_axis(bxl, d0 * L.inv_cell, n, ix, fx);
+      cic_axis(byl, d1 * L.inv_cell, n, iy, fy);
+      cic_axis(bzl, d2 * L.inv_cell, n, iz, fz);
+      int ox = ix - x0, oy = iy - y0, oz = iz - z0;
+      ox += ox < 0 ? n : 0;
+      oy += oy < 0 ? n : 0;
+      oz += oz < 0 ? n : 0;
+      float a[3];
+      if (fields_ok && ox < kTileX - 1 && oy < kTileY - 1 && oz < kTileZ - 1) {
+        const float* t = ft + (ox * kTileY + oy) * kTileZ + oz;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float* u = t + c * kFieldStride;
+          a[c] = trilerp(u[0], u[1], u[kTileZ], u[kTileZ + 1], u[kTileY * kTileZ], u[kTileY * kTileZ + 1],
+                         u[kTileY * kTileZ + kTileZ], u[kTileY * kTileZ + kTileZ + 1], fx, fy, fz);
+        }
+      } else {
+        const int jx = wrap_next(ix, n), jy = wrap_next(iy, n), jz = wrap_next(iz, n);
+        const int64_t r00 = static_cast<int64_t>(static_cast<unsigned>(ix * n + iy)) * n;
+        const int64_t r01 = static_cast<int64_t>(static_cast<unsigned>(ix * n + jy)) * n;
+        const int64_t r10 = static_cast<int64_t>(static_cast<unsigned>(jx * n + iy)) * n;
+        const int64_t r11 = static_cast<int64_t>(static_cast<unsigned>(jx * n + jy)) * n;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a[c] = trilinear(gf[c], r00, r01, r10, r11, iz, jz, fx, fy, fz);
+      }
+      m0 -= a[0] * kick;
+      m1 -= a[1] * kick;
+      m2 -= a[2] * kick;
+      mom[p] = m0;
+      mom[p + np] = m1;
+      mom[p + 2 * np] = m2;
+      if (drift != 0.f) {
+        d0 += m0 * drift;
+        d1 += m1 * drift;
+        d2 += m2 * drift;
+        disp[p] = d0;
+        disp[p + np] = d1;
+        disp[p + 2 * np] = d2;
+      }
+      cic_axis(bxl, d0 * L.inv_cell, n, ix, fx);
+      cic_axis(byl, d1 * L.inv_cell, n, iy, fy);
+      cic_axis(bzl, d2 * L.inv_cell, n, iz, fz);
+      ox = ix - x0;
+      oy = iy - y0;
+      oz = iz - z0;
+      ox += ox < 0 ? n : 0;
+      oy += oy < 0 ? n : 0;
+      oz += oz < 0 ? n : 0;
+      if (tiled && ox < kTileX - 1 && oy < kTileY - 1 && oz < kTileZ - 1) {
+        const float wx0 = (1.f - fx) * mass, wx1 = fx * mass;
+        const float wy0 = 1.f - fy, wy1 = fy, wz0 = 1.f - fz, wz1 = fz;
+        float* t = rt + (ox * kTileY + oy) * kTileZ + oz;
+        atomicAdd(t, wx0 * wy0 * wz0);
+        atomicAdd(t + 1, wx0 * wy0 * wz1);
+        atomicAdd(t + kTileZ, wx0 * wy1 * wz0);
+        atomicAdd(t + kTileZ + 1, wx0 * wy1 * wz1);
+        atomicAdd(t + kTileY * kTileZ, wx1 * wy0 * wz0);
+        atomicAdd(t + kTileY * kTileZ + 1, wx1 * wy0 * wz1);
+        atomicAdd(t + kTileY * kTileZ + kTileZ, wx1 * wy1 * wz0);
+        atomicAdd(t + kTileY * kTileZ + kTileZ + 1, wx1 * wy1 * wz1);
+      } else {
+        deposit_cic(rho, n, ix, iy, iz, fx, fy, fz, mass);
+      }
+    }
+  }
+  if (!tiled) return;
+  // a thread whose wait timed out lets the copies land before the block's shared memory goes away (again a
+  // bounded wait)
+  if (by_tma && !fields_ok) tma::mbar_wait(bar, 0);
+  __syncthreads();
+  const float4* rt4 = reinterpret_cast<const float4*>(rt);
+  for (int i = tid; i < kTileCells / 4; i += kTileThreads) {
+    const float4 v = rt4[i];
+    if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) continue;
+    const int r = i / kTileQuads, q = i - r * kTileQuads;
+    const int dx = r / kTileY, dy = r - dx * kTileY;
+    const size_t off = static_cast<size_t>(static_cast<unsigned>(tile_wrap(x0 + dx, n) * n + tile_wrap(y0 + dy, n))) * n +
+                       tile_wrap(z0 + 4 * q, n);
+    atomicAdd(reinterpret_cast<float4*>(rho + off), v);
+  }
+}
+
+// Error word of the stateless calls (a timed-out tile wait changes no result: the block takes the global path).
+__device__ int g_tile_err;
+
+hrt_status launch_kick_drift_tiled(const float* grad, int64_t n, double box, int64_t n_side, float* disp, float* mom,
+                                   double kick, double drift, float* rho_out, const int32_t* order,
+                                   const int32_t* key_start, cudaStream_t s, int mode, int* err) {
+  if (!particle_bricks_ok(n) || !order || !key_start || !rho_out)
+    return fail(HRT_ERR_INVALID_ARG, "the tiled kick-drift-deposit needs brick-sorted particles and a density");
+  const int64_t np = n_side * n_side * n_side;
+  const int64_t m = n * n * n;
+  HRT_CUDA(cudaMemsetAsync(rho_out, 0, static_cast<size_t>(m) * sizeof(float), s));
+  if (np == 0) return HRT_OK;
+  if (!err) HRT_CUDA(cudaGetSymbolAddress(reinterpret_cast<void**>(&err), g_tile_err));
+  FieldMaps maps{};
+  if (mode == kTilesTma) {
+    EncodeTiled enc = nullptr;
+    HRT_TRY(tensor_map_encoder(&enc));
+    const cuuint64_t dims[3] = {static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(n)};
+    const cuuint64_t strides[2] = {static_cast<cuuint64_t>(n) * sizeof(float),
+                                   static_cast<cuuint64_t>(n) * n * sizeof(float)};
+    const cuuint32_t tbox[3] = {kTileZ, kTileY, kTileX};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    for (int c = 0; c < 3; ++c) {
+      const CUresult r = enc(&maps.m[c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(grad + c * m), dims,
+                             strides, tbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return fail(HRT_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+    }
+  }
+  HRT_CUDA(cudaFuncSetAttribute(kick_drift_tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kTileSmem)));
+  const Lattice L = make_lattice(n_side, n, box, order);
+  const unsigned bricks = static_cast<unsigned>(m / (kBrickXY * kBrickXY * kBrickZ));
+  kick_drift_tiled_kernel<<<bricks, kTileThreads, kTileSmem, s>>>(
+      maps, mode == kTilesTma ? 1 : 0, grad, grad + m, grad + 2 * m, L, np, key_start, disp, mom,
+      static_cast<float>(kick), static_cast<float>(drift), particle_mass(n_side, n), rho_out, err);
+  HRT_LAUNCHED("kick_drift_tiled_kernel");
+  return HRT_OK;
 }
 
 hrt_status launch_kick_drift(const float* grad, int64_t n, double box, int64_t n_side, float* disp, float* mom,

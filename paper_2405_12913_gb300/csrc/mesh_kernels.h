@@ -17,13 +17,22 @@ hrt_status launch_cic_scatter_warp(const float* disp, int64_t n_side, int64_t n,
 hrt_status launch_cic_scatter(const float* disp, int64_t n_side, int64_t n, double box, float* rho,
                               cudaStream_t s, const int32_t* order = nullptr);
 
-// Counting sort of the particles by z-row segments of 32 mesh cells (row-major): slot i of the output holds the
-// particle that the key order puts there; disp, mom are [3][np] in slot order, order the slot -> lattice index
-// map (nullptr: lattice order, read in the rows-of-sites order).  Writes disp_out, mom_out, order_out; counts
-// (particle_sort_counts(n) ints) and keys, ranks, src (np ints each) are scratch.
+// Bricks of the cell order: 8 x 8 x 32 cells, 64 sort keys (z-row segments) each.
+constexpr int kBrickXY = 8;
+constexpr int kBrickZ = 32;
+constexpr int kBrickKeys = kBrickXY * kBrickXY;
+// Mesh sides whose particles are sorted into bricks (a multiple of 32, at most 1024).
+inline bool particle_bricks_ok(int64_t n) { return n >= kBrickZ && n <= 1024 && n % kBrickZ == 0; }
+
+// Counting sort of the particles by z-row segments of 32 mesh cells, grouped into bricks if `bricks` and
+// particle_bricks_ok(n), row-major otherwise: slot i of the output holds the particle that the key order puts
+// there; disp, mom are [3][np] in slot order, order the slot -> lattice index map (nullptr: lattice order, read in
+// the rows-of-sites order).  Writes disp_out, mom_out, order_out; counts (particle_sort_counts(n) ints) ends as
+// the exclusive scan of the key counts (the first slot of every key); keys, ranks, src (np ints each) are
+// scratch.
 hrt_status launch_particle_sort(const float* disp, const float* mom, const int32_t* order, int64_t n_side, int64_t n,
                                 double box, float* disp_out, float* mom_out, int32_t* order_out, int32_t* counts,
-                                int32_t* keys, int32_t* ranks, int32_t* src, cudaStream_t s);
+                                int32_t* keys, int32_t* ranks, int32_t* src, cudaStream_t s, bool bricks);
 // Size (ints) of the counts scratch of launch_particle_sort for mesh side n.
 int64_t particle_sort_counts(int64_t n);
 // Slot order back to lattice order: out[:, order[i]] = in[:, i] for [3][np] arrays.
@@ -44,6 +53,19 @@ hrt_status launch_set_callback_info(KspaceCallbackInfo* dst, const KspaceCallbac
 hrt_status launch_kick_drift(const float* grad, int64_t n, double box, int64_t n_side, float* disp, float* mom,
                              double kick, double drift, cudaStream_t s, float* rho_out = nullptr,
                              const int32_t* order = nullptr);
+// The kick-drift-deposit on brick-sorted particles (particle_bricks_ok(n)): one block per brick, slots
+// [key_start[64 b], key_start[64 b + 64]) (np after the last brick), with the brick's field tile and density tile
+// in shared memory.  Any slot ranges give the same result; particles outside their block's tile take the
+// global path.
+// mode: kTilesTma (TMA boxes for tiles inside the mesh, row copies for the wrapping ones) or kTilesRows (row
+// copies for all).  err (nullptr: a module-level word) receives kTileTimeout if a wait for a TMA box timed out.
+constexpr int kTilesRows = 1;
+constexpr int kTilesTma = 2;
+constexpr int kTileTimeout = 2;
+hrt_status launch_kick_drift_tiled(const float* grad, int64_t n, double box, int64_t n_side, float* disp, float* mom,
+                                   double kick, double drift, float* rho_out, const int32_t* order,
+                                   const int32_t* key_start, cudaStream_t s, int mode = kTilesTma,
+                                   int* err = nullptr);
 
 hrt_status launch_ic_kspace(const void* w_hat, int64_t n, double box, const float* table, void* out,
                             cudaStream_t s);

@@ -1,13 +1,17 @@
-// Counting sort of the particles by mesh cell (z-row segments of 32 cells, row-major), so that a warp's
-// particles gather from and deposit into neighbouring cells also after clustering has scattered lattice
-// neighbours over many lines.  The particles keep their Lagrangian displacements; a slot -> lattice index map
-// (order) says which lattice site each storage slot holds.
+// Counting sort of the particles by mesh cell, so that a block's particles gather from and deposit into
+// neighbouring cells also after clustering has scattered lattice neighbours over many lines.  The particles keep
+// their Lagrangian displacements; a slot -> lattice index map (order) says which lattice site each storage slot
+// holds.
 //
-// key(i) = (ix n + iy) ceil(n / 32) + iz / 32 of the cell the particle in slot i sits in; its rank within the
-// key comes from an atomic counter, the key offsets from an exclusive scan of the counters (three passes: block
-// sums, one-block scan of the block sums, block scans plus offsets).  Each destination offset + rank then learns
-// its source slot, and a gather moves displacements, momenta and the lattice index there (coalesced writes).
-// The order within a key depends on the atomics.
+// Keys are z-row segments of 32 cells.  Row order (the default): key = (ix n + iy) ceil(n / 32) + iz / 32.
+// Brick order (asked for by the tiled kick-drift-deposit, mesh sides that particle_bricks_ok accepts): the mesh
+// is cut into bricks of 8 x 8 x 32 cells, walked with bz slowest, then bx, then by, and a brick's 64 keys are
+// its (x, y) rows, key = brick * 64 + 8 (ix mod 8) + (iy mod 8); after the sort the particles of brick b occupy
+// the slots [offset(64 b), offset(64 b + 64)), which the tiled kick-drift-deposit takes as its block's range.  A particle's rank within its key comes from an
+// atomic counter, the key offsets from an exclusive scan of the counters (three passes: block sums, one-block
+// scan of the block sums, block scans plus offsets).  Each destination offset + rank then learns its source
+// slot, and a gather moves displacements, momenta and the lattice index there (coalesced writes).  The order
+// within a key depends on the atomics.
 #include <cuda_runtime.h>
 
 #include "common.h"
@@ -31,8 +35,8 @@ __device__ __forceinline__ int cell_of(int q_node, float d_cells, int n) {
 }
 
 __global__ void sort_key_kernel(const float* __restrict__ disp, const int32_t* __restrict__ order, int64_t np,
-                                int n_side, int ratio, int n, int nseg, float inv_cell, int32_t* __restrict__ counts,
-                                int32_t* __restrict__ keys, int32_t* __restrict__ ranks) {
+                                int n_side, int ratio, int n, int nseg, int bricks, float inv_cell,
+                                int32_t* __restrict__ counts, int32_t* __restrict__ keys, int32_t* __restrict__ ranks) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= np) return;
   const unsigned lag = order ? static_cast<unsigned>(__ldg(order + i)) : static_cast<unsigned>(i);
@@ -41,7 +45,14 @@ __global__ void sort_key_kernel(const float* __restrict__ disp, const int32_t* _
   const int ix = cell_of(qi * ratio, __ldg(disp + i) * inv_cell, n);
   const int iy = cell_of(qj * ratio, __ldg(disp + np + i) * inv_cell, n);
   const int iz = cell_of(qk * ratio, __ldg(disp + 2 * np + i) * inv_cell, n);
-  const int32_t key = (ix * n + iy) * nseg + iz / kSeg;
+  int32_t key;
+  if (bricks) {
+    const int nb = n / kBrickXY;
+    key = (((iz / kSeg) * nb + ix / kBrickXY) * nb + iy / kBrickXY) * kBrickKeys + (ix % kBrickXY) * kBrickXY +
+          iy % kBrickXY;
+  } else {
+    key = (ix * n + iy) * nseg + iz / kSeg;
+  }
   keys[i] = key;
   ranks[i] = atomicAdd(counts + key, 1);
 }
@@ -153,7 +164,7 @@ __global__ void unsort_kernel(const float* __restrict__ in, const int32_t* __res
 
 hrt_status launch_particle_sort(const float* disp, const float* mom, const int32_t* order, int64_t n_side, int64_t n,
                                 double box, float* disp_out, float* mom_out, int32_t* order_out, int32_t* counts,
-                                int32_t* keys, int32_t* ranks, int32_t* src, cudaStream_t s) {
+                                int32_t* keys, int32_t* ranks, int32_t* src, cudaStream_t s, bool bricks) {
   const int64_t np = n_side * n_side * n_side;
   if (np == 0) return HRT_OK;
   if (np > INT32_MAX) return fail(HRT_ERR_INVALID_ARG, "too many particles for the sort");
@@ -164,7 +175,8 @@ hrt_status launch_particle_sort(const float* disp, const float* mom, const int32
   HRT_CUDA(cudaMemsetAsync(counts, 0, static_cast<size_t>(T) * sizeof(int32_t), s));
   sort_key_kernel<<<blocks_for(np, 256), 256, 0, s>>>(disp, order, np, static_cast<int>(n_side),
                                                       static_cast<int>(n / n_side), static_cast<int>(n), nseg,
-                                                      static_cast<float>(n / box), counts, keys, ranks);
+                                                      bricks && particle_bricks_ok(n) ? 1 : 0, static_cast<float>(n / box),
+                                                      counts, keys, ranks);
   HRT_LAUNCHED("sort_key_kernel");
   int32_t* sums = counts + T;
   scan_sums_kernel<<<static_cast<unsigned>(nb), kScanThreads, 0, s>>>(counts, T, sums);

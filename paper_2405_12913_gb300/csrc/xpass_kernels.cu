@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "common.h"
+#include "tma.h"
 #include "xpass.h"
 
 namespace hrt {
@@ -44,10 +45,8 @@ namespace {
 constexpr int kXWarps = 8;
 constexpr int kXThreads = kXWarps * 32;
 constexpr int kTileBytes = 64 * 1024;  // TK pencils x n rows x 8 bytes, for every supported n
-// Bounded waits: each mbarrier probe may suspend the thread for up to kWaitHintNs; after kWaitTries probes
-// (about a second) the kernel records kXpassTimeout and returns.
-constexpr uint32_t kWaitHintNs = 20000;
-constexpr int kWaitTries = 1 << 16;
+// Bounded waits (tma::mbar_wait): after about a second the kernel records kXpassTimeout and returns.
+using namespace tma;
 
 __host__ __device__ constexpr int bit_reverse(int i, int bits) {
   int r = 0;
@@ -137,52 +136,6 @@ struct DftPencils<R1, INV, 0> {
 };
 
 // ---- shared memory, mbarriers and TMA (inline PTX) -------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-// True once the barrier's phase with the given parity has completed; false after the bounded number of probes.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int i = 0; i < kWaitTries; ++i) {
-    uint32_t ok = 0;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity), "r"(kWaitHintNs)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, uint32_t src, int c0, int c1, int c2) {
-  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];\n"
-               ::"l"(reinterpret_cast<uint64_t>(map)), "r"(src), "r"(c0), "r"(c1), "r"(c2)
-               : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
-// Waits until every committed store group has finished reading its shared-memory source.
-__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
-// Waits until every committed store group has completed.
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
-// Orders this thread's generic shared-memory writes before later TMA (async-proxy) accesses.
-__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
 // ---- tile geometry ----------------------------------------------------------------------------------------
 // TK = 8P pencils per tile; the tile is stored as NSUB sub-tiles of SUBW columns (rows of PITCH = 8 SUBW bytes,
@@ -325,7 +278,7 @@ __global__ void __launch_bounds__(kXThreads, 1)
   if (tid == 0) {
     mbar_init(bar0, 1);
     mbar_init(bar1, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    fence_mbar_init();
   }
   __syncthreads();
 
@@ -336,7 +289,7 @@ __global__ void __launch_bounds__(kXThreads, 1)
     for (int s = 0; s < G::NSUB; ++s)
 #pragma unroll
       for (int bx = 0; bx < G::BOXES; ++bx)
-        tma_load_2d(dst + s * G::SUB_BYTES + bx * G::ROWS_PER_BOX * G::PITCH, &in_map,
+        load_2d(dst + s * G::SUB_BYTES + bx * G::ROWS_PER_BOX * G::PITCH, &in_map,
                     2 * (t * TK + s * G::SUBW), bx * G::ROWS_PER_BOX, bar);
   };
   // one thread stores the staged tile at src as component comp of the set's output spectra
@@ -345,7 +298,7 @@ __global__ void __launch_bounds__(kXThreads, 1)
     for (int s = 0; s < G::NSUB; ++s)
 #pragma unroll
       for (int bx = 0; bx < G::BOXES; ++bx)
-        tma_store_3d(map, src + s * G::SUB_BYTES + bx * G::ROWS_PER_BOX * G::PITCH, 2 * (t * TK + s * G::SUBW),
+        store_3d(map, src + s * G::SUB_BYTES + bx * G::ROWS_PER_BOX * G::PITCH, 2 * (t * TK + s * G::SUBW),
                      bx * G::ROWS_PER_BOX, comp);
   };
 
@@ -496,9 +449,9 @@ __global__ void __launch_bounds__(kXThreads, 1)
   }
 }
 
-using EncodeTiled = PFN_cuTensorMapEncodeTiled_v12000;
+}  // namespace
 
-hrt_status encoder(EncodeTiled* out) {
+hrt_status tensor_map_encoder(EncodeTiled* out) {
   static std::once_flag once;
   static EncodeTiled fn = nullptr;
   static cudaError_t e = cudaSuccess;
@@ -513,13 +466,15 @@ hrt_status encoder(EncodeTiled* out) {
   return HRT_OK;
 }
 
+namespace {
+
 // Tensor map over the [comp][x][flat pencil] spectra: rank 2 (one spectrum) or 3; boxes of (2 SUBW floats) x
 // (rows per box) x 1.
 template <int R1>
 hrt_status make_map(CUtensorMap* map, const void* base, int n, int comps) {
   using G = Geo<R1>;
   EncodeTiled enc = nullptr;
-  HRT_TRY(encoder(&enc));
+  HRT_TRY(tensor_map_encoder(&enc));
   const uint64_t flat = static_cast<uint64_t>(n) * (n / 2 + 1);
   const cuuint64_t dims[3] = {2 * flat, static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(comps)};
   const cuuint64_t strides[2] = {flat * sizeof(float2), flat * sizeof(float2) * n};

@@ -74,6 +74,7 @@ _SIGS = {
     "hrt_cic_scatter_warp_aggregated": ([_P, _I64, _I64, _D, _P, _P], C.c_int),
     "hrt_particle_kick_drift": ([_P, _I64, _D, _I64, _P, _P, _D, _D, _P], C.c_int),
     "hrt_particle_kick_drift_deposit": ([_P, _I64, _D, _I64, _P, _P, _D, _D, _P, _P], C.c_int),
+    "hrt_particle_kick_drift_deposit_bricks": ([_P, _I64, _D, _I64, _P, _P, _P, _P, _D, _D, _P, _P], C.c_int),
     "hrt_kspace_gradient": ([_P, _I64, _D, _D, _P, _I32, _P, _P, _I32, _P, _P], C.c_int),
     "hrt_kspace_gradient_noalloc": ([_P, _I64, _D, _D, _P, _I32, _P, _P, _I32, _P, _P], C.c_int),
     "hrt_pm_create": ([_I64, _D, _I32, _P, _P], C.c_int),
@@ -101,6 +102,7 @@ _SIGS = {
     "hrt_set_ray_mesh": ([_P, _P], C.c_int),
     "hrt_set_checkpointing": ([_P, _I32], C.c_int),
     "hrt_set_particle_sort": ([_P, _I32], C.c_int),
+    "hrt_set_tiled_deposit": ([_P, _I32], C.c_int),
     "hrt_adjoint": ([_P, _P, _P, _P, _P], C.c_int),
     "hrt_ray_drift_free": ([_P, _D, _D, _P], C.c_int),
     "hrt_ray_readout": ([_P, _P, _P], C.c_int),
@@ -300,6 +302,15 @@ def hrt_particle_kick_drift_deposit(grad: torch.Tensor, n: int, box: float, n_si
                                                 _ptr(disp, torch.float32, "disp"), _ptr(mom, torch.float32, "mom"),
                                                 kick, drift, _ptr(rho, torch.float32, "rho"), _stream(stream)),
            "hrt_particle_kick_drift_deposit")
+
+
+def hrt_particle_kick_drift_deposit_bricks(grad: torch.Tensor, n: int, box: float, n_side: int, disp: torch.Tensor,
+                                           mom: torch.Tensor, order: torch.Tensor, key_start: torch.Tensor,
+                                           kick: float, drift: float, rho: torch.Tensor, stream=None):
+    _check(_lib.hrt_particle_kick_drift_deposit_bricks(
+        _ptr(grad, torch.float32, "grad"), n, box, n_side, _ptr(disp, torch.float32, "disp"),
+        _ptr(mom, torch.float32, "mom"), _ptr(order, torch.int32, "order"), _ptr(key_start, torch.int32, "key_start"),
+        kick, drift, _ptr(rho, torch.float32, "rho"), _stream(stream)), "hrt_particle_kick_drift_deposit_bricks")
 
 
 def hrt_kspace_gradient(rho_hat: torch.Tensor, n: int, box: float, pref: float, f: hrt_filter, n_out: int,
@@ -833,6 +844,11 @@ class Context:
     def hrt_set_particle_sort(self, every: int):
         """Re-sort the particles by mesh cell every `every` particle steps (0: keep lattice order)."""
         _check(_lib.hrt_set_particle_sort(self._h, every), "hrt_set_particle_sort")
+
+    def hrt_set_tiled_deposit(self, mode: int):
+        """Kick-drift-deposit: 0 per-particle gathers and reductions (the default), 2 shared-memory tiles by TMA on
+        brick-sorted particles, 1 tiles by row copies."""
+        _check(_lib.hrt_set_tiled_deposit(self._h, int(mode)), "hrt_set_tiled_deposit")
 
     def hrt_set_checkpointing(self, every: int):
         """Record the run from the next Zel'dovich ICs for hrt_adjoint (checkpoint every `every` steps; 0: off)."""
