@@ -193,7 +193,9 @@ def algorithmic_bytes(W):
     rays = W.n_rays
     return {
         "cic_scatter": 3 * 4 * npart + mesh,                 # positions read + density written
-        "kspace": spec + 3 * spec,                           # density spectrum read + 3 gradient spectra written
+        # density spectrum read + 3 gradient spectra written; on the split path (mesh sides 256, 512, 1024) the
+        # x-pass also zeroes the consumed density for the next deposit
+        "kspace": spec + 3 * spec + (mesh if W.n_mesh in (256, 512, 1024) else 0),
         "kick_drift": 4 * mesh + 2 * 2 * 3 * 4 * npart,      # 3 fields read, density written, disp/mom r+w
         "ray_step": 2 * rays * (16 + 8 + 16 + 16),           # ray state read and written (slab reads extra)
         "fft_r2c": mesh + spec,

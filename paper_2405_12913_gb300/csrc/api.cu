@@ -498,10 +498,12 @@ static KspaceCallbackInfo callback_info(const hrt_pm* pm, const float* tab, cons
 }
 
 // before_fields (optional): an event the stream waits for before the C2Rs overwrite grad / ray_grad (work on
-// another stream that still reads the previous fields).
+// another stream that still reads the previous fields).  clear_rho: on the split path the x-pass sets rho to
+// zero once the 2D R2C has consumed it (*cleared tells whether it did), which spares the next deposit its memset.
 static hrt_status pm_solve(hrt_pm* pm, float* rho, double pref, const hrt_filter* f, float* grad,
                            const hrt_filter* fr, float* ray_grad, hrt_ctx* prof = nullptr,
-                           cudaEvent_t before_fields = nullptr) {
+                           cudaEvent_t before_fields = nullptr, bool* cleared = nullptr) {
+  if (cleared) *cleared = false;
   static hrt_ctx no_profiling;
   hrt_ctx* pc = prof ? prof : &no_profiling;
   HRT_TRY(check_filter(f));
@@ -533,7 +535,9 @@ static hrt_status pm_solve(hrt_pm* pm, float* rho, double pref, const hrt_filter
     const XpassSet xb = rays ? set(pm->tab_b, *fr, pm->n_ray, gh + 3 * sp) : XpassSet{};
     {
       PhaseScope ps(pc, 4);
-      HRT_TRY(launch_xpass(pm->rho_hat, n, pm->box, pref, pm->xtw, xa, xb, pm->xerr, pm->stream));
+      HRT_TRY(launch_xpass(pm->rho_hat, n, pm->box, pref, pm->xtw, xa, xb, pm->xerr, pm->stream,
+                           cleared ? rho : nullptr, cleared ? n * n * n : 0));
+      if (cleared) *cleared = true;
     }
     if (before_fields) HRT_CUDA(cudaStreamWaitEvent(pm->stream, before_fields, 0));
     PhaseScope ps(pc, 5);
@@ -764,7 +768,9 @@ static hrt_status ctx_solve(hrt_ctx* ctx) {
   cudaEvent_t wait = ctx->rays_pending ? ctx->ev_rays : nullptr;
   ctx->rays_pending = false;
   ctx->force_valid = false;
-  HRT_TRY(pm_solve(ctx->pm, ctx->rho, ctx_pref(ctx, ctx->a), &f, ctx->grad, &fr, ctx->ray_grad, ctx, wait));
+  ctx->rho_clear = false;
+  HRT_TRY(pm_solve(ctx->pm, ctx->rho, ctx_pref(ctx, ctx->a), &f, ctx->grad, &fr, ctx->ray_grad, ctx, wait,
+                   &ctx->rho_clear));
   ctx->force_valid = true;
   return HRT_OK;
 }
@@ -1819,10 +1825,11 @@ hrt_status hrt::ctx_step(hrt_ctx* ctx, double a_next, int32_t source, double wei
     if (ctx->tiled_deposit != 0 && ctx->order_cur >= 0 && ctx->sort_bricks)
       s = launch_kick_drift_tiled(ctx->grad, ctx->cfg.n_mesh, ctx->cfg.box, ctx->cfg.n_side, ctx->disp, ctx->mom,
                                   kick, drift, ctx->rho, ctx_order(ctx), ctx->sort_scratch, ctx->stream,
-                                  ctx->tiled_deposit, ctx->pm ? ctx->pm->xerr : nullptr);
+                                  ctx->tiled_deposit, ctx->pm ? ctx->pm->xerr : nullptr, ctx->rho_clear);
     else
       s = launch_kick_drift(ctx->grad, ctx->cfg.n_mesh, ctx->cfg.box, ctx->cfg.n_side, ctx->disp, ctx->mom, kick,
-                            drift, ctx->stream, ctx->rho, ctx_order(ctx));
+                            drift, ctx->stream, ctx->rho, ctx_order(ctx), ctx->rho_clear);
+    ctx->rho_clear = false;
   }
   if (s != HRT_OK) return ctx_mark(ctx, s);
   ctx->a = a_next;

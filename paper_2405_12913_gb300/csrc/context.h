@@ -100,6 +100,8 @@ struct hrt_ctx {
   int32_t* sort_scratch = nullptr;
   int32_t sort_every = 0;
   int32_t steps_since_sort = 0;
+  // rho was set to zero by the last solve (split path): the next deposit needs no memset
+  bool rho_clear = false;
   // the sort of the current order used brick keys; the next step sorts whatever the interval (evolved particles)
   bool sort_bricks = false;
   bool sort_first = false;

@@ -679,12 +679,12 @@ __device__ int g_tile_err;
 
 hrt_status launch_kick_drift_tiled(const float* grad, int64_t n, double box, int64_t n_side, float* disp, float* mom,
                                    double kick, double drift, float* rho_out, const int32_t* order,
-                                   const int32_t* key_start, cudaStream_t s, int mode, int* err) {
+                                   const int32_t* key_start, cudaStream_t s, int mode, int* err, bool rho_zeroed) {
   if (!particle_bricks_ok(n) || !order || !key_start || !rho_out)
     return fail(HRT_ERR_INVALID_ARG, "the tiled kick-drift-deposit needs brick-sorted particles and a density");
   const int64_t np = n_side * n_side * n_side;
   const int64_t m = n * n * n;
-  HRT_CUDA(cudaMemsetAsync(rho_out, 0, static_cast<size_t>(m) * sizeof(float), s));
+  if (!rho_zeroed) HRT_CUDA(cudaMemsetAsync(rho_out, 0, static_cast<size_t>(m) * sizeof(float), s));
   if (np == 0) return HRT_OK;
   if (!err) HRT_CUDA(cudaGetSymbolAddress(reinterpret_cast<void**>(&err), g_tile_err));
   FieldMaps maps{};
@@ -715,10 +715,11 @@ hrt_status launch_kick_drift_tiled(const float* grad, int64_t n, double box, int
 }
 
 hrt_status launch_kick_drift(const float* grad, int64_t n, double box, int64_t n_side, float* disp, float* mom,
-                             double kick, double drift, cudaStream_t s, float* rho_out, const int32_t* order) {
+                             double kick, double drift, cudaStream_t s, float* rho_out, const int32_t* order,
+                             bool rho_zeroed) {
   int64_t np = n_side * n_side * n_side;
   int64_t m = n * n * n;
-  if (rho_out) HRT_CUDA(cudaMemsetAsync(rho_out, 0, static_cast<size_t>(m) * sizeof(float), s));
+  if (rho_out && !rho_zeroed) HRT_CUDA(cudaMemsetAsync(rho_out, 0, static_cast<size_t>(m) * sizeof(float), s));
   if (np == 0) return HRT_OK;
   const Lattice L = make_lattice(n_side, n, box, order);
   const dim3 grid = particle_grid(n_side, 256, order);

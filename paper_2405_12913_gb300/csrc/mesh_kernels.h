@@ -50,9 +50,10 @@ struct KspaceCallbackInfo;
 // Writes the caller info of the k-space load callback in stream order (kernel argument, no host wait).
 hrt_status launch_set_callback_info(KspaceCallbackInfo* dst, const KspaceCallbackInfo& v, cudaStream_t s);
 
+// rho_zeroed: rho_out is already zero (no memset before the deposit).
 hrt_status launch_kick_drift(const float* grad, int64_t n, double box, int64_t n_side, float* disp, float* mom,
                              double kick, double drift, cudaStream_t s, float* rho_out = nullptr,
-                             const int32_t* order = nullptr);
+                             const int32_t* order = nullptr, bool rho_zeroed = false);
 // The kick-drift-deposit on brick-sorted particles (particle_bricks_ok(n)): one block per brick, slots
 // [key_start[64 b], key_start[64 b + 64]) (np after the last brick), with the brick's field tile and density tile
 // in shared memory.  Any slot ranges give the same result; particles outside their block's tile take the
@@ -65,7 +66,7 @@ constexpr int kTileTimeout = 2;
 hrt_status launch_kick_drift_tiled(const float* grad, int64_t n, double box, int64_t n_side, float* disp, float* mom,
                                    double kick, double drift, float* rho_out, const int32_t* order,
                                    const int32_t* key_start, cudaStream_t s, int mode = kTilesTma,
-                                   int* err = nullptr);
+                                   int* err = nullptr, bool rho_zeroed = false);
 
 hrt_status launch_ic_kspace(const void* w_hat, int64_t n, double box, const float* table, void* out,
                             cudaStream_t s);

@@ -37,8 +37,10 @@ constexpr int kXpassTimeout = 1;
 size_t xpass_smem_bytes(int64_t n);
 // in: the (y, z)-transformed density [x][ky][xpass_row(n)] (16-byte aligned, as are the outputs); tw: device copy
 // of xpass_twiddles(n); err: device error word (kXpassTimeout is OR-ed into it).  Set a has 2 or 3 outputs, set
-// b none (n_out 0), 2 or 3.
+// b none (n_out 0), 2 or 3.  clear (or nullptr): a buffer of clear_floats floats (16-byte aligned, a multiple of
+// 4) that nothing reads or writes during the pass, set to zero by it.
 hrt_status launch_xpass(const void* in, int64_t n, double box, double pref, const float2* tw, const XpassSet& a,
-                        const XpassSet& b, int* err, cudaStream_t s);
+                        const XpassSet& b, int* err, cudaStream_t s, float* clear = nullptr,
+                        int64_t clear_floats = 0);
 
 }  // namespace hrt

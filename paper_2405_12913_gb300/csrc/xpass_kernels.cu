@@ -253,7 +253,8 @@ template <int R1, bool TWO>
 __global__ void __launch_bounds__(kXThreads, 1)
     xpass_kernel(const __grid_constant__ CUtensorMap in_map, const __grid_constant__ CUtensorMap out_a,
                  const __grid_constant__ CUtensorMap out_b, int nzc, int n_tiles, float kf, float scale,
-                 const float2* __restrict__ tw, XpassSet a, XpassSet b, int* __restrict__ err) {
+                 const float2* __restrict__ tw, XpassSet a, XpassSet b, int* __restrict__ err,
+                 float4* __restrict__ clear, int64_t clear_n4, int64_t clear_per) {
   using G = Geo<R1>;
   constexpr int P = G::P, N = G::N, TK = G::TK;
   extern __shared__ unsigned char smem_raw[];
@@ -319,6 +320,14 @@ __global__ void __launch_bounds__(kXThreads, 1)
   int k = 0;
   bool ok = true;
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++k) {
+    if (clear) {
+      // this tile's slice of a dead buffer (the density the 2D R2C has consumed), zeroed for the next deposit
+      // while the tile's copy is in flight: plain 16-byte stores of consecutive addresses, which the pass's
+      // spare DRAM bandwidth absorbs
+      const int64_t lo = static_cast<int64_t>(tile) * clear_per;
+      const int64_t hi = lo + clear_per < clear_n4 ? lo + clear_per : clear_n4;
+      for (int64_t i = lo + tid; i < hi; i += kXThreads) clear[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     const int cb = k & 1;
     unsigned char* const ib = cb ? ibuf1 : ibuf0;
     const uint32_t ibs = cb ? ib1 : ib0;
@@ -519,7 +528,8 @@ size_t xpass_smem_bytes(int64_t n) {
 
 template <int R1, bool TWO>
 static hrt_status launch_r1(const void* in, int64_t n, double box, double pref, const float2* tw,
-                            const XpassSet& a, const XpassSet& b, int* err, cudaStream_t s) {
+                            const XpassSet& a, const XpassSet& b, int* err, float* clear, int64_t clear_floats,
+                            cudaStream_t s) {
   using G = Geo<R1>;
   const int nzc = static_cast<int>(n / 2 + 1);
   const int64_t flat = n * nzc;
@@ -528,6 +538,8 @@ static hrt_status launch_r1(const void* in, int64_t n, double box, double pref, 
     if (x->n_out > 0 && (reinterpret_cast<uintptr_t>(x->out) & 15) != 0)
       return fail(HRT_ERR_INVALID_ARG, "x-pass: output spectra must be 16-byte aligned");
   if ((reinterpret_cast<uintptr_t>(in) & 15) != 0) return fail(HRT_ERR_INVALID_ARG, "x-pass: input must be 16-byte aligned");
+  if (clear && ((reinterpret_cast<uintptr_t>(clear) & 15) != 0 || clear_floats % 4 != 0 || clear_floats < 0))
+    return fail(HRT_ERR_INVALID_ARG, "x-pass: the buffer to clear must be 16-byte aligned, a multiple of 4 floats");
   CUtensorMap in_map, map_a, map_b;
   HRT_TRY(make_map<R1>(&in_map, in, static_cast<int>(n), 0));
   HRT_TRY(make_map<R1>(&map_a, a.out, static_cast<int>(n), a.n_out));
@@ -542,23 +554,31 @@ static hrt_status launch_r1(const void* in, int64_t n, double box, double pref, 
   const int tiles = static_cast<int>(flat / G::TK);
   const int grid = std::min(tiles, sms);
   const double scale = -pref / (static_cast<double>(n) * n * n);
+  const int64_t n4 = clear ? clear_floats / 4 : 0;
   xpass_kernel<R1, TWO><<<grid, kXThreads, smem, s>>>(in_map, map_a, map_b, nzc, tiles,
                                                       static_cast<float>(2.0 * M_PI / box), static_cast<float>(scale),
-                                                      tw, a, b, err);
+                                                      tw, a, b, err, n4 ? reinterpret_cast<float4*>(clear) : nullptr,
+                                                      n4, (n4 + tiles - 1) / tiles);
   HRT_LAUNCHED("xpass_kernel");
   return HRT_OK;
 }
 
 hrt_status launch_xpass(const void* in, int64_t n, double box, double pref, const float2* tw, const XpassSet& a,
-                        const XpassSet& b, int* err, cudaStream_t s) {
+                        const XpassSet& b, int* err, cudaStream_t s, float* clear, int64_t clear_floats) {
   // every set has the x and y components (and z when n_out is 3): the x-pass stores V as d_y V [and d_z V]
   if (a.n_out < 2 || a.n_out > 3 || b.n_out == 1 || b.n_out < 0 || b.n_out > 3 || !err)
     return fail(HRT_ERR_INVALID_ARG, "x-pass: bad output sets");
   const bool two = b.n_out > 0;
   switch (n) {
-    case 256: return two ? launch_r1<8, true>(in, n, box, pref, tw, a, b, err, s) : launch_r1<8, false>(in, n, box, pref, tw, a, b, err, s);
-    case 512: return two ? launch_r1<16, true>(in, n, box, pref, tw, a, b, err, s) : launch_r1<16, false>(in, n, box, pref, tw, a, b, err, s);
-    case 1024: return two ? launch_r1<32, true>(in, n, box, pref, tw, a, b, err, s) : launch_r1<32, false>(in, n, box, pref, tw, a, b, err, s);
+    case 256:
+      return two ? launch_r1<8, true>(in, n, box, pref, tw, a, b, err, clear, clear_floats, s)
+                 : launch_r1<8, false>(in, n, box, pref, tw, a, b, err, clear, clear_floats, s);
+    case 512:
+      return two ? launch_r1<16, true>(in, n, box, pref, tw, a, b, err, clear, clear_floats, s)
+                 : launch_r1<16, false>(in, n, box, pref, tw, a, b, err, clear, clear_floats, s);
+    case 1024:
+      return two ? launch_r1<32, true>(in, n, box, pref, tw, a, b, err, clear, clear_floats, s)
+                 : launch_r1<32, false>(in, n, box, pref, tw, a, b, err, clear, clear_floats, s);
     default: return fail(HRT_ERR_INVALID_ARG, "x-pass needs a mesh side of 256, 512 or 1024");
   }
 }
