@@ -252,15 +252,15 @@ def run_gpu(args, W, world, rank, local):
         ctx.hrt_set_ray_mesh(raymesh_config(hrt, W))
         ray_launches = 5
 
-    # the context sorts particles given by the caller at their first step, then every sort_every particle steps
-    # (6 own launches: cell keys, three scan passes, inversion, gather)
+    # the context sorts particles given by the caller before their first force, then every sort_every particle
+    # steps (6 own launches: cell keys, three scan passes, inversion, gather)
     sort_every = 4 if args.sort_every is None else args.sort_every
     since_sort = [0]
 
     def reset():
         ctx.hrt_init_particles(disp0, mom0, 1.0)
         ctx.hrt_init_rays(theta0)
-        since_sort[0] = sort_every - 1 if sort_every > 0 else 0
+        since_sort[0] = 0
 
     reset.state = (disp0, mom0, theta0)
 
@@ -271,7 +271,7 @@ def run_gpu(args, W, world, rank, local):
         for _ in range(k):
             if pos == len(grid) - 1:
                 reset()
-                launches += 3  # CIC scatter, k-space pass, ray initialisation
+                launches += 3 + (6 if sort_every > 0 else 0)  # sort, CIC scatter, k-space pass, ray initialisation
                 pos = 0
             n = pos + 1
             ctx.hrt_step(grid[n], slots.get(n, -1))
@@ -569,13 +569,15 @@ def adjoint_timing(hrt, seed):
 # ----------------------------------------------------------------------------------------------- learned form
 LEARNED_256 = os.path.join(ROOT, "paper_2405_12913_gb300", "data", "ray_correction_256m.npy")
 LEARNED_256_512 = os.path.join(ROOT, "paper_2405_12913_gb300", "data", "ray_correction_256m_512m.npy")
+LEARNED_PARTICLE = os.path.join(ROOT, "paper_2405_12913_gb300", "data", "particle_correction_256m_512m.npy")
 
 
 def learned_comparison(seeds=(100, 101, 102, 103)):
     """The learned ray-force correction against the plain kernel on the four held-out seeds of the coarse/fine pair
     workload (256^3 particles, box 256 Mpc/h, 4096^2 rays over 3.5 deg, source z = 1): the plain form on 256^3,
     512^3 and 768^3 meshes, the network trained on 256^3 pairs on the 256^3 mesh and the network trained on
-    256^3 and 512^3 pairs on the 512^3 mesh, each against the plain 1024^3 run of the same seed: reverse
+    256^3 and 512^3 pairs on the 512^3 mesh, and the particle-force network (force matching on 256^3 and 512^3
+    snapshots) on the 512^3 mesh, each against the plain 1024^3 run of the same seed: reverse
     co-evolution sim-steps/s (CUDA events, median over the seeds), the largest and the mean kappa P(ell) error over
     the seeds and the bins with ell <= 3000 (the range the networks were trained on) and ell <= 1e4, the largest
     error per bin, and the coarsest mesh of each form within 1 % in every bin on all four seeds (None: no mesh)."""
@@ -587,10 +589,13 @@ def learned_comparison(seeds=(100, 101, 102, 103)):
         return {"unavailable": "no trained parameters committed"}
     w256 = torch.tensor(np.load(LEARNED_256), dtype=torch.float32, device="cuda")
     w512 = torch.tensor(np.load(LEARNED_256_512), dtype=torch.float32, device="cuda")
+    forms = [(256, w256, "learned (256^3 pairs)"), (512, w512, "learned (256^3 + 512^3 pairs)")]
+    if os.path.exists(LEARNED_PARTICLE):
+        wp = torch.tensor(np.load(LEARNED_PARTICLE), dtype=torch.float32, device="cuda")
+        forms.append((512, None, "learned particle force (force matching)", wp))
     S = replace(learned.PairSpec(), n_pix=4096)
     res = learned.ladder_seeds(S, seeds, meshes=(256, 512, 768), cuts=(3000.0, S.ell_cut), log=lambda m: None,
-                               learned_forms=[(256, w256, "learned (256^3 pairs)"),
-                                              (512, w512, "learned (256^3 + 512^3 pairs)")])
+                               learned_forms=forms)
     rows = res["forms"]
     fine = rows[0]["sim_steps_per_s"]
     return {"workload": "pair_256p_{256,512,768}m_vs_1024m_4096r", "seeds": list(seeds),

@@ -775,10 +775,16 @@ static hrt_status ctx_solve(hrt_ctx* ctx) {
   return HRT_OK;
 }
 
-// CIC deposit of the current particles, then the gradient fields.
+// CIC deposit of the current particles, then the gradient fields.  Particles given by the caller are sorted by
+// cell first (when sorting is on), so that the deposit runs in cell order too.
 static hrt_status ctx_force(hrt_ctx* ctx) {
   const hrt_config& c = ctx->cfg;
   ctx->force_valid = false;
+  if (ctx->sort_first && ctx->sort_every > 0) {
+    PhaseScope ps(ctx, 7);
+    HRT_TRY(ctx_sort(ctx));
+    ctx->steps_since_sort = 0;
+  }
   {
     PhaseScope ps(ctx, 2);
     HRT_TRY(launch_cic_scatter(ctx->disp, c.n_side, c.n_mesh, c.box, ctx->rho, ctx->stream, ctx_order(ctx)));

