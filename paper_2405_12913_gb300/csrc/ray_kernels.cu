@@ -42,13 +42,26 @@ __device__ __forceinline__ void base_position(double obs, double r_ref, double t
   f0 = static_cast<float>(u - fl);
 }
 
+// Wraps k into [0, n): one compare for the usual k within a box of [0, n), the division only beyond.
+__device__ __forceinline__ int wrap_cell(int k, int n) {
+  if (k >= n) {
+    k -= n;
+    if (k >= n) k %= n;
+  } else if (k < 0) {
+    k += n;
+    if (k < 0) {
+      k %= n;
+      if (k < 0) k += n;
+    }
+  }
+  return k;
+}
+
 __device__ __forceinline__ void node_axis(int i0, float f0, float off, int n, int& i, float& f) {
   float u = f0 + off;
   float fl = floorf(u);
   f = u - fl;
-  int k = i0 + static_cast<int>(fl);
-  k %= n;
-  i = k < 0 ? k + n : k;
+  i = wrap_cell(i0 + static_cast<int>(fl), n);
 }
 
 __device__ __forceinline__ HalfKick half_kick(const RayStepParams& p, int j0, int j1, double th_x, double th_y,
@@ -119,8 +132,7 @@ __device__ __forceinline__ void box_axis(int i_s, float f_s, int sgn, int sh, in
     ib = sh - i_s;
     fb = 0.f;
   }
-  ib %= n;
-  if (ib < 0) ib += n;
+  ib = wrap_cell(ib, n);
 }
 
 __device__ __forceinline__ int pick(int axis, int a, int b, int c) { return axis == 0 ? a : (axis == 1 ? b : c); }

@@ -39,15 +39,25 @@ __device__ __forceinline__ int cell_of(int q_node, float d_cells, int n) {
 // found by __match_any_sync, ranked by lane within the group).  Every lane of a warp runs the matching, so the
 // kernel keeps out-of-range threads until then.
 __global__ void sort_key_kernel(const float* __restrict__ disp, const int32_t* __restrict__ order, int64_t np,
-                                int n_side, int ratio, int n, int nseg, int bricks, float inv_cell,
+                                int n_side, int lns, int ratio, int n, int nseg, int bricks, float inv_cell,
                                 int32_t* __restrict__ counts, int32_t* __restrict__ keys, int32_t* __restrict__ ranks) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   const bool valid = i < np;
   int32_t key = -1;
   if (valid) {
     const unsigned lag = order ? static_cast<unsigned>(__ldg(order + i)) : static_cast<unsigned>(i);
-    const unsigned ns = static_cast<unsigned>(n_side);
-    const int qk = static_cast<int>(lag % ns), qj = static_cast<int>((lag / ns) % ns), qi = static_cast<int>(lag / ns / ns);
+    int qi, qj, qk;
+    if (lns >= 0) {  // n_side a power of two: the lattice site by shifts
+      const unsigned mask = (1u << lns) - 1u;
+      qk = static_cast<int>(lag & mask);
+      qj = static_cast<int>((lag >> lns) & mask);
+      qi = static_cast<int>(lag >> (2 * lns));
+    } else {
+      const unsigned ns = static_cast<unsigned>(n_side);
+      qk = static_cast<int>(lag % ns);
+      qj = static_cast<int>((lag / ns) % ns);
+      qi = static_cast<int>(lag / ns / ns);
+    }
     const int ix = cell_of(qi * ratio, __ldg(disp + i) * inv_cell, n);
     const int iy = cell_of(qj * ratio, __ldg(disp + np + i) * inv_cell, n);
     const int iz = cell_of(qk * ratio, __ldg(disp + 2 * np + i) * inv_cell, n);
@@ -188,7 +198,10 @@ hrt_status launch_particle_sort(const float* disp, const float* mom, const int32
   const int64_t nb = (T + kScanItems - 1) / kScanItems;
   // counters, then the block sums after them
   HRT_CUDA(cudaMemsetAsync(counts, 0, static_cast<size_t>(T) * sizeof(int32_t), s));
-  sort_key_kernel<<<blocks_for(np, 256), 256, 0, s>>>(disp, order, np, static_cast<int>(n_side),
+  int lns = 0;
+  while ((int64_t{1} << lns) < n_side) ++lns;
+  if ((int64_t{1} << lns) != n_side) lns = -1;
+  sort_key_kernel<<<blocks_for(np, 256), 256, 0, s>>>(disp, order, np, static_cast<int>(n_side), lns,
                                                       static_cast<int>(n / n_side), static_cast<int>(n), nseg,
                                                       bricks && particle_bricks_ok(n) ? 1 : 0, static_cast<float>(n / box),
                                                       counts, keys, ranks);
