@@ -80,7 +80,7 @@ __device__ __forceinline__ int wrap(int i, int n) {
 __device__ __forceinline__ int box_index(int i, int sgn, int sh, int n) { return wrap(sgn > 0 ? i + sh : sh - i, n); }
 
 template <bool TILED>
-__global__ void __launch_bounds__(kTileX * kTileY) raymesh_project_kernel(const float* __restrict__ gx,
+__global__ void __launch_bounds__(kTileX * kTileY, 1) raymesh_project_kernel(const float* __restrict__ gx,
                                                                          const float* __restrict__ gy,
                                                                          const float* __restrict__ gz,
                                                                          const __grid_constant__ ProjectParams p,
@@ -217,7 +217,7 @@ __device__ __forceinline__ MeshKick mesh_kick(const MeshView& m, double thx, dou
   return h;
 }
 
-__global__ void __launch_bounds__(256) raymesh_ray_kernel(double2* __restrict__ theta, float2* __restrict__ eta,
+__global__ void __launch_bounds__(256, 1) raymesh_ray_kernel(double2* __restrict__ theta, float2* __restrict__ eta,
                                                           float4* __restrict__ Amat, float4* __restrict__ Bmat,
                                                           int64_t nr, const __grid_constant__ RayMeshParams p,
                                                           float* __restrict__ maps) {
