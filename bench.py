@@ -53,7 +53,7 @@ def parse():
     p.add_argument("--no-precision", action="store_true",
                    help="skip the per-output errors against the stored FP64 oracle outputs (and the FP32-angle ablation)")
     p.add_argument("--sort-every", type=int, default=None,
-                   help="re-sort the particles by mesh cell every K particle steps (default: the library's, 4; 0: never)")
+                   help="re-sort the particles by mesh cell every K particle steps (default: the library's, 8; 0: never)")
     p.add_argument("--tiled-deposit", type=int, default=0, choices=[0, 1, 2],
                    help="kick-drift-deposit: 0 per-particle gathers and reductions on z-row order (default), "
                         "2 shared-memory tiles by TMA on brick order, 1 tiles by row copies")
@@ -254,7 +254,7 @@ def run_gpu(args, W, world, rank, local):
 
     # the context sorts particles given by the caller before their first force, then every sort_every particle
     # steps (6 own launches: cell keys, three scan passes, inversion, gather)
-    sort_every = 4 if args.sort_every is None else args.sort_every
+    sort_every = 8 if args.sort_every is None else args.sort_every
     since_sort = [0]
 
     def reset():

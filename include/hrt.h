@@ -596,7 +596,7 @@ hrt_status hrt_raymesh_step_planes(const hrt_raymesh_config* cfg, const hrt_ray_
  * grouped into bricks of 8 x 8 x 32 cells while the tiled deposit of hrt_set_tiled_deposit is selected) before
  * the kick-drift-deposit, so that neighbouring threads gather from and deposit into neighbouring cells also
  * after clustering has spread lattice neighbours apart; 0 keeps lattice order (the default after hrt_create is
- * 4).  Particles given by hrt_init_particles or hrt_load_state are sorted before their first force (inside
+ * 8).  Particles given by hrt_init_particles or hrt_load_state are sorted before their first force (inside
  * the call); initial conditions, still in cell order, wait for the interval.  Only the storage order changes: every read-out
  * (hrt_read_particles, hrt_save_state) is in lattice order.  Extra device memory once sorting starts: 44 B per
  * particle and 4 B per 32 mesh cells. */

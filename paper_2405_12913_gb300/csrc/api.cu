@@ -1662,7 +1662,7 @@ hrt_status hrt_create(const hrt_config* cfg, void* stream, hrt_ctx** out) {
   hrt_ctx* ctx = new (std::nothrow) hrt_ctx();
   if (!ctx) return fail(HRT_ERR_OOM, "host allocation");
   ctx->cfg = *cfg;
-  ctx->sort_every = 4;
+  ctx->sort_every = 8;
   ctx->stream = as_stream(stream);
   const int64_t n = cfg->n_mesh, m = n * n * n, np = cfg->n_side * cfg->n_side * cfg->n_side;
   hrt_status s = hrt_pm_create(n, cfg->box, cfg->ray_fields, stream, &ctx->pm);
