@@ -687,6 +687,21 @@ hrt_status hrt_read_maps(hrt_ctx* ctx, int32_t source, float* kappa, float* gamm
 hrt_status hrt_read_particles(hrt_ctx* ctx, float* disp, float* mom, double* a_host, double* a_mom_host);
 hrt_status hrt_read_grad(hrt_ctx* ctx, float* grad /* [3][n^3] */);
 
+/* Asynchronous read-outs of the results of Algorithm 1 that a caller takes every step: the ray angles theta
+ * (FP64 [n_rays][2], advanced by Eq. "drift"; their difference from the initial angles is the deflection) and
+ * the convergence map kappa of source plane `source` (float32 [n_rays], the readout of Eqs. "obs_first_set").
+ * Each call snapshots the data into a device staging buffer on the context's stream, in order after the work
+ * queued so far, and copies it to host_dst on a separate copy stream, so that the copy runs beside the
+ * context's next steps; the call itself returns at once.  host_dst is host memory (pinned, for the copy to
+ * overlap) that stays valid until hrt_read_wait has returned HRT_OK, and holds the data from then on; copies
+ * into the same buffer land in the order of the calls.  hrt_read_wait blocks until every asynchronous copy so
+ * far has landed (bounded by hrt_set_host_wait_limit: HRT_ERR_TIMEOUT).  Device memory: 20 B per ray for the
+ * staging buffer, allocated on first use.  Errors: HRT_ERR_STATE without rays (or maps), HRT_ERR_INVALID_ARG
+ * for a NULL destination or a source out of range. */
+hrt_status hrt_read_rays_async(hrt_ctx* ctx, double* theta_host);
+hrt_status hrt_read_kappa_async(hrt_ctx* ctx, int32_t source, float* kappa_host);
+hrt_status hrt_read_wait(hrt_ctx* ctx);
+
 /* Opt-in checks for NaN and infinity (off by default).  With on = 1, hrt_init_particles and hrt_init_rays
  * scan the state they copied in and return HRT_ERR_NONFINITE before using it (the context then has no
  * particles, or no rays), and hrt_step / hrt_step_accumulate scan the particle state, the ray state and the

@@ -1612,6 +1612,7 @@ hrt_status hrt_destroy(hrt_ctx* ctx) {
   if (!ctx) return HRT_OK;
   cudaStream_t s = ctx->stream;
   if (ctx->ray_stream) cudaStreamSynchronize(ctx->ray_stream);
+  if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
   cudaStreamSynchronize(s);
   for (auto& v : ctx->phases)
     for (auto& ev : v) {
@@ -1646,7 +1647,12 @@ hrt_status hrt_destroy(hrt_ctx* ctx) {
   device_free(ctx->pcorr_table, s);
   device_free(ctx->corr_table, s);
   device_free(ctx->ray_table, s);
+  device_free(ctx->stage, s);
   cudaStreamSynchronize(s);
+  if (ctx->ev_staged) cudaEventDestroy(ctx->ev_staged);
+  for (cudaEvent_t e : ctx->ev_copied)
+    if (e) cudaEventDestroy(e);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   if (ctx->ev_fields) cudaEventDestroy(ctx->ev_fields);
   if (ctx->ev_rays) cudaEventDestroy(ctx->ev_rays);
   if (ctx->ray_stream) cudaStreamDestroy(ctx->ray_stream);
@@ -1952,6 +1958,86 @@ hrt_status hrt_read_maps(hrt_ctx* ctx, int32_t source, float* kappa, float* gamm
       hrt_status s = cuda_status(cudaMemcpyAsync(dst[i], base + i * r, r * sizeof(float), cudaMemcpyDefault, ctx->stream), "read map");
       if (s != HRT_OK) return ctx_mark(ctx, s);
     }
+  return HRT_OK;
+}
+
+namespace hrt {
+// The copy stream, its events and a staging buffer of at least `bytes` for the asynchronous read-outs, made on
+// first use (stream and events all or none).  A larger buffer replaces the old one once the copies still reading
+// it have finished.
+static hrt_status ctx_stage(hrt_ctx* ctx, size_t bytes) {
+  if (!ctx->copy_stream) {
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    hrt_status s = cuda_status(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "copy stream");
+    for (int i = 0; i < 3 && s == HRT_OK; ++i)
+      s = cuda_status(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming), "read-out event");
+    if (s != HRT_OK) {
+      for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+      if (cs) cudaStreamDestroy(cs);
+      return s;
+    }
+    ctx->copy_stream = cs;
+    ctx->ev_staged = ev[0];
+    ctx->ev_copied[0] = ev[1];
+    ctx->ev_copied[1] = ev[2];
+  }
+  if (ctx->stage_bytes >= bytes) return HRT_OK;
+  if (ctx->copy_pending[0] || ctx->copy_pending[1]) {
+    HRT_TRY(wait_stream(ctx->copy_stream, "read-out copies"));
+    ctx->copy_pending[0] = ctx->copy_pending[1] = false;
+  }
+  char* p = nullptr;
+  HRT_TRY(device_alloc(reinterpret_cast<void**>(&p), bytes, ctx->stream, "read-out staging"));
+  device_free(ctx->stage, ctx->stream);
+  ctx->stage = p;
+  ctx->stage_bytes = bytes;
+  return HRT_OK;
+}
+
+// One asynchronous read-out through staging region `region` (offset off): the device data is copied into the
+// region on the context stream, in order after the work queued so far and after the last copy out of the same
+// region, and from there to the host on the copy stream, where it runs beside the context's next kernels.
+static hrt_status ctx_read_async(hrt_ctx* ctx, int region, size_t off, const void* dev, size_t bytes, void* host) {
+  cudaStream_t st = ctx->stream;
+  if (ctx->copy_pending[region]) HRT_CUDA(cudaStreamWaitEvent(st, ctx->ev_copied[region], 0));
+  HRT_CUDA(cudaMemcpyAsync(ctx->stage + off, dev, bytes, cudaMemcpyDeviceToDevice, st));
+  HRT_CUDA(cudaEventRecord(ctx->ev_staged, st));
+  HRT_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_staged, 0));
+  HRT_CUDA(cudaMemcpyAsync(host, ctx->stage + off, bytes, cudaMemcpyDefault, ctx->copy_stream));
+  HRT_CUDA(cudaEventRecord(ctx->ev_copied[region], ctx->copy_stream));
+  ctx->copy_pending[region] = true;
+  return HRT_OK;
+}
+}  // namespace hrt
+
+hrt_status hrt_read_rays_async(hrt_ctx* ctx, double* theta_host) {
+  HRT_TRY(ctx_guard(ctx));
+  const int64_t r = ctx->rays.n_rays;
+  if (r == 0) return fail(HRT_ERR_STATE, "no rays");
+  if (!theta_host) return fail(HRT_ERR_INVALID_ARG, "NULL destination");
+  HRT_TRY(ctx_mark(ctx, ctx_stage(ctx, 20 * static_cast<size_t>(r))));
+  return ctx_mark(ctx, ctx_read_async(ctx, 0, 0, ctx->rays.theta, 16 * static_cast<size_t>(r), theta_host));
+}
+
+hrt_status hrt_read_kappa_async(hrt_ctx* ctx, int32_t source, float* kappa_host) {
+  HRT_TRY(ctx_guard(ctx));
+  const int64_t r = ctx->rays.n_rays;
+  if (r == 0 || !ctx->maps) return fail(HRT_ERR_STATE, "no maps");
+  if (source < 0 || source >= ctx->cfg.n_sources) return fail(HRT_ERR_INVALID_ARG, "source out of range");
+  if (!kappa_host) return fail(HRT_ERR_INVALID_ARG, "NULL destination");
+  HRT_TRY(ctx_mark(ctx, ctx_stage(ctx, 20 * static_cast<size_t>(r))));
+  return ctx_mark(ctx, ctx_read_async(ctx, 1, 16 * static_cast<size_t>(r),
+                                      ctx->maps + static_cast<int64_t>(source) * 4 * r, 4 * static_cast<size_t>(r),
+                                      kappa_host));
+}
+
+hrt_status hrt_read_wait(hrt_ctx* ctx) {
+  HRT_TRY(ctx_guard(ctx));
+  if (!ctx->copy_stream) return HRT_OK;
+  HRT_TRY(ctx_mark(ctx, wait_stream(ctx->copy_stream, "hrt_read_wait")));
+  ctx->copy_pending[0] = ctx->copy_pending[1] = false;
   return HRT_OK;
 }
 

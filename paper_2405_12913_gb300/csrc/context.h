@@ -75,6 +75,14 @@ struct hrt_ctx {
   cudaStream_t ray_stream = nullptr;
   cudaEvent_t ev_fields = nullptr, ev_rays = nullptr;
   bool rays_pending = false;
+  // asynchronous read-outs (hrt_read_rays_async, hrt_read_kappa_async): results are staged in a device buffer on
+  // the context stream and copied to the host on copy_stream, beside the next steps; region 0 holds the ray angles
+  // (16 B per ray), region 1 one convergence map (4 B per ray); ev_copied[i]: the last copy out of region i
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_staged = nullptr, ev_copied[2] = {nullptr, nullptr};
+  bool copy_pending[2] = {false, false};
+  char* stage = nullptr;
+  size_t stage_bytes = 0;
   // learned ray-force correction (NULL: plain)
   float* corr_w = nullptr;
   void* corr_wb = nullptr;

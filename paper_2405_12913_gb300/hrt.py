@@ -130,6 +130,9 @@ _SIGS = {
     "hrt_drift_free": ([_P, _D, _D], C.c_int),
     "hrt_read_rays": ([_P, _P, _P, _P, _P], C.c_int),
     "hrt_read_maps": ([_P, _I32, _P, _P, _P, _P], C.c_int),
+    "hrt_read_rays_async": ([_P, _P], C.c_int),
+    "hrt_read_kappa_async": ([_P, _I32, _P], C.c_int),
+    "hrt_read_wait": ([_P], C.c_int),
     "hrt_read_particles": ([_P, _P, _P, _P, _P], C.c_int),
     "hrt_read_grad": ([_P, _P], C.c_int),
     "hrt_ctx_kappa_power": ([_P, _I32, _I64, _D, _I32, _D, _D, _P, _P, _P], C.c_int),
@@ -197,6 +200,17 @@ def _ptr(t: torch.Tensor | None, dtype=None, name: str = "tensor") -> int | None
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def _host_ptr(t: torch.Tensor, dtype, name: str) -> int:
+    """Pointer of a contiguous host tensor (for the asynchronous read-outs)."""
+    if t.is_cuda:
+        raise ValueError(f"{name} must be a host tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.dtype != dtype:
         raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
     return t.data_ptr()
 
@@ -915,6 +929,24 @@ class Context:
         """Stream-ordered copies of the ray state into caller tensors in device or host memory (None skips)."""
         _check(_lib.hrt_read_rays(self._h, _any_ptr(theta, torch.float64, "theta"), _any_ptr(eta, torch.float32, "eta"),
                                   _any_ptr(A, torch.float32, "A"), _any_ptr(B, torch.float32, "B")), "hrt_read_rays")
+
+    def hrt_read_rays_async(self, theta: torch.Tensor):
+        """Asynchronous copy of the ray angles into a host tensor (float64 [n_rays, 2], pinned for overlap); valid
+        once hrt_read_wait has returned."""
+        if theta.numel() < 2 * self.n_rays:
+            raise ValueError("theta holds fewer than 2 * n_rays values")
+        _check(_lib.hrt_read_rays_async(self._h, _host_ptr(theta, torch.float64, "theta")), "hrt_read_rays_async")
+
+    def hrt_read_kappa_async(self, source: int, kappa: torch.Tensor):
+        """Asynchronous copy of the convergence map of `source` into a host tensor (float32 [n_rays])."""
+        if kappa.numel() < self.n_rays:
+            raise ValueError("kappa holds fewer than n_rays values")
+        _check(_lib.hrt_read_kappa_async(self._h, source, _host_ptr(kappa, torch.float32, "kappa")),
+               "hrt_read_kappa_async")
+
+    def hrt_read_wait(self):
+        """Waits (bounded) until every asynchronous read-out copy has landed."""
+        _check(_lib.hrt_read_wait(self._h), "hrt_read_wait")
 
     def hrt_read_maps_into(self, source: int, kappa: torch.Tensor | None, gamma1: torch.Tensor | None = None,
                            gamma2: torch.Tensor | None = None, omega: torch.Tensor | None = None):
