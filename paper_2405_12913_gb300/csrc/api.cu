@@ -787,7 +787,10 @@ static hrt_status ctx_force(hrt_ctx* ctx) {
   }
   {
     PhaseScope ps(ctx, 2);
-    HRT_TRY(launch_cic_scatter(ctx->disp, c.n_side, c.n_mesh, c.box, ctx->rho, ctx->stream, ctx_order(ctx)));
+    // the density is still zero if the last solve cleared it and nothing has been deposited since
+    const bool zeroed = ctx->rho_clear;
+    ctx->rho_clear = false;
+    HRT_TRY(launch_cic_scatter(ctx->disp, c.n_side, c.n_mesh, c.box, ctx->rho, ctx->stream, ctx_order(ctx), zeroed));
   }
   return ctx_solve(ctx);
 }

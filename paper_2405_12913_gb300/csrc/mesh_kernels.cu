@@ -260,10 +260,10 @@ hrt_status launch_cic_scatter_warp(const float* disp, int64_t n_side, int64_t n,
 }
 
 hrt_status launch_cic_scatter(const float* disp, int64_t n_side, int64_t n, double box, float* rho,
-                              cudaStream_t s, const int32_t* order) {
+                              cudaStream_t s, const int32_t* order, bool rho_zeroed) {
   int64_t np = n_side * n_side * n_side;
   size_t mesh_bytes = static_cast<size_t>(n) * n * n * sizeof(float);
-  HRT_CUDA(cudaMemsetAsync(rho, 0, mesh_bytes, s));
+  if (!rho_zeroed) HRT_CUDA(cudaMemsetAsync(rho, 0, mesh_bytes, s));
   if (np == 0) return HRT_OK;
   cic_scatter_kernel<<<particle_grid(n_side, 256, order), 256, 0, s>>>(disp, np, make_lattice(n_side, n, box, order),
                                                                        particle_mass(n_side, n), rho);

@@ -13,9 +13,10 @@ namespace hrt {
 // The same deposit with warp-aggregated atomics (n_side a power of two >= 32).
 hrt_status launch_cic_scatter_warp(const float* disp, int64_t n_side, int64_t n, double box, float* rho,
                                    cudaStream_t s);
-// order (or nullptr): particles stored in cell order, slot i holding lattice particle order[i].
+// order (or nullptr): particles stored in cell order, slot i holding lattice particle order[i]; rho_zeroed: rho
+// is already zero (no memset before the deposit).
 hrt_status launch_cic_scatter(const float* disp, int64_t n_side, int64_t n, double box, float* rho,
-                              cudaStream_t s, const int32_t* order = nullptr);
+                              cudaStream_t s, const int32_t* order = nullptr, bool rho_zeroed = false);
 
 // Bricks of the cell order: 8 x 8 x 32 cells, 64 sort keys (z-row segments) each.
 constexpr int kBrickXY = 8;
