@@ -269,10 +269,15 @@ class ForceTrainer:
     snapshots of fine-mesh runs, the coarse-mesh PM force with the learned factor g, interpolated at the
     particles, against the fine-mesh force there.  Loss per snapshot: sum_p |F_coarse - F_fine|^2 / sum_p
     |F_fine|^2.  Gradients go through the gather adjoint (``hrt_particle_kick_drift_adjoint``), forward FFTs of
-    the field cotangents and ``hrt_kspace_table_adjoint`` into the MLP; all arithmetic in libhrt kernels."""
+    the field cotangents and ``hrt_kspace_table_adjoint`` into the MLP; all arithmetic in libhrt kernels.
 
-    def __init__(self, S: PairSpec, n_coarse: int):
+    anchor = (kcell, weight): adds weight * mean over the table rows with |k| cell < kcell of (g - 1)^2, which holds
+    the factor at 1 on the large scales that the coarse mesh already resolves (the force error hardly weighs
+    them, yet they set the growth of the large-scale power)."""
+
+    def __init__(self, S: PairSpec, n_coarse: int, anchor=None):
         self.S, self.n = S, n_coarse
+        self.anchor = anchor
         self.cell = S.box / n_coarse
         self.kmax = math.sqrt(3.0) * math.pi / self.cell * 1.0001
         self.pm = _pm_cache(n_coarse, S.box)
@@ -321,6 +326,12 @@ class ForceTrainer:
         hrt.hrt_particle_kick_drift(fields, n, S.box, S.n_side, disp.clone(), fc, -1.0, 0.0)
         r = fc - sample["f_fine"]
         loss = float((r.double() ** 2).sum()) / sample["norm"]
+        low = None
+        if self.anchor is not None and mlp is not None:
+            kcell, weight = self.anchor
+            low = (sample["x"][:, 0] < kcell).to(torch.float32)
+            nlow = max(float(low.sum()), 1.0)
+            loss += weight * float((low * (table - 1.0) ** 2).sum()) / nlow
         if grad is not None:
             m_bar = (2.0 / sample["norm"]) * r
             g_bar = torch.zeros(3, n ** 3, device="cuda")
@@ -332,12 +343,14 @@ class ForceTrainer:
                 self.pm.forward_fft(g_bar[j].contiguous(), gbar_hat[j])
             tb = torch.zeros(N_TABLE, device="cuda")
             hrt.hrt_kspace_table_adjoint(gbar_hat, 3, sample["spec"], n, S.box, pref, f, tb)
+            if low is not None:
+                tb += (2.0 * self.anchor[1] / nlow) * low * (table - 1.0)
             mlp.accumulate(sample["x"], tb, grad)
         return loss
 
 
 def train_particle(S: PairSpec, train_seeds, test_seeds, iters: int = 300, lr: float = 2e-3, log=print,
-                   snapshots=(0.2, 0.4, 0.6, 0.8, 1.0), meshes=None):
+                   snapshots=(0.2, 0.4, 0.6, 0.8, 1.0), meshes=None, anchor=None):
     """Adam on the particle-correction MLP by force matching (ForceTrainer), over the coarse meshes (default
     S.n_coarse; ln N_mesh is an input, so one network serves them all) and the training seeds' snapshots; returns
     the network and the relative force errors of the plain and the learned coarse force on the held-out seeds."""
@@ -345,7 +358,7 @@ def train_particle(S: PairSpec, train_seeds, test_seeds, iters: int = 300, lr: f
     t0 = time.time()
     fg = S.forward_grid
     snaps = sorted({min(fg[1:], key=lambda a: abs(a - t)) for t in snapshots})
-    trainers = {m: ForceTrainer(S, m) for m in meshes}
+    trainers = {m: ForceTrainer(S, m, anchor) for m in meshes}
     test = {m: ForceTrainer(S, m) for m in meshes}
     for m in meshes:
         for s in train_seeds:
@@ -588,14 +601,18 @@ def main():
                     help="training seeds per Adam step, drawn from the training seeds (0: all)")
     ap.add_argument("--particle", action="store_true",
                     help="train the particle-force correction by force matching instead of the ray correction")
+    ap.add_argument("--anchor-kcell", type=float, default=0.0,
+                    help="particle training: hold g at 1 for |k| cell below this (0: no anchor)")
+    ap.add_argument("--anchor-weight", type=float, default=10.0, help="weight of that penalty")
     a = ap.parse_args()
     S = replace(PairSpec(), n_pix=a.n_pix, ell_cut=a.ell_cut)
     test = list(range(100, 100 + a.test_seeds))
     out = {}
     if a.particle:
         meshes = tuple(int(x) for x in a.meshes.split(",")) if a.meshes else None
+        anchor = (a.anchor_kcell, a.anchor_weight) if a.anchor_kcell > 0 else None
         mlp, res = train_particle(S, range(a.train_seeds), test, a.iters, a.lr, log=lambda m: print(m, flush=True),
-                                  meshes=meshes)
+                                  meshes=meshes, anchor=anchor)
         if a.out:
             np.save(a.out, mlp.state())
         print(json.dumps({"particle_training": res}))
