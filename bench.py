@@ -147,9 +147,16 @@ def measured_peaks():
 
 
 def kernel_source_hash(kernel: str) -> str:
+    """Hash of the kernel's source files with comments, trailing blanks and empty lines removed, so that only a
+    change of the code voids a recorded traffic figure."""
+    import re
     h = hashlib.sha256()
     for fn in KERNEL_SOURCES.get(kernel, []):
-        h.update(open(os.path.join(ROOT, "paper_2405_12913_gb300", "csrc", fn), "rb").read())
+        text = open(os.path.join(ROOT, "paper_2405_12913_gb300", "csrc", fn), encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        lines = [ln.rstrip() for ln in text.splitlines()]
+        h.update("\n".join(ln for ln in lines if ln).encode())
     return h.hexdigest()[:16]
 
 

@@ -1,11 +1,13 @@
 // Mesh kernels of the HRT hot path on sm_103a: CIC mass assignment, the fused k-space Poisson/gradient/
-// deconvolution kernel, the fused particle gather + kick + drift, and the Zel'dovich IC helpers.
+// deconvolution kernel (3D path), the fused particle gather + kick + drift + deposit, its shared-memory-tile
+// variant on brick-sorted particles, and the Zel'dovich and 2LPT IC helpers.
 //
-// All three mesh passes are bound by HBM bandwidth; the kernels are written for coalesced 4- and 8-byte
-// accesses with neighbouring threads on neighbouring cells, so that the CIC atomics and gathers hit lines already
-// resident in the 129 MB L2.  Particles come in one of two storage orders: fresh particles in Lagrangian-lattice
-// order, walked in Morton-ordered bricks of lattice sites, and the context's particles in cell order (re-sorted
-// by mesh cell every few steps, sort_kernels.cu), where a slot -> lattice-site map gives each thread its site.
+// The mesh passes are bound by HBM bandwidth or by the latency of their gathers; the kernels are written for
+// coalesced accesses with neighbouring threads on neighbouring cells, so that the gathers and the deposit's
+// 16-byte vector reductions hit lines already resident in the 129 MB L2.  Particles come in one of two storage
+// orders: fresh particles in Lagrangian-lattice order, walked in Morton-ordered bricks of lattice sites, and the
+// context's particles in cell order (re-sorted by mesh cell every few steps, sort_kernels.cu), where a
+// slot -> lattice-site map gives each thread its site.
 #include <cuda_runtime.h>
 
 #include <algorithm>
