@@ -1966,8 +1966,9 @@ hrt_status hrt_read_maps(hrt_ctx* ctx, int32_t source, float* kappa, float* gamm
 
 namespace hrt {
 // The copy stream, its events and a staging buffer of at least `bytes` for the asynchronous read-outs, made on
-// first use (stream and events all or none).  A larger buffer replaces the old one once the copies still reading
-// it have finished.
+// first use (stream and events all or none).  The regions' offsets follow the ray count, so a new layout (rays
+// initialised again with another count) first lets the copies still reading the old regions finish; a larger
+// buffer then replaces the old one.
 static hrt_status ctx_stage(hrt_ctx* ctx, size_t bytes) {
   if (!ctx->copy_stream) {
     cudaStream_t cs = nullptr;
@@ -1986,11 +1987,12 @@ static hrt_status ctx_stage(hrt_ctx* ctx, size_t bytes) {
     ctx->ev_copied[0] = ev[1];
     ctx->ev_copied[1] = ev[2];
   }
-  if (ctx->stage_bytes >= bytes) return HRT_OK;
-  if (ctx->copy_pending[0] || ctx->copy_pending[1]) {
+  if (bytes != ctx->stage_layout && (ctx->copy_pending[0] || ctx->copy_pending[1])) {
     HRT_TRY(wait_stream(ctx->copy_stream, "read-out copies"));
     ctx->copy_pending[0] = ctx->copy_pending[1] = false;
   }
+  ctx->stage_layout = bytes;
+  if (ctx->stage_bytes >= bytes) return HRT_OK;
   char* p = nullptr;
   HRT_TRY(device_alloc(reinterpret_cast<void**>(&p), bytes, ctx->stream, "read-out staging"));
   device_free(ctx->stage, ctx->stream);

@@ -82,7 +82,8 @@ struct hrt_ctx {
   cudaEvent_t ev_staged = nullptr, ev_copied[2] = {nullptr, nullptr};
   bool copy_pending[2] = {false, false};
   char* stage = nullptr;
-  size_t stage_bytes = 0;
+  size_t stage_bytes = 0;   // allocated
+  size_t stage_layout = 0;  // bytes of the layout in use (20 B per ray of the current rays)
   // learned ray-force correction (NULL: plain)
   float* corr_w = nullptr;
   void* corr_wb = nullptr;

@@ -83,6 +83,33 @@ def test_one_reused_host_buffer_ends_with_the_last_step(hrt):
     ctx.close()
 
 
+def test_rays_initialised_again_with_fewer_rays_keep_the_pending_copy(hrt):
+    # the staging regions follow the ray count: a read of the old rays still in flight must not be overwritten
+    # by the staging of a read made after the rays were initialised again with fewer rays
+    from paper_2405_12913_gb300.configs import COSMO_TINY as W
+    ctx = _context(hrt, W)
+    r = W.n_pix ** 2
+    grid = W.reverse_grid
+    ctx.hrt_step(grid[1])
+    h = torch.empty(r, 2, dtype=torch.float64, pin_memory=True)
+    ctx.hrt_read_rays_async(h)
+    d = torch.empty(r, 2, dtype=torch.float64, device="cuda")
+    ctx.hrt_read_rays_into(d)
+    n2 = W.n_pix // 2
+    ctx.hrt_init_rays(torch.tensor(synthetic.pixel_grid(n2, W.fov_deg * synthetic.DEGREE / 2), device="cuda"))
+    ctx.hrt_step(grid[2], 0)
+    k = torch.empty(n2 * n2, dtype=torch.float32, pin_memory=True)
+    ctx.hrt_read_kappa_async(0, k)
+    kd = torch.empty(n2 * n2, dtype=torch.float32, device="cuda")
+    ctx.hrt_read_maps_into(0, kd)
+    ctx.hrt_read_wait()
+    torch.cuda.synchronize()
+    assert torch.equal(h, d.cpu())
+    assert torch.equal(k, kd.cpu())
+    assert torch.count_nonzero(k) > 0
+    ctx.close()
+
+
 def test_async_readouts_reject_bad_arguments(hrt):
     from paper_2405_12913_gb300.configs import COSMO_TINY as W
     cfg = hrt.make_config(W.n_mesh, W.box, W.n_side, W.omega_m, W.h, W.n_s, W.sigma8, W.deconv_p, W.smooth_cells,
