@@ -6,6 +6,7 @@ import pytest
 from scipy import integrate
 
 from oracle import cosmology as cosmo
+from oracle import sim
 from oracle.units import C_LIGHT
 
 
@@ -25,10 +26,9 @@ def test_einstein_de_sitter_closed_forms(a):
     assert cosmo.kick_integral(b, a, om) == pytest.approx(-cosmo.kick_integral(a, b, om), rel=1e-13)
 
 
-def test_growth_against_ode():
-    # Linear growth ODE in a: D'' + (3/a + E'/E) D' - 1.5 Om / (a^5 E^2) D = 0, growing mode D ~ a early.
-    om = 0.3
-
+def _growth_ode(om):
+    """D(a) / D(1) of the linear growth ODE in a: D'' + (3/a + E'/E) D' - 1.5 Om / (a^5 E^2) D = 0, growing mode
+    D ~ a early."""
     def E(a):
         return math.sqrt(om / a ** 3 + 1 - om)
 
@@ -41,8 +41,31 @@ def test_growth_against_ode():
     a0 = 1e-3
     sol = integrate.solve_ivp(rhs, (a0, 1.0), [a0, 1.0], rtol=1e-12, atol=1e-15, dense_output=True)
     d1 = sol.sol(1.0)[0]
+    return lambda a: sol.sol(a)[0] / d1
+
+
+def test_growth_against_ode():
+    om = 0.3
+    d_ode = _growth_ode(om)
     for a in (0.05, 0.3, 0.6):
-        assert cosmo.growth_D1(a, om) == pytest.approx(sol.sol(a)[0] / d1, rel=2e-6)
+        assert cosmo.growth_D1(a, om) == pytest.approx(d_ode(a), rel=2e-6)
+
+
+def test_growth_weight_of_the_ray_kick():
+    # the time correction of the ray kick follows the linear potential, phi ∝ D1 / a (Sec. 3.2): constant in
+    # Einstein-de Sitter (D1 = a), 1 at the reference time, and in LCDM the ratio of D1 / a from the growth ODE
+    # (the potential decays, so it exceeds 1 at earlier times, farther out)
+    g = sim.growth_weight(0.4, 1.0)
+    for chi in (50.0, 800.0, 2500.0):
+        assert g(chi) == pytest.approx(1.0, rel=1e-10)
+    om, a_c = 0.3, 0.6
+    g = sim.growth_weight(a_c, om)
+    assert g(cosmo.chi_of_a(a_c, om)) == pytest.approx(1.0, rel=1e-12)
+    d_ode = _growth_ode(om)
+    for a in (0.2, 0.45, 0.8, 0.95):
+        want = (d_ode(a) / a) / (d_ode(a_c) / a_c)
+        assert g(cosmo.chi_of_a(a, om)) == pytest.approx(want, rel=1e-5)
+        assert (want > 1.0) == (a < a_c)
 
 
 def test_growth_rate_matches_finite_difference():

@@ -22,6 +22,28 @@ def test_zero_output_layer_is_the_plain_kernel():
     assert torch.equal(g, torch.ones(50, dtype=torch.float64))
 
 
+def test_a_chain_network_is_silu_three_times():
+    # parameters packed in the stated order (W1 [64][16], b1, W2 [64][64], b2, W3, b3, W4, b4) that route input
+    # column 1 through hidden units 0 -> 1 -> 2 with unit weights: g = 1 + silu(silu(silu(x_1))) + b4
+    H, IN = 64, 16
+    p = torch.zeros(mlp.N_PARAMS, dtype=torch.float64)
+    o = 0
+    p[o + 0 * IN + 1] = 1.0          # W1[0][1]
+    o += H * IN + H
+    p[o + 1 * H + 0] = 1.0           # W2[1][0]
+    o += H * H + H
+    p[o + 2 * H + 1] = 1.0           # W3[2][1]
+    o += H * H + H
+    p[o + 2] = 1.0                   # W4[2]
+    o += H
+    p[o] = 0.25                      # b4
+    assert o + 1 == mlp.N_PARAMS
+    x = torch.rand(10, 3, dtype=torch.float64) * 4 - 2
+    silu = torch.nn.functional.silu
+    want = 1.0 + silu(silu(silu(x[:, 1]))) + 0.25
+    assert torch.allclose(mlp.forward(x, p, False, False), want, rtol=1e-14, atol=1e-15)
+
+
 def test_silu_values():
     assert float(mlp.silu(torch.tensor(0.0))) == 0.0
     z = torch.tensor([-3.0, 0.5, 4.0], dtype=torch.float64)

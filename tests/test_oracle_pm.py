@@ -137,6 +137,39 @@ def test_kick_drift_with_zero_field():
     assert torch.allclose(d2, d + 0.25 * p, atol=0)
 
 
+def test_kick_drift_with_a_uniform_field():
+    # a uniform gradient is gathered exactly (the CIC weights sum to one); the drift moves the particles with the
+    # momentum after the kick
+    n, L = 4, 8.0
+    q = pm.lattice(n, L)
+    d = torch.tensor(synthetic.small_displacements(5, n, 0.3).T.copy())
+    p = torch.tensor(synthetic.small_displacements(6, n, 0.3).T.copy())
+    g0 = (0.7, -1.3, 0.2)
+    fields = [torch.full((8, 8, 8), v, dtype=torch.float64) for v in g0]
+    d2, p2 = pm.particle_kick_drift(d, p, q, fields, L, kick=0.4, drift=0.25)
+    want_p = p - 0.4 * torch.tensor(g0, dtype=torch.float64)
+    assert torch.allclose(p2, want_p, rtol=0, atol=1e-14)
+    assert torch.allclose(d2, d + 0.25 * want_p, rtol=0, atol=1e-14)
+
+
+def test_zeldovich_density_has_the_sign_of_the_linear_field():
+    # delta_k = w_k sqrt(P / V_cell) with delta = -div Psi: at a small growth factor the particles deposit
+    # 1 + D1 delta on a mesh equal to the lattice, so the deposited density at the lowest wavenumbers is the white
+    # noise times a positive factor (and a displacement of the wrong sign would give the opposite density)
+    n, L, a = 32, 512.0, 0.01
+    noise = synthetic.white_noise(21, n)
+    disp, _ = pm.zeldovich(noise, L, 0.3, 0.7, 0.96, 0.8, a)
+    assert float(disp.abs().max()) < 0.05 * L / n
+    rho = pm.cic_deposit(pm.lattice(n, L) + disp, L, n)
+    r_hat, w_hat = torch.fft.fftn(rho - 1.0), torch.fft.fftn(torch.tensor(noise))
+    f = pm.signed_freq(n).double()
+    nn = torch.sqrt(f.view(-1, 1, 1) ** 2 + f.view(1, -1, 1) ** 2 + f.view(1, 1, -1) ** 2)
+    low = (nn > 0) & (nn <= 3)
+    c = float((r_hat[low] * w_hat[low].conj()).real.sum()) / math.sqrt(
+        float((r_hat[low].abs() ** 2).sum()) * float((w_hat[low].abs() ** 2).sum()))
+    assert c > 0.9
+
+
 def test_zeldovich_momentum_ratio_and_power():
     om, h, ns, s8, a = 0.3, 0.7, 0.96, 0.8, 0.05
     n, L = 32, 256.0
@@ -218,6 +251,20 @@ def test_lpt_single_plane_wave_has_no_second_order_term():
     assert np.abs(psi1[:, [0, 2]].numpy()).max() < 1e-14
 
 
+@pytest.mark.parametrize("direction", [(1, 1, 0), (1, 0, -1), (1, -1, 1)])
+def test_lpt_plane_wave_along_a_diagonal_has_no_second_order_term(direction):
+    # a plane wave in any direction is one-dimensional motion: its 2LPT source sum_{i<j} phi_ii phi_jj - phi_ij^2
+    # vanishes only with the mixed derivatives subtracted; Psi1 = -(A / k^2) k sin(k . q)
+    n, box, amp = 16, 32.0, 0.25
+    kvec = 2.0 * math.pi / box * np.array(direction, dtype=np.float64)
+    q = pm.lattice(n, box).numpy()
+    delta = amp * np.cos(q @ kvec)
+    psi1, psi2 = pm.lpt_fields(torch.tensor(delta.reshape(n, n, n)), box)
+    assert np.abs(psi2.numpy()).max() < 1e-14
+    want = -(amp / float(kvec @ kvec)) * np.sin(q @ kvec)[:, None] * kvec[None, :]
+    assert np.allclose(psi1.numpy(), want, rtol=0, atol=1e-13)
+
+
 @pytest.mark.parametrize("axes", [(0, 1), (0, 2)])
 def test_lpt_two_orthogonal_waves_closed_form(axes):
     # phi1 = -(A cos kx + B cos ky) / k^2: the source is A B cos kx cos ky, phi2 = -A B cos kx cos ky / (2 k^2),
@@ -231,6 +278,39 @@ def test_lpt_two_orthogonal_waves_closed_form(axes):
     want[:, axes[0]] = a * b / (2 * k) * np.sin(u) * np.cos(v)
     want[:, axes[1]] = a * b / (2 * k) * np.cos(u) * np.sin(v)
     assert np.allclose(psi2.numpy(), want, atol=1e-13)
+
+
+def test_lpt_second_order_mode_follows_the_n_body():
+    # Two orthogonal plane waves at the fundamental mode, Einstein-de Sitter (D1 = a, D2 = -(3/7) a^2).  The
+    # Zel'dovich displacement has no (1, +-1, 0) modes; the 2LPT one, D2 (A B / 2k) (sin kx cos ky, cos kx sin ky),
+    # lives only there.  Particles started from Zel'dovich ICs at a = 0.01 and evolved by the PM leapfrog (mesh =
+    # lattice, no filter) build up that mode by a = 1.  The PM force is a little weak at the mesh scale, so the
+    # first-order modes grow by a factor r1 slightly below linear theory; the second-order mode, quadratic in them,
+    # must then reach r1^2 of the 2LPT amplitude (a wrong sign or coefficient of D2 misses by far more).
+    n, box, amp, om = 32, 100.0, 0.3, 1.0
+    c = sim.Cosmo(omega_m=om)
+    k = 2.0 * math.pi / box
+    q = pm.lattice(n, box).numpy()
+    delta = amp * np.cos(k * q[:, 0]) + amp * np.cos(k * q[:, 1])
+    # the white noise whose linear density (delta_k = w_k sqrt(P(k) / V_cell)) is these waves at a = 1
+    p_kf = float(cosmo.linear_power(k, om, c.h, c.n_s, cosmo.power_amplitude(om, c.h, c.n_s, c.sigma8)))
+    noise = (delta / math.sqrt(p_kf / (box / n) ** 3)).reshape(n, n, n)
+    part = sim.initial_particles(noise, box, c, 0.01)
+    grid = list(np.exp(np.linspace(math.log(0.01), 0.0, 41)))
+    part1, _ = sim.run_forward(part, grid, box, n, c, sim.Filter(0.0, 0.0))
+    disp2, _ = pm.lpt2(noise, box, om, c.h, c.n_s, c.sigma8, 1.0)
+    disp1, _ = pm.zeldovich(noise, box, om, c.h, c.n_s, c.sigma8, 1.0)
+
+    def mode(d, comp, m):
+        return complex(torch.fft.fftn(d[:, comp].reshape(n, n, n))[m])
+
+    for comp, first in ((0, (1, 0, 0)), (1, (0, 1, 0))):
+        r1 = mode(part1.disp, comp, first) / mode(disp1, comp, first)
+        assert abs(r1 - 1.0) < 0.03
+        for m in ((1, 1, 0), (1, n - 1, 0)):
+            assert abs(mode(disp1, comp, m)) < 1e-9 * abs(mode(disp2, comp, m))
+            r2 = mode(part1.disp, comp, m) / mode(disp2, comp, m)
+            assert abs(r2 / r1 ** 2 - 1.0) < 0.02
 
 
 def test_lpt_second_order_is_quadratic_and_eds_assembly():

@@ -118,11 +118,11 @@ def test_one_step_phase_space_jacobian_has_unit_determinant():
         assert float(torch.det(M)) == pytest.approx(1.0, abs=1e-12)
 
 
-def test_A_B_recursion_equals_autograd_derivative_of_trajectory():
+def check_ab_against_autograd(pixels):
     # A = d theta / d theta_0 and B = d eta / d theta_0 (Eqs. "A", "B") through several steps.
     gx, gy = _smooth_fields()
     chis = [0.0, 30.0, 75.0, 110.0, 170.0, 260.0]
-    for th in synthetic.pixel_grid(2, 0.3):
+    for th in pixels:
         t0 = torch.tensor(th, dtype=torch.float64)
 
         def final(t):
@@ -133,6 +133,10 @@ def test_A_B_recursion_equals_autograd_derivative_of_trajectory():
         st = _trace(t0[None], gx, gy, chis)
         assert torch.allclose(st["A"][0], jac[:2], rtol=1e-10, atol=1e-14)
         assert torch.allclose(st["B"][0], jac[2:], rtol=1e-10, atol=1e-12)
+
+
+def test_A_B_recursion_equals_autograd_derivative_of_trajectory():
+    check_ab_against_autograd(synthetic.pixel_grid(2, 0.3))
 
 
 def test_second_order_convergence_in_step_size():
