@@ -769,8 +769,14 @@ static hrt_status ctx_solve(hrt_ctx* ctx) {
   ctx->rays_pending = false;
   ctx->force_valid = false;
   ctx->rho_clear = false;
-  HRT_TRY(pm_solve(ctx->pm, ctx->rho, ctx_pref(ctx, ctx->a), &f, ctx->grad, &fr, ctx->ray_grad, ctx, wait,
-                   &ctx->rho_clear));
+  const hrt_status s = pm_solve(ctx->pm, ctx->rho, ctx_pref(ctx, ctx->a), &f, ctx->grad, &fr, ctx->ray_grad, ctx,
+                                wait, &ctx->rho_clear);
+  if (s != HRT_OK) {
+    // a solve that failed before its C2Rs waited for the ray step still joins it, so that whatever comes next on
+    // the context stream (reads of the rays, a new ray set freeing the old buffers) runs after the ray step
+    if (wait) cudaStreamWaitEvent(ctx->stream, wait, 0);
+    return s;
+  }
   ctx->force_valid = true;
   return HRT_OK;
 }
