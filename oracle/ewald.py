@@ -21,11 +21,15 @@ import numpy as np
 from scipy.special import erfc
 
 
-def grad_phi_3d(r: np.ndarray, box: float, n_real: int = 3, n_recip: int = 8) -> np.ndarray:
-    """Gradient of the periodic potential of a unit mass (G M = 1) at displacements r (n, 3) from it."""
+def grad_phi_3d(r: np.ndarray, box: float, n_real: int = 3, n_recip: int = 8,
+                alpha: float | None = None) -> np.ndarray:
+    """Gradient of the periodic potential of a unit mass (G M = 1) at displacements r (n, 3) from it.
+
+    ``alpha`` is the Ewald splitting parameter (default 2 / box); the sum does not depend on it once both
+    parts have converged."""
     r = np.atleast_2d(np.asarray(r, dtype=np.float64))
     r = r - box * np.round(r / box)
-    al = 2.0 / box * 1.0
+    al = 2.0 / box if alpha is None else alpha
     out = np.zeros_like(r)
     rng = range(-n_real, n_real + 1)
     for i in rng:
@@ -49,11 +53,13 @@ def grad_phi_3d(r: np.ndarray, box: float, n_real: int = 3, n_recip: int = 8) ->
     return out
 
 
-def deflection_sum_2d(b: np.ndarray, box: float, n_real: int = 4, n_recip: int = 10) -> np.ndarray:
-    """Zero-mean periodic lensing sum D(b) (n, 2) for transverse offsets b (n, 2) from the lens column."""
+def deflection_sum_2d(b: np.ndarray, box: float, n_real: int = 4, n_recip: int = 10,
+                      alpha: float | None = None) -> np.ndarray:
+    """Zero-mean periodic lensing sum D(b) (n, 2) for transverse offsets b (n, 2) from the lens column
+    (``alpha``: the splitting parameter, default 2 / box)."""
     b = np.atleast_2d(np.asarray(b, dtype=np.float64))
     b = b - box * np.round(b / box)
-    al = 2.0 / box
+    al = 2.0 / box if alpha is None else alpha
     out = np.zeros_like(b)
     rng = range(-n_real, n_real + 1)
     for i in rng:

@@ -76,6 +76,20 @@ def test_born_ewald_matches_closed_form_with_periodic_images(point_mass_run):
     assert np.allclose(born[small], hat, rtol=2e-3)
 
 
+def test_periodic_lensing_sum_is_independent_of_the_splitting():
+    # the 2D Ewald form of the image sum is exact for any splitting parameter, odd in b, and zero at the
+    # half-period points
+    L = 10.0
+    b = np.random.default_rng(4).uniform(-0.5, 0.5, (20, 2)) * L
+    d0 = ewald.deflection_sum_2d(b, L)
+    scale = np.abs(d0).max()
+    for alpha, n_real, n_recip in ((1.5 / L, 5, 10), (3.0 / L, 4, 14)):
+        d = ewald.deflection_sum_2d(b, L, n_real=n_real, n_recip=n_recip, alpha=alpha)
+        assert np.abs(d - d0).max() < 1e-12 * scale
+    assert np.abs(ewald.deflection_sum_2d(-b, L) + d0).max() < 1e-12 * scale
+    assert np.abs(ewald.deflection_sum_2d(np.array([[L / 2, 0.0], [L / 2, L / 2]]), L)).max() < 1e-12 * scale
+
+
 def test_power_of_single_cosine_mode():
     m, dth, amp, mx = 64, 1e-3, 0.02, 5
     x = np.arange(m)

@@ -16,7 +16,7 @@ import test_oracle_mlp as mlp_pins
 import test_oracle_pm as pm_pins
 import test_oracle_raymesh as rm_pins
 import test_oracle_rays as ray_pins
-from oracle import cosmology, mlp, pm, power, raymesh, rays, sim
+from oracle import cosmology, ewald, mlp, pm, power, raymesh, rays, sim
 
 _POINT_MASS = {}
 
@@ -37,6 +37,8 @@ PINS = {
     "mode_x": lambda: pm_pins.test_single_mode_poisson_gradient(0, 3),
     "mode_z": lambda: pm_pins.test_single_mode_poisson_gradient(2, 2),
     "ewald_force": pm_pins.test_pm_force_matches_periodic_direct_sum,
+    "ewald_3d": pm_pins.test_ewald_field_of_a_periodic_point_mass,
+    "ewald_2d": lens_pins.test_periodic_lensing_sum_is_independent_of_the_splitting,
     "gather_linear": pm_pins.test_gather_of_linear_field_is_exact,
     "kd_uniform": pm_pins.test_kick_drift_with_a_uniform_field,
     "growth_d2": pm_pins.test_low_k_power_grows_as_growth_factor_squared,
@@ -120,6 +122,19 @@ CASES = [
      "d2 = -3.0 / 7.0 * d1 * d1", "d2 = 3.0 / 7.0 * d1 * d1", ["lpt_eds", "lpt_dynamics"]),
     ("2LPT growth D2 with 1/7 for 3/7", pm,
      "d2 = -3.0 / 7.0 * d1 * d1", "d2 = -1.0 / 7.0 * d1 * d1", ["lpt_eds", "lpt_dynamics"]),
+    # the periodic point-mass sums that pin the PM force and the point-mass deflections (App. D)
+    ("Ewald: reciprocal part with 2 pi for 4 pi", ewald,
+     "amp = 4.0 * math.pi / box ** 3", "amp = 2.0 * math.pi / box ** 3", ["ewald_3d"]),
+    ("Ewald: real-space Gaussian term dropped", ewald,
+     "(erfc(al * s) + 2.0 * al * s / math.sqrt(math.pi) * np.exp(-(al * s) ** 2)) / s ** 3",
+     "erfc(al * s) / s ** 3", ["ewald_3d"]),
+    ("Ewald: reciprocal damping with 2 alpha^2", ewald,
+     "math.exp(-k2 / (4.0 * al * al)) / k2\n                out", "math.exp(-k2 / (2.0 * al * al)) / k2\n                out",
+     ["ewald_3d"]),
+    ("Ewald 2D: reciprocal part with 4 pi for 2 pi", ewald,
+     "amp = 2.0 * math.pi / box ** 2", "amp = 4.0 * math.pi / box ** 2", ["ewald_2d"]),
+    ("Ewald 2D: real-space damping exp(-al |b|^2)", ewald,
+     "np.exp(-al * al * s2) / s2", "np.exp(-al * s2) / s2", ["ewald_2d"]),
     # background and time integrals (Sec. 2, Sec. 3.2)
     ("Omega_m a^-2 in E(a)", cosmology,
      "om / a ** 3 + (1.0 - om)", "om / a ** 2 + (1.0 - om)", ["eds"]),

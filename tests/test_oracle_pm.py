@@ -94,6 +94,25 @@ def test_single_mode_poisson_gradient(axis, m):
             assert float(grads[j].abs().max()) < 1e-12
 
 
+def test_ewald_field_of_a_periodic_point_mass():
+    # The periodic sum, split into real- and reciprocal-space parts, is exact for any splitting parameter, so a
+    # wrong factor in either part shows as a dependence on it; near the mass the field is Newton's r / |r|^3 (the
+    # images and the background add O(|r| / L^3)); it vanishes at the half-period points and is odd in r.
+    L = 10.0
+    r = np.random.default_rng(3).uniform(-0.5, 0.5, (20, 3)) * L
+    g0 = ewald.grad_phi_3d(r, L)
+    scale = np.abs(g0).max()
+    for alpha, n_real, n_recip in ((1.5 / L, 4, 8), (3.0 / L, 3, 12)):
+        g = ewald.grad_phi_3d(r, L, n_real=n_real, n_recip=n_recip, alpha=alpha)
+        assert np.abs(g - g0).max() < 1e-12 * scale
+    near = np.array([[1e-3, 0.5e-3, -0.7e-3]]) * L
+    newton = near / np.linalg.norm(near) ** 3
+    assert np.abs(ewald.grad_phi_3d(near, L) - newton).max() < 1e-6 * np.abs(newton).max()
+    half = np.array([[L / 2, 0, 0], [0, L / 2, 0], [L / 2, L / 2, L / 2]])
+    assert np.abs(ewald.grad_phi_3d(half, L)).max() < 1e-12 * scale
+    assert np.abs(ewald.grad_phi_3d(-r, L) + g0).max() < 1e-12 * scale
+
+
 def test_pm_force_matches_periodic_direct_sum():
     # One mass in a periodic box; the PM gradient interpolated at test points 5..12 cells away agrees with the
     # 3D Ewald sum to the PM force accuracy with the 1-cell smoothing and sinc^-4 deconvolution.
