@@ -250,3 +250,43 @@ def test_context_particle_correction_is_the_stateless_solve_with_its_table(hrt):
     assert "particle force" in str(e.value)
     ctx.hrt_set_particle_correction(None)
     ctx.close()
+
+
+def test_adam_step_matches_the_textbook_update(hrt):
+    # Adam with bias correction (Kingma and Ba) in FP32 on the master weights, three steps against a plain FP32
+    # PyTorch restatement; the padding columns 3..15 of W1 stay as they were and are zero in the BF16 copy
+    n = hrt.MLP_PARAMS
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    w = torch.randn(n, device="cuda", generator=gen) * 0.2
+    w0 = w.clone()
+    m = torch.zeros(n, device="cuda")
+    v = torch.zeros(n, device="cuda")
+    wb = torch.empty(n, dtype=torch.bfloat16, device="cuda")
+    pad = torch.zeros(n, dtype=torch.bool, device="cuda")
+    pad[:64 * 16] = (torch.arange(64 * 16, device="cuda") % 16) >= 3
+    w_ref, m_ref, v_ref = w.clone(), m.clone(), v.clone()
+    lr, b1, b2, eps = 3e-3, 0.9, 0.999, 1e-8
+    # the FP32 constants of the update: beta and 1 - beta in single precision, the bias corrections formed in
+    # double and rounded once
+    f32 = lambda x: torch.tensor(x, dtype=torch.float32, device="cuda")  # noqa: E731
+    b1f, b2f = f32(b1), f32(b2)
+    for step in range(1, 4):
+        g = torch.randn(n, device="cuda", generator=gen)
+        hrt.hrt_mlp_adam(w, wb, g, m, v, lr, b1, b2, eps, step)
+        mr = b1f * m_ref + (1 - b1f) * g
+        vr = b2f * v_ref + (1 - b2f) * g * g
+        c1, c2 = f32(1 - b1 ** step), f32(1 - b2 ** step)
+        upd = w_ref - f32(lr) * (mr / c1) / (torch.sqrt(vr / c2) + f32(eps))
+        w_ref = torch.where(pad, w_ref, upd)
+        m_ref = torch.where(pad, m_ref, mr)
+        v_ref = torch.where(pad, v_ref, vr)
+    torch.cuda.synchronize()
+    assert torch.allclose(w, w_ref, rtol=1e-6, atol=1e-7)
+    # the kernel may contract b m + (1 - b) g into one FMA: where the terms cancel, the moments differ by a few
+    # ulps of the terms ((1 - b1) |g| < 0.5, (1 - b2) g^2 < 0.02), not of the result
+    assert torch.allclose(m, m_ref, rtol=1e-6, atol=1e-7) and torch.allclose(v, v_ref, rtol=1e-6, atol=1e-8)
+    assert torch.equal(wb[~pad], w[~pad].to(torch.bfloat16))
+    assert float(wb[pad].float().abs().max()) == 0.0
+    # Adam moves a weight by at most about lr per step (|m_hat| / sqrt(v_hat) <= 1.0012 here)
+    moved = (w - w0)[~pad].abs()
+    assert 0.5 * lr < float(moved.max()) <= 3.1 * lr
