@@ -42,6 +42,7 @@ PINS = {
     "gather_linear": pm_pins.test_gather_of_linear_field_is_exact,
     "kd_uniform": pm_pins.test_kick_drift_with_a_uniform_field,
     "growth_d2": pm_pins.test_low_k_power_grows_as_growth_factor_squared,
+    "fwd_rev": pm_pins.test_forward_then_reverse_returns_to_initial_conditions,
     "zeldovich": pm_pins.test_zeldovich_momentum_ratio_and_power,
     "zeldovich_sign": pm_pins.test_zeldovich_density_has_the_sign_of_the_linear_field,
     "lpt_diagonal": lambda: pm_pins.test_lpt_plane_wave_along_a_diagonal_has_no_second_order_term((1, -1, 1)),
@@ -122,6 +123,22 @@ CASES = [
      "d2 = -3.0 / 7.0 * d1 * d1", "d2 = 3.0 / 7.0 * d1 * d1", ["lpt_eds", "lpt_dynamics"]),
     ("2LPT growth D2 with 1/7 for 3/7", pm,
      "d2 = -3.0 / 7.0 * d1 * d1", "d2 = -1.0 / 7.0 * d1 * d1", ["lpt_eds", "lpt_dynamics"]),
+    # the particle leapfrog of the N-body driver (one force per step, Alg. 1)
+    ("kick to the end of the step instead of its middle", sim,
+     "kick = cosmo.kick_integral(part.a_p, a_half, om)", "kick = cosmo.kick_integral(part.a_p, a_next, om)",
+     ["growth_d2", "fwd_rev"]),
+    ("drift from the momentum time", sim,
+     "drift = cosmo.drift_integral(part.a_x, a_next, om)", "drift = cosmo.drift_integral(part.a_p, a_next, om)",
+     ["growth_d2", "fwd_rev"]),
+    ("Poisson prefactor times a instead of over a", sim,
+     "grads = pm_force(part, box, n_mesh, 1.5 * om / a_next, flt)\n    part = particle_sync",
+     "grads = pm_force(part, box, n_mesh, 1.5 * om * a_next, flt)\n    part = particle_sync", ["growth_d2"]),
+    ("synchronising kick stopped at the half step", sim,
+     "kick = cosmo.kick_integral(part.a_p, part.a_x, om)",
+     "kick = cosmo.kick_integral(part.a_p, 0.5 * (part.a_p + part.a_x), om)", ["fwd_rev"]),
+    ("momentum time not advanced", sim,
+     "return Particles(part.q, disp, mom, a_next, a_half)", "return Particles(part.q, disp, mom, a_next, part.a_p)",
+     ["growth_d2", "fwd_rev"]),
     # the periodic point-mass sums that pin the PM force and the point-mass deflections (App. D)
     ("Ewald: reciprocal part with 2 pi for 4 pi", ewald,
      "amp = 4.0 * math.pi / box ** 3", "amp = 2.0 * math.pi / box ** 3", ["ewald_3d"]),
