@@ -1,5 +1,6 @@
-"""CPU checks of the C-ABI library: it loads, exports every declared symbol, and its host-only FP64 cosmology
-matches the oracle.  No GPU compute is called here."""
+"""CPU checks of the C-ABI library: it loads, exports every declared symbol, and its host-only FP64 tables (the
+cosmology, a ray step's nodes and weights, the Zel'dovich transfer, the static prefactor) match the oracle.  No
+GPU compute is called here."""
 import ctypes
 import os
 import re
@@ -118,3 +119,75 @@ def test_host_raymesh_geometry_matches_oracle(lib):
             lib.RayMesh(lib.make_raymesh_config(*bad))
     with pytest.raises(lib.HRTError):   # an 8192^2 mesh against a limit of 1024
         lib.hrt_raymesh_geometry(lib.make_raymesh_config(0.5, 8, 1e-3, 4096, 1024), 1000.0, 1010.0, 2.0)
+
+
+def test_host_ray_step_table_matches_oracle(lib):
+    # the FP64 node table of one ray step (Alg. 1: two half shells of midpoint nodes, the kick weights of Eq. "kick"
+    # with its growth time correction, the drift coefficient of Eq. "drift"), either orientation, with and without a
+    # window, against the oracle's nodes and weights
+    import numpy as np
+    from oracle import cosmology as oc
+    from oracle import rays as orays
+    from oracle import sim as osim
+    from oracle.units import C_LIGHT
+    om = 0.3
+    g = lib.hrt_ray_geom()
+    g.n, g.box = 32, 64.0
+    g.observer[0], g.observer[1], g.observer[2] = 19.2, 38.4, 0.0
+    g.samples_per_cell = 1.5
+    cell = g.box / g.n
+    cases = ((100.0, 160.0, False, None), (160.0, 100.0, False, None), (800.0, 870.5, True, None),
+             (1500.0, 1400.0, True, None), (800.0, 870.5, True, (815.0, 850.0)))
+    for chi_a, chi_b, expanding, window in cases:
+        g.window_lo, g.window_hi = window if window else (-1e300, 1e300)
+        a_ref = oc.a_of_chi(chi_a, om) if expanding else 0.0
+        n1, n2, cw, cwr, chi, d = lib.hrt_ray_step_coefficients(g, chi_a, chi_b, a_ref, om)
+        weight = osim.growth_weight(a_ref, om) if expanding else (lambda c: 1.0)
+        chi_h = 0.5 * (chi_a + chi_b)
+        want_n, want_chi, want_cw = [], [], []
+        for lo, hi in ((chi_a, chi_h), (chi_h, chi_b)):
+            nodes, h = orays.half_shell_nodes(lo, hi, g.samples_per_cell, cell)
+            kept = [c for c in nodes if window is None or window[0] <= c < window[1]]
+            want_n.append(len(kept))
+            want_chi += kept
+            want_cw += [-(2.0 / C_LIGHT) * h * c * weight(c) for c in kept]
+        assert (n1, n2) == tuple(want_n)
+        if window:
+            # the window drops nodes of both half shells but keeps some
+            full = [len(orays.half_shell_nodes(lo, hi, g.samples_per_cell, cell)[0])
+                    for lo, hi in ((chi_a, chi_h), (chi_h, chi_b))]
+            assert 0 < n1 < full[0] and 0 < n2 < full[1]
+        want_chi, want_cw = np.array(want_chi), np.array(want_cw)
+        np.testing.assert_allclose(chi, want_chi, rtol=1e-14)
+        np.testing.assert_allclose(cw, want_cw, rtol=1e-9 if expanding else 1e-14)
+        np.testing.assert_allclose(cwr, want_cw * want_chi / cell, rtol=1e-9 if expanding else 1e-14)
+        assert d == pytest.approx((chi_b - chi_a) / (C_LIGHT * chi_h * chi_h), rel=1e-14)
+
+
+def test_host_ic_table_matches_oracle(lib):
+    # the Zel'dovich transfer per integer |n|^2, D1 sqrt(P(k) / V_cell) / k^2 / n_side^3 (0 at n = 0), and the
+    # momentum ratio a^2 E f, against the oracle's cosmology
+    import numpy as np
+    from oracle import cosmology as oc
+    n, box, a = 16, 200.0, 0.05
+    om, h, ns, s8 = 0.3, 0.7, 0.96, 0.8
+    t, ratio = lib.hrt_ic_table(n, box, om, h, ns, s8, a)
+    assert t.size == 3 * (n // 2) ** 2 + 1
+    n2 = np.arange(t.size, dtype=np.float64)
+    k = 2.0 * np.pi * np.sqrt(n2) / box
+    pk = oc.linear_power(k, om, h, ns, oc.power_amplitude(om, h, ns, s8))
+    want = np.zeros_like(t)
+    want[1:] = oc.growth_D1(a, om) * np.sqrt(pk[1:] / (box / n) ** 3) / k[1:] ** 2 / n ** 3
+    assert t[0] == 0.0
+    np.testing.assert_allclose(t, want, rtol=1e-8)
+    assert ratio == pytest.approx(a * a * oc.E(a, om) * oc.growth_f(a, om), rel=1e-10)
+
+
+def test_host_static_prefactor(lib):
+    import math
+    from oracle.units import G_NEWTON
+    assert lib.hrt_static_prefactor(1e15, 200.0) == pytest.approx(4 * math.pi * G_NEWTON * 1e15 / 200.0 ** 3,
+                                                                   rel=1e-14)
+    for mass, box in ((0.0, 200.0), (-1.0, 200.0), (1e15, 0.0), (float("nan"), 200.0), (1e15, float("inf"))):
+        with pytest.raises(lib.HRTError):
+            lib.hrt_static_prefactor(mass, box)
