@@ -18,8 +18,6 @@ import test_oracle_raymesh as rm_pins
 import test_oracle_rays as ray_pins
 from oracle import cosmology, ewald, mlp, pm, power, raymesh, rays, sim
 
-_POINT_MASS = {}
-
 
 def _point_mass_pins():
     # the point-mass pins on every eighth of their rays (16 rays from 0.1 to 20 cells)
