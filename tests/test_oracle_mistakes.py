@@ -59,6 +59,7 @@ PINS = {
     "free_drift": ray_pins.test_free_drift_is_exact_for_constant_momentum,
     "point_mass": _point_mass_pins,
     "power_mode": lens_pins.test_power_of_single_cosine_mode,
+    "kick_snapshot": lens_pins.test_reverse_run_refers_the_ray_kick_to_the_force_snapshot,
     "power_edges": lens_pins.test_bin_edges_put_exact_edge_modes_in_upper_bin,
     "mlp_chain": mlp_pins.test_a_chain_network_is_silu_three_times,
     "mlp_silu": mlp_pins.test_silu_values,
@@ -134,6 +135,9 @@ CASES = [
     ("synchronising kick stopped at the half step", sim,
      "kick = cosmo.kick_integral(part.a_p, part.a_x, om)",
      "kick = cosmo.kick_integral(part.a_p, 0.5 * (part.a_p + part.a_x), om)", ["fwd_rev"]),
+    ("ray kick's growth correction referred to the end of the step", sim,
+     "samples_per_cell,\n                                  growth_weight(a_n, om), gz=grads[2]",
+     "samples_per_cell,\n                                  growth_weight(a_n1, om), gz=grads[2]", ["kick_snapshot"]),
     ("momentum time not advanced", sim,
      "return Particles(part.q, disp, mom, a_next, a_half)", "return Particles(part.q, disp, mom, a_next, part.a_p)",
      ["growth_d2", "fwd_rev"]),
